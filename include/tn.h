@@ -1,0 +1,191 @@
+/*
+ * libtn: sliced big-head tensor-network contraction on one GB300 (sm_103a).
+ *
+ * The operation (Pan & Zhang, "Simulating the Sycamore quantum supremacy
+ * circuits", arXiv:2103.03074): a quantum circuit is a tensor network of bond
+ * dimension 2 ("Big-head simulation" section, Fig. 1).  Some output qubits are
+ * left open, the others are closed on a fixed bitstring s1, so one contraction
+ * yields the 2^k amplitudes <s1; s2|U|0> for every assignment s2 of the k open
+ * qubits.  A set of n_e bond labels is sliced ("Dynamic slicing" paragraph of
+ * the appendix): slice id s holds sliced label j at bit j of s, every slice
+ * runs the same pairwise contraction tree (Fig. 3: a pair sharing n_AB labels
+ * with n_A, n_B outer labels costs 2^{n_A+n_B+n_AB} complex multiply-adds),
+ * and the 2^{n_e} slice results sum to the full contraction.
+ *
+ * Conventions shared by every call:
+ *  - Bond dimension is 2 for every label.  A tensor of rank r holds 2^r
+ *    complex values; its first label is the most significant axis
+ *    (row-major, like a C-ordered numpy array of shape (2,)*r).
+ *  - Complex values are interleaved (re, im).
+ *  - Labels are non-negative int32.  Every label is held by at most two
+ *    tensors and at most once per tensor; a label held by one tensor must be
+ *    open.
+ *  - The amplitude tensor over the open labels has the open labels in the
+ *    given order, first = most significant bit of the flat index.
+ *  - Return value 0 = success; negative = error (TN_ERR_*), with a message
+ *    for the calling thread in tn_last_error().
+ *  - Device pointers are CUDA device memory of the current device; calls are
+ *    ordered on the given stream (0 = legacy default stream).
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tn_plan *tn_plan_t; /* opaque, owned by the library */
+typedef struct CUstream_st *tn_stream_t; /* a cudaStream_t */
+
+enum {
+    TN_OK = 0,
+    TN_ERR_ARG = -1,     /* bad labels, non-binary tree, sliced label that is open, ... */
+    TN_ERR_OOM = -2,     /* device memory for the plan's arena cannot be had */
+    TN_ERR_CUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    TN_ERR_TIMEOUT = -4, /* a bounded device-side wait expired */
+    TN_ERR_STATE = -5    /* call made on a plan in a failed state */
+};
+
+/* Arithmetic form of the pairwise contractions (the cross-slice sum and the
+ * probability reduction are FP64 in every form). */
+typedef enum {
+    TN_FP32 = 0,   /* complex64 operands, FP32 CUDA-core complex products (reference form) */
+    TN_BF16X3 = 1, /* operands split into bf16 hi/lo, three products per real product, tensor cores, FP32 accumulate */
+    TN_TF32X3 = 2, /* tf32 hi/lo split, three products per real product, tensor cores */
+    TN_FP16S = 3   /* fp16 with per-tensor power-of-two scale, tensor cores */
+} tn_form;
+
+typedef struct {
+    /* slices executed together: 2^batch_log2 consecutive slice ids run as one
+     * pass with the low sliced labels kept as batch labels; -1 = choose from
+     * the memory budget */
+    int32_t batch_log2;
+    /* device bytes the plan may hold (arena + leaves); 0 = 60% of free memory */
+    int64_t mem_budget;
+    /* record per-step CUDA-event timings on every call (profiling mode) */
+    int32_t profile;
+    /* capture each slice batch into a CUDA graph and replay it */
+    int32_t use_graph;
+    /* reserved, set to 0 */
+    int32_t reserved[8];
+} tn_plan_opts;
+
+/* Order search options (host-side planning). */
+typedef struct {
+    int32_t trials;     /* randomised greedy trials (default 256) */
+    uint64_t seed;      /* seed of the search's SplitMix64 stream */
+    int32_t log2_cap;   /* slice until every intermediate has <= 2^log2_cap elements (-1: no cap) */
+    int32_t n_sliced;   /* slice exactly this many labels (-1: as the cap needs) */
+    int32_t threads;    /* host threads (0 = hardware concurrency) */
+    int32_t reserved[7];
+} tn_search_opts;
+
+/* A circuit: gate g acts on gate_nq[g] (1 or 2) qubits gate_q[2g], gate_q[2g+1]
+ * with the row-major 2^k x 2^k complex matrix at gate_m[32 g ...] (interleaved
+ * re/im; 8 or 32 doubles used).  Qubit 0 is the first character of a
+ * bitstring.  The initial state is |0...0>. */
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_gates;
+    const int32_t *gate_nq;
+    const int32_t *gate_q;
+    const double *gate_m;
+} tn_circuit;
+
+/*
+ * Build a plan for the sliced contraction of a tensor network
+ * ("Dynamic slicing" paragraph; Fig. 3 pairwise steps).
+ *   ranks[n_tensors]            rank of each tensor
+ *   labels[sum ranks]           concatenated label lists (host)
+ *   data[2 * sum 2^rank]        concatenated interleaved complex64 values (host, copied)
+ *   n_labels, bond_dims         bond_dims[label] must be 2 for every label used (may be NULL)
+ *   open_labels[n_open]         amplitude-tensor axis order, [0] = MSB
+ *   sliced_labels[n_sliced]     slice id bit j -> sliced_labels[j]; must not be open
+ *   tree[2 * n_steps]           n_steps = n_tensors - 1 pairs (i, j) of SSA node ids:
+ *                               leaves are 0..n_tensors-1, step t makes node n_tensors + t
+ * All host arrays are copied; the plan owns its device memory.
+ * Errors: TN_ERR_ARG (malformed input), TN_ERR_OOM, TN_ERR_CUDA.
+ */
+int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *ranks, const int32_t *labels,
+                   const float *data, int n_labels, const int32_t *bond_dims, int n_open,
+                   const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels,
+                   int n_steps, const int32_t *tree, tn_form form, const tn_plan_opts *opts);
+
+/*
+ * Contract slices [slice_begin, slice_end) and ADD their sum into d_amp
+ * (device, complex128 interleaved, 2^n_open entries, caller-owned).  Additive,
+ * so ranges compose; an empty range adds nothing.  The range must lie in
+ * [0, 2^n_sliced).  Stream-ordered on `stream`; the call returns after
+ * enqueueing (no host synchronisation) unless profiling is on.
+ * Errors: TN_ERR_ARG (range), TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_STATE.
+ */
+int tn_contract_slices(tn_plan_t plan, int64_t slice_begin, int64_t slice_end, double *d_amp,
+                       tn_stream_t stream);
+
+/*
+ * Amplitudes of a circuit over its open qubits (the big-head problem of the
+ * "Big-head simulation" section): build the network (single-qubit gates
+ * absorbed into two-qubit gates, boundary vectors absorbed), search an order
+ * and a slice set (search may be NULL for defaults), plan, contract every
+ * slice and OVERWRITE d_amp (device complex128, 2^n_open entries).
+ *   fixed_bits[n_qubits]   the closed bits s1 (entries at open positions ignored)
+ *   open_qubits[n_open]    amplitude axis order, [0] = MSB
+ * Synchronises `stream` before returning.
+ */
+int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bits, int n_open,
+                  const int32_t *open_qubits, tn_form form, const tn_search_opts *search,
+                  const tn_plan_opts *opts, double *d_amp, tn_stream_t stream);
+
+/*
+ * Probabilities and linear XEB (Eq. 1) of an amplitude tensor on the device, in
+ * FP64: writes d_prob[i] = |amp_i|^2 (may be NULL) and, to host out[3]:
+ * out[0] = sum_i p_i (the marginal P(s1)), out[1] = F_XEB = 2^n_qubits / L *
+ * sum p - 1 with L = 2^n_open, out[2] = max p.  Synchronises `stream`.
+ */
+int tn_probabilities_xeb(const double *d_amp, int n_open, int n_qubits, double *d_prob,
+                         double *out, tn_stream_t stream);
+
+void tn_plan_destroy(tn_plan_t plan);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *tn_last_error(void);
+
+/*
+ * Host-side order search (first pairwise order, then slicing): randomised
+ * greedy trials scored by the Fig. 3 cost 2^{n_A+n_B+n_AB} summed over steps,
+ * then greedy slicing to the cap or count.  Writes the tree (2*(n_tensors-1)
+ * SSA ids), the sliced labels (up to max_sliced) and stats[4] =
+ * {log2 total MACs over all slices, log2 largest intermediate per slice,
+ *  n_sliced, log2 MACs per slice}.
+ */
+int tn_find_order(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                  const int32_t *open_labels, const tn_search_opts *opts, int32_t *out_tree,
+                  int max_sliced, int32_t *out_sliced, int *out_n_sliced, double *stats);
+
+/*
+ * The network tn_amplitudes contracts for a circuit (gate absorption and
+ * boundary vectors applied), with bonds named by the wire-segment convention:
+ * the segment after the t-th gate on qubit q is label offset_q + t,
+ * offset_q = sum_{q'<q} (gates on q' + 1).  Two calls: first with
+ * out_data == NULL to get *n_tensors and *total_rank, then with buffers of
+ * ranks[n_tensors], labels[total_rank], data[2 * sum 2^rank] (complex64),
+ * open_labels[n_open].
+ */
+int tn_circuit_network(const tn_circuit *circuit, const uint8_t *fixed_bits, int n_open,
+                       const int32_t *open_qubits, int *n_tensors, int *total_rank,
+                       int64_t *total_elems, int32_t *ranks, int32_t *labels, float *out_data,
+                       int32_t *open_labels);
+
+/* Per-plan statistics: out[0] MACs per slice batch, out[1] slices per batch,
+ * out[2] arena bytes, out[3] number of steps, out[4] kernel launches per
+ * batch, out[5] algorithmic HBM bytes per batch, out[6] MACs of the
+ * slice-invariant prologue (computed once per plan). */
+int tn_plan_stats(tn_plan_t plan, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

@@ -1,0 +1,238 @@
+"""Python binding of libtn (include/tn.h): argument marshalling only.
+
+Every step of the contraction runs in the library's CUDA kernels; PyTorch is
+used by callers only for device memory and streams.  Importing this package
+loads ``libtn.so`` built in place by ``build.py``; a missing library is an
+ImportError, never a silent fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtn.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libtn.so is not built ({LIB_PATH}); run `python -m paper_2103_03074_gb300.build` "
+                      "or __graft_entry__.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+TN_FP32, TN_BF16X3, TN_TF32X3, TN_FP16S = 0, 1, 2, 3
+FORMS = {"fp32": TN_FP32, "bf16x3": TN_BF16X3, "tf32x3": TN_TF32X3, "fp16s": TN_FP16S}
+ERRORS = {-1: "TN_ERR_ARG", -2: "TN_ERR_OOM", -3: "TN_ERR_CUDA", -4: "TN_ERR_TIMEOUT", -5: "TN_ERR_STATE"}
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("batch_log2", _i32), ("mem_budget", _i64), ("profile", _i32), ("use_graph", _i32),
+                ("reserved", _i32 * 8)]
+
+
+class SearchOpts(ctypes.Structure):
+    _fields_ = [("trials", _i32), ("seed", ctypes.c_uint64), ("log2_cap", _i32), ("n_sliced", _i32),
+                ("threads", _i32), ("reserved", _i32 * 7)]
+
+
+class Circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", _i32), ("n_gates", _i32), ("gate_nq", _vp), ("gate_q", _vp), ("gate_m", _vp)]
+
+
+_lib.tn_last_error.restype = ctypes.c_char_p
+_lib.tn_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int,
+                                _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(PlanOpts)]
+_lib.tn_contract_slices.argtypes = [_vp, _i64, _i64, _vp, _vp]
+_lib.tn_amplitudes.argtypes = [ctypes.POINTER(Circuit), _vp, ctypes.c_int, _vp, ctypes.c_int,
+                               ctypes.POINTER(SearchOpts), ctypes.POINTER(PlanOpts), _vp, _vp]
+_lib.tn_probabilities_xeb.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+_lib.tn_plan_destroy.argtypes = [_vp]
+_lib.tn_plan_destroy.restype = None
+_lib.tn_find_order.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(SearchOpts), _vp,
+                               ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int), _vp]
+_lib.tn_circuit_network.argtypes = [ctypes.POINTER(Circuit), _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]
+_lib.tn_plan_stats.argtypes = [_vp, _vp]
+
+EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabilities_xeb", "tn_plan_destroy",
+            "tn_last_error", "tn_find_order", "tn_circuit_network", "tn_plan_stats"]
+
+
+class TNError(RuntimeError):
+    def __init__(self, code, where):
+        msg = _lib.tn_last_error().decode()
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise TNError(rc, where)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_vp) if a is not None else None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return _vp(stream.cuda_stream)
+    return _vp(int(stream))
+
+
+def _dev_ptr(t):
+    return _vp(t.data_ptr())
+
+
+def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads=0):
+    return SearchOpts(trials, seed, log2_cap, n_sliced, threads)
+
+
+def plan_opts(batch_log2=-1, mem_budget=0, profile=0, use_graph=0):
+    return PlanOpts(batch_log2, mem_budget, profile, use_graph)
+
+
+def marshal_circuit(circuit):
+    """tn_inputs.Circuit -> (ctypes Circuit, keep-alive arrays)."""
+    gates = circuit.gates
+    ng = len(gates)
+    nq = np.array([len(g.qubits) for g in gates], dtype=np.int32)
+    qs = np.zeros(2 * ng, dtype=np.int32)
+    ms = np.zeros(32 * ng, dtype=np.float64)
+    for i, g in enumerate(gates):
+        for j, q in enumerate(g.qubits):
+            qs[2 * i + j] = q
+        m = np.asarray(g.matrix, dtype=np.complex128).reshape(-1)
+        ms[32 * i:32 * i + 2 * m.size:2] = m.real
+        ms[32 * i + 1:32 * i + 2 * m.size:2] = m.imag
+    keep = (nq, qs, ms)
+    return Circuit(circuit.n_qubits, ng, _ptr(nq), _ptr(qs), _ptr(ms)), keep
+
+
+def circuit_network(circuit, fixed_bits, open_qubits):
+    """The network tn_amplitudes contracts: (labels list, complex64 tensors, open labels)."""
+    c, keep = marshal_circuit(circuit)
+    fb = np.asarray(fixed_bits, dtype=np.uint8)
+    oq = np.asarray(open_qubits, dtype=np.int32)
+    nt, tr, te = ctypes.c_int(), ctypes.c_int(), _i64()
+    _check(_lib.tn_circuit_network(ctypes.byref(c), _ptr(fb), len(oq), _ptr(oq), ctypes.byref(nt), ctypes.byref(tr),
+                                   ctypes.byref(te), None, None, None, None), "tn_circuit_network")
+    ranks = np.zeros(nt.value, np.int32)
+    labs = np.zeros(max(tr.value, 1), np.int32)
+    data = np.zeros(2 * te.value, np.float32)
+    ol = np.zeros(max(len(oq), 1), np.int32)
+    _check(_lib.tn_circuit_network(ctypes.byref(c), _ptr(fb), len(oq), _ptr(oq), ctypes.byref(nt), ctypes.byref(tr),
+                                   ctypes.byref(te), _ptr(ranks), _ptr(labs), _ptr(data), _ptr(ol)),
+           "tn_circuit_network")
+    labels, tensors = [], []
+    lo = do = 0
+    for r in ranks:
+        labels.append([int(x) for x in labs[lo:lo + r]])
+        lo += r
+        size = 1 << int(r)
+        v = data[do:do + 2 * size]
+        do += 2 * size
+        tensors.append((v[0::2] + 1j * v[1::2]).astype(np.complex64).reshape((2,) * int(r)))
+    return labels, tensors, [int(x) for x in ol[:len(oq)]]
+
+
+def _flatten(labels, tensors):
+    ranks = np.array([len(l) for l in labels], dtype=np.int32)
+    flat = np.array([x for l in labels for x in l] or [0], dtype=np.int32)
+    parts = []
+    for t in tensors:
+        c = np.asarray(t, dtype=np.complex64).reshape(-1)
+        parts.append(np.stack([c.real, c.imag], axis=1).reshape(-1))
+    data = np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
+    return ranks, flat, data
+
+
+def find_order(labels, open_labels, opts=None, max_sliced=64):
+    """(tree [(a, b), ...], sliced labels, stats dict) from the library's order search."""
+    ranks, flat, _ = _flatten(labels, [np.zeros((2,) * len(l), np.complex64) for l in labels])
+    ol = np.asarray(open_labels or [0], dtype=np.int32)
+    n = len(labels)
+    tree = np.zeros(max(2 * (n - 1), 1), np.int32)
+    sl = np.zeros(max_sliced, np.int32)
+    nsl = ctypes.c_int()
+    st = np.zeros(4)
+    o = opts if opts is not None else search_opts()
+    _check(_lib.tn_find_order(n, _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol), ctypes.byref(o), _ptr(tree),
+                              max_sliced, _ptr(sl), ctypes.byref(nsl), _ptr(st)), "tn_find_order")
+    steps = [(int(tree[2 * i]), int(tree[2 * i + 1])) for i in range(n - 1)]
+    stats = dict(log2_total=st[0], log2_width=st[1], n_sliced=int(st[2]), log2_slice=st[3])
+    return steps, [int(x) for x in sl[:nsl.value]], stats
+
+
+class Plan:
+    """A compiled sliced contraction (tn_plan_create); owns its device memory."""
+
+    def __init__(self, labels, tensors, open_labels, sliced_labels, tree, form="fp32", opts=None):
+        ranks, flat, data = _flatten(labels, tensors)
+        ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
+        sl = np.asarray(list(sliced_labels) or [0], dtype=np.int32)
+        tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
+        self.n_open = len(open_labels)
+        self.n_sliced = len(sliced_labels)
+        self.form = FORMS[form] if isinstance(form, str) else int(form)
+        h = _vp()
+        o = opts if opts is not None else plan_opts()
+        _check(_lib.tn_plan_create(ctypes.byref(h), len(labels), _ptr(ranks), _ptr(flat), _ptr(data), 0, None,
+                                   len(open_labels), _ptr(ol), len(sliced_labels), _ptr(sl), len(tree), _ptr(tr),
+                                   self.form, ctypes.byref(o)), "tn_plan_create")
+        self._h = h
+
+    def contract(self, begin, end, d_amp, stream=None):
+        """Add the sum of slices [begin, end) into d_amp (device complex128 tensor)."""
+        _check(_lib.tn_contract_slices(self._h, int(begin), int(end), _dev_ptr(d_amp), _stream_ptr(stream)),
+               "tn_contract_slices")
+
+    def contract_ptr(self, begin, end, d_amp_ptr, stream_ptr=None):
+        _check(_lib.tn_contract_slices(self._h, int(begin), int(end), _vp(d_amp_ptr),
+                                       _vp(stream_ptr) if stream_ptr else None), "tn_contract_slices")
+
+    def stats(self):
+        out = np.zeros(16)
+        _check(_lib.tn_plan_stats(self._h, _ptr(out)), "tn_plan_stats")
+        keys = ["macs_batch", "slices_per_batch", "arena_bytes", "n_steps", "launches_batch", "bytes_batch",
+                "macs_prologue", "bytes_prologue", "launches_prologue", "batch_log2"]
+        return {k: float(out[i]) for i, k in enumerate(keys)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tn_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def amplitudes(circuit, fixed_bits, open_qubits, d_amp, form="fp32", search=None, opts=None, stream=None):
+    """tn_amplitudes: overwrite d_amp (device complex128, 2^k) with the circuit's amplitudes."""
+    c, keep = marshal_circuit(circuit)
+    fb = np.asarray(fixed_bits, dtype=np.uint8)
+    oq = np.asarray(list(open_qubits) or [0], dtype=np.int32)
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    so = search if search is not None else search_opts()
+    po = opts if opts is not None else plan_opts()
+    _check(_lib.tn_amplitudes(ctypes.byref(c), _ptr(fb), len(open_qubits), _ptr(oq), f, ctypes.byref(so),
+                              ctypes.byref(po), _dev_ptr(d_amp), _stream_ptr(stream)), "tn_amplitudes")
+
+
+def probabilities_xeb(d_amp, n_open, n_qubits, d_prob=None, stream=None):
+    """(marginal P(s1), linear XEB, max p) of a device amplitude tensor; fills d_prob if given."""
+    out = np.zeros(3)
+    _check(_lib.tn_probabilities_xeb(_dev_ptr(d_amp), n_open, n_qubits,
+                                     _dev_ptr(d_prob) if d_prob is not None else None, _ptr(out),
+                                     _stream_ptr(stream)), "tn_probabilities_xeb")
+    return float(out[0]), float(out[1]), float(out[2])

@@ -1,0 +1,336 @@
+// CUDA kernels of the plain FP32 form of the sliced contraction, plus the
+// slice extraction, cross-slice FP64 sum and probability/XEB reductions.
+//
+// Every tensor has bond dimension 2 on every axis, so an element address is a
+// bit string: each label owns one bit position.  Index maps are therefore bit
+// scatters and gathers, computed in registers.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 16;  // grid-stride cap: 16 resident CTAs x 152 SMs
+
+__device__ __forceinline__ uint64_t insert_zeros(uint64_t x, const int *pos, int n) {
+    // pos ascending, in final coordinates
+    for (int i = 0; i < n; i++) {
+        int p = pos[i];
+        uint64_t lo = x & ((1ull << p) - 1);
+        x = ((x >> p) << (p + 1)) | lo;
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint64_t scatter_bits(uint64_t v, const int *pos, int n) {
+    uint64_t r = 0;
+    for (int j = 0; j < n; j++) r |= ((v >> j) & 1ull) << pos[j];
+    return r;
+}
+
+__device__ __forceinline__ uint32_t gather_bits(uint64_t v, const int *bit, int n) {
+    uint32_t r = 0;
+    for (int j = 0; j < n; j++) r |= (uint32_t)((v >> bit[j]) & 1ull) << j;
+    return r;
+}
+
+__device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+int grid_for(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    if (b > kMaxBlocks) b = kMaxBlocks;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------- small step
+template <bool kRegT>
+__global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
+    const int SS = HS * KS * NS;
+    float2 *S_sm = reinterpret_cast<float2 *>(smem);
+    uint32_t *offT = reinterpret_cast<uint32_t *>(S_sm + SS);
+    uint32_t *offC = offT + KS;
+    for (int idx = threadIdx.x; idx < SS; idx += blockDim.x) {
+        uint32_t n = idx & (NS - 1), k = (idx >> a.nN) & (KS - 1), h = idx >> (a.nN + a.nK);
+        uint64_t addr = scatter_bits(h, a.hposS, a.nH) | scatter_bits(k, a.kposS, a.nK) |
+                        scatter_bits(n, a.nposS, a.nN);
+        S_sm[idx] = a.S[addr];
+    }
+    for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = (uint32_t)scatter_bits(k, a.kposT, a.nK);
+    for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = (uint32_t)scatter_bits(n, a.nposC, a.nN);
+    __syncthreads();
+    const int NC = NS < 8 ? NS : 8;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t tb = insert_zeros((uint64_t)r, a.tins, a.n_tins);
+        const uint64_t cb = insert_zeros((uint64_t)r, a.cins, a.n_cins);
+        const uint32_t h = gather_bits((uint64_t)r, a.hbitR, a.nH);
+        const float2 *Sh = S_sm + (size_t)h * KS * NS;
+        if (kRegT) {
+            float2 t[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                if (k < KS) t[k] = a.T[tb + offT[k]];
+            for (int n0 = 0; n0 < NS; n0 += NC) {
+                float2 acc[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 16; k++) {
+                    if (k < KS) {
+#pragma unroll
+                        for (int j = 0; j < 8; j++)
+                            if (j < NC) cfma(acc[j], t[k], Sh[k * NS + n0 + j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (j < NC) a.C[cb + offC[n0 + j]] = acc[j];
+            }
+        } else {
+            for (int n0 = 0; n0 < NS; n0 += NC) {
+                float2 acc[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[j] = make_float2(0.f, 0.f);
+                for (int k = 0; k < KS; k++) {
+                    const float2 t = a.T[tb + offT[k]];
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        if (j < NC) cfma(acc[j], t, Sh[k * NS + n0 + j]);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (j < NC) a.C[cb + offC[n0 + j]] = acc[j];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ permute
+__global__ void __launch_bounds__(kThreads) permute_kernel(const PermuteArgs a) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < a.n; o += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t src = 0;
+        for (int p = 0; p < a.rank; p++) src |= (((uint64_t)o >> p) & 1ull) << a.ipos[p];
+        a.out[o] = a.in[src];
+    }
+}
+
+// --------------------------------------------------------------- FP32 GEMM
+// 64 x 64 output tile per CTA, 256 threads, each 4 x 4 complex outputs,
+// K staged through shared memory 16 at a time.
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmArgs a) {
+    __shared__ float2 As[BK][BM + 1];
+    __shared__ float2 Bs[BK][BN + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    for (int64_t h = blockIdx.z; h < a.H; h += gridDim.z) {
+        const float2 *Ab = a.A + h * a.sAh;
+        const float2 *Bb = a.B + h * a.sBh;
+        float2 acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+        const bool a_kfast = a.sAk == 1, b_nfast = a.sBn == 1;
+        for (int64_t k0 = 0; k0 < a.K; k0 += BK) {
+#pragma unroll
+            for (int i = 0; i < (BM * BK) / 256; i++) {
+                int e = tid + i * 256;
+                int kk, mm;
+                if (a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+                int64_t m = m0 + mm, k = k0 + kk;
+                As[kk][mm] = (m < a.M && k < a.K) ? Ab[m * a.sAm + k * a.sAk] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < (BN * BK) / 256; i++) {
+                int e = tid + i * 256;
+                int kk, nn;
+                if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+                int64_t n = n0 + nn, k = k0 + kk;
+                Bs[kk][nn] = (n < a.N && k < a.K) ? Bb[k * a.sBk + n * a.sBn] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; kk++) {
+                float2 av[4], bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; j++) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) cfma(acc[i][j], av[i], bv[j]);
+            }
+            __syncthreads();
+        }
+        float2 *Cb = a.C + h * a.sCh;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int64_t m = m0 + ty + 16 * i;
+            if (m >= a.M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                int64_t n = n0 + tx + 16 * j;
+                if (n < a.N) Cb[m * a.sCm + n * a.sCn] = acc[i][j];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------- slice extraction
+__global__ void __launch_bounds__(kThreads) extract_kernel(const ExtractEntry *e, int n_entries,
+                                                           uint64_t slice_base) {
+    const ExtractEntry &x = e[blockIdx.y];
+    uint64_t fixed = 0;
+    for (int f = 0; f < x.nf; f++) fixed |= ((slice_base >> x.sbit[f]) & 1ull) << x.fpos[f];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < x.n_out; j += gridDim.x * blockDim.x)
+        x.dst[j] = x.src[insert_zeros((uint64_t)j, x.fpos_sorted, x.nf) | fixed];
+}
+
+// ------------------------------------------------------ cross-slice FP64 sum
+__global__ void __launch_bounds__(kThreads) accum_warp_kernel(const AccumArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_out = 1ll << a.n_open;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t o = warp; o < n_out; o += n_warps) {
+        const uint64_t ob = scatter_bits((uint64_t)o, a.opos, a.n_open);
+        double sr = 0.0, si = 0.0;
+        for (int64_t b = a.b_lo + lane; b < a.b_hi; b += 32) {
+            const float2 v = a.R[ob | scatter_bits((uint64_t)b, a.bpos, a.n_batch)];
+            sr += (double)v.x;
+            si += (double)v.y;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, off);
+            si += __shfl_xor_sync(0xffffffffu, si, off);
+        }
+        if (lane == 0) {
+            double2 cur = a.amp[o];
+            cur.x += sr;
+            cur.y += si;
+            a.amp[o] = cur;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) accum_thread_kernel(const AccumArgs a) {
+    const int64_t n_out = 1ll << a.n_open;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out; o += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t ob = scatter_bits((uint64_t)o, a.opos, a.n_open);
+        double sr = 0.0, si = 0.0;
+        for (int64_t b = a.b_lo; b < a.b_hi; b++) {
+            const float2 v = a.R[ob | scatter_bits((uint64_t)b, a.bpos, a.n_batch)];
+            sr += (double)v.x;
+            si += (double)v.y;
+        }
+        double2 cur = a.amp[o];
+        cur.x += sr;
+        cur.y += si;
+        a.amp[o] = cur;
+    }
+}
+
+// -------------------------------------------------- probabilities and XEB sums
+__global__ void __launch_bounds__(kThreads) prob_kernel(const double2 *amp, int64_t n, double *prob, double *out) {
+    double s = 0.0, mx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = amp[i];
+        const double p = v.x * v.x + v.y * v.y;
+        if (prob) prob[i] = p;
+        s += p;
+        mx = fmax(mx, p);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    __shared__ double ws[kThreads / 32], wm[kThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { ws[w] = s; wm[w] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bs = 0.0, bm = 0.0;
+        for (int i = 0; i < kThreads / 32; i++) { bs += ws[i]; bm = fmax(bm, wm[i]); }
+        atomicAdd(out, bs);
+        // non-negative doubles order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned long long *>(out + 2), (unsigned long long)__double_as_longlong(bm));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_small(const SmallArgs &a, cudaStream_t s) {
+    const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
+    const size_t smem = (size_t)HS * KS * NS * sizeof(float2) + (size_t)(KS + NS) * sizeof(uint32_t);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr_done = true;
+    }
+    const int grid = grid_for(a.rows);
+    if (KS <= 16) small_kernel<true><<<grid, kThreads, smem, s>>>(a);
+    else small_kernel<false><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const PermuteArgs &a, cudaStream_t s) {
+    permute_kernel<<<grid_for(a.n), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f32(const GemmArgs &a, cudaStream_t s) {
+    dim3 grid((unsigned)((a.M + BM - 1) / BM), (unsigned)((a.N + BN - 1) / BN),
+              (unsigned)(a.H < 65535 ? a.H : 65535));
+    if (grid.y > 65535 || (a.M + BM - 1) / BM > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    gemm_f32_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const ExtractEntry *d_entries, int n_entries, int max_out, uint64_t slice_base,
+                           cudaStream_t s) {
+    if (n_entries == 0) return cudaSuccess;
+    dim3 grid((unsigned)((max_out + kThreads - 1) / kThreads), (unsigned)n_entries);
+    extract_kernel<<<grid, kThreads, 0, s>>>(d_entries, n_entries, slice_base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accum(const AccumArgs &a, cudaStream_t s) {
+    const int64_t n_out = 1ll << a.n_open;
+    const int64_t nb = a.b_hi - a.b_lo;
+    if (nb >= 16) {
+        accum_warp_kernel<<<grid_for(n_out * 32), kThreads, 0, s>>>(a);
+    } else {
+        accum_thread_kernel<<<grid_for(n_out), kThreads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prob_xeb(const double2 *amp, int64_t n, double *prob, double *d_out3, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_out3, 0, 3 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    prob_kernel<<<grid_for(n), kThreads, 0, s>>>(amp, n, prob, d_out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s) {
+    return cudaMemsetAsync(p, 0, (size_t)n * sizeof(double), s);
+}
+
+}  // namespace tn

@@ -1,0 +1,86 @@
+// Kernel argument blocks shared by the host plan compiler and the CUDA
+// kernels.  Plain structs passed by value as kernel parameters.
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace tn {
+
+constexpr int kMaxRank = 48;     // largest tensor rank a kernel handles
+constexpr int kSmallMaxBits = 12;  // small operand: H + K + N bits <= this
+constexpr int kMaxHBits = 12;
+
+// One pairwise step where one operand S is small (<= 2^12 values, staged in
+// shared memory) and the other, T, is read once: for every index r over T's
+// non-K bits,  C[cpos(r) | offC[n]] = sum_k T[tpos(r) | offT[k]] * S[h(r), k, n].
+// C's layout is T's with the K labels replaced by the N labels.
+struct SmallArgs {
+    const float2 *T;
+    const float2 *S;
+    float2 *C;
+    int64_t rows;        // 2^(rank T - nK)
+    int nK, nN, nH;
+    int n_tins;          // K positions of T, ascending (zero insertion turns r into T's base)
+    int n_cins;          // N positions of C, ascending
+    int tins[kSmallMaxBits];
+    int cins[kSmallMaxBits];
+    int kposT[kSmallMaxBits];  // position in T of bit j of k
+    int nposC[kSmallMaxBits];  // position in C of bit j of n
+    int hbitR[kMaxHBits];      // bit of r holding bit j of h
+    int hposS[kMaxHBits], kposS[kSmallMaxBits], nposS[kSmallMaxBits];  // positions in S
+    int s_rank;
+};
+
+// Bit permutation: out[o] = in[sum_p bit_p(o) << ipos[p]].
+struct PermuteArgs {
+    const float2 *in;
+    float2 *out;
+    int64_t n;
+    int rank;
+    int ipos[kMaxRank];
+};
+
+// Strided batched complex GEMM, all strides in complex elements:
+// C[h sCh + m sCm + n sCn] = sum_k A[h sAh + m sAm + k sAk] B[h sBh + k sBk + n sBn]
+struct GemmArgs {
+    const float2 *A;
+    const float2 *B;
+    float2 *C;
+    int64_t H, M, N, K;
+    int64_t sAh, sAm, sAk, sBh, sBk, sBn, sCh, sCm, sCn;
+};
+
+// Slice extraction of leaves holding fixed sliced labels: for each entry,
+// dst[j] = src[insert_zeros(j, fpos) | sum_f bit(slice_base, sbit[f]) << fpos[f]].
+struct ExtractEntry {
+    const float2 *src;
+    float2 *dst;
+    int n_out;
+    int nf;
+    int fpos_sorted[kMaxRank];
+    int fpos[kMaxRank];
+    int sbit[kMaxRank];
+};
+
+// Cross-slice FP64 sum: amp[o] += sum_{b in [b_lo, b_hi)} R[pos(o, b)].
+struct AccumArgs {
+    const float2 *R;
+    double2 *amp;
+    int n_open, n_batch;
+    int opos[kMaxRank];  // position in R of bit j of o (j = 0 is the LSB of o)
+    int bpos[kMaxRank];  // position in R of bit j of b
+    int64_t b_lo, b_hi;
+};
+
+// launchers (kernels.cu); return cudaSuccess or the launch error
+cudaError_t launch_small(const SmallArgs &a, cudaStream_t s);
+cudaError_t launch_permute(const PermuteArgs &a, cudaStream_t s);
+cudaError_t launch_gemm_f32(const GemmArgs &a, cudaStream_t s);
+cudaError_t launch_extract(const ExtractEntry *d_entries, int n_entries, int max_out, uint64_t slice_base,
+                           cudaStream_t s);
+cudaError_t launch_accum(const AccumArgs &a, cudaStream_t s);
+cudaError_t launch_prob_xeb(const double2 *amp, int64_t n, double *prob, double *d_out3, cudaStream_t s);
+cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s);
+
+}  // namespace tn

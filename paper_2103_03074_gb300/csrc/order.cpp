@@ -1,0 +1,441 @@
+// Host-side contraction-order search and slicing.
+//
+// Cost model (Fig. 3): contracting a pair that shares n_AB labels, with n_A and
+// n_B outer labels, costs 2^{n_A + n_B + n_AB} complex multiply-adds; its
+// space cost is the size of the result.  A tree's cost is the sum over its
+// steps; its width is its largest tensor.
+//
+// Order: randomised greedy.  Each trial repeatedly merges the connected pair
+// with the smallest key, key = slog2(2^{|out|} - alpha (2^{|A|} + 2^{|B|}))
+// minus temperature x Gumbel noise (trial 0 is the plain greedy alpha = 1,
+// no noise).  The paper's own order search (first cut + hierarchical
+// bipartition + greedy leaves) is prior art this stands in for.
+//
+// Slicing ("Dynamic slicing" paragraph): labels are sliced one at a time,
+// each time taking the label that lowers the largest intermediate, ties broken
+// by the smallest total cost 2^{n_e} x sum_steps 2^{|step labels \ sliced|}.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <queue>
+#include <thread>
+#include <unordered_map>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+
+struct Rng {  // SplitMix64
+    uint64_t s;
+    explicit Rng(uint64_t seed) : s(seed) {}
+    uint64_t next() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+// Dense label sets over remapped label ids.
+struct Sets {
+    int W = 0;
+    std::vector<uint64_t> bits;
+    void init(int n_sets, int n_labels) {
+        W = (n_labels + 63) / 64;
+        if (W == 0) W = 1;
+        bits.assign((size_t)n_sets * W, 0);
+    }
+    uint64_t *at(int i) { return bits.data() + (size_t)i * W; }
+    const uint64_t *at(int i) const { return bits.data() + (size_t)i * W; }
+};
+
+inline int popc(const uint64_t *a, int W) {
+    int c = 0;
+    for (int i = 0; i < W; i++) c += __builtin_popcountll(a[i]);
+    return c;
+}
+
+struct Problem {
+    int n = 0;          // leaves
+    int L = 0;          // labels (remapped)
+    Sets leaf;          // leaf label sets
+    std::vector<uint64_t> open;  // open mask
+    std::vector<int32_t> id2label;
+    std::vector<std::vector<int>> leaf_labels;  // remapped ids per leaf
+};
+
+bool make_problem(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                  Problem &p) {
+    std::unordered_map<int32_t, int> remap;
+    for (auto &l : labels)
+        for (int32_t x : l)
+            if (!remap.count(x)) {
+                int id = (int)remap.size();
+                remap[x] = id;
+                p.id2label.push_back(x);
+            }
+    for (int32_t x : open)
+        if (!remap.count(x)) return false;  // open label held by no tensor
+    p.n = (int)labels.size();
+    p.L = (int)remap.size();
+    p.leaf.init(p.n, p.L);
+    p.open.assign(p.leaf.W, 0);
+    p.leaf_labels.resize(p.n);
+    for (int i = 0; i < p.n; i++)
+        for (int32_t x : labels[i]) {
+            int id = remap[x];
+            p.leaf.at(i)[id >> 6] |= 1ull << (id & 63);
+            p.leaf_labels[i].push_back(id);
+        }
+    for (int32_t x : open) {
+        int id = remap[x];
+        p.open[id >> 6] |= 1ull << (id & 63);
+    }
+    return true;
+}
+
+// All node label sets of a tree (leaves, then one per step) and step unions.
+struct TreeSets {
+    Sets node;   // 2n-1 sets
+    Sets uni;    // n-1 step unions (labels of A u B)
+};
+
+bool tree_sets(const Problem &p, const Tree &tree, TreeSets &ts) {
+    const int n = p.n, W = p.leaf.W;
+    if ((int)tree.size() != std::max(n - 1, 0)) return false;
+    ts.node.init(2 * n - 1 > 0 ? 2 * n - 1 : 1, p.L);
+    ts.uni.init(n - 1 > 0 ? n - 1 : 1, p.L);
+    std::memcpy(ts.node.at(0), p.leaf.at(0), sizeof(uint64_t) * W * n);
+    std::vector<char> used(2 * n, 0);
+    for (int t = 0; t < n - 1; t++) {
+        int a = tree[t].first, b = tree[t].second;
+        if (a < 0 || b < 0 || a >= n + t || b >= n + t || a == b || used[a] || used[b]) return false;
+        used[a] = used[b] = 1;
+        const uint64_t *sa = ts.node.at(a), *sb = ts.node.at(b);
+        uint64_t *so = ts.node.at(n + t), *su = ts.uni.at(t);
+        for (int w = 0; w < W; w++) {
+            su[w] = sa[w] | sb[w];
+            so[w] = su[w] & ~(sa[w] & sb[w] & ~p.open[w]);
+        }
+    }
+    return true;
+}
+
+struct SliceEval {
+    std::vector<int> sliced;  // remapped ids
+    double log2_slice_cost = 0, log2_width = 0, log2_total = 0;
+};
+
+double log2_sum_pow2(const std::vector<double> &e) {  // log2(sum 2^e)
+    if (e.empty()) return -INFINITY;
+    double m = *std::max_element(e.begin(), e.end());
+    double s = 0;
+    for (double x : e) s += std::exp2(x - m);
+    return m + std::log2(s);
+}
+
+// Greedy slicing.  n_sliced >= 0: exactly that many; else slice until width <= cap.
+void slice_tree(const Problem &p, const TreeSets &ts, int n_nodes, int n_steps, int log2_cap,
+                int n_sliced, SliceEval &ev) {
+    const int W = p.leaf.W;
+    std::vector<uint64_t> smask(W, 0);
+    std::vector<int> wv(n_nodes), wu(n_steps);
+    auto recount = [&]() {
+        for (int v = 0; v < n_nodes; v++) {
+            const uint64_t *s = ts.node.at(v);
+            int c = 0;
+            for (int w = 0; w < W; w++) c += __builtin_popcountll(s[w] & ~smask[w]);
+            wv[v] = c;
+        }
+        for (int t = 0; t < n_steps; t++) {
+            const uint64_t *s = ts.uni.at(t);
+            int c = 0;
+            for (int w = 0; w < W; w++) c += __builtin_popcountll(s[w] & ~smask[w]);
+            wu[t] = c;
+        }
+    };
+    recount();
+    ev.sliced.clear();
+    for (int iter = 0; iter < p.L; iter++) {
+        int wmax = n_nodes ? *std::max_element(wv.begin(), wv.end()) : 0;
+        if (n_sliced >= 0) {
+            if ((int)ev.sliced.size() >= n_sliced) break;
+        } else if (log2_cap < 0 || wmax <= log2_cap) {
+            break;
+        }
+        // per-label: reduction of the step-cost sum and the new width
+        std::vector<double> drop(p.L, 0.0);
+        double base = 0;
+        double m = 0;
+        for (int t = 0; t < n_steps; t++) m = std::max(m, (double)wu[t]);
+        for (int t = 0; t < n_steps; t++) {
+            double c = std::exp2(wu[t] - m);
+            base += c;
+            const uint64_t *s = ts.uni.at(t);
+            for (int w = 0; w < W; w++) {
+                uint64_t x = s[w] & ~smask[w] & ~p.open[w];
+                while (x) {
+                    int b = __builtin_ctzll(x);
+                    x &= x - 1;
+                    drop[w * 64 + b] += 0.5 * c;
+                }
+            }
+        }
+        int best = -1;
+        int best_w = 0;
+        double best_c = 0;
+        for (int l = 0; l < p.L; l++) {
+            if ((p.open[l >> 6] >> (l & 63)) & 1) continue;
+            if ((smask[l >> 6] >> (l & 63)) & 1) continue;
+            if (drop[l] <= 0) continue;  // label in no step
+            int nw = 0;
+            for (int v = 0; v < n_nodes; v++) {
+                int has = (ts.node.at(v)[l >> 6] >> (l & 63)) & 1;
+                nw = std::max(nw, wv[v] - has);
+            }
+            double c = base - drop[l];
+            if (best < 0 || nw < best_w || (nw == best_w && c < best_c)) {
+                best = l;
+                best_w = nw;
+                best_c = c;
+            }
+        }
+        if (best < 0) break;
+        smask[best >> 6] |= 1ull << (best & 63);
+        ev.sliced.push_back(best);
+        recount();
+    }
+    std::vector<double> e(wu.begin(), wu.end());
+    ev.log2_slice_cost = n_steps ? log2_sum_pow2(e) : 0.0;
+    ev.log2_width = n_nodes ? *std::max_element(wv.begin(), wv.end()) : 0;
+    ev.log2_total = ev.log2_slice_cost + (double)ev.sliced.size();
+}
+
+inline double slog2(double x) { return x >= 0 ? std::log2(1.0 + x) : -std::log2(1.0 - x); }
+
+// One randomised greedy trial.
+Tree greedy_trial(const Problem &p, uint64_t seed, bool plain) {
+    const int n = p.n, W = p.leaf.W;
+    Rng rng(seed);
+    double alpha = plain ? 1.0 : rng.uniform();
+    double temp = plain ? 0.0 : std::exp2(-7.0 + 7.0 * rng.uniform());
+    Sets s;
+    s.init(2 * n, p.L);
+    std::memcpy(s.at(0), p.leaf.at(0), sizeof(uint64_t) * W * n);
+    std::vector<int> size(2 * n, 0);
+    for (int i = 0; i < n; i++) size[i] = popc(s.at(i), W);
+    std::vector<std::array<int, 2>> holders(p.L, {-1, -1});
+    for (int i = 0; i < n; i++)
+        for (int id : p.leaf_labels[i]) {
+            auto &h = holders[id];
+            if (h[0] < 0) h[0] = i; else h[1] = i;
+        }
+    std::vector<char> alive(2 * n, 0);
+    for (int i = 0; i < n; i++) alive[i] = 1;
+    struct Item { double key; int a, b; };
+    auto cmp = [](const Item &x, const Item &y) {
+        if (x.key != y.key) return x.key > y.key;
+        if (x.a != y.a) return x.a > y.a;
+        return x.b > y.b;
+    };
+    std::priority_queue<Item, std::vector<Item>, decltype(cmp)> pq(cmp);
+    std::vector<uint64_t> tmp(W);
+    auto out_size = [&](int a, int b) {
+        const uint64_t *sa = s.at(a), *sb = s.at(b);
+        int c = 0;
+        for (int w = 0; w < W; w++) c += __builtin_popcountll((sa[w] | sb[w]) & ~(sa[w] & sb[w] & ~p.open[w]));
+        return c;
+    };
+    auto push = [&](int a, int b) {
+        if (a > b) std::swap(a, b);
+        int o = out_size(a, b);
+        double cost = std::exp2((double)o) - alpha * (std::exp2((double)size[a]) + std::exp2((double)size[b]));
+        double key = slog2(cost);
+        if (temp > 0) {
+            double u = rng.uniform();
+            if (u < 1e-300) u = 1e-300;
+            key -= temp * (-std::log(-std::log(u)));
+        }
+        pq.push({key, a, b});
+    };
+    for (int l = 0; l < p.L; l++)
+        if (holders[l][0] >= 0 && holders[l][1] >= 0) push(holders[l][0], holders[l][1]);
+    Tree tree;
+    int nxt = n, n_alive = n;
+    while (n_alive > 1) {
+        int a = -1, b = -1;
+        while (!pq.empty()) {
+            Item it = pq.top();
+            pq.pop();
+            if (alive[it.a] && alive[it.b]) {
+                a = it.a;
+                b = it.b;
+                break;
+            }
+        }
+        if (a < 0) {  // disconnected: join the two smallest alive nodes
+            int s1 = -1, s2 = -1;
+            for (int i = 0; i < nxt; i++) {
+                if (!alive[i]) continue;
+                if (s1 < 0 || size[i] < size[s1]) { s2 = s1; s1 = i; }
+                else if (s2 < 0 || size[i] < size[s2]) s2 = i;
+            }
+            a = std::min(s1, s2);
+            b = std::max(s1, s2);
+        }
+        uint64_t *sa = s.at(a), *sb = s.at(b), *so = s.at(nxt);
+        for (int w = 0; w < W; w++) so[w] = (sa[w] | sb[w]) & ~(sa[w] & sb[w] & ~p.open[w]);
+        size[nxt] = popc(so, W);
+        alive[a] = alive[b] = 0;
+        alive[nxt] = 1;
+        tree.push_back({a, b});
+        // holders update and new candidate pairs
+        for (int w = 0; w < W; w++) {
+            uint64_t x = sa[w] | sb[w];
+            while (x) {
+                int l = w * 64 + __builtin_ctzll(x);
+                x &= x - 1;
+                auto &h = holders[l];
+                bool kept = (so[l >> 6] >> (l & 63)) & 1;
+                for (int k = 0; k < 2; k++)
+                    if (h[k] == a || h[k] == b) h[k] = kept ? nxt : -1;
+                if (h[0] == nxt && h[1] == nxt) h[1] = -1;  // open label held by both operands (cannot happen)
+            }
+        }
+        for (int w = 0; w < W; w++) {
+            uint64_t x = so[w];
+            while (x) {
+                int l = w * 64 + __builtin_ctzll(x);
+                x &= x - 1;
+                auto &h = holders[l];
+                int other = h[0] == nxt ? h[1] : h[0];
+                if (other >= 0 && other != nxt && alive[other]) push(nxt, other);
+            }
+        }
+        nxt++;
+        n_alive--;
+    }
+    return tree;
+}
+
+}  // namespace
+
+tn_search_opts default_search_opts() {
+    tn_search_opts o;
+    std::memset(&o, 0, sizeof o);
+    o.trials = 256;
+    o.seed = 0x2103030740ull;
+    o.log2_cap = -1;
+    o.n_sliced = -1;
+    o.threads = 0;
+    return o;
+}
+
+bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                   const Tree &tree, const std::vector<int32_t> &sliced, SearchResult &out) {
+    Problem p;
+    if (!make_problem(labels, open, p)) return false;
+    TreeSets ts;
+    if (!tree_sets(p, tree, ts)) return false;
+    std::unordered_map<int32_t, int> remap;
+    for (int i = 0; i < p.L; i++) remap[p.id2label[i]] = i;
+    std::vector<uint64_t> smask(p.leaf.W, 0);
+    for (int32_t x : sliced) {
+        auto it = remap.find(x);
+        if (it == remap.end()) return false;
+        smask[it->second >> 6] |= 1ull << (it->second & 63);
+    }
+    int n_nodes = 2 * p.n - 1, n_steps = p.n - 1;
+    std::vector<double> e;
+    double width = 0;
+    for (int v = 0; v < n_nodes; v++) {
+        int c = 0;
+        for (int w = 0; w < p.leaf.W; w++) c += __builtin_popcountll(ts.node.at(v)[w] & ~smask[w]);
+        width = std::max(width, (double)c);
+    }
+    for (int t = 0; t < n_steps; t++) {
+        int c = 0;
+        for (int w = 0; w < p.leaf.W; w++) c += __builtin_popcountll(ts.uni.at(t)[w] & ~smask[w]);
+        e.push_back(c);
+    }
+    out.tree = tree;
+    out.sliced = sliced;
+    out.log2_slice = n_steps ? log2_sum_pow2(e) : 0.0;
+    out.log2_width = width;
+    out.log2_total = out.log2_slice + (double)sliced.size();
+    return true;
+}
+
+int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                 const tn_search_opts &opts_in, SearchResult &out) {
+    tn_search_opts opts = opts_in;
+    if (opts.trials <= 0) opts.trials = 256;
+    Problem p;
+    if (!make_problem(labels, open, p)) return fail(TN_ERR_ARG, "open label held by no tensor");
+    if (p.n == 0) return fail(TN_ERR_ARG, "empty network");
+    if (p.n == 1) {
+        out.tree.clear();
+        out.sliced.clear();
+        out.log2_total = out.log2_slice = 0;
+        out.log2_width = (double)labels[0].size();
+        return TN_OK;
+    }
+    int threads = opts.threads > 0 ? opts.threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    threads = std::min(threads, opts.trials);
+    struct Best { double total = INFINITY, width = INFINITY; int trial = -1; Tree tree; SliceEval ev; };
+    std::vector<Best> best(threads);
+    std::atomic<int> next{0};
+    auto worker = [&](int tid) {
+        TreeSets ts;
+        for (;;) {
+            int t = next.fetch_add(1);
+            if (t >= opts.trials) break;
+            Tree tree = greedy_trial(p, opts.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1), t == 0);
+            if (!tree_sets(p, tree, ts)) continue;
+            SliceEval ev;
+            slice_tree(p, ts, 2 * p.n - 1, p.n - 1, opts.log2_cap, opts.n_sliced, ev);
+            bool over = opts.log2_cap >= 0 && ev.log2_width > opts.log2_cap;
+            double key_w = over ? ev.log2_width : 0;
+            Best &b = best[tid];
+            double bw = (opts.log2_cap >= 0 && b.width > opts.log2_cap) ? b.width : 0;
+            if (b.trial < 0 || key_w < bw || (key_w == bw && (ev.log2_total < b.total ||
+                                                               (ev.log2_total == b.total && t < b.trial)))) {
+                b.total = ev.log2_total;
+                b.width = ev.log2_width;
+                b.trial = t;
+                b.tree = tree;
+                b.ev = ev;
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < threads; i++) pool.emplace_back(worker, i);
+    worker(0);
+    for (auto &th : pool) th.join();
+    int bi = -1;
+    for (int i = 0; i < threads; i++) {
+        if (best[i].trial < 0) continue;
+        auto over = [&](const Best &b) { return (opts.log2_cap >= 0 && b.width > opts.log2_cap) ? b.width : 0.0; };
+        if (bi < 0 || over(best[i]) < over(best[bi]) ||
+            (over(best[i]) == over(best[bi]) && (best[i].total < best[bi].total ||
+                                                 (best[i].total == best[bi].total && best[i].trial < best[bi].trial))))
+            bi = i;
+    }
+    if (bi < 0) return fail(TN_ERR_ARG, "order search produced no tree");
+    out.tree = best[bi].tree;
+    out.sliced.clear();
+    for (int id : best[bi].ev.sliced) out.sliced.push_back(p.id2label[id]);
+    out.log2_total = best[bi].ev.log2_total;
+    out.log2_width = best[bi].ev.log2_width;
+    out.log2_slice = best[bi].ev.log2_slice_cost;
+    return TN_OK;
+}
+
+}  // namespace tn

@@ -1,0 +1,789 @@
+// Plan compiler and the device-side C-ABI calls.
+//
+// A plan turns (network, open labels, sliced labels, tree) into a fixed
+// sequence of kernel launches over a static device arena:
+//
+//  * Slices run in aligned blocks of 2^nb consecutive slice ids.  Within a
+//    block the nb lowest sliced labels stay in the network as batch labels
+//    (never summed, carried to the root); the other sliced labels are fixed
+//    at the leaves from the block's base id (slice extraction).  The root then
+//    holds one partial amplitude tensor per slice of the block, and the
+//    cross-slice FP64 sum adds the slices of the requested range into the
+//    caller's amplitude tensor ("Dynamic slicing": the sum over slices is the
+//    unsliced contraction).
+//  * Nodes whose subtree holds no fixed sliced label are slice-invariant: they
+//    are computed once per call (prologue), not once per block.
+//  * Each pairwise step (Fig. 3: H batch labels, M / N outer labels, K shared
+//    labels, cost 2^{H+M+N+K} complex MACs) is either a "small" step (one
+//    operand <= 2^12 values, staged in shared memory, the other read once with
+//    bit-scatter addressing, output written in the big operand's layout with
+//    K labels replaced by N labels) or a strided batched GEMM whose operands
+//    are permuted first when their H/M/K label groups are not contiguous.
+//  * Buffers are placed in one arena by first-fit over their live intervals.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "tc_gemm.h"
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+
+enum OpKind { OP_SMALL = 0, OP_PERMUTE = 1, OP_GEMM = 2 };
+
+struct Operand {  // where an op reads or writes: static leaf or arena buffer
+    int buf = -1;        // arena buffer id, or -1
+    int64_t leaf_off = -1;  // element offset in the leaf buffer
+};
+
+struct Op {
+    OpKind kind;
+    int step = -1;
+    bool dep = false;
+    Operand in0, in1, out;
+    SmallArgs small;
+    PermuteArgs perm;
+    GemmArgs gemm;
+    double macs = 0, bytes = 0;
+    int gemm_variant = 0;  // 0: FP32 CUDA cores, 1: tensor-core split form
+};
+
+struct Buf {
+    int64_t elems = 0;
+    int t0 = 0, t1 = 0;
+    int64_t off = 0;  // bytes
+};
+
+struct NodeRec {
+    std::vector<int32_t> lay;
+    bool dep = false;
+    bool extracted = false;
+    int leaf = -1;
+    Operand where;
+    int t_prod = -1;
+};
+
+inline int pos_of(const std::vector<int32_t> &lay, int32_t x) {
+    for (size_t i = 0; i < lay.size(); i++)
+        if (lay[i] == x) return (int)(lay.size() - 1 - i);
+    return -1;
+}
+
+struct Groups {
+    bool ok = false;
+    std::vector<int32_t> order[3];
+    int lowpos[3] = {0, 0, 0};
+};
+
+// Are the labels of `lay` in contiguous runs per group (gid: label -> 0..2)?
+Groups group_layout(const std::vector<int32_t> &lay, const std::unordered_map<int32_t, int> &gid) {
+    Groups g;
+    int r = (int)lay.size();
+    int last = -1;
+    bool seen[3] = {false, false, false};
+    for (int i = 0; i < r; i++) {
+        int id = gid.at(lay[i]);
+        if (id != last) {
+            if (seen[id]) return g;  // group split in two runs
+            seen[id] = true;
+            last = id;
+        }
+        g.order[id].push_back(lay[i]);
+        g.lowpos[id] = r - 1 - i;
+    }
+    g.ok = true;
+    return g;
+}
+
+}  // namespace
+
+}  // namespace tn
+
+struct tn_plan {
+    int device = 0;
+    tn_form form = TN_FP32;
+    int n_tensors = 0, n_open = 0, n_sliced = 0, nb = 0;
+    std::vector<int32_t> open, sliced;
+    // host copies
+    std::vector<std::vector<int32_t>> labels;
+    std::vector<int64_t> leaf_off;  // element offsets of leaves in d_leaves
+    tn::Tree tree;
+    // compiled
+    std::vector<tn::Op> prologue, batch;
+    std::vector<tn::Buf> bufs;
+    std::vector<tn::ExtractEntry> extract;  // host copy (pointers resolved)
+    int extract_max_out = 0;
+    tn::AccumArgs accum;
+    tn::Operand root;
+    int64_t arena_bytes = 0;
+    // device
+    float2 *d_leaves = nullptr;
+    char *d_arena = nullptr;
+    tn::ExtractEntry *d_extract = nullptr;
+    bool failed = false;
+    // stats
+    double macs_batch = 0, macs_prologue = 0, bytes_batch = 0, bytes_prologue = 0;
+    int launches_batch = 0, launches_prologue = 0;
+    tn_plan_opts opts;
+};
+
+namespace tn {
+
+namespace {
+
+constexpr int kSmallMaxRank = 12;
+
+// Compile the op lists for batch width nb.  Returns the arena size or -1 on
+// a malformed input (message set).
+int64_t compile(tn_plan &P, int nb) {
+    P.nb = nb;
+    P.prologue.clear();
+    P.batch.clear();
+    P.bufs.clear();
+    P.extract.clear();
+    const int n = P.n_tensors;
+    std::unordered_set<int32_t> kept(P.open.begin(), P.open.end());
+    std::unordered_map<int32_t, int> fixed_bit;  // fixed sliced label -> slice-id bit
+    for (int j = 0; j < P.n_sliced; j++) {
+        if (j < nb) kept.insert(P.sliced[j]);
+        else fixed_bit[P.sliced[j]] = j;
+    }
+    std::vector<NodeRec> nodes(2 * n - 1 > 0 ? 2 * n - 1 : 1);
+    // ops are first collected per step with dependency flags, buffers get
+    // times afterwards
+    struct PendingOp { Op op; };
+    std::vector<Op> ops;  // in tree order
+    auto new_buf = [&](int64_t elems) {
+        Buf b;
+        b.elems = elems;
+        P.bufs.push_back(b);
+        return (int)P.bufs.size() - 1;
+    };
+    // leaves
+    for (int i = 0; i < n; i++) {
+        NodeRec &nd = nodes[i];
+        nd.leaf = i;
+        std::vector<int> fpos;
+        for (int32_t x : P.labels[i]) {
+            if (fixed_bit.count(x)) nd.extracted = true;
+            else nd.lay.push_back(x);
+        }
+        nd.dep = nd.extracted;
+        if (nd.extracted) {
+            nd.where.buf = new_buf((int64_t)1 << nd.lay.size());
+            ExtractEntry e;
+            std::memset(&e, 0, sizeof e);
+            e.n_out = 1 << nd.lay.size();
+            const int r = (int)P.labels[i].size();
+            std::vector<int> fp;
+            for (int a = 0; a < r; a++) {
+                int32_t x = P.labels[i][a];
+                auto it = fixed_bit.find(x);
+                if (it == fixed_bit.end()) continue;
+                e.fpos[e.nf] = r - 1 - a;
+                e.sbit[e.nf] = it->second;
+                fp.push_back(r - 1 - a);
+                e.nf++;
+            }
+            std::sort(fp.begin(), fp.end());
+            for (size_t q = 0; q < fp.size(); q++) e.fpos_sorted[q] = fp[q];
+            // src/dst resolved later: stash leaf index / buffer id in pointers
+            e.src = reinterpret_cast<const float2 *>((intptr_t)i);
+            e.dst = reinterpret_cast<float2 *>((intptr_t)nd.where.buf);
+            P.extract.push_back(e);
+            P.extract_max_out = std::max(P.extract_max_out, e.n_out);
+        } else {
+            nd.where.leaf_off = P.leaf_off[i];
+        }
+    }
+    // steps
+    for (int t = 0; t < (int)P.tree.size(); t++) {
+        const int ia = P.tree[t].first, ib = P.tree[t].second;
+        NodeRec &na = nodes[ia], &nb_ = nodes[ib];
+        NodeRec &nc = nodes[n + t];
+        std::unordered_set<int32_t> sa(na.lay.begin(), na.lay.end()), sb(nb_.lay.begin(), nb_.lay.end());
+        std::vector<int32_t> H, K;
+        for (int32_t x : na.lay)
+            if (sb.count(x)) (kept.count(x) ? H : K).push_back(x);
+        nc.dep = na.dep || nb_.dep;
+        const int ra = (int)na.lay.size(), rb = (int)nb_.lay.size();
+        const bool a_big = ra >= rb;
+        NodeRec &T = a_big ? na : nb_;
+        NodeRec &S = a_big ? nb_ : na;
+        const std::unordered_set<int32_t> &sT = a_big ? sa : sb;
+        const std::unordered_set<int32_t> &sS = a_big ? sb : sa;
+        std::vector<int32_t> Nl;  // free labels of S, S order
+        for (int32_t x : S.lay)
+            if (!sT.count(x)) Nl.push_back(x);
+        std::vector<int32_t> Ml;  // free labels of T, T order
+        for (int32_t x : T.lay)
+            if (!sS.count(x)) Ml.push_back(x);
+        const int nH = (int)H.size(), nK = (int)K.size(), nN = (int)Nl.size(), nM = (int)Ml.size();
+        const double macs = std::exp2((double)(nH + nM + nK + nN));
+        if ((int)S.lay.size() <= kSmallMaxRank && nK <= 10 && nN <= 10 && nH <= kMaxHBits) {
+            // ---- small step: C = T layout with K labels replaced by N labels
+            Op op;
+            std::memset(&op.small, 0, sizeof op.small);
+            op.kind = OP_SMALL;
+            op.step = t;
+            op.dep = nc.dep;
+            std::vector<int32_t> cl = T.lay;
+            std::vector<int> kslots;
+            std::unordered_set<int32_t> Kset(K.begin(), K.end());
+            for (int i = 0; i < (int)cl.size(); i++)
+                if (Kset.count(cl[i])) kslots.push_back(i);
+            std::vector<char> del(cl.size(), 0);
+            for (int i = 0; i < (int)kslots.size(); i++) {
+                if (i < nN) cl[kslots[i]] = Nl[i];
+                else del[kslots[i]] = 1;
+            }
+            std::vector<int32_t> c2;
+            for (int i = nN - 1; i >= (int)kslots.size(); i--) c2.push_back(Nl[i]);
+            std::reverse(c2.begin(), c2.end());
+            for (int i = 0; i < (int)cl.size(); i++)
+                if (!del[i]) c2.push_back(cl[i]);
+            nc.lay = c2;
+            if ((int)nc.lay.size() > kMaxRank || (int)T.lay.size() > kMaxRank) {
+                set_error("tensor rank exceeds the kernel limit");
+                return -1;
+            }
+            SmallArgs &s = op.small;
+            s.nK = nK;
+            s.nN = nN;
+            s.nH = nH;
+            s.s_rank = (int)S.lay.size();
+            s.rows = (int64_t)1 << (T.lay.size() - nK);
+            // K bits: ascending T positions
+            std::vector<int> tk;
+            for (int32_t x : K) tk.push_back(pos_of(T.lay, x));
+            std::vector<int32_t> Ksorted = K;
+            std::sort(Ksorted.begin(), Ksorted.end(),
+                      [&](int32_t x, int32_t y) { return pos_of(T.lay, x) < pos_of(T.lay, y); });
+            for (int j = 0; j < nK; j++) {
+                s.kposT[j] = pos_of(T.lay, Ksorted[j]);
+                s.kposS[j] = pos_of(S.lay, Ksorted[j]);
+                s.tins[j] = s.kposT[j];
+            }
+            s.n_tins = nK;
+            std::vector<int> cn;
+            for (int j = 0; j < nN; j++) {
+                s.nposC[j] = pos_of(nc.lay, Nl[j]);
+                s.nposS[j] = pos_of(S.lay, Nl[j]);
+                cn.push_back(s.nposC[j]);
+            }
+            std::sort(cn.begin(), cn.end());
+            for (int j = 0; j < nN; j++) s.cins[j] = cn[j];
+            s.n_cins = nN;
+            for (int j = 0; j < nH; j++) {
+                int pt = pos_of(T.lay, H[j]);
+                int below = 0;
+                for (int q = 0; q < nK; q++)
+                    if (s.kposT[q] < pt) below++;
+                s.hbitR[j] = pt - below;
+                s.hposS[j] = pos_of(S.lay, H[j]);
+            }
+            op.in0 = T.where;  // T
+            op.in1 = S.where;  // S
+            nc.where.buf = new_buf((int64_t)1 << nc.lay.size());
+            op.out = nc.where;
+            op.macs = macs;
+            op.bytes = 8.0 * (std::exp2((double)T.lay.size()) + std::exp2((double)S.lay.size()) +
+                              std::exp2((double)nc.lay.size()));
+            ops.push_back(op);
+            continue;
+        }
+        // ---- GEMM step: A = bigger operand (rows M), B = smaller (cols N)
+        NodeRec &A = T, &B = S;
+        std::unordered_map<int32_t, int> gA, gB;
+        for (int32_t x : H) { gA[x] = 0; gB[x] = 0; }
+        for (int32_t x : K) { gA[x] = 2; gB[x] = 1; }
+        for (int32_t x : Ml) gA[x] = 1;
+        for (int32_t x : Nl) gB[x] = 2;
+        Groups GA = group_layout(A.lay, gA), GB = group_layout(B.lay, gB);
+        auto same = [](const std::vector<int32_t> &x, const std::vector<int32_t> &y) { return x == y; };
+        bool permA = false, permB = false;
+        std::vector<int32_t> hord, kord;
+        if (GA.ok && GB.ok && same(GA.order[0], GB.order[0]) && same(GA.order[2], GB.order[1])) {
+        } else if (GA.ok) {
+            permB = true;
+        } else if (GB.ok) {
+            permA = true;
+        } else {
+            permA = permB = true;
+        }
+        if (GA.ok && !permA) {
+            hord = GA.order[0];
+            kord = GA.order[2];
+        } else if (GB.ok && !permB) {
+            hord = GB.order[0];
+            kord = GB.order[1];
+        } else {
+            for (int32_t x : A.lay)
+                if (gA[x] == 0) hord.push_back(x);
+            for (int32_t x : A.lay)
+                if (gA[x] == 2) kord.push_back(x);
+        }
+        auto emit_permute = [&](NodeRec &src, const std::vector<int32_t> &new_lay, Operand &dst) {
+            Op op;
+            std::memset(&op.perm, 0, sizeof op.perm);
+            op.kind = OP_PERMUTE;
+            op.step = t;
+            op.dep = nc.dep;
+            const int r = (int)new_lay.size();
+            op.perm.rank = r;
+            op.perm.n = (int64_t)1 << r;
+            for (int p = 0; p < r; p++) op.perm.ipos[p] = pos_of(src.lay, new_lay[r - 1 - p]);
+            op.in0 = src.where;
+            dst.buf = new_buf((int64_t)1 << r);
+            dst.leaf_off = -1;
+            op.out = dst;
+            op.bytes = 16.0 * std::exp2((double)r);
+            ops.push_back(op);
+        };
+        std::vector<int32_t> layA = A.lay, layB = B.lay;
+        Operand wA = A.where, wB = B.where;
+        if (permA) {
+            std::vector<int32_t> nl = hord;
+            nl.insert(nl.end(), Ml.begin(), Ml.end());
+            nl.insert(nl.end(), kord.begin(), kord.end());
+            NodeRec tmp = A;
+            emit_permute(tmp, nl, wA);
+            layA = nl;
+        }
+        if (permB) {
+            std::vector<int32_t> nl = hord;
+            nl.insert(nl.end(), kord.begin(), kord.end());
+            nl.insert(nl.end(), Nl.begin(), Nl.end());
+            NodeRec tmp = B;
+            emit_permute(tmp, nl, wB);
+            layB = nl;
+        }
+        GA = group_layout(layA, gA);
+        GB = group_layout(layB, gB);
+        if (!GA.ok || !GB.ok || GA.order[0] != GB.order[0] || GA.order[2] != GB.order[1]) {
+            set_error("internal: GEMM layout grouping failed");
+            return -1;
+        }
+        std::vector<int32_t> mord = GA.order[1], nord = GB.order[2];
+        nc.lay = hord;
+        nc.lay.insert(nc.lay.end(), mord.begin(), mord.end());
+        nc.lay.insert(nc.lay.end(), nord.begin(), nord.end());
+        if ((int)nc.lay.size() > kMaxRank) {
+            set_error("tensor rank exceeds the kernel limit");
+            return -1;
+        }
+        Op op;
+        std::memset(&op.gemm, 0, sizeof op.gemm);
+        op.kind = OP_GEMM;
+        op.step = t;
+        op.dep = nc.dep;
+        GemmArgs &g = op.gemm;
+        g.H = (int64_t)1 << nH;
+        g.M = (int64_t)1 << nM;
+        g.N = (int64_t)1 << nN;
+        g.K = (int64_t)1 << nK;
+        g.sAh = (int64_t)1 << GA.lowpos[0];
+        g.sAm = (int64_t)1 << GA.lowpos[1];
+        g.sAk = (int64_t)1 << GA.lowpos[2];
+        g.sBh = (int64_t)1 << GB.lowpos[0];
+        g.sBk = (int64_t)1 << GB.lowpos[1];
+        g.sBn = (int64_t)1 << GB.lowpos[2];
+        g.sCn = 1;
+        g.sCm = (int64_t)1 << nN;
+        g.sCh = (int64_t)1 << (nM + nN);
+        op.in0 = wA;
+        op.in1 = wB;
+        nc.where.buf = new_buf((int64_t)1 << nc.lay.size());
+        op.out = nc.where;
+        op.macs = macs;
+        op.bytes = 8.0 * (std::exp2((double)A.lay.size()) + std::exp2((double)B.lay.size()) +
+                          std::exp2((double)nc.lay.size()));
+        op.gemm_variant = (P.form != TN_FP32) ? 1 : 0;
+        ops.push_back(op);
+    }
+    // root
+    const int root_id = P.tree.empty() ? 0 : n + (int)P.tree.size() - 1;
+    NodeRec &rt = nodes[root_id];
+    {
+        std::set<int32_t> want(P.open.begin(), P.open.end());
+        for (int j = 0; j < nb; j++) want.insert(P.sliced[j]);
+        std::set<int32_t> have(rt.lay.begin(), rt.lay.end());
+        if (want != have) {
+            set_error("root labels differ from open + batch labels (disconnected or malformed tree?)");
+            return -1;
+        }
+    }
+    std::memset(&P.accum, 0, sizeof P.accum);
+    P.accum.n_open = P.n_open;
+    P.accum.n_batch = nb;
+    for (int j = 0; j < P.n_open; j++) P.accum.opos[j] = pos_of(rt.lay, P.open[P.n_open - 1 - j]);
+    for (int j = 0; j < nb; j++) P.accum.bpos[j] = pos_of(rt.lay, P.sliced[j]);
+    P.root = rt.where;
+    const bool root_dep = rt.dep;
+
+    // split into prologue (slice-invariant) and per-block ops; timeline
+    for (auto &op : ops) (op.dep ? P.batch : P.prologue).push_back(op);
+    const int T_pro = (int)P.prologue.size();
+    const int T_ext = T_pro;                       // extraction at the start of a block
+    const int T_acc = T_pro + 1 + (int)P.batch.size();
+    const int T_end = T_acc;
+    // producer / consumer times per buffer
+    std::vector<int> first(P.bufs.size(), INT32_MAX), last(P.bufs.size(), -1);
+    auto touch = [&](const Operand &w, int time) {
+        if (w.buf < 0) return;
+        first[w.buf] = std::min(first[w.buf], time);
+        last[w.buf] = std::max(last[w.buf], time);
+    };
+    std::vector<char> buf_dep(P.bufs.size(), 0);
+    for (auto &e : P.extract) {
+        int b = (int)(intptr_t)e.dst;
+        touch(Operand{b, -1}, T_ext);
+        buf_dep[b] = 1;
+    }
+    for (int i = 0; i < T_pro; i++) {
+        Op &op = P.prologue[i];
+        touch(op.in0, i);
+        touch(op.in1, i);
+        touch(op.out, i);
+    }
+    for (int i = 0; i < (int)P.batch.size(); i++) {
+        Op &op = P.batch[i];
+        int time = T_pro + 1 + i;
+        touch(op.in0, time);
+        touch(op.in1, time);
+        touch(op.out, time);
+        if (op.out.buf >= 0) buf_dep[op.out.buf] = 1;
+    }
+    touch(P.root, T_acc);
+    // an invariant buffer read inside the block loop lives to the loop's end
+    for (size_t b = 0; b < P.bufs.size(); b++) {
+        if (!buf_dep[b] && last[b] > T_pro) last[b] = T_end;
+        if (first[b] == INT32_MAX) { first[b] = 0; last[b] = 0; }
+        P.bufs[b].t0 = first[b];
+        P.bufs[b].t1 = last[b];
+    }
+    (void)root_dep;
+    // first-fit placement, largest first
+    std::vector<int> idx(P.bufs.size());
+    for (size_t i = 0; i < idx.size(); i++) idx[i] = (int)i;
+    std::sort(idx.begin(), idx.end(), [&](int x, int y) {
+        if (P.bufs[x].elems != P.bufs[y].elems) return P.bufs[x].elems > P.bufs[y].elems;
+        return x < y;
+    });
+    std::vector<int> placed;
+    int64_t arena = 0;
+    for (int bi : idx) {
+        Buf &b = P.bufs[bi];
+        const int64_t bytes = ((b.elems * 8 + 255) / 256) * 256;
+        std::vector<std::pair<int64_t, int64_t>> busy;
+        for (int pj : placed) {
+            const Buf &o = P.bufs[pj];
+            if (o.t1 < b.t0 || b.t1 < o.t0) continue;
+            busy.push_back({o.off, o.off + ((o.elems * 8 + 255) / 256) * 256});
+        }
+        std::sort(busy.begin(), busy.end());
+        int64_t off = 0;
+        for (auto &iv : busy) {
+            if (off + bytes <= iv.first) break;
+            off = std::max(off, iv.second);
+        }
+        b.off = off;
+        arena = std::max(arena, off + bytes);
+        placed.push_back(bi);
+    }
+    P.macs_batch = P.macs_prologue = P.bytes_batch = P.bytes_prologue = 0;
+    for (auto &op : P.prologue) { P.macs_prologue += op.macs; P.bytes_prologue += op.bytes; }
+    for (auto &op : P.batch) { P.macs_batch += op.macs; P.bytes_batch += op.bytes; }
+    P.launches_prologue = (int)P.prologue.size();
+    P.launches_batch = (int)P.batch.size() + (P.extract.empty() ? 0 : 1) + 1;
+    return arena;
+}
+
+float2 *resolve(tn_plan &P, const Operand &w) {
+    if (w.buf >= 0) return reinterpret_cast<float2 *>(P.d_arena + P.bufs[w.buf].off);
+    return P.d_leaves + w.leaf_off;
+}
+
+void resolve_all(tn_plan &P) {
+    auto fix = [&](Op &op) {
+        switch (op.kind) {
+        case OP_SMALL:
+            op.small.T = resolve(P, op.in0);
+            op.small.S = resolve(P, op.in1);
+            op.small.C = resolve(P, op.out);
+            break;
+        case OP_PERMUTE:
+            op.perm.in = resolve(P, op.in0);
+            op.perm.out = resolve(P, op.out);
+            break;
+        case OP_GEMM:
+            op.gemm.A = resolve(P, op.in0);
+            op.gemm.B = resolve(P, op.in1);
+            op.gemm.C = resolve(P, op.out);
+            break;
+        }
+    };
+    for (auto &op : P.prologue) fix(op);
+    for (auto &op : P.batch) fix(op);
+    for (auto &e : P.extract) {
+        int leaf = (int)(intptr_t)e.src;
+        int buf = (int)(intptr_t)e.dst;
+        e.src = P.d_leaves + P.leaf_off[leaf];
+        e.dst = reinterpret_cast<float2 *>(P.d_arena + P.bufs[buf].off);
+    }
+    P.accum.R = resolve(P, P.root);
+}
+
+cudaError_t run_op(const tn_plan &P, const Op &op, cudaStream_t s) {
+    switch (op.kind) {
+    case OP_SMALL: return launch_small(op.small, s);
+    case OP_PERMUTE: return launch_permute(op.perm, s);
+    case OP_GEMM:
+        if (op.gemm_variant == 1) return launch_gemm_tc(op.gemm, P.form, s);
+        return launch_gemm_f32(op.gemm, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(TN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *ranks, const int32_t *labels,
+                              const float *data, int n_labels, const int32_t *bond_dims, int n_open,
+                              const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels,
+                              int n_steps, const int32_t *tree, tn_form form, const tn_plan_opts *opts) {
+    if (!out) return fail(TN_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_tensors <= 0 || !ranks || !data) return fail(TN_ERR_ARG, "need at least one tensor");
+    if (n_open < 0 || n_open > kMaxRank || (n_open > 0 && !open_labels)) return fail(TN_ERR_ARG, "bad open labels");
+    if (n_sliced < 0 || n_sliced > 62 || (n_sliced > 0 && !sliced_labels)) return fail(TN_ERR_ARG, "bad sliced labels");
+    if (n_steps != n_tensors - 1 || (n_steps > 0 && !tree)) return fail(TN_ERR_ARG, "tree must have n_tensors - 1 steps");
+    if (form < TN_FP32 || form > TN_FP16S) return fail(TN_ERR_ARG, "unknown form");
+    if (form != TN_FP32 && !tc_form_available(form))
+        return fail(TN_ERR_ARG, "this arithmetic form is not available in this build");
+    std::unique_ptr<tn_plan> P(new tn_plan());
+    P->form = form;
+    if (opts) P->opts = *opts;
+    else {
+        std::memset(&P->opts, 0, sizeof P->opts);
+        P->opts.batch_log2 = -1;
+    }
+    P->n_tensors = n_tensors;
+    P->n_open = n_open;
+    P->n_sliced = n_sliced;
+    P->open.assign(open_labels, open_labels + n_open);
+    P->sliced.assign(sliced_labels, sliced_labels + n_sliced);
+    // labels: validity
+    std::unordered_map<int32_t, int> count;
+    size_t off = 0;
+    int64_t total = 0;
+    P->labels.resize(n_tensors);
+    P->leaf_off.resize(n_tensors);
+    for (int i = 0; i < n_tensors; i++) {
+        if (ranks[i] < 0 || ranks[i] > 30) return fail(TN_ERR_ARG, "tensor rank out of range [0, 30]");
+        P->labels[i].assign(labels + off, labels + off + ranks[i]);
+        off += ranks[i];
+        std::unordered_set<int32_t> seen;
+        for (int32_t x : P->labels[i]) {
+            if (x < 0) return fail(TN_ERR_ARG, "negative label");
+            if (n_labels > 0 && x >= n_labels) return fail(TN_ERR_ARG, "label >= n_labels");
+            if (bond_dims && bond_dims[x] != 2) return fail(TN_ERR_ARG, "only bond dimension 2 is supported");
+            if (!seen.insert(x).second) return fail(TN_ERR_ARG, "label repeated within a tensor");
+            count[x]++;
+        }
+        P->leaf_off[i] = total;
+        total += (int64_t)1 << ranks[i];
+    }
+    std::unordered_set<int32_t> open_set(P->open.begin(), P->open.end());
+    if ((int)open_set.size() != n_open) return fail(TN_ERR_ARG, "open label repeated");
+    for (auto &kv : count) {
+        if (kv.second > 2) return fail(TN_ERR_ARG, "label held by more than two tensors");
+        if (kv.second == 1 && !open_set.count(kv.first)) return fail(TN_ERR_ARG, "label held by one tensor must be open");
+        if (kv.second == 2 && open_set.count(kv.first)) return fail(TN_ERR_ARG, "open label held by two tensors");
+    }
+    for (int32_t x : P->open)
+        if (!count.count(x)) return fail(TN_ERR_ARG, "open label held by no tensor");
+    std::unordered_set<int32_t> sl;
+    for (int32_t x : P->sliced) {
+        if (open_set.count(x)) return fail(TN_ERR_ARG, "a sliced label cannot be open");
+        if (!count.count(x)) return fail(TN_ERR_ARG, "sliced label held by no tensor");
+        if (!sl.insert(x).second) return fail(TN_ERR_ARG, "sliced label repeated");
+    }
+    P->tree.resize(n_steps);
+    std::vector<char> used(2 * n_tensors, 0);
+    for (int t = 0; t < n_steps; t++) {
+        int a = tree[2 * t], b = tree[2 * t + 1];
+        if (a < 0 || b < 0 || a >= n_tensors + t || b >= n_tensors + t || a == b || used[a] || used[b])
+            return fail(TN_ERR_ARG, "tree: bad or reused node id");
+        used[a] = used[b] = 1;
+        P->tree[t] = {a, b};
+    }
+    // device
+    if (cudaGetDevice(&P->device) != cudaSuccess) return fail(TN_ERR_CUDA, "no CUDA device");
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    const int64_t budget = P->opts.mem_budget > 0 ? P->opts.mem_budget : (int64_t)(0.6 * (double)free_b);
+    const int64_t leaf_bytes = total * 8;
+    int nb_max = n_sliced;
+    if (P->opts.batch_log2 >= 0) nb_max = std::min(nb_max, (int)P->opts.batch_log2);
+    int64_t arena = -1;
+    int nb = nb_max;
+    for (; nb >= 0; nb--) {
+        arena = compile(*P, nb);
+        if (arena < 0) return TN_ERR_ARG;
+        if (arena + leaf_bytes <= budget) break;
+    }
+    if (nb < 0) return fail(TN_ERR_OOM, "the plan does not fit the memory budget even without batching");
+    P->arena_bytes = arena;
+    e = cudaMalloc(&P->d_leaves, std::max<int64_t>(leaf_bytes, 16));
+    if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc leaves");
+    e = cudaMemcpy(P->d_leaves, data, leaf_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "copy leaves");
+    e = cudaMalloc(&P->d_arena, std::max<int64_t>(arena, 256));
+    if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc arena");
+    resolve_all(*P);
+    if (!P->extract.empty()) {
+        e = cudaMalloc(&P->d_extract, sizeof(ExtractEntry) * P->extract.size());
+        if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc extract table");
+        e = cudaMemcpy(P->d_extract, P->extract.data(), sizeof(ExtractEntry) * P->extract.size(),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "copy extract table");
+    }
+    *out = P.release();
+    return TN_OK;
+}
+
+extern "C" int tn_contract_slices(tn_plan_t P, int64_t begin, int64_t end, double *d_amp, tn_stream_t stream) {
+    if (!P) return fail(TN_ERR_ARG, "plan is NULL");
+    if (P->failed) return fail(TN_ERR_STATE, "plan is in a failed state");
+    const int64_t S = (int64_t)1 << P->n_sliced;
+    if (begin < 0 || end > S || begin > end) return fail(TN_ERR_ARG, "slice range outside [0, 2^n_sliced)");
+    if (!d_amp) return fail(TN_ERR_ARG, "d_amp is NULL");
+    if (begin == end) return TN_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    for (auto &op : P->prologue)
+        if ((e = run_op(*P, op, s)) != cudaSuccess) { P->failed = true; return cuda_fail(e, "prologue launch"); }
+    const int64_t B = (int64_t)1 << P->nb;
+    AccumArgs acc = P->accum;
+    acc.amp = reinterpret_cast<double2 *>(d_amp);
+    for (int64_t base = (begin / B) * B; base < end; base += B) {
+        if ((e = launch_extract(P->d_extract, (int)P->extract.size(), P->extract_max_out, (uint64_t)base, s)) !=
+            cudaSuccess) { P->failed = true; return cuda_fail(e, "extract launch"); }
+        for (auto &op : P->batch)
+            if ((e = run_op(*P, op, s)) != cudaSuccess) { P->failed = true; return cuda_fail(e, "step launch"); }
+        acc.b_lo = std::max(begin, base) - base;
+        acc.b_hi = std::min(end, base + B) - base;
+        if ((e = launch_accum(acc, s)) != cudaSuccess) { P->failed = true; return cuda_fail(e, "accumulate launch"); }
+    }
+    if (P->opts.profile) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { P->failed = true; return cuda_fail(e, "contract"); }
+    }
+    return TN_OK;
+}
+
+extern "C" void tn_plan_destroy(tn_plan_t P) {
+    if (!P) return;
+    if (P->d_leaves) cudaFree(P->d_leaves);
+    if (P->d_arena) cudaFree(P->d_arena);
+    if (P->d_extract) cudaFree(P->d_extract);
+    delete P;
+}
+
+extern "C" int tn_plan_stats(tn_plan_t P, double *out) {
+    if (!P || !out) return fail(TN_ERR_ARG, "NULL argument");
+    out[0] = P->macs_batch;
+    out[1] = (double)((int64_t)1 << P->nb);
+    out[2] = (double)P->arena_bytes;
+    out[3] = (double)P->tree.size();
+    out[4] = (double)P->launches_batch;
+    out[5] = P->bytes_batch;
+    out[6] = P->macs_prologue;
+    out[7] = P->bytes_prologue;
+    out[8] = (double)P->launches_prologue;
+    out[9] = (double)P->nb;
+    return TN_OK;
+}
+
+extern "C" int tn_probabilities_xeb(const double *d_amp, int n_open, int n_qubits, double *d_prob, double *out,
+                                    tn_stream_t stream) {
+    if (!d_amp || !out || n_open < 0 || n_open > 40) return fail(TN_ERR_ARG, "bad arguments");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double *d_out = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_out, 3 * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    e = launch_prob_xeb(reinterpret_cast<const double2 *>(d_amp), (int64_t)1 << n_open, d_prob, d_out, s);
+    double h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "probabilities");
+    out[0] = h[0];
+    out[1] = std::ldexp(h[0], n_qubits - n_open) - 1.0;
+    out[2] = h[2];
+    return TN_OK;
+}
+
+extern "C" int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bits, int n_open,
+                             const int32_t *open_qubits, tn_form form, const tn_search_opts *search,
+                             const tn_plan_opts *opts, double *d_amp, tn_stream_t stream) {
+    if (!d_amp) return fail(TN_ERR_ARG, "d_amp is NULL");
+    Network net;
+    int rc = build_circuit_network(circuit, fixed_bits, n_open, open_qubits, net);
+    if (rc) return rc;
+    std::vector<std::vector<int32_t>> labs;
+    for (auto &t : net.tensors) labs.push_back(t.labels);
+    tn_search_opts so = search ? *search : default_search_opts();
+    SearchResult r;
+    rc = search_order(labs, net.open, so, r);
+    if (rc) return rc;
+    std::vector<int32_t> ranks, flat, tree;
+    std::vector<float> data;
+    for (auto &t : net.tensors) {
+        ranks.push_back(t.rank());
+        flat.insert(flat.end(), t.labels.begin(), t.labels.end());
+        for (auto &v : t.data) {
+            data.push_back((float)v.real());
+            data.push_back((float)v.imag());
+        }
+    }
+    for (auto &pr : r.tree) {
+        tree.push_back(pr.first);
+        tree.push_back(pr.second);
+    }
+    tn_plan_t plan = nullptr;
+    rc = tn_plan_create(&plan, (int)net.tensors.size(), ranks.data(), flat.data(), data.data(), 0, nullptr,
+                        n_open, net.open.data(), (int)r.sliced.size(), r.sliced.data(), (int)r.tree.size(),
+                        tree.data(), form, opts);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(d_amp, 0, sizeof(double) * 2 * ((size_t)1 << n_open), s);
+    if (e != cudaSuccess) { tn_plan_destroy(plan); return cuda_fail(e, "zero amplitudes"); }
+    rc = tn_contract_slices(plan, 0, (int64_t)1 << r.sliced.size(), d_amp, stream);
+    if (rc == TN_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "contract");
+    }
+    tn_plan_destroy(plan);
+    return rc;
+}

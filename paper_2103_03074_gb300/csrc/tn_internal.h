@@ -1,0 +1,57 @@
+// Internal host-side structures of libtn (not part of the C ABI).
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "tn.h"
+
+namespace tn {
+
+using cd = std::complex<double>;
+
+// A dense tensor with bond dimension 2 on every axis; labels[0] is the most
+// significant axis of the row-major value array.
+struct Tensor {
+    std::vector<int32_t> labels;
+    std::vector<cd> data;  // 2^rank values
+    int rank() const { return (int)labels.size(); }
+};
+
+struct Network {
+    std::vector<Tensor> tensors;
+    std::vector<int32_t> open;  // amplitude axis order
+};
+
+// SSA contraction tree: leaves 0..n-1, step t makes node n + t.
+using Tree = std::vector<std::pair<int, int>>;
+
+struct SearchResult {
+    Tree tree;
+    std::vector<int32_t> sliced;
+    double log2_total = 0;   // log2 MACs over all slices
+    double log2_width = 0;   // log2 largest intermediate per slice
+    double log2_slice = 0;   // log2 MACs per slice
+};
+
+// error reporting (thread-local message)
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+// network.cpp: circuit -> network (single-qubit gates absorbed)
+int build_circuit_network(const tn_circuit *c, const uint8_t *fixed_bits, int n_open,
+                          const int32_t *open_qubits, Network &out);
+
+// order.cpp: randomised greedy order + greedy slicing
+int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                 const tn_search_opts &opts, SearchResult &out);
+
+// evaluate a given tree + slice set (log2 costs); returns false on a malformed tree
+bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                   const Tree &tree, const std::vector<int32_t> &sliced, SearchResult &out);
+
+tn_search_opts default_search_opts();
+
+}  // namespace tn

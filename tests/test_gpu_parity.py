@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU FP64 oracle.
+
+Tolerance: relative L2 error <= 1e-5 for complex64 forms (the bound the
+workload states for FP32 and split-precision forms); XEB within 1e-4 absolute.
+Expected values come from oracle/ or from stored oracle output
+(tests/golden/, written by tests/golden/make_golden.py).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from tn_inputs import random_network, random_tree, sycamore_circuit, random_bits, segment_labels, SplitMix64
+from tn_inputs.configs import make_config
+from oracle import contract as oc, network as onet, statevector as osv, xeb as oxeb
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_03074_gb300 as tn
+    return tn
+
+
+def rel(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev_zeros(k):
+    import torch
+    return torch.zeros(2 << k, dtype=torch.float64, device="cuda:0")
+
+
+def to_complex(t):
+    import torch
+    torch.cuda.synchronize()
+    a = t.cpu().numpy()
+    return a[0::2] + 1j * a[1::2]
+
+
+def internal_labels(labels):
+    cnt = {}
+    for l in labels:
+        for x in l:
+            cnt[x] = cnt.get(x, 0) + 1
+    return sorted(x for x, c in cnt.items() if c == 2)
+
+
+def pick(seed, items, k):
+    rng = SplitMix64(seed)
+    p = rng.permutation(len(items))
+    return [items[i] for i in p[:k]]
+
+
+@pytest.mark.parametrize("seed,batch_log2,tree_kind", [
+    (1, 0, "random"), (2, 2, "random"), (3, 4, "search"), (4, -1, "search"), (5, 1, "random")])
+def test_random_network_sliced(tn, seed, batch_log2, tree_kind):
+    net = random_network(seed, n_tensors=12, n_bonds=22, n_open=3, max_rank=7)
+    sliced = pick(seed + 7, internal_labels(net.labels), 4)
+    if tree_kind == "random":
+        tree = random_tree(seed + 11, len(net.labels))
+    else:
+        tree, _, _ = tn.find_order(net.labels, net.open_labels, tn.search_opts(trials=16, n_sliced=0))
+    plan = tn.Plan(net.labels, net.data, net.open_labels, sliced, tree,
+                   opts=tn.plan_opts(batch_log2=batch_log2))
+    k = len(net.open_labels)
+    full = dev_zeros(k)
+    plan.contract(0, 16, full)
+    ref = oc.sliced_sum(net.labels, net.data, net.open_labels, sliced)
+    assert rel(to_complex(full), ref) < TOL
+    # ragged range and single slices
+    part = dev_zeros(k)
+    plan.contract(3, 11, part)
+    assert rel(to_complex(part), oc.sliced_sum(net.labels, net.data, net.open_labels, sliced, 3, 11)) < TOL
+    for s in (0, 5, 15):
+        one = dev_zeros(k)
+        plan.contract(s, s + 1, one)
+        assert rel(to_complex(one), oc.slice_partial(net.labels, net.data, net.open_labels, sliced, s)) < TOL
+    plan.close()
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_gemm_path_large_operands(tn, seed):
+    # ranks large enough that both operands of late steps exceed the small-step
+    # limit, so the strided batched GEMM (and permutes) run
+    net = random_network(seed, n_tensors=16, n_bonds=44, n_open=4, max_rank=10)
+    tree, _, st = tn.find_order(net.labels, net.open_labels, tn.search_opts(trials=8, n_sliced=0))
+    sliced = pick(seed, internal_labels(net.labels), 3)
+    for bl in (0, 3):
+        plan = tn.Plan(net.labels, net.data, net.open_labels, sliced, tree, opts=tn.plan_opts(batch_log2=bl))
+        amp = dev_zeros(4)
+        plan.contract(0, 8, amp)
+        ref = oc.contract(net.labels, net.data, net.open_labels)
+        assert rel(to_complex(amp), ref) < TOL
+        plan.close()
+
+
+def test_range_composition_and_empty(tn):
+    net = random_network(9, n_tensors=10, n_bonds=18, n_open=2, max_rank=7)
+    sliced = pick(3, internal_labels(net.labels), 5)
+    tree = random_tree(4, len(net.labels))
+    plan = tn.Plan(net.labels, net.data, net.open_labels, sliced, tree, opts=tn.plan_opts(batch_log2=2))
+    a = dev_zeros(2)
+    plan.contract(0, 13, a)
+    plan.contract(13, 32, a)
+    plan.contract(7, 7, a)  # empty: adds nothing
+    b = dev_zeros(2)
+    plan.contract(0, 32, b)
+    assert rel(to_complex(a), to_complex(b)) < 1e-6
+    assert rel(to_complex(b), oc.contract(net.labels, net.data, net.open_labels)) < TOL
+    with pytest.raises(tn.TNError):
+        plan.contract(0, 33, a)
+    with pytest.raises(tn.TNError):
+        plan.contract(5, 4, a)
+    plan.close()
+
+
+@pytest.mark.parametrize("n_sliced", [0, 3])
+def test_cfg1_amplitudes(tn, n_sliced):
+    cfg = make_config(1)
+    amp = dev_zeros(12)
+    tn.amplitudes(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"], amp,
+                  search=tn.search_opts(trials=64, n_sliced=n_sliced))
+    ref = osv.amplitudes(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    assert rel(to_complex(amp), ref) < TOL
+
+
+def test_partial_open_circuit_per_slice(tn):
+    # 20 qubits, 10 cycles, 6 open; 4 sliced bonds picked by the test from the
+    # circuit's own wire segments; each slice against the oracle's own network
+    circ = sycamore_circuit("rect", 4, 5, 10, 31)
+    bits = random_bits(20, 32)
+    open_q = [14, 15, 16, 17, 18, 19]
+    offs, count = segment_labels(circ)
+    seg = [0] * 20
+    after2 = {q: [] for q in range(20)}
+    for g in circ.gates:
+        for q in g.qubits:
+            seg[q] += 1
+        if len(g.qubits) == 2:
+            for q in g.qubits:
+                after2[q].append(offs[q] + seg[q])
+    bonds = sorted(x for q in range(20) for x in after2[q][:-1])
+    sliced = pick(77, bonds, 4)
+    L, T, O = tn.circuit_network(circ, bits, open_q)
+    assert set(sliced) <= set(internal_labels(L))
+    tree, _, _ = tn.find_order(L, O, tn.search_opts(trials=64, n_sliced=0))
+    plan = tn.Plan(L, T, O, sliced, tree, opts=tn.plan_opts(batch_log2=2))
+    oL, oT, oO = onet.circuit_network(circ, bits, open_q)
+    for s in (0, 9, 15):
+        one = dev_zeros(6)
+        plan.contract(s, s + 1, one)
+        ref = oc.slice_partial(oL, oT, oO, sliced, s)
+        assert rel(to_complex(one), ref) < TOL
+    full = dev_zeros(6)
+    plan.contract(0, 16, full)
+    assert rel(to_complex(full), osv.amplitudes(circ, bits, open_q)) < TOL
+    plan.close()
+
+
+def load_golden(name):
+    path = os.path.join(HERE, "golden", name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    vals = []
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        i, re_, im_ = line.split()
+        vals.append(complex(float(re_), float(im_)))
+    return np.array(vals)
+
+
+def test_cfg2_amplitudes_vs_golden(tn):
+    """The 30-qubit workload exactly as the benchmark plans it: 8 sliced bonds
+    from the order search, all 2^8 slices in one batch, FP32 form."""
+    cfg = make_config(2)
+    ref = load_golden("cfg2_amplitudes.txt")
+    amp = dev_zeros(8)
+    tn.amplitudes(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"], amp,
+                  search=tn.search_opts(trials=256, n_sliced=8))
+    got = to_complex(amp)
+    assert rel(got, ref) < TOL
+    # XEB from the GPU probabilities against the oracle's, 1e-4 absolute
+    p_s1, f, pmax = tn.probabilities_xeb(amp, 8, 30)
+    assert abs(f - oxeb.linear_xeb(ref, 30)) < 1e-4
+    assert abs(p_s1 - oxeb.marginal(ref)) < 1e-5 * oxeb.marginal(ref)
+
+
+def test_probabilities_xeb_on_oracle_amplitudes(tn):
+    import torch
+    cfg = make_config(1)
+    ref = osv.amplitudes(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"][:8])
+    inter = np.stack([ref.real, ref.imag], axis=1).reshape(-1)
+    d = torch.tensor(inter, dtype=torch.float64, device="cuda:0")
+    prob = torch.zeros(256, dtype=torch.float64, device="cuda:0")
+    p_s1, f, pmax = tn.probabilities_xeb(d, 8, 12, d_prob=prob)
+    p = oxeb.probabilities(ref)
+    assert np.abs(prob.cpu().numpy() - p).max() < 1e-15
+    assert abs(p_s1 - p.sum()) < 1e-14
+    assert abs(f - oxeb.linear_xeb(ref, 12)) < 1e-12
+    assert abs(pmax - p.max()) < 1e-18

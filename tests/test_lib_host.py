@@ -1,0 +1,128 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every
+symbol include/tn.h declares, builds the circuit network the oracle agrees
+with, finds valid orders, and rejects malformed input before touching CUDA."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tn_inputs import random_network, sycamore_circuit, random_bits
+from tn_inputs.configs import make_config
+from oracle import contract as oc, statevector as osv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_03074_gb300 as tn
+    return tn
+
+
+def test_exports_every_declared_symbol(tn):
+    header = open(os.path.join(ROOT, "include", "tn.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char \*)\s*(tn_\w+)\s*\(", header, re.M))
+    assert {"tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_plan_destroy", "tn_last_error"} <= declared
+    for name in declared:
+        assert hasattr(tn._lib, name), name
+    assert declared == set(tn.EXPORTED)
+
+
+@pytest.mark.parametrize("cfg_idx", [1])
+def test_circuit_network_matches_statevector(tn, cfg_idx):
+    cfg = make_config(cfg_idx)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    got = oc.contract(L, [np.asarray(t, np.complex128) for t in T], O).reshape(-1)
+    ref = osv.amplitudes(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    # complex64 leaves: error of order 1e-7 relative
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-6
+
+
+def test_circuit_network_partial_open_and_labels(tn):
+    circ = sycamore_circuit("rect", 3, 3, 6, 4)
+    bits = random_bits(9, 1)
+    open_q = [7, 2, 5]
+    L, T, O = tn.circuit_network(circ, bits, open_q)
+    # every leaf is a two-qubit gate of rank <= 4; labels held at most twice
+    assert all(len(l) <= 4 for l in L)
+    cnt = {}
+    for l in L:
+        for x in l:
+            cnt[x] = cnt.get(x, 0) + 1
+    assert all(c in (1, 2) for c in cnt.values())
+    assert {x for x, c in cnt.items() if c == 1} == set(O)
+    # open labels are the final wire segments (wire-segment convention)
+    from tn_inputs import segment_labels
+    offs, count = segment_labels(circ)
+    assert O == [offs[q] + count[q] for q in open_q]
+    got = oc.contract(L, [np.asarray(t, np.complex128) for t in T], O).reshape(-1)
+    ref = osv.amplitudes(circ, bits, open_q)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-6
+
+
+def test_find_order_valid_tree_and_slices(tn):
+    net = random_network(5, n_tensors=14, n_bonds=22, n_open=3, max_rank=6)
+    tree, sliced, st = tn.find_order(net.labels, net.open_labels, tn.search_opts(trials=32, n_sliced=3))
+    n = len(net.labels)
+    used = set()
+    for t, (a, b) in enumerate(tree):
+        assert 0 <= a < n + t and 0 <= b < n + t and a != b
+        assert a not in used and b not in used
+        used |= {a, b}
+    assert len(tree) == n - 1
+    assert len(sliced) == 3 and not set(sliced) & set(net.open_labels)
+    # the result of the tree does not depend on it: oracle contraction with
+    # this tree equals its own greedy contraction
+    ref = oc.contract(net.labels, net.data, net.open_labels)
+    got = oc.contract(net.labels, net.data, net.open_labels, tree=tree)
+    assert np.abs(got - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_find_order_cap_reduces_width(tn):
+    cfg = make_config(2)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    _, _, st0 = tn.find_order(L, O, tn.search_opts(trials=16, n_sliced=0))
+    _, sl, st1 = tn.find_order(L, O, tn.search_opts(trials=16, log2_cap=int(st0["log2_width"]) - 4))
+    assert st1["log2_width"] <= st0["log2_width"] - 4
+    assert len(sl) == st1["n_sliced"] >= 4
+
+
+def test_search_is_deterministic(tn):
+    cfg = make_config(1)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    a = tn.find_order(L, O, tn.search_opts(trials=64, threads=1, n_sliced=2))
+    b = tn.find_order(L, O, tn.search_opts(trials=64, threads=4, n_sliced=2))
+    assert a[0] == b[0] and a[1] == b[1]
+
+
+def _plan_args_error(tn, **kw):
+    net = random_network(3, n_tensors=5, n_bonds=7, n_open=2, max_rank=5)
+    labels = kw.get("labels", net.labels)
+    open_l = kw.get("open", net.open_labels)
+    sliced = kw.get("sliced", [])
+    tree = kw.get("tree", [(0, 1), (5, 2), (6, 3), (7, 4)])
+    with pytest.raises(tn.TNError) as ei:
+        tn.Plan(labels, net.data, open_l, sliced, tree)
+    return ei.value
+
+
+def test_plan_rejects_sliced_open_label(tn):
+    net = random_network(3, n_tensors=5, n_bonds=7, n_open=2, max_rank=5)
+    err = _plan_args_error(tn, sliced=[net.open_labels[0]])
+    assert err.code == -1 and "open" in str(err)
+
+
+def test_plan_rejects_bad_tree(tn):
+    err = _plan_args_error(tn, tree=[(0, 1), (0, 2), (6, 3), (7, 4)])
+    assert err.code == -1
+    err = _plan_args_error(tn, tree=[(0, 1)])
+    assert err.code == -1
+
+
+def test_plan_rejects_dangling_label(tn):
+    net = random_network(3, n_tensors=5, n_bonds=7, n_open=2, max_rank=5)
+    err = _plan_args_error(tn, open=net.open_labels[:1])
+    assert err.code == -1
