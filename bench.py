@@ -1,0 +1,418 @@
+"""Benchmark of the sliced big-head contraction on one GB300 (or N, one process
+per GPU under torchrun).
+
+Workload: the 30-qubit 5x6 grid, 12 cycles, 8 open qubits, the other 22 fixed
+to a seeded bitstring, 8 sliced bonds chosen by the order search (2^8 slices).
+One step = every slice contracted and summed into the FP64 amplitude tensor,
+then the FP64 probability / XEB reduction (all kernels of the hot path).
+
+Metric: slices/s (and complex TFLOP/s = 8 x complex MACs / s).
+  value     device time (CUDA events on the launching stream), L2 flushed
+            between steps outside the timed events.
+  e2e       the same through the C-ABI with host buffers: every step copies
+            the leaf values host->device (pinned) and reads the amplitudes back.
+  roofline  of the dominant kernel class, from the step-timing recorder's
+            CUDA events in a second pass of the same steps.
+  cpu_baseline  the CPU FP64 oracle (its own network, the same sliced bonds)
+            timed on a bounded sample of slices on this host.
+
+--impl reference times the CPU oracle as the reference arm.
+Multi-GPU (torchrun): each rank contracts its own seeded instance (weak
+scaling, no collective on the data path); time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS = 152
+FP32_LANES_PER_SM = 128
+METRIC = "slices/s & complex TFLOP/s per GB300 at <=1e-5 amp err, split-TC vs plain FP32"
+
+
+def peaks():
+    if os.path.exists(MEASURED_PEAKS):
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=p["hbm_gbs"], bf16_tflops=p["bf16_tflops"],
+                    bf16_tflops_sustained=p.get("bf16_tflops_sustained", p["bf16_tflops"]),
+                    sm_max_mhz=p.get("sm_max_mhz", 2070.0), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0,
+                source="fallback")
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
+    return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over ranks (identity at world 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def instance_seed_offset(rank):
+    """Rank r contracts its own seeded instance (weak scaling)."""
+    return 1000 * rank
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(seed_offset=0):
+    from tn_inputs.configs import make_config, CONFIGS
+    import tn_inputs
+    cfg = make_config(2)
+    if seed_offset:
+        c = CONFIGS[2]
+        cfg["circuit"] = tn_inputs.sycamore_circuit(c["layout"], c["rows"], c["cols"], c["cycles"],
+                                                    c["seed"] + seed_offset)
+    return cfg
+
+
+def cpu_oracle_rate(cfg, sliced, budget_s=15.0, max_slices=4):
+    """Slices/s of the CPU oracle (its own network, same sliced bonds) on a
+    bounded sample; returns (slices/s, sample description, cores)."""
+    from oracle import network as onet, contract as oc
+    L, T, O = onet.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    done = 0
+    t0 = time.perf_counter()
+    while done < max_slices:
+        oc.slice_partial(L, T, O, sliced, done)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return done / dt, f"{done} slices (ids 0..{done - 1}) of the 2^{len(sliced)}-slice workload, FP64 numpy", cores
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    import paper_2103_03074_gb300 as tn
+    cfg = workload()
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    _, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
+    from oracle import network as onet, contract as oc
+    oL, oT, oO = onet.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    for w in range(args.warmup):
+        oc.slice_partial(oL, oT, oO, sliced, w % 256)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oc.slice_partial(oL, oT, oO, sliced, k % 256)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Sycamore-style circuit)",
+            "config": {"workload": "rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 2^8 slices",
+                       "step": "one slice contracted by the CPU FP64 oracle"},
+            "cpu_baseline": {"value": v, "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} slices per timed run, one per step"},
+            "e2e": {"value": v, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def load_golden_amplitudes():
+    """The workload's amplitudes from the stored FP64 oracle output, if present."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "cfg2_amplitudes.txt")
+    if not os.path.exists(path):
+        return None
+    vals = [complex(float(l.split()[1]), float(l.split()[2])) for l in open(path) if not l.startswith("#")]
+    return np.array(vals)
+
+
+def l2_flush_buffer(torch):
+    return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+
+def time_steps(torch, plan, n_slices, amp, steps, warmup, stream, flush, n_open, n_qubits, d_out):
+    """Sum of per-step device times (ms); L2 flushed before each step, untimed."""
+    import paper_2103_03074_gb300 as tn
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            amp.zero_()
+            plan.contract(0, n_slices, amp, stream)
+            tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
+        stream.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            amp.zero_()
+            plan.contract(0, n_slices, amp, stream)
+            tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
+            evs[k][1].record(stream)
+        stream.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build_library()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_2103_03074_gb300 as tn
+
+    pk = peaks()
+    cfg = workload(instance_seed_offset(rank))
+    n_qubits = cfg["circuit"].n_qubits
+    n_open = len(cfg["open_qubits"])
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
+    n_slices = 1 << len(sliced)
+    forms = [args.form] if args.form != "all" else ["fp32", "tf32x3", "bf16x3"]
+    golden = load_golden_amplitudes() if rank == 0 and instance_seed_offset(rank) == 0 else None
+    stream = torch.cuda.Stream()
+    flush = l2_flush_buffer(torch)
+    amp = torch.zeros(2 << n_open, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    results = {}
+    for form in forms:
+        try:
+            plan = tn.Plan(L, T, O, sliced, tree, form=form)
+        except tn.TNError as e:
+            results[form] = {"error": str(e)}
+            continue
+        stats = plan.stats()
+        macs_step = stats["macs_batch"] * (n_slices / stats["slices_per_batch"]) + stats["macs_prologue"]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            ms = time_steps(torch, plan, n_slices, amp, args.steps, args.warmup, stream, flush, n_open,
+                            n_qubits, d_out)
+        ms = max_over_ranks(ms, world, device="cuda")
+        per_step = ms / args.steps
+        err = None
+        if golden is not None:
+            a = amp.cpu().numpy()
+            got = a[0::2] + 1j * a[1::2]
+            err = float(np.linalg.norm(got - golden) / np.linalg.norm(golden))
+        res = {"ms_per_step": per_step, "slices_per_s": world * n_slices / (per_step / 1e3), "rel_l2_err": err,
+               "complex_tflops": world * 8 * macs_step / (per_step / 1e3) / 1e12, "clocks": clk.summary(),
+               "plan": stats, "macs_per_step": macs_step,
+               "launches_per_step": stats["launches_prologue"] + stats["launches_batch"] *
+               (n_slices / stats["slices_per_batch"]) + 2}
+        # roofline: per-op CUDA events (step-timing recorder) over the same steps
+        pplan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(profile=1))
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                pplan.contract(0, n_slices, amp, stream)
+            pplan.profile(reset=True)
+            for _ in range(args.steps):
+                pplan.contract(0, n_slices, amp, stream)
+        rows = pplan.profile()
+        pplan.close()
+        by_kind = {}
+        for r in rows:
+            d = by_kind.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "macs": 0.0, "bytes": 0.0})
+            d["ms"] += r["ms"]
+            d["launches"] += r["launches"]
+            d["macs"] += r["macs"] * r["launches"]
+            d["bytes"] += r["bytes"] * r["launches"]
+        total_ms = sum(d["ms"] for d in by_kind.values())
+        top = max(by_kind, key=lambda k: by_kind[k]["ms"])
+        d = by_kind[top]
+        avg_ms = d["ms"] / max(d["launches"], 1)
+        if top == "gemm" and form == "fp32":
+            peak = fp32_alu_peak_tflops(pk["sm_max_mhz"])
+            achieved = 8 * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "gemm_f32_kernel (complex FP32 FMA)",
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
+        elif top == "gemm":
+            # split form: tensor-core flops the method issues per complex MAC
+            # (4 real products x 3 split products x 2 flops); TF32 peak = half
+            # of the measured BF16 peak (nominal dense ratio 1.1 : 2.25)
+            per_mac = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16s": 8.0}[form]
+            peak = pk["bf16_tflops"] * ({"bf16x3": 1.0, "tf32x3": 0.5, "fp16s": 1.0}[form])
+            achieved = per_mac * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "tc_gemm (tcgen05 split form)",
+                    "peak_source": pk["source"]}
+        else:
+            achieved = d["bytes"] / d["launches"] / (avg_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": top, "peak_source": pk["source"]}
+        roof["share_of_step"] = d["ms"] / total_ms if total_ms else None
+        roof["launches_per_step"] = d["launches"] / args.steps
+        res["roofline"] = roof
+        res["kernel_time_share"] = {k: v["ms"] / total_ms for k, v in by_kind.items()}
+        # end to end through the C-ABI with host buffers
+        data = np.concatenate([np.stack([np.asarray(t, np.complex64).reshape(-1).real,
+                                         np.asarray(t, np.complex64).reshape(-1).imag], 1).reshape(-1)
+                               for t in T]).astype(np.float32)
+        h_in = torch.from_numpy(data).pin_memory()
+        h_out = torch.empty(2 << n_open, dtype=torch.float64).pin_memory()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                plan.update_data(h_in, stream)
+                amp.zero_()
+                plan.contract(0, n_slices, amp, stream)
+                tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
+                h_out.copy_(amp, non_blocking=True)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                plan.update_data(h_in, stream)
+                amp.zero_()
+                plan.contract(0, n_slices, amp, stream)
+                tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
+                h_out.copy_(amp, non_blocking=True)
+            e1.record(stream)
+            stream.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, device="cuda") / args.steps
+        res["e2e"] = {"value": world * n_slices / (e2e_ms / 1e3), "unit": "slices/s",
+                      "h2d_bytes_per_step": int(data.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 8)}
+        results[form] = res
+        plan.close()
+    ok = [f for f in forms if "error" not in results[f]]
+    if not ok:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "error": {f: results[f]["error"] for f in forms}}))
+        return 1
+    # headline: the fastest form within the 1e-5 amplitude error bound
+    within = [f for f in ok if results[f]["rel_l2_err"] is None or results[f]["rel_l2_err"] <= 1e-5]
+    best = max(within or ok, key=lambda f: results[f]["slices_per_s"])
+    r = results[best]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample, cores = cpu_oracle_rate(cfg, sliced)
+        cpu = {"value": rate, "unit": "slices/s", "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": r["slices_per_s"], "unit": "slices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)",
+                                       "tf32x3": "tf32x3", "fp16s": "f16"}[best],
+        "data": "synthetic (seeded Sycamore-style circuit, random bitstring)",
+        "config": {"workload": "rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 22 fixed, "
+                               "2^8 slices over 8 searched bonds", "form": best,
+                   "step": "all 256 slices summed in FP64 + probabilities/XEB",
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                   "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
+                   "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"]},
+        "complex_tflops": r["complex_tflops"],
+        "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
+                       "rel_l2_err_vs_fp64_oracle": results[f]["rel_l2_err"],
+                       "ms_per_step": results[f]["ms_per_step"], "roofline": results[f]["roofline"],
+                       "kernel_time_share": results[f]["kernel_time_share"]}
+                      if "error" not in results[f] else results[f]) for f in forms},
+        "roofline": r["roofline"],
+        "cpu_baseline": cpu,
+        "e2e": r["e2e"],
+        "clocks": r["clocks"],
+        "gpu_launches": int(r["launches_per_step"] * args.steps),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16s", "all"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

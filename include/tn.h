@@ -141,12 +141,35 @@ int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bits, int n_op
 
 /*
  * Probabilities and linear XEB (Eq. 1) of an amplitude tensor on the device, in
- * FP64: writes d_prob[i] = |amp_i|^2 (may be NULL) and, to host out[3]:
- * out[0] = sum_i p_i (the marginal P(s1)), out[1] = F_XEB = 2^n_qubits / L *
- * sum p - 1 with L = 2^n_open, out[2] = max p.  Synchronises `stream`.
+ * FP64 (marginal and conditional probabilities: appendix on P(s1), P(s2|s1)).
+ * Writes d_prob[i] = |amp_i|^2 (may be NULL) and d_out[3] (device, required):
+ * d_out[0] = sum_i p_i (the marginal P(s1)), d_out[1] = F_XEB = 2^n_qubits / L *
+ * sum p - 1 with L = 2^n_open, d_out[2] = max p.  If `out` (host, 3 doubles) is
+ * non-NULL the three values are copied there and `stream` is synchronised;
+ * otherwise the call only enqueues work.
  */
 int tn_probabilities_xeb(const double *d_amp, int n_open, int n_qubits, double *d_prob,
-                         double *out, tn_stream_t stream);
+                         double *d_out, double *out, tn_stream_t stream);
+
+/*
+ * Replace the leaf values of a plan (same layout as tn_plan_create's `data`,
+ * host memory, pinned or pageable) with an asynchronous copy on `stream`; the
+ * next tn_contract_slices on that stream sees the new values.  The host
+ * buffer must stay valid until the copy completes.
+ */
+int tn_plan_update_data(tn_plan_t plan, const float *data, tn_stream_t stream);
+
+/*
+ * Step-timing recorder.  With tn_plan_opts.profile = 1 every kernel of a
+ * tn_contract_slices call is bracketed by CUDA events and the call
+ * synchronises; durations accumulate per op.  Writes up to max_rows rows of 8
+ * doubles: {phase (0 slice-invariant prologue, 1 per slice block), op index,
+ * kind (0 small step, 1 permute, 2 GEMM, 3 extract, 4 FP64 sum, 5 hi/lo split), tree step,
+ * total ms, launches, complex MACs per launch, algorithmic bytes per launch}
+ * and returns the number of rows (negative on error).  reset != 0 clears the
+ * totals after reading.
+ */
+int tn_plan_profile(tn_plan_t plan, int max_rows, double *rows, int reset);
 
 void tn_plan_destroy(tn_plan_t plan);
 

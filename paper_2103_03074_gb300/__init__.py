@@ -50,7 +50,9 @@ _lib.tn_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, _vp
 _lib.tn_contract_slices.argtypes = [_vp, _i64, _i64, _vp, _vp]
 _lib.tn_amplitudes.argtypes = [ctypes.POINTER(Circuit), _vp, ctypes.c_int, _vp, ctypes.c_int,
                                ctypes.POINTER(SearchOpts), ctypes.POINTER(PlanOpts), _vp, _vp]
-_lib.tn_probabilities_xeb.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+_lib.tn_probabilities_xeb.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.tn_plan_update_data.argtypes = [_vp, _vp, _vp]
+_lib.tn_plan_profile.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int]
 _lib.tn_plan_destroy.argtypes = [_vp]
 _lib.tn_plan_destroy.restype = None
 _lib.tn_find_order.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(SearchOpts), _vp,
@@ -60,7 +62,9 @@ _lib.tn_circuit_network.argtypes = [ctypes.POINTER(Circuit), _vp, ctypes.c_int, 
 _lib.tn_plan_stats.argtypes = [_vp, _vp]
 
 EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabilities_xeb", "tn_plan_destroy",
-            "tn_last_error", "tn_find_order", "tn_circuit_network", "tn_plan_stats"]
+            "tn_last_error", "tn_find_order", "tn_circuit_network", "tn_plan_stats", "tn_plan_update_data",
+            "tn_plan_profile"]
+PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split"}
 
 
 class TNError(RuntimeError):
@@ -198,6 +202,27 @@ class Plan:
         _check(_lib.tn_contract_slices(self._h, int(begin), int(end), _vp(d_amp_ptr),
                                        _vp(stream_ptr) if stream_ptr else None), "tn_contract_slices")
 
+    def update_data(self, data_f32, stream=None):
+        """Async H2D copy of new leaf values (flat interleaved complex64, host)."""
+        if hasattr(data_f32, "data_ptr"):
+            ptr = _vp(data_f32.data_ptr())
+        else:
+            ptr = data_f32.ctypes.data_as(_vp)
+        _check(_lib.tn_plan_update_data(self._h, ptr, _stream_ptr(stream)), "tn_plan_update_data")
+
+    def profile(self, reset=False, max_rows=4096):
+        """Per-op timing rows of the step-timing recorder (profile mode)."""
+        rows = np.zeros(8 * max_rows)
+        n = _lib.tn_plan_profile(self._h, max_rows, _ptr(rows), 1 if reset else 0)
+        if n < 0:
+            raise TNError(n, "tn_plan_profile")
+        out = []
+        for i in range(n):
+            r = rows[8 * i:8 * i + 8]
+            out.append(dict(phase=int(r[0]), index=int(r[1]), kind=PROFILE_KINDS[int(r[2])], step=int(r[3]),
+                            ms=float(r[4]), launches=int(r[5]), macs=float(r[6]), bytes=float(r[7])))
+        return out
+
     def stats(self):
         out = np.zeros(16)
         _check(_lib.tn_plan_stats(self._h, _ptr(out)), "tn_plan_stats")
@@ -229,10 +254,16 @@ def amplitudes(circuit, fixed_bits, open_qubits, d_amp, form="fp32", search=None
                               ctypes.byref(po), _dev_ptr(d_amp), _stream_ptr(stream)), "tn_amplitudes")
 
 
-def probabilities_xeb(d_amp, n_open, n_qubits, d_prob=None, stream=None):
-    """(marginal P(s1), linear XEB, max p) of a device amplitude tensor; fills d_prob if given."""
-    out = np.zeros(3)
+def probabilities_xeb(d_amp, n_open, n_qubits, d_prob=None, d_out=None, stream=None, sync=True):
+    """(marginal P(s1), linear XEB, max p) of a device amplitude tensor; fills d_prob if given.
+    With sync=False only enqueues the work and returns None (results in d_out)."""
+    import torch
+    if d_out is None:
+        d_out = torch.zeros(3, dtype=torch.float64, device=d_amp.device)
+    out = np.zeros(3) if sync else None
     _check(_lib.tn_probabilities_xeb(_dev_ptr(d_amp), n_open, n_qubits,
-                                     _dev_ptr(d_prob) if d_prob is not None else None, _ptr(out),
-                                     _stream_ptr(stream)), "tn_probabilities_xeb")
+                                     _dev_ptr(d_prob) if d_prob is not None else None, _dev_ptr(d_out),
+                                     _ptr(out), _stream_ptr(stream)), "tn_probabilities_xeb")
+    if not sync:
+        return None
     return float(out[0]), float(out[1]), float(out[2])

@@ -273,6 +273,8 @@ __global__ void __launch_bounds__(kThreads) prob_kernel(const double2 *amp, int6
     }
 }
 
+__global__ void xeb_finalize_kernel(double *out, int scale_exp) { out[1] = ldexp(out[0], scale_exp) - 1.0; }
+
 }  // namespace
 
 cudaError_t launch_small(const SmallArgs &a, cudaStream_t s) {
@@ -322,10 +324,13 @@ cudaError_t launch_accum(const AccumArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_prob_xeb(const double2 *amp, int64_t n, double *prob, double *d_out3, cudaStream_t s) {
+cudaError_t launch_prob_xeb(const double2 *amp, int64_t n, double *prob, double *d_out3, int scale_exp,
+                            cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(d_out3, 0, 3 * sizeof(double), s);
     if (e != cudaSuccess) return e;
     prob_kernel<<<grid_for(n), kThreads, 0, s>>>(amp, n, prob, d_out3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    xeb_finalize_kernel<<<1, 1, 0, s>>>(d_out3, scale_exp);
     return cudaGetLastError();
 }
 

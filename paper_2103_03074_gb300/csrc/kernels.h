@@ -80,7 +80,9 @@ cudaError_t launch_gemm_f32(const GemmArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractEntry *d_entries, int n_entries, int max_out, uint64_t slice_base,
                            cudaStream_t s);
 cudaError_t launch_accum(const AccumArgs &a, cudaStream_t s);
-cudaError_t launch_prob_xeb(const double2 *amp, int64_t n, double *prob, double *d_out3, cudaStream_t s);
+// d_out3: {sum p, 2^scale_exp * sum p - 1, max p}
+cudaError_t launch_prob_xeb(const double2 *amp, int64_t n, double *prob, double *d_out3, int scale_exp,
+                            cudaStream_t s);
 cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s);
 
 }  // namespace tn

@@ -40,7 +40,8 @@ namespace tn {
 
 namespace {
 
-enum OpKind { OP_SMALL = 0, OP_PERMUTE = 1, OP_GEMM = 2 };
+// values double as the step-timing recorder's kind codes (3 = extract, 4 = sum)
+enum OpKind { OP_SMALL = 0, OP_PERMUTE = 1, OP_GEMM = 2, OP_SPLIT = 5 };
 
 struct Operand {  // where an op reads or writes: static leaf or arena buffer
     int buf = -1;        // arena buffer id, or -1
@@ -55,6 +56,8 @@ struct Op {
     SmallArgs small;
     PermuteArgs perm;
     GemmArgs gemm;
+    SplitArgs split;
+    TcGemm tc;  // tensor-core GEMM (gemm_variant 1), resolved after arena allocation
     double macs = 0, bytes = 0;
     int gemm_variant = 0;  // 0: FP32 CUDA cores, 1: tensor-core split form
 };
@@ -136,6 +139,16 @@ struct tn_plan {
     double macs_batch = 0, macs_prologue = 0, bytes_batch = 0, bytes_prologue = 0;
     int launches_batch = 0, launches_prologue = 0;
     tn_plan_opts opts;
+    // step-timing recorder (profile mode)
+    struct ProfRow {
+        int phase, idx, kind, step;
+        double ms;
+        int64_t calls;
+        double macs, bytes;
+    };
+    std::vector<ProfRow> prof;
+    std::vector<cudaEvent_t> prof_ev;  // two per row
+    int64_t leaf_bytes = 0;
 };
 
 namespace tn {
@@ -409,7 +422,39 @@ int64_t compile(tn_plan &P, int nb) {
         op.macs = macs;
         op.bytes = 8.0 * (std::exp2((double)A.lay.size()) + std::exp2((double)B.lay.size()) +
                           std::exp2((double)nc.lay.size()));
-        op.gemm_variant = (P.form != TN_FP32) ? 1 : 0;
+        op.gemm_variant = 0;
+        if (P.form != TN_FP32 && tc_gemm_suitable(g)) {
+            // split both operands into hi/lo planes (K-major), then the
+            // tensor-core GEMM reads the planes through TMA
+            const int es = tc_plane_bytes(P.form);
+            auto emit_split = [&](const Operand &src, int64_t rows, int64_t s_h, int64_t s_row, int64_t s_k) {
+                Op sp;
+                std::memset(&sp.split, 0, sizeof sp.split);
+                sp.kind = OP_SPLIT;
+                sp.step = t;
+                sp.dep = nc.dep;
+                sp.split.H = g.H;
+                sp.split.rows = rows;
+                sp.split.K = g.K;
+                sp.split.s_h = s_h;
+                sp.split.s_row = s_row;
+                sp.split.s_k = s_k;
+                sp.in0 = src;
+                const int64_t bytes = 4 * g.H * rows * g.K * es;
+                Operand dst;
+                dst.buf = new_buf((bytes + 7) / 8);
+                sp.out = dst;
+                sp.bytes = 8.0 * (double)(g.H * rows * g.K) + (double)bytes;
+                ops.push_back(sp);
+                return dst;
+            };
+            Operand pa = emit_split(wA, g.M, g.sAh, g.sAm, g.sAk);
+            Operand pb = emit_split(wB, g.N, g.sBh, g.sBn, g.sBk);
+            op.gemm_variant = 1;
+            op.in0 = pa;
+            op.in1 = pb;
+            op.bytes = (double)(4 * es) * (double)(g.H * (g.M + g.N) * g.K) + 8.0 * (double)(g.H * g.M * g.N);
+        }
         ops.push_back(op);
     }
     // root
@@ -528,14 +573,27 @@ void resolve_all(tn_plan &P) {
             op.perm.out = resolve(P, op.out);
             break;
         case OP_GEMM:
-            op.gemm.A = resolve(P, op.in0);
-            op.gemm.B = resolve(P, op.in1);
-            op.gemm.C = resolve(P, op.out);
+            if (op.gemm_variant == 1) {
+                op.tc.a = op.gemm;
+                op.tc.a.C = resolve(P, op.out);
+                op.tc.form = P.form;
+                op.tc.planesA = resolve(P, op.in0);
+                op.tc.planesB = resolve(P, op.in1);
+            } else {
+                op.gemm.A = resolve(P, op.in0);
+                op.gemm.B = resolve(P, op.in1);
+                op.gemm.C = resolve(P, op.out);
+            }
+            break;
+        case OP_SPLIT:
+            op.split.X = resolve(P, op.in0);
+            op.split.P = resolve(P, op.out);
             break;
         }
     };
     for (auto &op : P.prologue) fix(op);
     for (auto &op : P.batch) fix(op);
+
     for (auto &e : P.extract) {
         int leaf = (int)(intptr_t)e.src;
         int buf = (int)(intptr_t)e.dst;
@@ -550,8 +608,9 @@ cudaError_t run_op(const tn_plan &P, const Op &op, cudaStream_t s) {
     case OP_SMALL: return launch_small(op.small, s);
     case OP_PERMUTE: return launch_permute(op.perm, s);
     case OP_GEMM:
-        if (op.gemm_variant == 1) return launch_gemm_tc(op.gemm, P.form, s);
+        if (op.gemm_variant == 1) return launch_gemm_tc(op.tc, s);
         return launch_gemm_f32(op.gemm, s);
+    case OP_SPLIT: return launch_split(op.split, P.form, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -654,6 +713,7 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
     }
     if (nb < 0) return fail(TN_ERR_OOM, "the plan does not fit the memory budget even without batching");
     P->arena_bytes = arena;
+    P->leaf_bytes = leaf_bytes;
     e = cudaMalloc(&P->d_leaves, std::max<int64_t>(leaf_bytes, 16));
     if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc leaves");
     e = cudaMemcpy(P->d_leaves, data, leaf_bytes, cudaMemcpyHostToDevice);
@@ -661,6 +721,10 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
     e = cudaMalloc(&P->d_arena, std::max<int64_t>(arena, 256));
     if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc arena");
     resolve_all(*P);
+    for (auto *ops : {&P->prologue, &P->batch})
+        for (auto &op : *ops)
+            if (op.kind == OP_GEMM && op.gemm_variant == 1 && !tc_prepare(op.tc))
+                return fail(TN_ERR_CUDA, "TMA descriptor encoding failed");
     if (!P->extract.empty()) {
         e = cudaMalloc(&P->d_extract, sizeof(ExtractEntry) * P->extract.size());
         if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc extract table");
@@ -672,6 +736,38 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
     return TN_OK;
 }
 
+namespace tn {
+namespace {
+
+// rows: prologue ops, extract, batch ops, accumulate
+void prof_init(tn_plan &P) {
+    if (!P.prof.empty()) return;
+    int idx = 0;
+    for (auto &op : P.prologue) P.prof.push_back({0, idx++, (int)op.kind, op.step, 0.0, 0, op.macs, op.bytes});
+    P.prof.push_back({1, 0, 3, -1, 0.0, 0, 0.0, 0.0});
+    idx = 0;
+    for (auto &op : P.batch) P.prof.push_back({1, idx++, (int)op.kind, op.step, 0.0, 0, op.macs, op.bytes});
+    P.prof.push_back({1, 0, 4, -1, 0.0, 0, 0.0, 0.0});
+    P.prof_ev.resize(2 * P.prof.size());
+    for (auto &ev : P.prof_ev) cudaEventCreate(&ev);
+}
+
+cudaError_t prof_collect(tn_plan &P, size_t r0, size_t r1, cudaStream_t s) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    for (size_t r = r0; r < r1; r++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P.prof_ev[2 * r], P.prof_ev[2 * r + 1]) == cudaSuccess) {
+            P.prof[r].ms += ms;
+            P.prof[r].calls += 1;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace tn
+
 extern "C" int tn_contract_slices(tn_plan_t P, int64_t begin, int64_t end, double *d_amp, tn_stream_t stream) {
     if (!P) return fail(TN_ERR_ARG, "plan is NULL");
     if (P->failed) return fail(TN_ERR_STATE, "plan is in a failed state");
@@ -680,25 +776,75 @@ extern "C" int tn_contract_slices(tn_plan_t P, int64_t begin, int64_t end, doubl
     if (!d_amp) return fail(TN_ERR_ARG, "d_amp is NULL");
     if (begin == end) return TN_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e;
+    const bool prof = P->opts.profile != 0;
+    if (prof) prof_init(*P);
+    cudaError_t e = cudaSuccess;
+    size_t row = 0;
+    auto timed = [&](auto &&launch) -> cudaError_t {
+        if (prof) cudaEventRecord(P->prof_ev[2 * row], s);
+        cudaError_t r = launch();
+        if (prof) cudaEventRecord(P->prof_ev[2 * row + 1], s);
+        row++;
+        return r;
+    };
     for (auto &op : P->prologue)
-        if ((e = run_op(*P, op, s)) != cudaSuccess) { P->failed = true; return cuda_fail(e, "prologue launch"); }
+        if ((e = timed([&] { return run_op(*P, op, s); })) != cudaSuccess) {
+            P->failed = true;
+            return cuda_fail(e, "prologue launch");
+        }
+    if (prof && (e = prof_collect(*P, 0, row, s)) != cudaSuccess) { P->failed = true; return cuda_fail(e, "profile"); }
+    const size_t row_block = row;
     const int64_t B = (int64_t)1 << P->nb;
     AccumArgs acc = P->accum;
     acc.amp = reinterpret_cast<double2 *>(d_amp);
     for (int64_t base = (begin / B) * B; base < end; base += B) {
-        if ((e = launch_extract(P->d_extract, (int)P->extract.size(), P->extract_max_out, (uint64_t)base, s)) !=
-            cudaSuccess) { P->failed = true; return cuda_fail(e, "extract launch"); }
+        row = row_block;
+        if ((e = timed([&] {
+                 return launch_extract(P->d_extract, (int)P->extract.size(), P->extract_max_out, (uint64_t)base, s);
+             })) != cudaSuccess) { P->failed = true; return cuda_fail(e, "extract launch"); }
         for (auto &op : P->batch)
-            if ((e = run_op(*P, op, s)) != cudaSuccess) { P->failed = true; return cuda_fail(e, "step launch"); }
+            if ((e = timed([&] { return run_op(*P, op, s); })) != cudaSuccess) {
+                P->failed = true;
+                return cuda_fail(e, "step launch");
+            }
         acc.b_lo = std::max(begin, base) - base;
         acc.b_hi = std::min(end, base + B) - base;
-        if ((e = launch_accum(acc, s)) != cudaSuccess) { P->failed = true; return cuda_fail(e, "accumulate launch"); }
+        if ((e = timed([&] { return launch_accum(acc, s); })) != cudaSuccess) {
+            P->failed = true;
+            return cuda_fail(e, "accumulate launch");
+        }
+        if (prof && (e = prof_collect(*P, row_block, row, s)) != cudaSuccess) {
+            P->failed = true;
+            return cuda_fail(e, "profile");
+        }
     }
-    if (P->opts.profile) {
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { P->failed = true; return cuda_fail(e, "contract"); }
+    if (prof && tc_read_error(s) != 0) {
+        P->failed = true;
+        return fail(TN_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
     }
+    return TN_OK;
+}
+
+extern "C" int tn_plan_profile(tn_plan_t P, int max_rows, double *rows, int reset) {
+    if (!P || (max_rows > 0 && !rows)) return fail(TN_ERR_ARG, "NULL argument");
+    int n = 0;
+    for (auto &r : P->prof) {
+        if (n >= max_rows) break;
+        double *o = rows + 8 * n;
+        o[0] = r.phase; o[1] = r.idx; o[2] = r.kind; o[3] = r.step;
+        o[4] = r.ms; o[5] = (double)r.calls; o[6] = r.macs; o[7] = r.bytes;
+        n++;
+    }
+    if (reset)
+        for (auto &r : P->prof) { r.ms = 0; r.calls = 0; }
+    return n;
+}
+
+extern "C" int tn_plan_update_data(tn_plan_t P, const float *data, tn_stream_t stream) {
+    if (!P || !data) return fail(TN_ERR_ARG, "NULL argument");
+    cudaError_t e = cudaMemcpyAsync(P->d_leaves, data, P->leaf_bytes, cudaMemcpyHostToDevice,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "tn_plan_update_data");
     return TN_OK;
 }
 
@@ -707,6 +853,7 @@ extern "C" void tn_plan_destroy(tn_plan_t P) {
     if (P->d_leaves) cudaFree(P->d_leaves);
     if (P->d_arena) cudaFree(P->d_arena);
     if (P->d_extract) cudaFree(P->d_extract);
+    for (auto &ev : P->prof_ev) cudaEventDestroy(ev);
     delete P;
 }
 
@@ -725,22 +872,18 @@ extern "C" int tn_plan_stats(tn_plan_t P, double *out) {
     return TN_OK;
 }
 
-extern "C" int tn_probabilities_xeb(const double *d_amp, int n_open, int n_qubits, double *d_prob, double *out,
-                                    tn_stream_t stream) {
-    if (!d_amp || !out || n_open < 0 || n_open > 40) return fail(TN_ERR_ARG, "bad arguments");
+extern "C" int tn_probabilities_xeb(const double *d_amp, int n_open, int n_qubits, double *d_prob, double *d_out,
+                                    double *out, tn_stream_t stream) {
+    if (!d_amp || !d_out || n_open < 0 || n_open > 40 || n_qubits < n_open) return fail(TN_ERR_ARG, "bad arguments");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    double *d_out = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_out, 3 * sizeof(double), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
-    e = launch_prob_xeb(reinterpret_cast<const double2 *>(d_amp), (int64_t)1 << n_open, d_prob, d_out, s);
-    double h[3] = {0, 0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFreeAsync(d_out, s);
+    cudaError_t e = launch_prob_xeb(reinterpret_cast<const double2 *>(d_amp), (int64_t)1 << n_open, d_prob, d_out,
+                                    n_qubits - n_open, s);
     if (e != cudaSuccess) return cuda_fail(e, "probabilities");
-    out[0] = h[0];
-    out[1] = std::ldexp(h[0], n_qubits - n_open) - 1.0;
-    out[2] = h[2];
+    if (out) {
+        e = cudaMemcpyAsync(out, d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "probabilities");
+    }
     return TN_OK;
 }
 
@@ -783,6 +926,7 @@ extern "C" int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bit
     if (rc == TN_OK) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "contract");
+        else if (tc_read_error(s) != 0) rc = fail(TN_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
     }
     tn_plan_destroy(plan);
     return rc;

@@ -1,9 +1,442 @@
+// Split-precision complex GEMM on the 5th-generation tensor cores (tcgen05).
+//
+// C[h, m, n] = sum_k A[h, m, k] B[h, k, n] for complex64 operands with the
+// strided layout of GemmArgs, in two forms:
+//   BF16x3: x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (Henry, Tang &
+//           Heinecke 2019), kind::f16 MMAs, 16 K values per MMA;
+//   TF32x3: hi = tf32(x), lo = tf32(x - hi) (Ootomo & Yokota 2022), kind::tf32
+//           MMAs, 8 K values per MMA.
+// A real product x*y is hi_x hi_y + hi_x lo_y + lo_x hi_y.  Complex products
+// use four real products (re = ar br - ai bi, im = ar bi + ai br), the minus
+// sign folded into the MMA's negate-A bit: 12 MMAs per K step.
+//
+// Two kernels:
+//  * split_kernel: the hi/lo split of an operand into four planes re_hi,
+//    re_lo, im_hi, im_lo, K-major, in global memory; one pass, coalesced
+//    through a shared-memory transpose when the operand is not K-contiguous;
+//  * tc_gemm_kernel: warp-specialised.  Warp 0 issues TMA loads of the planes
+//    (128-byte swizzle) into a 2-stage shared-memory ring; warp 1 issues the
+//    MMAs of each K chunk into one of two tensor-memory accumulator sets;
+//    warps 4-11 read each finished chunk's accumulators (tcgen05.ld) and add
+//    them into FP32 registers with round-to-nearest.  Flushing per chunk keeps
+//    the tensor core's truncating accumulation to a few MMAs; hi*hi and the
+//    correction products also sit in separate accumulators for the same
+//    reason (small addends aligned to a large running sum lose their low bits).
+//
+// CTA tile: 128 (M) x 64 (N); a K chunk is 128 bytes of a plane row (64 bf16
+// or 32 tf32 values).  Every mbarrier wait is bounded; on expiry the kernel
+// records an error in tc_error and returns after freeing its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
 #include "tc_gemm.h"
 
 namespace tn {
 
-bool tc_form_available(tn_form) { return false; }
+__device__ int tc_error = 0;
 
-cudaError_t launch_gemm_tc(const GemmArgs &, tn_form, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr int TM = 128, TN = 64;
+constexpr int kChunkBytes = 128;                        // one plane row of a chunk
+constexpr int kAPlane = TM * kChunkBytes;               // 16 KB
+constexpr int kBPlane = TN * kChunkBytes;               // 8 KB
+constexpr int kStageBytes = 4 * kAPlane + 4 * kBPlane;  // 96 KB
+constexpr int kStages = 2;
+constexpr int kThreads = 384;  // 12 warps
+constexpr int kFlushWarp0 = 4, kFlushWarps = 8;
+constexpr int kTmemCols = 512;  // 2 sets x {re, im, re corr, im corr} x 64
+constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(16 >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor (kind::f16 / kind::tf32): D f32, K-major A and B
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, int M, int N, bool neg_a) {
+    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((neg_a ? 1u : 0u) << 13) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool kTF32>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (kTF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    atomicExch(&tc_error, 1);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// --------------------------------------------------------------- split pass
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// planes[h][p][row][k]: p = re_hi, re_lo, im_hi, im_lo
+template <bool kTF32>
+__global__ void __launch_bounds__(256) split_kernel(const SplitArgs s) {
+    __shared__ float2 tile[32][33];
+    const int64_t row0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int64_t h = blockIdx.z; h < s.H; h += gridDim.z) {
+        const float2 *X = s.X + h * s.s_h;
+        // read: coalesced along the unit-stride dimension
+        if (s.s_row == 1 && s.s_k != 1) {
+            for (int i = ty; i < 32; i += 8) {
+                const int64_t k = k0 + i, row = row0 + tx;
+                tile[tx][i] = (k < s.K && row < s.rows) ? X[k * s.s_k + row] : make_float2(0.f, 0.f);
+            }
+        } else {
+            for (int i = ty; i < 32; i += 8) {
+                const int64_t row = row0 + i, k = k0 + tx;
+                tile[i][tx] = (k < s.K && row < s.rows) ? X[row * s.s_row + k * s.s_k] : make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        // write: coalesced along k
+        const int64_t plane = s.rows * s.K;
+        for (int i = ty; i < 32; i += 8) {
+            const int64_t row = row0 + i, k = k0 + tx;
+            if (row >= s.rows || k >= s.K) continue;
+            const float2 v = tile[i][tx];
+            const int64_t o = ((h * 4) * s.rows + row) * s.K + k;
+            if (kTF32) {
+                uint32_t *P = reinterpret_cast<uint32_t *>(s.P);
+                const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
+                P[o] = rh;
+                P[o + plane] = tf32_rna(v.x - __uint_as_float(rh));
+                P[o + 2 * plane] = ih;
+                P[o + 3 * plane] = tf32_rna(v.y - __uint_as_float(ih));
+            } else {
+                uint16_t *P = reinterpret_cast<uint16_t *>(s.P);
+                const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+                P[o] = __bfloat16_as_ushort(rh);
+                P[o + plane] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
+                P[o + 2 * plane] = __bfloat16_as_ushort(ih);
+                P[o + 3 * plane] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- GEMM
+struct GemmTcParams {
+    float2 *C;
+    int64_t H, M, N, K;  // K in complex elements
+    int64_t sCh, sCm, sCn;
+    int k_chunk;  // K values per 128-byte chunk (64 bf16 / 32 tf32)
+};
+
+template <bool kTF32>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const GemmTcParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint64_t *full = bar, *empty = bar + kStages, *tfull = bar + 2 * kStages, *tempty = bar + 2 * kStages + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * kStages + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+        }
+        for (int t = 0; t < 2; t++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[t])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty[t])), "r"(kFlushWarps));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TN;
+    const int h = blockIdx.z;
+    const int n_chunks = (int)((p.K + p.k_chunk - 1) / p.k_chunk);
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            for (int c = 0; c < n_chunks; c++) {
+                const int s = c % kStages, use = c / kStages;
+                if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (use - 1) & 1)) break;
+                unsigned char *st = smem + s * kStageBytes;
+                const uint32_t fb = smem_u32(&full[s]);
+                mbar_expect_tx(fb, kStageBytes);
+                tma_load_4d(smem_u32(st), &mapA, c * p.k_chunk, (int)m0, 0, h, fb);
+                tma_load_4d(smem_u32(st + 4 * kAPlane), &mapB, c * p.k_chunk, (int)n0, 0, h, fb);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t fmt = kTF32 ? 2u : 1u;  // tf32 : bf16
+            constexpr uint32_t IP = make_idesc(fmt, TM, TN, false), IN = make_idesc(fmt, TM, TN, true);
+            for (int c = 0; c < n_chunks; c++) {
+                const int s = c % kStages, use = c / kStages;
+                const int t = c & 1, tuse = c >> 1;
+                if (!mbar_wait(smem_u32(&full[s]), use & 1)) break;
+                if (tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) break;
+                fence_after();
+                const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + 4 * kAPlane;
+                const uint32_t d_re = tmem + t * 256, d_im = d_re + 64, c_re = d_re + 128, c_im = d_re + 192;
+#pragma unroll
+                for (int ks = 0; ks < 4; ks++) {  // 4 MMA K steps of 32 bytes per chunk
+                    const uint32_t ko = ks * 32;
+                    const uint64_t arh = make_desc(a0 + ko), arl = make_desc(a0 + kAPlane + ko);
+                    const uint64_t aih = make_desc(a0 + 2 * kAPlane + ko), ail = make_desc(a0 + 3 * kAPlane + ko);
+                    const uint64_t brh = make_desc(b0 + ko), brl = make_desc(b0 + kBPlane + ko);
+                    const uint64_t bih = make_desc(b0 + 2 * kBPlane + ko), bil = make_desc(b0 + 3 * kBPlane + ko);
+                    const uint32_t acc = ks > 0 ? 1u : 0u;  // each chunk starts fresh sums
+                    mma<kTF32>(d_re, arh, brh, IP, acc);
+                    mma<kTF32>(d_re, aih, bih, IN, 1u);
+                    mma<kTF32>(c_re, arh, brl, IP, acc);
+                    mma<kTF32>(c_re, arl, brh, IP, 1u);
+                    mma<kTF32>(c_re, aih, bil, IN, 1u);
+                    mma<kTF32>(c_re, ail, bih, IN, 1u);
+                    mma<kTF32>(d_im, arh, bih, IP, acc);
+                    mma<kTF32>(d_im, aih, brh, IP, 1u);
+                    mma<kTF32>(c_im, arh, bil, IP, acc);
+                    mma<kTF32>(c_im, arl, bih, IP, 1u);
+                    mma<kTF32>(c_im, aih, brl, IP, 1u);
+                    mma<kTF32>(c_im, ail, brh, IP, 1u);
+                }
+                mma_commit(smem_u32(&empty[s]));
+                mma_commit(smem_u32(&tfull[t]));
+            }
+        }
+    } else if (warp >= kFlushWarp0) {
+        // ---------------- accumulator flush + epilogue (8 warps)
+        const int fw = warp - kFlushWarp0;
+        const int lg = warp & 3, half = fw >> 2;  // TMEM lane group, column half
+        const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
+        float acc_re[32], acc_im[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) acc_re[j] = acc_im[j] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < n_chunks; c++) {
+            const int t = c & 1, tuse = c >> 1;
+            if (!mbar_wait(smem_u32(&tfull[t]), tuse & 1)) { ok = false; break; }
+            fence_after();
+            const uint32_t base = tmem + t * 256 + lane_off + half * 32;
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                uint32_t r0[16], r1[16], r2[16], r3[16];
+                tmem_ld16(base + q * 16, r0);        // re main
+                tmem_ld16(base + 64 + q * 16, r1);   // im main
+                tmem_ld16(base + 128 + q * 16, r2);  // re correction
+                tmem_ld16(base + 192 + q * 16, r3);  // im correction
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    acc_re[q * 16 + j] += __uint_as_float(r0[j]) + __uint_as_float(r2[j]);
+                    acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r3[j]);
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
+        }
+        const int64_t m = m0 + lg * 32 + lane;
+        if (ok && m < p.M) {
+            float2 *C = p.C + (int64_t)h * p.sCh + m * p.sCm;
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const int64_t n = n0 + half * 32 + j;
+                if (n < p.N) C[n * p.sCn] = make_float2(acc_re[j], acc_im[j]);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// planes [H][4][rows][K] of element size es; box = 128 bytes of K x box_rows x 4 planes x 1
+bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int64_t K, int es, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, 4, (cuuint64_t)H};
+    cuuint64_t strides[3] = {(cuuint64_t)(K * es), (cuuint64_t)(rows * K * es), (cuuint64_t)(4 * rows * K * es)};
+    cuuint32_t box[4] = {(cuuint32_t)(kChunkBytes / es), (cuuint32_t)box_rows, 4, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, planes, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_form_available(tn_form form) {
+    return (form == TN_BF16X3 || form == TN_TF32X3) && encode_fn() != nullptr;
+}
+
+int tc_plane_bytes(tn_form form) { return form == TN_TF32X3 ? 4 : 2; }
+
+bool tc_gemm_suitable(const GemmArgs &a) {
+    return a.M >= 64 && a.N >= 32 && a.K >= 32 && a.H <= 65535 && a.M < (1ll << 31) && a.N < (1ll << 31) &&
+           a.K < (1ll << 31);
+}
+
+bool tc_prepare(TcGemm &g) {
+    const int es = tc_plane_bytes(g.form);
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM)) return false;
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN)) return false;
+    return true;
+}
+
+cudaError_t launch_split(const SplitArgs &s, tn_form form, cudaStream_t st) {
+    dim3 grid((unsigned)((s.K + 31) / 32), (unsigned)((s.rows + 31) / 32), (unsigned)(s.H < 65535 ? s.H : 65535));
+    if (grid.y > 65535 || grid.x == 0 || grid.y == 0) return cudaErrorInvalidConfiguration;
+    if (form == TN_TF32X3) split_kernel<true><<<grid, 256, 0, st>>>(s);
+    else split_kernel<false><<<grid, 256, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
+    static bool attr[2] = {false, false};
+    const int tf = g.form == TN_TF32X3 ? 1 : 0;
+    if (!attr[tf]) {
+        cudaError_t e = tf ? cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kSmem)
+                           : cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kSmem);
+        if (e != cudaSuccess) return e;
+        attr[tf] = true;
+    }
+    GemmTcParams p;
+    p.C = g.a.C;
+    p.H = g.a.H;
+    p.M = g.a.M;
+    p.N = g.a.N;
+    p.K = g.a.K;
+    p.sCh = g.a.sCh;
+    p.sCm = g.a.sCm;
+    p.sCn = g.a.sCn;
+    p.k_chunk = kChunkBytes / tc_plane_bytes(g.form);
+    const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
+    if (gn > 65535 || g.a.H > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)gm, (unsigned)gn, (unsigned)g.a.H);
+    const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
+    const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
+    if (tf) tc_gemm_kernel<true><<<grid, kThreads, kSmem, s>>>(mA, mB, p);
+    else tc_gemm_kernel<false><<<grid, kThreads, kSmem, s>>>(mA, mB, p);
+    return cudaGetLastError();
+}
+
+int tc_read_error(cudaStream_t s) {
+    int v = 0, zero = 0;
+    cudaMemcpyFromSymbolAsync(&v, tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyToSymbolAsync(tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    return v;
+}
 
 }  // namespace tn

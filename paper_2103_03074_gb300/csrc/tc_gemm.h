@@ -7,10 +7,46 @@
 
 namespace tn {
 
-// true if `form` has a tensor-core GEMM in this build
+// Split of one GEMM operand X[h, row, k] = X[h s_h + row s_row + k s_k]
+// (complex64) into planes P[h][p][row][k], p = re_hi, re_lo, im_hi, im_lo,
+// each hi/lo pair in the form's element type (bf16 or tf32 kept in 32 bits).
+struct SplitArgs {
+    const float2 *X;
+    void *P;
+    int64_t H, rows, K;
+    int64_t s_h, s_row, s_k;
+};
+
+// One tensor-core GEMM: the GemmArgs contract plus the split planes of A
+// (rows = M) and B (rows = N) and their TMA descriptors.
+struct TcGemm {
+    GemmArgs a;
+    tn_form form;
+    void *planesA, *planesB;
+    alignas(64) unsigned char mapA[128];
+    alignas(64) unsigned char mapB[128];
+};
+
+// true if `form` has a tensor-core GEMM in this build (and the driver entry
+// point for TMA descriptors is reachable)
 bool tc_form_available(tn_form form);
 
-// Same contract as launch_gemm_f32, computed in the split form `form`.
-cudaError_t launch_gemm_tc(const GemmArgs &a, tn_form form, cudaStream_t s);
+// bytes per plane element of a split form (2: bf16, 4: tf32)
+int tc_plane_bytes(tn_form form);
+
+// Shapes the tensor-core kernel takes (smaller GEMMs stay on the FP32
+// CUDA-core kernel).
+bool tc_gemm_suitable(const GemmArgs &a);
+
+// Encode the TMA descriptors of g (pointers and form filled in); false if the
+// driver rejects them.
+bool tc_prepare(TcGemm &g);
+
+cudaError_t launch_split(const SplitArgs &s, tn_form form, cudaStream_t st);
+cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s);
+
+// Read and clear the device error word of the tensor-core kernels (0 = ok,
+// 1 = a bounded mbarrier wait expired); synchronises `s`.
+int tc_read_error(cudaStream_t s);
 
 }  // namespace tn

@@ -181,16 +181,22 @@ def load_golden(name):
     return np.array(vals)
 
 
-def test_cfg2_amplitudes_vs_golden(tn):
+@pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16x3"])
+def test_cfg2_amplitudes_vs_golden(tn, form):
     """The 30-qubit workload exactly as the benchmark plans it: 8 sliced bonds
-    from the order search, all 2^8 slices in one batch, FP32 form."""
+    from the order search (16384 trials), all 2^8 slices in one batch."""
     cfg = make_config(2)
     ref = load_golden("cfg2_amplitudes.txt")
     amp = dev_zeros(8)
-    tn.amplitudes(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"], amp,
-                  search=tn.search_opts(trials=256, n_sliced=8))
+    tn.amplitudes(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"], amp, form=form,
+                  search=tn.search_opts(trials=16384, n_sliced=8))
     got = to_complex(amp)
-    assert rel(got, ref) < TOL
+    print(f"cfg2 {form}: relative L2 error {rel(got, ref):.3e}")
+    # FP32 and TF32x3 meet the 1e-5 bound.  BF16x3 holds ~16 bits per operand
+    # (two bf16 pieces), which on this workload gives 1.17e-5 measured (the
+    # same as a round-to-nearest emulation of the split), so it is held to
+    # 2e-5 and is not a form that meets the stated bound here.
+    assert rel(got, ref) < (2e-5 if form == "bf16x3" else TOL)
     # XEB from the GPU probabilities against the oracle's, 1e-4 absolute
     p_s1, f, pmax = tn.probabilities_xeb(amp, 8, 30)
     assert abs(f - oxeb.linear_xeb(ref, 30)) < 1e-4

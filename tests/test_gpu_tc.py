@@ -1,0 +1,135 @@
+"""Tensor-core split-precision GEMMs (BF16x3 and TF32x3, four real products)
+on the GPU.
+
+Single-GEMM networks exercise each operand layout (K- or M/N-contiguous), tiles
+smaller than the kernel's 128 x 64 x 64 tile (zero-filled edges) and a batch
+label shared by both operands.  Each result is checked twice:
+  * against the exact product (complex128 numpy): relative L2 within the bound
+    of the split: two bf16 pieces hold ~16 bits, so ~3 x 2^-16 per product,
+    about 5e-6 in the L2 sense for random data (1e-5 asserted);
+  * against a test-side emulation of the same arithmetic (round-to-nearest
+    split, hi*hi + hi*lo + lo*hi, 4 real products, exact accumulation):
+    agreement to 5e-7.  The kernel adds each K chunk's tensor-core partial
+    sums into FP32 registers with round-to-nearest, so the only difference is
+    FP32 rounding of those sums; a kernel that dropped or misplaced any product
+    term would be off by 1e-3 (bf16) or 1e-6 (tf32) or more.
+FP32 form: the CUDA-core kernel against the exact product, 2e-6 (FP32 sums of
+up to 2048 products).
+"""
+import numpy as np
+import pytest
+
+from tn_inputs import SplitMix64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_03074_gb300 as tn
+    return tn
+
+
+def bf16(x):
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def tf32(x):
+    # round to nearest, ties away from zero, on a 10-bit mantissa
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def emulate_split_4m(a, b, rnd):
+    def parts(x):
+        h = rnd(x)
+        return h.astype(np.float64), rnd(np.asarray(x, np.float32) - h).astype(np.float64)
+
+    def rmm(x, y):
+        xh, xl = parts(x)
+        yh, yl = parts(y)
+        return xh @ yh + xh @ yl + xl @ yh
+    ar, ai = a.real.astype(np.float32), a.imag.astype(np.float32)
+    br, bi = b.real.astype(np.float32), b.imag.astype(np.float32)
+    return (rmm(ar, br) - rmm(ai, bi)) + 1j * (rmm(ar, bi) + rmm(ai, br))
+
+
+def rand_c64(seed, shape):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a.reshape(-1) - b.reshape(-1)) / np.linalg.norm(b.reshape(-1)))
+
+
+@pytest.mark.parametrize("m,k,n,a_kfirst,b_nfirst", [
+    (10, 10, 8, False, False),   # A [m][k] (K contiguous), B [k][n] (N contiguous)
+    (10, 9, 8, True, True),      # A [k][m] (M contiguous), B [n][k] (K contiguous)
+    (6, 7, 6, False, True),      # M = 64 < 128-row tile: zero-filled rows
+    (8, 5, 8, True, True),       # K = 32 < 64-wide chunk: zero-filled K
+    (9, 11, 6, True, False),
+])
+def test_single_gemm_bf16x3(tn, m, k, n, a_kfirst, b_nfirst):
+    import torch
+    M, K, N = 1 << m, 1 << k, 1 << n
+    A = rand_c64(m * 100 + k, (M, K))
+    B = rand_c64(n * 100 + k + 1, (K, N))
+    ml = list(range(0, m))
+    kl = list(range(100, 100 + k))
+    nl = list(range(200, 200 + n))
+    la = (kl + ml) if a_kfirst else (ml + kl)
+    ta = (A.T if a_kfirst else A).reshape((2,) * (m + k))
+    lb = (nl + kl) if b_nfirst else (kl + nl)
+    tb = (B.T if b_nfirst else B).reshape((2,) * (k + n))
+    open_l = ml + nl
+    exact = A.astype(np.complex128) @ B.astype(np.complex128)
+    emu = {"bf16x3": emulate_split_4m(A, B, bf16), "tf32x3": emulate_split_4m(A, B, tf32)}
+    for form, tol_exact in (("fp32", 2e-6), ("bf16x3", 1e-5), ("tf32x3", 1e-6)):
+        plan = tn.Plan([la, lb], [ta, tb], open_l, [], [(0, 1)], form=form)
+        amp = torch.zeros(2 * M * N, dtype=torch.float64, device="cuda")
+        plan.contract(0, 1, amp)
+        torch.cuda.synchronize()
+        g = amp.cpu().numpy()
+        got = (g[0::2] + 1j * g[1::2]).reshape(M, N)
+        assert rel(got, exact) < tol_exact, form
+        if form != "fp32":
+            assert rel(got, emu[form]) < 5e-7, form
+        if form == "bf16x3":
+            assert rel(emu[form], exact) > 1e-6  # the split form really is coarser than FP32
+        plan.close()
+
+
+@pytest.mark.parametrize("form", ["bf16x3", "tf32x3"])
+def test_batched_gemm_split(tn, form):
+    """A sliced label shared by both operands becomes a batch label of the
+    GEMM when the slices run as one batch."""
+    import torch
+    m, k, n = 8, 7, 7
+    M, K, N = 1 << m, 1 << k, 1 << n
+    ml, kl, nl = list(range(m)), list(range(100, 100 + k)), list(range(200, 200 + n))
+    h = 300  # two batch labels
+    la = [h, h + 1] + ml + kl
+    lb = [h, h + 1] + kl + nl
+    A = rand_c64(5, (4, M, K))
+    B = rand_c64(6, (4, K, N))
+    plan = tn.Plan([la, lb], [A.reshape((2,) * (m + k + 2)), B.reshape((2,) * (k + n + 2))], ml + nl,
+                   [h, h + 1], [(0, 1)], form=form, opts=tn.plan_opts(batch_log2=2))
+    amp = torch.zeros(2 * M * N, dtype=torch.float64, device="cuda")
+    plan.contract(0, 4, amp)
+    torch.cuda.synchronize()
+    g = amp.cpu().numpy()
+    got = (g[0::2] + 1j * g[1::2]).reshape(M, N)
+    # slice s: label h takes bit 0 of s, label h+1 bit 1; A index (h, h+1) -> 2*b0 + b1
+    exact = sum(A[2 * (s & 1) + (s >> 1)].astype(np.complex128) @ B[2 * (s & 1) + (s >> 1)].astype(np.complex128)
+                for s in range(4))
+    assert rel(got, exact) < 1e-5
+    plan.close()
