@@ -290,6 +290,9 @@ def run_native(args):
                 pplan.contract(0, n_slices, amp, stream)
         rows = pplan.profile()
         pplan.close()
+        if args.dump_profile:
+            with open(f"{args.dump_profile}.{form}.json", "w") as f:
+                json.dump({"steps": args.steps, "rows": rows}, f)
         by_kind = {}
         for r in rows:
             d = by_kind.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "macs": 0.0, "bytes": 0.0})
@@ -378,7 +381,8 @@ def run_native(args):
                    "step": "all 256 slices summed in FP64 + probabilities/XEB",
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
-                   "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"]},
+                   "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],
+                   "arena_bytes": r["plan"]["arena_bytes"]},
         "complex_tflops": r["complex_tflops"],
         "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
                        "rel_l2_err_vs_fp64_oracle": results[f]["rel_l2_err"],
@@ -406,6 +410,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16s", "all"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

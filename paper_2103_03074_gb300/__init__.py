@@ -212,15 +212,16 @@ class Plan:
 
     def profile(self, reset=False, max_rows=4096):
         """Per-op timing rows of the step-timing recorder (profile mode)."""
-        rows = np.zeros(8 * max_rows)
+        rows = np.zeros(12 * max_rows)
         n = _lib.tn_plan_profile(self._h, max_rows, _ptr(rows), 1 if reset else 0)
         if n < 0:
             raise TNError(n, "tn_plan_profile")
         out = []
         for i in range(n):
-            r = rows[8 * i:8 * i + 8]
+            r = rows[12 * i:12 * i + 12]
             out.append(dict(phase=int(r[0]), index=int(r[1]), kind=PROFILE_KINDS[int(r[2])], step=int(r[3]),
-                            ms=float(r[4]), launches=int(r[5]), macs=float(r[6]), bytes=float(r[7])))
+                            ms=float(r[4]), launches=int(r[5]), macs=float(r[6]), bytes=float(r[7]),
+                            shape=[float(x) for x in r[8:12]]))
         return out
 
     def stats(self):

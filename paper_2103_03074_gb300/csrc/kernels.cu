@@ -4,6 +4,7 @@
 // Every tensor has bond dimension 2 on every axis, so an element address is a
 // bit string: each label owns one bit position.  Index maps are therefore bit
 // scatters and gathers, computed in registers.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -116,12 +117,71 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     }
 }
 
-// ------------------------------------------------------------------ permute
-__global__ void __launch_bounds__(kThreads) permute_kernel(const PermuteArgs a) {
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < a.n; o += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t src = 0;
-        for (int p = 0; p < a.rank; p++) src |= (((uint64_t)o >> p) & 1ull) << a.ipos[p];
-        a.out[o] = a.in[src];
+// ------------------------------------------------------- tiled bit permute
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, float2 v) {
+    if (a.mode == 0) {
+        reinterpret_cast<float2 *>(a.out)[d] = v;
+    } else if (a.mode == 1) {
+        uint16_t *P = reinterpret_cast<uint16_t *>(a.out);
+        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+        P[d] = __bfloat16_as_ushort(rh);
+        P[d + a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
+        P[d + 2 * a.plane_stride] = __bfloat16_as_ushort(ih);
+        P[d + 3 * a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
+    } else {
+        uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
+        const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
+        P[d] = rh;
+        P[d + a.plane_stride] = tf32_rna(v.x - __uint_as_float(rh));
+        P[d + 2 * a.plane_stride] = ih;
+        P[d + 3 * a.plane_stride] = tf32_rna(v.y - __uint_as_float(ih));
+    }
+}
+
+// Each CTA builds the tile's offset tables once, then walks tiles two at a
+// time (two independent read batches in flight per thread).
+__global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) {
+    constexpr int T = 1 << kTileMaxBits;
+    __shared__ float2 buf[2][T];
+    __shared__ uint32_t src_off[T], w_of[T], dst_off[T];
+    const int tile = 1 << a.n_tile;
+    for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+        uint32_t w = 0, so = 0, d = 0;
+        for (int j = 0; j < a.n_tile; j++) {
+            const uint32_t b = (e >> j) & 1u;
+            w |= b << a.rd_w[j];
+            so |= b << a.rd_src[j];
+            d |= b << a.tile_dst[j];
+        }
+        src_off[e] = so;
+        w_of[e] = w;
+        dst_off[e] = d;
+    }
+    __syncthreads();
+    const int64_t n_rest = 1ll << a.n_rest;
+    for (int64_t r0 = 2 * (int64_t)blockIdx.x; r0 < n_rest; r0 += 2 * (int64_t)gridDim.x) {
+        const int nr = (r0 + 1 < n_rest) ? 2 : 1;
+        uint64_t s_rest[2], d_rest[2];
+        for (int q = 0; q < nr; q++) {
+            s_rest[q] = scatter_bits((uint64_t)(r0 + q), a.rest_src, a.n_rest);
+            d_rest[q] = scatter_bits((uint64_t)(r0 + q), a.rest_dst, a.n_rest);
+        }
+        for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+            const uint32_t so = src_off[e], w = w_of[e];
+            const float2 v0 = a.in[s_rest[0] | so];
+            if (nr == 2) buf[1][w] = a.in[s_rest[1] | so];
+            buf[0][w] = v0;
+        }
+        __syncthreads();
+        for (int q = 0; q < nr; q++)
+            for (int e = threadIdx.x; e < tile; e += blockDim.x) store_elem(a, d_rest[q] | dst_off[e], buf[q][e]);
+        __syncthreads();
     }
 }
 
@@ -292,8 +352,10 @@ cudaError_t launch_small(const SmallArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_permute(const PermuteArgs &a, cudaStream_t s) {
-    permute_kernel<<<grid_for(a.n), kThreads, 0, s>>>(a);
+cudaError_t launch_bitperm(const BitPermArgs &a, cudaStream_t s) {
+    const int64_t pairs = ((1ll << a.n_rest) + 1) / 2;
+    const int grid = (int)(pairs < kMaxBlocks ? pairs : kMaxBlocks);
+    bitperm_kernel<<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -32,13 +32,28 @@ struct SmallArgs {
     int s_rank;
 };
 
-// Bit permutation: out[o] = in[sum_p bit_p(o) << ipos[p]].
-struct PermuteArgs {
+// Bit permutation through a shared-memory tile, optionally fused with the
+// hi/lo split of split-precision GEMM operands.
+//   out index d (r bits) <- in[sum_p bit_p(d) << src_pos[p]]
+// mode 0: complex64 out[d];
+// mode 1/2: four planes (re_hi, re_lo, im_hi, im_lo) of bf16 (1) or tf32 held
+//           in 32 bits (2) at d + q * plane_stride, q = 0..3.
+// The tile holds the bits at the source's and the destination's lowest
+// positions, so reads and writes are both coalesced.
+constexpr int kTileMaxBits = 10;
+struct BitPermArgs {
     const float2 *in;
-    float2 *out;
-    int64_t n;
+    void *out;
     int rank;
-    int ipos[kMaxRank];
+    int mode;
+    int64_t plane_stride;
+    int n_tile;                      // tile bits
+    int tile_dst[kTileMaxBits];      // dest positions of tile bits, ascending (write order)
+    int rd_w[kTileMaxBits];          // read order bit j -> index into tile_dst
+    int rd_src[kTileMaxBits];        // read order bit j -> source position (ascending)
+    int n_rest;                      // remaining bits (grid-strided)
+    int rest_dst[kMaxRank];
+    int rest_src[kMaxRank];
 };
 
 // Strided batched complex GEMM, all strides in complex elements:
@@ -75,7 +90,7 @@ struct AccumArgs {
 
 // launchers (kernels.cu); return cudaSuccess or the launch error
 cudaError_t launch_small(const SmallArgs &a, cudaStream_t s);
-cudaError_t launch_permute(const PermuteArgs &a, cudaStream_t s);
+cudaError_t launch_bitperm(const BitPermArgs &a, cudaStream_t s);
 cudaError_t launch_gemm_f32(const GemmArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractEntry *d_entries, int n_entries, int max_out, uint64_t slice_base,
                            cudaStream_t s);

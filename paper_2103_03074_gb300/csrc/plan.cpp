@@ -54,9 +54,8 @@ struct Op {
     bool dep = false;
     Operand in0, in1, out;
     SmallArgs small;
-    PermuteArgs perm;
+    BitPermArgs bp;  // permute (mode 0) or fused permute + hi/lo split (OP_SPLIT)
     GemmArgs gemm;
-    SplitArgs split;
     TcGemm tc;  // tensor-core GEMM (gemm_variant 1), resolved after arena allocation
     double macs = 0, bytes = 0;
     int gemm_variant = 0;  // 0: FP32 CUDA cores, 1: tensor-core split form
@@ -109,6 +108,50 @@ Groups group_layout(const std::vector<int32_t> &lay, const std::unordered_map<in
     return g;
 }
 
+// Tiled bit permutation from layout `src` to layout `dst` (same label set).
+// The shared-memory tile takes the labels at the lowest positions of both
+// layouts, alternating, up to kTileMaxBits, so that both the reads and the
+// writes of a tile are runs of consecutive addresses.
+BitPermArgs make_bitperm(const std::vector<int32_t> &src, const std::vector<int32_t> &dst, int mode) {
+    BitPermArgs a;
+    std::memset(&a, 0, sizeof a);
+    const int r = (int)dst.size();
+    a.rank = r;
+    a.mode = mode;
+    a.plane_stride = (int64_t)1 << r;
+    std::vector<int> src_pos(r), dst_of_src(r);
+    for (int p = 0; p < r; p++) {
+        src_pos[p] = pos_of(src, dst[r - 1 - p]);
+        dst_of_src[src_pos[p]] = p;
+    }
+    const int nt = std::min(kTileMaxBits, r);
+    std::vector<char> in_tile(r, 0);
+    int cnt = 0;
+    for (int i = 0; i < r && cnt < nt; i++) {
+        if (!in_tile[i]) { in_tile[i] = 1; cnt++; }
+        if (cnt < nt && !in_tile[dst_of_src[i]]) { in_tile[dst_of_src[i]] = 1; cnt++; }
+    }
+    std::vector<int> tile;
+    for (int p = 0; p < r; p++) {
+        if (in_tile[p]) tile.push_back(p);
+        else {
+            a.rest_dst[a.n_rest] = p;
+            a.rest_src[a.n_rest] = src_pos[p];
+            a.n_rest++;
+        }
+    }
+    a.n_tile = (int)tile.size();
+    for (int j = 0; j < a.n_tile; j++) a.tile_dst[j] = tile[j];
+    std::vector<int> order(a.n_tile);
+    for (int j = 0; j < a.n_tile; j++) order[j] = j;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return src_pos[tile[x]] < src_pos[tile[y]]; });
+    for (int j = 0; j < a.n_tile; j++) {
+        a.rd_w[j] = order[j];
+        a.rd_src[j] = src_pos[tile[order[j]]];
+    }
+    return a;
+}
+
 }  // namespace
 
 }  // namespace tn
@@ -145,6 +188,7 @@ struct tn_plan {
         double ms;
         int64_t calls;
         double macs, bytes;
+        double shape[4];  // GEMM / split: H, M (rows), N, K; other kinds: output rank
     };
     std::vector<ProfRow> prof;
     std::vector<cudaEvent_t> prof_ev;  // two per row
@@ -318,77 +362,91 @@ int64_t compile(tn_plan &P, int nb) {
         }
         // ---- GEMM step: A = bigger operand (rows M), B = smaller (cols N)
         NodeRec &A = T, &B = S;
+        GemmArgs shape;
+        std::memset(&shape, 0, sizeof shape);
+        shape.H = (int64_t)1 << nH;
+        shape.M = (int64_t)1 << nM;
+        shape.N = (int64_t)1 << nN;
+        shape.K = (int64_t)1 << nK;
+        const bool use_tc = P.form != TN_FP32 && tc_gemm_suitable(shape);
+        std::vector<int32_t> hord, kord, mord, nord;
+        Operand wA = A.where, wB = B.where;
         std::unordered_map<int32_t, int> gA, gB;
         for (int32_t x : H) { gA[x] = 0; gB[x] = 0; }
         for (int32_t x : K) { gA[x] = 2; gB[x] = 1; }
         for (int32_t x : Ml) gA[x] = 1;
         for (int32_t x : Nl) gB[x] = 2;
-        Groups GA = group_layout(A.lay, gA), GB = group_layout(B.lay, gB);
-        auto same = [](const std::vector<int32_t> &x, const std::vector<int32_t> &y) { return x == y; };
-        bool permA = false, permB = false;
-        std::vector<int32_t> hord, kord;
-        if (GA.ok && GB.ok && same(GA.order[0], GB.order[0]) && same(GA.order[2], GB.order[1])) {
-        } else if (GA.ok) {
-            permB = true;
-        } else if (GB.ok) {
-            permA = true;
-        } else {
-            permA = permB = true;
-        }
-        if (GA.ok && !permA) {
-            hord = GA.order[0];
-            kord = GA.order[2];
-        } else if (GB.ok && !permB) {
-            hord = GB.order[0];
-            kord = GB.order[1];
-        } else {
+        Groups GA, GB;
+        if (use_tc) {
+            // the split pass reads each operand in whatever label order it has
+            // (a fused bit permutation), so the group orders are free: take A's
             for (int32_t x : A.lay)
                 if (gA[x] == 0) hord.push_back(x);
             for (int32_t x : A.lay)
                 if (gA[x] == 2) kord.push_back(x);
+            mord = Ml;
+            nord = Nl;
+        } else {
+            GA = group_layout(A.lay, gA);
+            GB = group_layout(B.lay, gB);
+            bool permA = false, permB = false;
+            if (GA.ok && GB.ok && GA.order[0] == GB.order[0] && GA.order[2] == GB.order[1]) {
+            } else if (GA.ok) {
+                permB = true;
+            } else if (GB.ok) {
+                permA = true;
+            } else {
+                permA = permB = true;
+            }
+            if (GA.ok && !permA) {
+                hord = GA.order[0];
+                kord = GA.order[2];
+            } else if (GB.ok && !permB) {
+                hord = GB.order[0];
+                kord = GB.order[1];
+            } else {
+                for (int32_t x : A.lay)
+                    if (gA[x] == 0) hord.push_back(x);
+                for (int32_t x : A.lay)
+                    if (gA[x] == 2) kord.push_back(x);
+            }
+            auto emit_permute = [&](const NodeRec &src, const std::vector<int32_t> &new_lay, Operand &dst) {
+                Op op;
+                op.kind = OP_PERMUTE;
+                op.step = t;
+                op.dep = nc.dep;
+                op.bp = make_bitperm(src.lay, new_lay, 0);
+                op.in0 = src.where;
+                dst.buf = new_buf((int64_t)1 << new_lay.size());
+                dst.leaf_off = -1;
+                op.out = dst;
+                op.bytes = 16.0 * std::exp2((double)new_lay.size());
+                ops.push_back(op);
+            };
+            std::vector<int32_t> layA = A.lay, layB = B.lay;
+            if (permA) {
+                std::vector<int32_t> nl = hord;
+                nl.insert(nl.end(), Ml.begin(), Ml.end());
+                nl.insert(nl.end(), kord.begin(), kord.end());
+                emit_permute(A, nl, wA);
+                layA = nl;
+            }
+            if (permB) {
+                std::vector<int32_t> nl = hord;
+                nl.insert(nl.end(), kord.begin(), kord.end());
+                nl.insert(nl.end(), Nl.begin(), Nl.end());
+                emit_permute(B, nl, wB);
+                layB = nl;
+            }
+            GA = group_layout(layA, gA);
+            GB = group_layout(layB, gB);
+            if (!GA.ok || !GB.ok || GA.order[0] != GB.order[0] || GA.order[2] != GB.order[1]) {
+                set_error("internal: GEMM layout grouping failed");
+                return -1;
+            }
+            mord = GA.order[1];
+            nord = GB.order[2];
         }
-        auto emit_permute = [&](NodeRec &src, const std::vector<int32_t> &new_lay, Operand &dst) {
-            Op op;
-            std::memset(&op.perm, 0, sizeof op.perm);
-            op.kind = OP_PERMUTE;
-            op.step = t;
-            op.dep = nc.dep;
-            const int r = (int)new_lay.size();
-            op.perm.rank = r;
-            op.perm.n = (int64_t)1 << r;
-            for (int p = 0; p < r; p++) op.perm.ipos[p] = pos_of(src.lay, new_lay[r - 1 - p]);
-            op.in0 = src.where;
-            dst.buf = new_buf((int64_t)1 << r);
-            dst.leaf_off = -1;
-            op.out = dst;
-            op.bytes = 16.0 * std::exp2((double)r);
-            ops.push_back(op);
-        };
-        std::vector<int32_t> layA = A.lay, layB = B.lay;
-        Operand wA = A.where, wB = B.where;
-        if (permA) {
-            std::vector<int32_t> nl = hord;
-            nl.insert(nl.end(), Ml.begin(), Ml.end());
-            nl.insert(nl.end(), kord.begin(), kord.end());
-            NodeRec tmp = A;
-            emit_permute(tmp, nl, wA);
-            layA = nl;
-        }
-        if (permB) {
-            std::vector<int32_t> nl = hord;
-            nl.insert(nl.end(), kord.begin(), kord.end());
-            nl.insert(nl.end(), Nl.begin(), Nl.end());
-            NodeRec tmp = B;
-            emit_permute(tmp, nl, wB);
-            layB = nl;
-        }
-        GA = group_layout(layA, gA);
-        GB = group_layout(layB, gB);
-        if (!GA.ok || !GB.ok || GA.order[0] != GB.order[0] || GA.order[2] != GB.order[1]) {
-            set_error("internal: GEMM layout grouping failed");
-            return -1;
-        }
-        std::vector<int32_t> mord = GA.order[1], nord = GB.order[2];
         nc.lay = hord;
         nc.lay.insert(nc.lay.end(), mord.begin(), mord.end());
         nc.lay.insert(nc.lay.end(), nord.begin(), nord.end());
@@ -397,64 +455,58 @@ int64_t compile(tn_plan &P, int nb) {
             return -1;
         }
         Op op;
-        std::memset(&op.gemm, 0, sizeof op.gemm);
         op.kind = OP_GEMM;
         op.step = t;
         op.dep = nc.dep;
         GemmArgs &g = op.gemm;
-        g.H = (int64_t)1 << nH;
-        g.M = (int64_t)1 << nM;
-        g.N = (int64_t)1 << nN;
-        g.K = (int64_t)1 << nK;
-        g.sAh = (int64_t)1 << GA.lowpos[0];
-        g.sAm = (int64_t)1 << GA.lowpos[1];
-        g.sAk = (int64_t)1 << GA.lowpos[2];
-        g.sBh = (int64_t)1 << GB.lowpos[0];
-        g.sBk = (int64_t)1 << GB.lowpos[1];
-        g.sBn = (int64_t)1 << GB.lowpos[2];
+        g = shape;
         g.sCn = 1;
         g.sCm = (int64_t)1 << nN;
         g.sCh = (int64_t)1 << (nM + nN);
-        op.in0 = wA;
-        op.in1 = wB;
-        nc.where.buf = new_buf((int64_t)1 << nc.lay.size());
-        op.out = nc.where;
         op.macs = macs;
-        op.bytes = 8.0 * (std::exp2((double)A.lay.size()) + std::exp2((double)B.lay.size()) +
-                          std::exp2((double)nc.lay.size()));
-        op.gemm_variant = 0;
-        if (P.form != TN_FP32 && tc_gemm_suitable(g)) {
-            // split both operands into hi/lo planes (K-major), then the
-            // tensor-core GEMM reads the planes through TMA
+        if (use_tc) {
+            // split both operands into hi/lo planes [h][q][row][k] (fused with
+            // their permutation); the tensor-core GEMM reads the planes by TMA
             const int es = tc_plane_bytes(P.form);
-            auto emit_split = [&](const Operand &src, int64_t rows, int64_t s_h, int64_t s_row, int64_t s_k) {
+            const int mode = es == 2 ? 1 : 2;
+            auto emit_split = [&](const NodeRec &src, const std::vector<int32_t> &rows) {
+                std::vector<int32_t> dl = hord;
+                dl.insert(dl.end(), rows.begin(), rows.end());
+                dl.insert(dl.end(), kord.begin(), kord.end());
                 Op sp;
-                std::memset(&sp.split, 0, sizeof sp.split);
                 sp.kind = OP_SPLIT;
                 sp.step = t;
                 sp.dep = nc.dep;
-                sp.split.H = g.H;
-                sp.split.rows = rows;
-                sp.split.K = g.K;
-                sp.split.s_h = s_h;
-                sp.split.s_row = s_row;
-                sp.split.s_k = s_k;
-                sp.in0 = src;
-                const int64_t bytes = 4 * g.H * rows * g.K * es;
+                sp.bp = make_bitperm(src.lay, dl, mode);
+                sp.in0 = src.where;
+                const int64_t elems = (int64_t)1 << dl.size();
                 Operand dst;
-                dst.buf = new_buf((bytes + 7) / 8);
+                dst.buf = new_buf((4 * elems * es + 7) / 8);
                 sp.out = dst;
-                sp.bytes = 8.0 * (double)(g.H * rows * g.K) + (double)bytes;
+                sp.bytes = 8.0 * (double)elems + 4.0 * es * (double)elems;
                 ops.push_back(sp);
                 return dst;
             };
-            Operand pa = emit_split(wA, g.M, g.sAh, g.sAm, g.sAk);
-            Operand pb = emit_split(wB, g.N, g.sBh, g.sBn, g.sBk);
+            op.in0 = emit_split(A, mord);
+            op.in1 = emit_split(B, nord);
             op.gemm_variant = 1;
-            op.in0 = pa;
-            op.in1 = pb;
+            op.tc.ksplit = tc_choose_ksplit(g, P.form);
             op.bytes = (double)(4 * es) * (double)(g.H * (g.M + g.N) * g.K) + 8.0 * (double)(g.H * g.M * g.N);
+        } else {
+            g.sAh = (int64_t)1 << GA.lowpos[0];
+            g.sAm = (int64_t)1 << GA.lowpos[1];
+            g.sAk = (int64_t)1 << GA.lowpos[2];
+            g.sBh = (int64_t)1 << GB.lowpos[0];
+            g.sBk = (int64_t)1 << GB.lowpos[1];
+            g.sBn = (int64_t)1 << GB.lowpos[2];
+            op.in0 = wA;
+            op.in1 = wB;
+            op.gemm_variant = 0;
+            op.bytes = 8.0 * (std::exp2((double)A.lay.size()) + std::exp2((double)B.lay.size()) +
+                              std::exp2((double)nc.lay.size()));
         }
+        nc.where.buf = new_buf((int64_t)1 << nc.lay.size());
+        op.out = nc.where;
         ops.push_back(op);
     }
     // root
@@ -569,8 +621,9 @@ void resolve_all(tn_plan &P) {
             op.small.C = resolve(P, op.out);
             break;
         case OP_PERMUTE:
-            op.perm.in = resolve(P, op.in0);
-            op.perm.out = resolve(P, op.out);
+        case OP_SPLIT:
+            op.bp.in = resolve(P, op.in0);
+            op.bp.out = resolve(P, op.out);
             break;
         case OP_GEMM:
             if (op.gemm_variant == 1) {
@@ -579,15 +632,12 @@ void resolve_all(tn_plan &P) {
                 op.tc.form = P.form;
                 op.tc.planesA = resolve(P, op.in0);
                 op.tc.planesB = resolve(P, op.in1);
+                if (op.tc.ksplit < 1) op.tc.ksplit = 1;
             } else {
                 op.gemm.A = resolve(P, op.in0);
                 op.gemm.B = resolve(P, op.in1);
                 op.gemm.C = resolve(P, op.out);
             }
-            break;
-        case OP_SPLIT:
-            op.split.X = resolve(P, op.in0);
-            op.split.P = resolve(P, op.out);
             break;
         }
     };
@@ -606,11 +656,11 @@ void resolve_all(tn_plan &P) {
 cudaError_t run_op(const tn_plan &P, const Op &op, cudaStream_t s) {
     switch (op.kind) {
     case OP_SMALL: return launch_small(op.small, s);
-    case OP_PERMUTE: return launch_permute(op.perm, s);
+    case OP_PERMUTE: return launch_bitperm(op.bp, s);
     case OP_GEMM:
         if (op.gemm_variant == 1) return launch_gemm_tc(op.tc, s);
         return launch_gemm_f32(op.gemm, s);
-    case OP_SPLIT: return launch_split(op.split, P.form, s);
+    case OP_SPLIT: return launch_bitperm(op.bp, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -740,14 +790,30 @@ namespace tn {
 namespace {
 
 // rows: prologue ops, extract, batch ops, accumulate
+tn_plan::ProfRow prof_row(int phase, int idx, const Op &op) {
+    tn_plan::ProfRow r{phase, idx, (int)op.kind, op.step, 0.0, 0, op.macs, op.bytes, {0, 0, 0, 0}};
+    if (op.kind == OP_GEMM) {
+        r.shape[0] = (double)op.gemm.H; r.shape[1] = (double)op.gemm.M;
+        r.shape[2] = (double)op.gemm.N; r.shape[3] = (double)op.gemm.K;
+    } else if (op.kind == OP_SPLIT) {
+        r.shape[1] = (double)op.bp.plane_stride;
+    } else if (op.kind == OP_SMALL) {
+        r.shape[0] = (double)op.small.nH; r.shape[1] = (double)op.small.rows;
+        r.shape[2] = (double)(1 << op.small.nN); r.shape[3] = (double)(1 << op.small.nK);
+    } else if (op.kind == OP_PERMUTE) {
+        r.shape[1] = (double)op.bp.plane_stride;
+    }
+    return r;
+}
+
 void prof_init(tn_plan &P) {
     if (!P.prof.empty()) return;
     int idx = 0;
-    for (auto &op : P.prologue) P.prof.push_back({0, idx++, (int)op.kind, op.step, 0.0, 0, op.macs, op.bytes});
-    P.prof.push_back({1, 0, 3, -1, 0.0, 0, 0.0, 0.0});
+    for (auto &op : P.prologue) P.prof.push_back(prof_row(0, idx++, op));
+    P.prof.push_back({1, 0, 3, -1, 0.0, 0, 0.0, 0.0, {0, 0, 0, 0}});
     idx = 0;
-    for (auto &op : P.batch) P.prof.push_back({1, idx++, (int)op.kind, op.step, 0.0, 0, op.macs, op.bytes});
-    P.prof.push_back({1, 0, 4, -1, 0.0, 0, 0.0, 0.0});
+    for (auto &op : P.batch) P.prof.push_back(prof_row(1, idx++, op));
+    P.prof.push_back({1, 0, 4, -1, 0.0, 0, 0.0, 0.0, {0, 0, 0, 0}});
     P.prof_ev.resize(2 * P.prof.size());
     for (auto &ev : P.prof_ev) cudaEventCreate(&ev);
 }
@@ -830,9 +896,10 @@ extern "C" int tn_plan_profile(tn_plan_t P, int max_rows, double *rows, int rese
     int n = 0;
     for (auto &r : P->prof) {
         if (n >= max_rows) break;
-        double *o = rows + 8 * n;
+        double *o = rows + 12 * n;
         o[0] = r.phase; o[1] = r.idx; o[2] = r.kind; o[3] = r.step;
         o[4] = r.ms; o[5] = (double)r.calls; o[6] = r.macs; o[7] = r.bytes;
+        for (int q = 0; q < 4; q++) o[8 + q] = r.shape[q];
         n++;
     }
     if (reset)

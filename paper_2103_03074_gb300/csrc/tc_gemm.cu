@@ -10,11 +10,10 @@
 // use four real products (re = ar br - ai bi, im = ar bi + ai br), the minus
 // sign folded into the MMA's negate-A bit: 12 MMAs per K step.
 //
-// Two kernels:
-//  * split_kernel: the hi/lo split of an operand into four planes re_hi,
-//    re_lo, im_hi, im_lo, K-major, in global memory; one pass, coalesced
-//    through a shared-memory transpose when the operand is not K-contiguous;
-//  * tc_gemm_kernel: warp-specialised.  Warp 0 issues TMA loads of the planes
+// The hi/lo split of each operand into four K-major planes (re_hi, re_lo,
+// im_hi, im_lo) is done beforehand by the tiled bit-permute kernel, fused with
+// whatever label permutation the operand needs (kernels.cu).
+// tc_gemm_kernel is warp-specialised.  Warp 0 issues TMA loads of the planes
 //    (128-byte swizzle) into a 2-stage shared-memory ring; warp 1 issues the
 //    MMAs of each K chunk into one of two tensor-memory accumulator sets;
 //    warps 4-11 read each finished chunk's accumulators (tcgen05.ld) and add
@@ -24,8 +23,13 @@
 //    reason (small addends aligned to a large running sum lose their low bits).
 //
 // CTA tile: 128 (M) x 64 (N); a K chunk is 128 bytes of a plane row (64 bf16
-// or 32 tf32 values).  Every mbarrier wait is bounded; on expiry the kernel
-// records an error in tc_error and returns after freeing its tensor memory.
+// or 32 tf32 values).  CTAs sharing an A tile are adjacent in the launch order
+// (N tiles vary fastest), so A is read from DRAM about once and re-served from
+// L2.  The output tile is staged in shared memory and written as whole rows.
+// GEMMs with fewer tiles than SMs split K over CTAs and add their partial
+// tiles with atomics into a zeroed output.  Every mbarrier wait is bounded; on
+// expiry the kernel records an error in tc_error and returns after freeing its
+// tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -138,67 +142,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// --------------------------------------------------------------- split pass
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// planes[h][p][row][k]: p = re_hi, re_lo, im_hi, im_lo
-template <bool kTF32>
-__global__ void __launch_bounds__(256) split_kernel(const SplitArgs s) {
-    __shared__ float2 tile[32][33];
-    const int64_t row0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-    for (int64_t h = blockIdx.z; h < s.H; h += gridDim.z) {
-        const float2 *X = s.X + h * s.s_h;
-        // read: coalesced along the unit-stride dimension
-        if (s.s_row == 1 && s.s_k != 1) {
-            for (int i = ty; i < 32; i += 8) {
-                const int64_t k = k0 + i, row = row0 + tx;
-                tile[tx][i] = (k < s.K && row < s.rows) ? X[k * s.s_k + row] : make_float2(0.f, 0.f);
-            }
-        } else {
-            for (int i = ty; i < 32; i += 8) {
-                const int64_t row = row0 + i, k = k0 + tx;
-                tile[i][tx] = (k < s.K && row < s.rows) ? X[row * s.s_row + k * s.s_k] : make_float2(0.f, 0.f);
-            }
-        }
-        __syncthreads();
-        // write: coalesced along k
-        const int64_t plane = s.rows * s.K;
-        for (int i = ty; i < 32; i += 8) {
-            const int64_t row = row0 + i, k = k0 + tx;
-            if (row >= s.rows || k >= s.K) continue;
-            const float2 v = tile[i][tx];
-            const int64_t o = ((h * 4) * s.rows + row) * s.K + k;
-            if (kTF32) {
-                uint32_t *P = reinterpret_cast<uint32_t *>(s.P);
-                const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
-                P[o] = rh;
-                P[o + plane] = tf32_rna(v.x - __uint_as_float(rh));
-                P[o + 2 * plane] = ih;
-                P[o + 3 * plane] = tf32_rna(v.y - __uint_as_float(ih));
-            } else {
-                uint16_t *P = reinterpret_cast<uint16_t *>(s.P);
-                const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-                P[o] = __bfloat16_as_ushort(rh);
-                P[o + plane] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
-                P[o + 2 * plane] = __bfloat16_as_ushort(ih);
-                P[o + 3 * plane] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------------- GEMM
 struct GemmTcParams {
     float2 *C;
     int64_t H, M, N, K;  // K in complex elements
     int64_t sCh, sCm, sCn;
     int k_chunk;  // K values per 128-byte chunk (64 bf16 / 32 tf32)
+    int ksplit;   // K partitions (blockIdx.z = h * ksplit + part); > 1: atomic adds
 };
 
 template <bool kTF32>
@@ -234,9 +184,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TN;
-    const int h = blockIdx.z;
-    const int n_chunks = (int)((p.K + p.k_chunk - 1) / p.k_chunk);
+    const int64_t n0 = (int64_t)blockIdx.x * TN, m0 = (int64_t)blockIdx.y * TM;
+    const int h = blockIdx.z / p.ksplit, part = blockIdx.z % p.ksplit;
+    const int all_chunks = (int)((p.K + p.k_chunk - 1) / p.k_chunk);
+    const int per = (all_chunks + p.ksplit - 1) / p.ksplit;
+    const int c_begin = part * per;
+    const int c_end = min(all_chunks, c_begin + per);
+    const int n_chunks = c_end > c_begin ? c_end - c_begin : 0;
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -247,8 +201,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unsigned char *st = smem + s * kStageBytes;
                 const uint32_t fb = smem_u32(&full[s]);
                 mbar_expect_tx(fb, kStageBytes);
-                tma_load_4d(smem_u32(st), &mapA, c * p.k_chunk, (int)m0, 0, h, fb);
-                tma_load_4d(smem_u32(st + 4 * kAPlane), &mapB, c * p.k_chunk, (int)n0, 0, h, fb);
+                const int kc = (c_begin + c) * p.k_chunk;
+                tma_load_4d(smem_u32(st), &mapA, kc, (int)m0, h, 0, fb);
+                tma_load_4d(smem_u32(st + 4 * kAPlane), &mapB, kc, (int)n0, h, 0, fb);
             }
         }
     } else if (warp == 1) {
@@ -322,12 +277,40 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
         }
         const int64_t m = m0 + lg * 32 + lane;
-        if (ok && m < p.M) {
-            float2 *C = p.C + (int64_t)h * p.sCh + m * p.sCm;
+        float2 *Ch = p.C + (int64_t)h * p.sCh;
+        if (p.ksplit > 1) {
+            // partial K range: add into the zeroed output
+            if (ok && m < p.M && n_chunks > 0) {
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const int64_t n = n0 + half * 32 + j;
-                if (n < p.N) C[n * p.sCn] = make_float2(acc_re[j], acc_im[j]);
+                for (int j = 0; j < 32; j++) {
+                    const int64_t n = n0 + half * 32 + j;
+                    if (n < p.N) atomicAdd(Ch + m * p.sCm + n * p.sCn, make_float2(acc_re[j], acc_im[j]));
+                }
+            }
+        } else {
+            // stage the 128 x 64 tile in shared memory (the TMA ring is idle:
+            // every load was consumed and every MMA has completed), then
+            // write whole rows: a warp stores one 512-byte row per instruction
+            constexpr int RS = 66;  // row stride in float2, 16-byte aligned
+            float2 *cs = reinterpret_cast<float2 *>(smem);
+            const int r = lg * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < 32; j++) cs[r * RS + half * 32 + j] = make_float2(acc_re[j], acc_im[j]);
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (ok) {
+                for (int rr = fw; rr < TM; rr += kFlushWarps) {
+                    const int64_t mm = m0 + rr;
+                    if (mm >= p.M) break;
+                    const int64_t n = n0 + 2 * lane;
+                    float2 *dst = Ch + mm * p.sCm;
+                    if (p.sCn == 1 && n + 1 < p.N) {
+                        const float4 v = *reinterpret_cast<const float4 *>(cs + rr * RS + 2 * lane);
+                        *reinterpret_cast<float4 *>(dst + n) = v;
+                    } else {
+                        if (n < p.N) dst[n * p.sCn] = cs[rr * RS + 2 * lane];
+                        if (n + 1 < p.N) dst[(n + 1) * p.sCn] = cs[rr * RS + 2 * lane + 1];
+                    }
+                }
             }
         }
     }
@@ -351,20 +334,23 @@ EncodeTiledFn encode_fn() {
         tried = true;
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<EncodeTiledFn>(p);
     }
     return fn;
 }
 
-// planes [H][4][rows][K] of element size es; box = 128 bytes of K x box_rows x 4 planes x 1
+// planes [4][H][rows][K] of element size es (plane-major, as the split pass
+// writes them); box = 128 bytes of K x box_rows x 1 batch x 4 planes, which
+// lands in shared memory as [plane][row][128 bytes]
 bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int64_t K, int es, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, 4, (cuuint64_t)H};
-    cuuint64_t strides[3] = {(cuuint64_t)(K * es), (cuuint64_t)(rows * K * es), (cuuint64_t)(4 * rows * K * es)};
-    cuuint32_t box[4] = {(cuuint32_t)(kChunkBytes / es), (cuuint32_t)box_rows, 4, 1};
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)H, 4};
+    cuuint64_t strides[3] = {(cuuint64_t)(K * es), (cuuint64_t)(rows * K * es), (cuuint64_t)(H * rows * K * es)};
+    cuuint32_t box[4] = {(cuuint32_t)(kChunkBytes / es), (cuuint32_t)box_rows, 1, 4};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, planes, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -381,8 +367,17 @@ bool tc_form_available(tn_form form) {
 int tc_plane_bytes(tn_form form) { return form == TN_TF32X3 ? 4 : 2; }
 
 bool tc_gemm_suitable(const GemmArgs &a) {
-    return a.M >= 64 && a.N >= 32 && a.K >= 32 && a.H <= 65535 && a.M < (1ll << 31) && a.N < (1ll << 31) &&
-           a.K < (1ll << 31);
+    return a.M >= 64 && a.N >= 32 && a.K >= 32 && a.H <= 65535 && (a.M + TM - 1) / TM <= 65535 &&
+           a.N < (1ll << 31) && a.K < (1ll << 31);
+}
+
+int tc_choose_ksplit(const GemmArgs &a, tn_form form) {
+    const int64_t tiles = ((a.M + TM - 1) / TM) * ((a.N + TN - 1) / TN) * a.H;
+    const int64_t chunks = (a.K * tc_plane_bytes(form) + kChunkBytes - 1) / kChunkBytes;
+    int64_t s = 1;
+    // at least 4 chunks per part; aim for two CTAs per SM
+    while (tiles * s * 2 <= 2 * 152 && chunks / (s * 2) >= 4 && a.H * s * 2 <= 65535) s *= 2;
+    return (int)s;
 }
 
 bool tc_prepare(TcGemm &g) {
@@ -390,14 +385,6 @@ bool tc_prepare(TcGemm &g) {
     if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM)) return false;
     if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN)) return false;
     return true;
-}
-
-cudaError_t launch_split(const SplitArgs &s, tn_form form, cudaStream_t st) {
-    dim3 grid((unsigned)((s.K + 31) / 32), (unsigned)((s.rows + 31) / 32), (unsigned)(s.H < 65535 ? s.H : 65535));
-    if (grid.y > 65535 || grid.x == 0 || grid.y == 0) return cudaErrorInvalidConfiguration;
-    if (form == TN_TF32X3) split_kernel<true><<<grid, 256, 0, st>>>(s);
-    else split_kernel<false><<<grid, 256, 0, st>>>(s);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
@@ -421,9 +408,15 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.sCm = g.a.sCm;
     p.sCn = g.a.sCn;
     p.k_chunk = kChunkBytes / tc_plane_bytes(g.form);
+    p.ksplit = g.ksplit > 0 ? g.ksplit : 1;
     const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
-    if (gn > 65535 || g.a.H > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)gm, (unsigned)gn, (unsigned)g.a.H);
+    if (gm > 65535 || g.a.H * p.ksplit > 65535) return cudaErrorInvalidConfiguration;
+    if (p.ksplit > 1) {
+        // C = [H][M][N] contiguous (the plan's GEMM output layout)
+        cudaError_t e = cudaMemsetAsync(g.a.C, 0, (size_t)(g.a.H * g.a.M * g.a.N) * sizeof(float2), s);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)gn, (unsigned)gm, (unsigned)(g.a.H * p.ksplit));
     const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
     const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
     if (tf) tc_gemm_kernel<true><<<grid, kThreads, kSmem, s>>>(mA, mB, p);

@@ -7,22 +7,14 @@
 
 namespace tn {
 
-// Split of one GEMM operand X[h, row, k] = X[h s_h + row s_row + k s_k]
-// (complex64) into planes P[h][p][row][k], p = re_hi, re_lo, im_hi, im_lo,
-// each hi/lo pair in the form's element type (bf16 or tf32 kept in 32 bits).
-struct SplitArgs {
-    const float2 *X;
-    void *P;
-    int64_t H, rows, K;
-    int64_t s_h, s_row, s_k;
-};
-
-// One tensor-core GEMM: the GemmArgs contract plus the split planes of A
-// (rows = M) and B (rows = N) and their TMA descriptors.
+// One tensor-core GEMM: the GemmArgs contract (C = [H][M][N] contiguous) plus
+// the split planes of A (rows = M) and B (rows = N), planes[q][h][row][k], and
+// their TMA descriptors.
 struct TcGemm {
     GemmArgs a;
     tn_form form;
     void *planesA, *planesB;
+    int ksplit;  // K partitions over CTAs (1: none)
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
 };
@@ -42,7 +34,9 @@ bool tc_gemm_suitable(const GemmArgs &a);
 // driver rejects them.
 bool tc_prepare(TcGemm &g);
 
-cudaError_t launch_split(const SplitArgs &s, tn_form form, cudaStream_t st);
+// K partitions for a GEMM whose tile grid alone would leave SMs idle.
+int tc_choose_ksplit(const GemmArgs &a, tn_form form);
+
 cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s);
 
 // Read and clear the device error word of the tensor-core kernels (0 = ok,
