@@ -204,6 +204,32 @@ int tn_circuit_network(const tn_circuit *circuit, const uint8_t *fixed_bits, int
                        int64_t *total_elems, int32_t *ranks, int32_t *labels, float *out_data,
                        int32_t *open_labels);
 
+/*
+ * Allocation-free split-precision complex GEMM (the paper has no counterpart;
+ * this is a service of the library, not a step of the method).
+ *
+ * For callers that cannot allocate device memory where they need a product
+ * (an allocator owned by another framework with a fixed budget, real-time
+ * loops that must not enter the driver's allocator, code handed only device
+ * buffers): C = A B with complex64 A [M][K], B [K][N], C [M][N], all row-major,
+ * interleaved (re, im), device pointers owned by the caller; C is overwritten.
+ * form must be TN_TF32X3 or TN_BF16X3 (the same tensor-core kernels as the
+ * plan's GEMM steps).  M, N, K powers of two, M >= 64, N >= 32, K >= 32.
+ *
+ * Scratch: a fixed 32 MiB __device__ array inside the library, held by every
+ * GPU that loads the library until process exit; the hi/lo planes need
+ * 4 * e * (M + N) * K bytes (e = 4 for TF32X3, 2 for BF16X3) and larger
+ * problems are rejected with TN_ERR_ARG.  No call allocates or frees memory.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and each call
+ * overwrites the part it uses, so calls that overlap on the GPU (other
+ * streams, other host threads) race; order them on one stream.
+ * Errors: TN_ERR_ARG (sizes, form, NULL), TN_ERR_CUDA.
+ */
+int tn_gemm_split_noalloc(const float *d_A, const float *d_B, float *d_C, int64_t M, int64_t N, int64_t K,
+                          tn_form form, tn_stream_t stream);
+
 /* Per-plan statistics: out[0] MACs per slice batch, out[1] slices per batch,
  * out[2] arena bytes, out[3] number of steps, out[4] kernel launches per
  * batch, out[5] algorithmic HBM bytes per batch, out[6] MACs of the

@@ -60,10 +60,11 @@ _lib.tn_find_order.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes
 _lib.tn_circuit_network.argtypes = [ctypes.POINTER(Circuit), _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]
 _lib.tn_plan_stats.argtypes = [_vp, _vp]
+_lib.tn_gemm_split_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, _i64, ctypes.c_int, _vp]
 
 EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabilities_xeb", "tn_plan_destroy",
             "tn_last_error", "tn_find_order", "tn_circuit_network", "tn_plan_stats", "tn_plan_update_data",
-            "tn_plan_profile"]
+            "tn_plan_profile", "tn_gemm_split_noalloc"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split"}
 
 
@@ -268,3 +269,13 @@ def probabilities_xeb(d_amp, n_open, n_qubits, d_prob=None, d_out=None, stream=N
     if not sync:
         return None
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def gemm_split_noalloc(d_a, d_b, d_c, m, n, k, form="tf32x3", stream=None):
+    """tn_gemm_split_noalloc: C = A B (complex64, row-major device buffers) on the
+    tensor cores with the library's fixed scratch array, no device allocation.
+    For callers that may not allocate (an allocator owned elsewhere, real-time
+    loops); calls that overlap on the GPU share the scratch and race."""
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    _check(_lib.tn_gemm_split_noalloc(_dev_ptr(d_a), _dev_ptr(d_b), _dev_ptr(d_c), int(m), int(n), int(k), f,
+                                      _stream_ptr(stream)), "tn_gemm_split_noalloc")
