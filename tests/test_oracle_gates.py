@@ -77,18 +77,23 @@ def test_rect_patterns_counts_and_matchings():
         assert len(all_pairs) == len(set(all_pairs)) == r * (c - 1) + (r - 1) * c
 
 
-def test_rotated_lattice_counts():
+def test_rotated_lattice_counts_and_orientation():
     sites, pats = rotated_lattice(6, 9, ((0, 0),))
     assert len(sites) == 53
-    assert tuple(len(pats[k]) for k in "ABCD") == (26, 18, 24, 16)
+    assert tuple(len(pats[k]) for k in "ABCD") == (26, 16, 24, 18)
     assert all(_is_matching(pats[k]) for k in "ABCD")
-    # each coupler joins sites in adjacent rows
-    for k in "ABCD":
+    # x position of a site: odd rows sit half a site to the right
+    x = lambda s: s[1] + 0.5 * (s[0] % 2)
+    for k, dx in (("A", 0.5), ("B", 0.5), ("C", -0.5), ("D", -0.5)):
         for a, b in pats[k]:
-            assert sites[b][0] == sites[a][0] + 1
+            assert sites[b][0] == sites[a][0] + 1          # adjacent rows
+            assert x(sites[b]) - x(sites[a]) == dx, k      # one orientation per A/B and per C/D
+    # every nearest-neighbour coupler of the lattice appears exactly once
+    all_pairs = sorted(tuple(sorted(p)) for k in "ABCD" for p in pats[k])
+    assert len(all_pairs) == len(set(all_pairs)) == 84
 
 
-@pytest.mark.parametrize("idx,n2", [(1, 34), (2, 147), (4, 292), (5, 420)])
+@pytest.mark.parametrize("idx,n2", [(1, 34), (2, 147), (4, 294), (5, 420)])
 def test_config_gate_counts(idx, n2):
     cfg = make_config(idx)
     assert cfg["circuit"].n_two_qubit() == n2

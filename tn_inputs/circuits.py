@@ -18,11 +18,14 @@ matrices nor the coupler patterns for a generic grid.  The readings used here:
 * Rectangular R x C grid, qubit q = r*C + c: A = horizontal (r,c)-(r,c+1) with
   c even, B = horizontal with c odd, C = vertical (r,c)-(r+1,c) with r even,
   D = vertical with r odd.
-* Rotated lattice (rows x cols sites, some removed): site (r,c) couples down to
-  (r+1,c) ("straight") and to (r+1, c-1) for even r / (r+1, c+1) for odd r
-  ("diagonal").  A = straight from even r, B = straight from odd r,
-  C = diagonal from even r, D = diagonal from odd r.  Qubits are the kept
-  sites numbered row-major.
+* Rotated lattice (rows x cols sites, some removed; odd rows sit half a site to
+  the right): site (r,c) couples down-right to (r+1,c) for even r and to
+  (r+1,c+1) for odd r, and down-left to (r+1,c-1) for even r and to (r+1,c)
+  for odd r.  A / B = down-right couplers from even / odd rows, C / D =
+  down-left couplers from even / odd rows, so A and B (and C and D) are the
+  two parities of one coupler orientation, as A/B and C/D are on the
+  rectangular grid, and each AB (CD) pair of layers sweeps a whole diagonal.
+  Qubits are the kept sites numbered row-major.
 * Bit order: qubit 0 is the most significant bit of a state-vector index.
 """
 from __future__ import annotations
@@ -106,12 +109,13 @@ def rotated_lattice(rows: int = 6, cols: int = 9, removed: Sequence[Tuple[int, i
     idx = {s: i for i, s in enumerate(sites)}
     pats: Dict[str, List[Tuple[int, int]]] = {k: [] for k in "ABCD"}
     for (r, c) in sites:
-        down = (r + 1, c)
-        if down in idx:
-            pats["A" if r % 2 == 0 else "B"].append((idx[(r, c)], idx[down]))
-        diag = (r + 1, c - 1) if r % 2 == 0 else (r + 1, c + 1)
-        if diag in idx:
-            pats["C" if r % 2 == 0 else "D"].append((idx[(r, c)], idx[diag]))
+        even = r % 2 == 0
+        down_right = (r + 1, c) if even else (r + 1, c + 1)
+        down_left = (r + 1, c - 1) if even else (r + 1, c)
+        if down_right in idx:
+            pats["A" if even else "B"].append((idx[(r, c)], idx[down_right]))
+        if down_left in idx:
+            pats["C" if even else "D"].append((idx[(r, c)], idx[down_left]))
     return sites, pats
 
 
