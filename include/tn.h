@@ -69,8 +69,13 @@ typedef struct {
     int32_t profile;
     /* capture each slice batch into a CUDA graph and replay it */
     int32_t use_graph;
+    /* tensor-core GEMM tuning (0 = library default): K bytes per pipeline
+     * stage and plane row (64 or 128), and K bytes between read-outs of the
+     * tensor-memory accumulators into FP32 registers (a multiple of it) */
+    int32_t tc_chunk_bytes;
+    int32_t tc_flush_bytes;
     /* reserved, set to 0 */
-    int32_t reserved[8];
+    int32_t reserved[6];
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

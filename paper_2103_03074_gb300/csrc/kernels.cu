@@ -70,50 +70,45 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = (uint32_t)scatter_bits(k, a.kposT, a.nK);
     for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = (uint32_t)scatter_bits(n, a.nposC, a.nN);
     __syncthreads();
+    // work item = (row r, chunk of up to 8 outputs n); rows vary fastest so
+    // consecutive threads read and write consecutive addresses
     const int NC = NS < 8 ? NS : 8;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.rows;
-         r += (int64_t)gridDim.x * blockDim.x) {
+    const int n_chunks = NS / NC;
+    const int64_t items = a.rows * n_chunks;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < items; w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = w % a.rows;
+        const int n0 = (int)(w / a.rows) * NC;
         const uint64_t tb = insert_zeros((uint64_t)r, a.tins, a.n_tins);
         const uint64_t cb = insert_zeros((uint64_t)r, a.cins, a.n_cins);
         const uint32_t h = gather_bits((uint64_t)r, a.hbitR, a.nH);
         const float2 *Sh = S_sm + (size_t)h * KS * NS;
+        float2 acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[j] = make_float2(0.f, 0.f);
         if (kRegT) {
             float2 t[16];
 #pragma unroll
             for (int k = 0; k < 16; k++)
                 if (k < KS) t[k] = a.T[tb + offT[k]];
-            for (int n0 = 0; n0 < NS; n0 += NC) {
-                float2 acc[8];
 #pragma unroll
-                for (int j = 0; j < 8; j++) acc[j] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int k = 0; k < 16; k++) {
-                    if (k < KS) {
-#pragma unroll
-                        for (int j = 0; j < 8; j++)
-                            if (j < NC) cfma(acc[j], t[k], Sh[k * NS + n0 + j]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 8; j++)
-                    if (j < NC) a.C[cb + offC[n0 + j]] = acc[j];
-            }
-        } else {
-            for (int n0 = 0; n0 < NS; n0 += NC) {
-                float2 acc[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) acc[j] = make_float2(0.f, 0.f);
-                for (int k = 0; k < KS; k++) {
-                    const float2 t = a.T[tb + offT[k]];
+            for (int k = 0; k < 16; k++) {
+                if (k < KS) {
 #pragma unroll
                     for (int j = 0; j < 8; j++)
-                        if (j < NC) cfma(acc[j], t, Sh[k * NS + n0 + j]);
+                        if (j < NC) cfma(acc[j], t[k], Sh[k * NS + n0 + j]);
                 }
+            }
+        } else {
+            for (int k = 0; k < KS; k++) {
+                const float2 t = a.T[tb + offT[k]];
 #pragma unroll
                 for (int j = 0; j < 8; j++)
-                    if (j < NC) a.C[cb + offC[n0 + j]] = acc[j];
+                    if (j < NC) cfma(acc[j], t, Sh[k * NS + n0 + j]);
             }
         }
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (j < NC) a.C[cb + offC[n0 + j]] = acc[j];
     }
 }
 
@@ -346,7 +341,7 @@ cudaError_t launch_small(const SmallArgs &a, cudaStream_t s) {
         cudaFuncSetAttribute(small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_done = true;
     }
-    const int grid = grid_for(a.rows);
+    const int grid = grid_for(a.rows * (NS < 8 ? 1 : NS / 8));
     if (KS <= 16) small_kernel<true><<<grid, kThreads, smem, s>>>(a);
     else small_kernel<false><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();

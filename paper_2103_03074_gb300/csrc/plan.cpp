@@ -633,6 +633,8 @@ void resolve_all(tn_plan &P) {
                 op.tc.planesA = resolve(P, op.in0);
                 op.tc.planesB = resolve(P, op.in1);
                 if (op.tc.ksplit < 1) op.tc.ksplit = 1;
+                op.tc.chunk_bytes = P.opts.tc_chunk_bytes;
+                op.tc.flush_bytes = P.opts.tc_flush_bytes;
             } else {
                 op.gemm.A = resolve(P, op.in0);
                 op.gemm.B = resolve(P, op.in1);

@@ -14,16 +14,16 @@
 // im_hi, im_lo) is done beforehand by the tiled bit-permute kernel, fused with
 // whatever label permutation the operand needs (kernels.cu).
 // tc_gemm_kernel is warp-specialised.  Warp 0 issues TMA loads of the planes
-//    (128-byte swizzle) into a 2-stage shared-memory ring; warp 1 issues the
-//    MMAs of each K chunk into one of two tensor-memory accumulator sets;
-//    warps 4-11 read each finished chunk's accumulators (tcgen05.ld) and add
-//    them into FP32 registers with round-to-nearest.  Flushing per chunk keeps
-//    the tensor core's truncating accumulation to a few MMAs; hi*hi and the
-//    correction products also sit in separate accumulators for the same
-//    reason (small addends aligned to a large running sum lose their low bits).
+// into a shared-memory ring (128-byte K chunks: 128-byte swizzle, 2 stages;
+// 64-byte chunks: 64-byte swizzle, 4 stages); warp 1 issues the MMAs of each
+// group of chunks into one of two tensor-memory accumulator sets; warps 4-11
+// read each finished group's accumulators (tcgen05.ld) and add them into FP32
+// registers with round-to-nearest.  Reading out every few hundred bytes of K
+// keeps the tensor core's truncating accumulation to a few dozen MMAs; hi*hi
+// and the correction products also sit in separate accumulators for the same
+// reason (small addends aligned to a large running sum lose their low bits).
 //
-// CTA tile: 128 (M) x 64 (N); a K chunk is 128 bytes of a plane row (64 bf16
-// or 32 tf32 values).  CTAs sharing an A tile are adjacent in the launch order
+// CTA tile: 128 (M) x 64 (N); a K chunk is 64 or 128 bytes of a plane row.  CTAs sharing an A tile are adjacent in the launch order
 // (N tiles vary fastest), so A is read from DRAM about once and re-served from
 // L2.  The output tile is staged in shared memory and written as whole rows.
 // GEMMs with fewer tiles than SMs split K over CTAs and add their partial
@@ -45,28 +45,42 @@ __device__ int tc_error = 0;
 namespace {
 
 constexpr int TM = 128, TN = 64;
-constexpr int kChunkBytes = 128;                        // one plane row of a chunk
-constexpr int kAPlane = TM * kChunkBytes;               // 16 KB
-constexpr int kBPlane = TN * kChunkBytes;               // 8 KB
-constexpr int kStageBytes = 4 * kAPlane + 4 * kBPlane;  // 96 KB
-constexpr int kStages = 2;
+// defaults from a sweep of (chunk, flush) on a 4 x 8192 x 512 x 2048 GEMM:
+// 128-byte chunks beat 64-byte ones at every flush interval; reading the
+// accumulators out every 512 bytes of K (instead of 128) is 8% faster and
+// keeps the error well inside the FP32 form's
+constexpr int kDefaultChunkBytes = 128, kDefaultFlushBytes = 512;
 constexpr int kThreads = 384;  // 12 warps
 constexpr int kFlushWarp0 = 4, kFlushWarps = 8;
 constexpr int kTmemCols = 512;  // 2 sets x {re, im, re corr, im corr} x 64
-constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+
+// Shared-memory ring for a K chunk of CB bytes per plane row: 4 planes of A
+// (128 rows) and of B (64 rows) per stage; 64-byte chunks use the 64-byte
+// swizzle and 4 stages, 128-byte chunks the 128-byte swizzle and 2 stages.
+template <int CB>
+struct Ring {
+    static constexpr int kAPlane = TM * CB;
+    static constexpr int kBPlane = TN * CB;
+    static constexpr int kStageBytes = 4 * kAPlane + 4 * kBPlane;
+    static constexpr int kStages = CB == 64 ? 4 : 2;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    static constexpr uint32_t kSBO = 8 * CB;                // 8 rows of one swizzle atom
+    static constexpr uint64_t kLayout = CB == 64 ? 4 : 2;  // descriptor swizzle code
+};
 constexpr uint32_t kSpinLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+template <int CB>
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)(16 >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(Ring<CB>::kSBO >> 4) << 32;  // stride byte offset: 8 rows
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= Ring<CB>::kLayout << 61;                 // swizzle mode
     return d;
 }
 
@@ -147,14 +161,18 @@ struct GemmTcParams {
     float2 *C;
     int64_t H, M, N, K;  // K in complex elements
     int64_t sCh, sCm, sCn;
-    int k_chunk;  // K values per 128-byte chunk (64 bf16 / 32 tf32)
-    int ksplit;   // K partitions (blockIdx.z = h * ksplit + part); > 1: atomic adds
+    int k_chunk;       // K values per chunk
+    int ksplit;        // K partitions (blockIdx.z = h * ksplit + part); > 1: atomic adds
+    int flush_chunks;  // chunks per accumulator read-out
 };
 
-template <bool kTF32>
+template <bool kTF32, int CB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
+    constexpr int kAPlane = Ring<CB>::kAPlane, kBPlane = Ring<CB>::kBPlane;
+    constexpr int kStageBytes = Ring<CB>::kStageBytes, kStages = Ring<CB>::kStages;
+    const int kFlushChunks = p.flush_chunks;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -213,20 +231,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             constexpr uint32_t IP = make_idesc(fmt, TM, TN, false), IN = make_idesc(fmt, TM, TN, true);
             for (int c = 0; c < n_chunks; c++) {
                 const int s = c % kStages, use = c / kStages;
-                const int t = c & 1, tuse = c >> 1;
+                const int g = c / kFlushChunks;             // flush group
+                const int t = g & 1, tuse = g >> 1;
+                const bool first = (c % kFlushChunks) == 0;
+                const bool last = (c % kFlushChunks) == kFlushChunks - 1 || c == n_chunks - 1;
                 if (!mbar_wait(smem_u32(&full[s]), use & 1)) break;
-                if (tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) break;
+                if (first && tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) break;
                 fence_after();
                 const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + 4 * kAPlane;
                 const uint32_t d_re = tmem + t * 256, d_im = d_re + 64, c_re = d_re + 128, c_im = d_re + 192;
 #pragma unroll
-                for (int ks = 0; ks < 4; ks++) {  // 4 MMA K steps of 32 bytes per chunk
+                for (int ks = 0; ks < CB / 32; ks++) {  // MMA K steps of 32 bytes
                     const uint32_t ko = ks * 32;
-                    const uint64_t arh = make_desc(a0 + ko), arl = make_desc(a0 + kAPlane + ko);
-                    const uint64_t aih = make_desc(a0 + 2 * kAPlane + ko), ail = make_desc(a0 + 3 * kAPlane + ko);
-                    const uint64_t brh = make_desc(b0 + ko), brl = make_desc(b0 + kBPlane + ko);
-                    const uint64_t bih = make_desc(b0 + 2 * kBPlane + ko), bil = make_desc(b0 + 3 * kBPlane + ko);
-                    const uint32_t acc = ks > 0 ? 1u : 0u;  // each chunk starts fresh sums
+                    const uint64_t arh = make_desc<CB>(a0 + ko), arl = make_desc<CB>(a0 + kAPlane + ko);
+                    const uint64_t aih = make_desc<CB>(a0 + 2 * kAPlane + ko);
+                    const uint64_t ail = make_desc<CB>(a0 + 3 * kAPlane + ko);
+                    const uint64_t brh = make_desc<CB>(b0 + ko), brl = make_desc<CB>(b0 + kBPlane + ko);
+                    const uint64_t bih = make_desc<CB>(b0 + 2 * kBPlane + ko);
+                    const uint64_t bil = make_desc<CB>(b0 + 3 * kBPlane + ko);
+                    const uint32_t acc = (first && ks == 0) ? 0u : 1u;  // each flush group starts fresh sums
                     mma<kTF32>(d_re, arh, brh, IP, acc);
                     mma<kTF32>(d_re, aih, bih, IN, 1u);
                     mma<kTF32>(c_re, arh, brl, IP, acc);
@@ -241,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mma<kTF32>(c_im, ail, brh, IP, 1u);
                 }
                 mma_commit(smem_u32(&empty[s]));
-                mma_commit(smem_u32(&tfull[t]));
+                if (last) mma_commit(smem_u32(&tfull[t]));
             }
         }
     } else if (warp >= kFlushWarp0) {
@@ -253,8 +276,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; j++) acc_re[j] = acc_im[j] = 0.f;
         bool ok = true;
-        for (int c = 0; c < n_chunks; c++) {
-            const int t = c & 1, tuse = c >> 1;
+        const int n_groups = (n_chunks + kFlushChunks - 1) / kFlushChunks;
+        for (int gi = 0; gi < n_groups; gi++) {
+            const int t = gi & 1, tuse = gi >> 1;
             if (!mbar_wait(smem_u32(&tfull[t]), tuse & 1)) { ok = false; break; }
             fence_after();
             const uint32_t base = tmem + t * 256 + lane_off + half * 32;
@@ -343,17 +367,19 @@ EncodeTiledFn encode_fn() {
 }
 
 // planes [4][H][rows][K] of element size es (plane-major, as the split pass
-// writes them); box = 128 bytes of K x box_rows x 1 batch x 4 planes, which
-// lands in shared memory as [plane][row][128 bytes]
-bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int64_t K, int es, int box_rows) {
+// writes them); box = cb bytes of K x box_rows x 1 batch x 4 planes, which
+// lands in shared memory as [plane][row][cb bytes], cb-byte swizzled
+bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int64_t K, int es, int box_rows,
+                   int cb) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)H, 4};
     cuuint64_t strides[3] = {(cuuint64_t)(K * es), (cuuint64_t)(rows * K * es), (cuuint64_t)(H * rows * K * es)};
-    cuuint32_t box[4] = {(cuuint32_t)(kChunkBytes / es), (cuuint32_t)box_rows, 1, 4};
+    cuuint32_t box[4] = {(cuuint32_t)(cb / es), (cuuint32_t)box_rows, 1, 4};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, planes, dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -373,7 +399,7 @@ bool tc_gemm_suitable(const GemmArgs &a) {
 
 int tc_choose_ksplit(const GemmArgs &a, tn_form form) {
     const int64_t tiles = ((a.M + TM - 1) / TM) * ((a.N + TN - 1) / TN) * a.H;
-    const int64_t chunks = (a.K * tc_plane_bytes(form) + kChunkBytes - 1) / kChunkBytes;
+    const int64_t chunks = (a.K * tc_plane_bytes(form) + 63) / 64;
     int64_t s = 1;
     // at least 4 chunks per part; aim for two CTAs per SM
     while (tiles * s * 2 <= 2 * 152 && chunks / (s * 2) >= 4 && a.H * s * 2 <= 65535) s *= 2;
@@ -382,22 +408,32 @@ int tc_choose_ksplit(const GemmArgs &a, tn_form form) {
 
 bool tc_prepare(TcGemm &g) {
     const int es = tc_plane_bytes(g.form);
-    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM)) return false;
-    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN)) return false;
+    if (g.chunk_bytes != 64 && g.chunk_bytes != 128) g.chunk_bytes = kDefaultChunkBytes;
+    if (g.flush_bytes < g.chunk_bytes) g.flush_bytes = kDefaultFlushBytes < g.chunk_bytes ? g.chunk_bytes : kDefaultFlushBytes;
+    if (g.a.K * es < g.chunk_bytes) g.chunk_bytes = 64;
+    const int cb = g.chunk_bytes;
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM, cb)) return false;
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN, cb)) return false;
     return true;
 }
 
-cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
-    static bool attr[2] = {false, false};
-    const int tf = g.form == TN_TF32X3 ? 1 : 0;
-    if (!attr[tf]) {
-        cudaError_t e = tf ? cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kSmem)
-                           : cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kSmem);
+template <bool kTF32, int CB>
+cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kTF32, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Ring<CB>::kSmem);
         if (e != cudaSuccess) return e;
-        attr[tf] = true;
+        attr = true;
     }
+    const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
+    const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
+    tc_gemm_kernel<kTF32, CB><<<grid, kThreads, Ring<CB>::kSmem, s>>>(mA, mB, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
+    const bool tf = g.form == TN_TF32X3;
     GemmTcParams p;
     p.C = g.a.C;
     p.H = g.a.H;
@@ -407,8 +443,10 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.sCh = g.a.sCh;
     p.sCm = g.a.sCm;
     p.sCn = g.a.sCn;
-    p.k_chunk = kChunkBytes / tc_plane_bytes(g.form);
+    p.k_chunk = g.chunk_bytes / tc_plane_bytes(g.form);
     p.ksplit = g.ksplit > 0 ? g.ksplit : 1;
+    p.flush_chunks = g.flush_bytes / g.chunk_bytes;
+    if (p.flush_chunks < 1) p.flush_chunks = 1;
     const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
     if (gm > 65535 || g.a.H * p.ksplit > 65535) return cudaErrorInvalidConfiguration;
     if (p.ksplit > 1) {
@@ -417,11 +455,9 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)gn, (unsigned)gm, (unsigned)(g.a.H * p.ksplit));
-    const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
-    const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
-    if (tf) tc_gemm_kernel<true><<<grid, kThreads, kSmem, s>>>(mA, mB, p);
-    else tc_gemm_kernel<false><<<grid, kThreads, kSmem, s>>>(mA, mB, p);
-    return cudaGetLastError();
+    if (g.chunk_bytes == 64)
+        return tf ? launch_variant<true, 64>(g, p, grid, s) : launch_variant<false, 64>(g, p, grid, s);
+    return tf ? launch_variant<true, 128>(g, p, grid, s) : launch_variant<false, 128>(g, p, grid, s);
 }
 
 int tc_read_error(cudaStream_t s) {

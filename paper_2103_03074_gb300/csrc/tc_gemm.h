@@ -14,7 +14,9 @@ struct TcGemm {
     GemmArgs a;
     tn_form form;
     void *planesA, *planesB;
-    int ksplit;  // K partitions over CTAs (1: none)
+    int ksplit;       // K partitions over CTAs (1: none)
+    int chunk_bytes;  // K chunk per TMA stage and plane row: 64 or 128 (0: default)
+    int flush_bytes;  // bytes of K between accumulator read-outs (multiple of chunk_bytes; 0: default)
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
 };

@@ -9,10 +9,12 @@ label shared by both operands.  Each result is checked twice:
     about 5e-6 in the L2 sense for random data (1e-5 asserted);
   * against a test-side emulation of the same arithmetic (round-to-nearest
     split, hi*hi + hi*lo + lo*hi, 4 real products, exact accumulation):
-    agreement to 5e-7.  The kernel adds each K chunk's tensor-core partial
-    sums into FP32 registers with round-to-nearest, so the only difference is
-    FP32 rounding of those sums; a kernel that dropped or misplaced any product
-    term would be off by 1e-3 (bf16) or 1e-6 (tf32) or more.
+    agreement to 1e-6.  The kernel reads the tensor-core partial sums out into
+    FP32 registers (round-to-nearest) every 512 bytes of K, so the difference
+    is the tensor core's truncating accumulation over 32 MMAs plus FP32
+    rounding: 6.4e-7 measured at K = 1024 (2.1e-6 when never read out, 1.5e-7
+    when read out every 128 bytes).  A kernel that dropped or misplaced any
+    product term would be off by ~5e-4 (tf32 lo/hi ratio) or ~4e-3 (bf16).
 FP32 form: the CUDA-core kernel against the exact product, 2e-6 (FP32 sums of
 up to 2048 products).
 """
@@ -102,7 +104,7 @@ def test_single_gemm_bf16x3(tn, m, k, n, a_kfirst, b_nfirst):
         got = (g[0::2] + 1j * g[1::2]).reshape(M, N)
         assert rel(got, exact) < tol_exact, form
         if form != "fp32":
-            assert rel(got, emu[form]) < 5e-7, form
+            assert rel(got, emu[form]) < 1e-6, form
         if form == "bf16x3":
             assert rel(emu[form], exact) > 1e-6  # the split form really is coarser than FP32
         plan.close()
