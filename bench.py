@@ -256,7 +256,7 @@ def run_native(args):
     results = {}
     for form in forms:
         try:
-            plan = tn.Plan(L, T, O, sliced, tree, form=form)
+            plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1))
         except tn.TNError as e:
             results[form] = {"error": str(e)}
             continue
@@ -379,6 +379,7 @@ def run_native(args):
         "config": {"workload": "rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 22 fixed, "
                                "2^8 slices over 8 searched bonds", "form": best,
                    "step": "all 256 slices summed in FP64 + probabilities/XEB",
+                   "executor": "CUDA-graph replay of the prologue and per-block body",
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
                    "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],

@@ -67,7 +67,10 @@ typedef struct {
     int64_t mem_budget;
     /* record per-step CUDA-event timings on every call (profiling mode) */
     int32_t profile;
-    /* capture each slice batch into a CUDA graph and replay it */
+    /* CUDA-graph replay: the first tn_contract_slices call runs eagerly, then
+     * captures the slice-invariant prologue and the per-block body into two
+     * graphs; later calls replay them (the slice extraction and the FP64 sum,
+     * whose arguments change per block, stay ordinary launches) */
     int32_t use_graph;
     /* tensor-core GEMM tuning (0 = library default): K bytes per pipeline
      * stage and plane row (64 or 128), and K bytes between read-outs of the
@@ -238,7 +241,9 @@ int tn_gemm_split_noalloc(const float *d_A, const float *d_B, float *d_C, int64_
 /* Per-plan statistics: out[0] MACs per slice batch, out[1] slices per batch,
  * out[2] arena bytes, out[3] number of steps, out[4] kernel launches per
  * batch, out[5] algorithmic HBM bytes per batch, out[6] MACs of the
- * slice-invariant prologue (computed once per plan). */
+ * slice-invariant prologue (computed once per call), out[7] its bytes,
+ * out[8] its launches, out[9] log2 slices per batch, out[10] calls served by
+ * CUDA-graph replay.  out must hold 11 doubles. */
 int tn_plan_stats(tn_plan_t plan, double *out);
 
 #ifdef __cplusplus

@@ -229,7 +229,7 @@ class Plan:
         out = np.zeros(16)
         _check(_lib.tn_plan_stats(self._h, _ptr(out)), "tn_plan_stats")
         keys = ["macs_batch", "slices_per_batch", "arena_bytes", "n_steps", "launches_batch", "bytes_batch",
-                "macs_prologue", "bytes_prologue", "launches_prologue", "batch_log2"]
+                "macs_prologue", "bytes_prologue", "launches_prologue", "batch_log2", "graph_replays"]
         return {k: float(out[i]) for i, k in enumerate(keys)}
 
     def close(self):

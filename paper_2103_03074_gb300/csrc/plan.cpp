@@ -193,6 +193,11 @@ struct tn_plan {
     std::vector<ProfRow> prof;
     std::vector<cudaEvent_t> prof_ev;  // two per row
     int64_t leaf_bytes = 0;
+    // CUDA-graph replay (opts.use_graph): the slice-invariant prologue and the
+    // per-block body, captured once after the first eager call
+    bool graphs_ready = false;
+    cudaGraphExec_t g_pro = nullptr, g_body = nullptr;
+    int64_t graph_calls = 0;
 };
 
 namespace tn {
@@ -820,6 +825,36 @@ void prof_init(tn_plan &P) {
     for (auto &ev : P.prof_ev) cudaEventCreate(&ev);
 }
 
+// Capture ops into an instantiated graph on a private stream (the ops' own
+// launch-time setup already ran in an eager call).
+cudaError_t capture_ops(const tn_plan &P, const std::vector<Op> &ops, cudaGraphExec_t *out) {
+    *out = nullptr;
+    if (ops.empty()) return cudaSuccess;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaSuccess;
+        for (const auto &op : ops)
+            if ((le = run_op(P, op, cs)) != cudaSuccess) break;
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+cudaError_t build_graphs(tn_plan &P) {
+    cudaError_t e = capture_ops(P, P.prologue, &P.g_pro);
+    if (e == cudaSuccess) e = capture_ops(P, P.batch, &P.g_body);
+    if (e == cudaSuccess) P.graphs_ready = true;
+    return e;
+}
+
 cudaError_t prof_collect(tn_plan &P, size_t r0, size_t r1, cudaStream_t s) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
@@ -847,6 +882,29 @@ extern "C" int tn_contract_slices(tn_plan_t P, int64_t begin, int64_t end, doubl
     const bool prof = P->opts.profile != 0;
     if (prof) prof_init(*P);
     cudaError_t e = cudaSuccess;
+    if (P->opts.use_graph && !prof && P->graphs_ready) {
+        // replay: prologue graph, then per block extract + body graph + FP64 sum
+        if (P->g_pro && (e = cudaGraphLaunch(P->g_pro, s)) != cudaSuccess) {
+            P->failed = true;
+            return cuda_fail(e, "prologue graph launch");
+        }
+        const int64_t B = (int64_t)1 << P->nb;
+        AccumArgs acc = P->accum;
+        acc.amp = reinterpret_cast<double2 *>(d_amp);
+        for (int64_t base = (begin / B) * B; base < end; base += B) {
+            e = launch_extract(P->d_extract, (int)P->extract.size(), P->extract_max_out, (uint64_t)base, s);
+            if (e == cudaSuccess && P->g_body) e = cudaGraphLaunch(P->g_body, s);
+            acc.b_lo = std::max(begin, base) - base;
+            acc.b_hi = std::min(end, base + B) - base;
+            if (e == cudaSuccess) e = launch_accum(acc, s);
+            if (e != cudaSuccess) {
+                P->failed = true;
+                return cuda_fail(e, "graph replay");
+            }
+        }
+        P->graph_calls++;
+        return TN_OK;
+    }
     size_t row = 0;
     auto timed = [&](auto &&launch) -> cudaError_t {
         if (prof) cudaEventRecord(P->prof_ev[2 * row], s);
@@ -890,6 +948,10 @@ extern "C" int tn_contract_slices(tn_plan_t P, int64_t begin, int64_t end, doubl
         P->failed = true;
         return fail(TN_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
     }
+    if (P->opts.use_graph && !prof && !P->graphs_ready && (e = build_graphs(*P)) != cudaSuccess) {
+        P->failed = true;
+        return cuda_fail(e, "graph capture");
+    }
     return TN_OK;
 }
 
@@ -923,6 +985,8 @@ extern "C" void tn_plan_destroy(tn_plan_t P) {
     if (P->d_arena) cudaFree(P->d_arena);
     if (P->d_extract) cudaFree(P->d_extract);
     for (auto &ev : P->prof_ev) cudaEventDestroy(ev);
+    if (P->g_pro) cudaGraphExecDestroy(P->g_pro);
+    if (P->g_body) cudaGraphExecDestroy(P->g_body);
     delete P;
 }
 
@@ -938,6 +1002,7 @@ extern "C" int tn_plan_stats(tn_plan_t P, double *out) {
     out[7] = P->bytes_prologue;
     out[8] = (double)P->launches_prologue;
     out[9] = (double)P->nb;
+    out[10] = (double)P->graph_calls;
     return TN_OK;
 }
 

@@ -216,3 +216,25 @@ def test_probabilities_xeb_on_oracle_amplitudes(tn):
     assert abs(p_s1 - p.sum()) < 1e-14
     assert abs(f - oxeb.linear_xeb(ref, 12)) < 1e-12
     assert abs(pmax - p.max()) < 1e-18
+
+
+@pytest.mark.parametrize("form", ["fp32", "tf32x3"])
+def test_graph_replay_matches_oracle(tn, form):
+    """use_graph: the first call runs eagerly and captures the prologue and the
+    per-block body; later calls replay the graphs.  Full and ragged ranges,
+    several blocks per call."""
+    net = random_network(31, n_tensors=16, n_bonds=40, n_open=3, max_rank=10)
+    sliced = pick(5, internal_labels(net.labels), 4)
+    tree, _, _ = tn.find_order(net.labels, net.open_labels, tn.search_opts(trials=8, n_sliced=0))
+    plan = tn.Plan(net.labels, net.data, net.open_labels, sliced, tree, form=form,
+                   opts=tn.plan_opts(batch_log2=2, use_graph=1))
+    ref = oc.sliced_sum(net.labels, net.data, net.open_labels, sliced)
+    for rep in range(3):
+        amp = dev_zeros(3)
+        plan.contract(0, 16, amp)
+        assert rel(to_complex(amp), ref) < TOL, rep
+    part = dev_zeros(3)
+    plan.contract(3, 13, part)
+    assert rel(to_complex(part), oc.sliced_sum(net.labels, net.data, net.open_labels, sliced, 3, 13)) < TOL
+    assert plan.stats()["graph_replays"] >= 3
+    plan.close()
