@@ -38,6 +38,7 @@ extern "C" {
 #endif
 
 typedef struct tn_plan *tn_plan_t; /* opaque, owned by the library */
+typedef struct tn_costmodel *tn_costmodel_t; /* opaque learned step-cost model */
 typedef struct CUstream_st *tn_stream_t; /* a cudaStream_t */
 
 enum {
@@ -88,7 +89,16 @@ typedef struct {
     int32_t log2_cap;   /* slice until every intermediate has <= 2^log2_cap elements (-1: no cap) */
     int32_t n_sliced;   /* slice exactly this many labels (-1: as the cap needs) */
     int32_t threads;    /* host threads (0 = hardware concurrency) */
-    int32_t reserved[7];
+    /* learned ranking: with cost_model set and candidates > 1, the best
+     * `candidates` trees by the analytic cost are compiled (for rank_form, with
+     * 2^rank_batch_log2 slices per pass, -1 = all sliced labels) and the one
+     * with the smallest predicted device time wins; otherwise the analytic
+     * cost (total complex MACs over all slices) decides */
+    int32_t candidates;
+    int32_t rank_batch_log2;
+    int32_t rank_form;
+    tn_costmodel_t cost_model;
+    int32_t reserved[2];
 } tn_search_opts;
 
 /* A circuit: gate g acts on gate_nq[g] (1 or 2) qubits gate_q[2g], gate_q[2g+1]
@@ -237,6 +247,41 @@ int tn_circuit_network(const tn_circuit *circuit, const uint8_t *fixed_bits, int
  */
 int tn_gemm_split_noalloc(const float *d_A, const float *d_B, float *d_C, int64_t M, int64_t N, int64_t K,
                           tn_form form, tn_stream_t stream);
+
+/*
+ * Learned step-cost model: an MLP (16 features -> 64 -> 64 -> 1, ReLU, FP32)
+ * that predicts log2 of a step's device time in ms from the step features of
+ * tn_plan_op_features.  Trained on the GPU by the library's own forward,
+ * backward and Adam kernels on timings from tn_plan_profile.  Not a step of
+ * the paper's method: it ranks candidate contraction trees for the search.
+ *   create: seeded He-normal initialisation.
+ *   params: copy the flat parameter vector out (get) and/or in (set), host
+ *           memory, n_params floats (W1[64][16], b1, W2[64][64], b2, w3, b3).
+ *   grad:   mean-squared-error loss and its gradient for device features
+ *           d_X[n][16] and targets d_T[n]; gradient copied to d_grad (device,
+ *           n_params floats, may be NULL); loss to host (synchronises).
+ *   train:  `epochs` full-batch Adam steps (learning rate lr); final loss to
+ *           host (synchronises).
+ *   predict: d_Y[n] = model(d_X), stream-ordered.
+ */
+int tn_costmodel_create(tn_costmodel_t *out, uint64_t seed);
+void tn_costmodel_destroy(tn_costmodel_t cm);
+int tn_costmodel_params(tn_costmodel_t cm, float *get, const float *set, int *n_params);
+int tn_costmodel_grad(tn_costmodel_t cm, const float *d_X, const float *d_T, int64_t n, float *d_grad,
+                      double *loss, tn_stream_t stream);
+int tn_costmodel_train(tn_costmodel_t cm, const float *d_X, const float *d_T, int64_t n, int epochs, float lr,
+                       double *final_loss, tn_stream_t stream);
+int tn_costmodel_predict(tn_costmodel_t cm, const float *d_X, float *d_Y, int64_t n, tn_stream_t stream);
+
+/*
+ * Step features (16 floats per kernel step, in the order of tn_plan_profile's
+ * rows without the extraction and FP64-sum rows): kind one-hot {small step,
+ * permute, FP32 GEMM, tensor-core GEMM, hi/lo split}, log2(MACs+1)/32,
+ * log2(bytes+1)/32, log2 of the four shape entries /32, TF32 flag, BF16 flag,
+ * log2(parallel work units)/32, log2(K partitions)/8, 1.  Returns the number
+ * of steps written (at most max_ops) or a negative error.
+ */
+int tn_plan_op_features(tn_plan_t plan, float *out, int max_ops);
 
 /* Per-plan statistics: out[0] MACs per slice batch, out[1] slices per batch,
  * out[2] arena bytes, out[3] number of steps, out[4] kernel launches per

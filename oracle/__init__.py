@@ -21,7 +21,9 @@ Routes (each function cites the passage of the paper it follows):
   only on tiny inputs to pin the routes above.
 * ``xeb``          - probabilities, linear XEB (Eq. 1), marginal and
   conditional probabilities (appendix on conditional probabilities).
+* ``mlp``          - float64 forward/backward of the learned step-cost MLP
+  (not a step of the paper's method; checks the GPU training kernels).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
-from . import statevector, network, contract, bruteforce, xeb  # noqa: F401
+from . import statevector, network, contract, bruteforce, xeb, mlp  # noqa: F401

@@ -37,7 +37,8 @@ class PlanOpts(ctypes.Structure):
 
 class SearchOpts(ctypes.Structure):
     _fields_ = [("trials", _i32), ("seed", ctypes.c_uint64), ("log2_cap", _i32), ("n_sliced", _i32),
-                ("threads", _i32), ("reserved", _i32 * 7)]
+                ("threads", _i32), ("candidates", _i32), ("rank_batch_log2", _i32), ("rank_form", _i32),
+                ("cost_model", _vp), ("reserved", _i32 * 2)]
 
 
 class Circuit(ctypes.Structure):
@@ -61,10 +62,22 @@ _lib.tn_circuit_network.argtypes = [ctypes.POINTER(Circuit), _vp, ctypes.c_int, 
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]
 _lib.tn_plan_stats.argtypes = [_vp, _vp]
 _lib.tn_gemm_split_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, _i64, ctypes.c_int, _vp]
+_lib.tn_costmodel_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_uint64]
+_lib.tn_costmodel_destroy.argtypes = [_vp]
+_lib.tn_costmodel_destroy.restype = None
+_lib.tn_costmodel_params.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int)]
+_lib.tn_costmodel_grad.argtypes = [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+_lib.tn_costmodel_train.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, ctypes.c_float,
+                                    ctypes.POINTER(ctypes.c_double), _vp]
+_lib.tn_costmodel_predict.argtypes = [_vp, _vp, _vp, _i64, _vp]
+_lib.tn_plan_op_features.argtypes = [_vp, _vp, ctypes.c_int]
+COST_FEATURES = 16
 
 EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabilities_xeb", "tn_plan_destroy",
             "tn_last_error", "tn_find_order", "tn_circuit_network", "tn_plan_stats", "tn_plan_update_data",
-            "tn_plan_profile", "tn_gemm_split_noalloc"]
+            "tn_plan_profile", "tn_gemm_split_noalloc", "tn_costmodel_create", "tn_costmodel_destroy",
+            "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
+            "tn_plan_op_features"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split"}
 
 
@@ -96,8 +109,11 @@ def _dev_ptr(t):
     return _vp(t.data_ptr())
 
 
-def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads=0):
-    return SearchOpts(trials, seed, log2_cap, n_sliced, threads)
+def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads=0, candidates=0,
+                rank_batch_log2=-1, rank_form="fp32", cost_model=None):
+    f = FORMS[rank_form] if isinstance(rank_form, str) else int(rank_form)
+    cm = cost_model._h if cost_model is not None else None
+    return SearchOpts(trials, seed, log2_cap, n_sliced, threads, candidates, rank_batch_log2, f, cm)
 
 
 def plan_opts(batch_log2=-1, mem_budget=0, profile=0, use_graph=0, tc_chunk_bytes=0, tc_flush_bytes=0):
@@ -225,6 +241,15 @@ class Plan:
                             shape=[float(x) for x in r[8:12]]))
         return out
 
+    def op_features(self, max_ops=4096):
+        """Step features (rows of 16) in the order of profile() rows without
+        the extraction and FP64-sum rows."""
+        out = np.zeros(COST_FEATURES * max_ops, dtype=np.float32)
+        n = _lib.tn_plan_op_features(self._h, _ptr(out), max_ops)
+        if n < 0:
+            raise TNError(n, "tn_plan_op_features")
+        return out[:COST_FEATURES * n].reshape(n, COST_FEATURES)
+
     def stats(self):
         out = np.zeros(16)
         _check(_lib.tn_plan_stats(self._h, _ptr(out)), "tn_plan_stats")
@@ -279,3 +304,56 @@ def gemm_split_noalloc(d_a, d_b, d_c, m, n, k, form="tf32x3", stream=None):
     f = FORMS[form] if isinstance(form, str) else int(form)
     _check(_lib.tn_gemm_split_noalloc(_dev_ptr(d_a), _dev_ptr(d_b), _dev_ptr(d_c), int(m), int(n), int(k), f,
                                       _stream_ptr(stream)), "tn_gemm_split_noalloc")
+
+
+class CostModel:
+    """Learned step-cost model (tn_costmodel_*): predicts log2 of a step's
+    device time in ms from its 16 features; trained on the GPU by the
+    library's own forward/backward/Adam kernels."""
+
+    def __init__(self, seed=1):
+        h = _vp()
+        _check(_lib.tn_costmodel_create(ctypes.byref(h), seed), "tn_costmodel_create")
+        self._h = h
+        n = ctypes.c_int()
+        _check(_lib.tn_costmodel_params(self._h, None, None, ctypes.byref(n)), "tn_costmodel_params")
+        self.n_params = n.value
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(_lib.tn_costmodel_params(self._h, _ptr(out), None, None), "tn_costmodel_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(_lib.tn_costmodel_params(self._h, None, _ptr(p), None), "tn_costmodel_params")
+
+    def grad(self, d_x, d_t, d_grad=None, stream=None):
+        """(loss, device gradient) of the mean squared error on device data."""
+        loss = ctypes.c_double()
+        n = d_t.numel()
+        _check(_lib.tn_costmodel_grad(self._h, _dev_ptr(d_x), _dev_ptr(d_t), n,
+                                      _dev_ptr(d_grad) if d_grad is not None else None, ctypes.byref(loss),
+                                      _stream_ptr(stream)), "tn_costmodel_grad")
+        return loss.value
+
+    def train(self, d_x, d_t, epochs=500, lr=1e-3, stream=None):
+        loss = ctypes.c_double()
+        _check(_lib.tn_costmodel_train(self._h, _dev_ptr(d_x), _dev_ptr(d_t), d_t.numel(), int(epochs), float(lr),
+                                       ctypes.byref(loss), _stream_ptr(stream)), "tn_costmodel_train")
+        return loss.value
+
+    def predict(self, d_x, d_y, stream=None):
+        _check(_lib.tn_costmodel_predict(self._h, _dev_ptr(d_x), _dev_ptr(d_y), d_y.numel(), _stream_ptr(stream)),
+               "tn_costmodel_predict")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tn_costmodel_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -38,7 +38,7 @@ extern "C" int tn_find_order(int n_tensors, const int32_t *ranks, const int32_t 
     std::vector<int32_t> open(open_labels, open_labels + n_open);
     tn_search_opts o = opts ? *opts : default_search_opts();
     SearchResult r;
-    int rc = search_order(labs, open, o, r);
+    int rc = search_ranked(labs, open, o, r);
     if (rc) return rc;
     if ((int)r.sliced.size() > max_sliced) return fail(TN_ERR_ARG, "tn_find_order: max_sliced too small");
     if (out_tree)

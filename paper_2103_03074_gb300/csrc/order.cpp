@@ -335,6 +335,10 @@ tn_search_opts default_search_opts() {
     o.log2_cap = -1;
     o.n_sliced = -1;
     o.threads = 0;
+    o.candidates = 0;
+    o.rank_batch_log2 = -1;
+    o.rank_form = TN_FP32;
+    o.cost_model = nullptr;
     return o;
 }
 
@@ -373,27 +377,35 @@ bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::v
     return true;
 }
 
-int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
-                 const tn_search_opts &opts_in, SearchResult &out) {
+int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                     const tn_search_opts &opts_in, int k, std::vector<SearchResult> &out) {
     tn_search_opts opts = opts_in;
     if (opts.trials <= 0) opts.trials = 256;
+    if (k < 1) k = 1;
+    out.clear();
     Problem p;
     if (!make_problem(labels, open, p)) return fail(TN_ERR_ARG, "open label held by no tensor");
     if (p.n == 0) return fail(TN_ERR_ARG, "empty network");
     if (p.n == 1) {
-        out.tree.clear();
-        out.sliced.clear();
-        out.log2_total = out.log2_slice = 0;
-        out.log2_width = (double)labels[0].size();
+        SearchResult r;
+        r.log2_width = (double)labels[0].size();
+        out.push_back(r);
         return TN_OK;
     }
     int threads = opts.threads > 0 ? opts.threads : (int)std::max(1u, std::thread::hardware_concurrency());
     threads = std::min(threads, opts.trials);
-    struct Best { double total = INFINITY, width = INFINITY; int trial = -1; Tree tree; SliceEval ev; };
-    std::vector<Best> best(threads);
+    struct Cand { double key_w, total, width; int trial; Tree tree; SliceEval ev; };
+    // order: smaller over-cap width, then smaller total cost, then lower trial
+    auto better = [](const Cand &a, const Cand &b) {
+        if (a.key_w != b.key_w) return a.key_w < b.key_w;
+        if (a.total != b.total) return a.total < b.total;
+        return a.trial < b.trial;
+    };
+    std::vector<std::vector<Cand>> keep(threads);
     std::atomic<int> next{0};
     auto worker = [&](int tid) {
         TreeSets ts;
+        auto &mine = keep[tid];
         for (;;) {
             int t = next.fetch_add(1);
             if (t >= opts.trials) break;
@@ -401,17 +413,14 @@ int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vec
             if (!tree_sets(p, tree, ts)) continue;
             SliceEval ev;
             slice_tree(p, ts, 2 * p.n - 1, p.n - 1, opts.log2_cap, opts.n_sliced, ev);
-            bool over = opts.log2_cap >= 0 && ev.log2_width > opts.log2_cap;
-            double key_w = over ? ev.log2_width : 0;
-            Best &b = best[tid];
-            double bw = (opts.log2_cap >= 0 && b.width > opts.log2_cap) ? b.width : 0;
-            if (b.trial < 0 || key_w < bw || (key_w == bw && (ev.log2_total < b.total ||
-                                                               (ev.log2_total == b.total && t < b.trial)))) {
-                b.total = ev.log2_total;
-                b.width = ev.log2_width;
-                b.trial = t;
-                b.tree = tree;
-                b.ev = ev;
+            const bool over = opts.log2_cap >= 0 && ev.log2_width > opts.log2_cap;
+            Cand c{over ? ev.log2_width : 0.0, ev.log2_total, ev.log2_width, t, std::move(tree), ev};
+            if ((int)mine.size() < k) {
+                mine.push_back(std::move(c));
+                std::sort(mine.begin(), mine.end(), better);
+            } else if (better(c, mine.back())) {
+                mine.back() = std::move(c);
+                std::sort(mine.begin(), mine.end(), better);
             }
         }
     };
@@ -419,22 +428,34 @@ int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vec
     for (int i = 1; i < threads; i++) pool.emplace_back(worker, i);
     worker(0);
     for (auto &th : pool) th.join();
-    int bi = -1;
-    for (int i = 0; i < threads; i++) {
-        if (best[i].trial < 0) continue;
-        auto over = [&](const Best &b) { return (opts.log2_cap >= 0 && b.width > opts.log2_cap) ? b.width : 0.0; };
-        if (bi < 0 || over(best[i]) < over(best[bi]) ||
-            (over(best[i]) == over(best[bi]) && (best[i].total < best[bi].total ||
-                                                 (best[i].total == best[bi].total && best[i].trial < best[bi].trial))))
-            bi = i;
+    std::vector<Cand> all;
+    for (auto &v : keep)
+        for (auto &c : v) all.push_back(std::move(c));
+    std::sort(all.begin(), all.end(), better);
+    for (auto &c : all) {
+        if ((int)out.size() >= k) break;
+        bool dup = false;
+        for (auto &o : out)
+            if (o.tree == c.tree) { dup = true; break; }
+        if (dup) continue;
+        SearchResult r;
+        r.tree = c.tree;
+        for (int id : c.ev.sliced) r.sliced.push_back(p.id2label[id]);
+        r.log2_total = c.ev.log2_total;
+        r.log2_width = c.ev.log2_width;
+        r.log2_slice = c.ev.log2_slice_cost;
+        out.push_back(std::move(r));
     }
-    if (bi < 0) return fail(TN_ERR_ARG, "order search produced no tree");
-    out.tree = best[bi].tree;
-    out.sliced.clear();
-    for (int id : best[bi].ev.sliced) out.sliced.push_back(p.id2label[id]);
-    out.log2_total = best[bi].ev.log2_total;
-    out.log2_width = best[bi].ev.log2_width;
-    out.log2_slice = best[bi].ev.log2_slice_cost;
+    if (out.empty()) return fail(TN_ERR_ARG, "order search produced no tree");
+    return TN_OK;
+}
+
+int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                 const tn_search_opts &opts, SearchResult &out) {
+    std::vector<SearchResult> top;
+    int rc = search_order_top(labels, open, opts, 1, top);
+    if (rc) return rc;
+    out = top[0];
     return TN_OK;
 }
 

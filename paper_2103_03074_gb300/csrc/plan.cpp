@@ -32,6 +32,7 @@
 
 #include <cuda_runtime.h>
 
+#include "costmodel.h"
 #include "kernels.h"
 #include "tc_gemm.h"
 #include "tn_internal.h"
@@ -680,6 +681,135 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 }  // namespace tn
 
+namespace tn {
+namespace {
+
+inline float l2f(double x) { return (float)(std::log2(x + 1.0) / 32.0); }
+
+// 16 step features (see tn_plan_op_features in tn.h)
+void op_features(const Op &op, tn_form form, float *f) {
+    for (int i = 0; i < kCostFeatures; i++) f[i] = 0.f;
+    double sh[4] = {0, 0, 0, 0}, units = 1, ksplit = 1;
+    int kind = 0;
+    switch (op.kind) {
+    case OP_SMALL: {
+        kind = 0;
+        const double nc = (1 << op.small.nN) < 8 ? 1.0 : (double)((1 << op.small.nN) / 8);
+        sh[0] = std::exp2(op.small.nH); sh[1] = (double)op.small.rows;
+        sh[2] = std::exp2(op.small.nN); sh[3] = std::exp2(op.small.nK);
+        units = (double)op.small.rows * nc;
+        break;
+    }
+    case OP_PERMUTE:
+        kind = 1;
+        sh[1] = (double)op.bp.plane_stride;
+        units = (double)op.bp.plane_stride;
+        break;
+    case OP_GEMM:
+        kind = op.gemm_variant == 1 ? 3 : 2;
+        sh[0] = (double)op.gemm.H; sh[1] = (double)op.gemm.M; sh[2] = (double)op.gemm.N; sh[3] = (double)op.gemm.K;
+        if (op.gemm_variant == 1) {
+            ksplit = op.tc.ksplit > 0 ? op.tc.ksplit : 1;
+            units = std::ceil(sh[1] / 128.0) * std::ceil(sh[2] / 64.0) * sh[0] * ksplit;
+        } else {
+            units = std::ceil(sh[1] / 64.0) * std::ceil(sh[2] / 64.0) * sh[0];
+        }
+        break;
+    case OP_SPLIT:
+        kind = 4;
+        sh[1] = (double)op.bp.plane_stride;
+        units = (double)op.bp.plane_stride;
+        break;
+    }
+    f[kind] = 1.f;
+    f[5] = l2f(op.macs);
+    f[6] = l2f(op.bytes);
+    for (int q = 0; q < 4; q++) f[7 + q] = l2f(sh[q]);
+    const bool tc = (op.kind == OP_GEMM && op.gemm_variant == 1) || op.kind == OP_SPLIT;
+    f[11] = (tc && form == TN_TF32X3) ? 1.f : 0.f;
+    f[12] = (tc && form == TN_BF16X3) ? 1.f : 0.f;
+    f[13] = l2f(units);
+    f[14] = (float)(std::log2(ksplit) / 8.0);
+    f[15] = 1.f;
+}
+
+}  // namespace
+
+int search_ranked(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                  const tn_search_opts &opts, SearchResult &out) {
+    if (!opts.cost_model || opts.candidates <= 1) return search_order(labels, open, opts, out);
+    std::vector<SearchResult> cands;
+    int rc = search_order_top(labels, open, opts, opts.candidates, cands);
+    if (rc) return rc;
+    std::vector<double> pred;
+    int best = 0;
+    rc = rank_candidates(labels, open, cands, opts, pred, best);
+    if (rc) return rc;
+    out = cands[best];
+    return TN_OK;
+}
+
+int rank_candidates(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                    const std::vector<SearchResult> &cands, const tn_search_opts &opts, std::vector<double> &pred_ms,
+                    int &best) {
+    best = 0;
+    pred_ms.assign(cands.size(), 0.0);
+    if (!opts.cost_model || cands.empty()) return TN_OK;
+    const tn_form form = (opts.rank_form >= TN_FP32 && opts.rank_form <= TN_FP16S) ? (tn_form)opts.rank_form : TN_FP32;
+    std::vector<float> X;
+    struct Span { size_t pro0, pro1, bat0, bat1; double blocks; };
+    std::vector<Span> spans;
+    for (const auto &c : cands) {
+        tn_plan P;
+        P.form = form;
+        P.n_tensors = (int)labels.size();
+        P.labels = labels;
+        P.open = open;
+        P.n_open = (int)open.size();
+        P.sliced = c.sliced;
+        P.n_sliced = (int)c.sliced.size();
+        P.tree = c.tree;
+        P.leaf_off.resize(labels.size());
+        int64_t off = 0;
+        for (size_t i = 0; i < labels.size(); i++) {
+            P.leaf_off[i] = off;
+            off += (int64_t)1 << labels[i].size();
+        }
+        int nb = P.n_sliced;
+        if (opts.rank_batch_log2 >= 0) nb = std::min(nb, (int)opts.rank_batch_log2);
+        if (compile(P, nb) < 0) return TN_ERR_ARG;
+        Span sp;
+        float f[kCostFeatures];
+        sp.pro0 = X.size() / kCostFeatures;
+        for (const auto &op : P.prologue) {
+            op_features(op, form, f);
+            X.insert(X.end(), f, f + kCostFeatures);
+        }
+        sp.pro1 = sp.bat0 = X.size() / kCostFeatures;
+        for (const auto &op : P.batch) {
+            op_features(op, form, f);
+            X.insert(X.end(), f, f + kCostFeatures);
+        }
+        sp.bat1 = X.size() / kCostFeatures;
+        sp.blocks = std::exp2((double)(P.n_sliced - nb));
+        spans.push_back(sp);
+    }
+    std::vector<float> Y;
+    int rc = cost_predict_host(opts.cost_model, X, Y);
+    if (rc) return rc;
+    for (size_t i = 0; i < cands.size(); i++) {
+        double t = 0;
+        for (size_t r = spans[i].pro0; r < spans[i].pro1; r++) t += std::exp2((double)Y[r]);
+        double tb = 0;
+        for (size_t r = spans[i].bat0; r < spans[i].bat1; r++) tb += std::exp2((double)Y[r]);
+        pred_ms[i] = t + spans[i].blocks * tb;
+        if (pred_ms[i] < pred_ms[best]) best = (int)i;
+    }
+    return TN_OK;
+}
+
+}  // namespace tn
+
 using namespace tn;
 
 extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *ranks, const int32_t *labels,
@@ -971,6 +1101,18 @@ extern "C" int tn_plan_profile(tn_plan_t P, int max_rows, double *rows, int rese
     return n;
 }
 
+extern "C" int tn_plan_op_features(tn_plan_t P, float *out, int max_ops) {
+    if (!P || (max_ops > 0 && !out)) return fail(TN_ERR_ARG, "NULL argument");
+    int n = 0;
+    for (auto *ops : {&P->prologue, &P->batch})
+        for (const auto &op : *ops) {
+            if (n >= max_ops) return n;
+            op_features(op, P->form, out + (size_t)n * kCostFeatures);
+            n++;
+        }
+    return n;
+}
+
 extern "C" int tn_plan_update_data(tn_plan_t P, const float *data, tn_stream_t stream) {
     if (!P || !data) return fail(TN_ERR_ARG, "NULL argument");
     cudaError_t e = cudaMemcpyAsync(P->d_leaves, data, P->leaf_bytes, cudaMemcpyHostToDevice,
@@ -1032,7 +1174,7 @@ extern "C" int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bit
     for (auto &t : net.tensors) labs.push_back(t.labels);
     tn_search_opts so = search ? *search : default_search_opts();
     SearchResult r;
-    rc = search_order(labs, net.open, so, r);
+    rc = search_ranked(labs, net.open, so, r);
     if (rc) return rc;
     std::vector<int32_t> ranks, flat, tree;
     std::vector<float> data;

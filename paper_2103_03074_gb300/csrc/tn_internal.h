@@ -47,6 +47,18 @@ int build_circuit_network(const tn_circuit *c, const uint8_t *fixed_bits, int n_
 // order.cpp: randomised greedy order + greedy slicing
 int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
                  const tn_search_opts &opts, SearchResult &out);
+// the k best distinct trials by the analytic key (over-cap width, total MACs)
+int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                     const tn_search_opts &opts, int k, std::vector<SearchResult> &out);
+
+// plan.cpp: order search with learned ranking when opts.cost_model is set
+int search_ranked(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                  const tn_search_opts &opts, SearchResult &out);
+// plan.cpp: learned ranking of candidate trees (index of the predicted
+// fastest; predicted ms per candidate in pred_ms)
+int rank_candidates(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                    const std::vector<SearchResult> &cands, const tn_search_opts &opts, std::vector<double> &pred_ms,
+                    int &best);
 
 // evaluate a given tree + slice set (log2 costs); returns false on a malformed tree
 bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,

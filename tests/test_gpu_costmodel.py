@@ -1,0 +1,175 @@
+"""Learned step-cost model on the GPU (tn_costmodel_*).
+
+* Gradient and prediction of the library's own CUDA kernels against the float64
+  numpy oracle (oracle/mlp.py, pinned by finite differences): relative L2
+  1e-4 (FP32 accumulation over a few hundred terms per gradient entry).
+* Training on per-step timings recorded by the step-timing recorder on a set
+  of plans, evaluated on held-out plans (measured time judges the error).
+* Ranking: among candidate trees of one workload, the tree the model predicts
+  fastest against the tree with the smallest analytic cost (complex MACs),
+  both timed; the model's pick must not be slower, and the gain is printed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tn_inputs import sycamore_circuit, random_bits, random_network
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_03074_gb300 as tn
+    return tn
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_gradient_and_forward_match_oracle(tn):
+    import torch
+    cm = tn.CostModel(seed=3)
+    p = cm.get_params()
+    rng = np.random.default_rng(4)
+    X = rng.uniform(0, 1, (1000, 16)).astype(np.float32)
+    X[:, 15] = 1
+    T = rng.standard_normal(1000).astype(np.float32)
+    dX, dT = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    dG = torch.zeros(cm.n_params, dtype=torch.float32, device="cuda")
+    loss = cm.grad(dX, dT, dG)
+    L, g = mlp.grad(p.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - L) < 1e-5 * max(1.0, L)
+    assert rel(dG.cpu().numpy(), g) < 1e-4
+    dY = torch.zeros(1000, dtype=torch.float32, device="cuda")
+    cm.predict(dX, dY)
+    torch.cuda.synchronize()
+    assert rel(dY.cpu().numpy(), mlp.forward(p, X)) < 1e-5
+    cm.close()
+
+
+def profile_plan(tn, plan, n_slices, reps=3):
+    """(features, log2 ms per launch) of every kernel step of a profiled plan."""
+    import torch
+    amp = torch.zeros(2 << plan.n_open, dtype=torch.float64, device="cuda")
+    plan.contract(0, n_slices, amp)
+    plan.profile(reset=True)
+    for _ in range(reps):
+        plan.contract(0, n_slices, amp)
+    rows = [r for r in plan.profile() if r["kind"] not in ("extract", "accumulate")]
+    feats = plan.op_features()
+    assert len(rows) == len(feats)
+    y = np.array([math.log2(max(r["ms"] / max(r["launches"], 1), 1e-4)) for r in rows], dtype=np.float32)
+    return feats, y
+
+
+def workload_plans(tn, seeds, forms=("fp32", "tf32x3", "bf16x3")):
+    out = []
+    for i, seed in enumerate(seeds):
+        rows, cols = [(3, 5), (4, 4), (4, 5), (3, 6), (4, 6)][i % 5]
+        circ = sycamore_circuit("rect", rows, cols, 8 + (seed % 5), seed)
+        n = circ.n_qubits
+        open_q = list(range(n - 6, n))
+        L, T, O = tn.circuit_network(circ, random_bits(n, seed), open_q)
+        ns = 2 + seed % 4
+        tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=16 + seed % 32, seed=seed, n_sliced=ns))
+        form = forms[i % len(forms)]
+        out.append((L, T, O, sliced, tree, form))
+    return out
+
+
+def collect(tn, plans):
+    X, Y, groups = [], [], []
+    for gi, (L, T, O, sliced, tree, form) in enumerate(plans):
+        plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(profile=1))
+        f, y = profile_plan(tn, plan, 1 << len(sliced))
+        plan.close()
+        X.append(f)
+        Y.append(y)
+        groups += [gi] * len(y)
+    return np.concatenate(X), np.concatenate(Y), np.array(groups)
+
+
+def test_training_predicts_held_out_plans(tn):
+    import torch
+    plans = workload_plans(tn, list(range(1, 31)))
+    X, Y, g = collect(tn, plans)
+    train = g % 5 != 0
+    cm = tn.CostModel(seed=7)
+    dX = torch.from_numpy(X[train]).cuda()
+    dT = torch.from_numpy(Y[train]).cuda()
+    l0 = cm.grad(dX, dT)
+    l1 = cm.train(dX, dT, epochs=3000, lr=3e-3)
+    assert l1 < 0.2 * l0
+    dXt = torch.from_numpy(X[~train]).cuda()
+    dYt = torch.zeros(int((~train).sum()), dtype=torch.float32, device="cuda")
+    cm.predict(dXt, dYt)
+    torch.cuda.synchronize()
+    err = np.abs(dYt.cpu().numpy() - Y[~train])
+    base = np.abs(Y[train].mean() - Y[~train])
+    print(f"cost model: train loss {l0:.3f} -> {l1:.3f}; held-out mean |log2 err| {err.mean():.3f} "
+          f"(predicting the mean: {base.mean():.3f}), {int(train.sum())} train / {int((~train).sum())} test steps")
+    assert err.mean() < 0.5 * base.mean()
+    assert err.mean() < 1.0
+    cm.close()
+
+
+def timed(tn, plan, n_slices, reps=5):
+    import torch
+    amp = torch.zeros(2 << plan.n_open, dtype=torch.float64, device="cuda")
+    plan.contract(0, n_slices, amp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.contract(0, n_slices, amp)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def test_learned_ranking_versus_analytic_cost(tn):
+    import torch
+    # train on plans of other circuits
+    X, Y, _ = collect(tn, workload_plans(tn, list(range(101, 131)), forms=("tf32x3",)))
+    cm = tn.CostModel(seed=11)
+    cm.train(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), epochs=3000, lr=3e-3)
+    # candidates for a held-out workload: best trees of several search seeds
+    circ = sycamore_circuit("rect", 5, 5, 12, 4242)
+    L, T, O = tn.circuit_network(circ, random_bits(25, 7), list(range(17, 25)))
+    cands = []
+    for seed in range(12):
+        tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=24, seed=1000 + seed, n_sliced=6))
+        if all(tree != c[0] for c in cands):
+            cands.append((tree, sliced, st["log2_total"]))
+    meas, pred = [], []
+    for tree, sliced, _ in cands:
+        plan = tn.Plan(L, T, O, sliced, tree, form="tf32x3", opts=tn.plan_opts(use_graph=1))
+        meas.append(timed(tn, plan, 64))
+        f = plan.op_features()
+        plan.close()
+        d = torch.zeros(len(f), dtype=torch.float32, device="cuda")
+        cm.predict(torch.from_numpy(f).cuda(), d)
+        torch.cuda.synchronize()
+        pred.append(float(np.sum(2.0 ** d.cpu().numpy())))
+    meas, pred = np.array(meas), np.array(pred)
+    analytic = np.array([c[2] for c in cands])
+    i_a, i_m = int(np.argmin(analytic)), int(np.argmin(pred))
+    print(f"ranking over {len(cands)} trees: analytic pick {meas[i_a]:.3f} ms, model pick {meas[i_m]:.3f} ms, "
+          f"best {meas.min():.3f} ms; gain {meas[i_a] / meas[i_m]:.2f}x; "
+          f"median |log2(pred/meas)| {np.median(np.abs(np.log2(pred / meas))):.2f}")
+    assert meas[i_m] <= 1.05 * meas[i_a]
+    # the library-side ranking inside the order search uses the same model
+    tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=24, seed=1000, n_sliced=6, candidates=8,
+                                                          rank_form="tf32x3", cost_model=cm))
+    assert len(tree) == len(L) - 1 and len(sliced) == 6
+    cm.close()
