@@ -247,7 +247,7 @@ def run_native(args):
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
     tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
     n_slices = 1 << len(sliced)
-    forms = [args.form] if args.form != "all" else ["fp32", "tf32x3", "bf16x3"]
+    forms = [args.form] if args.form != "all" else ["fp32", "tf32x3", "bf16x3", "fp16s"]
     golden = load_golden_amplitudes() if rank == 0 and instance_seed_offset(rank) == 0 else None
     stream = torch.cuda.Stream()
     flush = l2_flush_buffer(torch)
@@ -314,7 +314,7 @@ def run_native(args):
             # split form: tensor-core flops the method issues per complex MAC
             # (4 real products x 3 split products x 2 flops); TF32 peak = half
             # of the measured BF16 peak (nominal dense ratio 1.1 : 2.25)
-            per_mac = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16s": 8.0}[form]
+            per_mac = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16s": 8.0}[form]  # fp16s: 4 real products
             peak = pk["bf16_tflops"] * ({"bf16x3": 1.0, "tf32x3": 0.5, "fp16s": 1.0}[form])
             achieved = per_mac * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

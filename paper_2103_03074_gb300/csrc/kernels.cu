@@ -5,6 +5,7 @@
 // bit string: each label owns one bit position.  Index maps are therefore bit
 // scatters and gathers, computed in registers.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -129,6 +130,11 @@ __device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, flo
         P[d + a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
         P[d + 2 * a.plane_stride] = __bfloat16_as_ushort(ih);
         P[d + 3 * a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
+    } else if (a.mode == 3) {
+        const int e = fp16s_exponent(__uint_as_float(*a.scale));
+        __half *P = reinterpret_cast<__half *>(a.out);
+        P[d] = __float2half_rn(ldexpf(v.x, -e));
+        P[d + a.plane_stride] = __float2half_rn(ldexpf(v.y, -e));
     } else {
         uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
         const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
@@ -178,6 +184,19 @@ __global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) 
             for (int e = threadIdx.x; e < tile; e += blockDim.x) store_elem(a, d_rest[q] | dst_off[e], buf[q][e]);
         __syncthreads();
     }
+}
+
+// ----------------------------------------------------------------- max |x|
+__global__ void __launch_bounds__(kThreads) maxabs_kernel(const MaxAbsArgs a) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = a.in[i];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    // non-negative floats order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(a.slot, __float_as_uint(m));
 }
 
 // --------------------------------------------------------------- FP32 GEMM
@@ -367,6 +386,13 @@ cudaError_t launch_extract(const ExtractEntry *d_entries, int n_entries, int max
     if (n_entries == 0) return cudaSuccess;
     dim3 grid((unsigned)((max_out + kThreads - 1) / kThreads), (unsigned)n_entries);
     extract_kernel<<<grid, kThreads, 0, s>>>(d_entries, n_entries, slice_base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs(const MaxAbsArgs &a, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.slot, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    maxabs_kernel<<<grid_for(a.n), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Kernel argument blocks shared by the host plan compiler and the CUDA
 // kernels.  Plain structs passed by value as kernel parameters.
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -37,7 +38,10 @@ struct SmallArgs {
 //   out index d (r bits) <- in[sum_p bit_p(d) << src_pos[p]]
 // mode 0: complex64 out[d];
 // mode 1/2: four planes (re_hi, re_lo, im_hi, im_lo) of bf16 (1) or tf32 held
-//           in 32 bits (2) at d + q * plane_stride, q = 0..3.
+//           in 32 bits (2) at d + q * plane_stride, q = 0..3;
+// mode 3:   two fp16 planes (re, im) of x * 2^-e, e = ilogb(max|x|) - 13 from
+//           the max-abs slot `scale` (a float stored as its bits), so the
+//           largest scaled value lies in [2^13, 2^14).
 // The tile holds the bits at the source's and the destination's lowest
 // positions, so reads and writes are both coalesced.
 constexpr int kTileMaxBits = 10;
@@ -54,7 +58,25 @@ struct BitPermArgs {
     int n_rest;                      // remaining bits (grid-strided)
     int rest_dst[kMaxRank];
     int rest_src[kMaxRank];
+    const unsigned *scale;           // mode 3: max-abs slot of the operand
 };
+
+// max over |re|, |im| of n complex values into *slot (float bits; the
+// launcher zeroes the slot first)
+struct MaxAbsArgs {
+    const float2 *in;
+    int64_t n;
+    unsigned *slot;
+};
+
+// power-of-two exponent e of the FP16S scale for a max-abs value: the largest
+// scaled magnitude max * 2^-e lies in [2^13, 2^14)
+__host__ __device__ inline int fp16s_exponent(float maxabs) {
+    if (!(maxabs > 0.f)) return 0;
+    int ex;
+    frexpf(maxabs, &ex);  // maxabs in [2^(ex-1), 2^ex)
+    return ex - 14;
+}
 
 // Strided batched complex GEMM, all strides in complex elements:
 // C[h sCh + m sCm + n sCn] = sum_k A[h sAh + m sAm + k sAk] B[h sBh + k sBk + n sBn]
@@ -91,6 +113,7 @@ struct AccumArgs {
 // launchers (kernels.cu); return cudaSuccess or the launch error
 cudaError_t launch_small(const SmallArgs &a, cudaStream_t s);
 cudaError_t launch_bitperm(const BitPermArgs &a, cudaStream_t s);
+cudaError_t launch_maxabs(const MaxAbsArgs &a, cudaStream_t s);
 cudaError_t launch_gemm_f32(const GemmArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractEntry *d_entries, int n_entries, int max_out, uint64_t slice_base,
                            cudaStream_t s);

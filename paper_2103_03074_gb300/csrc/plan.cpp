@@ -42,7 +42,7 @@ namespace tn {
 namespace {
 
 // values double as the step-timing recorder's kind codes (3 = extract, 4 = sum)
-enum OpKind { OP_SMALL = 0, OP_PERMUTE = 1, OP_GEMM = 2, OP_SPLIT = 5 };
+enum OpKind { OP_SMALL = 0, OP_PERMUTE = 1, OP_GEMM = 2, OP_SPLIT = 5, OP_MAXABS = 6 };
 
 struct Operand {  // where an op reads or writes: static leaf or arena buffer
     int buf = -1;        // arena buffer id, or -1
@@ -54,7 +54,10 @@ struct Op {
     int step = -1;
     bool dep = false;
     Operand in0, in1, out;
+    Operand aux;    // FP16S: the pair of max-abs slots (read by splits and the GEMM)
+    int aux_idx = 0;  // slot index used by a max-abs op or a scaled split
     SmallArgs small;
+    MaxAbsArgs mx;
     BitPermArgs bp;  // permute (mode 0) or fused permute + hi/lo split (OP_SPLIT)
     GemmArgs gemm;
     TcGemm tc;  // tensor-core GEMM (gemm_variant 1), resolved after arena allocation
@@ -471,10 +474,32 @@ int64_t compile(tn_plan &P, int nb) {
         g.sCh = (int64_t)1 << (nM + nN);
         op.macs = macs;
         if (use_tc) {
-            // split both operands into hi/lo planes [h][q][row][k] (fused with
-            // their permutation); the tensor-core GEMM reads the planes by TMA
-            const int es = tc_plane_bytes(P.form);
-            const int mode = es == 2 ? 1 : 2;
+            // split both operands into hi/lo planes [q][h][row][k] (fused with
+            // their permutation); the tensor-core GEMM reads the planes by TMA.
+            // FP16S: a max-abs pass per operand first picks its power-of-two
+            // scale, and the split writes scaled fp16 planes {re, im}
+            const int es = tc_plane_bytes(P.form), np = tc_plane_count(P.form);
+            const bool scaled = P.form == TN_FP16S;
+            const int mode = scaled ? 3 : (es == 2 ? 1 : 2);
+            Operand slots;
+            if (scaled) {
+                slots.buf = new_buf(1);  // two uint32 slots
+                int idx = 0;
+                for (const NodeRec *src : {&A, &B}) {
+                    Op mo;
+                    mo.kind = OP_MAXABS;
+                    mo.step = t;
+                    mo.dep = nc.dep;
+                    std::memset(&mo.mx, 0, sizeof mo.mx);
+                    mo.mx.n = (int64_t)1 << src->lay.size();
+                    mo.in0 = src->where;
+                    mo.out = slots;
+                    mo.aux_idx = idx++;
+                    mo.bytes = 8.0 * (double)mo.mx.n;
+                    ops.push_back(mo);
+                }
+            }
+            int split_idx = 0;
             auto emit_split = [&](const NodeRec &src, const std::vector<int32_t> &rows) {
                 std::vector<int32_t> dl = hord;
                 dl.insert(dl.end(), rows.begin(), rows.end());
@@ -485,11 +510,16 @@ int64_t compile(tn_plan &P, int nb) {
                 sp.dep = nc.dep;
                 sp.bp = make_bitperm(src.lay, dl, mode);
                 sp.in0 = src.where;
+                if (scaled) {
+                    sp.aux = slots;
+                    sp.aux_idx = split_idx;
+                }
+                split_idx++;
                 const int64_t elems = (int64_t)1 << dl.size();
                 Operand dst;
-                dst.buf = new_buf((4 * elems * es + 7) / 8);
+                dst.buf = new_buf((np * elems * es + 7) / 8);
                 sp.out = dst;
-                sp.bytes = 8.0 * (double)elems + 4.0 * es * (double)elems;
+                sp.bytes = 8.0 * (double)elems + (double)np * es * (double)elems;
                 ops.push_back(sp);
                 return dst;
             };
@@ -497,7 +527,8 @@ int64_t compile(tn_plan &P, int nb) {
             op.in1 = emit_split(B, nord);
             op.gemm_variant = 1;
             op.tc.ksplit = tc_choose_ksplit(g, P.form);
-            op.bytes = (double)(4 * es) * (double)(g.H * (g.M + g.N) * g.K) + 8.0 * (double)(g.H * g.M * g.N);
+            if (scaled) op.aux = slots;
+            op.bytes = (double)(np * es) * (double)(g.H * (g.M + g.N) * g.K) + 8.0 * (double)(g.H * g.M * g.N);
         } else {
             g.sAh = (int64_t)1 << GA.lowpos[0];
             g.sAm = (int64_t)1 << GA.lowpos[1];
@@ -559,6 +590,7 @@ int64_t compile(tn_plan &P, int nb) {
         touch(op.in0, i);
         touch(op.in1, i);
         touch(op.out, i);
+        touch(op.aux, i);
     }
     for (int i = 0; i < (int)P.batch.size(); i++) {
         Op &op = P.batch[i];
@@ -566,6 +598,7 @@ int64_t compile(tn_plan &P, int nb) {
         touch(op.in0, time);
         touch(op.in1, time);
         touch(op.out, time);
+        touch(op.aux, time);
         if (op.out.buf >= 0) buf_dep[op.out.buf] = 1;
     }
     touch(P.root, T_acc);
@@ -630,6 +663,11 @@ void resolve_all(tn_plan &P) {
         case OP_SPLIT:
             op.bp.in = resolve(P, op.in0);
             op.bp.out = resolve(P, op.out);
+            if (op.aux.buf >= 0) op.bp.scale = reinterpret_cast<const unsigned *>(resolve(P, op.aux)) + op.aux_idx;
+            break;
+        case OP_MAXABS:
+            op.mx.in = resolve(P, op.in0);
+            op.mx.slot = reinterpret_cast<unsigned *>(resolve(P, op.out)) + op.aux_idx;
             break;
         case OP_GEMM:
             if (op.gemm_variant == 1) {
@@ -641,6 +679,7 @@ void resolve_all(tn_plan &P) {
                 if (op.tc.ksplit < 1) op.tc.ksplit = 1;
                 op.tc.chunk_bytes = P.opts.tc_chunk_bytes;
                 op.tc.flush_bytes = P.opts.tc_flush_bytes;
+                op.tc.scales = op.aux.buf >= 0 ? reinterpret_cast<const unsigned *>(resolve(P, op.aux)) : nullptr;
             } else {
                 op.gemm.A = resolve(P, op.in0);
                 op.gemm.B = resolve(P, op.in1);
@@ -669,6 +708,7 @@ cudaError_t run_op(const tn_plan &P, const Op &op, cudaStream_t s) {
         if (op.gemm_variant == 1) return launch_gemm_tc(op.tc, s);
         return launch_gemm_f32(op.gemm, s);
     case OP_SPLIT: return launch_bitperm(op.bp, s);
+    case OP_MAXABS: return launch_maxabs(op.mx, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -720,12 +760,17 @@ void op_features(const Op &op, tn_form form, float *f) {
         sh[1] = (double)op.bp.plane_stride;
         units = (double)op.bp.plane_stride;
         break;
+    case OP_MAXABS:  // a read-only bandwidth pass, closest to a permute
+        kind = 1;
+        sh[1] = (double)op.mx.n;
+        units = (double)op.mx.n;
+        break;
     }
     f[kind] = 1.f;
     f[5] = l2f(op.macs);
     f[6] = l2f(op.bytes);
     for (int q = 0; q < 4; q++) f[7 + q] = l2f(sh[q]);
-    const bool tc = (op.kind == OP_GEMM && op.gemm_variant == 1) || op.kind == OP_SPLIT;
+    const bool tc = (op.kind == OP_GEMM && op.gemm_variant == 1) || op.kind == OP_SPLIT || op.kind == OP_MAXABS;
     f[11] = (tc && form == TN_TF32X3) ? 1.f : 0.f;
     f[12] = (tc && form == TN_BF16X3) ? 1.f : 0.f;
     f[13] = l2f(units);
@@ -939,6 +984,8 @@ tn_plan::ProfRow prof_row(int phase, int idx, const Op &op) {
         r.shape[2] = (double)(1 << op.small.nN); r.shape[3] = (double)(1 << op.small.nK);
     } else if (op.kind == OP_PERMUTE) {
         r.shape[1] = (double)op.bp.plane_stride;
+    } else if (op.kind == OP_MAXABS) {
+        r.shape[1] = (double)op.mx.n;
     }
     return r;
 }

@@ -54,15 +54,19 @@ constexpr int kThreads = 384;  // 12 warps
 constexpr int kFlushWarp0 = 4, kFlushWarps = 8;
 constexpr int kTmemCols = 512;  // 2 sets x {re, im, re corr, im corr} x 64
 
-// Shared-memory ring for a K chunk of CB bytes per plane row: 4 planes of A
-// (128 rows) and of B (64 rows) per stage; 64-byte chunks use the 64-byte
-// swizzle and 4 stages, 128-byte chunks the 128-byte swizzle and 2 stages.
-template <int CB>
+// operand forms of the kernel template
+constexpr int kBF16 = 0, kTF32 = 1, kFP16 = 2;
+
+// Shared-memory ring for a K chunk of CB bytes per plane row: NP planes of A
+// (128 rows) and of B (64 rows) per stage (4 for the hi/lo split forms, 2 for
+// FP16S); as many stages as fit in 192 KB, at most 6.  64-byte chunks use the
+// 64-byte swizzle, 128-byte chunks the 128-byte swizzle.
+template <int CB, int NP = 4>
 struct Ring {
     static constexpr int kAPlane = TM * CB;
     static constexpr int kBPlane = TN * CB;
-    static constexpr int kStageBytes = 4 * kAPlane + 4 * kBPlane;
-    static constexpr int kStages = CB == 64 ? 4 : 2;
+    static constexpr int kStageBytes = NP * kAPlane + NP * kBPlane;
+    static constexpr int kStages = (196608 / kStageBytes) < 6 ? (196608 / kStageBytes) : 6;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
     static constexpr uint32_t kSBO = 8 * CB;                // 8 rows of one swizzle atom
     static constexpr uint64_t kLayout = CB == 64 ? 4 : 2;  // descriptor swizzle code
@@ -90,9 +94,9 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, int M, int
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-template <bool kTF32>
+template <int KIND>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    if (kTF32) {
+    if (KIND == kTF32) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
@@ -164,14 +168,16 @@ struct GemmTcParams {
     int k_chunk;       // K values per chunk
     int ksplit;        // K partitions (blockIdx.z = h * ksplit + part); > 1: atomic adds
     int flush_chunks;  // chunks per accumulator read-out
+    const unsigned *scales;  // FP16S: max-abs slots of A and B (float bits)
 };
 
-template <bool kTF32, int CB>
+template <int KIND, int CB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
-    constexpr int kAPlane = Ring<CB>::kAPlane, kBPlane = Ring<CB>::kBPlane;
-    constexpr int kStageBytes = Ring<CB>::kStageBytes, kStages = Ring<CB>::kStages;
+    constexpr int NP = KIND == kFP16 ? 2 : 4;
+    constexpr int kAPlane = Ring<CB, NP>::kAPlane, kBPlane = Ring<CB, NP>::kBPlane;
+    constexpr int kStageBytes = Ring<CB, NP>::kStageBytes, kStages = Ring<CB, NP>::kStages;
     const int kFlushChunks = p.flush_chunks;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
@@ -221,13 +227,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(fb, kStageBytes);
                 const int kc = (c_begin + c) * p.k_chunk;
                 tma_load_4d(smem_u32(st), &mapA, kc, (int)m0, h, 0, fb);
-                tma_load_4d(smem_u32(st + 4 * kAPlane), &mapB, kc, (int)n0, h, 0, fb);
+                tma_load_4d(smem_u32(st + NP * kAPlane), &mapB, kc, (int)n0, h, 0, fb);
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t fmt = kTF32 ? 2u : 1u;  // tf32 : bf16
+            constexpr uint32_t fmt = KIND == kTF32 ? 2u : (KIND == kBF16 ? 1u : 0u);  // tf32 / bf16 / f16
             constexpr uint32_t IP = make_idesc(fmt, TM, TN, false), IN = make_idesc(fmt, TM, TN, true);
             for (int c = 0; c < n_chunks; c++) {
                 const int s = c % kStages, use = c / kStages;
@@ -238,8 +244,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!mbar_wait(smem_u32(&full[s]), use & 1)) break;
                 if (first && tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) break;
                 fence_after();
-                const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + 4 * kAPlane;
+                const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + NP * kAPlane;
                 const uint32_t d_re = tmem + t * 256, d_im = d_re + 64, c_re = d_re + 128, c_im = d_re + 192;
+                if (KIND == kFP16) {
+                    // one scaled fp16 piece per value: planes {re, im}
+#pragma unroll
+                    for (int ks = 0; ks < CB / 32; ks++) {
+                        const uint32_t ko = ks * 32;
+                        const uint64_t ar = make_desc<CB>(a0 + ko), ai = make_desc<CB>(a0 + kAPlane + ko);
+                        const uint64_t br = make_desc<CB>(b0 + ko), bi = make_desc<CB>(b0 + kBPlane + ko);
+                        const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+                        mma<KIND>(d_re, ar, br, IP, acc);
+                        mma<KIND>(d_re, ai, bi, IN, 1u);
+                        mma<KIND>(d_im, ar, bi, IP, acc);
+                        mma<KIND>(d_im, ai, br, IP, 1u);
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                    if (last) mma_commit(smem_u32(&tfull[t]));
+                    continue;
+                }
 #pragma unroll
                 for (int ks = 0; ks < CB / 32; ks++) {  // MMA K steps of 32 bytes
                     const uint32_t ko = ks * 32;
@@ -250,18 +273,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t bih = make_desc<CB>(b0 + 2 * kBPlane + ko);
                     const uint64_t bil = make_desc<CB>(b0 + 3 * kBPlane + ko);
                     const uint32_t acc = (first && ks == 0) ? 0u : 1u;  // each flush group starts fresh sums
-                    mma<kTF32>(d_re, arh, brh, IP, acc);
-                    mma<kTF32>(d_re, aih, bih, IN, 1u);
-                    mma<kTF32>(c_re, arh, brl, IP, acc);
-                    mma<kTF32>(c_re, arl, brh, IP, 1u);
-                    mma<kTF32>(c_re, aih, bil, IN, 1u);
-                    mma<kTF32>(c_re, ail, bih, IN, 1u);
-                    mma<kTF32>(d_im, arh, bih, IP, acc);
-                    mma<kTF32>(d_im, aih, brh, IP, 1u);
-                    mma<kTF32>(c_im, arh, bil, IP, acc);
-                    mma<kTF32>(c_im, arl, bih, IP, 1u);
-                    mma<kTF32>(c_im, aih, brl, IP, 1u);
-                    mma<kTF32>(c_im, ail, brh, IP, 1u);
+                    mma<KIND>(d_re, arh, brh, IP, acc);
+                    mma<KIND>(d_re, aih, bih, IN, 1u);
+                    mma<KIND>(c_re, arh, brl, IP, acc);
+                    mma<KIND>(c_re, arl, brh, IP, 1u);
+                    mma<KIND>(c_re, aih, bil, IN, 1u);
+                    mma<KIND>(c_re, ail, bih, IN, 1u);
+                    mma<KIND>(d_im, arh, bih, IP, acc);
+                    mma<KIND>(d_im, aih, brh, IP, 1u);
+                    mma<KIND>(c_im, arh, bil, IP, acc);
+                    mma<KIND>(c_im, arl, bih, IP, 1u);
+                    mma<KIND>(c_im, aih, brl, IP, 1u);
+                    mma<KIND>(c_im, ail, brh, IP, 1u);
                 }
                 mma_commit(smem_u32(&empty[s]));
                 if (last) mma_commit(smem_u32(&tfull[t]));
@@ -285,20 +308,36 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int q = 0; q < 2; q++) {
                 uint32_t r0[16], r1[16], r2[16], r3[16];
-                tmem_ld16(base + q * 16, r0);        // re main
-                tmem_ld16(base + 64 + q * 16, r1);   // im main
-                tmem_ld16(base + 128 + q * 16, r2);  // re correction
-                tmem_ld16(base + 192 + q * 16, r3);  // im correction
+                tmem_ld16(base + q * 16, r0);       // re main
+                tmem_ld16(base + 64 + q * 16, r1);  // im main
+                if (KIND != kFP16) {
+                    tmem_ld16(base + 128 + q * 16, r2);  // re correction
+                    tmem_ld16(base + 192 + q * 16, r3);  // im correction
+                }
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    acc_re[q * 16 + j] += __uint_as_float(r0[j]) + __uint_as_float(r2[j]);
-                    acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r3[j]);
+                    if (KIND != kFP16) {
+                        acc_re[q * 16 + j] += __uint_as_float(r0[j]) + __uint_as_float(r2[j]);
+                        acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r3[j]);
+                    } else {
+                        acc_re[q * 16 + j] += __uint_as_float(r0[j]);
+                        acc_im[q * 16 + j] += __uint_as_float(r1[j]);
+                    }
                 }
             }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
+        }
+        if (KIND == kFP16) {
+            // undo the operands' power-of-two scales (exact)
+            const int e = fp16s_exponent(__uint_as_float(p.scales[0])) + fp16s_exponent(__uint_as_float(p.scales[1]));
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                acc_re[j] = ldexpf(acc_re[j], e);
+                acc_im[j] = ldexpf(acc_im[j], e);
+            }
         }
         const int64_t m = m0 + lg * 32 + lane;
         float2 *Ch = p.C + (int64_t)h * p.sCh;
@@ -366,18 +405,18 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// planes [4][H][rows][K] of element size es (plane-major, as the split pass
-// writes them); box = cb bytes of K x box_rows x 1 batch x 4 planes, which
+// planes [np][H][rows][K] of element size es (plane-major, as the split pass
+// writes them); box = cb bytes of K x box_rows x 1 batch x np planes, which
 // lands in shared memory as [plane][row][cb bytes], cb-byte swizzled
 bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int64_t K, int es, int box_rows,
-                   int cb) {
+                   int cb, int np, CUtensorMapDataType dtype) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)H, 4};
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)H, (cuuint64_t)np};
     cuuint64_t strides[3] = {(cuuint64_t)(K * es), (cuuint64_t)(rows * K * es), (cuuint64_t)(H * rows * K * es)};
-    cuuint32_t box[4] = {(cuuint32_t)(cb / es), (cuuint32_t)box_rows, 1, 4};
+    cuuint32_t box[4] = {(cuuint32_t)(cb / es), (cuuint32_t)box_rows, 1, (cuuint32_t)np};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = fn(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, planes, dims,
+    CUresult r = fn(map, dtype, 4, planes, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -387,10 +426,12 @@ bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int6
 }  // namespace
 
 bool tc_form_available(tn_form form) {
-    return (form == TN_BF16X3 || form == TN_TF32X3) && encode_fn() != nullptr;
+    return (form == TN_BF16X3 || form == TN_TF32X3 || form == TN_FP16S) && encode_fn() != nullptr;
 }
 
 int tc_plane_bytes(tn_form form) { return form == TN_TF32X3 ? 4 : 2; }
+
+int tc_plane_count(tn_form form) { return form == TN_FP16S ? 2 : 4; }
 
 bool tc_gemm_suitable(const GemmArgs &a) {
     return a.M >= 64 && a.N >= 32 && a.K >= 32 && a.H <= 65535 && (a.M + TM - 1) / TM <= 65535 &&
@@ -411,29 +452,34 @@ bool tc_prepare(TcGemm &g) {
     if (g.chunk_bytes != 64 && g.chunk_bytes != 128) g.chunk_bytes = kDefaultChunkBytes;
     if (g.flush_bytes < g.chunk_bytes) g.flush_bytes = kDefaultFlushBytes < g.chunk_bytes ? g.chunk_bytes : kDefaultFlushBytes;
     if (g.a.K * es < g.chunk_bytes) g.chunk_bytes = 64;
-    const int cb = g.chunk_bytes;
-    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM, cb)) return false;
-    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN, cb)) return false;
+    const int cb = g.chunk_bytes, np = tc_plane_count(g.form);
+    const CUtensorMapDataType dt = g.form == TN_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : g.form == TN_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM, cb, np, dt))
+        return false;
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN, cb, np, dt))
+        return false;
     return true;
 }
 
-template <bool kTF32, int CB>
+template <int KIND, int CB>
 cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
+    constexpr int NP = KIND == kFP16 ? 2 : 4;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kTF32, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Ring<CB>::kSmem);
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<KIND, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Ring<CB, NP>::kSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
     const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
-    tc_gemm_kernel<kTF32, CB><<<grid, kThreads, Ring<CB>::kSmem, s>>>(mA, mB, p);
+    tc_gemm_kernel<KIND, CB><<<grid, kThreads, Ring<CB, NP>::kSmem, s>>>(mA, mB, p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
-    const bool tf = g.form == TN_TF32X3;
     GemmTcParams p;
     p.C = g.a.C;
     p.H = g.a.H;
@@ -447,6 +493,8 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.ksplit = g.ksplit > 0 ? g.ksplit : 1;
     p.flush_chunks = g.flush_bytes / g.chunk_bytes;
     if (p.flush_chunks < 1) p.flush_chunks = 1;
+    p.scales = g.scales;
+    if (g.form == TN_FP16S && !g.scales) return cudaErrorInvalidValue;
     const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
     if (gm > 65535 || g.a.H * p.ksplit > 65535) return cudaErrorInvalidConfiguration;
     if (p.ksplit > 1) {
@@ -455,9 +503,11 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)gn, (unsigned)gm, (unsigned)(g.a.H * p.ksplit));
-    if (g.chunk_bytes == 64)
-        return tf ? launch_variant<true, 64>(g, p, grid, s) : launch_variant<false, 64>(g, p, grid, s);
-    return tf ? launch_variant<true, 128>(g, p, grid, s) : launch_variant<false, 128>(g, p, grid, s);
+    if (g.form == TN_TF32X3)
+        return g.chunk_bytes == 64 ? launch_variant<kTF32, 64>(g, p, grid, s) : launch_variant<kTF32, 128>(g, p, grid, s);
+    if (g.form == TN_BF16X3)
+        return g.chunk_bytes == 64 ? launch_variant<kBF16, 64>(g, p, grid, s) : launch_variant<kBF16, 128>(g, p, grid, s);
+    return g.chunk_bytes == 64 ? launch_variant<kFP16, 64>(g, p, grid, s) : launch_variant<kFP16, 128>(g, p, grid, s);
 }
 
 int tc_read_error(cudaStream_t s) {

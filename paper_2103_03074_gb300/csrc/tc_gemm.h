@@ -17,6 +17,7 @@ struct TcGemm {
     int ksplit;       // K partitions over CTAs (1: none)
     int chunk_bytes;  // K chunk per TMA stage and plane row: 64 or 128 (0: default)
     int flush_bytes;  // bytes of K between accumulator read-outs (multiple of chunk_bytes; 0: default)
+    const unsigned *scales;  // FP16S: device max-abs slots of A and B (float bits)
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
 };
@@ -25,8 +26,12 @@ struct TcGemm {
 // point for TMA descriptors is reachable)
 bool tc_form_available(tn_form form);
 
-// bytes per plane element of a split form (2: bf16, 4: tf32)
+// bytes per plane element of a split form (2: bf16 / fp16, 4: tf32)
 int tc_plane_bytes(tn_form form);
+
+// planes per operand: 4 for the hi/lo split forms (re_hi, re_lo, im_hi,
+// im_lo), 2 for FP16S (re, im)
+int tc_plane_count(tn_form form);
 
 // Shapes the tensor-core kernel takes (smaller GEMMs stay on the FP32
 // CUDA-core kernel).

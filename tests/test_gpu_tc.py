@@ -16,7 +16,10 @@ label shared by both operands.  Each result is checked twice:
     when read out every 128 bytes).  A kernel that dropped or misplaced any
     product term would be off by ~5e-4 (tf32 lo/hi ratio) or ~4e-3 (bf16).
 FP32 form: the CUDA-core kernel against the exact product, 2e-6 (FP32 sums of
-up to 2048 products).
+up to 2048 products).  FP16S form (one fp16 piece per value after a per-operand
+power-of-two scale): 2e-3 against the exact product (the bound stated for the
+scaled-FP16 form; fp16 keeps 11 bits, ~3.5e-4 per GEMM), 1e-6 against its
+emulation.
 """
 import numpy as np
 import pytest
@@ -64,6 +67,20 @@ def emulate_split_4m(a, b, rnd):
     return (rmm(ar, br) - rmm(ai, bi)) + 1j * (rmm(ar, bi) + rmm(ai, br))
 
 
+def emulate_fp16s_4m(a, b):
+    """Scaled FP16 form: each operand scaled by 2^-e (e from its max |re|,|im|
+    so the largest scaled value lies in [2^13, 2^14)), rounded to fp16, four
+    real products accumulated exactly, result scaled back by 2^(eA + eB)."""
+    def scaled(x):
+        mx = max(np.abs(x.real).max(), np.abs(x.imag).max())
+        e = np.frexp(np.float32(mx))[1] - 14
+        xs = (x.astype(np.complex64) * np.float32(2.0 ** -e))
+        return (xs.real.astype(np.float16).astype(np.float64), xs.imag.astype(np.float16).astype(np.float64), e)
+    ar, ai, ea = scaled(a)
+    br, bi, eb = scaled(b)
+    return ((ar @ br - ai @ bi) + 1j * (ar @ bi + ai @ br)) * 2.0 ** (ea + eb)
+
+
 def rand_c64(seed, shape):
     rng = np.random.default_rng(seed)
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
@@ -94,8 +111,9 @@ def test_single_gemm_bf16x3(tn, m, k, n, a_kfirst, b_nfirst):
     tb = (B.T if b_nfirst else B).reshape((2,) * (k + n))
     open_l = ml + nl
     exact = A.astype(np.complex128) @ B.astype(np.complex128)
-    emu = {"bf16x3": emulate_split_4m(A, B, bf16), "tf32x3": emulate_split_4m(A, B, tf32)}
-    for form, tol_exact in (("fp32", 2e-6), ("bf16x3", 1e-5), ("tf32x3", 1e-6)):
+    emu = {"bf16x3": emulate_split_4m(A, B, bf16), "tf32x3": emulate_split_4m(A, B, tf32),
+           "fp16s": emulate_fp16s_4m(A, B)}
+    for form, tol_exact in (("fp32", 2e-6), ("bf16x3", 1e-5), ("tf32x3", 1e-6), ("fp16s", 2e-3)):
         plan = tn.Plan([la, lb], [ta, tb], open_l, [], [(0, 1)], form=form)
         amp = torch.zeros(2 * M * N, dtype=torch.float64, device="cuda")
         plan.contract(0, 1, amp)
@@ -110,7 +128,7 @@ def test_single_gemm_bf16x3(tn, m, k, n, a_kfirst, b_nfirst):
         plan.close()
 
 
-@pytest.mark.parametrize("form", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("form", ["bf16x3", "tf32x3", "fp16s"])
 def test_batched_gemm_split(tn, form):
     """A sliced label shared by both operands becomes a batch label of the
     GEMM when the slices run as one batch."""
@@ -133,5 +151,5 @@ def test_batched_gemm_split(tn, form):
     # slice s: label h takes bit 0 of s, label h+1 bit 1; A index (h, h+1) -> 2*b0 + b1
     exact = sum(A[2 * (s & 1) + (s >> 1)].astype(np.complex128) @ B[2 * (s & 1) + (s >> 1)].astype(np.complex128)
                 for s in range(4))
-    assert rel(got, exact) < 1e-5
+    assert rel(got, exact) < (2e-3 if form == "fp16s" else 1e-5)
     plan.close()
