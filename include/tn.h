@@ -39,6 +39,7 @@ extern "C" {
 
 typedef struct tn_plan *tn_plan_t; /* opaque, owned by the library */
 typedef struct tn_costmodel *tn_costmodel_t; /* opaque learned step-cost model */
+typedef struct tn_batch *tn_batch_t; /* opaque batch of plans run as one graph */
 typedef struct CUstream_st *tn_stream_t; /* a cudaStream_t */
 
 enum {
@@ -282,6 +283,32 @@ int tn_costmodel_predict(tn_costmodel_t cm, const float *d_X, float *d_Y, int64_
  * of steps written (at most max_ops) or a negative error.
  */
 int tn_plan_op_features(tn_plan_t plan, float *out, int max_ops);
+
+/*
+ * Batch of independent plans (many circuits of uneven size, each with its own
+ * slices) run together.  The batch borrows the plans and their amplitude
+ * buffers (device complex128, 2^n_open each; plans and buffers must outlive
+ * the batch).  tn_batch_run OVERWRITES each buffer with the sum over all of
+ * that plan's slices.  The first run is eager on `stream` and synchronises it;
+ * it then captures one CUDA graph in which the plans are spread over
+ * n_streams concurrent branches (longest job first by complex MACs); later
+ * runs are one graph launch on `stream`.
+ */
+int tn_batch_create(tn_batch_t *out, int n_plans, const tn_plan_t *plans, double *const *d_amps, int n_streams);
+int tn_batch_run(tn_batch_t batch, tn_stream_t stream);
+void tn_batch_destroy(tn_batch_t batch);
+
+/*
+ * Autotuner for the plan's tensor-core GEMM steps: times each of them under a
+ * few (K chunk bytes, accumulator read-out bytes) configurations on the
+ * plan's current buffers (reps timed launches each, CUDA events on `stream`)
+ * and keeps the fastest.  Results are cached for the process by step
+ * signature (form, H, M, N, K), so later plans with the same steps reuse
+ * them without timing.  Synchronises `stream`; the GEMM outputs in the arena
+ * are overwritten (call it before contracting, or contract again after).
+ * Drops CUDA graphs captured before (they are recaptured on the next call).
+ */
+int tn_plan_autotune(tn_plan_t plan, int reps, tn_stream_t stream);
 
 /* Per-plan statistics: out[0] MACs per slice batch, out[1] slices per batch,
  * out[2] arena bytes, out[3] number of steps, out[4] kernel launches per

@@ -71,13 +71,18 @@ _lib.tn_costmodel_train.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, ctypes.c_
                                     ctypes.POINTER(ctypes.c_double), _vp]
 _lib.tn_costmodel_predict.argtypes = [_vp, _vp, _vp, _i64, _vp]
 _lib.tn_plan_op_features.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.tn_plan_autotune.argtypes = [_vp, ctypes.c_int, _vp]
+_lib.tn_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, ctypes.c_int]
+_lib.tn_batch_run.argtypes = [_vp, _vp]
+_lib.tn_batch_destroy.argtypes = [_vp]
+_lib.tn_batch_destroy.restype = None
 COST_FEATURES = 16
 
 EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabilities_xeb", "tn_plan_destroy",
             "tn_last_error", "tn_find_order", "tn_circuit_network", "tn_plan_stats", "tn_plan_update_data",
             "tn_plan_profile", "tn_gemm_split_noalloc", "tn_costmodel_create", "tn_costmodel_destroy",
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
-            "tn_plan_op_features"]
+            "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -241,6 +246,10 @@ class Plan:
                             shape=[float(x) for x in r[8:12]]))
         return out
 
+    def autotune(self, reps=3, stream=None):
+        """tn_plan_autotune: pick each tensor-core GEMM's (chunk, read-out) by timing."""
+        _check(_lib.tn_plan_autotune(self._h, int(reps), _stream_ptr(stream)), "tn_plan_autotune")
+
     def op_features(self, max_ops=4096):
         """Step features (rows of 16) in the order of profile() rows without
         the extraction and FP64-sum rows."""
@@ -350,6 +359,35 @@ class CostModel:
     def close(self):
         if getattr(self, "_h", None):
             _lib.tn_costmodel_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """tn_batch_*: many independent plans run together (one CUDA graph after the
+    first run); run() overwrites each plan's amplitude tensor."""
+
+    def __init__(self, plans, amps, n_streams=4):
+        self._plans = list(plans)  # keep alive
+        self._amps = list(amps)
+        hp = (_vp * len(plans))(*[p._h for p in plans])
+        ha = (_vp * len(amps))(*[a.data_ptr() for a in amps])
+        h = _vp()
+        _check(_lib.tn_batch_create(ctypes.byref(h), len(plans), ctypes.cast(hp, _vp), ctypes.cast(ha, _vp),
+                                    int(n_streams)), "tn_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_lib.tn_batch_run(self._h, _stream_ptr(stream)), "tn_batch_run")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tn_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -25,6 +25,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <set>
 #include <string>
 #include <unordered_map>
@@ -1146,6 +1148,211 @@ extern "C" int tn_plan_profile(tn_plan_t P, int max_rows, double *rows, int rese
     if (reset)
         for (auto &r : P->prof) { r.ms = 0; r.calls = 0; }
     return n;
+}
+
+namespace tn {
+namespace {
+
+// (form, H, M, N, K) -> tuned (chunk bytes, read-out bytes), process-wide
+std::map<std::tuple<int, int64_t, int64_t, int64_t, int64_t>, std::pair<int, int>> g_tuned;
+std::mutex g_tuned_mu;
+
+}  // namespace
+}  // namespace tn
+
+extern "C" int tn_plan_autotune(tn_plan_t P, int reps, tn_stream_t stream) {
+    if (!P) return fail(TN_ERR_ARG, "plan is NULL");
+    if (P->failed) return fail(TN_ERR_STATE, "plan is in a failed state");
+    if (reps < 1) reps = 3;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    static const int kCand[][2] = {{128, 512}, {128, 2048}, {128, 256}, {64, 512}, {64, 2048}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(TN_ERR_CUDA, "cudaEventCreate");
+    int rc = TN_OK;
+    for (auto *ops : {&P->prologue, &P->batch})
+        for (auto &op : *ops) {
+            if (op.kind != OP_GEMM || op.gemm_variant != 1) continue;
+            const auto key = std::make_tuple((int)P->form, op.tc.a.H, op.tc.a.M, op.tc.a.N, op.tc.a.K);
+            {
+                std::lock_guard<std::mutex> lk(g_tuned_mu);
+                auto it = g_tuned.find(key);
+                if (it != g_tuned.end()) {
+                    op.tc.chunk_bytes = it->second.first;
+                    op.tc.flush_bytes = it->second.second;
+                    if (!tc_prepare(op.tc)) rc = fail(TN_ERR_CUDA, "TMA descriptor encoding failed");
+                    continue;
+                }
+            }
+            // time each candidate on the current buffers (values do not matter)
+            float best_ms = 1e30f;
+            int best = 0;
+            for (int ci = 0; ci < (int)(sizeof kCand / sizeof kCand[0]); ci++) {
+                TcGemm g = op.tc;
+                g.chunk_bytes = kCand[ci][0];
+                g.flush_bytes = kCand[ci][1];
+                if (!tc_prepare(g)) continue;
+                cudaError_t e = launch_gemm_tc(g, s);  // warm-up
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && e == cudaSuccess; r++) e = launch_gemm_tc(g, s);
+                cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "autotune");
+                    break;
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = ci;
+                }
+            }
+            if (rc) break;
+            op.tc.chunk_bytes = kCand[best][0];
+            op.tc.flush_bytes = kCand[best][1];
+            if (!tc_prepare(op.tc)) { rc = fail(TN_ERR_CUDA, "TMA descriptor encoding failed"); break; }
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            g_tuned[key] = {kCand[best][0], kCand[best][1]};
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == TN_OK && tc_read_error(s) != 0) rc = fail(TN_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
+    if (rc) P->failed = true;
+    // graphs captured earlier hold the old configuration
+    if (P->graphs_ready) {
+        if (P->g_pro) cudaGraphExecDestroy(P->g_pro);
+        if (P->g_body) cudaGraphExecDestroy(P->g_body);
+        P->g_pro = P->g_body = nullptr;
+        P->graphs_ready = false;
+    }
+    return rc;
+}
+
+struct tn_batch {
+    std::vector<tn_plan_t> plans;
+    std::vector<double *> amps;
+    int n_streams = 4;
+    std::vector<int> stream_of;  // plan -> worker stream (longest job first)
+    cudaGraphExec_t exec = nullptr;
+    int64_t runs = 0;
+};
+
+namespace tn {
+namespace {
+
+// every op of one plan for all its slices, overwriting its amplitude tensor
+cudaError_t enqueue_plan_all(const tn_plan &P, double *amp, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(amp, 0, sizeof(double) * 2 * ((size_t)1 << P.n_open), s);
+    for (const auto &op : P.prologue)
+        if (e == cudaSuccess) e = run_op(P, op, s);
+    const int64_t B = (int64_t)1 << P.nb, S = (int64_t)1 << P.n_sliced;
+    AccumArgs acc = P.accum;
+    acc.amp = reinterpret_cast<double2 *>(amp);
+    for (int64_t base = 0; base < S && e == cudaSuccess; base += B) {
+        e = launch_extract(P.d_extract, (int)P.extract.size(), P.extract_max_out, (uint64_t)base, s);
+        for (const auto &op : P.batch)
+            if (e == cudaSuccess) e = run_op(P, op, s);
+        acc.b_lo = 0;
+        acc.b_hi = B;
+        if (e == cudaSuccess) e = launch_accum(acc, s);
+    }
+    return e;
+}
+
+cudaError_t capture_batch(tn_batch &b) {
+    cudaStream_t s0;
+    cudaError_t e = cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaStream_t> ws(b.n_streams, nullptr);
+    std::vector<cudaEvent_t> done(b.n_streams, nullptr);
+    cudaEvent_t fork = nullptr;
+    for (int i = 0; i < b.n_streams && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaEventRecord(fork, s0);
+        for (int i = 0; i < b.n_streams && le == cudaSuccess; i++) le = cudaStreamWaitEvent(ws[i], fork, 0);
+        for (size_t p = 0; p < b.plans.size() && le == cudaSuccess; p++)
+            le = enqueue_plan_all(*b.plans[p], b.amps[p], ws[b.stream_of[p]]);
+        for (int i = 0; i < b.n_streams && le == cudaSuccess; i++) {
+            le = cudaEventRecord(done[i], ws[i]);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(s0, done[i], 0);
+        }
+        e = cudaStreamEndCapture(s0, &g);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (int i = 0; i < b.n_streams; i++) {
+        if (ws[i]) cudaStreamDestroy(ws[i]);
+        if (done[i]) cudaEventDestroy(done[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    cudaStreamDestroy(s0);
+    return e;
+}
+
+}  // namespace
+}  // namespace tn
+
+extern "C" int tn_batch_create(tn_batch_t *out, int n_plans, const tn_plan_t *plans, double *const *d_amps,
+                               int n_streams) {
+    if (!out) return fail(TN_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_plans <= 0 || !plans || !d_amps) return fail(TN_ERR_ARG, "tn_batch_create: need plans and amplitudes");
+    std::unique_ptr<tn_batch> b(new tn_batch());
+    b->n_streams = n_streams > 0 ? std::min(n_streams, 32) : 4;
+    std::vector<double> work(n_plans);
+    for (int i = 0; i < n_plans; i++) {
+        if (!plans[i] || !d_amps[i]) return fail(TN_ERR_ARG, "tn_batch_create: NULL plan or amplitude buffer");
+        if (plans[i]->failed) return fail(TN_ERR_STATE, "tn_batch_create: a plan is in a failed state");
+        b->plans.push_back(plans[i]);
+        b->amps.push_back(d_amps[i]);
+        const tn_plan &P = *plans[i];
+        work[i] = P.macs_prologue + P.macs_batch * std::exp2((double)(P.n_sliced - P.nb)) + 1.0;
+    }
+    // longest job first onto the least-loaded stream
+    std::vector<int> order(n_plans);
+    for (int i = 0; i < n_plans; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    std::vector<double> load(b->n_streams, 0.0);
+    b->stream_of.assign(n_plans, 0);
+    for (int i : order) {
+        int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->stream_of[i] = k;
+        load[k] += work[i];
+    }
+    *out = b.release();
+    return TN_OK;
+}
+
+extern "C" int tn_batch_run(tn_batch_t b, tn_stream_t stream) {
+    if (!b) return fail(TN_ERR_ARG, "batch is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (!b->exec) {
+        // first run: eager on the caller's stream (sets up every kernel), then capture
+        for (size_t p = 0; p < b->plans.size() && e == cudaSuccess; p++)
+            e = enqueue_plan_all(*b->plans[p], b->amps[p], s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = capture_batch(*b);
+    } else {
+        e = cudaGraphLaunch(b->exec, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tn_batch_run");
+    b->runs++;
+    return TN_OK;
+}
+
+extern "C" void tn_batch_destroy(tn_batch_t b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
 }
 
 extern "C" int tn_plan_op_features(tn_plan_t P, float *out, int max_ops) {
