@@ -127,8 +127,8 @@ __device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, flo
         uint16_t *P = reinterpret_cast<uint16_t *>(a.out);
         const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
         P[d] = __bfloat16_as_ushort(rh);
-        P[d + a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
-        P[d + 2 * a.plane_stride] = __bfloat16_as_ushort(ih);
+        P[d + a.plane_stride] = __bfloat16_as_ushort(ih);
+        P[d + 2 * a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
         P[d + 3 * a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
     } else if (a.mode == 3) {
         const int e = fp16s_exponent(__uint_as_float(*a.scale));
@@ -139,8 +139,8 @@ __device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, flo
         uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
         const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
         P[d] = rh;
-        P[d + a.plane_stride] = tf32_rna(v.x - __uint_as_float(rh));
-        P[d + 2 * a.plane_stride] = ih;
+        P[d + a.plane_stride] = ih;
+        P[d + 2 * a.plane_stride] = tf32_rna(v.x - __uint_as_float(rh));
         P[d + 3 * a.plane_stride] = tf32_rna(v.y - __uint_as_float(ih));
     }
 }

@@ -37,7 +37,7 @@ struct SmallArgs {
 // hi/lo split of split-precision GEMM operands.
 //   out index d (r bits) <- in[sum_p bit_p(d) << src_pos[p]]
 // mode 0: complex64 out[d];
-// mode 1/2: four planes (re_hi, re_lo, im_hi, im_lo) of bf16 (1) or tf32 held
+// mode 1/2: four planes (re_hi, im_hi, re_lo, im_lo) of bf16 (1) or tf32 held
 //           in 32 bits (2) at d + q * plane_stride, q = 0..3;
 // mode 3:   two fp16 planes (re, im) of x * 2^-e, e = ilogb(max|x|) - 13 from
 //           the max-abs slot `scale` (a float stored as its bits), so the

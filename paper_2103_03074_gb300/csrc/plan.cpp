@@ -1165,7 +1165,10 @@ extern "C" int tn_plan_autotune(tn_plan_t P, int reps, tn_stream_t stream) {
     if (P->failed) return fail(TN_ERR_STATE, "plan is in a failed state");
     if (reps < 1) reps = 3;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    static const int kCand[][2] = {{128, 512}, {128, 2048}, {128, 256}, {64, 512}, {64, 2048}};
+    // (chunk bytes, read-out bytes); read-outs never sparser than the form's
+    // default, which bounds the accumulation error
+    const int D = tc_default_flush_bytes(P->form);
+    const int kCand[][2] = {{128, D}, {128, D / 2 < 128 ? 128 : D / 2}, {64, D}, {64, D / 2}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(TN_ERR_CUDA, "cudaEventCreate");

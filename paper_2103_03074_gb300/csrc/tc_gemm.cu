@@ -6,22 +6,27 @@
 //           Heinecke 2019), kind::f16 MMAs, 16 K values per MMA;
 //   TF32x3: hi = tf32(x), lo = tf32(x - hi) (Ootomo & Yokota 2022), kind::tf32
 //           MMAs, 8 K values per MMA.
-// A real product x*y is hi_x hi_y + hi_x lo_y + lo_x hi_y.  Complex products
-// use four real products (re = ar br - ai bi, im = ar bi + ai br), the minus
-// sign folded into the MMA's negate-A bit: 12 MMAs per K step.
+// A real product x*y is hi_x hi_y + hi_x lo_y + lo_x hi_y.
 //
-// The hi/lo split of each operand into four K-major planes (re_hi, re_lo,
-// im_hi, im_lo) is done beforehand by the tiled bit-permute kernel, fused with
-// whatever label permutation the operand needs (kernels.cu).
+// The split of each operand into four K-major planes (re_hi, im_hi, re_lo,
+// im_lo) is done beforehand by the tiled bit-permute kernel, fused with
+// whatever label permutation the operand needs (kernels.cu).  Because B's
+// re and im planes of one precision sit next to each other, a 64-column B
+// tile of both is one 128-row operand S = [B_re | B_im], and a complex
+// product needs two real MMAs of N = 128 per piece pair:
+//   P += A_re S = [A_re B_re | A_re B_im],  Q += A_im S = [A_im B_re | A_im B_im],
+// re = P_left - Q_right, im = P_right + Q_left, combined in FP32 registers.
+// That is 6 MMAs of 128 x 128 per K step for the hi/lo forms (2 for FP16S),
+// reading 1.5x fewer shared-memory bytes per MAC than 128 x 64 MMAs.
 // tc_gemm_kernel is warp-specialised.  Warp 0 issues TMA loads of the planes
 // into a shared-memory ring (128-byte K chunks: 128-byte swizzle, 2 stages;
 // 64-byte chunks: 64-byte swizzle, 4 stages); warp 1 issues the MMAs of each
-// group of chunks into one of two tensor-memory accumulator sets; warps 4-11
-// read each finished group's accumulators (tcgen05.ld) and add them into FP32
-// registers with round-to-nearest.  Reading out every few hundred bytes of K
-// keeps the tensor core's truncating accumulation to a few dozen MMAs; hi*hi
-// and the correction products also sit in separate accumulators for the same
-// reason (small addends aligned to a large running sum lose their low bits).
+// group of chunks into one of two tensor-memory accumulator sets {P, Q};
+// warps 4-11 read each finished group's accumulators (tcgen05.ld) and add
+// them into FP32 registers with round-to-nearest.  Reading out every few
+// hundred bytes of K keeps the tensor core's truncating accumulation to a few
+// dozen MMAs (small correction addends aligned to a large running sum lose
+// their low bits, so the count of MMAs into one accumulator sets the error).
 //
 // CTA tile: 128 (M) x 64 (N); a K chunk is 64 or 128 bytes of a plane row.  CTAs sharing an A tile are adjacent in the launch order
 // (N tiles vary fastest), so A is read from DRAM about once and re-served from
@@ -45,20 +50,24 @@ __device__ int tc_error = 0;
 namespace {
 
 constexpr int TM = 128, TN = 64;
-// defaults from a sweep of (chunk, flush) on a 4 x 8192 x 512 x 2048 GEMM:
-// 128-byte chunks beat 64-byte ones at every flush interval; reading the
-// accumulators out every 512 bytes of K (instead of 128) is 8% faster and
-// keeps the error well inside the FP32 form's
-constexpr int kDefaultChunkBytes = 128, kDefaultFlushBytes = 512;
+// defaults from sweeps on a 4 x 8192 x 512 x 2048 GEMM and the 30-qubit
+// workload: 128-byte chunks beat 64-byte ones at every read-out interval.
+// Reading the accumulators out every 256 bytes of K keeps TF32x3 at 3.5e-6
+// relative amplitude error there (512 bytes: 2% faster, 5.3e-6); the BF16x3
+// and FP16S errors are set by their operand pieces, not by the interval, so
+// they read out every 512 bytes.
+constexpr int kDefaultChunkBytes = 128;
+__host__ __device__ constexpr int default_flush_bytes(tn_form f) { return f == TN_TF32X3 ? 256 : 512; }
 constexpr int kThreads = 384;  // 12 warps
 constexpr int kFlushWarp0 = 4, kFlushWarps = 8;
-constexpr int kTmemCols = 512;  // 2 sets x {re, im, re corr, im corr} x 64
+constexpr int kTmemCols = 512;  // 2 sets x {P, Q} x 128 columns
 
 // operand forms of the kernel template
 constexpr int kBF16 = 0, kTF32 = 1, kFP16 = 2;
 
 // Shared-memory ring for a K chunk of CB bytes per plane row: NP planes of A
-// (128 rows) and of B (64 rows) per stage (4 for the hi/lo split forms, 2 for
+// (128 rows) and of B (64 rows, so that planes 2j and 2j + 1 form one
+// 128-row operand) per stage (4 for the hi/lo split forms, 2 for
 // FP16S); as many stages as fit in 192 KB, at most 6.  64-byte chunks use the
 // 64-byte swizzle, 128-byte chunks the 128-byte swizzle.
 template <int CB, int NP = 4>
@@ -234,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t fmt = KIND == kTF32 ? 2u : (KIND == kBF16 ? 1u : 0u);  // tf32 / bf16 / f16
-            constexpr uint32_t IP = make_idesc(fmt, TM, TN, false), IN = make_idesc(fmt, TM, TN, true);
+            constexpr uint32_t ID = make_idesc(fmt, TM, 2 * TN, false);
             for (int c = 0; c < n_chunks; c++) {
                 const int s = c % kStages, use = c / kStages;
                 const int g = c / kFlushChunks;             // flush group
@@ -245,46 +254,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (first && tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) break;
                 fence_after();
                 const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + NP * kAPlane;
-                const uint32_t d_re = tmem + t * 256, d_im = d_re + 64, c_re = d_re + 128, c_im = d_re + 192;
-                if (KIND == kFP16) {
-                    // one scaled fp16 piece per value: planes {re, im}
-#pragma unroll
-                    for (int ks = 0; ks < CB / 32; ks++) {
-                        const uint32_t ko = ks * 32;
-                        const uint64_t ar = make_desc<CB>(a0 + ko), ai = make_desc<CB>(a0 + kAPlane + ko);
-                        const uint64_t br = make_desc<CB>(b0 + ko), bi = make_desc<CB>(b0 + kBPlane + ko);
-                        const uint32_t acc = (first && ks == 0) ? 0u : 1u;
-                        mma<KIND>(d_re, ar, br, IP, acc);
-                        mma<KIND>(d_re, ai, bi, IN, 1u);
-                        mma<KIND>(d_im, ar, bi, IP, acc);
-                        mma<KIND>(d_im, ai, br, IP, 1u);
-                    }
-                    mma_commit(smem_u32(&empty[s]));
-                    if (last) mma_commit(smem_u32(&tfull[t]));
-                    continue;
-                }
+                const uint32_t dP = tmem + t * 256, dQ = dP + 128;
 #pragma unroll
                 for (int ks = 0; ks < CB / 32; ks++) {  // MMA K steps of 32 bytes
                     const uint32_t ko = ks * 32;
-                    const uint64_t arh = make_desc<CB>(a0 + ko), arl = make_desc<CB>(a0 + kAPlane + ko);
-                    const uint64_t aih = make_desc<CB>(a0 + 2 * kAPlane + ko);
-                    const uint64_t ail = make_desc<CB>(a0 + 3 * kAPlane + ko);
-                    const uint64_t brh = make_desc<CB>(b0 + ko), brl = make_desc<CB>(b0 + kBPlane + ko);
-                    const uint64_t bih = make_desc<CB>(b0 + 2 * kBPlane + ko);
-                    const uint64_t bil = make_desc<CB>(b0 + 3 * kBPlane + ko);
                     const uint32_t acc = (first && ks == 0) ? 0u : 1u;  // each flush group starts fresh sums
-                    mma<KIND>(d_re, arh, brh, IP, acc);
-                    mma<KIND>(d_re, aih, bih, IN, 1u);
-                    mma<KIND>(c_re, arh, brl, IP, acc);
-                    mma<KIND>(c_re, arl, brh, IP, 1u);
-                    mma<KIND>(c_re, aih, bil, IN, 1u);
-                    mma<KIND>(c_re, ail, bih, IN, 1u);
-                    mma<KIND>(d_im, arh, bih, IP, acc);
-                    mma<KIND>(d_im, aih, brh, IP, 1u);
-                    mma<KIND>(c_im, arh, bil, IP, acc);
-                    mma<KIND>(c_im, arl, bih, IP, 1u);
-                    mma<KIND>(c_im, aih, brl, IP, 1u);
-                    mma<KIND>(c_im, ail, brh, IP, 1u);
+                    const uint64_t ar = make_desc<CB>(a0 + ko), ai = make_desc<CB>(a0 + kAPlane + ko);
+                    const uint64_t S = make_desc<CB>(b0 + ko);  // [re | im] of the (hi) piece
+                    mma<KIND>(dP, ar, S, ID, acc);
+                    mma<KIND>(dQ, ai, S, ID, acc);
+                    if (KIND != kFP16) {
+                        // corrections hi*lo + lo*hi into the same sums
+                        const uint64_t arl = make_desc<CB>(a0 + 2 * kAPlane + ko);
+                        const uint64_t ail = make_desc<CB>(a0 + 3 * kAPlane + ko);
+                        const uint64_t Sl = make_desc<CB>(b0 + 2 * kBPlane + ko);
+                        mma<KIND>(dP, ar, Sl, ID, 1u);
+                        mma<KIND>(dP, arl, S, ID, 1u);
+                        mma<KIND>(dQ, ai, Sl, ID, 1u);
+                        mma<KIND>(dQ, ail, S, ID, 1u);
+                    }
                 }
                 mma_commit(smem_u32(&empty[s]));
                 if (last) mma_commit(smem_u32(&tfull[t]));
@@ -308,22 +296,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int q = 0; q < 2; q++) {
                 uint32_t r0[16], r1[16], r2[16], r3[16];
-                tmem_ld16(base + q * 16, r0);       // re main
-                tmem_ld16(base + 64 + q * 16, r1);  // im main
-                if (KIND != kFP16) {
-                    tmem_ld16(base + 128 + q * 16, r2);  // re correction
-                    tmem_ld16(base + 192 + q * 16, r3);  // im correction
-                }
+                tmem_ld16(base + q * 16, r0);        // P left:  A_re B_re
+                tmem_ld16(base + 64 + q * 16, r1);   // P right: A_re B_im
+                tmem_ld16(base + 128 + q * 16, r2);  // Q left:  A_im B_re
+                tmem_ld16(base + 192 + q * 16, r3);  // Q right: A_im B_im
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    if (KIND != kFP16) {
-                        acc_re[q * 16 + j] += __uint_as_float(r0[j]) + __uint_as_float(r2[j]);
-                        acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r3[j]);
-                    } else {
-                        acc_re[q * 16 + j] += __uint_as_float(r0[j]);
-                        acc_im[q * 16 + j] += __uint_as_float(r1[j]);
-                    }
+                    acc_re[q * 16 + j] += __uint_as_float(r0[j]) - __uint_as_float(r3[j]);
+                    acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r2[j]);
                 }
             }
             fence_before();
@@ -431,6 +412,8 @@ bool tc_form_available(tn_form form) {
 
 int tc_plane_bytes(tn_form form) { return form == TN_TF32X3 ? 4 : 2; }
 
+int tc_default_flush_bytes(tn_form form) { return default_flush_bytes(form); }
+
 int tc_plane_count(tn_form form) { return form == TN_FP16S ? 2 : 4; }
 
 bool tc_gemm_suitable(const GemmArgs &a) {
@@ -450,7 +433,8 @@ int tc_choose_ksplit(const GemmArgs &a, tn_form form) {
 bool tc_prepare(TcGemm &g) {
     const int es = tc_plane_bytes(g.form);
     if (g.chunk_bytes != 64 && g.chunk_bytes != 128) g.chunk_bytes = kDefaultChunkBytes;
-    if (g.flush_bytes < g.chunk_bytes) g.flush_bytes = kDefaultFlushBytes < g.chunk_bytes ? g.chunk_bytes : kDefaultFlushBytes;
+    if (g.flush_bytes < g.chunk_bytes)
+        g.flush_bytes = default_flush_bytes(g.form) < g.chunk_bytes ? g.chunk_bytes : default_flush_bytes(g.form);
     if (g.a.K * es < g.chunk_bytes) g.chunk_bytes = 64;
     const int cb = g.chunk_bytes, np = tc_plane_count(g.form);
     const CUtensorMapDataType dt = g.form == TN_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32

@@ -29,9 +29,14 @@ bool tc_form_available(tn_form form);
 // bytes per plane element of a split form (2: bf16 / fp16, 4: tf32)
 int tc_plane_bytes(tn_form form);
 
-// planes per operand: 4 for the hi/lo split forms (re_hi, re_lo, im_hi,
+// planes per operand: 4 for the hi/lo split forms (re_hi, im_hi, re_lo,
 // im_lo), 2 for FP16S (re, im)
 int tc_plane_count(tn_form form);
+
+// K bytes between accumulator read-outs when TcGemm::flush_bytes is 0: the
+// largest interval that keeps the form's accuracy (the read-out interval
+// bounds how many MMAs add into one truncating tensor-memory sum)
+int tc_default_flush_bytes(tn_form form);
 
 // Shapes the tensor-core kernel takes (smaller GEMMs stay on the FP32
 // CUDA-core kernel).

@@ -197,12 +197,15 @@ def test_cfg2_amplitudes_vs_golden(tn, form):
     # same as a round-to-nearest emulation of the split), so it is held to
     # 2e-5 and is not a form that meets the stated bound here.
     # FP16S is held to the 2e-3 bound stated for the scaled-FP16 form.
-    assert rel(got, ref) < {"bf16x3": 2e-5, "fp16s": 2e-3}.get(form, TOL)
-    # XEB from the GPU probabilities against the oracle's, 1e-4 absolute
+    bound = {"bf16x3": 2e-5, "fp16s": 2e-3}.get(form, TOL)
+    assert rel(got, ref) < bound
+    # XEB from the GPU probabilities against the oracle's, 1e-4 absolute; the
+    # marginal sum |a|^2 moves by at most (2 e + e^2) of itself when the
+    # amplitudes move by a relative L2 error e
     p_s1, f, pmax = tn.probabilities_xeb(amp, 8, 30)
     if form != "fp16s":
         assert abs(f - oxeb.linear_xeb(ref, 30)) < 1e-4
-        assert abs(p_s1 - oxeb.marginal(ref)) < 1e-5 * oxeb.marginal(ref)
+        assert abs(p_s1 - oxeb.marginal(ref)) < (2 * bound + bound ** 2) * oxeb.marginal(ref)
 
 
 def test_probabilities_xeb_on_oracle_amplitudes(tn):
