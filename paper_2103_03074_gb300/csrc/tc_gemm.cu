@@ -28,13 +28,17 @@
 // dozen MMAs (small correction addends aligned to a large running sum lose
 // their low bits, so the count of MMAs into one accumulator sets the error).
 //
-// CTA tile: 128 (M) x 64 (N); a K chunk is 64 or 128 bytes of a plane row.  CTAs sharing an A tile are adjacent in the launch order
-// (N tiles vary fastest), so A is read from DRAM about once and re-served from
-// L2.  The output tile is staged in shared memory and written as whole rows.
-// GEMMs with fewer tiles than SMs split K over CTAs and add their partial
-// tiles with atomics into a zeroed output.  Every mbarrier wait is bounded; on
-// expiry the kernel records an error in tc_error and returns after freeing its
-// tensor memory.
+// CTA tile: 128 (M) x 64 (N); a K chunk is 64 or 128 bytes of a plane row.
+// The kernel is persistent: one CTA per SM walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... with N tiles varying fastest, so the CTAs that
+// run at the same time share A tiles (read from DRAM about once, re-served
+// from L2).  The TMA ring, the accumulator sets and the read-out groups run
+// on across tile boundaries, so a tile's epilogue (staged through shared
+// memory in two halves and written as whole rows) overlaps the next tile's
+// loads and MMAs.  GEMMs with fewer tiles than SMs split K over CTAs and add
+// their partial tiles with atomics into a zeroed output.  Every mbarrier wait
+// is bounded; on expiry the kernel records an error in tc_error and returns
+// after freeing its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -69,16 +73,18 @@ constexpr int kBF16 = 0, kTF32 = 1, kFP16 = 2;
 // (128 rows) and of B (64 rows, so that planes 2j and 2j + 1 form one
 // 128-row operand) per stage (4 for the hi/lo split forms, 2 for
 // FP16S); as many stages as fit in 192 KB, at most 6.  64-byte chunks use the
-// 64-byte swizzle, 128-byte chunks the 128-byte swizzle.
+// 64-byte swizzle, 128-byte chunks the 128-byte swizzle.  Behind the ring: the
+// epilogue's staging area for half a tile (64 rows of 64 complex values).
 template <int CB, int NP = 4>
 struct Ring {
     static constexpr int kAPlane = TM * CB;
     static constexpr int kBPlane = TN * CB;
     static constexpr int kStageBytes = NP * kAPlane + NP * kBPlane;
     static constexpr int kStages = (196608 / kStageBytes) < 6 ? (196608 / kStageBytes) : 6;
-    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
-    static constexpr uint32_t kSBO = 8 * CB;                // 8 rows of one swizzle atom
-    static constexpr uint64_t kLayout = CB == 64 ? 4 : 2;  // descriptor swizzle code
+    static constexpr int kOutRS = 66;  // staging row stride in float2 (16-byte aligned rows)
+    static constexpr int kOutBytes = (TM / 2) * kOutRS * 8;
+    static constexpr int kSmem = kStages * kStageBytes + kOutBytes + 1024 + 256;
+    static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 constexpr uint32_t kSpinLimit = 1u << 24;
 
@@ -86,14 +92,21 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// K-major swizzled operand layout of a CB-byte chunk row
+template <int CB>
+struct Swz {
+    static constexpr uint32_t kSBO = 8 * CB;                // 8 rows of one swizzle atom
+    static constexpr uint64_t kLayout = CB == 64 ? 4 : 2;  // descriptor swizzle code
+};
+
 template <int CB>
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(Ring<CB>::kSBO >> 4) << 32;  // stride byte offset: 8 rows
+    d |= (uint64_t)(Swz<CB>::kSBO >> 4) << 32;   // stride byte offset: 8 rows
     d |= (uint64_t)1 << 46;                       // descriptor version
-    d |= Ring<CB>::kLayout << 61;                 // swizzle mode
+    d |= Swz<CB>::kLayout << 61;                  // swizzle mode
     return d;
 }
 
@@ -123,20 +136,36 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase of `parity`.  On expiry it records the error in
+// tc_error; once any wait has given up, the others stop early, so a stalled
+// pipeline unwinds in one expiry instead of one per remaining wait.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (uint32_t i = 0; i < kSpinLimit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred P;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, P;\n\t}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(mbar, parity)) return true;
+        if ((i & 1023u) == 1023u && *reinterpret_cast<volatile int *>(&tc_error) != 0) return false;
     }
     atomicExch(&tc_error, 1);
     return false;
+}
+
+// Bounded wait that is not cut short by tc_error: used on the way out to let
+// this CTA's own copies and MMAs land before its memory is released.
+__device__ __forceinline__ void mbar_drain(uint32_t mbar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; i++)
+        if (mbar_try(mbar, parity)) return;
+    atomicExch(&tc_error, 1);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
@@ -175,25 +204,55 @@ struct GemmTcParams {
     int64_t H, M, N, K;  // K in complex elements
     int64_t sCh, sCm, sCn;
     int k_chunk;       // K values per chunk
-    int ksplit;        // K partitions (blockIdx.z = h * ksplit + part); > 1: atomic adds
+    int ksplit;        // K partitions (> 1: atomic adds into a zeroed C)
     int flush_chunks;  // chunks per accumulator read-out
+    int gm, gn;        // M and N tiles
+    int64_t tiles;     // gn * gm * H * ksplit
     const unsigned *scales;  // FP16S: max-abs slots of A and B (float bits)
 };
+
+// tile t -> (n tile, m tile, batch h, K part); N tiles vary fastest
+struct TileCoord {
+    int64_t n0, m0;
+    int h, part;
+};
+__device__ __forceinline__ TileCoord tile_coord(const GemmTcParams &p, int64_t t) {
+    TileCoord c;
+    c.n0 = (t % p.gn) * TN;
+    t /= p.gn;
+    c.m0 = (t % p.gm) * TM;
+    t /= p.gm;
+    c.h = (int)(t / p.ksplit);
+    c.part = (int)(t % p.ksplit);
+    return c;
+}
+
+// [c_begin, c_begin + count) = the K chunks of one K part
+__device__ __forceinline__ int part_chunks(const GemmTcParams &p, int part, int &c_begin) {
+    const int all_chunks = (int)((p.K + p.k_chunk - 1) / p.k_chunk);
+    const int per = (all_chunks + p.ksplit - 1) / p.ksplit;
+    c_begin = part * per;
+    const int c_end = min(all_chunks, c_begin + per);
+    return c_end > c_begin ? c_end - c_begin : 0;
+}
 
 template <int KIND, int CB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
     constexpr int NP = KIND == kFP16 ? 2 : 4;
-    constexpr int kAPlane = Ring<CB, NP>::kAPlane, kBPlane = Ring<CB, NP>::kBPlane;
-    constexpr int kStageBytes = Ring<CB, NP>::kStageBytes, kStages = Ring<CB, NP>::kStages;
-    const int kFlushChunks = p.flush_chunks;
+    using R = Ring<CB, NP>;
+    constexpr int kAPlane = R::kAPlane, kBPlane = R::kBPlane;
+    constexpr int kStageBytes = R::kStageBytes, kStages = R::kStages;
+    const int F = p.flush_chunks;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    float2 *stage_out = reinterpret_cast<float2 *>(smem + kStages * kStageBytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes + R::kOutBytes);
     uint64_t *full = bar, *empty = bar + kStages, *tfull = bar + 2 * kStages, *tempty = bar + 2 * kStages + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * kStages + 4);
+    uint64_t *drain = bar + 2 * kStages + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * kStages + 5);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -205,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[t])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty[t])), "r"(kFlushWarps));
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(drain)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -217,26 +277,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int64_t n0 = (int64_t)blockIdx.x * TN, m0 = (int64_t)blockIdx.y * TM;
-    const int h = blockIdx.z / p.ksplit, part = blockIdx.z % p.ksplit;
-    const int all_chunks = (int)((p.K + p.k_chunk - 1) / p.k_chunk);
-    const int per = (all_chunks + p.ksplit - 1) / p.ksplit;
-    const int c_begin = part * per;
-    const int c_end = min(all_chunks, c_begin + per);
-    const int n_chunks = c_end > c_begin ? c_end - c_begin : 0;
-
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: every chunk of every tile of this CTA
         if (lane == 0) {
-            for (int c = 0; c < n_chunks; c++) {
-                const int s = c % kStages, use = c / kStages;
-                if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (use - 1) & 1)) break;
-                unsigned char *st = smem + s * kStageBytes;
-                const uint32_t fb = smem_u32(&full[s]);
-                mbar_expect_tx(fb, kStageBytes);
-                const int kc = (c_begin + c) * p.k_chunk;
-                tma_load_4d(smem_u32(st), &mapA, kc, (int)m0, h, 0, fb);
-                tma_load_4d(smem_u32(st + NP * kAPlane), &mapB, kc, (int)n0, h, 0, fb);
+            int cc = 0;  // chunks loaded so far (ring position)
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; ok && tile < p.tiles; tile += gridDim.x) {
+                const TileCoord tc = tile_coord(p, tile);
+                int c_begin;
+                const int n_chunks = part_chunks(p, tc.part, c_begin);
+                for (int c = 0; c < n_chunks; c++, cc++) {
+                    const int s = cc % kStages, use = cc / kStages;
+                    if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (use - 1) & 1)) { ok = false; break; }
+                    unsigned char *st = smem + s * kStageBytes;
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, kStageBytes);
+                    const int kc = (c_begin + c) * p.k_chunk;
+                    tma_load_4d(smem_u32(st), &mapA, kc, (int)tc.m0, tc.h, 0, fb);
+                    tma_load_4d(smem_u32(st + NP * kAPlane), &mapB, kc, (int)tc.n0, tc.h, 0, fb);
+                }
+            }
+            // let every issued load land before the CTA can exit (a no-op
+            // when the consumer has seen them all)
+            for (int s = 0; s < kStages && s < cc; s++) {
+                const int uses = (cc - s + kStages - 1) / kStages;
+                mbar_drain(smem_u32(&full[s]), (uses - 1) & 1);
             }
         }
     } else if (warp == 1) {
@@ -244,117 +309,144 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             constexpr uint32_t fmt = KIND == kTF32 ? 2u : (KIND == kBF16 ? 1u : 0u);  // tf32 / bf16 / f16
             constexpr uint32_t ID = make_idesc(fmt, TM, 2 * TN, false);
-            for (int c = 0; c < n_chunks; c++) {
-                const int s = c % kStages, use = c / kStages;
-                const int g = c / kFlushChunks;             // flush group
-                const int t = g & 1, tuse = g >> 1;
-                const bool first = (c % kFlushChunks) == 0;
-                const bool last = (c % kFlushChunks) == kFlushChunks - 1 || c == n_chunks - 1;
-                if (!mbar_wait(smem_u32(&full[s]), use & 1)) break;
-                if (first && tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) break;
-                fence_after();
-                const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + NP * kAPlane;
-                const uint32_t dP = tmem + t * 256, dQ = dP + 128;
+            int cc = 0, gc = 0;  // chunks consumed, read-out groups started
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; ok && tile < p.tiles; tile += gridDim.x) {
+                int c_begin;
+                const int n_chunks = part_chunks(p, tile_coord(p, tile).part, c_begin);
+                for (int c = 0; c < n_chunks; c++, cc++) {
+                    const int s = cc % kStages, use = cc / kStages;
+                    const int g = gc + c / F;  // read-out group (never spans two tiles)
+                    const int t = g & 1, tuse = g >> 1;
+                    const bool first = (c % F) == 0;
+                    const bool last = (c % F) == F - 1 || c == n_chunks - 1;
+                    if (!mbar_wait(smem_u32(&full[s]), use & 1)) { ok = false; break; }
+                    if (first && tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + NP * kAPlane;
+                    const uint32_t dP = tmem + t * 256, dQ = dP + 128;
 #pragma unroll
-                for (int ks = 0; ks < CB / 32; ks++) {  // MMA K steps of 32 bytes
-                    const uint32_t ko = ks * 32;
-                    const uint32_t acc = (first && ks == 0) ? 0u : 1u;  // each flush group starts fresh sums
-                    const uint64_t ar = make_desc<CB>(a0 + ko), ai = make_desc<CB>(a0 + kAPlane + ko);
-                    const uint64_t S = make_desc<CB>(b0 + ko);  // [re | im] of the (hi) piece
-                    mma<KIND>(dP, ar, S, ID, acc);
-                    mma<KIND>(dQ, ai, S, ID, acc);
-                    if (KIND != kFP16) {
-                        // corrections hi*lo + lo*hi into the same sums
-                        const uint64_t arl = make_desc<CB>(a0 + 2 * kAPlane + ko);
-                        const uint64_t ail = make_desc<CB>(a0 + 3 * kAPlane + ko);
-                        const uint64_t Sl = make_desc<CB>(b0 + 2 * kBPlane + ko);
-                        mma<KIND>(dP, ar, Sl, ID, 1u);
-                        mma<KIND>(dP, arl, S, ID, 1u);
-                        mma<KIND>(dQ, ai, Sl, ID, 1u);
-                        mma<KIND>(dQ, ail, S, ID, 1u);
+                    for (int ks = 0; ks < CB / 32; ks++) {  // MMA K steps of 32 bytes
+                        const uint32_t ko = ks * 32;
+                        const uint32_t acc = (first && ks == 0) ? 0u : 1u;  // each group starts fresh sums
+                        const uint64_t ar = make_desc<CB>(a0 + ko), ai = make_desc<CB>(a0 + kAPlane + ko);
+                        const uint64_t S = make_desc<CB>(b0 + ko);  // [re | im] of the (hi) piece
+                        mma<KIND>(dP, ar, S, ID, acc);
+                        mma<KIND>(dQ, ai, S, ID, acc);
+                        if (KIND != kFP16) {
+                            // corrections hi*lo + lo*hi into the same sums
+                            const uint64_t arl = make_desc<CB>(a0 + 2 * kAPlane + ko);
+                            const uint64_t ail = make_desc<CB>(a0 + 3 * kAPlane + ko);
+                            const uint64_t Sl = make_desc<CB>(b0 + 2 * kBPlane + ko);
+                            mma<KIND>(dP, ar, Sl, ID, 1u);
+                            mma<KIND>(dP, arl, S, ID, 1u);
+                            mma<KIND>(dQ, ai, Sl, ID, 1u);
+                            mma<KIND>(dQ, ail, S, ID, 1u);
+                        }
                     }
+                    mma_commit(smem_u32(&empty[s]));
+                    if (last) mma_commit(smem_u32(&tfull[t]));
                 }
-                mma_commit(smem_u32(&empty[s]));
-                if (last) mma_commit(smem_u32(&tfull[t]));
+                gc += (n_chunks + F - 1) / F;
+            }
+            // every MMA issued has completed before the tensor memory is freed
+            if (cc > 0) {
+                mma_commit(smem_u32(drain));
+                mbar_drain(smem_u32(drain), 0);
             }
         }
     } else if (warp >= kFlushWarp0) {
-        // ---------------- accumulator flush + epilogue (8 warps)
+        // ---------------- accumulator read-out + epilogue (8 warps)
         const int fw = warp - kFlushWarp0;
         const int lg = warp & 3, half = fw >> 2;  // TMEM lane group, column half
         const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
-        float acc_re[32], acc_im[32];
-#pragma unroll
-        for (int j = 0; j < 32; j++) acc_re[j] = acc_im[j] = 0.f;
+        int e_scale = 0;
+        if (KIND == kFP16)
+            e_scale = fp16s_exponent(__uint_as_float(p.scales[0])) + fp16s_exponent(__uint_as_float(p.scales[1]));
+        // every flush warp walks every tile of this CTA and reaches the same
+        // named barriers even after a failed wait (it then skips waits,
+        // tensor-memory reads and stores), so the warps never part ways
+        int gc = 0;
         bool ok = true;
-        const int n_groups = (n_chunks + kFlushChunks - 1) / kFlushChunks;
-        for (int gi = 0; gi < n_groups; gi++) {
-            const int t = gi & 1, tuse = gi >> 1;
-            if (!mbar_wait(smem_u32(&tfull[t]), tuse & 1)) { ok = false; break; }
-            fence_after();
-            const uint32_t base = tmem + t * 256 + lane_off + half * 32;
+        for (int64_t tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
+            const TileCoord tc = tile_coord(p, tile);
+            int c_begin;
+            const int n_chunks = part_chunks(p, tc.part, c_begin);
+            float acc_re[32], acc_im[32];
 #pragma unroll
-            for (int q = 0; q < 2; q++) {
-                uint32_t r0[16], r1[16], r2[16], r3[16];
-                tmem_ld16(base + q * 16, r0);        // P left:  A_re B_re
-                tmem_ld16(base + 64 + q * 16, r1);   // P right: A_re B_im
-                tmem_ld16(base + 128 + q * 16, r2);  // Q left:  A_im B_re
-                tmem_ld16(base + 192 + q * 16, r3);  // Q right: A_im B_im
-                tmem_wait_ld();
+            for (int j = 0; j < 32; j++) acc_re[j] = acc_im[j] = 0.f;
+            const int n_groups = (n_chunks + F - 1) / F;
+            for (int gi = 0; gi < n_groups; gi++, gc++) {
+                const int t = gc & 1, tuse = gc >> 1;
+                if (ok && !mbar_wait(smem_u32(&tfull[t]), tuse & 1)) ok = false;
+                if (!ok) continue;
+                fence_after();
+                const uint32_t base = tmem + t * 256 + lane_off + half * 32;
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    acc_re[q * 16 + j] += __uint_as_float(r0[j]) - __uint_as_float(r3[j]);
-                    acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r2[j]);
-                }
-            }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
-        }
-        if (KIND == kFP16) {
-            // undo the operands' power-of-two scales (exact)
-            const int e = fp16s_exponent(__uint_as_float(p.scales[0])) + fp16s_exponent(__uint_as_float(p.scales[1]));
+                for (int q = 0; q < 2; q++) {
+                    uint32_t r0[16], r1[16], r2[16], r3[16];
+                    tmem_ld16(base + q * 16, r0);        // P left:  A_re B_re
+                    tmem_ld16(base + 64 + q * 16, r1);   // P right: A_re B_im
+                    tmem_ld16(base + 128 + q * 16, r2);  // Q left:  A_im B_re
+                    tmem_ld16(base + 192 + q * 16, r3);  // Q right: A_im B_im
+                    tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                acc_re[j] = ldexpf(acc_re[j], e);
-                acc_im[j] = ldexpf(acc_im[j], e);
-            }
-        }
-        const int64_t m = m0 + lg * 32 + lane;
-        float2 *Ch = p.C + (int64_t)h * p.sCh;
-        if (p.ksplit > 1) {
-            // partial K range: add into the zeroed output
-            if (ok && m < p.M && n_chunks > 0) {
-#pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const int64_t n = n0 + half * 32 + j;
-                    if (n < p.N) atomicAdd(Ch + m * p.sCm + n * p.sCn, make_float2(acc_re[j], acc_im[j]));
-                }
-            }
-        } else {
-            // stage the 128 x 64 tile in shared memory (the TMA ring is idle:
-            // every load was consumed and every MMA has completed), then
-            // write whole rows: a warp stores one 512-byte row per instruction
-            constexpr int RS = 66;  // row stride in float2, 16-byte aligned
-            float2 *cs = reinterpret_cast<float2 *>(smem);
-            const int r = lg * 32 + lane;
-#pragma unroll
-            for (int j = 0; j < 32; j++) cs[r * RS + half * 32 + j] = make_float2(acc_re[j], acc_im[j]);
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            if (ok) {
-                for (int rr = fw; rr < TM; rr += kFlushWarps) {
-                    const int64_t mm = m0 + rr;
-                    if (mm >= p.M) break;
-                    const int64_t n = n0 + 2 * lane;
-                    float2 *dst = Ch + mm * p.sCm;
-                    if (p.sCn == 1 && n + 1 < p.N) {
-                        const float4 v = *reinterpret_cast<const float4 *>(cs + rr * RS + 2 * lane);
-                        *reinterpret_cast<float4 *>(dst + n) = v;
-                    } else {
-                        if (n < p.N) dst[n * p.sCn] = cs[rr * RS + 2 * lane];
-                        if (n + 1 < p.N) dst[(n + 1) * p.sCn] = cs[rr * RS + 2 * lane + 1];
+                    for (int j = 0; j < 16; j++) {
+                        acc_re[q * 16 + j] += __uint_as_float(r0[j]) - __uint_as_float(r3[j]);
+                        acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r2[j]);
                     }
                 }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
+            }
+            if (KIND == kFP16) {
+                // undo the operands' power-of-two scales (exact)
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    acc_re[j] = ldexpf(acc_re[j], e_scale);
+                    acc_im[j] = ldexpf(acc_im[j], e_scale);
+                }
+            }
+            float2 *Ch = p.C + (int64_t)tc.h * p.sCh;
+            if (p.ksplit > 1) {
+                // partial K range: add into the zeroed output
+                const int64_t m = tc.m0 + lg * 32 + lane;
+                if (ok && m < p.M && n_chunks > 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int64_t n = tc.n0 + half * 32 + j;
+                        if (n < p.N) atomicAdd(Ch + m * p.sCm + n * p.sCn, make_float2(acc_re[j], acc_im[j]));
+                    }
+                }
+                continue;
+            }
+            // stage half a tile (64 rows) at a time, then write whole rows: a
+            // warp stores one 512-byte row per instruction
+            constexpr int RS = R::kOutRS;
+#pragma unroll
+            for (int hp = 0; hp < 2; hp++) {
+                if ((lg >> 1) == hp) {
+                    const int r = (lg & 1) * 32 + lane;
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        stage_out[r * RS + half * 32 + j] = make_float2(acc_re[j], acc_im[j]);
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                for (int rr = fw; ok && rr < TM / 2; rr += kFlushWarps) {
+                    const int64_t mm = tc.m0 + hp * (TM / 2) + rr;
+                    if (mm >= p.M) break;
+                    const int64_t n = tc.n0 + 2 * lane;
+                    float2 *dst = Ch + mm * p.sCm;
+                    if (p.sCn == 1 && n + 1 < p.N) {
+                        const float4 v = *reinterpret_cast<const float4 *>(stage_out + rr * RS + 2 * lane);
+                        *reinterpret_cast<float4 *>(dst + n) = v;
+                    } else {
+                        if (n < p.N) dst[n * p.sCn] = stage_out[rr * RS + 2 * lane];
+                        if (n + 1 < p.N) dst[(n + 1) * p.sCn] = stage_out[rr * RS + 2 * lane + 1];
+                    }
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
             }
         }
     }
@@ -480,13 +572,26 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.scales = g.scales;
     if (g.form == TN_FP16S && !g.scales) return cudaErrorInvalidValue;
     const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
-    if (gm > 65535 || g.a.H * p.ksplit > 65535) return cudaErrorInvalidConfiguration;
+    if (gm > INT32_MAX || gn > INT32_MAX) return cudaErrorInvalidConfiguration;
+    p.gm = (int)gm;
+    p.gn = (int)gn;
+    p.tiles = gm * gn * g.a.H * p.ksplit;
     if (p.ksplit > 1) {
         // C = [H][M][N] contiguous (the plan's GEMM output layout)
         cudaError_t e = cudaMemsetAsync(g.a.C, 0, (size_t)(g.a.H * g.a.M * g.a.N) * sizeof(float2), s);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((unsigned)gn, (unsigned)gm, (unsigned)(g.a.H * p.ksplit));
+    // persistent: one CTA per SM (the ring and staging fill the SM's shared
+    // memory), at most one per tile
+    static int sm_count[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (sm_count[dev] == 0) {
+        cudaError_t e = cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)(p.tiles < sm_count[dev] ? p.tiles : sm_count[dev]));
     if (g.form == TN_TF32X3)
         return g.chunk_bytes == 64 ? launch_variant<kTF32, 64>(g, p, grid, s) : launch_variant<kTF32, 128>(g, p, grid, s);
     if (g.form == TN_BF16X3)
