@@ -247,7 +247,7 @@ def run_native(args):
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
     tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
     n_slices = 1 << len(sliced)
-    forms = [args.form] if args.form != "all" else ["fp32", "tf32x3", "bf16x3", "fp16s"]
+    forms = [args.form] if args.form != "all" else ["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"]
     golden = load_golden_amplitudes() if rank == 0 and instance_seed_offset(rank) == 0 else None
     stream = torch.cuda.Stream()
     flush = l2_flush_buffer(torch)
@@ -314,8 +314,8 @@ def run_native(args):
             # split form: tensor-core flops the method issues per complex MAC
             # (4 real products x 3 split products x 2 flops); TF32 peak = half
             # of the measured BF16 peak (nominal dense ratio 1.1 : 2.25)
-            per_mac = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16s": 8.0}[form]  # fp16s: 4 real products
-            peak = pk["bf16_tflops"] * ({"bf16x3": 1.0, "tf32x3": 0.5, "fp16s": 1.0}[form])
+            per_mac = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16x3": 24.0, "fp16s": 8.0}[form]  # fp16s: 4 products
+            peak = pk["bf16_tflops"] * ({"bf16x3": 1.0, "tf32x3": 0.5, "fp16x3": 1.0, "fp16s": 1.0}[form])
             achieved = per_mac * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None, "kernel": "tc_gemm (tcgen05 split form)",
@@ -374,7 +374,8 @@ def run_native(args):
         "metric": METRIC, "value": r["slices_per_s"], "unit": "slices/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)",
-                                       "tf32x3": "tf32x3", "fp16s": "f16"}[best],
+                                       "tf32x3": "tf32x3", "fp16x3": "fp16x3 (scaled, fp32 accumulate)",
+                                       "fp16s": "f16"}[best],
         "data": "synthetic (seeded Sycamore-style circuit, random bitstring)",
         "config": {"workload": "rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 22 fixed, "
                                "2^8 slices over 8 searched bonds", "form": best,
@@ -409,7 +410,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16s", "all"])
+    ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "all"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
     args = ap.parse_args()

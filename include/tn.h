@@ -57,7 +57,9 @@ typedef enum {
     TN_FP32 = 0,   /* complex64 operands, FP32 CUDA-core complex products (reference form) */
     TN_BF16X3 = 1, /* operands split into bf16 hi/lo, three products per real product, tensor cores, FP32 accumulate */
     TN_TF32X3 = 2, /* tf32 hi/lo split, three products per real product, tensor cores */
-    TN_FP16S = 3   /* fp16 with per-tensor power-of-two scale, tensor cores */
+    TN_FP16S = 3,  /* fp16 with per-tensor power-of-two scale, tensor cores */
+    TN_FP16X3 = 4  /* per-tensor power-of-two scale, then an fp16 hi/lo split, three products per real
+                      product, tensor cores, FP32 accumulate (about the TF32x3 precision at the fp16 rate) */
 } tn_form;
 
 typedef struct {
@@ -183,7 +185,7 @@ int tn_plan_update_data(tn_plan_t plan, const float *data, tn_stream_t stream);
  * tn_contract_slices call is bracketed by CUDA events and the call
  * synchronises; durations accumulate per op.  Writes up to max_rows rows of 12
  * doubles: {phase (0 slice-invariant prologue, 1 per slice block), op index,
- * kind (0 small step, 1 permute, 2 GEMM, 3 extract, 4 FP64 sum, 5 hi/lo split, 6 FP16S max-abs), tree step,
+ * kind (0 small step, 1 permute, 2 GEMM, 3 extract, 4 FP64 sum, 5 hi/lo split, 6 max-abs of a scaled form), tree step,
  * total ms, launches, complex MACs per launch, algorithmic bytes per launch,
  * shape[4]} with shape = {H, M, N, K} for a GEMM, {H, rows, 0, K} for a split,
  * {batch bits, rows, 2^N, 2^K} for a small step, {0, elements, 0, 0} for a permute

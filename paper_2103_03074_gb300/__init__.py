@@ -21,8 +21,8 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-TN_FP32, TN_BF16X3, TN_TF32X3, TN_FP16S = 0, 1, 2, 3
-FORMS = {"fp32": TN_FP32, "bf16x3": TN_BF16X3, "tf32x3": TN_TF32X3, "fp16s": TN_FP16S}
+TN_FP32, TN_BF16X3, TN_TF32X3, TN_FP16S, TN_FP16X3 = 0, 1, 2, 3, 4
+FORMS = {"fp32": TN_FP32, "bf16x3": TN_BF16X3, "tf32x3": TN_TF32X3, "fp16s": TN_FP16S, "fp16x3": TN_FP16X3}
 ERRORS = {-1: "TN_ERR_ARG", -2: "TN_ERR_OOM", -3: "TN_ERR_CUDA", -4: "TN_ERR_TIMEOUT", -5: "TN_ERR_STATE"}
 
 _vp = ctypes.c_void_p

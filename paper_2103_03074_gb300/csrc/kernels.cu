@@ -135,6 +135,15 @@ __device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, flo
         __half *P = reinterpret_cast<__half *>(a.out);
         P[d] = __float2half_rn(ldexpf(v.x, -e));
         P[d + a.plane_stride] = __float2half_rn(ldexpf(v.y, -e));
+    } else if (a.mode == 4) {
+        const int e = fp16s_exponent(__uint_as_float(*a.scale));
+        __half *P = reinterpret_cast<__half *>(a.out);
+        const float xr = ldexpf(v.x, -e), xi = ldexpf(v.y, -e);  // exact (power of two)
+        const __half rh = __float2half_rn(xr), ih = __float2half_rn(xi);
+        P[d] = rh;
+        P[d + a.plane_stride] = ih;
+        P[d + 2 * a.plane_stride] = __float2half_rn(xr - __half2float(rh));
+        P[d + 3 * a.plane_stride] = __float2half_rn(xi - __half2float(ih));
     } else {
         uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
         const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);

@@ -41,7 +41,9 @@ struct SmallArgs {
 //           in 32 bits (2) at d + q * plane_stride, q = 0..3;
 // mode 3:   two fp16 planes (re, im) of x * 2^-e, e = ilogb(max|x|) - 13 from
 //           the max-abs slot `scale` (a float stored as its bits), so the
-//           largest scaled value lies in [2^13, 2^14).
+//           largest scaled value lies in [2^13, 2^14);
+// mode 4:   four fp16 planes (re_hi, im_hi, re_lo, im_lo) of the same scaled
+//           value: hi = fp16(x 2^-e), lo = fp16(x 2^-e - hi).
 // The tile holds the bits at the source's and the destination's lowest
 // positions, so reads and writes are both coalesced.
 constexpr int kTileMaxBits = 10;

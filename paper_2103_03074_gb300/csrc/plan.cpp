@@ -56,8 +56,13 @@ struct Op {
     int step = -1;
     bool dep = false;
     Operand in0, in1, out;
-    Operand aux;    // FP16S: the pair of max-abs slots (read by splits and the GEMM)
+    Operand aux;    // scaled forms: the pair of max-abs slots (read by splits and the GEMM)
     int aux_idx = 0;  // slot index used by a max-abs op or a scaled split
+    // tensor-core GEMM of a scaled form whose output feeds a scaled split: the
+    // epilogue also writes max |re|, |im| of the output into this slot, in
+    // place of a separate max-abs pass over the output
+    Operand maxout;
+    int maxout_idx = 0;
     SmallArgs small;
     MaxAbsArgs mx;
     BitPermArgs bp;  // permute (mode 0) or fused permute + hi/lo split (OP_SPLIT)
@@ -478,16 +483,28 @@ int64_t compile(tn_plan &P, int nb) {
         if (use_tc) {
             // split both operands into hi/lo planes [q][h][row][k] (fused with
             // their permutation); the tensor-core GEMM reads the planes by TMA.
-            // FP16S: a max-abs pass per operand first picks its power-of-two
-            // scale, and the split writes scaled fp16 planes {re, im}
+            // scaled forms (FP16S, FP16X3): a max-abs pass per operand first
+            // picks its power-of-two scale, and the split writes scaled fp16
+            // planes {re, im} or {re_hi, im_hi, re_lo, im_lo}
             const int es = tc_plane_bytes(P.form), np = tc_plane_count(P.form);
-            const bool scaled = P.form == TN_FP16S;
-            const int mode = scaled ? 3 : (es == 2 ? 1 : 2);
+            const bool scaled = P.form == TN_FP16S || P.form == TN_FP16X3;
+            const int mode = P.form == TN_FP16S ? 3 : P.form == TN_FP16X3 ? 4 : (es == 2 ? 1 : 2);
             Operand slots;
             if (scaled) {
                 slots.buf = new_buf(1);  // two uint32 slots
                 int idx = 0;
                 for (const NodeRec *src : {&A, &B}) {
+                    // an operand written by a tensor-core GEMM without split K
+                    // gets its max from that GEMM's epilogue
+                    Op *prod = nullptr;
+                    if (src->where.buf >= 0)
+                        for (auto &o : ops)
+                            if (o.out.buf == src->where.buf) prod = &o;
+                    if (prod && prod->kind == OP_GEMM && prod->gemm_variant == 1 && prod->tc.ksplit == 1) {
+                        prod->maxout = slots;
+                        prod->maxout_idx = idx++;
+                        continue;
+                    }
                     Op mo;
                     mo.kind = OP_MAXABS;
                     mo.step = t;
@@ -593,6 +610,7 @@ int64_t compile(tn_plan &P, int nb) {
         touch(op.in1, i);
         touch(op.out, i);
         touch(op.aux, i);
+        touch(op.maxout, i);
     }
     for (int i = 0; i < (int)P.batch.size(); i++) {
         Op &op = P.batch[i];
@@ -601,7 +619,9 @@ int64_t compile(tn_plan &P, int nb) {
         touch(op.in1, time);
         touch(op.out, time);
         touch(op.aux, time);
+        touch(op.maxout, time);
         if (op.out.buf >= 0) buf_dep[op.out.buf] = 1;
+        if (op.maxout.buf >= 0) buf_dep[op.maxout.buf] = 1;
     }
     touch(P.root, T_acc);
     // an invariant buffer read inside the block loop lives to the loop's end
@@ -682,6 +702,9 @@ void resolve_all(tn_plan &P) {
                 op.tc.chunk_bytes = P.opts.tc_chunk_bytes;
                 op.tc.flush_bytes = P.opts.tc_flush_bytes;
                 op.tc.scales = op.aux.buf >= 0 ? reinterpret_cast<const unsigned *>(resolve(P, op.aux)) : nullptr;
+                op.tc.max_slot = op.maxout.buf >= 0
+                                     ? reinterpret_cast<unsigned *>(resolve(P, op.maxout)) + op.maxout_idx
+                                     : nullptr;
             } else {
                 op.gemm.A = resolve(P, op.in0);
                 op.gemm.B = resolve(P, op.in1);
@@ -802,7 +825,7 @@ int rank_candidates(const std::vector<std::vector<int32_t>> &labels, const std::
     best = 0;
     pred_ms.assign(cands.size(), 0.0);
     if (!opts.cost_model || cands.empty()) return TN_OK;
-    const tn_form form = (opts.rank_form >= TN_FP32 && opts.rank_form <= TN_FP16S) ? (tn_form)opts.rank_form : TN_FP32;
+    const tn_form form = (opts.rank_form >= TN_FP32 && opts.rank_form <= TN_FP16X3) ? (tn_form)opts.rank_form : TN_FP32;
     std::vector<float> X;
     struct Span { size_t pro0, pro1, bat0, bat1; double blocks; };
     std::vector<Span> spans;
@@ -869,7 +892,7 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
     if (n_open < 0 || n_open > kMaxRank || (n_open > 0 && !open_labels)) return fail(TN_ERR_ARG, "bad open labels");
     if (n_sliced < 0 || n_sliced > 62 || (n_sliced > 0 && !sliced_labels)) return fail(TN_ERR_ARG, "bad sliced labels");
     if (n_steps != n_tensors - 1 || (n_steps > 0 && !tree)) return fail(TN_ERR_ARG, "tree must have n_tensors - 1 steps");
-    if (form < TN_FP32 || form > TN_FP16S) return fail(TN_ERR_ARG, "unknown form");
+    if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
     if (form != TN_FP32 && !tc_form_available(form))
         return fail(TN_ERR_ARG, "this arithmetic form is not available in this build");
     std::unique_ptr<tn_plan> P(new tn_plan());

@@ -1,12 +1,18 @@
 // Split-precision complex GEMM on the 5th-generation tensor cores (tcgen05).
 //
 // C[h, m, n] = sum_k A[h, m, k] B[h, k, n] for complex64 operands with the
-// strided layout of GemmArgs, in two forms:
-//   BF16x3: x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (Henry, Tang &
-//           Heinecke 2019), kind::f16 MMAs, 16 K values per MMA;
-//   TF32x3: hi = tf32(x), lo = tf32(x - hi) (Ootomo & Yokota 2022), kind::tf32
-//           MMAs, 8 K values per MMA.
-// A real product x*y is hi_x hi_y + hi_x lo_y + lo_x hi_y.
+// strided layout of GemmArgs, in four forms:
+//   BF16x3:  x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (Henry, Tang &
+//            Heinecke 2019), kind::f16 MMAs, 16 K values per MMA;
+//   TF32x3:  hi = tf32(x), lo = tf32(x - hi) (Ootomo & Yokota 2022), kind::tf32
+//            MMAs, 8 K values per MMA;
+//   FP16X3:  each operand scaled by a power of two 2^-e so that its largest
+//            |re|, |im| lies in [2^13, 2^14), then hi = fp16(x), lo = fp16(x -
+//            hi): 22 significant bits like TF32x3 at the kind::f16 rate, the
+//            scale keeping hi and (above 2^-3 of it) lo in fp16's normal range;
+//   FP16S:   the scaled value as one fp16 piece.
+// A real product x*y is hi_x hi_y + hi_x lo_y + lo_x hi_y; the scaled forms'
+// results are multiplied back by 2^(eA + eB) in the epilogue (exact).
 //
 // The split of each operand into four K-major planes (re_hi, im_hi, re_lo,
 // im_lo) is done beforehand by the tiled bit-permute kernel, fused with
@@ -61,13 +67,19 @@ constexpr int TM = 128, TN = 64;
 // and FP16S errors are set by their operand pieces, not by the interval, so
 // they read out every 512 bytes.
 constexpr int kDefaultChunkBytes = 128;
-__host__ __device__ constexpr int default_flush_bytes(tn_form f) { return f == TN_TF32X3 ? 256 : 512; }
+__host__ __device__ constexpr int default_flush_bytes(tn_form f) {
+    return (f == TN_TF32X3 || f == TN_FP16X3) ? 256 : 512;
+}
 constexpr int kThreads = 384;  // 12 warps
 constexpr int kFlushWarp0 = 4, kFlushWarps = 8;
 constexpr int kTmemCols = 512;  // 2 sets x {P, Q} x 128 columns
 
 // operand forms of the kernel template
-constexpr int kBF16 = 0, kTF32 = 1, kFP16 = 2;
+constexpr int kBF16 = 0, kTF32 = 1, kFP16 = 2, kFP16X3 = 3;
+// one piece per value (planes re, im) or hi/lo pieces (re_hi, im_hi, re_lo, im_lo)
+__host__ __device__ constexpr bool kind_split(int kind) { return kind != kFP16; }
+// operands carry a per-operand power-of-two scale that the epilogue undoes
+__host__ __device__ constexpr bool kind_scaled(int kind) { return kind == kFP16 || kind == kFP16X3; }
 
 // Shared-memory ring for a K chunk of CB bytes per plane row: NP planes of A
 // (128 rows) and of B (64 rows, so that planes 2j and 2j + 1 form one
@@ -208,7 +220,8 @@ struct GemmTcParams {
     int flush_chunks;  // chunks per accumulator read-out
     int gm, gn;        // M and N tiles
     int64_t tiles;     // gn * gm * H * ksplit
-    const unsigned *scales;  // FP16S: max-abs slots of A and B (float bits)
+    const unsigned *scales;  // scaled forms: max-abs slots of A and B (float bits)
+    unsigned *max_slot;      // optional: atomic max of |re|, |im| over C (float bits)
 };
 
 // tile t -> (n tile, m tile, batch h, K part); N tiles vary fastest
@@ -240,7 +253,7 @@ template <int KIND, int CB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
-    constexpr int NP = KIND == kFP16 ? 2 : 4;
+    constexpr int NP = kind_split(KIND) ? 4 : 2;
     using R = Ring<CB, NP>;
     constexpr int kAPlane = R::kAPlane, kBPlane = R::kBPlane;
     constexpr int kStageBytes = R::kStageBytes, kStages = R::kStages;
@@ -333,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t S = make_desc<CB>(b0 + ko);  // [re | im] of the (hi) piece
                         mma<KIND>(dP, ar, S, ID, acc);
                         mma<KIND>(dQ, ai, S, ID, acc);
-                        if (KIND != kFP16) {
+                        if (kind_split(KIND)) {
                             // corrections hi*lo + lo*hi into the same sums
                             const uint64_t arl = make_desc<CB>(a0 + 2 * kAPlane + ko);
                             const uint64_t ail = make_desc<CB>(a0 + 3 * kAPlane + ko);
@@ -361,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int lg = warp & 3, half = fw >> 2;  // TMEM lane group, column half
         const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
         int e_scale = 0;
-        if (KIND == kFP16)
+        if (kind_scaled(KIND))
             e_scale = fp16s_exponent(__uint_as_float(p.scales[0])) + fp16s_exponent(__uint_as_float(p.scales[1]));
         // every flush warp walks every tile of this CTA and reaches the same
         // named barriers even after a failed wait (it then skips waits,
@@ -400,13 +413,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
             }
-            if (KIND == kFP16) {
+            if (kind_scaled(KIND)) {
                 // undo the operands' power-of-two scales (exact)
 #pragma unroll
                 for (int j = 0; j < 32; j++) {
                     acc_re[j] = ldexpf(acc_re[j], e_scale);
                     acc_im[j] = ldexpf(acc_im[j], e_scale);
                 }
+            }
+            if (p.max_slot && ok) {
+                // max |re|, |im| of the tile (rows and columns past the edge
+                // hold zeros: their operand rows were zero-filled); non-negative
+                // floats order like their bit patterns
+                float mx = 0.f;
+#pragma unroll
+                for (int j = 0; j < 32; j++) mx = fmaxf(mx, fmaxf(fabsf(acc_re[j]), fabsf(acc_im[j])));
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                if (lane == 0) atomicMax(p.max_slot, __float_as_uint(mx));
             }
             float2 *Ch = p.C + (int64_t)tc.h * p.sCh;
             if (p.ksplit > 1) {
@@ -499,7 +523,7 @@ bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int6
 }  // namespace
 
 bool tc_form_available(tn_form form) {
-    return (form == TN_BF16X3 || form == TN_TF32X3 || form == TN_FP16S) && encode_fn() != nullptr;
+    return (form == TN_BF16X3 || form == TN_TF32X3 || form == TN_FP16S || form == TN_FP16X3) && encode_fn() != nullptr;
 }
 
 int tc_plane_bytes(tn_form form) { return form == TN_TF32X3 ? 4 : 2; }
@@ -541,7 +565,7 @@ bool tc_prepare(TcGemm &g) {
 
 template <int KIND, int CB>
 cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
-    constexpr int NP = KIND == kFP16 ? 2 : 4;
+    constexpr int NP = kind_split(KIND) ? 4 : 2;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<KIND, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -570,7 +594,13 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.flush_chunks = g.flush_bytes / g.chunk_bytes;
     if (p.flush_chunks < 1) p.flush_chunks = 1;
     p.scales = g.scales;
-    if (g.form == TN_FP16S && !g.scales) return cudaErrorInvalidValue;
+    p.max_slot = g.max_slot;
+    if (g.max_slot) {
+        if (p.ksplit > 1) return cudaErrorInvalidValue;  // partial tiles: their max is not C's
+        cudaError_t e = cudaMemsetAsync(g.max_slot, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
+    if ((g.form == TN_FP16S || g.form == TN_FP16X3) && !g.scales) return cudaErrorInvalidValue;
     const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
     if (gm > INT32_MAX || gn > INT32_MAX) return cudaErrorInvalidConfiguration;
     p.gm = (int)gm;
@@ -596,6 +626,9 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
         return g.chunk_bytes == 64 ? launch_variant<kTF32, 64>(g, p, grid, s) : launch_variant<kTF32, 128>(g, p, grid, s);
     if (g.form == TN_BF16X3)
         return g.chunk_bytes == 64 ? launch_variant<kBF16, 64>(g, p, grid, s) : launch_variant<kBF16, 128>(g, p, grid, s);
+    if (g.form == TN_FP16X3)
+        return g.chunk_bytes == 64 ? launch_variant<kFP16X3, 64>(g, p, grid, s)
+                                   : launch_variant<kFP16X3, 128>(g, p, grid, s);
     return g.chunk_bytes == 64 ? launch_variant<kFP16, 64>(g, p, grid, s) : launch_variant<kFP16, 128>(g, p, grid, s);
 }
 

@@ -17,7 +17,8 @@ struct TcGemm {
     int ksplit;       // K partitions over CTAs (1: none)
     int chunk_bytes;  // K chunk per TMA stage and plane row: 64 or 128 (0: default)
     int flush_bytes;  // bytes of K between accumulator read-outs (multiple of chunk_bytes; 0: default)
-    const unsigned *scales;  // FP16S: device max-abs slots of A and B (float bits)
+    const unsigned *scales;  // FP16S / FP16X3: device max-abs slots of A and B (float bits)
+    unsigned *max_slot;      // optional: receives max |re|, |im| of C (float bits; zeroed by the launch)
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
 };
@@ -30,7 +31,7 @@ bool tc_form_available(tn_form form);
 int tc_plane_bytes(tn_form form);
 
 // planes per operand: 4 for the hi/lo split forms (re_hi, im_hi, re_lo,
-// im_lo), 2 for FP16S (re, im)
+// im_lo: BF16x3, TF32x3, FP16X3), 2 for FP16S (re, im)
 int tc_plane_count(tn_form form);
 
 // K bytes between accumulator read-outs when TcGemm::flush_bytes is 0: the

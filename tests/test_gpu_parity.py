@@ -181,7 +181,7 @@ def load_golden(name):
     return np.array(vals)
 
 
-@pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16x3", "fp16s"])
+@pytest.mark.parametrize("form", ["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"])
 def test_cfg2_amplitudes_vs_golden(tn, form):
     """The 30-qubit workload exactly as the benchmark plans it: 8 sliced bonds
     from the order search (16384 trials), all 2^8 slices in one batch."""

@@ -81,6 +81,30 @@ def emulate_fp16s_4m(a, b):
     return ((ar @ br - ai @ bi) + 1j * (ar @ bi + ai @ br)) * 2.0 ** (ea + eb)
 
 
+def emulate_fp16x3_4m(a, b):
+    """Scaled FP16 hi/lo form: each operand scaled by 2^-e as in the FP16S
+    form, hi = fp16(x), lo = fp16(x - hi) (round to nearest, subnormals
+    kept), hi*hi + hi*lo + lo*hi per real product, four real products
+    accumulated exactly, result scaled back by 2^(eA + eB)."""
+    def scaled(x):
+        mx = max(np.abs(x.real).max(), np.abs(x.imag).max())
+        e = np.frexp(np.float32(mx))[1] - 14
+        xs = x.astype(np.complex64) * np.float32(2.0 ** -e)
+
+        def parts(v):
+            v = np.asarray(v, np.float32)
+            h = v.astype(np.float16)
+            lo = (v - h.astype(np.float32)).astype(np.float16)
+            return h.astype(np.float64), lo.astype(np.float64)
+        return parts(xs.real), parts(xs.imag), e
+
+    def rmm(x, y):
+        return x[0] @ y[0] + x[0] @ y[1] + x[1] @ y[0]
+    ar, ai, ea = scaled(a)
+    br, bi, eb = scaled(b)
+    return ((rmm(ar, br) - rmm(ai, bi)) + 1j * (rmm(ar, bi) + rmm(ai, br))) * 2.0 ** (ea + eb)
+
+
 def rand_c64(seed, shape):
     rng = np.random.default_rng(seed)
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
@@ -112,8 +136,9 @@ def test_single_gemm_bf16x3(tn, m, k, n, a_kfirst, b_nfirst):
     open_l = ml + nl
     exact = A.astype(np.complex128) @ B.astype(np.complex128)
     emu = {"bf16x3": emulate_split_4m(A, B, bf16), "tf32x3": emulate_split_4m(A, B, tf32),
-           "fp16s": emulate_fp16s_4m(A, B)}
-    for form, tol_exact in (("fp32", 2e-6), ("bf16x3", 1e-5), ("tf32x3", 1e-6), ("fp16s", 2e-3)):
+           "fp16s": emulate_fp16s_4m(A, B), "fp16x3": emulate_fp16x3_4m(A, B)}
+    for form, tol_exact in (("fp32", 2e-6), ("bf16x3", 1e-5), ("tf32x3", 1e-6), ("fp16x3", 1e-6),
+                            ("fp16s", 2e-3)):
         plan = tn.Plan([la, lb], [ta, tb], open_l, [], [(0, 1)], form=form)
         amp = torch.zeros(2 * M * N, dtype=torch.float64, device="cuda")
         plan.contract(0, 1, amp)
@@ -128,7 +153,7 @@ def test_single_gemm_bf16x3(tn, m, k, n, a_kfirst, b_nfirst):
         plan.close()
 
 
-@pytest.mark.parametrize("form", ["bf16x3", "tf32x3", "fp16s"])
+@pytest.mark.parametrize("form", ["bf16x3", "tf32x3", "fp16x3", "fp16s"])
 def test_batched_gemm_split(tn, form):
     """A sliced label shared by both operands becomes a batch label of the
     GEMM when the slices run as one batch."""
