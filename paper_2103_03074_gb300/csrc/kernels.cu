@@ -120,46 +120,97 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
-__device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, float2 v) {
+// The hi/lo (or scaled) pieces of one complex value for the split modes.
+struct Pieces {
+    uint32_t q[4];  // plane values (16-bit modes in the low half)
+};
+
+__device__ __forceinline__ Pieces split_value(int mode, float2 v, int e) {
+    Pieces r;
+    if (mode == 1) {
+        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+        r.q[0] = __bfloat16_as_ushort(rh);
+        r.q[1] = __bfloat16_as_ushort(ih);
+        r.q[2] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
+        r.q[3] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
+    } else if (mode == 2) {
+        const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
+        r.q[0] = rh;
+        r.q[1] = ih;
+        r.q[2] = tf32_rna(v.x - __uint_as_float(rh));
+        r.q[3] = tf32_rna(v.y - __uint_as_float(ih));
+    } else {  // 3, 4: scaled by 2^-e (exact), then one fp16 piece or hi/lo
+        const float xr = ldexpf(v.x, -e), xi = ldexpf(v.y, -e);
+        const __half rh = __float2half_rn(xr), ih = __float2half_rn(xi);
+        r.q[0] = __half_as_ushort(rh);
+        r.q[1] = __half_as_ushort(ih);
+        r.q[2] = __half_as_ushort(__float2half_rn(xr - __half2float(rh)));
+        r.q[3] = __half_as_ushort(__float2half_rn(xi - __half2float(ih)));
+    }
+    return r;
+}
+
+__device__ __forceinline__ int mode_planes(int mode) { return mode == 3 ? 2 : 4; }
+
+// one destination element
+__device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, float2 v, int e) {
     if (a.mode == 0) {
         reinterpret_cast<float2 *>(a.out)[d] = v;
-    } else if (a.mode == 1) {
+        return;
+    }
+    const Pieces pc = split_value(a.mode, v, e);
+    const int np = mode_planes(a.mode);
+    if (a.mode == 2) {
+        uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
+        for (int q = 0; q < np; q++) P[d + q * a.plane_stride] = pc.q[q];
+    } else {
         uint16_t *P = reinterpret_cast<uint16_t *>(a.out);
-        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-        P[d] = __bfloat16_as_ushort(rh);
-        P[d + a.plane_stride] = __bfloat16_as_ushort(ih);
-        P[d + 2 * a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
-        P[d + 3 * a.plane_stride] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
-    } else if (a.mode == 3) {
-        const int e = fp16s_exponent(__uint_as_float(*a.scale));
-        __half *P = reinterpret_cast<__half *>(a.out);
-        P[d] = __float2half_rn(ldexpf(v.x, -e));
-        P[d + a.plane_stride] = __float2half_rn(ldexpf(v.y, -e));
-    } else if (a.mode == 4) {
-        const int e = fp16s_exponent(__uint_as_float(*a.scale));
-        __half *P = reinterpret_cast<__half *>(a.out);
-        const float xr = ldexpf(v.x, -e), xi = ldexpf(v.y, -e);  // exact (power of two)
-        const __half rh = __float2half_rn(xr), ih = __float2half_rn(xi);
-        P[d] = rh;
-        P[d + a.plane_stride] = ih;
-        P[d + 2 * a.plane_stride] = __float2half_rn(xr - __half2float(rh));
-        P[d + 3 * a.plane_stride] = __float2half_rn(xi - __half2float(ih));
+        for (int q = 0; q < np; q++) P[d + q * a.plane_stride] = (uint16_t)pc.q[q];
+    }
+}
+
+// destination elements d and d + 1 (d even): one vector store per plane
+__device__ __forceinline__ void store_pair(const BitPermArgs &a, uint64_t d, float2 v0, float2 v1, int e) {
+    if (a.mode == 0) {
+        reinterpret_cast<float4 *>(a.out)[d >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
+        return;
+    }
+    const Pieces p0 = split_value(a.mode, v0, e), p1 = split_value(a.mode, v1, e);
+    const int np = mode_planes(a.mode);
+    if (a.mode == 2) {
+        uint2 *P = reinterpret_cast<uint2 *>(a.out);
+        for (int q = 0; q < np; q++) P[(d + q * a.plane_stride) >> 1] = make_uint2(p0.q[q], p1.q[q]);
     } else {
         uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
-        const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
-        P[d] = rh;
-        P[d + a.plane_stride] = ih;
-        P[d + 2 * a.plane_stride] = tf32_rna(v.x - __uint_as_float(rh));
-        P[d + 3 * a.plane_stride] = tf32_rna(v.y - __uint_as_float(ih));
+        for (int q = 0; q < np; q++) P[(d + q * a.plane_stride) >> 1] = p0.q[q] | (p1.q[q] << 16);
     }
 }
 
 // Each CTA builds the tile's offset tables once, then walks tiles two at a
-// time (two independent read batches in flight per thread).
+// time (two independent read batches in flight per thread).  Source bit 0
+// and destination bit 0 are always tile bits (the first read-order and the
+// first write-order bit), so with aligned buffers a thread moves two
+// neighbouring elements per load and per store.
 __global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) {
     constexpr int T = 1 << kTileMaxBits;
     __shared__ float2 buf[2][T];
     __shared__ uint32_t src_off[T], w_of[T], dst_off[T];
+    // the rest index scattered 6 bits at a time through lookup tables
+    constexpr int kChunk = 6, kChunks = (kMaxRank + kChunk - 1) / kChunk;
+    __shared__ uint64_t rest_tab[2][kChunks][1 << kChunk];
+    const int n_chunk = (a.n_rest + kChunk - 1) / kChunk;
+    for (int i = threadIdx.x; i < n_chunk << kChunk; i += blockDim.x) {
+        const int c = i >> kChunk, v = i & ((1 << kChunk) - 1);
+        const int nb = min(kChunk, a.n_rest - c * kChunk);
+        uint64_t so = 0, d = 0;
+        for (int j = 0; j < nb; j++) {
+            const uint64_t b = (uint64_t)((v >> j) & 1);
+            so |= b << a.rest_src[c * kChunk + j];
+            d |= b << a.rest_dst[c * kChunk + j];
+        }
+        rest_tab[0][c][v] = so;
+        rest_tab[1][c][v] = d;
+    }
     const int tile = 1 << a.n_tile;
     for (int e = threadIdx.x; e < tile; e += blockDim.x) {
         uint32_t w = 0, so = 0, d = 0;
@@ -173,24 +224,52 @@ __global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) 
         w_of[e] = w;
         dst_off[e] = d;
     }
+    const int es = a.mode >= 3 ? fp16s_exponent(__uint_as_float(*a.scale)) : 0;
     __syncthreads();
     const int64_t n_rest = 1ll << a.n_rest;
+    const int half = tile >> 1;
     for (int64_t r0 = 2 * (int64_t)blockIdx.x; r0 < n_rest; r0 += 2 * (int64_t)gridDim.x) {
         const int nr = (r0 + 1 < n_rest) ? 2 : 1;
         uint64_t s_rest[2], d_rest[2];
         for (int q = 0; q < nr; q++) {
-            s_rest[q] = scatter_bits((uint64_t)(r0 + q), a.rest_src, a.n_rest);
-            d_rest[q] = scatter_bits((uint64_t)(r0 + q), a.rest_dst, a.n_rest);
+            s_rest[q] = d_rest[q] = 0;
+            const uint64_t rr = (uint64_t)(r0 + q);
+            for (int c = 0; c < n_chunk; c++) {
+                const int v = (int)((rr >> (c * kChunk)) & ((1 << kChunk) - 1));
+                s_rest[q] |= rest_tab[0][c][v];
+                d_rest[q] |= rest_tab[1][c][v];
+            }
         }
-        for (int e = threadIdx.x; e < tile; e += blockDim.x) {
-            const uint32_t so = src_off[e], w = w_of[e];
-            const float2 v0 = a.in[s_rest[0] | so];
-            if (nr == 2) buf[1][w] = a.in[s_rest[1] | so];
-            buf[0][w] = v0;
+        if (a.pair_rd) {
+            for (int e2 = threadIdx.x; e2 < half; e2 += blockDim.x) {
+                const uint32_t so = src_off[2 * e2];
+                const uint32_t w0 = w_of[2 * e2], w1 = w_of[2 * e2 + 1];
+                const float4 v0 = reinterpret_cast<const float4 *>(a.in)[(s_rest[0] | so) >> 1];
+                if (nr == 2) {
+                    const float4 v1 = reinterpret_cast<const float4 *>(a.in)[(s_rest[1] | so) >> 1];
+                    buf[1][w0] = make_float2(v1.x, v1.y);
+                    buf[1][w1] = make_float2(v1.z, v1.w);
+                }
+                buf[0][w0] = make_float2(v0.x, v0.y);
+                buf[0][w1] = make_float2(v0.z, v0.w);
+            }
+        } else {
+            for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+                const uint32_t so = src_off[e], w = w_of[e];
+                const float2 v0 = a.in[s_rest[0] | so];
+                if (nr == 2) buf[1][w] = a.in[s_rest[1] | so];
+                buf[0][w] = v0;
+            }
         }
         __syncthreads();
-        for (int q = 0; q < nr; q++)
-            for (int e = threadIdx.x; e < tile; e += blockDim.x) store_elem(a, d_rest[q] | dst_off[e], buf[q][e]);
+        if (a.pair_wr) {
+            for (int q = 0; q < nr; q++)
+                for (int e2 = threadIdx.x; e2 < half; e2 += blockDim.x)
+                    store_pair(a, d_rest[q] | dst_off[2 * e2], buf[q][2 * e2], buf[q][2 * e2 + 1], es);
+        } else {
+            for (int q = 0; q < nr; q++)
+                for (int e = threadIdx.x; e < tile; e += blockDim.x) store_elem(a, d_rest[q] | dst_off[e], buf[q][e], es);
+        }
         __syncthreads();
     }
 }
@@ -375,7 +454,15 @@ cudaError_t launch_small(const SmallArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_bitperm(const BitPermArgs &a, cudaStream_t s) {
+cudaError_t launch_bitperm(const BitPermArgs &args, cudaStream_t s) {
+    BitPermArgs a = args;
+    // pairs of neighbouring elements: source / destination bit 0 lies in the
+    // tile (always, for rank >= 1); vector accesses need 16-byte aligned input
+    // (leaf tensors can start at odd element offsets) and an aligned output
+    const uintptr_t in = reinterpret_cast<uintptr_t>(a.in), out = reinterpret_cast<uintptr_t>(a.out);
+    const bool tile_ok = a.n_tile >= 1 && a.rd_src[0] == 0 && a.tile_dst[0] == 0;
+    a.pair_rd = tile_ok && (in % 16) == 0;
+    a.pair_wr = tile_ok && (out % 16) == 0 && (a.mode == 0 || (a.plane_stride % 2) == 0);
     const int64_t pairs = ((1ll << a.n_rest) + 1) / 2;
     const int grid = (int)(pairs < kMaxBlocks ? pairs : kMaxBlocks);
     bitperm_kernel<<<grid, kThreads, 0, s>>>(a);

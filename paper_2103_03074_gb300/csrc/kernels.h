@@ -60,7 +60,8 @@ struct BitPermArgs {
     int n_rest;                      // remaining bits (grid-strided)
     int rest_dst[kMaxRank];
     int rest_src[kMaxRank];
-    const unsigned *scale;           // mode 3: max-abs slot of the operand
+    const unsigned *scale;           // modes 3, 4: max-abs slot of the operand
+    int pair_rd, pair_wr;            // set by the launcher: two neighbouring elements per access
 };
 
 // max over |re|, |im| of n complex values into *slot (float bits; the

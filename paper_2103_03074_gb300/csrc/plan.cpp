@@ -138,9 +138,23 @@ BitPermArgs make_bitperm(const std::vector<int32_t> &src, const std::vector<int3
     const int nt = std::min(kTileMaxBits, r);
     std::vector<char> in_tile(r, 0);
     int cnt = 0;
-    for (int i = 0; i < r && cnt < nt; i++) {
-        if (!in_tile[i]) { in_tile[i] = 1; cnt++; }
-        if (cnt < nt && !in_tile[dst_of_src[i]]) { in_tile[dst_of_src[i]] = 1; cnt++; }
+    auto add = [&](int p) {
+        if (p < r && cnt < nt && !in_tile[p]) { in_tile[p] = 1; cnt++; }
+    };
+    // first the low destination bits of a 128-byte store run per plane (16
+    // elements of complex64, 32 of a 32-bit plane, 64 of a 16-bit plane) and
+    // the low source bits of a 128-byte load run (16 complex64 elements),
+    // then destination and source bits alternately
+    const int d_need = mode == 0 ? 4 : (mode == 2 ? 5 : 6), s_need = 4;
+    int i_d = 0, i_s = 0;
+    while (cnt < nt && (i_d < d_need || i_s < s_need)) {
+        if (i_d < d_need) add(i_d++);
+        if (i_s < s_need && i_s < r) add(dst_of_src[i_s++]);
+        else if (i_s < s_need) i_s = s_need;
+    }
+    for (; cnt < nt && (i_d < r || i_s < r);) {
+        if (i_d < r) add(i_d++);
+        if (i_s < r) add(dst_of_src[i_s++]);
     }
     std::vector<int> tile;
     for (int p = 0; p < r; p++) {
