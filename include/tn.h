@@ -81,8 +81,13 @@ typedef struct {
      * tensor-memory accumulators into FP32 registers (a multiple of it) */
     int32_t tc_chunk_bytes;
     int32_t tc_flush_bytes;
+    /* 0 (default) or 1: a tensor-core GEMM of the BF16x3 / TF32x3 forms whose
+     * output feeds the next step's hi/lo split writes that split's planes
+     * itself (in the next step's layout) when its epilogue writes stay
+     * coalesced, instead of complex64 output plus a split pass; -1: off */
+    int32_t tc_planar;
     /* reserved, set to 0 */
-    int32_t reserved[6];
+    int32_t reserved[5];
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

@@ -114,44 +114,6 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
 }
 
 // ------------------------------------------------------- tiled bit permute
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// The hi/lo (or scaled) pieces of one complex value for the split modes.
-struct Pieces {
-    uint32_t q[4];  // plane values (16-bit modes in the low half)
-};
-
-__device__ __forceinline__ Pieces split_value(int mode, float2 v, int e) {
-    Pieces r;
-    if (mode == 1) {
-        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-        r.q[0] = __bfloat16_as_ushort(rh);
-        r.q[1] = __bfloat16_as_ushort(ih);
-        r.q[2] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
-        r.q[3] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
-    } else if (mode == 2) {
-        const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
-        r.q[0] = rh;
-        r.q[1] = ih;
-        r.q[2] = tf32_rna(v.x - __uint_as_float(rh));
-        r.q[3] = tf32_rna(v.y - __uint_as_float(ih));
-    } else {  // 3, 4: scaled by 2^-e (exact), then one fp16 piece or hi/lo
-        const float xr = ldexpf(v.x, -e), xi = ldexpf(v.y, -e);
-        const __half rh = __float2half_rn(xr), ih = __float2half_rn(xi);
-        r.q[0] = __half_as_ushort(rh);
-        r.q[1] = __half_as_ushort(ih);
-        r.q[2] = __half_as_ushort(__float2half_rn(xr - __half2float(rh)));
-        r.q[3] = __half_as_ushort(__float2half_rn(xi - __half2float(ih)));
-    }
-    return r;
-}
-
-__device__ __forceinline__ int mode_planes(int mode) { return mode == 3 ? 2 : 4; }
-
 // one destination element
 __device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, float2 v, int e) {
     if (a.mode == 0) {

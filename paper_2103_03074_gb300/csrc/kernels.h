@@ -5,6 +5,10 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#ifdef __CUDACC__
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#endif
 
 namespace tn {
 
@@ -80,6 +84,50 @@ __host__ __device__ inline int fp16s_exponent(float maxabs) {
     frexpf(maxabs, &ex);  // maxabs in [2^(ex-1), 2^ex)
     return ex - 14;
 }
+
+#ifdef __CUDACC__
+// round to nearest (ties away) on tf32's 10-bit mantissa, in a 32-bit container
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// The pieces of one complex value for the split modes of BitPermArgs
+// (1 bf16 hi/lo, 2 tf32 hi/lo, 3 scaled fp16, 4 scaled fp16 hi/lo), plane
+// order (re_hi, im_hi, re_lo, im_lo); 16-bit pieces in the low half.
+struct Pieces {
+    uint32_t q[4];
+};
+
+__device__ __forceinline__ Pieces split_value(int mode, float2 v, int e) {
+    Pieces r;
+    if (mode == 1) {
+        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+        r.q[0] = __bfloat16_as_ushort(rh);
+        r.q[1] = __bfloat16_as_ushort(ih);
+        r.q[2] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
+        r.q[3] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
+    } else if (mode == 2) {
+        const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
+        r.q[0] = rh;
+        r.q[1] = ih;
+        r.q[2] = tf32_rna(v.x - __uint_as_float(rh));
+        r.q[3] = tf32_rna(v.y - __uint_as_float(ih));
+    } else {  // 3, 4: scaled by 2^-e (exact), then one fp16 piece or hi/lo
+        const float xr = ldexpf(v.x, -e), xi = ldexpf(v.y, -e);
+        const __half rh = __float2half_rn(xr), ih = __float2half_rn(xi);
+        r.q[0] = __half_as_ushort(rh);
+        r.q[1] = __half_as_ushort(ih);
+        r.q[2] = __half_as_ushort(__float2half_rn(xr - __half2float(rh)));
+        r.q[3] = __half_as_ushort(__float2half_rn(xi - __half2float(ih)));
+    }
+    return r;
+}
+
+// planes written by a split mode
+__device__ __forceinline__ int mode_planes(int mode) { return mode == 3 ? 2 : 4; }
+#endif
 
 // Strided batched complex GEMM, all strides in complex elements:
 // C[h sCh + m sCm + n sCn] = sum_k A[h sAh + m sAm + k sAk] B[h sBh + k sBk + n sBn]

@@ -206,7 +206,7 @@ struct tn_plan {
     // stats
     double macs_batch = 0, macs_prologue = 0, bytes_batch = 0, bytes_prologue = 0;
     int launches_batch = 0, launches_prologue = 0;
-    tn_plan_opts opts;
+    tn_plan_opts opts = {};
     // step-timing recorder (profile mode)
     struct ProfRow {
         int phase, idx, kind, step;
@@ -230,6 +230,57 @@ namespace tn {
 namespace {
 
 constexpr int kSmallMaxRank = 12;
+
+// The op of `ops` that writes buffer w.buf (nullptr for a leaf or none).
+Op *producer_of(std::vector<Op> &ops, const Operand &w) {
+    if (w.buf < 0) return nullptr;
+    for (auto &o : ops)
+        if (o.out.buf == w.buf) return &o;
+    return nullptr;
+}
+
+// Is w written by a tensor-core GEMM that could split its own output into
+// the next step's planes (no split K, plain output so far)?
+bool planar_candidate(std::vector<Op> &ops, const Operand &w) {
+    const Op *p = producer_of(ops, w);
+    return p && p->kind == OP_GEMM && p->gemm_variant == 1 && p->tc.ksplit == 1 && p->tc.out.mode == 0;
+}
+
+// Planar epilogue of a producer GEMM whose output (layout src, bit groups
+// h | m | n of nH, nM, nN bits from the top) is written as split planes in
+// layout dst.  Returns false when fewer than min_run low destination bits
+// come from the epilogue's half tile (its writes would not be coalesced).
+bool make_planar(const std::vector<int32_t> &src, const std::vector<int32_t> &dst, int nH, int nM, int nN, int mode,
+                 int min_run, TcPlanarOut &o) {
+    const int r = (int)src.size();
+    if (r != (int)dst.size() || r != nH + nM + nN || nM < 6 || r > kMaxRank) return false;
+    std::memset(&o, 0, sizeof o);
+    o.mode = mode;
+    o.plane_stride = (int64_t)1 << r;
+    o.nH = nH;
+    o.nM = nM;
+    o.nN = nN;
+    std::vector<int> dpos(r);
+    for (int sp = 0; sp < r; sp++) {
+        dpos[sp] = pos_of(dst, src[r - 1 - sp]);
+        if (dpos[sp] < 0) return false;
+    }
+    for (int j = 0; j < nN; j++) o.npos[j] = (int8_t)dpos[j];
+    for (int j = 0; j < nM; j++) o.mpos[j] = (int8_t)dpos[nN + j];
+    for (int j = 0; j < nH; j++) o.hpos[j] = (int8_t)dpos[nN + nM + j];
+    std::vector<std::pair<int, int>> bits;  // (destination position, tile bit)
+    for (int b = 0; b < std::min(6, nN); b++) bits.push_back({o.npos[b], b});
+    for (int b = 0; b < 6; b++) bits.push_back({o.mpos[b], 6 + b});
+    std::sort(bits.begin(), bits.end());
+    o.ntb = (int)bits.size();
+    int run = 0;
+    for (int k = 0; k < o.ntb; k++) {
+        o.tb[k] = (int8_t)bits[k].second;
+        o.tpos[k] = (int8_t)bits[k].first;
+        if (bits[k].first == k && run == k) run++;
+    }
+    return run >= min_run;
+}
 
 // Compile the op lists for batch width nb.  Returns the arena size or -1 on
 // a malformed input (message set).
@@ -293,6 +344,26 @@ int64_t compile(tn_plan &P, int nb) {
         } else {
             nd.where.leaf_off = P.leaf_off[i];
         }
+    }
+    // label sets of every node, and for each node the labels its parent step
+    // contracts (shared with the sibling, not kept): a tensor-core step puts
+    // those lowest in its output so that the parent's operand split (or this
+    // step's planar epilogue) moves contiguous runs
+    std::vector<std::unordered_set<int32_t>> lset(nodes.size());
+    for (int i = 0; i < n; i++) lset[i].insert(nodes[i].lay.begin(), nodes[i].lay.end());
+    std::vector<std::unordered_set<int32_t>> parentK(nodes.size());
+    for (int t = 0; t < (int)P.tree.size(); t++) {
+        const int ia = P.tree[t].first, ib = P.tree[t].second;
+        std::unordered_set<int32_t> &o = lset[n + t];
+        for (int32_t x : lset[ia])
+            if (!lset[ib].count(x) || kept.count(x)) o.insert(x);
+        for (int32_t x : lset[ib])
+            if (!lset[ia].count(x)) o.insert(x);
+        for (int32_t x : lset[ia])
+            if (lset[ib].count(x) && !kept.count(x)) {
+                parentK[ia].insert(x);
+                parentK[ib].insert(x);
+            }
     }
     // steps
     for (int t = 0; t < (int)P.tree.size(); t++) {
@@ -409,13 +480,23 @@ int64_t compile(tn_plan &P, int nb) {
         Groups GA, GB;
         if (use_tc) {
             // the split pass reads each operand in whatever label order it has
-            // (a fused bit permutation), so the group orders are free: take A's
+            // (a fused bit permutation), so the group orders are free.  K
+            // follows the operand a tensor-core GEMM will write in planar
+            // form (its lowest labels are this step's K labels), else A;
+            // rows and columns put the parent step's K labels lowest.
+            const NodeRec &kref = (!planar_candidate(ops, A.where) && planar_candidate(ops, B.where)) ? B : A;
+            const std::unordered_set<int32_t> Kset(K.begin(), K.end());
             for (int32_t x : A.lay)
                 if (gA[x] == 0) hord.push_back(x);
-            for (int32_t x : A.lay)
-                if (gA[x] == 2) kord.push_back(x);
-            mord = Ml;
-            nord = Nl;
+            for (int32_t x : kref.lay)
+                if (Kset.count(x)) kord.push_back(x);
+            const std::unordered_set<int32_t> &pk = parentK[n + t];
+            for (int pass = 0; pass < 2; pass++) {
+                for (int32_t x : Ml)
+                    if ((pk.count(x) != 0) == (pass == 1)) mord.push_back(x);
+                for (int32_t x : Nl)
+                    if ((pk.count(x) != 0) == (pass == 1)) nord.push_back(x);
+            }
         } else {
             GA = group_layout(A.lay, gA);
             GB = group_layout(B.lay, gB);
@@ -486,6 +567,7 @@ int64_t compile(tn_plan &P, int nb) {
         }
         Op op;
         op.kind = OP_GEMM;
+        std::memset(&op.tc, 0, sizeof op.tc);
         op.step = t;
         op.dep = nc.dep;
         GemmArgs &g = op.gemm;
@@ -537,6 +619,28 @@ int64_t compile(tn_plan &P, int nb) {
                 std::vector<int32_t> dl = hord;
                 dl.insert(dl.end(), rows.begin(), rows.end());
                 dl.insert(dl.end(), kord.begin(), kord.end());
+                const int64_t elems = (int64_t)1 << dl.size();
+                // the GEMM that wrote src splits its own output into these
+                // planes when its epilogue writes can be coalesced (runs of
+                // at least 64 bytes per plane).  Not for the scaled forms:
+                // their plane scale is the max of the whole output, known
+                // only after the producer's last tile.
+                if (P.opts.tc_planar >= 0 && !scaled && planar_candidate(ops, src.where)) {
+                    Op *prod = producer_of(ops, src.where);
+                    TcPlanarOut o;
+                    const int nHp = __builtin_ctzll((uint64_t)prod->gemm.H);
+                    const int nMp = __builtin_ctzll((uint64_t)prod->gemm.M);
+                    const int nNp = __builtin_ctzll((uint64_t)prod->gemm.N);
+                    if (make_planar(src.lay, dl, nHp, nMp, nNp, mode, es == 2 ? 5 : 4, o)) {
+                        Operand dst;
+                        dst.buf = new_buf((np * elems * es + 7) / 8);
+                        prod->tc.out = o;
+                        prod->out = dst;
+                        prod->bytes += (double)np * es * (double)elems - 8.0 * (double)elems;
+                        split_idx++;
+                        return dst;
+                    }
+                }
                 Op sp;
                 sp.kind = OP_SPLIT;
                 sp.step = t;
@@ -548,7 +652,6 @@ int64_t compile(tn_plan &P, int nb) {
                     sp.aux_idx = split_idx;
                 }
                 split_idx++;
-                const int64_t elems = (int64_t)1 << dl.size();
                 Operand dst;
                 dst.buf = new_buf((np * elems * es + 7) / 8);
                 sp.out = dst;
@@ -641,7 +744,11 @@ int64_t compile(tn_plan &P, int nb) {
     // an invariant buffer read inside the block loop lives to the loop's end
     for (size_t b = 0; b < P.bufs.size(); b++) {
         if (!buf_dep[b] && last[b] > T_pro) last[b] = T_end;
-        if (first[b] == INT32_MAX) { first[b] = 0; last[b] = 0; }
+        if (first[b] == INT32_MAX) {  // never used (a GEMM output replaced by its planar form)
+            first[b] = 0;
+            last[b] = 0;
+            P.bufs[b].elems = 0;
+        }
         P.bufs[b].t0 = first[b];
         P.bufs[b].t1 = last[b];
     }
@@ -716,6 +823,7 @@ void resolve_all(tn_plan &P) {
                 op.tc.chunk_bytes = P.opts.tc_chunk_bytes;
                 op.tc.flush_bytes = P.opts.tc_flush_bytes;
                 op.tc.scales = op.aux.buf >= 0 ? reinterpret_cast<const unsigned *>(resolve(P, op.aux)) : nullptr;
+                if (op.tc.out.mode != 0) op.tc.out.planes = resolve(P, op.out);
                 op.tc.max_slot = op.maxout.buf >= 0
                                      ? reinterpret_cast<unsigned *>(resolve(P, op.maxout)) + op.maxout_idx
                                      : nullptr;

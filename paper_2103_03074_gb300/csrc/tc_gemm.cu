@@ -95,7 +95,8 @@ struct Ring {
     static constexpr int kStages = (196608 / kStageBytes) < 6 ? (196608 / kStageBytes) : 6;
     static constexpr int kOutRS = 66;  // staging row stride in float2 (16-byte aligned rows)
     static constexpr int kOutBytes = (TM / 2) * kOutRS * 8;
-    static constexpr int kSmem = kStages * kStageBytes + kOutBytes + 1024 + 256;
+    static constexpr int kJtabBytes = 64 * 8;  // planar epilogue: (stage offset, destination offset) per group
+    static constexpr int kSmem = kStages * kStageBytes + kOutBytes + 1024 + 256 + kJtabBytes;
     static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 constexpr uint32_t kSpinLimit = 1u << 24;
@@ -222,6 +223,7 @@ struct GemmTcParams {
     int64_t tiles;     // gn * gm * H * ksplit
     const unsigned *scales;  // scaled forms: max-abs slots of A and B (float bits)
     unsigned *max_slot;      // optional: atomic max of |re|, |im| over C (float bits)
+    TcPlanarOut out;         // planar epilogue (out.mode > 0)
 };
 
 // tile t -> (n tile, m tile, batch h, K part); N tiles vary fastest
@@ -249,6 +251,93 @@ __device__ __forceinline__ int part_chunks(const GemmTcParams &p, int part, int 
     return c_end > c_begin ? c_end - c_begin : 0;
 }
 
+__device__ __forceinline__ uint64_t scatter8(uint64_t v, const int8_t *pos, int n) {
+    uint64_t r = 0;
+    for (int j = 0; j < n; j++) r |= ((v >> j) & 1ull) << pos[j];
+    return r;
+}
+
+__device__ __forceinline__ void plane_store1(const TcPlanarOut &o, uint64_t d, float2 v, int e) {
+    const Pieces pc = split_value(o.mode, v, e);
+    const int np = mode_planes(o.mode);
+    if (o.mode == 2) {
+        uint32_t *P = reinterpret_cast<uint32_t *>(o.planes);
+        for (int q = 0; q < np; q++) P[d + q * o.plane_stride] = pc.q[q];
+    } else {
+        uint16_t *P = reinterpret_cast<uint16_t *>(o.planes);
+        for (int q = 0; q < np; q++) P[d + q * o.plane_stride] = (uint16_t)pc.q[q];
+    }
+}
+
+// elements d, d + 1 (d even)
+__device__ __forceinline__ void plane_store2(const TcPlanarOut &o, uint64_t d, float2 v0, float2 v1, int e) {
+    const Pieces p0 = split_value(o.mode, v0, e), p1 = split_value(o.mode, v1, e);
+    const int np = mode_planes(o.mode);
+    if (o.mode == 2) {
+        uint2 *P = reinterpret_cast<uint2 *>(o.planes);
+        for (int q = 0; q < np; q++) P[(d + q * o.plane_stride) >> 1] = make_uint2(p0.q[q], p1.q[q]);
+    } else {
+        uint32_t *P = reinterpret_cast<uint32_t *>(o.planes);
+        for (int q = 0; q < np; q++) P[(d + q * o.plane_stride) >> 1] = p0.q[q] | (p1.q[q] << 16);
+    }
+}
+
+// Planar epilogue tables.  The half tile's elements are enumerated in
+// destination order j = (j_hi, j_lo): j_lo (6 bits) is lane 2 l + q, j_hi a
+// group.  Per lane: stage and destination offsets of its two j_lo; per group
+// (shared memory, computed once per launch): those of j_hi.
+struct PlanarLane {
+    int s[2];       // staging offset (row * RS + column)
+    uint32_t d[2];  // destination offset
+    bool pair;      // d[1] = d[0] + 1 with d[0] even: one vector store per plane
+};
+
+__device__ __forceinline__ void planar_bits(const TcPlanarOut &o, int j, int k0, int k1, int RS, int &so,
+                                            uint32_t &d) {
+    int r = 0, c = 0;
+    d = 0;
+    for (int k = k0; k < k1; k++)
+        if ((j >> (k - k0)) & 1) {
+            const int b = o.tb[k];
+            if (b < 6) c |= 1 << b;
+            else r |= 1 << (b - 6);
+            d |= 1u << o.tpos[k];
+        }
+    so = r * RS + c;
+}
+
+__device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane, int RS) {
+    PlanarLane L;
+    const int nlo = o.ntb < 6 ? o.ntb : 6;
+    for (int q = 0; q < 2; q++) planar_bits(o, 2 * lane + q, 0, nlo, RS, L.s[q], L.d[q]);
+    L.pair = o.ntb >= 6 && o.tpos[0] == 0;
+    return L;
+}
+
+// Split the staged half tile (rows mh .. mh + 63) into the next step's
+// planes: warp fw of the 8 epilogue warps takes the groups j_hi = fw, fw + 8,
+// ...; each lane two neighbouring elements of a group.
+__device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_t mh, int64_t n0, const float2 *st,
+                                             const uint2 *jtab, const PlanarLane &L, int fw, int lane) {
+    const uint64_t base = scatter8((uint64_t)h, o.hpos, o.nH) | scatter8((uint64_t)mh, o.mpos, o.nM) |
+                          scatter8((uint64_t)n0, o.npos, o.nN);
+    const int nlo = o.ntb < 6 ? o.ntb : 6;
+    const int n_hi = 1 << (o.ntb - nlo);
+    const bool v1 = 2 * lane + 1 < (1 << nlo), v0 = 2 * lane < (1 << nlo);
+    for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
+        const uint2 g = jtab[jh];
+        const float2 a = st[(int)g.x + L.s[0]];
+        const float2 b = st[(int)g.x + L.s[1]];
+        const uint64_t d0 = base + g.y + L.d[0];
+        if (L.pair) {
+            plane_store2(o, d0, a, b, 0);
+        } else {
+            if (v0) plane_store1(o, d0, a, 0);
+            if (v1) plane_store1(o, base + g.y + L.d[1], b, 0);
+        }
+    }
+}
+
 template <int KIND, int CB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -266,6 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *full = bar, *empty = bar + kStages, *tfull = bar + 2 * kStages, *tempty = bar + 2 * kStages + 2;
     uint64_t *drain = bar + 2 * kStages + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * kStages + 5);
+    uint2 *jtab = reinterpret_cast<uint2 *>(smem + kStages * kStageBytes + R::kOutBytes + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -379,6 +469,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         // every flush warp walks every tile of this CTA and reaches the same
         // named barriers even after a failed wait (it then skips waits,
         // tensor-memory reads and stores), so the warps never part ways
+        PlanarLane pl;
+        if (p.out.mode != 0) {
+            pl = planar_lane(p.out, lane, R::kOutRS);
+            const int nlo = p.out.ntb < 6 ? p.out.ntb : 6;
+            for (int jh = fw * 32 + lane; jh < (1 << (p.out.ntb - nlo)); jh += kFlushWarps * 32) {
+                int so;
+                uint32_t d;
+                planar_bits(p.out, jh, nlo, p.out.ntb, R::kOutRS, so, d);
+                jtab[jh] = make_uint2((uint32_t)so, d);
+            }
+            // published to the other epilogue warps by the first staging barrier
+        }
         int gc = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
@@ -457,7 +559,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         stage_out[r * RS + half * 32 + j] = make_float2(acc_re[j], acc_im[j]);
                 }
                 asm volatile("bar.sync 1, 256;" ::: "memory");
-                for (int rr = fw; ok && rr < TM / 2; rr += kFlushWarps) {
+                if (p.out.mode != 0) {
+                    if (ok && tc.m0 + hp * (TM / 2) < p.M)
+                        planar_write(p.out, tc.h, tc.m0 + hp * (TM / 2), tc.n0, stage_out, jtab, pl, fw, lane);
+                }
+                for (int rr = fw; ok && p.out.mode == 0 && rr < TM / 2; rr += kFlushWarps) {
                     const int64_t mm = tc.m0 + hp * (TM / 2) + rr;
                     if (mm >= p.M) break;
                     const int64_t n = tc.n0 + 2 * lane;
@@ -595,6 +701,12 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     if (p.flush_chunks < 1) p.flush_chunks = 1;
     p.scales = g.scales;
     p.max_slot = g.max_slot;
+    p.out = g.out;
+    // planar output only for the unscaled split forms: a scaled form's plane
+    // scale needs the max of the whole output before any tile is written
+    if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || (p.out.mode != 1 && p.out.mode != 2) ||
+                            p.out.plane_stride > (int64_t(1) << 31) || p.out.ntb > 12))
+        return cudaErrorInvalidValue;
     if (g.max_slot) {
         if (p.ksplit > 1) return cudaErrorInvalidValue;  // partial tiles: their max is not C's
         cudaError_t e = cudaMemsetAsync(g.max_slot, 0, sizeof(unsigned), s);

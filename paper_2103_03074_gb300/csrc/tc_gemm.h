@@ -7,6 +7,24 @@
 
 namespace tn {
 
+// Optional epilogue that writes C straight into the next step's split planes
+// (that step's operand layout and split mode) instead of complex64 C, so no
+// separate split pass reads C back.  Output element (h, m, n) goes to plane
+// offset scatter(h, hpos) | scatter(m, mpos) | scatter(n, npos).  Within the
+// epilogue's half tile (64 rows x 64 columns) the tile bits are enumerated in
+// destination order (tb / tpos), so a warp's 64 consecutive elements land in
+// as few 128-byte segments per plane as the layout allows.
+struct TcPlanarOut {
+    int mode;               // 0: complex64 C (no split); 1 (bf16) or 2 (tf32) hi/lo split as in BitPermArgs
+    void *planes;
+    int64_t plane_stride;   // elements per plane
+    int nH, nM, nN;         // bits of h, m, n
+    int8_t hpos[kMaxRank], mpos[kMaxRank], npos[kMaxRank];  // destination bit of each bit
+    int ntb;                // tile bits, ordered by destination position:
+    int8_t tb[12];          //   0..5 column bit c, 6..11 row bit r (of the half tile)
+    int8_t tpos[12];        //   their destination positions
+};
+
 // One tensor-core GEMM: the GemmArgs contract (C = [H][M][N] contiguous) plus
 // the split planes of A (rows = M) and B (rows = N), planes[q][h][row][k], and
 // their TMA descriptors.
@@ -19,6 +37,7 @@ struct TcGemm {
     int flush_bytes;  // bytes of K between accumulator read-outs (multiple of chunk_bytes; 0: default)
     const unsigned *scales;  // FP16S / FP16X3: device max-abs slots of A and B (float bits)
     unsigned *max_slot;      // optional: receives max |re|, |im| of C (float bits; zeroed by the launch)
+    TcPlanarOut out;         // out.mode 0: plain complex64 C
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
 };

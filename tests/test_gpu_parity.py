@@ -208,6 +208,31 @@ def test_cfg2_amplitudes_vs_golden(tn, form):
         assert abs(p_s1 - oxeb.marginal(ref)) < (2 * bound + bound ** 2) * oxeb.marginal(ref)
 
 
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
+def test_planar_epilogue_matches_split_pass(tn, form):
+    """GEMMs that write the next step's hi/lo planes from their epilogue
+    (tc_planar on, the default) against complex64 output plus a separate
+    split pass (tc_planar -1): the same pieces and products, so they agree to
+    FP32 rounding of the split-K atomics elsewhere in the plan (1e-6), and
+    both meet the form's bound against the FP64 golden amplitudes."""
+    import torch
+    cfg = make_config(2)
+    ref = load_golden("cfg2_amplitudes.txt")
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
+    got = {}
+    for planar in (0, -1):
+        plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(tc_planar=planar))
+        amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+        plan.contract(0, 1 << len(sliced), amp)
+        torch.cuda.synchronize()
+        got[planar] = to_complex(amp)
+        plan.close()
+    assert rel(got[0], got[-1]) < 1e-6
+    bound = {"bf16x3": 2e-5}.get(form, TOL)
+    assert rel(got[0], ref) < bound and rel(got[-1], ref) < bound
+
+
 def test_probabilities_xeb_on_oracle_amplitudes(tn):
     import torch
     cfg = make_config(1)
