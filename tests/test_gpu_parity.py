@@ -233,6 +233,22 @@ def test_planar_epilogue_matches_split_pass(tn, form):
     assert rel(got[0], ref) < bound and rel(got[-1], ref) < bound
 
 
+def test_sharded_contract_single_rank(tn):
+    """The multi-rank helper at world size 1: the rank's range is every slice
+    and the host sum is the identity, so it reproduces the golden amplitudes."""
+    import torch
+    from paper_2103_03074_gb300.shard import sharded_contract
+    cfg = make_config(2)
+    ref = load_golden("cfg2_amplitudes.txt")
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
+    plan = tn.Plan(L, T, O, sliced, tree, form="fp32")
+    amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+    got = sharded_contract(plan, amp, 0, 1)
+    plan.close()
+    assert rel(got.reshape(-1), ref) < TOL
+
+
 def test_probabilities_xeb_on_oracle_amplitudes(tn):
     import torch
     cfg = make_config(1)
