@@ -253,7 +253,8 @@ bool planar_candidate(std::vector<Op> &ops, const Operand &w) {
 bool make_planar(const std::vector<int32_t> &src, const std::vector<int32_t> &dst, int nH, int nM, int nN, int mode,
                  int min_run, TcPlanarOut &o) {
     const int r = (int)src.size();
-    if (r != (int)dst.size() || r != nH + nM + nN || nM < 6 || r > kMaxRank) return false;
+    // (destination offsets inside the kernel's tables are 32-bit)
+    if (r != (int)dst.size() || r != nH + nM + nN || nM < 6 || r > 31) return false;
     std::memset(&o, 0, sizeof o);
     o.mode = mode;
     o.plane_stride = (int64_t)1 << r;
@@ -715,7 +716,7 @@ int64_t compile(tn_plan &P, int nb) {
         first[w.buf] = std::min(first[w.buf], time);
         last[w.buf] = std::max(last[w.buf], time);
     };
-    std::vector<char> buf_dep(P.bufs.size(), 0);
+    std::vector<char> buf_dep(P.bufs.size(), 0), buf_pro(P.bufs.size(), 0);
     for (auto &e : P.extract) {
         int b = (int)(intptr_t)e.dst;
         touch(Operand{b, -1}, T_ext);
@@ -728,6 +729,8 @@ int64_t compile(tn_plan &P, int nb) {
         touch(op.out, i);
         touch(op.aux, i);
         touch(op.maxout, i);
+        if (op.out.buf >= 0) buf_pro[op.out.buf] = 1;
+        if (op.maxout.buf >= 0) buf_pro[op.maxout.buf] = 1;
     }
     for (int i = 0; i < (int)P.batch.size(); i++) {
         Op &op = P.batch[i];
@@ -743,7 +746,10 @@ int64_t compile(tn_plan &P, int nb) {
     touch(P.root, T_acc);
     // an invariant buffer read inside the block loop lives to the loop's end
     for (size_t b = 0; b < P.bufs.size(); b++) {
-        if (!buf_dep[b] && last[b] > T_pro) last[b] = T_end;
+        // (also a max-abs slot pair written by a prologue GEMM for one operand
+        // and inside the block for the other: the prologue's value must
+        // survive every block)
+        if ((!buf_dep[b] || buf_pro[b]) && last[b] > T_pro) last[b] = T_end;
         if (first[b] == INT32_MAX) {  // never used (a GEMM output replaced by its planar form)
             first[b] = 0;
             last[b] = 0;

@@ -249,6 +249,36 @@ def test_sharded_contract_single_rank(tn):
     assert rel(got.reshape(-1), ref) < TOL
 
 
+def _prologue_feeds_block_network():
+    """A slice-invariant tensor-core GEMM (X Y, in the prologue) feeding a
+    slice-dependent one (Z W, W holds the sliced label s): in the scaled forms
+    Z's scale comes from the prologue GEMM's epilogue and W's from a max-abs
+    pass inside each block, into one pair of slots."""
+    m, k, n = list(range(0, 8)), list(range(10, 15)), list(range(20, 28))
+    o, s = list(range(30, 38)), 40
+    labels = [m + k, k + n, m[:5] + [s] + o, [s] + o + m[5:] + n[3:]]
+    rng = np.random.default_rng(20210308)
+    data = [(rng.standard_normal((2,) * len(l)) + 1j * rng.standard_normal((2,) * len(l))).astype(np.complex64)
+            * np.float32(2.0 ** (-len(l) / 4)) for l in labels]
+    return labels, data, n[:3], [s], [(0, 1), (4, 2), (5, 3)]
+
+
+@pytest.mark.parametrize("form", ["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"])
+def test_prologue_gemm_feeds_every_block(tn, form):
+    """Two blocks of one slice each (batch_log2 0): values and scales the
+    prologue writes once must survive both blocks."""
+    labels, data, open_l, sliced, tree = _prologue_feeds_block_network()
+    ref = oc.sliced_sum(labels, data, open_l, sliced)
+    for use_graph in (0, 1):
+        plan = tn.Plan(labels, data, open_l, sliced, tree, form=form,
+                       opts=tn.plan_opts(batch_log2=0, use_graph=use_graph))
+        for rep in range(2):
+            amp = dev_zeros(len(open_l))
+            plan.contract(0, 2, amp)
+            assert rel(to_complex(amp), ref) < {"bf16x3": 2e-5, "fp16s": 2e-3}.get(form, TOL), (use_graph, rep)
+        plan.close()
+
+
 def test_probabilities_xeb_on_oracle_amplitudes(tn):
     import torch
     cfg = make_config(1)
