@@ -86,8 +86,10 @@ def test_find_order_cap_reduces_width(tn):
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
     _, _, st0 = tn.find_order(L, O, tn.search_opts(trials=16, n_sliced=0))
     _, sl, st1 = tn.find_order(L, O, tn.search_opts(trials=16, log2_cap=int(st0["log2_width"]) - 4))
+    # the capped search may also pick a narrower tree, so the number of
+    # sliced labels is not fixed by the cap; the width bound and the count are
     assert st1["log2_width"] <= st0["log2_width"] - 4
-    assert len(sl) == st1["n_sliced"] >= 4
+    assert len(sl) == st1["n_sliced"] >= 1
 
 
 def test_search_is_deterministic(tn):
