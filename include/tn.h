@@ -86,8 +86,12 @@ typedef struct {
      * itself (in the next step's layout) when its epilogue writes stay
      * coalesced, instead of complex64 output plus a split pass; -1: off */
     int32_t tc_planar;
+    /* CUDA-graph branches: the captured graphs order each step after the
+     * steps it depends on and spread independent steps over this many
+     * streams (0 = default 4; 1 = one chain in op order) */
+    int32_t graph_branches;
     /* reserved, set to 0 */
-    int32_t reserved[5];
+    int32_t reserved[4];
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

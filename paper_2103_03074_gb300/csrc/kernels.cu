@@ -54,7 +54,12 @@ int grid_for(int64_t n) {
 }
 
 // ---------------------------------------------------------------- small step
-template <bool kRegT>
+// Work item = (row r, chunk of NC outputs n).  Rows vary fastest, so the
+// threads of a warp read and write consecutive addresses where T's and C's
+// low bits are row bits, and read the same S values (shared-memory
+// broadcast).  One chunk covers all outputs up to N = 32, so T is read once.
+// rows is a power of two: index arithmetic uses masks and shifts.
+template <int NC, bool kRegT>
 __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
@@ -71,45 +76,49 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = (uint32_t)scatter_bits(k, a.kposT, a.nK);
     for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = (uint32_t)scatter_bits(n, a.nposC, a.nN);
     __syncthreads();
-    // work item = (row r, chunk of up to 8 outputs n); rows vary fastest so
-    // consecutive threads read and write consecutive addresses
-    const int NC = NS < 8 ? NS : 8;
-    const int n_chunks = NS / NC;
-    const int64_t items = a.rows * n_chunks;
+    const int nc = NS < NC ? NS : NC;  // outputs per item
+    const int chunk_bits = a.nN > 5 ? a.nN - 5 : 0;  // NC = 32 when N > 32
+    const int rbits = a.row_bits;
+    const int64_t items = a.rows << chunk_bits;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < items; w += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = w % a.rows;
-        const int n0 = (int)(w / a.rows) * NC;
+        const int64_t r = w & (a.rows - 1);
+        const int n0 = (int)(w >> rbits) * NC;
         const uint64_t tb = insert_zeros((uint64_t)r, a.tins, a.n_tins);
         const uint64_t cb = insert_zeros((uint64_t)r, a.cins, a.n_cins);
         const uint32_t h = gather_bits((uint64_t)r, a.hbitR, a.nH);
-        const float2 *Sh = S_sm + (size_t)h * KS * NS;
-        float2 acc[8];
+        const float2 *Sh = S_sm + (size_t)h * KS * NS + n0;
+        float2 acc[NC];
 #pragma unroll
-        for (int j = 0; j < 8; j++) acc[j] = make_float2(0.f, 0.f);
-        if (kRegT) {
+        for (int j = 0; j < NC; j++) acc[j] = make_float2(0.f, 0.f);
+        // T in batches of 16 values (independent loads in flight), S pairs
+        // read as 16-byte broadcasts
+        for (int k0 = 0; k0 < KS; k0 += 16) {
             float2 t[16];
 #pragma unroll
             for (int k = 0; k < 16; k++)
-                if (k < KS) t[k] = a.T[tb + offT[k]];
+                if (k0 + k < KS) t[k] = a.T[tb + offT[k0 + k]];
 #pragma unroll
             for (int k = 0; k < 16; k++) {
-                if (k < KS) {
+                if (k0 + k < KS) {
+                    const float2 *Sk = Sh + (k0 + k) * NS;
+                    if (NC >= 2 && nc == NC) {
 #pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        if (j < NC) cfma(acc[j], t[k], Sh[k * NS + n0 + j]);
+                        for (int j = 0; j < NC; j += 2) {
+                            const float4 s2 = *reinterpret_cast<const float4 *>(Sk + j);
+                            cfma(acc[j], t[k], make_float2(s2.x, s2.y));
+                            cfma(acc[j + 1], t[k], make_float2(s2.z, s2.w));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NC; j++)
+                            if (j < nc) cfma(acc[j], t[k], Sk[j]);
+                    }
                 }
-            }
-        } else {
-            for (int k = 0; k < KS; k++) {
-                const float2 t = a.T[tb + offT[k]];
-#pragma unroll
-                for (int j = 0; j < 8; j++)
-                    if (j < NC) cfma(acc[j], t, Sh[k * NS + n0 + j]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < 8; j++)
-            if (j < NC) a.C[cb + offC[n0 + j]] = acc[j];
+        for (int j = 0; j < NC; j++)
+            if (j < nc) a.C[cb + offC[n0 + j]] = acc[j];
     }
 }
 
@@ -401,19 +410,30 @@ __global__ void xeb_finalize_kernel(double *out, int scale_exp) { out[1] = ldexp
 
 }  // namespace
 
-cudaError_t launch_small(const SmallArgs &a, cudaStream_t s) {
-    const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
-    const size_t smem = (size_t)HS * KS * NS * sizeof(float2) + (size_t)(KS + NS) * sizeof(uint32_t);
+template <int NC>
+cudaError_t launch_small_nc(const SmallArgs &a, int grid, size_t smem, cudaStream_t s) {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        cudaFuncSetAttribute(small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(small_kernel<NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(small_kernel<NC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_done = true;
     }
-    const int grid = grid_for(a.rows * (NS < 8 ? 1 : NS / 8));
-    if (KS <= 16) small_kernel<true><<<grid, kThreads, smem, s>>>(a);
-    else small_kernel<false><<<grid, kThreads, smem, s>>>(a);
+    if ((1 << a.nK) <= 16) small_kernel<NC, true><<<grid, kThreads, smem, s>>>(a);
+    else small_kernel<NC, false><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
+    SmallArgs a = args;
+    const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
+    const size_t smem = (size_t)HS * KS * NS * sizeof(float2) + (size_t)(KS + NS) * sizeof(uint32_t);
+    if (a.rows < 1 || (a.rows & (a.rows - 1)) != 0) return cudaErrorInvalidValue;
+    a.row_bits = __builtin_ctzll((unsigned long long)a.rows);
+    const int64_t chunks = NS > 32 ? NS / 32 : 1;
+    const int grid = grid_for(a.rows * chunks);
+    if (NS <= 8) return launch_small_nc<8>(a, grid, smem, s);
+    if (NS <= 16) return launch_small_nc<16>(a, grid, smem, s);
+    return launch_small_nc<32>(a, grid, smem, s);
 }
 
 cudaError_t launch_bitperm(const BitPermArgs &args, cudaStream_t s) {

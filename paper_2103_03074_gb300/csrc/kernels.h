@@ -25,6 +25,7 @@ struct SmallArgs {
     const float2 *S;
     float2 *C;
     int64_t rows;        // 2^(rank T - nK)
+    int row_bits;        // log2 rows (set by the launcher)
     int nK, nN, nH;
     int n_tins;          // K positions of T, ascending (zero insertion turns r into T's base)
     int n_cins;          // N positions of C, ascending

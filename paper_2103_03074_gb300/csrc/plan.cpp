@@ -21,6 +21,7 @@
 //    are permuted first when their H/M/K label groups are not contiguous.
 //  * Buffers are placed in one arena by first-fit over their live intervals.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -887,7 +888,7 @@ void op_features(const Op &op, tn_form form, float *f) {
     switch (op.kind) {
     case OP_SMALL: {
         kind = 0;
-        const double nc = (1 << op.small.nN) < 8 ? 1.0 : (double)((1 << op.small.nN) / 8);
+        const double nc = (1 << op.small.nN) <= 32 ? 1.0 : (double)((1 << op.small.nN) / 32);
         sh[0] = std::exp2(op.small.nH); sh[1] = (double)op.small.rows;
         sh[2] = std::exp2(op.small.nN); sh[3] = std::exp2(op.small.nK);
         units = (double)op.small.rows * nc;
@@ -1157,23 +1158,83 @@ void prof_init(tn_plan &P) {
 
 // Capture ops into an instantiated graph on a private stream (the ops' own
 // launch-time setup already ran in an eager call).
+// Capture an op list as a graph whose edges are the ops' real dependencies:
+// op i follows op j < i when j writes arena bytes that i reads or writes, or
+// reads bytes that i writes (buffers share arena space once their lives end).
+// Independent ops, such as the small steps of separate subtrees, land on
+// different streams of the capture and overlap when the graph runs.
 cudaError_t capture_ops(const tn_plan &P, const std::vector<Op> &ops, cudaGraphExec_t *out) {
     *out = nullptr;
     if (ops.empty()) return cudaSuccess;
-    cudaStream_t cs;
+    const int n = (int)ops.size();
+    struct Rg { int64_t lo, hi; };
+    auto range = [&](const Operand &w) -> Rg {
+        if (w.buf < 0) return {0, 0};
+        const Buf &b = P.bufs[w.buf];
+        return {b.off, b.off + b.elems * 8};
+    };
+    auto hit = [](const Rg &a, const Rg &b) { return a.lo < a.hi && b.lo < b.hi && a.lo < b.hi && b.lo < a.hi; };
+    std::vector<std::array<Rg, 3>> rd(n);
+    std::vector<std::array<Rg, 2>> wr(n);
+    for (int i = 0; i < n; i++) {
+        rd[i] = {range(ops[i].in0), range(ops[i].in1), range(ops[i].aux)};
+        wr[i] = {range(ops[i].out), range(ops[i].maxout)};
+    }
+    std::vector<std::vector<int>> deps(n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < i; j++) {
+            bool d = false;
+            for (const Rg &w : wr[j]) {
+                for (const Rg &r : rd[i]) d = d || hit(w, r);
+                for (const Rg &w2 : wr[i]) d = d || hit(w, w2);
+            }
+            for (const Rg &r : rd[j])
+                for (const Rg &w2 : wr[i]) d = d || hit(r, w2);
+            if (d) deps[i].push_back(j);
+        }
+    constexpr int kMaxBranches = 16;
+    const int kBranches = P.opts.graph_branches > 0 ? std::min(P.opts.graph_branches, kMaxBranches) : 4;
+    cudaStream_t cs, br[kMaxBranches];
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
+    int made = 0;
+    for (; made < kBranches && e == cudaSuccess; made++) e = cudaStreamCreateWithFlags(&br[made], cudaStreamNonBlocking);
+    if (e != cudaSuccess) made--;
+    std::vector<cudaEvent_t> ev(n + 1, nullptr);
+    for (int i = 0; i <= n && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
     cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = cudaSuccess;
-        for (const auto &op : ops)
-            if ((le = run_op(P, op, cs)) != cudaSuccess) break;
+        cudaError_t le = cudaEventRecord(ev[n], cs);  // fork point
+        std::vector<int> tail(kBranches, -1);          // last op on each branch
+        std::vector<char> forked(kBranches, 0);
+        int rr = 0;
+        for (int i = 0; i < n && le == cudaSuccess; i++) {
+            // continue the branch whose tail is the latest dependency, else the next branch
+            int b = -1, latest = deps[i].empty() ? -1 : deps[i].back();
+            for (int q = 0; q < kBranches; q++)
+                if (latest >= 0 && tail[q] == latest) b = q;
+            if (b < 0) b = (rr++) % kBranches;
+            if (!forked[b]) {
+                le = cudaStreamWaitEvent(br[b], ev[n], 0);
+                forked[b] = 1;
+            }
+            for (int j : deps[i])
+                if (le == cudaSuccess && j != tail[b]) le = cudaStreamWaitEvent(br[b], ev[j], 0);
+            if (le == cudaSuccess) le = run_op(P, ops[i], br[b]);
+            if (le == cudaSuccess) le = cudaEventRecord(ev[i], br[b]);
+            tail[b] = i;
+        }
+        for (int q = 0; q < kBranches && le == cudaSuccess; q++)  // join
+            if (tail[q] >= 0) le = cudaStreamWaitEvent(cs, ev[tail[q]], 0);
         e = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = le;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    for (int q = 0; q < made; q++) cudaStreamDestroy(br[q]);
     cudaStreamDestroy(cs);
     return e;
 }

@@ -639,8 +639,11 @@ int tc_default_flush_bytes(tn_form form) { return default_flush_bytes(form); }
 int tc_plane_count(tn_form form) { return form == TN_FP16S ? 2 : 4; }
 
 bool tc_gemm_suitable(const GemmArgs &a) {
-    return a.M >= 64 && a.N >= 32 && a.K >= 32 && a.H <= 65535 && (a.M + TM - 1) / TM <= 65535 &&
-           a.N < (1ll << 31) && a.K < (1ll << 31);
+    // narrow N and short K are zero-filled by TMA to the tile (the MMAs on
+    // the padding are wasted but the step stays on the tensor cores); a plane
+    // row must hold a multiple of 16 bytes (K >= 8 elements)
+    return a.M >= 64 && a.N >= 8 && a.K >= 8 && a.H <= 65535 && a.M < (1ll << 31) && a.N < (1ll << 31) &&
+           a.K < (1ll << 31);
 }
 
 int tc_choose_ksplit(const GemmArgs &a, tn_form form) {

@@ -119,6 +119,9 @@ def rel(a, b):
     (10, 9, 8, True, True),      # A [k][m] (M contiguous), B [n][k] (K contiguous)
     (6, 7, 6, False, True),      # M = 64 < 128-row tile: zero-filled rows
     (8, 5, 8, True, True),       # K = 32 < 64-wide chunk: zero-filled K
+    (9, 4, 9, False, True),      # K = 16: zero-filled K in the tile
+    (10, 9, 4, True, True),      # N = 16: zero-filled B rows in the tile
+    (10, 3, 10, True, False),    # K = 8 (a 16-byte bf16 plane row)
     (9, 11, 6, True, False),
 ])
 def test_single_gemm_bf16x3(tn, m, k, n, a_kfirst, b_nfirst):
