@@ -90,8 +90,14 @@ typedef struct {
      * steps it depends on and spread independent steps over this many
      * streams (0 = default 4; 1 = one chain in op order) */
     int32_t graph_branches;
+    /* split forms: a step with a small operand (which would run on the
+     * CUDA-core small-step kernel) goes to the tensor-core GEMM instead when
+     * its K and N both have >= 3 bits, K + N has >= small_tc_bits bits and T
+     * has >= 2^16 rows (0 = never, the default: on the 30-qubit workload the
+     * extra split pass costs more than the tensor cores save) */
+    int32_t small_tc_bits;
     /* reserved, set to 0 */
-    int32_t reserved[4];
+    int32_t reserved[3];
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

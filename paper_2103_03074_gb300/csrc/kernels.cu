@@ -59,7 +59,7 @@ int grid_for(int64_t n) {
 // low bits are row bits, and read the same S values (shared-memory
 // broadcast).  One chunk covers all outputs up to N = 32, so T is read once.
 // rows is a power of two: index arithmetic uses masks and shifts.
-template <int NC, bool kRegT>
+template <int NC>
 __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = (uint32_t)scatter_bits(n, a.nposC, a.nN);
     __syncthreads();
     const int nc = NS < NC ? NS : NC;  // outputs per item
-    const int chunk_bits = a.nN > 5 ? a.nN - 5 : 0;  // NC = 32 when N > 32
+    constexpr int kNcBits = NC == 32 ? 5 : (NC == 16 ? 4 : 3);
+    const int chunk_bits = a.nN > kNcBits ? a.nN - kNcBits : 0;
     const int rbits = a.row_bits;
     const int64_t items = a.rows << chunk_bits;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < items; w += (int64_t)gridDim.x * blockDim.x) {
@@ -90,15 +91,16 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
         float2 acc[NC];
 #pragma unroll
         for (int j = 0; j < NC; j++) acc[j] = make_float2(0.f, 0.f);
-        // T in batches of 16 values (independent loads in flight), S pairs
+        // T in batches of 4 values (independent loads in flight; larger
+        // batches cost occupancy with 32 outputs per item), S pairs
         // read as 16-byte broadcasts
-        for (int k0 = 0; k0 < KS; k0 += 16) {
-            float2 t[16];
+        for (int k0 = 0; k0 < KS; k0 += 4) {
+            float2 t[4];
 #pragma unroll
-            for (int k = 0; k < 16; k++)
+            for (int k = 0; k < 4; k++)
                 if (k0 + k < KS) t[k] = a.T[tb + offT[k0 + k]];
 #pragma unroll
-            for (int k = 0; k < 16; k++) {
+            for (int k = 0; k < 4; k++) {
                 if (k0 + k < KS) {
                     const float2 *Sk = Sh + (k0 + k) * NS;
                     if (NC >= 2 && nc == NC) {
@@ -414,12 +416,10 @@ template <int NC>
 cudaError_t launch_small_nc(const SmallArgs &a, int grid, size_t smem, cudaStream_t s) {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(small_kernel<NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        cudaFuncSetAttribute(small_kernel<NC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(small_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_done = true;
     }
-    if ((1 << a.nK) <= 16) small_kernel<NC, true><<<grid, kThreads, smem, s>>>(a);
-    else small_kernel<NC, false><<<grid, kThreads, smem, s>>>(a);
+    small_kernel<NC><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -429,10 +429,10 @@ cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
     const size_t smem = (size_t)HS * KS * NS * sizeof(float2) + (size_t)(KS + NS) * sizeof(uint32_t);
     if (a.rows < 1 || (a.rows & (a.rows - 1)) != 0) return cudaErrorInvalidValue;
     a.row_bits = __builtin_ctzll((unsigned long long)a.rows);
-    const int64_t chunks = NS > 32 ? NS / 32 : 1;
-    const int grid = grid_for(a.rows * chunks);
-    if (NS <= 8) return launch_small_nc<8>(a, grid, smem, s);
-    if (NS <= 16) return launch_small_nc<16>(a, grid, smem, s);
+    const int nc = NS <= 8 ? 8 : (NS <= 16 ? 16 : 32);  // outputs per work item
+    const int grid = grid_for(a.rows * (NS > nc ? NS / nc : 1));
+    if (nc == 8) return launch_small_nc<8>(a, grid, smem, s);
+    if (nc == 16) return launch_small_nc<16>(a, grid, smem, s);
     return launch_small_nc<32>(a, grid, smem, s);
 }
 

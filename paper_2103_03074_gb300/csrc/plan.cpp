@@ -391,7 +391,12 @@ int64_t compile(tn_plan &P, int nb) {
             if (!sS.count(x)) Ml.push_back(x);
         const int nH = (int)H.size(), nK = (int)K.size(), nN = (int)Nl.size(), nM = (int)Ml.size();
         const double macs = std::exp2((double)(nH + nM + nK + nN));
-        if ((int)S.lay.size() <= kSmallMaxRank && nK <= 10 && nN <= 10 && nH <= kMaxHBits) {
+        // a small step with enough arithmetic per T element goes to the
+        // tensor cores in the split forms (the CUDA-core kernel is bound by
+        // FP32 issue there, not by memory)
+        const bool small_to_tc = P.opts.small_tc_bits > 0 && P.form != TN_FP32 && nK >= 3 && nN >= 3 &&
+                                 nK + nN >= P.opts.small_tc_bits && (int)T.lay.size() - nK >= 16;
+        if ((int)S.lay.size() <= kSmallMaxRank && nK <= 10 && nN <= 10 && nH <= kMaxHBits && !small_to_tc) {
             // ---- small step: C = T layout with K labels replaced by N labels
             Op op;
             std::memset(&op.small, 0, sizeof op.small);
