@@ -268,8 +268,9 @@ int tn_gemm_split_noalloc(const float *d_A, const float *d_B, float *d_C, int64_
 
 /*
  * Learned step-cost model: an MLP (16 features -> 64 -> 64 -> 1, ReLU, FP32)
- * that predicts log2 of a step's device time in ms from the step features of
- * tn_plan_op_features.  Trained on the GPU by the library's own forward,
+ * that predicts, from the step features of tn_plan_op_features, log2 of a
+ * step's device time over its roofline time (feature 14); the predicted time
+ * in ms is 2^(output + 16 * feature 14).  Trained on the GPU by the library's own forward,
  * backward and Adam kernels on timings from tn_plan_profile.  Not a step of
  * the paper's method: it ranks candidate contraction trees for the search.
  *   create: seeded He-normal initialisation.
@@ -296,7 +297,10 @@ int tn_costmodel_predict(tn_costmodel_t cm, const float *d_X, float *d_Y, int64_
  * rows without the extraction and FP64-sum rows): kind one-hot {small step,
  * permute, FP32 GEMM, tensor-core GEMM, hi/lo split}, log2(MACs+1)/32,
  * log2(bytes+1)/32, log2 of the four shape entries /32, TF32 flag, BF16 flag,
- * log2(parallel work units)/32, log2(K partitions)/8, 1.  Returns the number
+ * log2(parallel work units, K partitions included)/32, log2(roofline ms)/16, 1.
+ * The roofline time is max(bytes / 7 TB/s, flops / peak of the unit) + 2 us,
+ * peaks 80 TFLOP/s FP32 (8 flops per complex MAC) and 2.25 (tf32: 1.125)
+ * PFLOP/s tensor (24 flops per complex MAC, 8 for FP16S).  Returns the number
  * of steps written (at most max_ops) or a negative error.
  */
 int tn_plan_op_features(tn_plan_t plan, float *out, int max_ops);

@@ -885,6 +885,28 @@ namespace {
 
 inline float l2f(double x) { return (float)(std::log2(x + 1.0) / 32.0); }
 
+// Roofline time of one step in ms: the larger of its algorithmic bytes over
+// HBM bandwidth and its arithmetic over the peak of the unit that runs it,
+// plus a launch floor.  Nominal GB300 figures: 7 TB/s HBM3e, 80 TFLOP/s FP32
+// FMA (152 SMs x 128 lanes x 2 x 2.07 GHz), 2.25 PFLOP/s dense f16/bf16 and
+// half of that for tf32 on the tensor cores.  A tensor-core complex MAC
+// issues 24 flops in the hi/lo forms (4 real products x 3 piece products) and
+// 8 in FP16S.  The cost model learns log2(measured / this), which varies far
+// less across sizes than the time itself and so extrapolates to steps larger
+// than the ones it was trained on.
+double roofline_ms(const Op &op, tn_form form) {
+    const double hbm = 7.0e12, fp32 = 80.0e12, floor_ms = 2.0e-3;
+    double flops = 0.0, peak = fp32;
+    if (op.kind == OP_SMALL || (op.kind == OP_GEMM && op.gemm_variant != 1)) {
+        flops = 8.0 * op.macs;
+    } else if (op.kind == OP_GEMM) {
+        flops = (form == TN_FP16S ? 8.0 : 24.0) * op.macs;
+        peak = form == TN_TF32X3 ? 1.125e15 : 2.25e15;
+    }
+    const double t = std::max(op.bytes / hbm, flops / peak) * 1e3;
+    return t + floor_ms;
+}
+
 // 16 step features (see tn_plan_op_features in tn.h)
 void op_features(const Op &op, tn_form form, float *f) {
     for (int i = 0; i < kCostFeatures; i++) f[i] = 0.f;
@@ -933,7 +955,7 @@ void op_features(const Op &op, tn_form form, float *f) {
     f[11] = (tc && form == TN_TF32X3) ? 1.f : 0.f;
     f[12] = (tc && form == TN_BF16X3) ? 1.f : 0.f;
     f[13] = l2f(units);
-    f[14] = (float)(std::log2(ksplit) / 8.0);
+    f[14] = (float)(std::log2(roofline_ms(op, form)) / kRoofFeatureScale);
     f[15] = 1.f;
 }
 
@@ -1003,9 +1025,14 @@ int rank_candidates(const std::vector<std::vector<int32_t>> &labels, const std::
     if (rc) return rc;
     for (size_t i = 0; i < cands.size(); i++) {
         double t = 0;
-        for (size_t r = spans[i].pro0; r < spans[i].pro1; r++) t += std::exp2((double)Y[r]);
+        // the model's output is log2(time / roofline time); feature 14 holds
+        // log2(roofline time) / kRoofFeatureScale
+        auto step_ms = [&](size_t r) {
+            return std::exp2((double)Y[r] + kRoofFeatureScale * (double)X[r * kCostFeatures + 14]);
+        };
+        for (size_t r = spans[i].pro0; r < spans[i].pro1; r++) t += step_ms(r);
         double tb = 0;
-        for (size_t r = spans[i].bat0; r < spans[i].bat1; r++) tb += std::exp2((double)Y[r]);
+        for (size_t r = spans[i].bat0; r < spans[i].bat1; r++) tb += step_ms(r);
         pred_ms[i] = t + spans[i].blocks * tb;
         if (pred_ms[i] < pred_ms[best]) best = (int)i;
     }

@@ -5,6 +5,8 @@
   1e-4 (FP32 accumulation over a few hundred terms per gradient entry).
 * Training on per-step timings recorded by the step-timing recorder on a set
   of plans, evaluated on held-out plans (measured time judges the error).
+  The network learns log2(measured time / roofline time), the roofline time
+  being feature 14 (log2 ms / 16); predicted log2 ms = 16 f14 + output.
 * Ranking: among candidate trees of one workload, the tree the model predicts
   fastest against the tree with the smallest analytic cost (complex MACs),
   both timed; the model's pick must not be slower, and the gain is printed.
@@ -72,6 +74,18 @@ def profile_plan(tn, plan, n_slices, reps=3):
     return feats, y
 
 
+ROOF_SCALE = 16.0
+
+
+def residual(X, y):
+    """Training target of the model: log2(time) minus log2(roofline time)."""
+    return (y - ROOF_SCALE * X[:, 14]).astype(np.float32)
+
+
+def predicted_log2_ms(X, out):
+    return ROOF_SCALE * X[:, 14] + out
+
+
 def workload_plans(tn, seeds, forms=("fp32", "tf32x3", "bf16x3")):
     out = []
     for i, seed in enumerate(seeds):
@@ -108,7 +122,7 @@ def test_training_predicts_held_out_plans(tn):
     train = g % 5 != 0
     cm = tn.CostModel(seed=7)
     dX = torch.from_numpy(X[train]).cuda()
-    dT = torch.from_numpy(Y[train]).cuda()
+    dT = torch.from_numpy(residual(X[train], Y[train])).cuda()
     l0 = cm.grad(dX, dT)
     l1 = cm.train(dX, dT, epochs=3000, lr=3e-3)
     assert l1 < 0.2 * l0
@@ -116,7 +130,7 @@ def test_training_predicts_held_out_plans(tn):
     dYt = torch.zeros(int((~train).sum()), dtype=torch.float32, device="cuda")
     cm.predict(dXt, dYt)
     torch.cuda.synchronize()
-    err = np.abs(dYt.cpu().numpy() - Y[~train])
+    err = np.abs(predicted_log2_ms(X[~train], dYt.cpu().numpy()) - Y[~train])
     base = np.abs(Y[train].mean() - Y[~train])
     print(f"cost model: train loss {l0:.3f} -> {l1:.3f}; held-out mean |log2 err| {err.mean():.3f} "
           f"(predicting the mean: {base.mean():.3f}), {int(train.sum())} train / {int((~train).sum())} test steps")
@@ -144,7 +158,7 @@ def test_learned_ranking_versus_analytic_cost(tn):
     # train on plans of other circuits
     X, Y, _ = collect(tn, workload_plans(tn, list(range(101, 131)), forms=("tf32x3",)))
     cm = tn.CostModel(seed=11)
-    cm.train(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), epochs=3000, lr=3e-3)
+    cm.train(torch.from_numpy(X).cuda(), torch.from_numpy(residual(X, Y)).cuda(), epochs=3000, lr=3e-3)
     # candidates for a held-out workload: best trees of several search seeds
     circ = sycamore_circuit("rect", 5, 5, 12, 4242)
     L, T, O = tn.circuit_network(circ, random_bits(25, 7), list(range(17, 25)))
@@ -162,7 +176,7 @@ def test_learned_ranking_versus_analytic_cost(tn):
         d = torch.zeros(len(f), dtype=torch.float32, device="cuda")
         cm.predict(torch.from_numpy(f).cuda(), d)
         torch.cuda.synchronize()
-        pred.append(float(np.sum(2.0 ** d.cpu().numpy())))
+        pred.append(float(np.sum(2.0 ** predicted_log2_ms(f, d.cpu().numpy()))))
     meas, pred = np.array(meas), np.array(pred)
     analytic = np.array([c[2] for c in cands])
     i_a, i_m = int(np.argmin(analytic)), int(np.argmin(pred))
