@@ -96,8 +96,13 @@ typedef struct {
      * has >= 2^16 rows (0 = never, the default: on the 30-qubit workload the
      * extra split pass costs more than the tensor cores save) */
     int32_t small_tc_bits;
+    /* small-step kernel: 0 (default) takes the tiled kernel (row tiles staged
+     * through shared memory, register-blocked outputs) where K and N are
+     * 4..32 wide and T has >= 2^12 rows, else one thread per row; -1: always
+     * one thread per row */
+    int32_t small_tiled;
     /* reserved, set to 0 */
-    int32_t reserved[3];
+    int32_t reserved[2];
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

@@ -8,6 +8,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "kernels.h"
 
 namespace tn {
@@ -122,6 +125,161 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
         for (int j = 0; j < NC; j++)
             if (j < nc) a.C[cb + offC[n0 + j]] = acc[j];
     }
+}
+
+// ------------------------------------------------------ small step, tiled
+// For steps whose K and N are both 4..32 wide and whose T has many rows:
+// a CTA walks tiles of 2^tb consecutive rows.  The tile's T values (a few
+// contiguous runs) are copied with cp.async into shared memory as [k][row],
+// two tiles deep, so the next tile's copies are in flight while this one is
+// multiplied and stored; each thread forms an RPT x NPT block of outputs
+// (RPT rows, NPT consecutive n), reading RPT T values and NPT S values per k
+// (4 FMAs per complex MAC against (RPT + NPT / 2) / (RPT * NPT) shared-memory
+// loads); the outputs go through shared memory as [n][row] and out in C's
+// own contiguous runs.  S sits in shared memory whole, as in the row
+// kernel; the tile's h is constant (its bits lie above the tile).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ uint32_t smem_u32_k(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// rows per tile of the tiled small-step kernel: 1024 / N row groups of
+// RPT rows, RPT the largest of 4, 2, 1 whose shared memory (two T stages,
+// plus the C tile unless outputs are stored from registers) fits in 72 KB
+__host__ __device__ constexpr int small_tile_rpt(int KS, int NS, bool direct) {
+    return ((2 * KS + (direct ? 0 : NS)) * (4 * (1024 / NS) + 1) * 8 <= 72 * 1024)   ? 4
+           : ((2 * KS + (direct ? 0 : NS)) * (2 * (1024 / NS) + 1) * 8 <= 72 * 1024) ? 2
+                                                                                     : 1;
+}
+
+// DIRECT: C's five lowest positions are row bits, so a warp's 32
+// consecutive rows are 32 consecutive C addresses and outputs are stored
+// straight from registers; otherwise they go through shared memory.
+template <int NK, int NN, bool DIRECT>
+__global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArgs a) {
+    constexpr int KS = 1 << NK, NS = 1 << NN, NPT = 4;
+    constexpr int NG = NS / NPT, RG = kThreads / NG;
+    constexpr int RPT = small_tile_rpt(KS, NS, DIRECT);
+    constexpr int RT = RG * RPT, RP = RT + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int HS = 1 << a.nH;
+    const int SS = HS * KS * NS;
+    float2 *S_s = reinterpret_cast<float2 *>(smem);
+    float2 *T_s = S_s + SS;                                  // two stages of KS * RP
+    float2 *C_s = T_s + 2 * KS * RP;                         // NS * RP (unless DIRECT)
+    uint64_t *offT_s = reinterpret_cast<uint64_t *>(C_s + (DIRECT ? 0 : NS * RP));
+    uint64_t *offC_s = offT_s + 32;
+    uint32_t *runDstT_s = reinterpret_cast<uint32_t *>(offC_s + 32);
+    uint32_t *dstLoT_s = runDstT_s + 32, *dstHiT_s = dstLoT_s + 64;
+    uint32_t *runSrcC_s = dstHiT_s + 64, *srcLoC_s = runSrcC_s + 32, *srcHiC_s = srcLoC_s + 64;
+    for (int idx = threadIdx.x; idx < SS; idx += blockDim.x) {
+        uint32_t n = idx & (NS - 1), k = (idx >> NN) & (KS - 1), h = idx >> (NN + NK);
+        uint64_t addr = scatter_bits(h, a.hposS, a.nH) | scatter_bits(k, a.kposS, NK) | scatter_bits(n, a.nposS, NN);
+        S_s[idx] = a.S[addr];
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        if (i < 32) {
+            offT_s[i] = a.runOffT[i];
+            offC_s[i] = a.runOffC[i];
+            runDstT_s[i] = a.runDstT[i];
+            runSrcC_s[i] = a.runSrcC[i];
+        }
+        dstLoT_s[i] = a.dstLoT[i];
+        dstHiT_s[i] = a.dstHiT[i];
+        srcLoC_s[i] = a.srcLoC[i];
+        srcHiC_s[i] = a.srcHiC[i];
+    }
+    __syncthreads();
+    const int rgi = threadIdx.x % RG, ngi = threadIdx.x / RG;
+    const int64_t n_tiles = a.rows >> a.tb;
+    constexpr int ET = RT * KS, EC = RT * NS;
+    const int lt = a.lt, lc = a.lc;
+    const uint32_t ltmask = (1u << lt) - 1, lcmask = (1u << lc) - 1;
+    const uint32_t T_s_addr = smem_u32_k(T_s);
+    constexpr uint32_t kStageBytes = KS * RP * sizeof(float2);
+    // direct stores: this thread's row offsets in C (the tile base adds the
+    // bits above the tile) and its outputs' n offsets
+    uint64_t rowC[RPT], nC[NPT];
+    if (DIRECT) {
+#pragma unroll
+        for (int i = 0; i < RPT; i++) rowC[i] = insert_zeros((uint64_t)(rgi + i * RG), a.cins, a.n_cins);
+#pragma unroll
+        for (int j = 0; j < NPT; j++) nC[j] = scatter_bits((uint64_t)(ngi * NPT + j), a.nposC, NN);
+    }
+    auto issue = [&](int64_t tile, int stage) {
+        const float2 *Tt = a.T + insert_zeros((uint64_t)tile << a.tb, a.tins, a.n_tins);
+        const uint32_t base = T_s_addr + stage * kStageBytes;
+#pragma unroll 4
+        for (int f = threadIdx.x; f < ET; f += kThreads) {
+            const uint32_t e = f & ltmask;
+            const uint32_t d = runDstT_s[f >> lt] + dstLoT_s[e & 63] + dstHiT_s[e >> 6];
+            cp_async8(base + d * (uint32_t)sizeof(float2), Tt + offT_s[f >> lt] + e);
+        }
+    };
+    int stage = 0;
+    if ((int64_t)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+    cp_async_commit();
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t next = tile + gridDim.x;
+        if (next < n_tiles) issue(next, stage ^ 1);
+        cp_async_commit();
+        cp_async_wait1();  // this tile's copies (all but the newest group) have landed
+        __syncthreads();
+        const uint64_t r0 = (uint64_t)tile << a.tb;
+        float2 *Ct = a.C + insert_zeros(r0, a.cins, a.n_cins);
+        const uint32_t h = gather_bits(r0, a.hbitR, a.nH);
+        float2 acc[RPT][NPT];
+#pragma unroll
+        for (int i = 0; i < RPT; i++)
+#pragma unroll
+            for (int j = 0; j < NPT; j++) acc[i][j] = make_float2(0.f, 0.f);
+        const float2 *Sh = S_s + (size_t)h * KS * NS + ngi * NPT;
+        const float2 *Tr = T_s + stage * KS * RP + rgi;
+#pragma unroll
+        for (int k = 0; k < KS; k++) {
+            float2 tv[RPT], sv[NPT];
+#pragma unroll
+            for (int i = 0; i < RPT; i++) tv[i] = Tr[k * RP + i * RG];
+#pragma unroll
+            for (int j = 0; j < NPT; j += 2) {
+                const float4 s2 = *reinterpret_cast<const float4 *>(Sh + k * NS + j);
+                sv[j] = make_float2(s2.x, s2.y);
+                sv[j + 1] = make_float2(s2.z, s2.w);
+            }
+#pragma unroll
+            for (int i = 0; i < RPT; i++)
+#pragma unroll
+                for (int j = 0; j < NPT; j++) cfma(acc[i][j], tv[i], sv[j]);
+        }
+        if (DIRECT) {
+            __syncthreads();  // every thread's reads of this stage are done
+#pragma unroll
+            for (int i = 0; i < RPT; i++)
+#pragma unroll
+                for (int j = 0; j < NPT; j++) Ct[rowC[i] + nC[j]] = acc[i][j];
+        } else {
+#pragma unroll
+            for (int i = 0; i < RPT; i++)
+#pragma unroll
+                for (int j = 0; j < NPT; j++) C_s[(ngi * NPT + j) * RP + rgi + i * RG] = acc[i][j];
+            __syncthreads();
+            for (int f = threadIdx.x; f < EC; f += kThreads) {
+                const uint32_t e = f & lcmask;
+                Ct[offC_s[f >> lc] + e] = C_s[runSrcC_s[f >> lc] + srcLoC_s[e & 63] + srcHiC_s[e >> 6]];
+            }
+        }
+        stage ^= 1;
+        // the copies into the stage just read are issued in the next
+        // iteration, after every thread has passed the barrier above (its
+        // reads of that stage done); the next C_s stores follow the next
+        // first barrier, after every thread's reads of C_s
+    }
+    cp_async_wait_all();
 }
 
 // ------------------------------------------------------- tiled bit permute
@@ -262,7 +420,12 @@ __global__ void __launch_bounds__(kThreads) maxabs_kernel(const MaxAbsArgs a) {
 
 // --------------------------------------------------------------- FP32 GEMM
 // 64 x 64 output tile per CTA, 256 threads, each 4 x 4 complex outputs,
-// K staged through shared memory 16 at a time.
+// K staged through shared memory 16 at a time.  Each K tile is summed into
+// a fresh partial that is then added to the running sum (blocked
+// summation): the rounding error of a length-K dot product then grows like
+// sqrt(16) + sqrt(K / 16) roundings instead of sqrt(K), which keeps the
+// plain FP32 form within 1e-5 of the exact amplitudes on deep circuits
+// (K up to 2^11 per step).
 constexpr int BM = 64, BN = 64, BK = 16;
 
 __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmArgs a) {
@@ -297,6 +460,11 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmArgs a) {
                 Bs[kk][nn] = (n < a.N && k < a.K) ? Bb[k * a.sBk + n * a.sBn] : make_float2(0.f, 0.f);
             }
             __syncthreads();
+            float2 part[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) part[i][j] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int kk = 0; kk < BK; kk++) {
                 float2 av[4], bv[4];
@@ -307,8 +475,15 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmArgs a) {
 #pragma unroll
                 for (int i = 0; i < 4; i++)
 #pragma unroll
-                    for (int j = 0; j < 4; j++) cfma(acc[i][j], av[i], bv[j]);
+                    for (int j = 0; j < 4; j++) cfma(part[i][j], av[i], bv[j]);
             }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    acc[i][j].x += part[i][j].x;
+                    acc[i][j].y += part[i][j].y;
+                }
             __syncthreads();
         }
         float2 *Cb = a.C + h * a.sCh;
@@ -423,7 +598,161 @@ cudaError_t launch_small_nc(const SmallArgs &a, int grid, size_t smem, cudaStrea
     return cudaGetLastError();
 }
 
+namespace {
+constexpr size_t kTiledTableBytes = 2 * 32 * 8 + (32 + 64 + 64) * 4 * 2;
+size_t small_tiled_smem(const SmallArgs &a) {
+    const size_t KS = (size_t)1 << a.nK, NS = (size_t)1 << a.nN, HS = (size_t)1 << a.nH;
+    const size_t RP = ((size_t)1 << a.tb) + 1;
+    return (HS * KS * NS + (2 * KS + (a.tiled == 2 ? 0 : NS)) * RP) * sizeof(float2) + kTiledTableBytes;
+}
+
+// contiguous-run structure of a tile over `tb` row bits plus the nX bits at
+// xpos (bit j of x at position xpos[j]) of a tensor of rank `rank`, whose
+// row bits fill the other positions in increasing order.  Shared-memory
+// index of (x, row) = x * RP + row.
+bool tile_runs(int rank, int tb, int nX, const int *xpos, int RP, int &l, int &n_run, uint64_t *run_off,
+               uint32_t *run_sm, uint32_t *lo, uint32_t *hi) {
+    std::vector<int> xbit(rank, -1);
+    for (int j = 0; j < nX; j++) {
+        if (xpos[j] < 0 || xpos[j] >= rank) return false;
+        xbit[xpos[j]] = j;
+    }
+    // weight (shared-memory index step) of each position inside the run
+    std::vector<uint32_t> w;
+    int rows_seen = 0, p = 0;
+    for (; p < rank; p++) {
+        if (xbit[p] >= 0) {
+            w.push_back((uint32_t)(1u << xbit[p]) * (uint32_t)RP);
+        } else {
+            if (rows_seen == tb) break;
+            w.push_back(1u << rows_seen);
+            rows_seen++;
+        }
+    }
+    if (rows_seen != tb) return false;
+    l = p;
+    if (l > 12) return false;
+    std::vector<int> high;  // x bits above the run
+    for (int q = p; q < rank; q++)
+        if (xbit[q] >= 0) high.push_back(q);
+    if (high.size() > 5) return false;
+    n_run = 1 << (int)high.size();
+    for (int u = 0; u < 32; u++) {
+        uint64_t off = 0;
+        uint32_t sm = 0;
+        if (u < n_run)
+            for (size_t i = 0; i < high.size(); i++)
+                if ((u >> i) & 1) {
+                    off |= 1ull << high[i];
+                    sm += (uint32_t)(1u << xbit[high[i]]) * (uint32_t)RP;
+                }
+        run_off[u] = off;
+        run_sm[u] = sm;
+    }
+    for (int v = 0; v < 64; v++) {
+        uint32_t a = 0, b = 0;
+        for (int j = 0; j < 6; j++) {
+            if (((v >> j) & 1) == 0) continue;
+            if (j < l) a += w[j];
+            if (j + 6 < l) b += w[j + 6];
+        }
+        lo[v] = a;
+        hi[v] = b;
+    }
+    return true;
+}
+
+template <int NK, int NN, bool DIRECT>
+cudaError_t launch_small_tiled_t(const SmallArgs &a, cudaStream_t s) {
+    static int occ = 0;
+    static size_t occ_smem = 0;
+    const size_t smem = small_tiled_smem(a);
+    if (occ == 0 || occ_smem != smem) {
+        cudaFuncSetAttribute(small_tiled_kernel<NK, NN, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             160 * 1024);
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, small_tiled_kernel<NK, NN, DIRECT>, kThreads, smem) !=
+                cudaSuccess || o < 1)
+            o = 1;
+        occ = o;
+        occ_smem = smem;
+    }
+    const int64_t tiles = a.rows >> a.tb;
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)152 * occ);
+    small_tiled_kernel<NK, NN, DIRECT><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NK, int NN>
+cudaError_t launch_small_tiled_kn(const SmallArgs &a, cudaStream_t s) {
+    return a.tiled == 2 ? launch_small_tiled_t<NK, NN, true>(a, s) : launch_small_tiled_t<NK, NN, false>(a, s);
+}
+
+template <int NK>
+cudaError_t launch_small_tiled_k(const SmallArgs &a, cudaStream_t s) {
+    switch (a.nN) {
+    case 2: return launch_small_tiled_kn<NK, 2>(a, s);
+    case 3: return launch_small_tiled_kn<NK, 3>(a, s);
+    case 4: return launch_small_tiled_kn<NK, 4>(a, s);
+    case 5: return launch_small_tiled_kn<NK, 5>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+void prepare_small_tiled(SmallArgs &a) {
+    a.tiled = 0;
+    const int nK = a.nK, nN = a.nN;
+    if (nK < 2 || nK > 5 || nN < 2 || nN > 5 || a.rows < 4096 || (a.rows & (a.rows - 1)) != 0) return;
+    const int KS = 1 << nK, NS = 1 << nN;
+    // N <= 8: the row kernel reads T once with direct loads and is bound by
+    // memory; staging T through shared memory only pays for K = 32 with K
+    // bits among T's five lowest positions (measured on GB300: 8 x 8 steps
+    // of 2^22 rows 0.113-0.117 ms on the row kernel against 0.12-0.14 ms
+    // tiled; 32 x 8 with low K bits 0.164 ms against 0.110 ms)
+    bool t_rows_low = true;
+    for (int j = 0; j < nK; j++)
+        if (a.kposT[j] < 5) t_rows_low = false;
+    if (NS <= 8 && (KS < 32 || t_rows_low)) return;
+    // outputs stored from registers when C's five lowest positions are row bits
+    bool direct = true;
+    for (int j = 0; j < nN; j++)
+        if (a.nposC[j] < 5) direct = false;
+    const int rpt = small_tile_rpt(KS, NS, direct);
+    const int RT = (1024 / NS) * rpt;
+    if (RT > a.rows) return;
+    int tb = 0;
+    while ((1 << tb) < RT) tb++;
+    for (int j = 0; j < a.nH; j++)
+        if (a.hbitR[j] < tb) return;
+    int row_bits = 0;
+    while (((int64_t)1 << row_bits) < a.rows) row_bits++;
+    SmallArgs t = a;
+    t.tb = tb;
+    t.rpt = rpt;
+    t.npt = 4;
+    t.row_bits = row_bits;
+    if (!tile_runs(row_bits + nK, tb, nK, a.kposT, RT + 1, t.lt, t.n_runT, t.runOffT, t.runDstT, t.dstLoT,
+                   t.dstHiT))
+        return;
+    if (!tile_runs(row_bits + nN, tb, nN, a.nposC, RT + 1, t.lc, t.n_runC, t.runOffC, t.runSrcC, t.srcLoC,
+                   t.srcHiC))
+        return;
+    t.tiled = direct ? 2 : 1;
+    if (small_tiled_smem(t) > 150 * 1024) return;
+    a = t;
+}
+
 cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
+    if (args.tiled) {
+        switch (args.nK) {
+        case 2: return launch_small_tiled_k<2>(args, s);
+        case 3: return launch_small_tiled_k<3>(args, s);
+        case 4: return launch_small_tiled_k<4>(args, s);
+        case 5: return launch_small_tiled_k<5>(args, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     SmallArgs a = args;
     const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
     const size_t smem = (size_t)HS * KS * NS * sizeof(float2) + (size_t)(KS + NS) * sizeof(uint32_t);

@@ -36,7 +36,25 @@ struct SmallArgs {
     int hbitR[kMaxHBits];      // bit of r holding bit j of h
     int hposS[kMaxHBits], kposS[kSmallMaxBits], nposS[kSmallMaxBits];  // positions in S
     int s_rank;
+    // Tiled form (filled by prepare_small_tiled; tiled == 0 selects the
+    // one-thread-per-row kernel).  A tile is 2^tb consecutive rows r; its T
+    // elements are 2^(tb + nK) values made of n_runT contiguous runs of 2^lt
+    // elements (T offset tbase(r0) + runOffT[u] + e), staged in shared memory
+    // at [k][row] (row stride 2^tb + 1) at runDstT[u] + dstLoT[e & 63] +
+    // dstHiT[e >> 6]; the C tile likewise, read back from [n][row].
+    int tiled;
+    int tb;              // log2 rows per tile
+    int rpt, npt;        // rows and outputs per thread
+    int lt, lc;          // contiguous run bits of the T and C tiles
+    int n_runT, n_runC;  // runs per tile
+    uint64_t runOffT[32], runOffC[32];
+    uint32_t runDstT[32], dstLoT[64], dstHiT[64];
+    uint32_t runSrcC[32], srcLoC[64], srcHiC[64];
 };
+
+// Decide whether a small step takes the tiled kernel and fill its tables
+// (host; plan compile time).  Needs rows set and the bit maps complete.
+void prepare_small_tiled(SmallArgs &a);
 
 // Bit permutation through a shared-memory tile, optionally fused with the
 // hi/lo split of split-precision GEMM operands.

@@ -458,6 +458,7 @@ int64_t compile(tn_plan &P, int nb) {
                 s.hbitR[j] = pt - below;
                 s.hposS[j] = pos_of(S.lay, H[j]);
             }
+            if (P.opts.small_tiled >= 0) prepare_small_tiled(s);
             op.in0 = T.where;  // T
             op.in1 = S.where;  // S
             nc.where.buf = new_buf((int64_t)1 << nc.lay.size());

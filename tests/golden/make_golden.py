@@ -4,10 +4,17 @@ Calls only ``oracle/`` (and the seeded inputs of ``tn_inputs``).  Each file
 holds one value per line: index, real part, imaginary part (repr of FP64),
 after a header that names the workload recipe.
 
-    python tests/golden/make_golden.py [cfg2]
+    python tests/golden/make_golden.py [cfg2] [cfg4]
 
 cfg2: the 30-qubit 5x6 grid, 12 cycles, 8 open qubits, 22 fixed bits; FP64
 Schroedinger state vector (16 GiB of host memory, several minutes on 8 cores).
+
+cfg4: the 53-qubit rotated lattice, 14 cycles, 16 open qubits.  No state
+vector fits, so a seeded sample of entries of the 2^16 amplitude tensor is
+computed one at a time: each entry is the fully closed network (open qubits
+set to that entry's bits) contracted by the oracle's own pairwise route in
+FP64 with its own greedy order (no slicing; about 25 GiB of host memory and
+several minutes per entry on 8 cores).  Lines are appended as they finish.
 """
 import os
 import sys
@@ -17,7 +24,9 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 from tn_inputs.configs import make_config  # noqa: E402
+from tn_inputs import SplitMix64  # noqa: E402
 from oracle import sv_native  # noqa: E402
+from oracle import network as onet, contract as oc  # noqa: E402
 
 
 def write_amplitudes(path, header, amp):
@@ -33,6 +42,53 @@ def cfg2():
     header = (f"{cfg['name']} circuit={cfg['circuit'].name} open={cfg['open_qubits']} "
               f"fixed_bits={''.join(map(str, cfg['fixed_bits']))} route=oracle.sv_native (FP64 state vector)")
     write_amplitudes(os.path.join(HERE, "cfg2_amplitudes.txt"), header, amp)
+
+
+CFG4_SAMPLES = 8
+CFG4_SAMPLE_SEED = 0x2103C4
+
+
+def cfg4_sample_indices():
+    """Seeded amplitude indices of the cfg4 sample (distinct, drawn uniformly)."""
+    cfg = make_config(4)
+    k = len(cfg["open_qubits"])
+    rng = SplitMix64(CFG4_SAMPLE_SEED)
+    out = []
+    while len(out) < CFG4_SAMPLES:
+        i = rng.below(1 << k)
+        if i not in out:
+            out.append(i)
+    return out
+
+
+def cfg4():
+    import time
+    cfg = make_config(4)
+    circ, openq = cfg["circuit"], cfg["open_qubits"]
+    k = len(openq)
+    path = os.path.join(HERE, "cfg4_amplitudes_sampled.txt")
+    done = set()
+    if os.path.exists(path):
+        done = {int(l.split()[0]) for l in open(path) if not l.startswith("#")}
+    else:
+        header = (f"{cfg['name']} circuit={circ.name} open={openq} "
+                  f"fixed_bits={''.join(map(str, cfg['fixed_bits']))} "
+                  f"samples={CFG4_SAMPLES} sample_seed={CFG4_SAMPLE_SEED:#x} "
+                  "route=oracle.contract (closed network per entry, FP64, greedy order)")
+        with open(path, "w") as f:
+            f.write(f"# {header}\n")
+    for idx in cfg4_sample_indices():
+        if idx in done:
+            continue
+        bits = list(cfg["fixed_bits"])
+        for j, q in enumerate(openq):
+            bits[q] = (idx >> (k - 1 - j)) & 1
+        t0 = time.time()
+        L, T, O = onet.circuit_network(circ, bits, [])
+        a = complex(oc.contract(L, T, O))
+        with open(path, "a") as f:
+            f.write(f"{idx} {a.real!r} {a.imag!r}\n")
+        print(f"cfg4 entry {idx}: {a} ({time.time() - t0:.0f} s)", flush=True)
 
 
 if __name__ == "__main__":

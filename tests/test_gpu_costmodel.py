@@ -7,9 +7,10 @@
   of plans, evaluated on held-out plans (measured time judges the error).
   The network learns log2(measured time / roofline time), the roofline time
   being feature 14 (log2 ms / 16); predicted log2 ms = 16 f14 + output.
-* Ranking: among candidate trees of one workload, the tree the model predicts
-  fastest against the tree with the smallest analytic cost (complex MACs),
-  both timed; the model's pick must not be slower, and the gain is printed.
+* Ranking: among candidate trees of held-out workloads, the tree the model
+  predicts fastest against the tree with the smallest analytic cost (complex
+  MACs), both timed; the model's picks must not be slower in total, and the
+  gain is printed.
 """
 import math
 
@@ -95,9 +96,11 @@ def workload_plans(tn, seeds, forms=("fp32", "tf32x3", "bf16x3")):
         open_q = list(range(n - 6, n))
         L, T, O = tn.circuit_network(circ, random_bits(n, seed), open_q)
         ns = 2 + seed % 4
-        # one plain greedy trial (no reconfiguration): steps of widely varying
-        # size, from launch-bound to bandwidth- and tensor-bound
-        tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=1, seed=seed, n_sliced=ns))
+        # alternately one plain greedy trial (steps of widely varying size,
+        # from launch-bound to bandwidth- and tensor-bound) and the searched
+        # tree (reconfigured subtrees, the kind of tree the ranking sees)
+        trials = 1 if i % 2 == 0 else 24
+        tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=trials, seed=seed, n_sliced=ns))
         form = forms[i % len(forms)]
         out.append((L, T, O, sliced, tree, form))
     return out
@@ -153,38 +156,58 @@ def timed(tn, plan, n_slices, reps=5):
     return e0.elapsed_time(e1) / reps
 
 
+HELD_OUT = [(5, 5, 12, 4242), (4, 6, 12, 4243), (5, 5, 11, 4244), (4, 7, 10, 4245)]
+
+
 def test_learned_ranking_versus_analytic_cost(tn):
+    """Among the distinct best trees of 12 search seeds for each of four
+    held-out circuits, the tree the model predicts fastest against the tree
+    with the fewest complex MACs, each timed as a CUDA graph replayed as one
+    chain of steps (graph_branches 1: its time is the sum of its steps, the
+    quantity the model predicts).  Over the four circuits the model's picks
+    must not take longer in total than the analytic picks (3% timing
+    slack); the gain is printed."""
     import torch
-    # train on plans of other circuits
     X, Y, _ = collect(tn, workload_plans(tn, list(range(101, 131)), forms=("tf32x3",)))
     cm = tn.CostModel(seed=11)
     cm.train(torch.from_numpy(X).cuda(), torch.from_numpy(residual(X, Y)).cuda(), epochs=3000, lr=3e-3)
-    # candidates for a held-out workload: best trees of several search seeds
+    tot_a = tot_m = tot_best = 0.0
+    errs = []
+    for rows, cols, cycles, seed in HELD_OUT:
+        circ = sycamore_circuit("rect", rows, cols, cycles, seed)
+        n = circ.n_qubits
+        L, T, O = tn.circuit_network(circ, random_bits(n, 7), list(range(n - 8, n)))
+        cands = []
+        for s in range(12):
+            tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=24, seed=1000 + s, n_sliced=6))
+            if all(tree != c[0] for c in cands):
+                cands.append((tree, sliced, st["log2_total"]))
+        meas, pred = [], []
+        for tree, sliced, _ in cands:
+            plan = tn.Plan(L, T, O, sliced, tree, form="tf32x3", opts=tn.plan_opts(use_graph=1, graph_branches=1))
+            meas.append(timed(tn, plan, 64))
+            f = plan.op_features()
+            plan.close()
+            d = torch.zeros(len(f), dtype=torch.float32, device="cuda")
+            cm.predict(torch.from_numpy(f).cuda(), d)
+            torch.cuda.synchronize()
+            pred.append(float(np.sum(2.0 ** predicted_log2_ms(f, d.cpu().numpy()))))
+        meas, pred = np.array(meas), np.array(pred)
+        analytic = np.array([c[2] for c in cands])
+        i_a, i_m = int(np.argmin(analytic)), int(np.argmin(pred))
+        tot_a += meas[i_a]
+        tot_m += meas[i_m]
+        tot_best += meas.min()
+        errs += list(np.abs(np.log2(pred / meas)))
+        print(f"{rows}x{cols} m{cycles}: {len(cands)} trees, analytic pick {meas[i_a]:.3f} ms, "
+              f"model pick {meas[i_m]:.3f} ms, best {meas.min():.3f} ms")
+    print(f"ranking over {len(HELD_OUT)} held-out circuits: analytic picks {tot_a:.3f} ms, model picks "
+          f"{tot_m:.3f} ms, best {tot_best:.3f} ms; gain {tot_a / tot_m:.3f}x; "
+          f"median |log2(pred/meas)| {np.median(errs):.2f}")
+    assert tot_m <= 1.03 * tot_a
+    # the library-side ranking inside the order search uses the same model
     circ = sycamore_circuit("rect", 5, 5, 12, 4242)
     L, T, O = tn.circuit_network(circ, random_bits(25, 7), list(range(17, 25)))
-    cands = []
-    for seed in range(12):
-        tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=24, seed=1000 + seed, n_sliced=6))
-        if all(tree != c[0] for c in cands):
-            cands.append((tree, sliced, st["log2_total"]))
-    meas, pred = [], []
-    for tree, sliced, _ in cands:
-        plan = tn.Plan(L, T, O, sliced, tree, form="tf32x3", opts=tn.plan_opts(use_graph=1))
-        meas.append(timed(tn, plan, 64))
-        f = plan.op_features()
-        plan.close()
-        d = torch.zeros(len(f), dtype=torch.float32, device="cuda")
-        cm.predict(torch.from_numpy(f).cuda(), d)
-        torch.cuda.synchronize()
-        pred.append(float(np.sum(2.0 ** predicted_log2_ms(f, d.cpu().numpy()))))
-    meas, pred = np.array(meas), np.array(pred)
-    analytic = np.array([c[2] for c in cands])
-    i_a, i_m = int(np.argmin(analytic)), int(np.argmin(pred))
-    print(f"ranking over {len(cands)} trees: analytic pick {meas[i_a]:.3f} ms, model pick {meas[i_m]:.3f} ms, "
-          f"best {meas.min():.3f} ms; gain {meas[i_a] / meas[i_m]:.2f}x; "
-          f"median |log2(pred/meas)| {np.median(np.abs(np.log2(pred / meas))):.2f}")
-    assert meas[i_m] <= 1.05 * meas[i_a]
-    # the library-side ranking inside the order search uses the same model
     tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=24, seed=1000, n_sliced=6, candidates=8,
                                                           rank_form="tf32x3", cost_model=cm))
     assert len(tree) == len(L) - 1 and len(sliced) == 6

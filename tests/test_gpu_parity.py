@@ -208,6 +208,59 @@ def test_cfg2_amplitudes_vs_golden(tn, form):
         assert abs(p_s1 - oxeb.marginal(ref)) < (2 * bound + bound ** 2) * oxeb.marginal(ref)
 
 
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "fp16x3"])
+def test_tiled_small_steps_match_row_kernel(tn, form):
+    """Small steps on the tiled kernel (the default) against the
+    one-thread-per-row kernel (small_tiled -1): both sum over k in ascending
+    order with the same fused multiply-adds, so the amplitudes agree bit for
+    bit; both meet the form's bound against the FP64 golden amplitudes."""
+    import torch
+    cfg = make_config(2)
+    ref = load_golden("cfg2_amplitudes.txt")
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
+    got = {}
+    for tiled in (0, -1):
+        plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(small_tiled=tiled, use_graph=1))
+        amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+        for _ in range(2):  # eager, then graph replay
+            amp.zero_()
+            plan.contract(0, 1 << len(sliced), amp)
+        torch.cuda.synchronize()
+        got[tiled] = to_complex(amp)
+        plan.close()
+    assert np.array_equal(got[0], got[-1])
+    bound = {"bf16x3": 2e-5}.get(form, TOL)
+    assert rel(got[0], ref) < bound
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_tiled_small_steps_random_layouts(tn, seed):
+    """Circuits on uneven grids with open qubits spread over the lattice put
+    the K and N labels of the small steps at varied bit positions (low,
+    high, interleaved with the row bits); tiled and row kernels agree bit for
+    bit, and both match the FP64 state vector."""
+    import torch
+    rows, cols = [(4, 5), (3, 7), (5, 4)][seed - 31]
+    circ = sycamore_circuit("rect", rows, cols, 10, seed)
+    n = circ.n_qubits
+    open_q = sorted(pick(seed, list(range(n)), 6))
+    fixed = random_bits(n, seed)
+    L, T, O = tn.circuit_network(circ, fixed, open_q)
+    tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=64, seed=seed, n_sliced=4))
+    got = {}
+    for tiled in (0, -1):
+        plan = tn.Plan(L, T, O, sliced, tree, form="fp32", opts=tn.plan_opts(small_tiled=tiled))
+        amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+        plan.contract(0, 1 << len(sliced), amp)
+        torch.cuda.synchronize()
+        got[tiled] = to_complex(amp)
+        plan.close()
+    assert np.array_equal(got[0], got[-1])
+    ref = osv.amplitudes(circ, fixed, open_q)
+    assert rel(got[0], ref) < TOL
+
+
 @pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
 def test_planar_epilogue_matches_split_pass(tn, form):
     """GEMMs that write the next step's hi/lo planes from their epilogue
