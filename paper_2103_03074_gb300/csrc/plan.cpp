@@ -254,8 +254,7 @@ bool planar_candidate(std::vector<Op> &ops, const Operand &w) {
 bool make_planar(const std::vector<int32_t> &src, const std::vector<int32_t> &dst, int nH, int nM, int nN, int mode,
                  int min_run, TcPlanarOut &o) {
     const int r = (int)src.size();
-    // (destination offsets inside the kernel's tables are 32-bit)
-    if (r != (int)dst.size() || r != nH + nM + nN || nM < 6 || r > 31) return false;
+    if (r != (int)dst.size() || r != nH + nM + nN || nM < 6 || r > kMaxRank) return false;
     std::memset(&o, 0, sizeof o);
     o.mode = mode;
     o.plane_stride = (int64_t)1 << r;
@@ -274,6 +273,9 @@ bool make_planar(const std::vector<int32_t> &src, const std::vector<int32_t> &ds
     for (int b = 0; b < std::min(6, nN); b++) bits.push_back({o.npos[b], b});
     for (int b = 0; b < 6; b++) bits.push_back({o.mpos[b], 6 + b});
     std::sort(bits.begin(), bits.end());
+    // the kernel's offsets inside a half tile are 32-bit (the tile base is
+    // 64-bit), so every tile bit must land below destination bit 32
+    if (bits.back().first >= 32) return false;
     o.ntb = (int)bits.size();
     int run = 0;
     for (int k = 0; k < o.ntb; k++) {

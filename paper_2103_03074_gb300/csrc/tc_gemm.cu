@@ -706,9 +706,11 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.max_slot = g.max_slot;
     p.out = g.out;
     // planar output only for the unscaled split forms: a scaled form's plane
-    // scale needs the max of the whole output before any tile is written
+    // scale needs the max of the whole output before any tile is written.
+    // Plane offsets are 64-bit (a tile's own offsets 32-bit, checked when
+    // the plan builds the tables)
     if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || (p.out.mode != 1 && p.out.mode != 2) ||
-                            p.out.plane_stride > (int64_t(1) << 31) || p.out.ntb > 12))
+                            p.out.plane_stride > (int64_t(1) << 44) || p.out.ntb > 12))
         return cudaErrorInvalidValue;
     if (g.max_slot) {
         if (p.ksplit > 1) return cudaErrorInvalidValue;  // partial tiles: their max is not C's
