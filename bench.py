@@ -164,6 +164,13 @@ WORKLOADS = {
                       desc="rotated6x9m1_m20_open21_cap31: 53 qubits, 20 cycles, 21 open, 32 fixed, "
                            "intermediates <= 2^31, a fixed 64-slice subset (ids 0..63) of the searched slice set"),
 }
+# the batched workload: 256 independent seeded circuits of uneven size
+# (16-30 qubits, 8-14 cycles, 6-10 open, 2^0-2^6 slices each) in one
+# multi-stream CUDA graph (tn_batch_*); its parity is checked circuit by
+# circuit in the GPU tests
+BATCH_DESC = ("batch256: 256 seeded circuits on rectangular grids of 16-30 qubits, 8-14 cycles, 6-10 open qubits, "
+              "2^0-2^6 slices each, one multi-stream CUDA graph")
+
 # forms whose error bound is 1e-5 by construction (22+ significant bits per
 # operand): the headline may take them where no oracle value exists
 ACCURATE_FORMS = ("fp32", "tf32x3", "fp16x3")
@@ -267,6 +274,66 @@ def time_steps(torch, plan, n_slices, amp, steps, warmup, stream, flush, n_open,
             evs[k][1].record(stream)
         stream.synchronize()
     return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def run_batch(args):
+    """The batched workload: every circuit's slices in one tn_batch_run."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_03074_gb300 as tn
+    from tn_inputs.configs import batch_recipes, make_batch_member
+    torch.cuda.set_device(0)
+    members = [make_batch_member(r) for r in batch_recipes()]
+    nets = []
+    for m in members:
+        L, T, O = tn.circuit_network(m["circuit"], m["fixed_bits"], m["open_qubits"])
+        tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=32, n_sliced=m["n_sliced"]))
+        nets.append((L, T, O, tree, sliced, st))
+    n_slices = sum(1 << len(x[4]) for x in nets)
+    macs = sum((1 << len(x[4])) * 2.0 ** x[5]["log2_slice"] for x in nets)
+    forms = [args.form] if args.form != "all" else ["fp32", "tf32x3", "fp16x3"]
+    stream = torch.cuda.Stream()
+    flush = l2_flush_buffer(torch)
+    results = {}
+    for form in forms:
+        plans, amps = [], []
+        for L, T, O, tree, sliced, st in nets:
+            plans.append(tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(batch_log2=3)))
+            amps.append(torch.zeros(2 << len(O), dtype=torch.float64, device="cuda"))
+        batch = tn.Batch(plans, amps, n_streams=8)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                batch.run(stream)
+            stream.synchronize()
+            with Clocks(0) as clk:
+                tot = 0.0
+                for _ in range(args.steps):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    batch.run(stream)
+                    e1.record(stream)
+                    stream.synchronize()
+                    tot += e0.elapsed_time(e1)
+        ms = tot / args.steps
+        results[form] = {"ms_per_step": ms, "slices_per_s": n_slices / (ms / 1e3),
+                         "complex_tflops": 8 * macs / (ms / 1e3) / 1e12, "clocks": clk.summary()}
+        batch.close()
+        for p in plans:
+            p.close()
+    best = max([f for f in forms if f in ACCURATE_FORMS] or forms, key=lambda f: results[f]["slices_per_s"])
+    r = results[best]
+    line = {"metric": METRIC, "value": r["slices_per_s"], "unit": "slices/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": best, "data": "synthetic (seeded Sycamore-style circuits, random bitstrings)",
+            "config": {"workload": BATCH_DESC, "form": best, "circuits": len(members), "slices_per_step": n_slices,
+                       "complex_macs_per_step": macs,
+                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
+            "complex_tflops": r["complex_tflops"], "forms": results, "clocks": r["clocks"],
+            "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line))
+    return 0
 
 
 def run_native(args):
@@ -480,7 +547,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "all"])
-    ap.add_argument("--workload", default="rect5x6", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rect5x6", choices=sorted(WORKLOADS) + ["batch256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
     args = ap.parse_args()
@@ -488,6 +555,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch256":
+        return run_batch(args)
     return run_native(args)
 
 
