@@ -193,6 +193,48 @@ int tn_probabilities_xeb(const double *d_amp, int n_open, int n_qubits, double *
                          double *d_out, double *out, tn_stream_t stream);
 
 /*
+ * Post-selection ("Fidelity" paragraph, Eq. 1, Fig. 2 right): the
+ * probabilities p_i = re_i^2 + im_i^2 (FP64, products and sum rounded
+ * separately) of the amplitude tensor d_amp (device complex128, 2^n_open
+ * entries, interleaved re/im) are sorted in decreasing order on the device,
+ * and for each of the n_points counts N_j (host int64, 1 <= N_j <= 2^n_open)
+ * out_xeb[j] (host) receives the XEB of the N_j most probable bitstrings,
+ * F_j = 2^n_qubits / N_j * (sum of the N_j largest p) - 1.  d_order (device
+ * int64 [2^n_open], may be NULL) receives the indices in that order (equal
+ * probabilities in any order).  n_open <= 31, n_points <= 65535.  Device
+ * scratch (12 bytes per entry plus small arrays) comes from the stream-ordered
+ * allocator and is released before return; the call synchronises `stream`.
+ * Errors: TN_ERR_ARG (bad sizes or counts), TN_ERR_OOM, TN_ERR_CUDA.
+ */
+int tn_postselect_xeb(const double *d_amp, int n_open, int n_qubits, int n_points, const int64_t *counts,
+                      double *out_xeb, int64_t *d_order, tn_stream_t stream);
+
+/*
+ * Sampling from the conditional distribution P(s2|s1) = P(s1;s2) / P(s1)
+ * (appendix on conditional and marginal probabilities) by inverse
+ * transform: with the cumulative probabilities c_i = sum_{i' <= i} p_i' in
+ * index order (FP64), sample j is the smallest index i with c_i > u_j * P(s1),
+ * P(s1) = sum of all p.  The uniform numbers are inputs: d_u (device double
+ * [n_samples], each in [0, 1)); d_out (device int64 [n_samples]) receives
+ * amplitude indices (bit j of the index = open qubit j, MSB first).  Stream-
+ * ordered; scratch of 8 bytes per entry from the stream-ordered allocator.
+ * n_open <= 40.  Errors: TN_ERR_ARG, TN_ERR_OOM, TN_ERR_CUDA.
+ */
+int tn_conditional_sample(const double *d_amp, int n_open, int64_t n_samples, const double *d_u, int64_t *d_out,
+                          tn_stream_t stream);
+
+/*
+ * Histogram of x_i = p_i * scale over n_bins equal bins of [0, x_max) plus an
+ * overflow bin (Fig. 2 left with scale = 2^n_qubits; Fig. 5 with scale =
+ * 2^n_open / P(s1)): bin b = floor(x / (x_max / n_bins)) computed in FP64
+ * (clamped to n_bins - 1 below x_max), bin n_bins counts x >= x_max.
+ * d_counts: device int64 [n_bins + 1], overwritten.  n_bins <= 4096.
+ * Stream-ordered.  Errors: TN_ERR_ARG, TN_ERR_CUDA.
+ */
+int tn_probability_histogram(const double *d_amp, int n_open, double scale, int n_bins, double x_max,
+                             int64_t *d_counts, tn_stream_t stream);
+
+/*
  * Replace the leaf values of a plan (same layout as tn_plan_create's `data`,
  * host memory, pinned or pageable) with an asynchronous copy on `stream`; the
  * next tn_contract_slices on that stream sees the new values.  The host

@@ -78,13 +78,18 @@ _lib.tn_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, ct
 _lib.tn_batch_run.argtypes = [_vp, _vp]
 _lib.tn_batch_destroy.argtypes = [_vp]
 _lib.tn_batch_destroy.restype = None
+_lib.tn_postselect_xeb.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.tn_conditional_sample.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp]
+_lib.tn_probability_histogram.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _vp,
+                                          _vp]
 COST_FEATURES = 16
 
 EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabilities_xeb", "tn_plan_destroy",
             "tn_last_error", "tn_find_order", "tn_circuit_network", "tn_plan_stats", "tn_plan_update_data",
             "tn_plan_profile", "tn_gemm_split_noalloc", "tn_costmodel_create", "tn_costmodel_destroy",
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
-            "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy"]
+            "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
+            "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -307,6 +312,32 @@ def probabilities_xeb(d_amp, n_open, n_qubits, d_prob=None, d_out=None, stream=N
     if not sync:
         return None
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def postselect_xeb(d_amp, n_open, n_qubits, counts, d_order=None, stream=None):
+    """tn_postselect_xeb: XEB of the N most probable bitstrings for each N in
+    counts (sorted on the device); fills d_order (device int64) if given."""
+    cnt = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+    out = np.zeros(max(len(cnt), 1))
+    _check(_lib.tn_postselect_xeb(_dev_ptr(d_amp), int(n_open), int(n_qubits), len(cnt),
+                                  _ptr(cnt) if len(cnt) else None, _ptr(out),
+                                  _dev_ptr(d_order) if d_order is not None else None, _stream_ptr(stream)),
+           "tn_postselect_xeb")
+    return out[:len(cnt)]
+
+
+def conditional_sample(d_amp, n_open, d_u, d_out, stream=None):
+    """tn_conditional_sample: d_out[j] = amplitude index drawn from P(s2|s1)
+    by inverse transform of the uniform d_u[j] (device arrays)."""
+    _check(_lib.tn_conditional_sample(_dev_ptr(d_amp), int(n_open), int(d_u.numel()), _dev_ptr(d_u),
+                                      _dev_ptr(d_out), _stream_ptr(stream)), "tn_conditional_sample")
+
+
+def probability_histogram(d_amp, n_open, scale, n_bins, x_max, d_counts, stream=None):
+    """tn_probability_histogram: counts of p * scale in n_bins bins of [0, x_max)
+    plus an overflow bin (device int64 d_counts[n_bins + 1])."""
+    _check(_lib.tn_probability_histogram(_dev_ptr(d_amp), int(n_open), float(scale), int(n_bins), float(x_max),
+                                         _dev_ptr(d_counts), _stream_ptr(stream)), "tn_probability_histogram")
 
 
 def gemm_split_noalloc(d_a, d_b, d_c, m, n, k, form="tf32x3", stream=None):

@@ -19,7 +19,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels.cu", "tc_gemm.cu", "noalloc.cu", "costmodel.cu"]
+CU_SOURCES = ["kernels.cu", "tc_gemm.cu", "noalloc.cu", "costmodel.cu", "postselect.cu"]
 CPP_SOURCES = ["plan.cpp", "network.cpp", "order.cpp", "api_host.cpp"]
 
 
