@@ -386,6 +386,16 @@ int tn_plan_autotune(tn_plan_t plan, int reps, tn_stream_t stream);
  * CUDA-graph replay.  out must hold 11 doubles. */
 int tn_plan_stats(tn_plan_t plan, double *out);
 
+/*
+ * Text description of a plan's compiled ops, one line each, in execution
+ * order (slice-invariant prologue first, then the per-block body): step,
+ * kind, shape and the kernel variant chosen (small-step kernel and store
+ * mode, tensor-core or FP32 GEMM, split-K, planar outputs), with notes on
+ * declined fusions.  Writes at most cap - 1 characters and a terminating
+ * NUL to out (host, may be NULL when cap is 0); returns the full length.
+ */
+int tn_plan_describe(tn_plan_t plan, char *out, int cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,7 @@ _lib.tn_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, ct
 _lib.tn_batch_run.argtypes = [_vp, _vp]
 _lib.tn_batch_destroy.argtypes = [_vp]
 _lib.tn_batch_destroy.restype = None
+_lib.tn_plan_describe.argtypes = [_vp, _vp, ctypes.c_int]
 _lib.tn_postselect_xeb.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.tn_conditional_sample.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp]
 _lib.tn_probability_histogram.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _vp,
@@ -89,7 +90,7 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_plan_profile", "tn_gemm_split_noalloc", "tn_costmodel_create", "tn_costmodel_destroy",
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
-            "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram"]
+            "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -267,6 +268,15 @@ class Plan:
         if n < 0:
             raise TNError(n, "tn_plan_op_features")
         return out[:COST_FEATURES * n].reshape(n, COST_FEATURES)
+
+    def describe(self):
+        """tn_plan_describe: one line per compiled op (kind, shape, kernel variant)."""
+        n = _lib.tn_plan_describe(self._h, None, 0)
+        if n < 0:
+            raise TNError(n, "tn_plan_describe")
+        buf = ctypes.create_string_buffer(n + 1)
+        _lib.tn_plan_describe(self._h, buf, n + 1)
+        return buf.value.decode()
 
     def stats(self):
         out = np.zeros(16)

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "kernels.h"
@@ -127,6 +128,66 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     }
 }
 
+// ------------------------------------------------- small step, K per warp
+// For steps with a long K (>= 32) and too few (row, output chunk) items to
+// fill the GPU with one thread per item: one warp per item, lanes taking
+// k = lane, lane + 32, ...; the partial sums are combined by warp shuffles
+// and lane j stores output j.
+template <int NC>
+__global__ void __launch_bounds__(kThreads) small_ksplit_kernel(const SmallArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
+    const int SS = HS * KS * NS;
+    float2 *S_sm = reinterpret_cast<float2 *>(smem);
+    uint32_t *offT = reinterpret_cast<uint32_t *>(S_sm + SS);
+    uint32_t *offC = offT + KS;
+    for (int idx = threadIdx.x; idx < SS; idx += blockDim.x) {
+        uint32_t n = idx & (NS - 1), k = (idx >> a.nN) & (KS - 1), h = idx >> (a.nN + a.nK);
+        uint64_t addr = scatter_bits(h, a.hposS, a.nH) | scatter_bits(k, a.kposS, a.nK) |
+                        scatter_bits(n, a.nposS, a.nN);
+        S_sm[idx] = a.S[addr];
+    }
+    for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = (uint32_t)scatter_bits(k, a.kposT, a.nK);
+    for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = (uint32_t)scatter_bits(n, a.nposC, a.nN);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nc = NS < NC ? NS : NC;
+    constexpr int kNcBits = NC == 32 ? 5 : (NC == 16 ? 4 : 3);
+    const int chunk_bits = a.nN > kNcBits ? a.nN - kNcBits : 0;
+    const int rbits = a.row_bits;
+    const int64_t items = a.rows << chunk_bits;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < items; w += warps) {
+        const int64_t r = w & (a.rows - 1);
+        const int n0 = (int)(w >> rbits) * NC;
+        const uint64_t tb = insert_zeros((uint64_t)r, a.tins, a.n_tins);
+        const uint64_t cb = insert_zeros((uint64_t)r, a.cins, a.n_cins);
+        const uint32_t h = gather_bits((uint64_t)r, a.hbitR, a.nH);
+        const float2 *Sh = S_sm + (size_t)h * KS * NS + n0;
+        float2 acc[NC];
+#pragma unroll
+        for (int j = 0; j < NC; j++) acc[j] = make_float2(0.f, 0.f);
+        for (int k = lane; k < KS; k += 32) {
+            const float2 t = a.T[tb + offT[k]];
+            const float2 *Sk = Sh + k * NS;
+#pragma unroll
+            for (int j = 0; j < NC; j++)
+                if (j < nc) cfma(acc[j], t, Sk[j]);
+        }
+        float2 mine = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < NC; j++) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, off);
+                acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, off);
+            }
+            if (lane == j) mine = acc[j];
+        }
+        if (lane < nc) a.C[cb + offC[n0 + lane]] = mine;
+    }
+}
+
 // ------------------------------------------------------ small step, tiled
 // For steps whose K and N are both 4..32 wide and whose T has many rows:
 // a CTA walks tiles of 2^tb consecutive rows.  The tile's T values (a few
@@ -157,11 +218,15 @@ __host__ __device__ constexpr int small_tile_rpt(int KS, int NS, bool direct) {
                                                                                      : 1;
 }
 
-// DIRECT: C's five lowest positions are row bits, so a warp's 32
+// STORE 1 (direct): C's five lowest positions are row bits, so a warp's 32
 // consecutive rows are 32 consecutive C addresses and outputs are stored
-// straight from registers; otherwise they go through shared memory.
-template <int NK, int NN, bool DIRECT>
+// straight from registers.  STORE 0: outputs go through shared memory and
+// out in C's own runs.  STORE 2 (planar): through shared memory and out as
+// the next tensor-core step's hi/lo planes, in destination runs, two
+// neighbouring elements per thread.
+template <int NK, int NN, int STORE>
 __global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArgs a) {
+    constexpr bool DIRECT = STORE == 1;
     constexpr int KS = 1 << NK, NS = 1 << NN, NPT = 4;
     constexpr int NG = NS / NPT, RG = kThreads / NG;
     constexpr int RPT = small_tile_rpt(KS, NS, DIRECT);
@@ -173,10 +238,10 @@ __global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArg
     float2 *T_s = S_s + SS;                                  // two stages of KS * RP
     float2 *C_s = T_s + 2 * KS * RP;                         // NS * RP (unless DIRECT)
     uint64_t *offT_s = reinterpret_cast<uint64_t *>(C_s + (DIRECT ? 0 : NS * RP));
-    uint64_t *offC_s = offT_s + 32;
-    uint32_t *runDstT_s = reinterpret_cast<uint32_t *>(offC_s + 32);
+    uint64_t *offC_s = offT_s + 32;  // 64 low-bit entries, then 64 high-bit entries
+    uint32_t *runDstT_s = reinterpret_cast<uint32_t *>(offC_s + 128);
     uint32_t *dstLoT_s = runDstT_s + 32, *dstHiT_s = dstLoT_s + 64;
-    uint32_t *runSrcC_s = dstHiT_s + 64, *srcLoC_s = runSrcC_s + 32, *srcHiC_s = srcLoC_s + 64;
+    uint32_t *runSrcC_s = dstHiT_s + 64, *srcLoC_s = runSrcC_s + 128, *srcHiC_s = srcLoC_s + 64;
     for (int idx = threadIdx.x; idx < SS; idx += blockDim.x) {
         uint32_t n = idx & (NS - 1), k = (idx >> NN) & (KS - 1), h = idx >> (NN + NK);
         uint64_t addr = scatter_bits(h, a.hposS, a.nH) | scatter_bits(k, a.kposS, NK) | scatter_bits(n, a.nposS, NN);
@@ -185,10 +250,12 @@ __global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArg
     for (int i = threadIdx.x; i < 64; i += blockDim.x) {
         if (i < 32) {
             offT_s[i] = a.runOffT[i];
-            offC_s[i] = a.runOffC[i];
             runDstT_s[i] = a.runDstT[i];
-            runSrcC_s[i] = a.runSrcC[i];
         }
+        offC_s[i] = a.runOffCLo[i];
+        offC_s[64 + i] = a.runOffCHi[i];
+        runSrcC_s[i] = a.runSrcCLo[i];
+        runSrcC_s[64 + i] = a.runSrcCHi[i];
         dstLoT_s[i] = a.dstLoT[i];
         dstHiT_s[i] = a.dstHiT[i];
         srcLoC_s[i] = a.srcLoC[i];
@@ -268,9 +335,34 @@ __global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArg
 #pragma unroll
                 for (int j = 0; j < NPT; j++) C_s[(ngi * NPT + j) * RP + rgi + i * RG] = acc[i][j];
             __syncthreads();
-            for (int f = threadIdx.x; f < EC; f += kThreads) {
-                const uint32_t e = f & lcmask;
-                Ct[offC_s[f >> lc] + e] = C_s[runSrcC_s[f >> lc] + srcLoC_s[e & 63] + srcHiC_s[e >> 6]];
+            if (STORE == 0) {
+                for (int f = threadIdx.x; f < EC; f += kThreads) {
+                    const uint32_t u = f >> lc, e = f & lcmask;
+                    Ct[offC_s[u & 63] + offC_s[64 + (u >> 6)] + e] =
+                        C_s[runSrcC_s[u & 63] + runSrcC_s[64 + (u >> 6)] + srcLoC_s[e & 63] + srcHiC_s[e >> 6]];
+                }
+            } else {
+                // destination of the tile's first element: the row bits above
+                // the tile, each at its destination position
+                uint64_t dbase = 0;
+                for (int i = a.tb; i < a.row_bits; i++) dbase |= ((r0 >> i) & 1ull) << a.drow[i];
+                for (int f = 2 * threadIdx.x; f < EC; f += 2 * kThreads) {
+                    const uint32_t u = f >> lc, e = f & lcmask;  // e even, e + 1 in the same run
+                    const uint32_t rs = runSrcC_s[u & 63] + runSrcC_s[64 + (u >> 6)];
+                    const float2 v0 = C_s[rs + srcLoC_s[e & 63] + srcHiC_s[e >> 6]];
+                    const float2 v1 = C_s[rs + srcLoC_s[(e + 1) & 63] + srcHiC_s[(e + 1) >> 6]];
+                    const uint64_t d = dbase + offC_s[u & 63] + offC_s[64 + (u >> 6)] + e;
+                    const Pieces p0 = split_value(a.planar_mode, v0, 0), p1 = split_value(a.planar_mode, v1, 0);
+                    if (a.planar_mode == 2) {
+                        uint2 *P = reinterpret_cast<uint2 *>(a.C);
+#pragma unroll
+                        for (int q = 0; q < 4; q++) P[(d + q * a.plane_stride) >> 1] = make_uint2(p0.q[q], p1.q[q]);
+                    } else {
+                        uint32_t *P = reinterpret_cast<uint32_t *>(a.C);
+#pragma unroll
+                        for (int q = 0; q < 4; q++) P[(d + q * a.plane_stride) >> 1] = p0.q[q] | (p1.q[q] << 16);
+                    }
+                }
             }
         }
         stage ^= 1;
@@ -599,7 +691,7 @@ cudaError_t launch_small_nc(const SmallArgs &a, int grid, size_t smem, cudaStrea
 }
 
 namespace {
-constexpr size_t kTiledTableBytes = 2 * 32 * 8 + (32 + 64 + 64) * 4 * 2;
+constexpr size_t kTiledTableBytes = (32 + 128) * 8 + (32 + 64 + 64 + 128 + 64 + 64) * 4;
 size_t small_tiled_smem(const SmallArgs &a) {
     const size_t KS = (size_t)1 << a.nK, NS = (size_t)1 << a.nN, HS = (size_t)1 << a.nH;
     const size_t RP = ((size_t)1 << a.tb) + 1;
@@ -662,16 +754,77 @@ bool tile_runs(int rank, int tb, int nX, const int *xpos, int RP, int &l, int &n
     return true;
 }
 
-template <int NK, int NN, bool DIRECT>
+// contiguous-run structure of a tile given each tile bit's position in the
+// tensor written and its weight (shared-memory index step); run tables in
+// two levels (low and high six bits of the run index)
+bool tile_runs_pos(std::vector<std::pair<int, uint32_t>> bits, int &l, int &n_run, uint64_t *off_lo,
+                   uint64_t *off_hi, uint32_t *sm_lo, uint32_t *sm_hi, uint32_t *lo, uint32_t *hi) {
+    std::sort(bits.begin(), bits.end());
+    int p = 0;
+    while (p < (int)bits.size() && bits[p].first == p) p++;
+    l = p;
+    const int nh = (int)bits.size() - l;
+    if (l > 12 || nh > 12) return false;
+    n_run = 1 << nh;
+    for (int v = 0; v < 64; v++) {
+        uint64_t ol = 0, oh = 0;
+        uint32_t sl = 0, sh = 0;
+        for (int i = 0; i < 6; i++) {
+            if (((v >> i) & 1) == 0) continue;
+            if (i < nh) {
+                ol |= 1ull << bits[l + i].first;
+                sl += bits[l + i].second;
+            }
+            if (i + 6 < nh) {
+                oh |= 1ull << bits[l + 6 + i].first;
+                sh += bits[l + 6 + i].second;
+            }
+        }
+        off_lo[v] = ol;
+        off_hi[v] = oh;
+        sm_lo[v] = sl;
+        sm_hi[v] = sh;
+    }
+    for (int v = 0; v < 64; v++) {
+        uint32_t a = 0, b = 0;
+        for (int j = 0; j < 6; j++) {
+            if (((v >> j) & 1) == 0) continue;
+            if (j < l) a += bits[j].second;
+            if (j + 6 < l) b += bits[j + 6].second;
+        }
+        lo[v] = a;
+        hi[v] = b;
+    }
+    return true;
+}
+
+// the C tile's bits: the first tb row positions (weights 1 << i) and the N
+// positions (weights (1 << j) * RP), each at position dest(q) of C position q
+std::vector<std::pair<int, uint32_t>> c_tile_bits(const SmallArgs &a, int row_bits, int tb, int RP,
+                                                  const int *cdest) {
+    const int rc = row_bits + a.nN;
+    std::vector<char> isn(rc, 0);
+    for (int j = 0; j < a.nN; j++) isn[a.nposC[j]] = 1;
+    std::vector<int> rowpos;
+    for (int q = 0; q < rc; q++)
+        if (!isn[q]) rowpos.push_back(q);
+    std::vector<std::pair<int, uint32_t>> bits;
+    for (int i = 0; i < tb; i++) bits.push_back({cdest ? cdest[rowpos[i]] : rowpos[i], 1u << i});
+    for (int j = 0; j < a.nN; j++)
+        bits.push_back({cdest ? cdest[a.nposC[j]] : a.nposC[j], (1u << j) * (uint32_t)RP});
+    return bits;
+}
+
+template <int NK, int NN, int STORE>
 cudaError_t launch_small_tiled_t(const SmallArgs &a, cudaStream_t s) {
     static int occ = 0;
     static size_t occ_smem = 0;
     const size_t smem = small_tiled_smem(a);
     if (occ == 0 || occ_smem != smem) {
-        cudaFuncSetAttribute(small_tiled_kernel<NK, NN, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(small_tiled_kernel<NK, NN, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              160 * 1024);
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, small_tiled_kernel<NK, NN, DIRECT>, kThreads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, small_tiled_kernel<NK, NN, STORE>, kThreads, smem) !=
                 cudaSuccess || o < 1)
             o = 1;
         occ = o;
@@ -679,13 +832,15 @@ cudaError_t launch_small_tiled_t(const SmallArgs &a, cudaStream_t s) {
     }
     const int64_t tiles = a.rows >> a.tb;
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)152 * occ);
-    small_tiled_kernel<NK, NN, DIRECT><<<grid, kThreads, smem, s>>>(a);
+    small_tiled_kernel<NK, NN, STORE><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int NK, int NN>
 cudaError_t launch_small_tiled_kn(const SmallArgs &a, cudaStream_t s) {
-    return a.tiled == 2 ? launch_small_tiled_t<NK, NN, true>(a, s) : launch_small_tiled_t<NK, NN, false>(a, s);
+    if (a.tiled == 2) return launch_small_tiled_t<NK, NN, 1>(a, s);
+    if (a.tiled == 3) return launch_small_tiled_t<NK, NN, 2>(a, s);
+    return launch_small_tiled_t<NK, NN, 0>(a, s);
 }
 
 template <int NK>
@@ -735,12 +890,75 @@ void prepare_small_tiled(SmallArgs &a) {
     if (!tile_runs(row_bits + nK, tb, nK, a.kposT, RT + 1, t.lt, t.n_runT, t.runOffT, t.runDstT, t.dstLoT,
                    t.dstHiT))
         return;
-    if (!tile_runs(row_bits + nN, tb, nN, a.nposC, RT + 1, t.lc, t.n_runC, t.runOffC, t.runSrcC, t.srcLoC,
-                   t.srcHiC))
+    if (!tile_runs_pos(c_tile_bits(a, row_bits, tb, RT + 1, nullptr), t.lc, t.n_runC, t.runOffCLo, t.runOffCHi,
+                       t.runSrcCLo, t.runSrcCHi, t.srcLoC, t.srcHiC))
         return;
     t.tiled = direct ? 2 : 1;
     if (small_tiled_smem(t) > 150 * 1024) return;
     a = t;
+}
+
+template <int NC>
+cudaError_t launch_small_ksplit_nc(const SmallArgs &a, int grid, size_t smem, cudaStream_t s) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(small_ksplit_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr_done = true;
+    }
+    small_ksplit_kernel<NC><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small_ksplit(const SmallArgs &a, int nc, int grid, size_t smem, cudaStream_t s) {
+    if (nc == 8) return launch_small_ksplit_nc<8>(a, grid, smem, s);
+    if (nc == 16) return launch_small_ksplit_nc<16>(a, grid, smem, s);
+    return launch_small_ksplit_nc<32>(a, grid, smem, s);
+}
+
+int prepare_small_planar(SmallArgs &a, const int *cdest, int mode, int64_t plane_stride, int *run_bits) {
+    if (run_bits) *run_bits = -1;
+    if (!a.tiled || (mode != 1 && mode != 2)) return 1;
+    SmallArgs t = a;
+    const int KS = 1 << a.nK, NS = 1 << a.nN;
+    const int rpt = small_tile_rpt(KS, NS, false);
+    const int RT = (1024 / NS) * rpt;
+    if (RT > a.rows) return 2;
+    int tb = 0;
+    while ((1 << tb) < RT) tb++;
+    for (int j = 0; j < a.nH; j++)
+        if (a.hbitR[j] < tb) return 2;
+    int row_bits = 0;
+    while (((int64_t)1 << row_bits) < a.rows) row_bits++;
+    const int rc = row_bits + a.nN;
+    if (rc > kMaxRank) return 2;
+    t.tb = tb;
+    t.rpt = rpt;
+    t.npt = 4;
+    t.row_bits = row_bits;
+    if (!tile_runs(row_bits + a.nK, tb, a.nK, a.kposT, RT + 1, t.lt, t.n_runT, t.runOffT, t.runDstT, t.dstLoT,
+                   t.dstHiT))
+        return 3;
+    const std::vector<std::pair<int, uint32_t>> bits = c_tile_bits(a, row_bits, tb, RT + 1, cdest);
+    for (const auto &b : bits)
+        if (b.first < 0 || b.first >= rc) return 4;
+    const bool runs_ok = tile_runs_pos(bits, t.lc, t.n_runC, t.runOffCLo, t.runOffCHi, t.runSrcCLo, t.runSrcCHi,
+                                       t.srcLoC, t.srcHiC);
+    if (run_bits) *run_bits = t.lc;
+    if (!runs_ok || t.lc < 5) return 4;  // destination runs of at least 32 elements
+    // destination of each row bit above the tile
+    std::vector<char> isn(rc, 0);
+    for (int j = 0; j < a.nN; j++) isn[a.nposC[j]] = 1;
+    std::vector<int> rowpos;
+    for (int q = 0; q < rc; q++)
+        if (!isn[q]) rowpos.push_back(q);
+    std::memset(t.drow, 0, sizeof t.drow);
+    for (int i = tb; i < row_bits; i++) t.drow[i] = (int8_t)cdest[rowpos[i]];
+    t.planar_mode = mode;
+    t.plane_stride = plane_stride;
+    t.tiled = 3;
+    if (small_tiled_smem(t) > 150 * 1024) return 5;
+    a = t;
+    return 0;
 }
 
 cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
@@ -759,7 +977,13 @@ cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
     if (a.rows < 1 || (a.rows & (a.rows - 1)) != 0) return cudaErrorInvalidValue;
     a.row_bits = __builtin_ctzll((unsigned long long)a.rows);
     const int nc = NS <= 8 ? 8 : (NS <= 16 ? 16 : 32);  // outputs per work item
-    const int grid = grid_for(a.rows * (NS > nc ? NS / nc : 1));
+    const int64_t items = a.rows * (NS > nc ? NS / nc : 1);
+    if (a.nK >= 5 && items < 152 * 128) {
+        // long K, few items: one warp per item (K split over the lanes)
+        const int grid = (int)std::min<int64_t>((items * 32 + kThreads - 1) / kThreads, kMaxBlocks);
+        return launch_small_ksplit(a, nc, grid, smem, s);
+    }
+    const int grid = grid_for(items);
     if (nc == 8) return launch_small_nc<8>(a, grid, smem, s);
     if (nc == 16) return launch_small_nc<16>(a, grid, smem, s);
     return launch_small_nc<32>(a, grid, smem, s);

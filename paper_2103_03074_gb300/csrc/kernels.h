@@ -41,20 +41,41 @@ struct SmallArgs {
     // elements are 2^(tb + nK) values made of n_runT contiguous runs of 2^lt
     // elements (T offset tbase(r0) + runOffT[u] + e), staged in shared memory
     // at [k][row] (row stride 2^tb + 1) at runDstT[u] + dstLoT[e & 63] +
-    // dstHiT[e >> 6]; the C tile likewise, read back from [n][row].
+    // dstHiT[e >> 6]; the C tile likewise (two-level run tables), read back
+    // from [n][row].
     int tiled;
     int tb;              // log2 rows per tile
     int rpt, npt;        // rows and outputs per thread
     int lt, lc;          // contiguous run bits of the T and C tiles
     int n_runT, n_runC;  // runs per tile
-    uint64_t runOffT[32], runOffC[32];
+    uint64_t runOffT[32];
     uint32_t runDstT[32], dstLoT[64], dstHiT[64];
-    uint32_t runSrcC[32], srcLoC[64], srcHiC[64];
+    // C runs u (up to 4096): offset runOffCLo[u & 63] + runOffCHi[u >> 6],
+    // shared-memory index runSrcCLo[u & 63] + runSrcCHi[u >> 6]
+    uint64_t runOffCLo[64], runOffCHi[64];
+    uint32_t runSrcCLo[64], runSrcCHi[64], srcLoC[64], srcHiC[64];
+    // planar store (tiled == 3): instead of complex64 C, the tile writes the
+    // next tensor-core step's hi/lo planes (planar_mode 1 bf16, 2 tf32) at C
+    // (the planes' base), plane q at offset q * plane_stride; the C tables
+    // above then describe runs in the destination layout, and row bit i of r
+    // (i >= tb) lands at destination position drow[i]
+    int planar_mode;
+    int64_t plane_stride;
+    int8_t drow[kMaxRank];
 };
 
 // Decide whether a small step takes the tiled kernel and fill its tables
 // (host; plan compile time).  Needs rows set and the bit maps complete.
 void prepare_small_tiled(SmallArgs &a);
+
+// Make a tiled small step write split planes (mode 1 bf16, 2 tf32; planes of
+// plane_stride elements) in a destination layout given by cdest[q], the
+// destination position of C position q.  Returns 0 on success; otherwise a
+// unchanged and a reason: 1 not tiled, 2 tile does not fit the rows or the
+// batch bits, 3 T tables, 4 destination runs shorter than 32 elements or
+// more than 32 runs per tile (*run_bits = the run length's bits), 5 shared
+// memory.
+int prepare_small_planar(SmallArgs &a, const int *cdest, int mode, int64_t plane_stride, int *run_bits);
 
 // Bit permutation through a shared-memory tile, optionally fused with the
 // hi/lo split of split-precision GEMM operands.

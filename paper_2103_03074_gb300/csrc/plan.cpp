@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -71,6 +72,7 @@ struct Op {
     TcGemm tc;  // tensor-core GEMM (gemm_variant 1), resolved after arena allocation
     double macs = 0, bytes = 0;
     int gemm_variant = 0;  // 0: FP32 CUDA cores, 1: tensor-core split form
+    std::string note;      // plan-time decisions, for tn_plan_describe
 };
 
 struct Buf {
@@ -635,6 +637,33 @@ int64_t compile(tn_plan &P, int nb) {
                 // at least 64 bytes per plane).  Not for the scaled forms:
                 // their plane scale is the max of the whole output, known
                 // only after the producer's last tile.
+                // likewise a tiled small step: its store phase writes the
+                // planes in destination runs
+                if (P.opts.tc_planar >= 0 && !scaled && (mode == 1 || mode == 2) && src.lay.size() == dl.size()) {
+                    Op *prod = producer_of(ops, src.where);
+                    if (prod && prod->kind == OP_SMALL && prod->small.tiled) {
+                        const int r = (int)dl.size();
+                        std::vector<int> cdest(r, -1);
+                        for (int q = 0; q < r; q++) {
+                            const int di = pos_of(dl, src.lay[r - 1 - q]);
+                            cdest[q] = di;  // pos_of gives the bit position (first label = MSB)
+                        }
+                        SmallArgs sa = prod->small;
+                        int run_bits = -1;
+                        const int why = prepare_small_planar(sa, cdest.data(), mode, elems, &run_bits);
+                        prod->note = why == 0 ? "planar store" : "planar store declined: reason " + std::to_string(why) +
+                                                                     ", destination run bits " + std::to_string(run_bits);
+                        if (why == 0) {
+                            Operand dst;
+                            dst.buf = new_buf((np * elems * es + 7) / 8);
+                            prod->small = sa;
+                            prod->out = dst;
+                            prod->bytes += (double)np * es * (double)elems - 8.0 * (double)elems;
+                            split_idx++;
+                            return dst;
+                        }
+                    }
+                }
                 if (P.opts.tc_planar >= 0 && !scaled && planar_candidate(ops, src.where)) {
                     Op *prod = producer_of(ops, src.where);
                     TcPlanarOut o;
@@ -1634,6 +1663,52 @@ extern "C" void tn_plan_destroy(tn_plan_t P) {
     if (P->g_pro) cudaGraphExecDestroy(P->g_pro);
     if (P->g_body) cudaGraphExecDestroy(P->g_body);
     delete P;
+}
+
+extern "C" int tn_plan_describe(tn_plan_t P, char *out, int cap) {
+    if (!P || cap < 0 || (cap > 0 && !out)) return fail(TN_ERR_ARG, "bad arguments");
+    std::string txt;
+    char line[512];
+    auto put = [&](const char *phase, const Op &op) {
+        switch (op.kind) {
+        case OP_SMALL: {
+            const SmallArgs &a = op.small;
+            const char *kern = a.tiled == 1 ? "tiled, staged C" : a.tiled == 2 ? "tiled, direct C"
+                               : a.tiled == 3 ? "tiled, planar" : "row";
+            std::snprintf(line, sizeof line, "%s step %d small rows=%lld K=%d N=%d H=%d kernel=%s", phase, op.step,
+                          (long long)a.rows, 1 << a.nK, 1 << a.nN, 1 << a.nH, kern);
+            break;
+        }
+        case OP_GEMM:
+            if (op.gemm_variant == 1)
+                std::snprintf(line, sizeof line, "%s step %d gemm H=%lld M=%lld N=%lld K=%lld tensor-core ksplit=%d out=%s",
+                              phase, op.step, (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N,
+                              (long long)op.gemm.K, op.tc.ksplit, op.tc.out.mode ? "planes" : "complex64");
+            else
+                std::snprintf(line, sizeof line, "%s step %d gemm H=%lld M=%lld N=%lld K=%lld fp32", phase, op.step,
+                              (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N, (long long)op.gemm.K);
+            break;
+        case OP_PERMUTE:
+        case OP_SPLIT:
+            std::snprintf(line, sizeof line, "%s step %d %s rank=%d mode=%d", phase, op.step,
+                          op.kind == OP_SPLIT ? "split" : "permute", op.bp.rank, op.bp.mode);
+            break;
+        case OP_MAXABS:
+            std::snprintf(line, sizeof line, "%s step %d maxabs n=%lld", phase, op.step, (long long)op.mx.n);
+            break;
+        }
+        txt += line;
+        if (!op.note.empty()) txt += " (" + op.note + ")";
+        txt += "\n";
+    };
+    for (const auto &op : P->prologue) put("prologue", op);
+    for (const auto &op : P->batch) put("batch", op);
+    if (cap > 0) {
+        const size_t n = std::min(txt.size(), (size_t)cap - 1);
+        std::memcpy(out, txt.data(), n);
+        out[n] = 0;
+    }
+    return (int)txt.size();
 }
 
 extern "C" int tn_plan_stats(tn_plan_t P, double *out) {
