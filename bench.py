@@ -226,7 +226,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Sycamore-style circuit)",
-            "config": {"workload": "rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 2^8 slices",
+            "config": {"workload": WORKLOADS["rect5x6"]["desc"],
                        "step": "one slice contracted by the CPU FP64 oracle"},
             "cpu_baseline": {"value": v, "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{args.steps} slices per timed run, one per step"},
