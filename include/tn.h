@@ -141,7 +141,9 @@ typedef struct {
  * ("Dynamic slicing" paragraph; Fig. 3 pairwise steps).
  *   ranks[n_tensors]            rank of each tensor
  *   labels[sum ranks]           concatenated label lists (host)
- *   data[2 * sum 2^rank]        concatenated interleaved complex64 values (host, copied)
+ *   data[2 * sum 2^rank]        concatenated interleaved complex64 values (host, copied;
+ *                               NULL: the leaves start as zeros and are set later
+ *                               with tn_plan_update_data)
  *   n_labels, bond_dims         bond_dims[label] must be 2 for every label used (may be NULL)
  *   open_labels[n_open]         amplitude-tensor axis order, [0] = MSB
  *   sliced_labels[n_sliced]     slice id bit j -> sliced_labels[j]; must not be open
@@ -272,6 +274,48 @@ const char *tn_last_error(void);
 int tn_find_order(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                   const int32_t *open_labels, const tn_search_opts *opts, int32_t *out_tree,
                   int max_sliced, int32_t *out_sliced, int *out_n_sliced, double *stats);
+
+/*
+ * Order search for the two-stage big-head form ("Big-head simulation"
+ * section, Fig. 1; appendix on the first cut): the tail starts with every
+ * tensor holding an open label and grows one neighbouring tensor at a time,
+ * always the one leaving the smallest cut, up to tail_max tensors (0: half
+ * the network); the prefix with the smallest cut is kept.  Then the head's
+ * order is searched with the cut labels as its open labels (sliced as opts'
+ * cap or count asks; the sliced labels are internal to the head) and the
+ * tail's with cut + open labels (not sliced), and the two trees are joined
+ * at the root: out_tree (2 * (n_tensors - 1) SSA ids) has the cut at its
+ * last step.  stats[7] = {log2 head MACs per slice, log2 head width,
+ * head slices, log2 tail MACs, log2 tail width, cut bonds, log2 total MACs}.
+ */
+int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                            const int32_t *open_labels, int tail_max, const tn_search_opts *opts, int32_t *out_tree,
+                            int max_sliced, int32_t *out_sliced_head, int *out_n_sliced_head, double *stats);
+
+/*
+ * Two-stage big-head contraction ("Big-head simulation" section): the
+ * tree's last step must join the head (no open label) and the tail (every
+ * open label); the labels they share are the first cut C.  Stage 1
+ * contracts the head, summed over sliced_head (labels internal to the
+ * head), into v_head over C (complex128, FP64 sum; axes C in increasing
+ * label order, first = most significant).  Stage 2 contracts the tail with
+ * v_head as one more leaf (rounded to complex64), summed over sliced_tail
+ * (tail labels or cut labels, not open), into d_amp (device complex128
+ * [2^n_open], overwritten).  v_head depends only on the closed bits, so one
+ * head contraction serves every assignment of the open qubits; slicing cut
+ * bonds in stage 2 bounds the tail's intermediates.  d_vhead (device
+ * complex128 [2^|C|], may be NULL) receives v_head; *n_cut (may be NULL)
+ * receives |C|.  Network arguments, forms and options as for
+ * tn_plan_create; the two plans are built, run and released inside the
+ * call, which synchronises `stream`.  Errors: TN_ERR_ARG when the root
+ * step is not such a cut, a sliced label is on the wrong side or |C| > 40;
+ * else as tn_plan_create and tn_contract_slices.
+ */
+int tn_head_tail_amplitudes(int n_tensors, const int32_t *ranks, const int32_t *labels, const float *data,
+                            int n_open, const int32_t *open_labels, int n_steps, const int32_t *tree,
+                            int n_sliced_head, const int32_t *sliced_head, int n_sliced_tail,
+                            const int32_t *sliced_tail, tn_form form, const tn_plan_opts *opts, double *d_amp,
+                            double *d_vhead, int *n_cut, tn_stream_t stream);
 
 /*
  * The network tn_amplitudes contracts for a circuit (gate absorption and

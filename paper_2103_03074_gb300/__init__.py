@@ -79,6 +79,12 @@ _lib.tn_batch_run.argtypes = [_vp, _vp]
 _lib.tn_batch_destroy.argtypes = [_vp]
 _lib.tn_batch_destroy.restype = None
 _lib.tn_plan_describe.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.tn_find_order_head_tail.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int,
+                                         ctypes.POINTER(SearchOpts), _vp, ctypes.c_int, _vp,
+                                         ctypes.POINTER(ctypes.c_int), _vp]
+_lib.tn_head_tail_amplitudes.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                         ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int,
+                                         ctypes.POINTER(PlanOpts), _vp, _vp, ctypes.POINTER(ctypes.c_int), _vp]
 _lib.tn_postselect_xeb.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.tn_conditional_sample.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp]
 _lib.tn_probability_histogram.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _vp,
@@ -90,7 +96,8 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_plan_profile", "tn_gemm_split_noalloc", "tn_costmodel_create", "tn_costmodel_destroy",
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
-            "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe"]
+            "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
+            "tn_find_order_head_tail", "tn_head_tail_amplitudes"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -205,6 +212,46 @@ def find_order(labels, open_labels, opts=None, max_sliced=64):
     steps = [(int(tree[2 * i]), int(tree[2 * i + 1])) for i in range(n - 1)]
     stats = dict(log2_total=st[0], log2_width=st[1], n_sliced=int(st[2]), log2_slice=st[3])
     return steps, [int(x) for x in sl[:nsl.value]], stats
+
+
+def find_order_head_tail(labels, open_labels, tail_max=0, opts=None, max_sliced=64):
+    """tn_find_order_head_tail: (tree whose last step is the first cut, head
+    sliced labels, stats dict)."""
+    ranks = np.asarray([len(l) for l in labels], dtype=np.int32)
+    flat = np.asarray([x for l in labels for x in l] or [0], dtype=np.int32)
+    ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
+    tree = np.zeros(2 * (len(labels) - 1), dtype=np.int32)
+    sl = np.zeros(max_sliced, dtype=np.int32)
+    nsl = ctypes.c_int(0)
+    st = np.zeros(7)
+    o = opts if opts is not None else search_opts()
+    _check(_lib.tn_find_order_head_tail(len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol),
+                                        int(tail_max), ctypes.byref(o), _ptr(tree), max_sliced, _ptr(sl),
+                                        ctypes.byref(nsl), _ptr(st)), "tn_find_order_head_tail")
+    steps = [(int(tree[2 * t]), int(tree[2 * t + 1])) for t in range(len(labels) - 1)]
+    keys = ["log2_head_slice", "log2_head_width", "n_sliced_head", "log2_tail", "log2_tail_width", "n_cut",
+            "log2_total"]
+    return steps, [int(x) for x in sl[:nsl.value]], dict(zip(keys, (float(x) for x in st)))
+
+
+def head_tail_amplitudes(labels, tensors, open_labels, tree, sliced_head, sliced_tail, d_amp, form="fp32",
+                         opts=None, d_vhead=None, stream=None):
+    """tn_head_tail_amplitudes: two-stage contraction into d_amp (device
+    complex128); returns the number of cut bonds."""
+    ranks, flat, data = _flatten(labels, tensors)
+    ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
+    tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
+    sh = np.asarray(list(sliced_head) or [0], dtype=np.int32)
+    st = np.asarray(list(sliced_tail) or [0], dtype=np.int32)
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    o = opts if opts is not None else plan_opts()
+    nc = ctypes.c_int(0)
+    _check(_lib.tn_head_tail_amplitudes(len(labels), _ptr(ranks), _ptr(flat), _ptr(data), len(open_labels),
+                                        _ptr(ol), len(tree), _ptr(tr), len(sliced_head), _ptr(sh),
+                                        len(sliced_tail), _ptr(st), f, ctypes.byref(o), _dev_ptr(d_amp),
+                                        _dev_ptr(d_vhead) if d_vhead is not None else None, ctypes.byref(nc),
+                                        _stream_ptr(stream)), "tn_head_tail_amplitudes")
+    return nc.value
 
 
 class Plan:

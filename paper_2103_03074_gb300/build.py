@@ -20,7 +20,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels.cu", "tc_gemm.cu", "noalloc.cu", "costmodel.cu", "postselect.cu"]
-CPP_SOURCES = ["plan.cpp", "network.cpp", "order.cpp", "api_host.cpp"]
+CPP_SOURCES = ["plan.cpp", "network.cpp", "order.cpp", "api_host.cpp", "headtail.cpp"]
 
 
 def _newer(src_paths, out):

@@ -1020,6 +1020,21 @@ cudaError_t launch_extract(const ExtractEntry *d_entries, int n_entries, int max
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void c128_to_c64_kernel(const double2 *src, float2 *dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        dst[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+}  // namespace
+
+cudaError_t launch_c128_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    c128_to_c64_kernel<<<grid_for(n), kThreads, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_maxabs(const MaxAbsArgs &a, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.slot, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;

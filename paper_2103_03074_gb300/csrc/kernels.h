@@ -213,5 +213,7 @@ cudaError_t launch_accum(const AccumArgs &a, cudaStream_t s);
 cudaError_t launch_prob_xeb(const double2 *amp, int64_t n, double *prob, double *d_out3, int scale_exp,
                             cudaStream_t s);
 cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s);
+// dst[i] = complex64(src[i]) (round to nearest)
+cudaError_t launch_c128_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t s);
 
 }  // namespace tn

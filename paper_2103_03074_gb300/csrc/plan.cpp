@@ -1081,7 +1081,7 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
                               int n_steps, const int32_t *tree, tn_form form, const tn_plan_opts *opts) {
     if (!out) return fail(TN_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (n_tensors <= 0 || !ranks || !data) return fail(TN_ERR_ARG, "need at least one tensor");
+    if (n_tensors <= 0 || !ranks) return fail(TN_ERR_ARG, "need at least one tensor");
     if (n_open < 0 || n_open > kMaxRank || (n_open > 0 && !open_labels)) return fail(TN_ERR_ARG, "bad open labels");
     if (n_sliced < 0 || n_sliced > 62 || (n_sliced > 0 && !sliced_labels)) return fail(TN_ERR_ARG, "bad sliced labels");
     if (n_steps != n_tensors - 1 || (n_steps > 0 && !tree)) return fail(TN_ERR_ARG, "tree must have n_tensors - 1 steps");
@@ -1166,7 +1166,8 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
     P->leaf_bytes = leaf_bytes;
     e = cudaMalloc(&P->d_leaves, std::max<int64_t>(leaf_bytes, 16));
     if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc leaves");
-    e = cudaMemcpy(P->d_leaves, data, leaf_bytes, cudaMemcpyHostToDevice);
+    e = data ? cudaMemcpy(P->d_leaves, data, leaf_bytes, cudaMemcpyHostToDevice)
+             : cudaMemset(P->d_leaves, 0, std::max<int64_t>(leaf_bytes, 16));  // leaves set later
     if (e != cudaSuccess) return cuda_fail(e, "copy leaves");
     e = cudaMalloc(&P->d_arena, std::max<int64_t>(arena, 256));
     if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc arena");
@@ -1664,6 +1665,28 @@ extern "C" void tn_plan_destroy(tn_plan_t P) {
     if (P->g_body) cudaGraphExecDestroy(P->g_body);
     delete P;
 }
+
+namespace tn {
+// replace leaf `leaf`'s values by host complex64 data (interleaved, 2^rank
+// values), stream-ordered
+int plan_load_leaf_host(tn_plan_t P, int leaf, const float *src, cudaStream_t s) {
+    if (!P || !src || leaf < 0 || leaf >= P->n_tensors) return fail(TN_ERR_ARG, "plan_load_leaf_host: bad arguments");
+    const int64_t n = (int64_t)1 << P->labels[leaf].size();
+    cudaError_t e = cudaMemcpyAsync(P->d_leaves + P->leaf_off[leaf], src, sizeof(float2) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("plan_load_leaf_host: ") + cudaGetErrorString(e));
+    return TN_OK;
+}
+
+// replace leaf `leaf`'s values by complex128 device data (rounded to
+// complex64), stream-ordered; the leaf keeps its rank and labels
+int plan_load_leaf_c128(tn_plan_t P, int leaf, const double *d_src, cudaStream_t s) {
+    if (!P || !d_src || leaf < 0 || leaf >= P->n_tensors) return fail(TN_ERR_ARG, "plan_load_leaf_c128: bad arguments");
+    const int64_t n = (int64_t)1 << P->labels[leaf].size();
+    cudaError_t e = launch_c128_to_c64(reinterpret_cast<const double2 *>(d_src), P->d_leaves + P->leaf_off[leaf], n, s);
+    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("plan_load_leaf_c128: ") + cudaGetErrorString(e));
+    return TN_OK;
+}
+}  // namespace tn
 
 extern "C" int tn_plan_describe(tn_plan_t P, char *out, int cap) {
     if (!P || cap < 0 || (cap > 0 && !out)) return fail(TN_ERR_ARG, "bad arguments");

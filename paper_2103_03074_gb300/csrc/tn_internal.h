@@ -66,4 +66,10 @@ bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::v
 
 tn_search_opts default_search_opts();
 
+// plan.cpp: replace a plan leaf's values by complex128 device data (rounded
+// to complex64), stream-ordered
+int plan_load_leaf_c128(tn_plan_t plan, int leaf, const double *d_src, CUstream_st *stream);
+// plan.cpp: replace a plan leaf's values by host complex64 data, stream-ordered
+int plan_load_leaf_host(tn_plan_t plan, int leaf, const float *src, CUstream_st *stream);
+
 }  // namespace tn

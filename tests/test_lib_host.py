@@ -128,3 +128,32 @@ def test_plan_rejects_dangling_label(tn):
     net = random_network(3, n_tensors=5, n_bonds=7, n_open=2, max_rank=5)
     err = _plan_args_error(tn, open=net.open_labels[:1])
     assert err.code == -1
+
+
+def test_head_tail_order_has_the_cut_at_its_root(tn):
+    """tn_find_order_head_tail: a valid SSA tree whose last step joins a side
+    without open labels (the head) and a side holding all of them; the head
+    is sliced as asked; the reported cut equals the labels the sides share."""
+    from tn_inputs import sycamore_circuit, random_bits
+    circ = sycamore_circuit("rect", 4, 5, 10, 77)
+    L, T, O = tn.circuit_network(circ, random_bits(20, 77), list(range(15, 20)))
+    tree, sliced, st = tn.find_order_head_tail(L, O, opts=tn.search_opts(trials=64, n_sliced=2))
+    n = len(L)
+    assert len(tree) == n - 1 and len(sliced) == 2
+    used = set()
+    for t, (a, b) in enumerate(tree):
+        assert 0 <= a < n + t and 0 <= b < n + t and a != b and a not in used and b not in used
+        used.update((a, b))
+
+    def leaves(x):
+        return [x] if x < n else leaves(tree[x - n][0]) + leaves(tree[x - n][1])
+    sides = [set(), set()]
+    for k, root in enumerate(tree[-1]):
+        for i in leaves(root):
+            sides[k].update(L[i])
+    opens = [len(s & set(O)) for s in sides]
+    assert sorted(opens) == [0, len(O)]
+    head = sides[0] if opens[0] == 0 else sides[1]
+    tail = sides[1] if opens[0] == 0 else sides[0]
+    assert st["n_cut"] == len(head & tail)
+    assert all(x in head and x not in tail for x in sliced)
