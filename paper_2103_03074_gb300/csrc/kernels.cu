@@ -1037,6 +1037,7 @@ cudaError_t launch_c128_to_c64(const double2 *src, float2 *dst, int64_t n, cudaS
 
 cudaError_t launch_maxabs(const MaxAbsArgs &a, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.slot, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess && a.companion) e = cudaMemsetAsync(a.companion, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     maxabs_kernel<<<grid_for(a.n), kThreads, 0, s>>>(a);
     return cudaGetLastError();

@@ -114,6 +114,7 @@ struct MaxAbsArgs {
     const float2 *in;
     int64_t n;
     unsigned *slot;
+    unsigned *companion;  // optional: zeroed with the slot (a consumer's true-max slot)
 };
 
 // power-of-two exponent e of the FP16S scale for a max-abs value: the largest

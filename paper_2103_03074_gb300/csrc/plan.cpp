@@ -599,7 +599,10 @@ int64_t compile(tn_plan &P, int nb) {
             const int mode = P.form == TN_FP16S ? 3 : P.form == TN_FP16X3 ? 4 : (es == 2 ? 1 : 2);
             Operand slots;
             if (scaled) {
-                slots.buf = new_buf(1);  // two uint32 slots
+                // four uint32 slots: the A and B operands' plane scales (max
+                // |re|, |im|, or a planar producer's bound-derived value), then
+                // a planar producer's true max of each (0 otherwise)
+                slots.buf = new_buf(2);
                 int idx = 0;
                 for (const NodeRec *src : {&A, &B}) {
                     // an operand written by a tensor-core GEMM without split K
@@ -664,7 +667,8 @@ int64_t compile(tn_plan &P, int nb) {
                         }
                     }
                 }
-                if (P.opts.tc_planar >= 0 && !scaled && planar_candidate(ops, src.where)) {
+                if (P.opts.tc_planar >= 0 && planar_candidate(ops, src.where) &&
+                    (!scaled || producer_of(ops, src.where)->maxout.buf >= 0)) {
                     Op *prod = producer_of(ops, src.where);
                     TcPlanarOut o;
                     const int nHp = __builtin_ctzll((uint64_t)prod->gemm.H);
@@ -855,6 +859,7 @@ void resolve_all(tn_plan &P) {
         case OP_MAXABS:
             op.mx.in = resolve(P, op.in0);
             op.mx.slot = reinterpret_cast<unsigned *>(resolve(P, op.out)) + op.aux_idx;
+            op.mx.companion = op.mx.slot + 2;  // the operand's true-max slot
             break;
         case OP_GEMM:
             if (op.gemm_variant == 1) {

@@ -318,7 +318,7 @@ __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane
 // planes: warp fw of the 8 epilogue warps takes the groups j_hi = fw, fw + 8,
 // ...; each lane two neighbouring elements of a group.
 __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_t mh, int64_t n0, const float2 *st,
-                                             const uint2 *jtab, const PlanarLane &L, int fw, int lane) {
+                                             const uint2 *jtab, const PlanarLane &L, int fw, int lane, int e) {
     const uint64_t base = scatter8((uint64_t)h, o.hpos, o.nH) | scatter8((uint64_t)mh, o.mpos, o.nM) |
                           scatter8((uint64_t)n0, o.npos, o.nN);
     const int nlo = o.ntb < 6 ? o.ntb : 6;
@@ -330,10 +330,10 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_
         const float2 b = st[(int)g.x + L.s[1]];
         const uint64_t d0 = base + g.y + L.d[0];
         if (L.pair) {
-            plane_store2(o, d0, a, b, 0);
+            plane_store2(o, d0, a, b, e);
         } else {
-            if (v0) plane_store1(o, d0, a, 0);
-            if (v1) plane_store1(o, base + g.y + L.d[1], b, 0);
+            if (v0) plane_store1(o, d0, a, e);
+            if (v1) plane_store1(o, base + g.y + L.d[1], b, e);
         }
     }
 }
@@ -466,6 +466,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         int e_scale = 0;
         if (kind_scaled(KIND))
             e_scale = fp16s_exponent(__uint_as_float(p.scales[0])) + fp16s_exponent(__uint_as_float(p.scales[1]));
+        // Scaled planar output (modes 3, 4): the planes' exponent comes from a
+        // bound, since the output's max is known only after the last tile.
+        // With the operands' true maxima below 2^(tA + 14) and 2^(tB + 14)
+        // (tA, tB their scale exponents), a component of C is below
+        // 2K 2^(tA + 14) 2^(tB + 14), so e_out = tA + tB + 15 + ceil(log2 K)
+        // keeps every scaled value below 2^14.  The next step reads e_out
+        // from the max slot (2^(e_out + 13)) and the output's true max from
+        // the slot two places on, so the bound never builds on another bound.
+        int e_out = 0;
+        if (kind_scaled(KIND) && (p.out.mode == 3 || p.out.mode == 4)) {
+            int lk = 0;
+            while (((int64_t)1 << lk) < p.K) lk++;
+            float mA = __uint_as_float(p.scales[2]), mB = __uint_as_float(p.scales[3]);
+            if (!(mA > 0.f)) mA = __uint_as_float(p.scales[0]);
+            if (!(mB > 0.f)) mB = __uint_as_float(p.scales[1]);
+            e_out = fp16s_exponent(mA) + fp16s_exponent(mB) + 15 + lk;
+        }
         // every flush warp walks every tile of this CTA and reaches the same
         // named barriers even after a failed wait (it then skips waits,
         // tensor-memory reads and stores), so the warps never part ways
@@ -532,6 +549,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < 32; j++) mx = fmaxf(mx, fmaxf(fabsf(acc_re[j]), fabsf(acc_im[j])));
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                if (p.out.mode == 3 || p.out.mode == 4) {
+                    if (lane == 0) atomicMax(p.max_slot + 2, __float_as_uint(mx));  // true max
+                    mx = ldexpf(1.f, e_out + 13);  // the planes' exponent
+                }
                 if (lane == 0) atomicMax(p.max_slot, __float_as_uint(mx));
             }
             float2 *Ch = p.C + (int64_t)tc.h * p.sCh;
@@ -561,7 +582,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("bar.sync 1, 256;" ::: "memory");
                 if (p.out.mode != 0) {
                     if (ok && tc.m0 + hp * (TM / 2) < p.M)
-                        planar_write(p.out, tc.h, tc.m0 + hp * (TM / 2), tc.n0, stage_out, jtab, pl, fw, lane);
+                        planar_write(p.out, tc.h, tc.m0 + hp * (TM / 2), tc.n0, stage_out, jtab, pl, fw, lane,
+                                     e_out);
                 }
                 for (int rr = fw; ok && p.out.mode == 0 && rr < TM / 2; rr += kFlushWarps) {
                     const int64_t mm = tc.m0 + hp * (TM / 2) + rr;
@@ -705,16 +727,23 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.scales = g.scales;
     p.max_slot = g.max_slot;
     p.out = g.out;
-    // planar output only for the unscaled split forms: a scaled form's plane
-    // scale needs the max of the whole output before any tile is written.
-    // Plane offsets are 64-bit (a tile's own offsets 32-bit, checked when
-    // the plan builds the tables)
-    if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || (p.out.mode != 1 && p.out.mode != 2) ||
+    // planar output: bf16 / tf32 hi/lo (modes 1, 2) or scaled fp16 (3, 4)
+    // with the bound-derived exponent.  Plane offsets are 64-bit (a tile's
+    // own offsets 32-bit, checked when the plan builds the tables)
+    if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || p.out.mode < 1 || p.out.mode > 4 ||
                             p.out.plane_stride > (int64_t(1) << 44) || p.out.ntb > 12))
+        return cudaErrorInvalidValue;
+    // a scaled planar output needs a scaled form (its operands' exponents)
+    // and the slot through which the next step reads the planes' exponent
+    if ((p.out.mode == 3 || p.out.mode == 4) &&
+        (!((g.form == TN_FP16S && p.out.mode == 3) || (g.form == TN_FP16X3 && p.out.mode == 4)) || !g.max_slot))
         return cudaErrorInvalidValue;
     if (g.max_slot) {
         if (p.ksplit > 1) return cudaErrorInvalidValue;  // partial tiles: their max is not C's
+        // the slot and its companion two places on (the true max, written
+        // only by a scaled planar output; 0 tells the consumer to use the slot)
         cudaError_t e = cudaMemsetAsync(g.max_slot, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g.max_slot + 2, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
     if ((g.form == TN_FP16S || g.form == TN_FP16X3) && !g.scales) return cudaErrorInvalidValue;

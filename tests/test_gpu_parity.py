@@ -261,13 +261,14 @@ def test_tiled_small_steps_random_layouts(tn, seed):
     assert rel(got[0], ref) < TOL
 
 
-@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "fp16x3", "fp16s"])
 def test_planar_epilogue_matches_split_pass(tn, form):
     """GEMMs that write the next step's hi/lo planes from their epilogue
     (tc_planar on, the default) against complex64 output plus a separate
-    split pass (tc_planar -1): the same pieces and products, so they agree to
-    FP32 rounding of the split-K atomics elsewhere in the plan (1e-6), and
-    both meet the form's bound against the FP64 golden amplitudes."""
+    split pass (tc_planar -1).  BF16x3 / TF32x3: the same pieces and
+    products, so they agree to FP32 rounding of the split-K atomics elsewhere
+    in the plan (1e-6).  Both meet the form's bound against the FP64 golden
+    amplitudes."""
     import torch
     cfg = make_config(2)
     ref = load_golden("cfg2_amplitudes.txt")
@@ -281,8 +282,15 @@ def test_planar_epilogue_matches_split_pass(tn, form):
         torch.cuda.synchronize()
         got[planar] = to_complex(amp)
         plan.close()
-    assert rel(got[0], got[-1]) < 1e-6
-    bound = {"bf16x3": 2e-5}.get(form, TOL)
+    # the scaled forms' planar outputs take their exponent from a bound
+    # (eA + eB + 15 + log2 K) instead of the output's max, which moves the
+    # fp16 pieces' rounding: the two runs then agree to the forms' own
+    # accuracy rather than to 1e-6
+    agree = {"fp16x3": 5e-6, "fp16s": 2e-3}.get(form, 1e-6)
+    print(f"planar vs split pass, {form}: {rel(got[0], got[-1]):.2e}; vs oracle {rel(got[0], ref):.2e} / "
+          f"{rel(got[-1], ref):.2e}")
+    assert rel(got[0], got[-1]) < agree
+    bound = {"bf16x3": 2e-5, "fp16s": 2e-3}.get(form, TOL)
     assert rel(got[0], ref) < bound and rel(got[-1], ref) < bound
 
 
