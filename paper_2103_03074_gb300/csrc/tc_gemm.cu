@@ -283,14 +283,24 @@ __device__ __forceinline__ void plane_store2(const TcPlanarOut &o, uint64_t d, f
 }
 
 // Planar epilogue tables.  The half tile's elements are enumerated in
-// destination order j = (j_hi, j_lo): j_lo (6 bits) is lane 2 l + q, j_hi a
-// group.  Per lane: stage and destination offsets of its two j_lo; per group
-// (shared memory, computed once per launch): those of j_hi.
+// destination order j = (j_hi, j_lo): j_lo (6 bits; 7 for quads) is lane
+// k l + q (k = 2 elements per lane, or 4 when the destination's two lowest
+// bits both come from the tile), j_hi a group.  Per lane: stage and
+// destination offsets of its j_lo; per group (shared memory, computed once
+// per launch): those of j_hi.
 struct PlanarLane {
-    int s[2];       // staging offset (row * RS + column)
-    uint32_t d[2];  // destination offset
+    int s[4];       // staging offset (row * RS + column)
+    uint32_t d[4];  // destination offset
     bool pair;      // d[1] = d[0] + 1 with d[0] even: one vector store per plane
+    bool quad;      // d[q] = d[0] + q with d[0] a multiple of 4
 };
+
+__device__ __forceinline__ bool planar_quad(const TcPlanarOut &o) {
+    return o.ntb >= 7 && o.tpos[0] == 0 && o.tpos[1] == 1;
+}
+__device__ __forceinline__ int planar_nlo(const TcPlanarOut &o) {
+    return planar_quad(o) ? 7 : (o.ntb < 6 ? o.ntb : 6);
+}
 
 __device__ __forceinline__ void planar_bits(const TcPlanarOut &o, int j, int k0, int k1, int RS, int &so,
                                             uint32_t &d) {
@@ -308,21 +318,48 @@ __device__ __forceinline__ void planar_bits(const TcPlanarOut &o, int j, int k0,
 
 __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane, int RS) {
     PlanarLane L;
-    const int nlo = o.ntb < 6 ? o.ntb : 6;
-    for (int q = 0; q < 2; q++) planar_bits(o, 2 * lane + q, 0, nlo, RS, L.s[q], L.d[q]);
+    const int nlo = planar_nlo(o);
+    L.quad = planar_quad(o);
+    const int per = L.quad ? 4 : 2;
+    for (int q = 0; q < 4; q++) {
+        L.s[q] = 0;
+        L.d[q] = 0;
+        if (q < per) planar_bits(o, per * lane + q, 0, nlo, RS, L.s[q], L.d[q]);
+    }
     L.pair = o.ntb >= 6 && o.tpos[0] == 0;
     return L;
 }
 
 // Split the staged half tile (rows mh .. mh + 63) into the next step's
 // planes: warp fw of the 8 epilogue warps takes the groups j_hi = fw, fw + 8,
-// ...; each lane two neighbouring elements of a group.
+// ...; each lane two (or four) neighbouring elements of a group.
 __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_t mh, int64_t n0, const float2 *st,
                                              const uint2 *jtab, const PlanarLane &L, int fw, int lane, int e) {
     const uint64_t base = scatter8((uint64_t)h, o.hpos, o.nH) | scatter8((uint64_t)mh, o.mpos, o.nM) |
                           scatter8((uint64_t)n0, o.npos, o.nN);
-    const int nlo = o.ntb < 6 ? o.ntb : 6;
+    const int nlo = planar_nlo(o);
     const int n_hi = 1 << (o.ntb - nlo);
+    if (L.quad) {
+        const int np = mode_planes(o.mode);
+        for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
+            const uint2 g = jtab[jh];
+            Pieces pc[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) pc[q] = split_value(o.mode, st[(int)g.x + L.s[q]], e);
+            const uint64_t d0 = base + g.y + L.d[0];  // a multiple of 4
+            if (o.mode == 2) {
+                uint4 *P = reinterpret_cast<uint4 *>(o.planes);
+                for (int q = 0; q < np; q++)
+                    P[(d0 + q * o.plane_stride) >> 2] = make_uint4(pc[0].q[q], pc[1].q[q], pc[2].q[q], pc[3].q[q]);
+            } else {
+                uint2 *P = reinterpret_cast<uint2 *>(o.planes);
+                for (int q = 0; q < np; q++)
+                    P[(d0 + q * o.plane_stride) >> 2] =
+                        make_uint2(pc[0].q[q] | (pc[1].q[q] << 16), pc[2].q[q] | (pc[3].q[q] << 16));
+            }
+        }
+        return;
+    }
     const bool v1 = 2 * lane + 1 < (1 << nlo), v0 = 2 * lane < (1 << nlo);
     for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
         const uint2 g = jtab[jh];
@@ -489,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         PlanarLane pl;
         if (p.out.mode != 0) {
             pl = planar_lane(p.out, lane, R::kOutRS);
-            const int nlo = p.out.ntb < 6 ? p.out.ntb : 6;
+            const int nlo = planar_nlo(p.out);
             for (int jh = fw * 32 + lane; jh < (1 << (p.out.ntb - nlo)); jh += kFlushWarps * 32) {
                 int so;
                 uint32_t d;
