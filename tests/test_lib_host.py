@@ -157,3 +157,64 @@ def test_head_tail_order_has_the_cut_at_its_root(tn):
     tail = sides[1] if opens[0] == 0 else sides[0]
     assert st["n_cut"] == len(head & tail)
     assert all(x in head and x not in tail for x in sliced)
+
+
+def _sides(tree, labels, n):
+    def leaves(x):
+        return [x] if x < n else leaves(tree[x - n][0]) + leaves(tree[x - n][1])
+    return [set(l for i in leaves(r) for l in labels[i]) for r in tree[-1]]
+
+
+def test_head_tail_rejects_bad_cuts_and_slices(tn):
+    """tn_head_tail_amplitudes checks its tree and sliced labels on the host,
+    before any CUDA call: a root step with open legs on both sides, a head
+    sliced label outside the head, an open label sliced in the tail."""
+    import torch
+    from tn_inputs import random_tree
+    amp = torch.zeros(64, dtype=torch.float64)  # never touched: the call fails first
+    # a random tree whose root has open legs on both sides
+    for seed in range(1, 50):
+        net = random_network(seed, n_tensors=8, n_bonds=12, n_open=4, max_rank=6)
+        tree = random_tree(seed, len(net.labels))
+        s = _sides(tree, net.labels, len(net.labels))
+        if all(x & set(net.open_labels) for x in s):
+            break
+    with pytest.raises(tn.TNError) as e:
+        tn.head_tail_amplitudes(net.labels, net.data, net.open_labels, tree, [], [], amp)
+    assert e.value.code == -1 and "both sides" in str(e.value)
+    # a proper head/tail tree with misplaced sliced labels
+    circ = sycamore_circuit("rect", 3, 4, 6, 5)
+    L, T, O = tn.circuit_network(circ, random_bits(12, 5), list(range(8, 12)))
+    tree, sl_head, st = tn.find_order_head_tail(L, O, opts=tn.search_opts(trials=16, n_sliced=0))
+    head, tail = _sides(tree, L, len(L))
+    if head & set(O):
+        head, tail = tail, head
+    with pytest.raises(tn.TNError) as e:
+        tn.head_tail_amplitudes(L, T, O, tree, [sorted(tail - head)[0]], [], amp)
+    assert "head sliced label" in str(e.value)
+    with pytest.raises(tn.TNError) as e:
+        tn.head_tail_amplitudes(L, T, O, tree, [], [O[0]], amp)
+    assert "tail sliced label" in str(e.value)
+
+
+def test_postselect_and_histogram_reject_bad_arguments(tn):
+    """Count and size checks of tn_postselect_xeb, tn_conditional_sample and
+    tn_probability_histogram run before any CUDA call."""
+    import torch
+    amp = torch.zeros(32, dtype=torch.float64)
+    for counts in ([0], [17], [1, 2, 100]):
+        with pytest.raises(tn.TNError) as e:
+            tn.postselect_xeb(amp, 4, 10, counts)
+        assert e.value.code == -1
+    cnt = torch.zeros(5, dtype=torch.int64)
+    for n_bins, x_max, scale in ((0, 1.0, 1.0), (5000, 1.0, 1.0), (4, 0.0, 1.0), (4, 1.0, -1.0)):
+        with pytest.raises(tn.TNError):
+            tn.probability_histogram(amp, 4, scale, n_bins, x_max, cnt)
+    with pytest.raises(tn.TNError):
+        tn.conditional_sample(amp, 41, torch.zeros(3, dtype=torch.float64), torch.zeros(3, dtype=torch.int64))
+
+
+def test_find_order_head_tail_rejects_networks_without_open_legs(tn):
+    net = random_network(4, n_tensors=6, n_bonds=9, n_open=0, max_rank=5)
+    with pytest.raises(tn.TNError):
+        tn.find_order_head_tail(net.labels, [])
