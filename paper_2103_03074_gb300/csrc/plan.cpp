@@ -1092,7 +1092,7 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
     if (n_steps != n_tensors - 1 || (n_steps > 0 && !tree)) return fail(TN_ERR_ARG, "tree must have n_tensors - 1 steps");
     if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
     if (form != TN_FP32 && !tc_form_available(form))
-        return fail(TN_ERR_ARG, "this arithmetic form is not available in this build");
+        return fail(TN_ERR_ARG, "this arithmetic form is not compiled into this library");
     std::unique_ptr<tn_plan> P(new tn_plan());
     P->form = form;
     if (opts) P->opts = *opts;

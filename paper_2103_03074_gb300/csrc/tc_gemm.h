@@ -42,8 +42,8 @@ struct TcGemm {
     alignas(64) unsigned char mapB[128];
 };
 
-// true if `form` has a tensor-core GEMM in this build (and the driver entry
-// point for TMA descriptors is reachable)
+// true if `form` has a tensor-core GEMM compiled into this library (and the
+// driver entry point for TMA descriptors is reachable)
 bool tc_form_available(tn_form form);
 
 // bytes per plane element of a split form (2: bf16 / fp16, 4: tf32)
