@@ -153,6 +153,9 @@ class Clocks:
 # Workloads.  The default is the bench line; the 53-qubit ones are extra
 # measurement lines (--workload), with steps that take seconds.
 WORKLOADS = {
+    "rect3x4": dict(cfg=1, search=dict(trials=256, n_sliced=0), timed_slices=None, golden=None,
+                    desc="rect3x4_m8_allopen: 12 qubits, 8 cycles, all 12 open, no slicing "
+                         "(one contraction per step: a latency-bound circuit)"),
     "rect5x6": dict(cfg=2, search=dict(trials=16384, n_sliced=8), timed_slices=None,
                     golden="cfg2_amplitudes.txt",
                     desc="rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 22 fixed, "
@@ -194,16 +197,18 @@ def cpu_oracle_rate(cfg, sliced, budget_s=15.0, max_slices=4):
     bounded sample; returns (slices/s, sample description, cores)."""
     from oracle import network as onet, contract as oc
     L, T, O = onet.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    n_slices = 1 << len(sliced)
     done = 0
     t0 = time.perf_counter()
     while done < max_slices:
-        oc.slice_partial(L, T, O, sliced, done)
+        oc.slice_partial(L, T, O, sliced, done % n_slices)
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     cores = os.cpu_count()
-    return done / dt, f"{done} slices (ids 0..{done - 1}) of the 2^{len(sliced)}-slice workload, FP64 numpy", cores
+    ids = f"ids 0..{min(done, n_slices) - 1}" + (" repeated" if done > n_slices else "")
+    return done / dt, f"{done} slice contractions ({ids}) of the 2^{len(sliced)}-slice workload, FP64 numpy", cores
 
 
 def run_reference(args):
@@ -354,7 +359,7 @@ def run_native(args):
 
     pk = peaks()
     wl = WORKLOADS[args.workload]
-    big = args.workload != "rect5x6"
+    big = args.workload in ("syc53_m14", "syc53_m20")
     cfg = workload(args.workload, instance_seed_offset(rank))
     n_qubits = cfg["circuit"].n_qubits
     n_open = len(cfg["open_qubits"])
