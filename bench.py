@@ -365,6 +365,8 @@ def run_native(args):
     n_open = len(cfg["open_qubits"])
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
     tree, sliced, st = tn.find_order(L, O, tn.search_opts(**wl["search"]))
+    if args.branch_merge:
+        tree, _ = tn.merge_branches(L, O, sliced, tree)
     n_total = 1 << len(sliced)
     n_slices = min(n_total, wl["timed_slices"] or n_total)
     if args.form != "all":
@@ -554,6 +556,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "all"])
     ap.add_argument("--workload", default="rect5x6", choices=sorted(WORKLOADS) + ["batch256"])
+    ap.add_argument("--branch-merge", action="store_true",
+                    help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
     args = ap.parse_args()

@@ -276,6 +276,21 @@ int tn_find_order(int n_tensors, const int32_t *ranks, const int32_t *labels, in
                   int max_sliced, int32_t *out_sliced, int *out_n_sliced, double *stats);
 
 /*
+ * Branch merging (appendix, "Details of simulations"): in a tree, a large
+ * tensor X met by two small ones in turn, ((X a) b), is rewritten as
+ * (X (a b)) when a, b and their product have rank <= max_small_rank (0: 12)
+ * and a per-step time estimate drops by at least 5% (the larger of the
+ * step's bytes over 7 TB/s and its FP32 flops over 80 TFLOP/s, sliced labels
+ * kept as batch labels); repeated until nothing improves.  The result is the
+ * same contraction (pairwise contraction is associative).  tree_out receives
+ * the rewritten SSA tree (2 * (n_tensors - 1) ids, may alias tree_in);
+ * stats[3] = {rewrites, log2 MACs per block before, after}.
+ */
+int tn_merge_branches(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                      const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
+                      const int32_t *tree_in, int max_small_rank, int32_t *tree_out, double *stats);
+
+/*
  * Order search for the two-stage big-head form ("Big-head simulation"
  * section, Fig. 1; appendix on the first cut): the tail starts with every
  * tensor holding an open label and grows one neighbouring tensor at a time,

@@ -79,6 +79,8 @@ _lib.tn_batch_run.argtypes = [_vp, _vp]
 _lib.tn_batch_destroy.argtypes = [_vp]
 _lib.tn_batch_destroy.restype = None
 _lib.tn_plan_describe.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.tn_merge_branches.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                   ctypes.c_int, _vp, _vp]
 _lib.tn_find_order_head_tail.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int,
                                          ctypes.POINTER(SearchOpts), _vp, ctypes.c_int, _vp,
                                          ctypes.POINTER(ctypes.c_int), _vp]
@@ -97,7 +99,7 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
             "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
-            "tn_find_order_head_tail", "tn_head_tail_amplitudes"]
+            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -212,6 +214,23 @@ def find_order(labels, open_labels, opts=None, max_sliced=64):
     steps = [(int(tree[2 * i]), int(tree[2 * i + 1])) for i in range(n - 1)]
     stats = dict(log2_total=st[0], log2_width=st[1], n_sliced=int(st[2]), log2_slice=st[3])
     return steps, [int(x) for x in sl[:nsl.value]], stats
+
+
+def merge_branches(labels, open_labels, sliced_labels, tree, max_small_rank=0):
+    """tn_merge_branches: (rewritten tree, stats dict) with ((X a) b) turned
+    into (X (a b)) where that lowers the estimated step time."""
+    ranks = np.asarray([len(l) for l in labels], dtype=np.int32)
+    flat = np.asarray([x for l in labels for x in l] or [0], dtype=np.int32)
+    ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
+    sl = np.asarray(list(sliced_labels) or [0], dtype=np.int32)
+    tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
+    out = np.zeros(max(2 * len(tree), 1), dtype=np.int32)
+    st = np.zeros(3)
+    _check(_lib.tn_merge_branches(len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol),
+                                  len(sliced_labels), _ptr(sl), len(tree), _ptr(tr), int(max_small_rank), _ptr(out),
+                                  _ptr(st)), "tn_merge_branches")
+    steps = [(int(out[2 * t]), int(out[2 * t + 1])) for t in range(len(tree))]
+    return steps, dict(rewrites=int(st[0]), log2_macs_before=float(st[1]), log2_macs_after=float(st[2]))
 
 
 def find_order_head_tail(labels, open_labels, tail_max=0, opts=None, max_sliced=64):

@@ -682,3 +682,171 @@ int search_order(const std::vector<std::vector<int32_t>> &labels, const std::vec
 }
 
 }  // namespace tn
+
+// ---------------------------------------------------------------- branch merging
+// A big tensor X met by two small ones in turn, ((X a) b), streams X through
+// memory twice; (X (a b)) merges the small ones first and streams X once, at
+// the price of more arithmetic when a and b share no bond ("Details of
+// simulations": merging branches balances the pairwise contractions).  The
+// rewrite is kept where a per-step time estimate drops: the larger of the
+// step's bytes over 7 TB/s and its FP32 flops over 80 TFLOP/s, with sliced
+// labels kept as batch labels (as the executor runs a block of slices).
+namespace tn {
+namespace {
+
+struct BNode {
+    int l = -1, r = -1;  // children (internal nodes); -1 for leaves
+};
+
+double step_time(int ra, int rb, int rc, int ru) {
+    const double bytes = 8.0 * (std::exp2(ra) + std::exp2(rb) + std::exp2(rc));
+    const double flops = 8.0 * std::exp2(ru);
+    return std::max(bytes / 7.0e12, flops / 80.0e12);
+}
+
+}  // namespace
+}  // namespace tn
+
+extern "C" int tn_merge_branches(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                                 const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels,
+                                 int n_steps, const int32_t *tree_in, int max_small_rank, int32_t *tree_out,
+                                 double *stats) {
+    using namespace tn;
+    if (n_tensors < 1 || !ranks || !labels || n_steps != n_tensors - 1 || (n_steps > 0 && (!tree_in || !tree_out)) ||
+        n_open < 0 || (n_open > 0 && !open_labels) || n_sliced < 0 || (n_sliced > 0 && !sliced_labels))
+        return fail(TN_ERR_ARG, "tn_merge_branches: bad arguments");
+    const int n = n_tensors;
+    std::vector<std::vector<int32_t>> labs(n);
+    size_t off = 0;
+    for (int i = 0; i < n; i++) {
+        if (ranks[i] < 0 || ranks[i] > 62) return fail(TN_ERR_ARG, "tn_merge_branches: rank out of range");
+        labs[i].assign(labels + off, labels + off + ranks[i]);
+        off += ranks[i];
+    }
+    // sliced labels stay in the tensors (batch labels), like open labels
+    std::vector<int32_t> kept(open_labels, open_labels + n_open);
+    kept.insert(kept.end(), sliced_labels, sliced_labels + n_sliced);
+    Problem p;
+    if (!make_problem(labs, kept, p)) return fail(TN_ERR_ARG, "tn_merge_branches: kept label held by no tensor");
+    Tree tree(n_steps);
+    for (int t = 0; t < n_steps; t++) tree[t] = {tree_in[2 * t], tree_in[2 * t + 1]};
+    TreeSets ts;
+    if (!tree_sets(p, tree, ts)) return fail(TN_ERR_ARG, "tn_merge_branches: malformed tree");
+    if (n_steps == 0) {
+        if (stats) stats[0] = stats[1] = stats[2] = 0;
+        return TN_OK;
+    }
+    const int W = p.leaf.W, nn = 2 * n - 1;
+    std::vector<BNode> node(nn);
+    for (int t = 0; t < n_steps; t++) node[n + t] = {tree[t].first, tree[t].second};
+    const int root = nn - 1;
+    // label sets bottom-up (children before parents: any post-order)
+    Sets set;
+    set.init(nn, p.L);
+    std::vector<int> order;
+    auto post = [&]() {
+        order.clear();
+        std::vector<std::pair<int, bool>> st{{root, false}};
+        while (!st.empty()) {
+            auto [x, done] = st.back();
+            st.pop_back();
+            if (x < n || done) {
+                order.push_back(x);
+                continue;
+            }
+            st.push_back({x, true});
+            st.push_back({node[x].r, false});
+            st.push_back({node[x].l, false});
+        }
+    };
+    auto compute = [&](int x) {
+        uint64_t *so = set.at(x);
+        if (x < n) {
+            std::memcpy(so, p.leaf.at(x), sizeof(uint64_t) * W);
+            return;
+        }
+        const uint64_t *sa = set.at(node[x].l), *sb = set.at(node[x].r);
+        for (int w = 0; w < W; w++) so[w] = (sa[w] | sb[w]) & ~(sa[w] & sb[w] & ~p.open[w]);
+    };
+    auto rank_of = [&](int x) { return popc(set.at(x), W); };
+    auto union_rank = [&](int a, int b) {
+        int c = 0;
+        for (int w = 0; w < W; w++) c += __builtin_popcountll(set.at(a)[w] | set.at(b)[w]);
+        return c;
+    };
+    auto out_rank = [&](int a, int b) {  // rank of the contraction of a and b
+        int c = 0;
+        for (int w = 0; w < W; w++) {
+            const uint64_t sa = set.at(a)[w], sb = set.at(b)[w];
+            c += __builtin_popcountll((sa | sb) & ~(sa & sb & ~p.open[w]));
+        }
+        return c;
+    };
+    auto log2_macs = [&]() {
+        std::vector<double> e;
+        for (int x = n; x < nn; x++) e.push_back((double)union_rank(node[x].l, node[x].r));
+        return log2_sum_pow2(e);
+    };
+    post();
+    for (int x : order) compute(x);
+    const double before = log2_macs();
+    const int small = max_small_rank > 0 ? max_small_rank : 12;
+    int rewrites = 0;
+    for (int pass = 0; pass < 64; pass++) {
+        bool changed = false;
+        post();
+        for (int P : order) {
+            if (P < n) continue;
+            for (int side = 0; side < 2; side++) {
+                const int Q = side == 0 ? node[P].l : node[P].r, b = side == 0 ? node[P].r : node[P].l;
+                if (Q < n || rank_of(b) > small) continue;
+                // X: the larger child of Q, a: the smaller
+                int X = node[Q].l, a = node[Q].r;
+                if (rank_of(a) > rank_of(X)) std::swap(X, a);
+                if (rank_of(a) > small) continue;
+                const int rm = out_rank(a, b);
+                if (rm > small) continue;
+                const double t_old = step_time(rank_of(X), rank_of(a), rank_of(Q), union_rank(X, a)) +
+                                     step_time(rank_of(Q), rank_of(b), rank_of(P), union_rank(Q, b));
+                // after: M = (a b), P = (X M); P's labels are unchanged
+                const int rp = rank_of(P);
+                int ru = 0;  // |X u M|
+                for (int w = 0; w < W; w++) {
+                    const uint64_t sa = set.at(a)[w], sb = set.at(b)[w];
+                    const uint64_t sm = (sa | sb) & ~(sa & sb & ~p.open[w]);
+                    ru += __builtin_popcountll(set.at(X)[w] | sm);
+                }
+                const double t_new = step_time(rank_of(a), rank_of(b), rm, union_rank(a, b)) +
+                                     step_time(rank_of(X), rm, rp, ru);
+                if (t_new < 0.95 * t_old) {
+                    node[Q] = {a, b};
+                    node[P] = {X, Q};
+                    compute(Q);
+                    compute(P);
+                    rewrites++;
+                    changed = true;
+                    break;
+                }
+            }
+        }
+        if (!changed) break;
+    }
+    // re-linearise: post-order, leaves keep their ids, steps numbered anew
+    post();
+    std::vector<int> id(nn, -1);
+    for (int i = 0; i < n; i++) id[i] = i;
+    int next = n, t = 0;
+    for (int x : order) {
+        if (x < n) continue;
+        tree_out[2 * t] = id[node[x].l];
+        tree_out[2 * t + 1] = id[node[x].r];
+        id[x] = next++;
+        t++;
+    }
+    if (stats) {
+        stats[0] = rewrites;
+        stats[1] = before;
+        stats[2] = log2_macs();
+    }
+    return TN_OK;
+}

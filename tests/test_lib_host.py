@@ -218,3 +218,38 @@ def test_find_order_head_tail_rejects_networks_without_open_legs(tn):
     net = random_network(4, n_tensors=6, n_bonds=9, n_open=0, max_rank=5)
     with pytest.raises(tn.TNError):
         tn.find_order_head_tail(net.labels, [])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_branch_merging_keeps_the_contraction(tn, seed):
+    """tn_merge_branches rewrites ((X a) b) into (X (a b)): a valid SSA tree
+    over the same leaves whose contraction (by the FP64 oracle, following
+    each tree) equals the original's, on random and circuit networks."""
+    from tn_inputs import random_tree
+    net = random_network(seed, n_tensors=14, n_bonds=24, n_open=3, max_rank=6)
+    tree = random_tree(seed, len(net.labels))
+    sliced = internal_labels_of(net.labels)[:2]
+    merged, st = tn.merge_branches(net.labels, net.open_labels, sliced, tree, max_small_rank=6)
+    n = len(net.labels)
+    used = set()
+    for t, (a, b) in enumerate(merged):
+        assert 0 <= a < n + t and 0 <= b < n + t and a != b and a not in used and b not in used
+        used.update((a, b))
+    ref = oc.contract(net.labels, net.data, net.open_labels, tree=tree)
+    got = oc.contract(net.labels, net.data, net.open_labels, tree=merged)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    circ = sycamore_circuit("rect", 3, 4, 8, seed)
+    L, T, O = tn.circuit_network(circ, random_bits(12, seed), list(range(8, 12)))
+    ctree, csl, _ = tn.find_order(L, O, tn.search_opts(trials=16, n_sliced=2))
+    cm, cst = tn.merge_branches(L, O, csl, ctree)
+    a0 = oc.contract(L, T, O, tree=ctree)
+    a1 = oc.contract(L, T, O, tree=cm)
+    assert np.allclose(a1, a0, rtol=1e-12, atol=1e-12 * np.abs(a0).max())
+
+
+def internal_labels_of(labels):
+    cnt = {}
+    for l in labels:
+        for x in l:
+            cnt[x] = cnt.get(x, 0) + 1
+    return sorted(x for x, c in cnt.items() if c == 2)
