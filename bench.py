@@ -294,7 +294,7 @@ def run_batch(args):
     nets = []
     for m in members:
         L, T, O = tn.circuit_network(m["circuit"], m["fixed_bits"], m["open_qubits"])
-        tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=32, n_sliced=m["n_sliced"]))
+        tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=32, n_sliced=m["n_sliced"], method=args.search_method))
         nets.append((L, T, O, tree, sliced, st))
     n_slices = sum(1 << len(x[4]) for x in nets)
     macs = sum((1 << len(x[4])) * 2.0 ** x[5]["log2_slice"] for x in nets)
@@ -335,7 +335,8 @@ def run_batch(args):
             "vs_baseline": None, "dtype": best, "data": "synthetic (seeded Sycamore-style circuits, random bitstrings)",
             "config": {"workload": BATCH_DESC, "form": best, "circuits": len(members), "slices_per_step": n_slices,
                        "complex_macs_per_step": macs,
-                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
+                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                       "order_search": args.search_method},
             "complex_tflops": r["complex_tflops"], "forms": results, "clocks": r["clocks"],
             "roofline": None, "cpu_baseline": None, "e2e": None}
     print(json.dumps(line))
@@ -364,7 +365,7 @@ def run_native(args):
     n_qubits = cfg["circuit"].n_qubits
     n_open = len(cfg["open_qubits"])
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**wl["search"]))
+    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**wl["search"], method=args.search_method))
     if args.branch_merge:
         tree, _ = tn.merge_branches(L, O, sliced, tree)
     n_total = 1 << len(sliced)
@@ -526,7 +527,8 @@ def run_native(args):
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
                    "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],
-                   "arena_bytes": r["plan"]["arena_bytes"]},
+                   "arena_bytes": r["plan"]["arena_bytes"], "order_search": args.search_method,
+                   "branch_merge": bool(args.branch_merge)},
         "complex_tflops": r["complex_tflops"],
         "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
                        "rel_l2_err_vs_fp64_oracle": results[f]["rel_l2_err"],
@@ -556,6 +558,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "all"])
     ap.add_argument("--workload", default="rect5x6", choices=sorted(WORKLOADS) + ["batch256"])
+    ap.add_argument("--search-method", default="greedy", choices=["greedy", "bipartition", "mixed"],
+                    help="order-search trials: randomised greedy (default), hierarchical bipartition, or both")
     ap.add_argument("--branch-merge", action="store_true",
                     help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

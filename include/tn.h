@@ -121,7 +121,14 @@ typedef struct {
     int32_t rank_batch_log2;
     int32_t rank_form;
     tn_costmodel_t cost_model;
-    int32_t reserved[2];
+    /* trial kind: 0 randomised greedy (default); 1 hierarchical bipartition
+     * (appendix, "Finding contraction order using hierarchical
+     * partitioning": min-cut splits down to parts of a few dozen tensors,
+     * greedy inside a part; trial 0 takes the paper's parts of <= 60
+     * tensors, the others draw the balance window and part size); 2 both,
+     * alternating.  Slicing and subtree reconfiguration follow either way. */
+    int32_t method;
+    int32_t reserved;
 } tn_search_opts;
 
 /* A circuit: gate g acts on gate_nq[g] (1 or 2) qubits gate_q[2g], gate_q[2g+1]
@@ -265,8 +272,10 @@ const char *tn_last_error(void);
 
 /*
  * Host-side order search (first pairwise order, then slicing): randomised
- * greedy trials scored by the Fig. 3 cost 2^{n_A+n_B+n_AB} summed over steps,
- * then greedy slicing to the cap or count.  Writes the tree (2*(n_tensors-1)
+ * greedy or hierarchical-bipartition trials (opts->method) scored by the
+ * Fig. 3 cost 2^{n_A+n_B+n_AB} summed over steps, then greedy slicing to the
+ * cap or count and subtree reconfiguration of the best trees.  TN_ERR_ARG
+ * for an unknown method.  Writes the tree (2*(n_tensors-1)
  * SSA ids), the sliced labels (up to max_sliced) and stats[4] =
  * {log2 total MACs over all slices, log2 largest intermediate per slice,
  *  n_sliced, log2 MACs per slice}.
@@ -295,7 +304,10 @@ int tn_merge_branches(int n_tensors, const int32_t *ranks, const int32_t *labels
  * section, Fig. 1; appendix on the first cut): the tail starts with every
  * tensor holding an open label and grows one neighbouring tensor at a time,
  * always the one leaving the smallest cut, up to tail_max tensors (0: half
- * the network); the prefix with the smallest cut is kept.  Then the head's
+ * the network); the prefix with the smallest cut is kept.  With
+ * opts->method >= 1 (bipartition) that tail is then refined by
+ * Fiduccia-Mattheyses passes, the open-leg tensors held in the tail and its
+ * size kept within the limit.  Then the head's
  * order is searched with the cut labels as its open labels (sliced as opts'
  * cap or count asks; the sliced labels are internal to the head) and the
  * tail's with cut + open labels (not sliced), and the two trees are joined

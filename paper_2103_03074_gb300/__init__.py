@@ -40,7 +40,7 @@ class PlanOpts(ctypes.Structure):
 class SearchOpts(ctypes.Structure):
     _fields_ = [("trials", _i32), ("seed", ctypes.c_uint64), ("log2_cap", _i32), ("n_sliced", _i32),
                 ("threads", _i32), ("candidates", _i32), ("rank_batch_log2", _i32), ("rank_form", _i32),
-                ("cost_model", _vp), ("reserved", _i32 * 2)]
+                ("cost_model", _vp), ("method", _i32), ("reserved", _i32)]
 
 
 class Circuit(ctypes.Structure):
@@ -131,11 +131,18 @@ def _dev_ptr(t):
     return _vp(t.data_ptr())
 
 
+SEARCH_METHODS = {"greedy": 0, "bipartition": 1, "mixed": 2}
+
+
 def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads=0, candidates=0,
-                rank_batch_log2=-1, rank_form="fp32", cost_model=None):
+                rank_batch_log2=-1, rank_form="fp32", cost_model=None, method="greedy"):
+    """Order-search options (tn_search_opts).  method: "greedy" (randomised
+    greedy trials), "bipartition" (hierarchical min-cut bipartition, greedy
+    inside parts of a few dozen tensors) or "mixed" (alternating)."""
     f = FORMS[rank_form] if isinstance(rank_form, str) else int(rank_form)
+    m = SEARCH_METHODS[method] if isinstance(method, str) else int(method)
     cm = cost_model._h if cost_model is not None else None
-    return SearchOpts(trials, seed, log2_cap, n_sliced, threads, candidates, rank_batch_log2, f, cm)
+    return SearchOpts(trials, seed, log2_cap, n_sliced, threads, candidates, rank_batch_log2, f, cm, m)
 
 
 def plan_opts(batch_log2=-1, mem_budget=0, profile=0, use_graph=0, tc_chunk_bytes=0, tc_flush_bytes=0,

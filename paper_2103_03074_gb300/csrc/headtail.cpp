@@ -295,6 +295,26 @@ extern "C" int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, cons
     }
     std::fill(in_tail.begin(), in_tail.end(), 0);
     for (size_t k = 0; k < best_len; k++) in_tail[order[k]] = 1;
+    if (opts && opts->method >= 1) {
+        // the partition step of the first cut: Fiduccia-Mattheyses passes
+        // from the grown tail, the open-leg tensors held in the tail and
+        // the tail kept between them and the size limit
+        std::vector<std::vector<int>> nb(n);
+        std::vector<char> fixed(n, 0);
+        std::vector<int> side(n);
+        for (int i = 0; i < n; i++) {
+            side[i] = in_tail[i] ? 0 : 1;
+            for (int32_t x : labs[i]) {
+                if (open.count(x)) fixed[i] = 1;
+                const auto &h = holders[x];
+                if (h.size() == 2 && h[0] != h[1]) nb[i].push_back(h[0] == i ? h[1] : h[0]);
+            }
+        }
+        int n_fixed = 0;
+        for (char f : fixed) n_fixed += f;
+        fm_refine(nb, side, &fixed, n_fixed, std::max(limit, (int)best_len), 16);
+        for (int i = 0; i < n; i++) in_tail[i] = side[i] == 0;
+    }
     std::vector<int> head, tail;
     for (int i = 0; i < n; i++) (in_tail[i] ? tail : head).push_back(i);
     std::vector<int32_t> cut;

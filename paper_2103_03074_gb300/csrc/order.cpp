@@ -8,8 +8,9 @@
 // Order: randomised greedy.  Each trial repeatedly merges the connected pair
 // with the smallest key, key = slog2(2^{|out|} - alpha (2^{|A|} + 2^{|B|}))
 // minus temperature x Gumbel noise (trial 0 is the plain greedy alpha = 1,
-// no noise).  The paper's own order search (first cut + hierarchical
-// bipartition + greedy leaves) is prior art this stands in for.
+// no noise).  Or (method 1, or every other trial with method 2) hierarchical
+// bipartition as in the paper's appendix: min-cut splits down to parts of a
+// few dozen tensors, greedy inside a part (bipartition_trial below).
 //
 // Slicing ("Dynamic slicing" paragraph): labels are sliced one at a time
 // under two greedy rules (lower the widest intermediate first; or, among the
@@ -349,6 +350,221 @@ Tree greedy_trial(const Problem &p, uint64_t seed, bool plain) {
     return tree;
 }
 
+}  // namespace
+
+// Fiduccia-Mattheyses refinement of a two-way split (nb: one entry per
+// shared bond, side: 0 or 1 per vertex).  Each pass moves, one at a time,
+// the unlocked vertex whose move lowers the cut most while the count of
+// side-0 vertices stays in [lo, hi], locks it, and keeps the best prefix of
+// the pass (ties: the more even split); vertices marked in `fixed` never
+// move.  Passes repeat while the cut drops, at most max_passes.  Returns
+// the cut.
+int fm_refine(const std::vector<std::vector<int>> &nb, std::vector<int> &side, const std::vector<char> *fixed, int lo,
+              int hi, int max_passes) {
+    const int m = (int)side.size();
+    std::vector<int> gain(m);
+    std::vector<char> locked(m);
+    int cut = 0, n0 = 0;
+    for (int i = 0; i < m; i++) {
+        gain[i] = 0;
+        for (int j : nb[i]) gain[i] += side[j] != side[i] ? 1 : -1;
+        if (side[i] == 0) {
+            n0++;
+            for (int j : nb[i]) cut += side[j] == 1;
+        }
+    }
+    for (int pass = 0; pass < max_passes; pass++) {
+        for (int i = 0; i < m; i++) locked[i] = fixed ? (*fixed)[i] : 0;
+        std::vector<int> moves;
+        int cur = cut, c0 = n0, pbest = cut, pbest_len = 0;
+        int pbest_imb = std::abs(2 * n0 - m);
+        for (int s = 0; s < m; s++) {
+            int bi = -1;
+            for (int i = 0; i < m; i++) {
+                if (locked[i]) continue;
+                const int nc0 = c0 + (side[i] == 0 ? -1 : 1);
+                if (nc0 < lo || nc0 > hi) continue;
+                if (bi < 0 || gain[i] > gain[bi]) bi = i;
+            }
+            if (bi < 0) break;
+            cur -= gain[bi];
+            c0 += side[bi] == 0 ? -1 : 1;
+            for (int j : nb[bi]) gain[j] += side[j] == side[bi] ? 2 : -2;
+            gain[bi] = -gain[bi];
+            side[bi] ^= 1;
+            locked[bi] = 1;
+            moves.push_back(bi);
+            const int imb = std::abs(2 * c0 - m);
+            if (cur < pbest || (cur == pbest && imb < pbest_imb)) {
+                pbest = cur;
+                pbest_imb = imb;
+                pbest_len = (int)moves.size();
+            }
+        }
+        // undo the moves past the best prefix
+        for (int s = (int)moves.size() - 1; s >= pbest_len; s--) {
+            const int i = moves[s];
+            c0 += side[i] == 0 ? -1 : 1;
+            for (int j : nb[i]) gain[j] += side[j] == side[i] ? 2 : -2;
+            gain[i] = -gain[i];
+            side[i] ^= 1;
+        }
+        const bool better = pbest < cut;
+        cut = pbest;
+        n0 = c0;
+        if (!better) break;
+    }
+    return cut;
+}
+
+namespace {
+
+// Hierarchical bipartition (appendix, "Finding contraction order using
+// hierarchical partitioning"; Fig. 3 gives the cost of each split): the
+// network is split in two parts sharing few bonds, each part again, until a
+// part holds at most leaf_max tensors; such a part is contracted in greedy
+// order, and the parts are joined in the order of the splits (the split at
+// the top is the tree's last step).  One split: a region grown from a random
+// tensor, always taking the outside tensor with the most bonds into the
+// region, to a random size inside the balance window; then fm_refine
+// inside the window; the best of `restarts` such splits is kept.
+// The paper's clustering partitioner is not public; this is a plain
+// min-cut bisection in its place.
+struct Bisector {
+    const Problem &p;
+    Rng rng;
+    double eps;
+    int leaf_max, restarts;
+    bool plain_leaves;
+    std::vector<std::array<int, 2>> holders;  // the (up to) two leaves holding each label
+    std::vector<int> where;                   // leaf -> index in the current part, or -1
+    Tree tree;
+    int nxt;
+
+    Bisector(const Problem &pr, uint64_t seed, double e, int lm, int rs, bool plain)
+        : p(pr), rng(seed), eps(e), leaf_max(lm), restarts(rs), plain_leaves(plain), holders(pr.L, {-1, -1}),
+          where(pr.n, -1), nxt(pr.n) {
+        for (int i = 0; i < p.n; i++)
+            for (int id : p.leaf_labels[i]) {
+                auto &h = holders[id];
+                if (h[0] < 0) h[0] = i; else if (h[0] != i) h[1] = i;
+            }
+    }
+
+    int other(int id, int v) const { return holders[id][0] == v ? holders[id][1] : holders[id][0]; }
+
+    // greedy order inside part S, the labels leaving S taken as open
+    int greedy_part(const std::vector<int> &S) {
+        const int m = (int)S.size(), W = p.leaf.W;
+        Problem sub;
+        sub.n = m;
+        sub.L = p.L;
+        sub.leaf.init(m, p.L);
+        sub.open = p.open;
+        sub.leaf_labels.resize(m);
+        for (int i = 0; i < m; i++) where[S[i]] = i;
+        for (int i = 0; i < m; i++) {
+            std::memcpy(sub.leaf.at(i), p.leaf.at(S[i]), sizeof(uint64_t) * W);
+            sub.leaf_labels[i] = p.leaf_labels[S[i]];
+            for (int id : p.leaf_labels[S[i]]) {
+                const int o = other(id, S[i]);
+                if (o < 0 || where[o] < 0) sub.open[id >> 6] |= 1ull << (id & 63);
+            }
+        }
+        for (int v : S) where[v] = -1;
+        const Tree t = greedy_trial(sub, rng.next(), plain_leaves);
+        std::vector<int> map(2 * m - 1);
+        for (int i = 0; i < m; i++) map[i] = S[i];
+        for (int s = 0; s < (int)t.size(); s++) {
+            tree.push_back({map[t[s].first], map[t[s].second]});
+            map[m + s] = nxt++;
+        }
+        return map[2 * m - 2];
+    }
+
+    // split S into two parts inside the balance window with a small cut
+    void split(const std::vector<int> &S, std::vector<int> &A, std::vector<int> &B) {
+        const int m = (int)S.size();
+        for (int i = 0; i < m; i++) where[S[i]] = i;
+        std::vector<std::vector<int>> nb(m);  // one entry per shared label
+        for (int i = 0; i < m; i++)
+            for (int id : p.leaf_labels[S[i]]) {
+                const int o = other(id, S[i]);
+                if (o >= 0 && where[o] >= 0) nb[i].push_back(where[o]);
+            }
+        for (int v : S) where[v] = -1;
+        int lo = (int)std::ceil(0.5 * (1.0 - eps) * m), hi = (int)std::floor(0.5 * (1.0 + eps) * m);
+        lo = std::max(lo, 1);
+        hi = std::min(hi, m - 1);
+        if (lo > hi) lo = hi = m / 2;
+        std::vector<int> best_side;
+        int best_cut = -1, best_imb = 0;
+        std::vector<int> side(m), conn(m);
+        for (int r = 0; r < restarts; r++) {
+            // region growth from a random tensor to a random size in [lo, hi]
+            const int target = lo + (int)(rng.next() % (uint64_t)(hi - lo + 1));
+            std::fill(side.begin(), side.end(), 1);
+            std::fill(conn.begin(), conn.end(), 0);
+            int n0 = 0;
+            int v = (int)(rng.next() % (uint64_t)m);
+            for (;;) {
+                side[v] = 0;
+                n0++;
+                for (int j : nb[v]) conn[j]++;
+                if (n0 >= target) break;
+                int bv = -1, bc = -1, ties = 0;
+                for (int j = 0; j < m; j++) {
+                    if (side[j] == 0) continue;
+                    if (conn[j] > bc) { bc = conn[j]; bv = j; ties = 1; }
+                    else if (conn[j] == bc && rng.next() % (uint64_t)(++ties) == 0) bv = j;
+                }
+                v = bv;
+            }
+            const int cut = fm_refine(nb, side, nullptr, lo, hi, 12);
+            n0 = 0;
+            for (int i = 0; i < m; i++) n0 += side[i] == 0;
+            const int imb = std::abs(2 * n0 - m);
+            if (best_cut < 0 || cut < best_cut || (cut == best_cut && imb < best_imb)) {
+                best_cut = cut;
+                best_imb = imb;
+                best_side = side;
+            }
+        }
+        A.clear();
+        B.clear();
+        for (int i = 0; i < m; i++) (best_side[i] == 0 ? A : B).push_back(S[i]);
+    }
+
+    int build(const std::vector<int> &S) {
+        if (S.size() == 1) return S[0];
+        if ((int)S.size() <= leaf_max) return greedy_part(S);
+        std::vector<int> A, B;
+        split(S, A, B);
+        const int a = build(A), b = build(B);
+        tree.push_back({std::min(a, b), std::max(a, b)});
+        return nxt++;
+    }
+};
+
+// One hierarchical-bipartition trial.  plain: the balance window +-10%,
+// parts of <= 60 tensors (the paper's setting) and plain greedy inside;
+// else the window, the part size and the greedy noise are drawn from seed.
+Tree bipartition_trial(const Problem &p, uint64_t seed, bool plain) {
+    Rng rng(seed);
+    double eps = 0.1;
+    int leaf_max = 60, restarts = 4;
+    if (!plain) {
+        eps = 0.02 + 0.58 * rng.uniform();
+        leaf_max = (int)std::lround(std::exp2(1.0 + 5.0 * rng.uniform()));
+        restarts = 1 + (int)(rng.next() % 4);
+    }
+    Bisector bs(p, rng.next(), eps, std::max(leaf_max, 2), restarts, plain);
+    std::vector<int> all(p.n);
+    for (int i = 0; i < p.n; i++) all[i] = i;
+    bs.build(all);
+    return bs.tree;
+}
+
 // Subtree reconfiguration.  For each internal node v, the subtree below v is
 // cut at a frontier of up to kmax tensors (expanding the costliest step
 // first) and the frontier is re-contracted in the cheapest order, found by
@@ -561,6 +777,7 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     Problem p;
     if (!make_problem(labels, open, p)) return fail(TN_ERR_ARG, "open label held by no tensor");
     if (p.n == 0) return fail(TN_ERR_ARG, "empty network");
+    if (opts.method < 0 || opts.method > 2) return fail(TN_ERR_ARG, "unknown order-search method");
     if (p.n == 1) {
         SearchResult r;
         r.log2_width = (double)labels[0].size();
@@ -587,7 +804,10 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
         for (;;) {
             int t = next.fetch_add(1);
             if (t >= opts.trials) break;
-            Tree tree = greedy_trial(p, opts.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1), t == 0);
+            const uint64_t ts_seed = opts.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1);
+            const bool bip = opts.method == 1 || (opts.method == 2 && (t & 1));
+            Tree tree = bip ? bipartition_trial(p, ts_seed, t == (opts.method == 2 ? 1 : 0))
+                            : greedy_trial(p, ts_seed, t == 0);
             if (!tree_sets(p, tree, ts)) continue;
             SliceEval ev;
             // both slicing rules; the cheaper result that meets the cap wins

@@ -66,6 +66,13 @@ bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::v
 
 tn_search_opts default_search_opts();
 
+// order.cpp: Fiduccia-Mattheyses refinement of a two-way split of a graph
+// (nb: one entry per shared bond; side: 0/1 per vertex, refined in place;
+// the side-0 count stays in [lo, hi]; vertices marked in fixed never move);
+// returns the cut
+int fm_refine(const std::vector<std::vector<int>> &nb, std::vector<int> &side, const std::vector<char> *fixed, int lo,
+              int hi, int max_passes);
+
 // plan.cpp: replace a plan leaf's values by complex128 device data (rounded
 // to complex64), stream-ordered
 int plan_load_leaf_c128(tn_plan_t plan, int leaf, const double *d_src, CUstream_st *stream);

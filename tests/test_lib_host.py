@@ -130,14 +130,24 @@ def test_plan_rejects_dangling_label(tn):
     assert err.code == -1
 
 
-def test_head_tail_order_has_the_cut_at_its_root(tn):
+@pytest.mark.parametrize("method", ["greedy", "bipartition"])
+def test_head_tail_order_has_the_cut_at_its_root(tn, method):
     """tn_find_order_head_tail: a valid SSA tree whose last step joins a side
     without open labels (the head) and a side holding all of them; the head
-    is sliced as asked; the reported cut equals the labels the sides share."""
+    is sliced as asked; the reported cut equals the labels the sides share.
+    The bipartition method refines the first cut, which never grows it, and
+    its tree contracts (FP64 oracle) to the state vector's amplitudes."""
     from tn_inputs import sycamore_circuit, random_bits
     circ = sycamore_circuit("rect", 4, 5, 10, 77)
-    L, T, O = tn.circuit_network(circ, random_bits(20, 77), list(range(15, 20)))
-    tree, sliced, st = tn.find_order_head_tail(L, O, opts=tn.search_opts(trials=64, n_sliced=2))
+    bits = random_bits(20, 77)
+    L, T, O = tn.circuit_network(circ, bits, list(range(15, 20)))
+    tree, sliced, st = tn.find_order_head_tail(L, O, opts=tn.search_opts(trials=64, n_sliced=2, method=method))
+    if method != "greedy":
+        st0 = tn.find_order_head_tail(L, O, opts=tn.search_opts(trials=64, n_sliced=2))[2]
+        assert st["n_cut"] <= st0["n_cut"]
+        amp = oc.contract(L, [np.asarray(t, np.complex128) for t in T], O, tree=tree).reshape(-1)
+        sv = osv.amplitudes(circ, bits, list(range(15, 20)))
+        assert np.linalg.norm(amp - sv) / np.linalg.norm(sv) < 1e-6
     n = len(L)
     assert len(tree) == n - 1 and len(sliced) == 2
     used = set()
@@ -253,3 +263,55 @@ def internal_labels_of(labels):
         for x in l:
             cnt[x] = cnt.get(x, 0) + 1
     return sorted(x for x, c in cnt.items() if c == 2)
+
+
+@pytest.mark.parametrize("method", ["bipartition", "mixed"])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_bipartition_search_gives_valid_exact_trees(tn, method, seed):
+    """Hierarchical-bipartition trials (appendix, "Finding contraction order
+    using hierarchical partitioning"): a valid SSA tree over every leaf, whose
+    FP64 oracle contraction equals the plain one on a random network and the
+    state vector on a circuit network (3x4 grid, parts of a few tensors, so
+    the splits, not only the greedy inside a part, decide the tree)."""
+    net = random_network(seed, n_tensors=18, n_bonds=30, n_open=3, max_rank=6)
+    tree, sliced, st = tn.find_order(net.labels, net.open_labels,
+                                     tn.search_opts(trials=24, n_sliced=2, method=method))
+    n = len(net.labels)
+    used = set()
+    for t, (a, b) in enumerate(tree):
+        assert 0 <= a < n + t and 0 <= b < n + t and a != b and a not in used and b not in used
+        used.update((a, b))
+    assert len(tree) == n - 1 and len(sliced) == 2
+    ref = oc.contract(net.labels, net.data, net.open_labels)
+    got = oc.contract(net.labels, net.data, net.open_labels, tree=tree)
+    assert np.abs(got - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+    circ = sycamore_circuit("rect", 3, 4, 8, seed)
+    bits = random_bits(12, seed)
+    L, T, O = tn.circuit_network(circ, bits, [9, 10, 11])
+    ctree, _, _ = tn.find_order(L, O, tn.search_opts(trials=24, n_sliced=0, method=method))
+    amp = oc.contract(L, [np.asarray(t, np.complex128) for t in T], O, tree=ctree).reshape(-1)
+    sv = osv.amplitudes(circ, bits, [9, 10, 11])
+    assert np.linalg.norm(amp - sv) / np.linalg.norm(sv) < 1e-6
+
+
+def test_bipartition_search_is_deterministic_and_checks_its_method(tn):
+    cfg = make_config(1)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    a = tn.find_order(L, O, tn.search_opts(trials=64, threads=1, n_sliced=2, method="bipartition"))
+    b = tn.find_order(L, O, tn.search_opts(trials=64, threads=4, n_sliced=2, method="bipartition"))
+    assert a[0] == b[0] and a[1] == b[1]
+    with pytest.raises(tn.TNError):
+        tn.find_order(L, O, tn.search_opts(trials=4, method=3))
+
+
+def test_bipartition_finds_cheaper_trees_on_the_53_qubit_network(tn):
+    """On the 53-qubit 14-cycle network (294 tensors, intermediates capped at
+    2^30), hierarchical bipartition ends below randomised greedy in total
+    complex MACs at the same number of trials (the appendix's reason for
+    partitioning: the split structure keeps every pairwise step small)."""
+    cfg = make_config(4)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    _, _, g = tn.find_order(L, O, tn.search_opts(trials=256, log2_cap=30))
+    _, _, b = tn.find_order(L, O, tn.search_opts(trials=256, log2_cap=30, method="bipartition"))
+    assert b["log2_width"] <= 30 and g["log2_width"] <= 30
+    assert b["log2_total"] < g["log2_total"] - 0.5, (b, g)
