@@ -275,7 +275,9 @@ const char *tn_last_error(void);
  * greedy or hierarchical-bipartition trials (opts->method) scored by the
  * Fig. 3 cost 2^{n_A+n_B+n_AB} summed over steps, then greedy slicing to the
  * cap or count and subtree reconfiguration of the best trees.  TN_ERR_ARG
- * for an unknown method.  Writes the tree (2*(n_tensors-1)
+ * for an unknown method, or a network that breaks tn_plan_create's rules
+ * (a label held by more than two tensors or twice by one, a label held once
+ * that is not open, an open label held twice or listed twice).  Writes the tree (2*(n_tensors-1)
  * SSA ids), the sliced labels (up to max_sliced) and stats[4] =
  * {log2 total MACs over all slices, log2 largest intermediate per slice,
  *  n_sliced, log2 MACs per slice}.

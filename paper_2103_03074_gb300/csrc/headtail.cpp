@@ -243,6 +243,8 @@ extern "C" int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, cons
         if (ranks[i] < 0 || ranks[i] > 62) return fail(TN_ERR_ARG, "tn_find_order_head_tail: rank out of range");
     const int n = n_tensors;
     const auto labs = parse_labels(n, ranks, labels);
+    if (const char *bad = check_network(labs, std::vector<int32_t>(open_labels, open_labels + n_open)))
+        return fail(TN_ERR_ARG, std::string("tn_find_order_head_tail: ") + bad);
     const std::set<int32_t> open(open_labels, open_labels + n_open);
     std::unordered_map<int32_t, std::vector<int>> holders;
     for (int i = 0; i < n; i++)

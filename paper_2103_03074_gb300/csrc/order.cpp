@@ -80,18 +80,29 @@ struct Problem {
     std::vector<std::vector<int>> leaf_labels;  // remapped ids per leaf
 };
 
-bool make_problem(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
-                  Problem &p) {
+// Builds the search's view of a network; returns nullptr, or what is wrong
+// with it (a label is a bond between at most two tensors, each holding it
+// once; every kept label is held by some tensor).
+const char *make_problem(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                         Problem &p) {
     std::unordered_map<int32_t, int> remap;
-    for (auto &l : labels)
-        for (int32_t x : l)
-            if (!remap.count(x)) {
-                int id = (int)remap.size();
-                remap[x] = id;
+    std::vector<int> holders;
+    for (auto &l : labels) {
+        for (int32_t x : l) {
+            auto it = remap.find(x);
+            if (it == remap.end()) {
+                it = remap.emplace(x, (int)remap.size()).first;
                 p.id2label.push_back(x);
+                holders.push_back(0);
             }
+            if (++holders[it->second] > 2) return "label held by more than two tensors";
+        }
+        for (size_t a = 0; a < l.size(); a++)
+            for (size_t b = a + 1; b < l.size(); b++)
+                if (l[a] == l[b]) return "label repeated within a tensor";
+    }
     for (int32_t x : open)
-        if (!remap.count(x)) return false;  // open label held by no tensor
+        if (!remap.count(x)) return "open label held by no tensor";
     p.n = (int)labels.size();
     p.L = (int)remap.size();
     p.leaf.init(p.n, p.L);
@@ -107,7 +118,7 @@ bool make_problem(const std::vector<std::vector<int32_t>> &labels, const std::ve
         int id = remap[x];
         p.open[id >> 6] |= 1ull << (id & 63);
     }
-    return true;
+    return nullptr;
 }
 
 // All node label sets of a tree (leaves, then one per step) and step unions.
@@ -718,6 +729,27 @@ Tree reconfigure(const Problem &p, const Tree &tree, const std::vector<uint64_t>
 
 }  // namespace
 
+const char *check_network(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open) {
+    std::unordered_map<int32_t, int> cnt;
+    for (const auto &l : labels) {
+        for (size_t a = 0; a < l.size(); a++) {
+            for (size_t b = a + 1; b < l.size(); b++)
+                if (l[a] == l[b]) return "label repeated within a tensor";
+            if (++cnt[l[a]] > 2) return "label held by more than two tensors";
+        }
+    }
+    std::unordered_map<int32_t, int> seen;
+    for (int32_t x : open) {
+        auto it = cnt.find(x);
+        if (it == cnt.end()) return "open label held by no tensor";
+        if (it->second == 2) return "open label held by two tensors";
+        if (++seen[x] > 1) return "open label repeated";
+    }
+    for (const auto &kv : cnt)
+        if (kv.second == 1 && !seen.count(kv.first)) return "label held by one tensor must be open";
+    return nullptr;
+}
+
 tn_search_opts default_search_opts() {
     tn_search_opts o;
     std::memset(&o, 0, sizeof o);
@@ -736,7 +768,7 @@ tn_search_opts default_search_opts() {
 bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
                    const Tree &tree, const std::vector<int32_t> &sliced, SearchResult &out) {
     Problem p;
-    if (!make_problem(labels, open, p)) return false;
+    if (make_problem(labels, open, p)) return false;
     TreeSets ts;
     if (!tree_sets(p, tree, ts)) return false;
     std::unordered_map<int32_t, int> remap;
@@ -775,7 +807,8 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     if (k < 1) k = 1;
     out.clear();
     Problem p;
-    if (!make_problem(labels, open, p)) return fail(TN_ERR_ARG, "open label held by no tensor");
+    if (const char *bad = check_network(labels, open)) return fail(TN_ERR_ARG, std::string("order search: ") + bad);
+    if (const char *bad = make_problem(labels, open, p)) return fail(TN_ERR_ARG, std::string("order search: ") + bad);
     if (p.n == 0) return fail(TN_ERR_ARG, "empty network");
     if (opts.method < 0 || opts.method > 2) return fail(TN_ERR_ARG, "unknown order-search method");
     if (p.n == 1) {
@@ -838,6 +871,7 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     for (auto &v : keep)
         for (auto &c : v) all.push_back(std::move(c));
     std::sort(all.begin(), all.end(), better);
+    if (all.empty()) return fail(TN_ERR_ARG, "order search produced no tree");
     if ((int)all.size() > kk) all.resize(kk);
     // subtree reconfiguration of the best few trees, under their slicing,
     // then slicing again and a second round under the new slice set
@@ -947,7 +981,7 @@ extern "C" int tn_merge_branches(int n_tensors, const int32_t *ranks, const int3
     std::vector<int32_t> kept(open_labels, open_labels + n_open);
     kept.insert(kept.end(), sliced_labels, sliced_labels + n_sliced);
     Problem p;
-    if (!make_problem(labs, kept, p)) return fail(TN_ERR_ARG, "tn_merge_branches: kept label held by no tensor");
+    if (const char *bad = make_problem(labs, kept, p)) return fail(TN_ERR_ARG, std::string("tn_merge_branches: ") + bad);
     Tree tree(n_steps);
     for (int t = 0; t < n_steps; t++) tree[t] = {tree_in[2 * t], tree_in[2 * t + 1]};
     TreeSets ts;

@@ -66,6 +66,12 @@ bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::v
 
 tn_search_opts default_search_opts();
 
+// order.cpp: the network rules tn_plan_create also enforces (each label held
+// by one or two tensors, at most once by each; the labels held once are
+// exactly the open ones, each listed once); nullptr if they hold, else what
+// is wrong
+const char *check_network(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open);
+
 // order.cpp: Fiduccia-Mattheyses refinement of a two-way split of a graph
 // (nb: one entry per shared bond; side: 0/1 per vertex, refined in place;
 // the side-0 count stays in [lo, hi]; vertices marked in fixed never move);

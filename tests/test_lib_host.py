@@ -315,3 +315,24 @@ def test_bipartition_finds_cheaper_trees_on_the_53_qubit_network(tn):
     _, _, b = tn.find_order(L, O, tn.search_opts(trials=256, log2_cap=30, method="bipartition"))
     assert b["log2_width"] <= 30 and g["log2_width"] <= 30
     assert b["log2_total"] < g["log2_total"] - 0.5, (b, g)
+
+
+@pytest.mark.parametrize("labels,open_labels,why", [
+    ([[1, 2], [1, 3], [1, 4], [2, 3, 4, 5]], [5], "more than two tensors"),
+    ([[1, 1], [2]], [2], "repeated within a tensor"),
+    ([[1, 2], [2, 3]], [1], "must be open"),
+    ([[1, 2], [2, 1, 3]], [1, 3], "open label held by two tensors"),
+    ([[1, 2], [2, 3]], [1, 3, 1], "open label repeated"),
+    ([[1, 2], [2, 3]], [1, 3, 9], "held by no tensor"),
+])
+def test_order_search_rejects_malformed_networks(tn, labels, open_labels, why):
+    """The order searches apply tn_plan_create's network rules on the host
+    (a label is a bond between at most two tensors, held once by each; the
+    labels held once are the open ones) and return TN_ERR_ARG, whatever the
+    method; a label held twice by one tensor used to leave the greedy search
+    without any valid tree."""
+    for method in ("greedy", "bipartition"):
+        with pytest.raises(tn.TNError, match=why):
+            tn.find_order(labels, open_labels, tn.search_opts(trials=4, method=method))
+    with pytest.raises(tn.TNError):
+        tn.find_order_head_tail(labels, open_labels, opts=tn.search_opts(trials=4))
