@@ -128,7 +128,12 @@ typedef struct {
      * tensors, the others draw the balance window and part size); 2 both,
      * alternating.  Slicing and subtree reconfiguration follow either way. */
     int32_t method;
-    int32_t reserved;
+    /* what ranks the trials: 0 total complex MACs over all slices (default);
+     * 1 the roofline time of the tree compiled for rank_form with
+     * 2^rank_batch_log2 slices per block (-1: the largest block whose arena
+     * fits 160 GiB), as tn_estimate_tree_ms prices it.  Either way the
+     * learned ranking (cost_model, candidates) then picks among the best. */
+    int32_t objective;
 } tn_search_opts;
 
 /* A circuit: gate g acts on gate_nq[g] (1 or 2) qubits gate_q[2g], gate_q[2g+1]
@@ -285,6 +290,25 @@ const char *tn_last_error(void);
 int tn_find_order(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                   const int32_t *open_labels, const tn_search_opts *opts, int32_t *out_tree,
                   int max_sliced, int32_t *out_sliced, int *out_n_sliced, double *stats);
+
+/*
+ * Analytic time of a tree (the FLOP/memory fallback of the learned cost
+ * model): the plan tn_plan_create would build for `form` is compiled on the
+ * host (no CUDA call) and every op is priced at its roofline time, the
+ * larger of its algorithmic bytes over 7 TB/s and its flops over its unit's
+ * peak (FP32 CUDA cores 80 TFLOP/s, tensor cores 2.25 PFLOP/s, 1.125 for
+ * TF32x3), plus 2 us per launch; the slice-invariant prologue counts once,
+ * the per-block body once per block.  The block holds 2^batch_log2 slices
+ * (capped at n_sliced); batch_log2 < 0 takes the largest block whose arena
+ * and leaves fit arena_budget bytes (<= 0: 160 GiB), as tn_plan_create
+ * sizes it.  Network, sliced labels and tree as for tn_plan_create (same
+ * checks, TN_ERR_ARG).  *out_ms: milliseconds for all 2^n_sliced slices;
+ * out_batch_log2 / out_arena (may be NULL): the block width and arena bytes.
+ */
+int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                        const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
+                        const int32_t *tree, tn_form form, int batch_log2, int64_t arena_budget, double *out_ms,
+                        int *out_batch_log2, int64_t *out_arena);
 
 /*
  * Branch merging (appendix, "Details of simulations"): in a tree, a large

@@ -40,7 +40,7 @@ class PlanOpts(ctypes.Structure):
 class SearchOpts(ctypes.Structure):
     _fields_ = [("trials", _i32), ("seed", ctypes.c_uint64), ("log2_cap", _i32), ("n_sliced", _i32),
                 ("threads", _i32), ("candidates", _i32), ("rank_batch_log2", _i32), ("rank_form", _i32),
-                ("cost_model", _vp), ("method", _i32), ("reserved", _i32)]
+                ("cost_model", _vp), ("method", _i32), ("objective", _i32)]
 
 
 class Circuit(ctypes.Structure):
@@ -99,7 +99,7 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
             "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
-            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches"]
+            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -132,17 +132,21 @@ def _dev_ptr(t):
 
 
 SEARCH_METHODS = {"greedy": 0, "bipartition": 1, "mixed": 2}
+SEARCH_OBJECTIVES = {"macs": 0, "roofline": 1}
 
 
 def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads=0, candidates=0,
-                rank_batch_log2=-1, rank_form="fp32", cost_model=None, method="greedy"):
+                rank_batch_log2=-1, rank_form="fp32", cost_model=None, method="greedy", objective="macs"):
     """Order-search options (tn_search_opts).  method: "greedy" (randomised
     greedy trials), "bipartition" (hierarchical min-cut bipartition, greedy
-    inside parts of a few dozen tensors) or "mixed" (alternating)."""
+    inside parts of a few dozen tensors) or "mixed" (alternating).
+    objective: "macs" (total complex MACs) or "roofline" (the tree's plan for
+    rank_form priced at its roofline time, as estimate_tree_ms does)."""
     f = FORMS[rank_form] if isinstance(rank_form, str) else int(rank_form)
     m = SEARCH_METHODS[method] if isinstance(method, str) else int(method)
+    ob = SEARCH_OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
     cm = cost_model._h if cost_model is not None else None
-    return SearchOpts(trials, seed, log2_cap, n_sliced, threads, candidates, rank_batch_log2, f, cm, m)
+    return SearchOpts(trials, seed, log2_cap, n_sliced, threads, candidates, rank_batch_log2, f, cm, m, ob)
 
 
 def plan_opts(batch_log2=-1, mem_budget=0, profile=0, use_graph=0, tc_chunk_bytes=0, tc_flush_bytes=0,
@@ -221,6 +225,26 @@ def find_order(labels, open_labels, opts=None, max_sliced=64):
     steps = [(int(tree[2 * i]), int(tree[2 * i + 1])) for i in range(n - 1)]
     stats = dict(log2_total=st[0], log2_width=st[1], n_sliced=int(st[2]), log2_slice=st[3])
     return steps, [int(x) for x in sl[:nsl.value]], stats
+
+
+def estimate_tree_ms(labels, open_labels, sliced_labels, tree, form="fp32", batch_log2=-1, arena_budget=0):
+    """tn_estimate_tree_ms: (ms for all slices, block width in sliced bits,
+    arena bytes) of the plan the tree compiles to, every op at its roofline
+    time (host only, no GPU needed)."""
+    ranks = np.asarray([len(l) for l in labels], dtype=np.int32)
+    flat = np.asarray([x for l in labels for x in l] or [0], dtype=np.int32)
+    ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
+    sl = np.asarray(list(sliced_labels) or [0], dtype=np.int32)
+    tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    ms = ctypes.c_double(0)
+    nb = ctypes.c_int(0)
+    arena = ctypes.c_int64(0)
+    _check(_lib.tn_estimate_tree_ms(len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol),
+                                    len(sliced_labels), _ptr(sl), len(tree), _ptr(tr), f, int(batch_log2),
+                                    ctypes.c_int64(int(arena_budget)), ctypes.byref(ms), ctypes.byref(nb),
+                                    ctypes.byref(arena)), "tn_estimate_tree_ms")
+    return ms.value, nb.value, arena.value
 
 
 def merge_branches(labels, open_labels, sliced_labels, tree, max_small_rank=0):

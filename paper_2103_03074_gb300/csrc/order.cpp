@@ -811,6 +811,17 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     if (const char *bad = make_problem(labels, open, p)) return fail(TN_ERR_ARG, std::string("order search: ") + bad);
     if (p.n == 0) return fail(TN_ERR_ARG, "empty network");
     if (opts.method < 0 || opts.method > 2) return fail(TN_ERR_ARG, "unknown order-search method");
+    if (opts.objective < 0 || opts.objective > 1) return fail(TN_ERR_ARG, "unknown order-search objective");
+    const tn_form rform =
+        (opts.rank_form >= TN_FP32 && opts.rank_form <= TN_FP16X3) ? (tn_form)opts.rank_form : TN_FP32;
+    // the trials' score: log2 of total MACs, or of the compiled plan's roofline time
+    const auto score = [&](const Tree &tree, const SliceEval &ev) {
+        if (opts.objective != 1) return ev.log2_total;
+        std::vector<int32_t> sl;
+        for (int id : ev.sliced) sl.push_back(p.id2label[id]);
+        const double ms = tree_roofline_ms(labels, open, tree, sl, rform, opts.rank_batch_log2, kNominalArenaBytes);
+        return ms > 0 ? std::log2(ms) : (double)INFINITY;
+    };
     if (p.n == 1) {
         SearchResult r;
         r.log2_width = (double)labels[0].size();
@@ -819,8 +830,11 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     }
     int threads = opts.threads > 0 ? opts.threads : (int)std::max(1u, std::thread::hardware_concurrency());
     threads = std::min(threads, opts.trials);
-    struct Cand { double key_w, total, width; int trial; Tree tree; SliceEval ev; };
-    // order: smaller over-cap width, then smaller total cost, then lower trial
+    // total: the score the candidates are ranked by; rl: the roofline score
+    // (objective 1 only)
+    struct Cand { double key_w, total, width; int trial; Tree tree; SliceEval ev; double rl = 0; };
+    // order: smaller over-cap width, then the smaller score (log2 MACs or log2
+    // roofline ms), then lower trial
     auto better = [](const Cand &a, const Cand &b) {
         if (a.key_w != b.key_w) return a.key_w < b.key_w;
         if (a.total != b.total) return a.total < b.total;
@@ -829,8 +843,17 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     // every thread keeps its kk best, so the union holds the global kk best
     // whatever the thread count (the search is deterministic in the seed)
     const int kk = std::max(k, 4);
-    std::vector<std::vector<Cand>> keep(threads);
+    std::vector<std::vector<Cand>> keep(threads), keep_m(threads);
     std::atomic<int> next{0};
+    const auto insert = [&](std::vector<Cand> &mine, Cand &&c) {
+        if ((int)mine.size() < kk) {
+            mine.push_back(std::move(c));
+            std::sort(mine.begin(), mine.end(), better);
+        } else if (better(c, mine.back())) {
+            mine.back() = std::move(c);
+            std::sort(mine.begin(), mine.end(), better);
+        }
+    };
     auto worker = [&](int tid) {
         TreeSets ts;
         auto &mine = keep[tid];
@@ -853,14 +876,13 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
             };
             if (key(ev1) < key(ev)) ev = std::move(ev1);
             const bool over = opts.log2_cap >= 0 && ev.log2_width > opts.log2_cap;
-            Cand c{over ? ev.log2_width : 0.0, ev.log2_total, ev.log2_width, t, std::move(tree), ev};
-            if ((int)mine.size() < kk) {
-                mine.push_back(std::move(c));
-                std::sort(mine.begin(), mine.end(), better);
-            } else if (better(c, mine.back())) {
-                mine.back() = std::move(c);
-                std::sort(mine.begin(), mine.end(), better);
-            }
+            const double sc = score(tree, ev);
+            // the roofline objective also keeps the best trials by MACs:
+            // reconfiguration reshapes a tree, so its time before says
+            // little about its time after
+            if (opts.objective == 1)
+                insert(keep_m[tid], Cand{over ? ev.log2_width : 0.0, ev.log2_total, ev.log2_width, t, tree, ev, sc});
+            insert(mine, Cand{over ? ev.log2_width : 0.0, sc, ev.log2_width, t, std::move(tree), ev, sc});
         }
     };
     std::vector<std::thread> pool;
@@ -873,6 +895,24 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     std::sort(all.begin(), all.end(), better);
     if (all.empty()) return fail(TN_ERR_ARG, "order search produced no tree");
     if ((int)all.size() > kk) all.resize(kk);
+    if (opts.objective == 1) {
+        // the MAC-ranked candidates first, in the order (and so with the
+        // reconfiguration seeds) a MAC-ranked search gives them, then the
+        // time-ranked ones it lacks: the time-ranked pick can only improve
+        // on the MAC-ranked one; all ranked by roofline time from here on
+        std::vector<Cand> bym;
+        for (auto &v : keep_m)
+            for (auto &c : v) bym.push_back(std::move(c));
+        std::sort(bym.begin(), bym.end(), better);
+        if ((int)bym.size() > kk) bym.resize(kk);
+        for (auto &c : all) {
+            bool dup = false;
+            for (const auto &b : bym) dup = dup || b.trial == c.trial;
+            if (!dup) bym.push_back(std::move(c));
+        }
+        all = std::move(bym);
+        for (auto &c : all) c.total = c.rl;
+    }
     // subtree reconfiguration of the best few trees, under their slicing,
     // then slicing again and a second round under the new slice set
     if (opts.trials > 1) {
@@ -899,15 +939,16 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
                 ev = key(e1) < key(e0) ? std::move(e1) : std::move(e0);
             }
             const bool over = opts.log2_cap >= 0 && ev.log2_width > opts.log2_cap;
-            extra[i] = Cand{over ? ev.log2_width : 0.0, ev.log2_total, ev.log2_width, c.trial, std::move(t), ev};
+            const double sc = score(t, ev);
+            extra[i] = Cand{over ? ev.log2_width : 0.0, sc, ev.log2_width, c.trial, std::move(t), ev};
         };
         for (int i = 1; i < R; i++) pool2.emplace_back(improve, i);
         improve(0);
         for (auto &th : pool2) th.join();
         for (auto &c : extra)
             if (!c.tree.empty()) all.push_back(std::move(c));
-        std::sort(all.begin(), all.end(), better);
     }
+    std::sort(all.begin(), all.end(), better);
     for (auto &c : all) {
         if ((int)out.size() >= k) break;
         bool dup = false;

@@ -1080,16 +1080,143 @@ int rank_candidates(const std::vector<std::vector<int32_t>> &labels, const std::
 
 using namespace tn;
 
+namespace tn {
+
+// Roofline time of a compiled plan, for all 2^n_sliced slices: every op at
+// roofline_ms (bytes over HBM bandwidth or flops over its unit's peak, plus
+// a launch floor), the slice-invariant prologue once and the per-block body
+// once per block.  The batch width is batch_log2 when >= 0 (capped at
+// n_sliced), else the largest whose arena and leaves fit `budget` bytes, as
+// tn_plan_create chooses it (0 when none fits).  Host only.
+int plan_roofline(tn_plan &P, int batch_log2, double budget, int64_t leaf_bytes, double &ms, int &nb_out,
+                  int64_t &arena_out) {
+    int nb = batch_log2 >= 0 ? std::min(batch_log2, P.n_sliced) : P.n_sliced;
+    int64_t arena = compile(P, nb);
+    if (arena < 0) return TN_ERR_ARG;
+    if (batch_log2 < 0 && (double)(arena + leaf_bytes) > budget && nb > 0) {
+        // the arena grows with the batch width: bisect for the largest fit
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            const int64_t a = compile(P, mid);
+            if (a < 0) return TN_ERR_ARG;
+            if ((double)(a + leaf_bytes) <= budget) lo = mid; else hi = mid - 1;
+        }
+        nb = lo;
+        arena = compile(P, nb);
+        if (arena < 0) return TN_ERR_ARG;
+    }
+    double pro = 0, body = 0;
+    for (const auto &op : P.prologue) pro += roofline_ms(op, P.form);
+    for (const auto &op : P.batch) body += roofline_ms(op, P.form);
+    ms = pro + std::exp2((double)(P.n_sliced - nb)) * body;
+    nb_out = nb;
+    arena_out = arena;
+    return TN_OK;
+}
+
+double tree_roofline_ms(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                        const Tree &tree, const std::vector<int32_t> &sliced, tn_form form, int batch_log2,
+                        double budget) {
+    tn_plan P;
+    P.form = form;
+    P.n_tensors = (int)labels.size();
+    P.labels = labels;
+    P.open = open;
+    P.n_open = (int)open.size();
+    P.sliced = sliced;
+    P.n_sliced = (int)sliced.size();
+    P.tree = tree;
+    P.leaf_off.resize(labels.size());
+    int64_t off = 0;
+    for (size_t i = 0; i < labels.size(); i++) {
+        P.leaf_off[i] = off;
+        off += (int64_t)1 << labels[i].size();
+    }
+    double ms = -1;
+    int nb = 0;
+    int64_t arena = 0;
+    if (plan_roofline(P, batch_log2, budget, off * 8, ms, nb, arena)) return -1.0;
+    return ms;
+}
+
+}  // namespace tn
+
+namespace tn {
+
+// The host half of plan creation (no CUDA call): checks the network, the
+// open and sliced labels and the tree, and copies them into P; *total_elems
+// receives the leaves' element count.
+int plan_host_setup(tn_plan &P, int n_tensors, const int32_t *ranks, const int32_t *labels, int n_labels,
+                    const int32_t *bond_dims, int n_open, const int32_t *open_labels, int n_sliced,
+                    const int32_t *sliced_labels, int n_steps, const int32_t *tree, int64_t *total_elems) {
+    if (n_tensors <= 0 || !ranks) return fail(TN_ERR_ARG, "need at least one tensor");
+    if (n_open < 0 || n_open > kMaxRank || (n_open > 0 && !open_labels)) return fail(TN_ERR_ARG, "bad open labels");
+    if (n_sliced < 0 || n_sliced > 62 || (n_sliced > 0 && !sliced_labels)) return fail(TN_ERR_ARG, "bad sliced labels");
+    if (n_steps != n_tensors - 1 || (n_steps > 0 && !tree)) return fail(TN_ERR_ARG, "tree must have n_tensors - 1 steps");
+    P.n_tensors = n_tensors;
+
+    P.n_open = n_open;
+    P.n_sliced = n_sliced;
+    P.open.assign(open_labels, open_labels + n_open);
+    P.sliced.assign(sliced_labels, sliced_labels + n_sliced);
+    // labels: validity
+    std::unordered_map<int32_t, int> count;
+    size_t off = 0;
+    int64_t total = 0;
+    P.labels.resize(n_tensors);
+    P.leaf_off.resize(n_tensors);
+    for (int i = 0; i < n_tensors; i++) {
+        if (ranks[i] < 0 || ranks[i] > 30) return fail(TN_ERR_ARG, "tensor rank out of range [0, 30]");
+        P.labels[i].assign(labels + off, labels + off + ranks[i]);
+        off += ranks[i];
+        std::unordered_set<int32_t> seen;
+        for (int32_t x : P.labels[i]) {
+            if (x < 0) return fail(TN_ERR_ARG, "negative label");
+            if (n_labels > 0 && x >= n_labels) return fail(TN_ERR_ARG, "label >= n_labels");
+            if (bond_dims && bond_dims[x] != 2) return fail(TN_ERR_ARG, "only bond dimension 2 is supported");
+            if (!seen.insert(x).second) return fail(TN_ERR_ARG, "label repeated within a tensor");
+            count[x]++;
+        }
+        P.leaf_off[i] = total;
+        total += (int64_t)1 << ranks[i];
+    }
+    std::unordered_set<int32_t> open_set(P.open.begin(), P.open.end());
+    if ((int)open_set.size() != n_open) return fail(TN_ERR_ARG, "open label repeated");
+    for (auto &kv : count) {
+        if (kv.second > 2) return fail(TN_ERR_ARG, "label held by more than two tensors");
+        if (kv.second == 1 && !open_set.count(kv.first)) return fail(TN_ERR_ARG, "label held by one tensor must be open");
+        if (kv.second == 2 && open_set.count(kv.first)) return fail(TN_ERR_ARG, "open label held by two tensors");
+    }
+    for (int32_t x : P.open)
+        if (!count.count(x)) return fail(TN_ERR_ARG, "open label held by no tensor");
+    std::unordered_set<int32_t> sl;
+    for (int32_t x : P.sliced) {
+        if (open_set.count(x)) return fail(TN_ERR_ARG, "a sliced label cannot be open");
+        if (!count.count(x)) return fail(TN_ERR_ARG, "sliced label held by no tensor");
+        if (!sl.insert(x).second) return fail(TN_ERR_ARG, "sliced label repeated");
+    }
+    P.tree.resize(n_steps);
+    std::vector<char> used(2 * n_tensors, 0);
+    for (int t = 0; t < n_steps; t++) {
+        int a = tree[2 * t], b = tree[2 * t + 1];
+        if (a < 0 || b < 0 || a >= n_tensors + t || b >= n_tensors + t || a == b || used[a] || used[b])
+            return fail(TN_ERR_ARG, "tree: bad or reused node id");
+        used[a] = used[b] = 1;
+        P.tree[t] = {a, b};
+    }
+    *total_elems = total;
+    return TN_OK;
+}
+
+}  // namespace tn
+
 extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *ranks, const int32_t *labels,
                               const float *data, int n_labels, const int32_t *bond_dims, int n_open,
                               const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels,
                               int n_steps, const int32_t *tree, tn_form form, const tn_plan_opts *opts) {
     if (!out) return fail(TN_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (n_tensors <= 0 || !ranks) return fail(TN_ERR_ARG, "need at least one tensor");
-    if (n_open < 0 || n_open > kMaxRank || (n_open > 0 && !open_labels)) return fail(TN_ERR_ARG, "bad open labels");
-    if (n_sliced < 0 || n_sliced > 62 || (n_sliced > 0 && !sliced_labels)) return fail(TN_ERR_ARG, "bad sliced labels");
-    if (n_steps != n_tensors - 1 || (n_steps > 0 && !tree)) return fail(TN_ERR_ARG, "tree must have n_tensors - 1 steps");
     if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
     if (form != TN_FP32 && !tc_form_available(form))
         return fail(TN_ERR_ARG, "this arithmetic form is not compiled into this library");
@@ -1100,56 +1227,10 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
         std::memset(&P->opts, 0, sizeof P->opts);
         P->opts.batch_log2 = -1;
     }
-    P->n_tensors = n_tensors;
-    P->n_open = n_open;
-    P->n_sliced = n_sliced;
-    P->open.assign(open_labels, open_labels + n_open);
-    P->sliced.assign(sliced_labels, sliced_labels + n_sliced);
-    // labels: validity
-    std::unordered_map<int32_t, int> count;
-    size_t off = 0;
     int64_t total = 0;
-    P->labels.resize(n_tensors);
-    P->leaf_off.resize(n_tensors);
-    for (int i = 0; i < n_tensors; i++) {
-        if (ranks[i] < 0 || ranks[i] > 30) return fail(TN_ERR_ARG, "tensor rank out of range [0, 30]");
-        P->labels[i].assign(labels + off, labels + off + ranks[i]);
-        off += ranks[i];
-        std::unordered_set<int32_t> seen;
-        for (int32_t x : P->labels[i]) {
-            if (x < 0) return fail(TN_ERR_ARG, "negative label");
-            if (n_labels > 0 && x >= n_labels) return fail(TN_ERR_ARG, "label >= n_labels");
-            if (bond_dims && bond_dims[x] != 2) return fail(TN_ERR_ARG, "only bond dimension 2 is supported");
-            if (!seen.insert(x).second) return fail(TN_ERR_ARG, "label repeated within a tensor");
-            count[x]++;
-        }
-        P->leaf_off[i] = total;
-        total += (int64_t)1 << ranks[i];
-    }
-    std::unordered_set<int32_t> open_set(P->open.begin(), P->open.end());
-    if ((int)open_set.size() != n_open) return fail(TN_ERR_ARG, "open label repeated");
-    for (auto &kv : count) {
-        if (kv.second > 2) return fail(TN_ERR_ARG, "label held by more than two tensors");
-        if (kv.second == 1 && !open_set.count(kv.first)) return fail(TN_ERR_ARG, "label held by one tensor must be open");
-        if (kv.second == 2 && open_set.count(kv.first)) return fail(TN_ERR_ARG, "open label held by two tensors");
-    }
-    for (int32_t x : P->open)
-        if (!count.count(x)) return fail(TN_ERR_ARG, "open label held by no tensor");
-    std::unordered_set<int32_t> sl;
-    for (int32_t x : P->sliced) {
-        if (open_set.count(x)) return fail(TN_ERR_ARG, "a sliced label cannot be open");
-        if (!count.count(x)) return fail(TN_ERR_ARG, "sliced label held by no tensor");
-        if (!sl.insert(x).second) return fail(TN_ERR_ARG, "sliced label repeated");
-    }
-    P->tree.resize(n_steps);
-    std::vector<char> used(2 * n_tensors, 0);
-    for (int t = 0; t < n_steps; t++) {
-        int a = tree[2 * t], b = tree[2 * t + 1];
-        if (a < 0 || b < 0 || a >= n_tensors + t || b >= n_tensors + t || a == b || used[a] || used[b])
-            return fail(TN_ERR_ARG, "tree: bad or reused node id");
-        used[a] = used[b] = 1;
-        P->tree[t] = {a, b};
-    }
+    int rc0 = plan_host_setup(*P, n_tensors, ranks, labels, n_labels, bond_dims, n_open, open_labels, n_sliced,
+                              sliced_labels, n_steps, tree, &total);
+    if (rc0) return rc0;
     // device
     if (cudaGetDevice(&P->device) != cudaSuccess) return fail(TN_ERR_CUDA, "no CUDA device");
     size_t free_b = 0, total_b = 0;
@@ -1813,4 +1894,29 @@ extern "C" int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bit
     }
     tn_plan_destroy(plan);
     return rc;
+}
+
+extern "C" int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                                   const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels,
+                                   int n_steps, const int32_t *tree, tn_form form, int batch_log2,
+                                   int64_t arena_budget, double *out_ms, int *out_batch_log2, int64_t *out_arena) {
+    if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
+    if (!out_ms) return fail(TN_ERR_ARG, "out_ms is NULL");
+    tn_plan P;
+    P.form = form;
+    P.opts.batch_log2 = -1;
+    int64_t total = 0;
+    int rc = plan_host_setup(P, n_tensors, ranks, labels, 0, nullptr, n_open, open_labels, n_sliced, sliced_labels,
+                             n_steps, tree, &total);
+    if (rc) return rc;
+    const double budget = arena_budget > 0 ? (double)arena_budget : kNominalArenaBytes;
+    double ms = 0;
+    int nb = 0;
+    int64_t arena = 0;
+    rc = plan_roofline(P, batch_log2, budget, total * 8, ms, nb, arena);
+    if (rc) return rc;
+    *out_ms = ms;
+    if (out_batch_log2) *out_batch_log2 = nb;
+    if (out_arena) *out_arena = arena;
+    return TN_OK;
 }

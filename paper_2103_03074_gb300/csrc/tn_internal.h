@@ -66,6 +66,17 @@ bool evaluate_tree(const std::vector<std::vector<int32_t>> &labels, const std::v
 
 tn_search_opts default_search_opts();
 
+// plan.cpp: roofline time (ms, all slices) of a tree compiled for `form`
+// with batch_log2 batch bits (< 0: the largest batch whose arena fits
+// `budget` bytes); negative when the tree does not compile.  Host only.
+double tree_roofline_ms(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
+                        const Tree &tree, const std::vector<int32_t> &sliced, tn_form form, int batch_log2,
+                        double budget);
+// the arena budget the search and tn_estimate_tree_ms assume when none is
+// given: 60% of a GB300's ~275 GiB of free HBM, as tn_plan_create's default
+// budget gives on an idle device
+constexpr double kNominalArenaBytes = 160.0 * 1073741824.0;
+
 // order.cpp: the network rules tn_plan_create also enforces (each label held
 // by one or two tensors, at most once by each; the labels held once are
 // exactly the open ones, each listed once); nullptr if they hold, else what

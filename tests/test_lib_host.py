@@ -336,3 +336,65 @@ def test_order_search_rejects_malformed_networks(tn, labels, open_labels, why):
             tn.find_order(labels, open_labels, tn.search_opts(trials=4, method=method))
     with pytest.raises(tn.TNError):
         tn.find_order_head_tail(labels, open_labels, opts=tn.search_opts(trials=4))
+
+
+def test_estimate_tree_ms_prices_each_op_at_its_roofline(tn):
+    """tn_estimate_tree_ms compiles the plan on the host and prices each op
+    at max(bytes / 7 TB/s, flops / unit peak) + 2 us.  One small step (a
+    rank-4 tensor met by a rank-20 one over 2 bonds): 8 B x (|T| + |S| + |C|)
+    against 8 flops per MAC on the 80 TFLOP/s CUDA cores.  One GEMM-shaped
+    step (2^14 x 2^10 x 2^14) in FP32: 8 flops per MAC on the CUDA cores; in
+    the tensor-core forms between 24 (8 for FP16S) tensor flops per MAC at
+    2.25 PFLOP/s and the FP32 time."""
+    T, S = list(range(20)), [18, 19, 20, 21]
+    ms, nb, arena = tn.estimate_tree_ms([T, S], list(range(18)) + [20, 21], [], [(0, 1)], form="fp32")
+    byts, macs = 8.0 * (2 ** 20 + 2 ** 4 + 2 ** 20), 2.0 ** 22
+    assert ms == pytest.approx(max(byts / 7e12, 8 * macs / 80e12) * 1e3 + 2e-3, rel=1e-12)
+    assert nb == 0 and arena >= 8 * 2 ** 20
+    A, B = list(range(24)), list(range(14, 38))
+    O = list(range(14)) + list(range(24, 38))
+    macs = 2.0 ** 38
+    f32, _, _ = tn.estimate_tree_ms([A, B], O, [], [(0, 1)], form="fp32")
+    assert f32 == pytest.approx(8 * macs / 80e12 * 1e3 + 2e-3, rel=1e-9)
+    for form, fl in (("bf16x3", 24), ("fp16x3", 24), ("fp16s", 8)):
+        t, _, _ = tn.estimate_tree_ms([A, B], O, [], [(0, 1)], form=form)
+        assert fl * macs / 2.25e15 * 1e3 < t < f32, form
+    with pytest.raises(tn.TNError):
+        tn.estimate_tree_ms([A, B], O, [], [(0, 0)], form="bf16x3")  # malformed tree
+
+
+def test_estimate_tree_ms_counts_blocks_and_the_prologue(tn):
+    """Slicing: the per-block body counts once per block and a slice-
+    invariant subtree once in all.  On the 30-qubit network with its 8
+    sliced bonds, a block of 2^8 slices prices below 2^8 blocks of one
+    slice (launch floors, narrower steps), and every block width gives a
+    time at least the sum of the roofline floors of one launch per step."""
+    cfg = make_config(2)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sl, st = tn.find_order(L, O, tn.search_opts(trials=64, n_sliced=8))
+    t8, nb8, a8 = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", batch_log2=8)
+    t0, nb0, a0 = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", batch_log2=0)
+    assert (nb8, nb0) == (8, 0) and a8 > a0
+    assert t8 < t0
+    # the budget picks the block: a budget between the two arenas gives fewer bits
+    tb, nbb, ab = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", arena_budget=(a0 + a8) // 2)
+    assert 0 <= nbb < 8 and ab <= (a0 + a8) // 2
+
+
+def test_roofline_objective_ranks_trees_by_estimated_time(tn):
+    """objective="roofline" keeps the trials with the smallest estimated time
+    (and, as candidates for reconfiguration, the smallest MAC counts) and
+    returns the tree with the smallest estimate: on the 53-qubit 14-cycle
+    network it is no slower, by tn_estimate_tree_ms, than the MAC-ranked
+    tree of the same trials."""
+    cfg = make_config(4)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    est = {}
+    for ob in ("macs", "roofline"):
+        tree, sl, st = tn.find_order(L, O, tn.search_opts(trials=128, log2_cap=30, method="bipartition",
+                                                            objective=ob, rank_form="fp16x3"))
+        assert st["log2_width"] <= 30
+        est[ob] = tn.estimate_tree_ms(L, O, sl, tree, form="fp16x3")[0]
+    assert est["roofline"] <= est["macs"] * 1.0001, est
+    with pytest.raises(tn.TNError):
+        tn.find_order(L, O, tn.search_opts(trials=2, objective=2))
