@@ -1155,7 +1155,6 @@ int plan_host_setup(tn_plan &P, int n_tensors, const int32_t *ranks, const int32
     if (n_sliced < 0 || n_sliced > 62 || (n_sliced > 0 && !sliced_labels)) return fail(TN_ERR_ARG, "bad sliced labels");
     if (n_steps != n_tensors - 1 || (n_steps > 0 && !tree)) return fail(TN_ERR_ARG, "tree must have n_tensors - 1 steps");
     P.n_tensors = n_tensors;
-
     P.n_open = n_open;
     P.n_sliced = n_sliced;
     P.open.assign(open_labels, open_labels + n_open);
