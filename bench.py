@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -190,6 +191,22 @@ def workload(name="rect5x6", seed_offset=0):
         cfg["circuit"] = tn_inputs.sycamore_circuit(c["layout"], c["rows"], c["cols"], c["cycles"],
                                                     c["seed"] + seed_offset)
     return cfg
+
+
+def step_roofline(tn, L, O, sliced, tree, form, slices_per_batch, n_slices, measured_ms):
+    """One timed step against its compiled plan's roofline time: the plan's
+    ops priced on the host by tn_estimate_tree_ms (nominal peaks: 7 TB/s HBM,
+    80 TFLOP/s FP32, 2.25 PFLOP/s tensor, 1.125 for TF32x3, + 2 us a launch)
+    at the plan's own block width, the prologue once and the body once per
+    block of the step.  Never raises: an error becomes the entry."""
+    try:
+        nb = int(round(math.log2(slices_per_batch)))
+        e = tn.estimate_tree_ms(L, O, sliced, tree, form=form, batch_log2=nb)
+        est = e.prologue_ms + (n_slices / float(1 << e.batch_log2)) * e.block_ms
+        return {"estimate_ms": est, "measured_ms": measured_ms, "frac": est / measured_ms,
+                "peaks": "nominal (7 TB/s, 80 / 2250 / 1125 TFLOP/s) + 2 us per launch"}
+    except Exception as exc:  # the bench line must not depend on this extra key
+        return {"error": str(exc)}
 
 
 def cpu_oracle_rate(cfg, sliced, budget_s=15.0, max_slices=4):
@@ -465,6 +482,8 @@ def run_native(args):
         roof["roofline_time_frac"] = d["t_roof"] / d["ms"] if d["ms"] else None
         res["roofline"] = roof
         res["kernel_time_share"] = {k: v["ms"] / total_ms for k, v in by_kind.items()}
+        res["step_roofline"] = step_roofline(tn, L, O, sliced, tree, form, stats["slices_per_batch"], n_slices,
+                                             per_step)
         # end to end through the C-ABI with host buffers
         if big:
             res["e2e"] = None
@@ -533,9 +552,11 @@ def run_native(args):
         "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
                        "rel_l2_err_vs_fp64_oracle": results[f]["rel_l2_err"],
                        "ms_per_step": results[f]["ms_per_step"], "roofline": results[f]["roofline"],
-                       "kernel_time_share": results[f]["kernel_time_share"]}
+                       "kernel_time_share": results[f]["kernel_time_share"],
+                       "step_roofline": results[f].get("step_roofline")}
                       if "error" not in results[f] else results[f]) for f in forms},
         "roofline": r["roofline"],
+        "step_roofline": r.get("step_roofline"),
         "cpu_baseline": cpu,
         "e2e": r["e2e"],
         "clocks": r["clocks"],

@@ -302,13 +302,15 @@ int tn_find_order(int n_tensors, const int32_t *ranks, const int32_t *labels, in
  * (capped at n_sliced); batch_log2 < 0 takes the largest block whose arena
  * and leaves fit arena_budget bytes (<= 0: 160 GiB), as tn_plan_create
  * sizes it.  Network, sliced labels and tree as for tn_plan_create (same
- * checks, TN_ERR_ARG).  *out_ms: milliseconds for all 2^n_sliced slices;
- * out_batch_log2 / out_arena (may be NULL): the block width and arena bytes.
+ * checks, TN_ERR_ARG).  *out_ms: milliseconds for all 2^n_sliced slices,
+ * = *out_prologue_ms + 2^(n_sliced - *out_batch_log2) * *out_block_ms;
+ * out_batch_log2, out_arena (arena bytes), out_prologue_ms (the
+ * slice-invariant ops) and out_block_ms (one block) may be NULL.
  */
 int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                         const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
                         const int32_t *tree, tn_form form, int batch_log2, int64_t arena_budget, double *out_ms,
-                        int *out_batch_log2, int64_t *out_arena);
+                        int *out_batch_log2, int64_t *out_arena, double *out_prologue_ms, double *out_block_ms);
 
 /*
  * Branch merging (appendix, "Details of simulations"): in a tree, a large

@@ -7,6 +7,7 @@ ImportError, never a silent fallback.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import os
 
@@ -227,24 +228,27 @@ def find_order(labels, open_labels, opts=None, max_sliced=64):
     return steps, [int(x) for x in sl[:nsl.value]], stats
 
 
+TreeEstimate = collections.namedtuple("TreeEstimate", "ms batch_log2 arena prologue_ms block_ms")
+
+
 def estimate_tree_ms(labels, open_labels, sliced_labels, tree, form="fp32", batch_log2=-1, arena_budget=0):
-    """tn_estimate_tree_ms: (ms for all slices, block width in sliced bits,
-    arena bytes) of the plan the tree compiles to, every op at its roofline
-    time (host only, no GPU needed)."""
+    """tn_estimate_tree_ms: TreeEstimate(ms for all slices, block width in
+    sliced bits, arena bytes, prologue ms, ms per block) of the plan the tree
+    compiles to, every op at its roofline time (host only, no GPU needed)."""
     ranks = np.asarray([len(l) for l in labels], dtype=np.int32)
     flat = np.asarray([x for l in labels for x in l] or [0], dtype=np.int32)
     ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
     sl = np.asarray(list(sliced_labels) or [0], dtype=np.int32)
     tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
     f = FORMS[form] if isinstance(form, str) else int(form)
-    ms = ctypes.c_double(0)
+    ms, pro, blk = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
     nb = ctypes.c_int(0)
     arena = ctypes.c_int64(0)
     _check(_lib.tn_estimate_tree_ms(len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol),
                                     len(sliced_labels), _ptr(sl), len(tree), _ptr(tr), f, int(batch_log2),
                                     ctypes.c_int64(int(arena_budget)), ctypes.byref(ms), ctypes.byref(nb),
-                                    ctypes.byref(arena)), "tn_estimate_tree_ms")
-    return ms.value, nb.value, arena.value
+                                    ctypes.byref(arena), ctypes.byref(pro), ctypes.byref(blk)), "tn_estimate_tree_ms")
+    return TreeEstimate(ms.value, nb.value, arena.value, pro.value, blk.value)
 
 
 def merge_branches(labels, open_labels, sliced_labels, tree, max_small_rank=0):

@@ -1089,7 +1089,7 @@ namespace tn {
 // n_sliced), else the largest whose arena and leaves fit `budget` bytes, as
 // tn_plan_create chooses it (0 when none fits).  Host only.
 int plan_roofline(tn_plan &P, int batch_log2, double budget, int64_t leaf_bytes, double &ms, int &nb_out,
-                  int64_t &arena_out) {
+                  int64_t &arena_out, double *pro_out = nullptr, double *body_out = nullptr) {
     int nb = batch_log2 >= 0 ? std::min(batch_log2, P.n_sliced) : P.n_sliced;
     int64_t arena = compile(P, nb);
     if (arena < 0) return TN_ERR_ARG;
@@ -1112,6 +1112,8 @@ int plan_roofline(tn_plan &P, int batch_log2, double budget, int64_t leaf_bytes,
     ms = pro + std::exp2((double)(P.n_sliced - nb)) * body;
     nb_out = nb;
     arena_out = arena;
+    if (pro_out) *pro_out = pro;
+    if (body_out) *body_out = body;
     return TN_OK;
 }
 
@@ -1898,7 +1900,8 @@ extern "C" int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bit
 extern "C" int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                                    const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels,
                                    int n_steps, const int32_t *tree, tn_form form, int batch_log2,
-                                   int64_t arena_budget, double *out_ms, int *out_batch_log2, int64_t *out_arena) {
+                                   int64_t arena_budget, double *out_ms, int *out_batch_log2, int64_t *out_arena,
+                                   double *out_prologue_ms, double *out_block_ms) {
     if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
     if (!out_ms) return fail(TN_ERR_ARG, "out_ms is NULL");
     tn_plan P;
@@ -1912,7 +1915,7 @@ extern "C" int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const in
     double ms = 0;
     int nb = 0;
     int64_t arena = 0;
-    rc = plan_roofline(P, batch_log2, budget, total * 8, ms, nb, arena);
+    rc = plan_roofline(P, batch_log2, budget, total * 8, ms, nb, arena, out_prologue_ms, out_block_ms);
     if (rc) return rc;
     *out_ms = ms;
     if (out_batch_log2) *out_batch_log2 = nb;

@@ -347,17 +347,17 @@ def test_estimate_tree_ms_prices_each_op_at_its_roofline(tn):
     the tensor-core forms between 24 (8 for FP16S) tensor flops per MAC at
     2.25 PFLOP/s and the FP32 time."""
     T, S = list(range(20)), [18, 19, 20, 21]
-    ms, nb, arena = tn.estimate_tree_ms([T, S], list(range(18)) + [20, 21], [], [(0, 1)], form="fp32")
+    ms, nb, arena, pro, blk = tn.estimate_tree_ms([T, S], list(range(18)) + [20, 21], [], [(0, 1)], form="fp32")
     byts, macs = 8.0 * (2 ** 20 + 2 ** 4 + 2 ** 20), 2.0 ** 22
     assert ms == pytest.approx(max(byts / 7e12, 8 * macs / 80e12) * 1e3 + 2e-3, rel=1e-12)
-    assert nb == 0 and arena >= 8 * 2 ** 20
+    assert nb == 0 and arena >= 8 * 2 ** 20 and pro + blk == pytest.approx(ms, rel=1e-12)
     A, B = list(range(24)), list(range(14, 38))
     O = list(range(14)) + list(range(24, 38))
     macs = 2.0 ** 38
-    f32, _, _ = tn.estimate_tree_ms([A, B], O, [], [(0, 1)], form="fp32")
+    f32 = tn.estimate_tree_ms([A, B], O, [], [(0, 1)], form="fp32").ms
     assert f32 == pytest.approx(8 * macs / 80e12 * 1e3 + 2e-3, rel=1e-9)
     for form, fl in (("bf16x3", 24), ("fp16x3", 24), ("fp16s", 8)):
-        t, _, _ = tn.estimate_tree_ms([A, B], O, [], [(0, 1)], form=form)
+        t = tn.estimate_tree_ms([A, B], O, [], [(0, 1)], form=form).ms
         assert fl * macs / 2.25e15 * 1e3 < t < f32, form
     with pytest.raises(tn.TNError):
         tn.estimate_tree_ms([A, B], O, [], [(0, 0)], form="bf16x3")  # malformed tree
@@ -372,12 +372,13 @@ def test_estimate_tree_ms_counts_blocks_and_the_prologue(tn):
     cfg = make_config(2)
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
     tree, sl, st = tn.find_order(L, O, tn.search_opts(trials=64, n_sliced=8))
-    t8, nb8, a8 = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", batch_log2=8)
-    t0, nb0, a0 = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", batch_log2=0)
+    t8, nb8, a8, p8, b8 = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", batch_log2=8)
+    t0, nb0, a0, p0, b0 = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", batch_log2=0)
     assert (nb8, nb0) == (8, 0) and a8 > a0
     assert t8 < t0
+    assert t8 == pytest.approx(p8 + b8, rel=1e-12) and t0 == pytest.approx(p0 + 256 * b0, rel=1e-12)
     # the budget picks the block: a budget between the two arenas gives fewer bits
-    tb, nbb, ab = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", arena_budget=(a0 + a8) // 2)
+    tb, nbb, ab, _, _ = tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3", arena_budget=(a0 + a8) // 2)
     assert 0 <= nbb < 8 and ab <= (a0 + a8) // 2
 
 
