@@ -382,7 +382,9 @@ def run_native(args):
     n_qubits = cfg["circuit"].n_qubits
     n_open = len(cfg["open_qubits"])
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**wl["search"], method=args.search_method))
+    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**wl["search"], method=args.search_method,
+                                                          objective=args.objective,
+                                                          rank_form="bf16x3" if args.form == "all" else args.form))
     if args.branch_merge:
         tree, _ = tn.merge_branches(L, O, sliced, tree)
     n_total = 1 << len(sliced)
@@ -547,6 +549,7 @@ def run_native(args):
                    "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
                    "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],
                    "arena_bytes": r["plan"]["arena_bytes"], "order_search": args.search_method,
+                   "order_objective": args.objective,
                    "branch_merge": bool(args.branch_merge)},
         "complex_tflops": r["complex_tflops"],
         "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
@@ -581,6 +584,9 @@ def main():
     ap.add_argument("--workload", default="rect5x6", choices=sorted(WORKLOADS) + ["batch256"])
     ap.add_argument("--search-method", default="greedy", choices=["greedy", "bipartition", "mixed"],
                     help="order-search trials: randomised greedy (default), hierarchical bipartition, or both")
+    ap.add_argument("--objective", default="macs", choices=["macs", "roofline"],
+                    help="rank the search's trees by total MACs (default) or by the roofline time of their "
+                         "compiled plan (tn_estimate_tree_ms) for --form (bf16x3 with --form all)")
     ap.add_argument("--branch-merge", action="store_true",
                     help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
