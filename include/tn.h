@@ -348,6 +348,30 @@ int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, const int32_t *
                             int max_sliced, int32_t *out_sliced_head, int *out_n_sliced_head, double *stats);
 
 /*
+ * Open qubits chosen from the first cut ("Big-head simulation" section: the
+ * open qubits are those whose last tensors fall in G_tail, a small region
+ * behind a narrow cut; the appendix tries first cuts until the contraction's
+ * cost is acceptable).  In the circuit's network with every qubit open
+ * (gates absorbed as tn_circuit_network builds it), a connected tail grows
+ * from each tensor holding a qubit's last wire segment, one neighbouring
+ * tensor at a time, always the one leaving the smallest cut among those that
+ * keep at most n_open qubit ends in the tail (ties: more qubit ends, then the
+ * lower tensor id, or in 15 more growths per seed a random one from a fixed
+ * SplitMix64 stream), up to half the network.  Every tail holding exactly
+ * n_open ends is a candidate.  Without opts the smallest cut wins; with opts
+ * the order search (opts as for tn_find_order) prices the network of each of
+ * the 8 smallest-cut candidates and the cheapest wins.  Writes the open
+ * qubits (n_open, increasing), the tail's tensor ids in the all-open network
+ * (out_tail, room for its tensor count; may be NULL), their count, the cut
+ * (bonds between tail and head) and *out_log2_cost (log2 total MACs of the
+ * winner's search, -1 without opts; may be NULL).  TN_ERR_ARG unless
+ * 1 <= n_open < n_qubits, or when no connected tail holds exactly n_open
+ * ends.
+ */
+int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, const tn_search_opts *opts, int32_t *out_open_qubits,
+                          int32_t *out_tail, int *out_n_tail, int *out_cut, double *out_log2_cost);
+
+/*
  * Two-stage big-head contraction ("Big-head simulation" section): the
  * tree's last step must join the head (no open label) and the tail (every
  * open label); the labels they share are the first cut C.  Stage 1

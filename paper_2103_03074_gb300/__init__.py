@@ -100,7 +100,7 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
             "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
-            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms"]
+            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -266,6 +266,23 @@ def merge_branches(labels, open_labels, sliced_labels, tree, max_small_rank=0):
                                   _ptr(st)), "tn_merge_branches")
     steps = [(int(out[2 * t]), int(out[2 * t + 1])) for t in range(len(tree))]
     return steps, dict(rewrites=int(st[0]), log2_macs_before=float(st[1]), log2_macs_after=float(st[2]))
+
+
+def choose_open_qubits(circuit, n_open, opts=None):
+    """tn_choose_open_qubits: (open qubits, tail tensor ids in the all-open
+    network, cut, log2 cost or -1) for the open set behind a small first cut
+    (with opts: the cheapest to contract of the 8 smallest cuts)."""
+    c, keep = marshal_circuit(circuit)
+    n_max = len(circuit.gates) + 2 * circuit.n_qubits + 1
+    oq = np.zeros(n_open, dtype=np.int32)
+    tail = np.zeros(n_max, dtype=np.int32)
+    nt = ctypes.c_int(0)
+    cut = ctypes.c_int(0)
+    cost = ctypes.c_double(0)
+    _check(_lib.tn_choose_open_qubits(ctypes.byref(c), int(n_open), ctypes.byref(opts) if opts is not None else None,
+                                      _ptr(oq), _ptr(tail), ctypes.byref(nt), ctypes.byref(cut),
+                                      ctypes.byref(cost)), "tn_choose_open_qubits")
+    return [int(x) for x in oq], [int(x) for x in tail[:nt.value]], cut.value, cost.value
 
 
 def find_order_head_tail(labels, open_labels, tail_max=0, opts=None, max_sliced=64):

@@ -378,3 +378,136 @@ extern "C" int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, cons
     }
     return TN_OK;
 }
+
+extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, const tn_search_opts *opts,
+                                     int32_t *out_open_qubits, int32_t *out_tail, int *out_n_tail, int *out_cut,
+                                     double *out_log2_cost) {
+    if (!circuit || !out_open_qubits || circuit->n_qubits < 2 || n_open < 1 || n_open >= circuit->n_qubits)
+        return fail(TN_ERR_ARG, "tn_choose_open_qubits: need a circuit and 1 <= n_open < n_qubits");
+    const int nq = circuit->n_qubits;
+    std::vector<int32_t> all(nq);
+    for (int q = 0; q < nq; q++) all[q] = q;
+    Network net;
+    int rc = build_circuit_network(circuit, nullptr, nq, all.data(), net);
+    if (rc) return rc;
+    const int n = (int)net.tensors.size();
+    std::unordered_map<int32_t, std::vector<int>> holders;
+    for (int i = 0; i < n; i++)
+        for (int32_t x : net.tensors[i].labels) holders[x].push_back(i);
+    // the tensor holding each qubit's last wire segment (an open leg here)
+    std::vector<std::vector<int>> qubits_of(n);
+    for (int q = 0; q < nq; q++) qubits_of[holders[net.open[q]][0]].push_back(q);
+    // bonds between tensors (one per shared label)
+    std::vector<std::vector<int>> nb(n);
+    for (const auto &kv : holders)
+        if (kv.second.size() == 2 && kv.second[0] != kv.second[1]) {
+            nb[kv.second[0]].push_back(kv.second[1]);
+            nb[kv.second[1]].push_back(kv.second[0]);
+        }
+    // candidate tails: (cut, open qubits) -> the tail that reached it first
+    struct Cand { int cut; std::vector<int32_t> qubits; std::vector<char> in; };
+    std::vector<Cand> cands;
+    auto record = [&](int cut, const std::vector<char> &in) {
+        std::vector<int32_t> qs;
+        for (int q = 0; q < nq; q++)
+            if (in[holders[net.open[q]][0]]) qs.push_back(q);
+        for (auto &c : cands)
+            if (c.qubits == qs) {
+                if (cut < c.cut) { c.cut = cut; c.in = in; }
+                return;
+            }
+        cands.push_back({cut, qs, in});
+    };
+    std::vector<char> in(n);
+    std::vector<int> conn(n);
+    // equal cuts are frequent and the order they are taken in steers the
+    // growth: every seed tensor grows kRuns times, the first with ties to
+    // the lower index, the others to a random one (SplitMix64, fixed seed)
+    constexpr int kRuns = 16;
+    uint64_t rs = 0x2103030740ull;
+    auto next_u64 = [&rs]() {
+        rs += 0x9E3779B97F4A7C15ull;
+        uint64_t z = rs;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int run = 0; run < n * kRuns; run++) {
+        const int seed = run / kRuns;
+        const bool random_ties = run % kRuns != 0;
+        if (qubits_of[seed].empty() || (int)qubits_of[seed].size() > n_open) continue;
+        std::fill(in.begin(), in.end(), 0);
+        std::fill(conn.begin(), conn.end(), 0);
+        int v = seed, cut = 0, n_in = 0, n_q = 0;
+        for (;;) {
+            // add v to the tail
+            in[v] = 1;
+            n_in++;
+            n_q += (int)qubits_of[v].size();
+            cut += (int)nb[v].size() - 2 * conn[v];
+            for (int u : nb[v]) conn[u]++;
+            if (n_q == n_open) record(cut, in);
+            if (n_in >= n / 2) break;
+            // the neighbour leaving the smallest cut without exceeding n_open
+            // open qubits (ties: more open qubits, then the lower index or a
+            // random one); the tail stays connected, which keeps the open
+            // qubits together (a tail of scattered last-layer tensors reaches
+            // the same cut for any open set)
+            int pick = -1, pick_cut = 0, pick_q = 0, ties = 0;
+            for (int u = 0; u < n; u++) {
+                if (in[u] || conn[u] == 0) continue;
+                const int uq = (int)qubits_of[u].size();
+                if (n_q + uq > n_open) continue;
+                const int c = cut + (int)nb[u].size() - 2 * conn[u];
+                if (pick < 0 || c < pick_cut || (c == pick_cut && uq > pick_q)) {
+                    pick = u;
+                    pick_cut = c;
+                    pick_q = uq;
+                    ties = 1;
+                } else if (random_ties && c == pick_cut && uq == pick_q && next_u64() % (uint64_t)(++ties) == 0) {
+                    pick = u;
+                }
+            }
+            if (pick < 0) break;
+            v = pick;
+        }
+    }
+    if (cands.empty()) return fail(TN_ERR_ARG, "tn_choose_open_qubits: no connected tail holds exactly n_open qubit ends");
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.cut < b.cut; });
+    // with search options: of the kPick smallest cuts, the open set whose
+    // network the order search contracts most cheaply (the paper tries
+    // first cuts until the contraction's complexity is acceptable)
+    constexpr int kPick = 8;
+    int best = 0;
+    double best_cost = -1.0;
+    if (opts) {
+        const int m = std::min<int>(kPick, (int)cands.size());
+        for (int i = 0; i < m; i++) {
+            Network sub;
+            std::vector<uint8_t> zeros(nq, 0);
+            rc = build_circuit_network(circuit, zeros.data(), n_open, cands[i].qubits.data(), sub);
+            if (rc) return rc;
+            std::vector<std::vector<int32_t>> labs;
+            for (const auto &t : sub.tensors) labs.push_back(t.labels);
+            SearchResult r;
+            rc = search_order(labs, sub.open, *opts, r);
+            if (rc) return rc;
+            if (best_cost < 0 || r.log2_total < best_cost) {
+                best_cost = r.log2_total;
+                best = i;
+            }
+        }
+    }
+    const Cand &c = cands[best];
+    for (int k = 0; k < n_open; k++) out_open_qubits[k] = c.qubits[k];
+    int nt = 0;
+    for (int i = 0; i < n; i++)
+        if (c.in[i]) {
+            if (out_tail) out_tail[nt] = i;
+            nt++;
+        }
+    if (out_n_tail) *out_n_tail = nt;
+    if (out_cut) *out_cut = c.cut;
+    if (out_log2_cost) *out_log2_cost = best_cost;
+    return TN_OK;
+}

@@ -842,7 +842,9 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     };
     // every thread keeps its kk best, so the union holds the global kk best
     // whatever the thread count (the search is deterministic in the seed)
-    const int kk = std::max(k, 4);
+    // bipartition trees change more under reconfiguration, so more of them
+    // are reconfigured (greedy keeps its measured 4)
+    const int kk = std::max(k, opts.method == 0 ? 4 : 16);
     std::vector<std::vector<Cand>> keep(threads), keep_m(threads);
     std::atomic<int> next{0};
     const auto insert = [&](std::vector<Cand> &mine, Cand &&c) {

@@ -399,3 +399,77 @@ def test_roofline_objective_ranks_trees_by_estimated_time(tn):
     assert est["roofline"] <= est["macs"] * 1.0001, est
     with pytest.raises(tn.TNError):
         tn.find_order(L, O, tn.search_opts(trials=2, objective=2))
+
+
+def _best_connected_tail(L, O, nq, k):
+    """Brute force: the smallest cut over connected tensor sets of at most
+    half the network holding exactly k qubit ends (None if there is none)."""
+    h = {}
+    for i, l in enumerate(L):
+        for x in l:
+            h.setdefault(x, []).append(i)
+    ends = {q: h[O[q]][0] for q in range(nq)}
+    n, best = len(L), None
+    for mask in range(1, 1 << n):
+        S = {i for i in range(n) if mask >> i & 1}
+        if len(S) > n // 2 or sum(1 for q in range(nq) if ends[q] in S) != k:
+            continue
+        start = next(iter(S))
+        seen, stack = {start}, [start]
+        while stack:
+            u = stack.pop()
+            for x in L[u]:
+                for w in h[x]:
+                    if w in S and w not in seen:
+                        seen.add(w)
+                        stack.append(w)
+        if seen != S:
+            continue
+        cut = sum(1 for hh in h.values() if len(hh) == 2 and ((hh[0] in S) != (hh[1] in S)))
+        best = cut if best is None else min(best, cut)
+    return best, h, ends
+
+
+@pytest.mark.parametrize("r,c,cyc,seed,k", [(2, 2, 3, 2, 2), (2, 3, 2, 3, 2), (3, 2, 2, 5, 2), (2, 3, 3, 9, 2),
+                                            (3, 3, 3, 10, 3), (2, 4, 2, 11, 4), (3, 3, 2, 12, 2), (2, 5, 2, 15, 4),
+                                            (2, 3, 2, 7, 4)])
+def test_choose_open_qubits_finds_the_best_connected_tail(tn, r, c, cyc, seed, k):
+    """tn_choose_open_qubits ("Big-head simulation": the open qubits are
+    those whose last tensors lie behind the first cut): on circuits small
+    enough to enumerate every tensor set, its tail has the smallest cut of
+    all connected sets with exactly k qubit ends, and what it returns is
+    consistent: the tail is connected, holds the ends of exactly the returned
+    qubits, and cuts the reported number of bonds."""
+    circ = sycamore_circuit("rect", r, c, cyc, seed)
+    nq = circ.n_qubits
+    L, T, O = tn.circuit_network(circ, np.zeros(nq, np.uint8), list(range(nq)))
+    best, h, ends = _best_connected_tail(L, O, nq, k)
+    if best is None:
+        with pytest.raises(tn.TNError):
+            tn.choose_open_qubits(circ, k)
+        return
+    oq, tail, cut, cost = tn.choose_open_qubits(circ, k)
+    assert cut == best and cost == -1
+    S = set(tail)
+    assert oq == sorted(oq) and len(set(oq)) == k
+    assert sorted(q for q in range(nq) if ends[q] in S) == oq
+    assert cut == sum(1 for hh in h.values() if len(hh) == 2 and ((hh[0] in S) != (hh[1] in S)))
+
+
+def test_choose_open_qubits_prices_the_candidates(tn):
+    """With search options the smallest-cut candidates are priced by the
+    order search: the returned cost is that search's cost on the network with
+    the returned open qubits, and no higher than the smallest-cut set's."""
+    cfg = make_config(2)
+    circ = cfg["circuit"]
+    opts = tn.search_opts(trials=16, n_sliced=4)
+    oq0, _, cut0, c0 = tn.choose_open_qubits(circ, 8)
+    oq, tail, cut, cost = tn.choose_open_qubits(circ, 8, opts)
+    assert c0 == -1 and cut >= cut0
+    L, T, O = tn.circuit_network(circ, cfg["fixed_bits"], oq)
+    assert cost == pytest.approx(tn.find_order(L, O, opts)[2]["log2_total"], abs=1e-12)
+    L0, T0, O0 = tn.circuit_network(circ, cfg["fixed_bits"], oq0)
+    assert cost <= tn.find_order(L0, O0, opts)[2]["log2_total"] + 1e-12
+    for bad in (0, circ.n_qubits):
+        with pytest.raises(tn.TNError):
+            tn.choose_open_qubits(circ, bad)
