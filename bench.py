@@ -381,6 +381,11 @@ def run_native(args):
     cfg = workload(args.workload, instance_seed_offset(rank))
     n_qubits = cfg["circuit"].n_qubits
     n_open = len(cfg["open_qubits"])
+    if args.choose_open:
+        # the paper's choice: the open qubits behind a small first cut, the
+        # cheapest to contract of the smallest cuts (tn_choose_open_qubits)
+        cfg["open_qubits"] = tn.choose_open_qubits(
+            cfg["circuit"], n_open, tn.search_opts(**dict(wl["search"], trials=64), method="bipartition"))[0]
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
     tree, sliced, st = tn.find_order(L, O, tn.search_opts(**wl["search"], method=args.search_method,
                                                           objective=args.objective,
@@ -396,7 +401,7 @@ def run_native(args):
     else:
         forms = ["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"]
     golden = None
-    if wl["golden"] and rank == 0 and instance_seed_offset(rank) == 0:
+    if wl["golden"] and rank == 0 and instance_seed_offset(rank) == 0 and not args.choose_open:
         golden = load_golden_amplitudes(wl["golden"])
     stream = torch.cuda.Stream()
     flush = l2_flush_buffer(torch)
@@ -550,6 +555,7 @@ def run_native(args):
                    "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],
                    "arena_bytes": r["plan"]["arena_bytes"], "order_search": args.search_method,
                    "order_objective": args.objective,
+                   "open_qubits": cfg["open_qubits"] if args.choose_open else "fixed (the workload's)",
                    "branch_merge": bool(args.branch_merge)},
         "complex_tflops": r["complex_tflops"],
         "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
@@ -587,6 +593,9 @@ def main():
     ap.add_argument("--objective", default="macs", choices=["macs", "roofline"],
                     help="rank the search's trees by total MACs (default) or by the roofline time of their "
                          "compiled plan (tn_estimate_tree_ms) for --form (bf16x3 with --form all)")
+    ap.add_argument("--choose-open", action="store_true",
+                    help="take the open qubits behind a small first cut (tn_choose_open_qubits) instead of the "
+                         "workload's fixed set; the stored oracle amplitudes then do not apply (no error reported)")
     ap.add_argument("--branch-merge", action="store_true",
                     help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
