@@ -213,6 +213,24 @@ void slice_tree(const Problem &p, const TreeSets &ts, int n_nodes, int n_steps, 
                 }
             }
         }
+        // slicing label l lowers the widest intermediate only when every
+        // widest node holds l (to wmax - 1: the others are narrower
+        // already), so the new width follows from how many widest nodes
+        // hold l
+        std::vector<int> in_widest_cnt(p.L, 0);
+        int n_widest = 0;
+        for (int v = 0; v < n_nodes; v++) {
+            if (wv[v] != wmax) continue;
+            n_widest++;
+            const uint64_t *sv = ts.node.at(v);
+            for (int w = 0; w < W; w++) {
+                uint64_t x = sv[w];
+                while (x) {
+                    in_widest_cnt[w * 64 + __builtin_ctzll(x)]++;
+                    x &= x - 1;
+                }
+            }
+        }
         int best = -1;
         int best_w = 0;
         double best_c = 0;
@@ -220,13 +238,8 @@ void slice_tree(const Problem &p, const TreeSets &ts, int n_nodes, int n_steps, 
             if ((p.open[l >> 6] >> (l & 63)) & 1) continue;
             if ((smask[l >> 6] >> (l & 63)) & 1) continue;
             if (drop[l] <= 0) continue;  // label in no step
-            int nw = 0;
-            bool in_widest = false;
-            for (int v = 0; v < n_nodes; v++) {
-                int has = (ts.node.at(v)[l >> 6] >> (l & 63)) & 1;
-                nw = std::max(nw, wv[v] - has);
-                if (has && wv[v] == wmax) in_widest = true;
-            }
+            const bool in_widest = in_widest_cnt[l] > 0;
+            const int nw = (n_widest > 0 && in_widest_cnt[l] == n_widest) ? wmax - 1 : wmax;
             double c = base - drop[l];
             if (rule == 1) {
                 if (!in_widest) continue;
