@@ -313,6 +313,17 @@ int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labe
                         int *out_batch_log2, int64_t *out_arena, double *out_prologue_ms, double *out_block_ms);
 
 /*
+ * The plan tn_estimate_tree_ms prices, as text: one line per compiled op as
+ * tn_plan_describe writes it (phase, step, kind, shape, kernel variant,
+ * plan-time notes), each with its roofline_ms; no CUDA call.  Arguments as
+ * for tn_estimate_tree_ms.  Writes up to cap - 1 characters and a NUL to out
+ * (cap 0: out may be NULL) and returns the full length, or a negative error.
+ */
+int tn_describe_tree(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                     const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
+                     const int32_t *tree, tn_form form, int batch_log2, int64_t arena_budget, char *out, int cap);
+
+/*
  * Branch merging (appendix, "Details of simulations"): in a tree, a large
  * tensor X met by two small ones in turn, ((X a) b), is rewritten as
  * (X (a b)) when a, b and their product have rank <= max_small_rank (0: 12)

@@ -100,7 +100,7 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
             "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
-            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits"]
+            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits", "tn_describe_tree"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -249,6 +249,25 @@ def estimate_tree_ms(labels, open_labels, sliced_labels, tree, form="fp32", batc
                                     ctypes.c_int64(int(arena_budget)), ctypes.byref(ms), ctypes.byref(nb),
                                     ctypes.byref(arena), ctypes.byref(pro), ctypes.byref(blk)), "tn_estimate_tree_ms")
     return TreeEstimate(ms.value, nb.value, arena.value, pro.value, blk.value)
+
+
+def describe_tree(labels, open_labels, sliced_labels, tree, form="fp32", batch_log2=-1, arena_budget=0):
+    """tn_describe_tree: the ops the tree's plan compiles to (host only), one
+    line each with its roofline_ms."""
+    ranks = np.asarray([len(l) for l in labels], dtype=np.int32)
+    flat = np.asarray([x for l in labels for x in l] or [0], dtype=np.int32)
+    ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
+    sl = np.asarray(list(sliced_labels) or [0], dtype=np.int32)
+    tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    args = (len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol), len(sliced_labels), _ptr(sl),
+            len(tree), _ptr(tr), f, int(batch_log2), ctypes.c_int64(int(arena_budget)))
+    n = _lib.tn_describe_tree(*args, None, 0)
+    if n < 0:
+        _check(n, "tn_describe_tree")
+    buf = ctypes.create_string_buffer(n + 1)
+    _check(min(0, _lib.tn_describe_tree(*args, buf, n + 1)), "tn_describe_tree")
+    return buf.value.decode()
 
 
 def merge_branches(labels, open_labels, sliced_labels, tree, max_small_rank=0):

@@ -1775,8 +1775,11 @@ int plan_load_leaf_c128(tn_plan_t P, int leaf, const double *d_src, cudaStream_t
 }
 }  // namespace tn
 
-extern "C" int tn_plan_describe(tn_plan_t P, char *out, int cap) {
-    if (!P || cap < 0 || (cap > 0 && !out)) return fail(TN_ERR_ARG, "bad arguments");
+namespace tn {
+
+// One line per compiled op (kind, shape, kernel variant, plan-time notes);
+// with with_roofline, each line also gives the op's roofline time.
+std::string describe_ops(const tn_plan &P, bool with_roofline) {
     std::string txt;
     char line[512];
     auto put = [&](const char *phase, const Op &op) {
@@ -1808,17 +1811,32 @@ extern "C" int tn_plan_describe(tn_plan_t P, char *out, int cap) {
             break;
         }
         txt += line;
+        if (with_roofline) {
+            std::snprintf(line, sizeof line, " roofline_ms=%.6g", roofline_ms(op, P.form));
+            txt += line;
+        }
         if (!op.note.empty()) txt += " (" + op.note + ")";
         txt += "\n";
     };
-    for (const auto &op : P->prologue) put("prologue", op);
-    for (const auto &op : P->batch) put("batch", op);
+    for (const auto &op : P.prologue) put("prologue", op);
+    for (const auto &op : P.batch) put("batch", op);
+    return txt;
+}
+
+int copy_text(const std::string &txt, char *out, int cap) {
     if (cap > 0) {
         const size_t n = std::min(txt.size(), (size_t)cap - 1);
         std::memcpy(out, txt.data(), n);
         out[n] = 0;
     }
     return (int)txt.size();
+}
+
+}  // namespace tn
+
+extern "C" int tn_plan_describe(tn_plan_t P, char *out, int cap) {
+    if (!P || cap < 0 || (cap > 0 && !out)) return fail(TN_ERR_ARG, "bad arguments");
+    return copy_text(describe_ops(*P, false), out, cap);
 }
 
 extern "C" int tn_plan_stats(tn_plan_t P, double *out) {
@@ -1921,4 +1939,26 @@ extern "C" int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const in
     if (out_batch_log2) *out_batch_log2 = nb;
     if (out_arena) *out_arena = arena;
     return TN_OK;
+}
+
+extern "C" int tn_describe_tree(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                                const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
+                                const int32_t *tree, tn_form form, int batch_log2, int64_t arena_budget, char *out,
+                                int cap) {
+    if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
+    if (cap < 0 || (cap > 0 && !out)) return fail(TN_ERR_ARG, "bad output buffer");
+    tn_plan P;
+    P.form = form;
+    P.opts.batch_log2 = -1;
+    int64_t total = 0;
+    int rc = plan_host_setup(P, n_tensors, ranks, labels, 0, nullptr, n_open, open_labels, n_sliced, sliced_labels,
+                             n_steps, tree, &total);
+    if (rc) return rc;
+    const double budget = arena_budget > 0 ? (double)arena_budget : kNominalArenaBytes;
+    double ms = 0;
+    int nb = 0;
+    int64_t arena = 0;
+    rc = plan_roofline(P, batch_log2, budget, total * 8, ms, nb, arena);
+    if (rc) return rc;
+    return copy_text(describe_ops(P, true), out, cap);
 }

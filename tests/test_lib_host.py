@@ -473,3 +473,22 @@ def test_choose_open_qubits_prices_the_candidates(tn):
     for bad in (0, circ.n_qubits):
         with pytest.raises(tn.TNError):
             tn.choose_open_qubits(circ, bad)
+
+
+def test_describe_tree_lists_the_priced_ops(tn):
+    """tn_describe_tree (host only) lists the ops of the plan that
+    tn_estimate_tree_ms prices: the prologue lines' roofline times add up to
+    its prologue time and the batch lines' to its block time; a tensor-core
+    form lists tensor-core GEMMs, the FP32 form CUDA-core ones."""
+    import re as _re
+    cfg = make_config(2)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sl, _ = tn.find_order(L, O, tn.search_opts(trials=64, n_sliced=8))
+    for form in ("bf16x3", "fp32"):
+        txt = tn.describe_tree(L, O, sl, tree, form=form, batch_log2=8)
+        e = tn.estimate_tree_ms(L, O, sl, tree, form=form, batch_log2=8)
+        pro = sum(float(m) for m in _re.findall(r"^prologue .*roofline_ms=([0-9.e+-]+)", txt, _re.M))
+        body = sum(float(m) for m in _re.findall(r"^batch .*roofline_ms=([0-9.e+-]+)", txt, _re.M))
+        assert pro == pytest.approx(e.prologue_ms, rel=1e-4) and body == pytest.approx(e.block_ms, rel=1e-4)
+        gemms = [l for l in txt.splitlines() if " gemm " in l]
+        assert gemms and all(("tensor-core" in l) == (form != "fp32") for l in gemms)
