@@ -301,16 +301,18 @@ int tn_find_order(int n_tensors, const int32_t *ranks, const int32_t *labels, in
  * the per-block body once per block.  The block holds 2^batch_log2 slices
  * (capped at n_sliced); batch_log2 < 0 takes the largest block whose arena
  * and leaves fit arena_budget bytes (<= 0: 160 GiB), as tn_plan_create
- * sizes it.  Network, sliced labels and tree as for tn_plan_create (same
- * checks, TN_ERR_ARG).  *out_ms: milliseconds for all 2^n_sliced slices,
+ * sizes it.  Network, sliced labels, tree and opts (plan options, may be
+ * NULL; their batch_log2 is ignored) as for tn_plan_create (same checks,
+ * TN_ERR_ARG).  *out_ms: milliseconds for all 2^n_sliced slices,
  * = *out_prologue_ms + 2^(n_sliced - *out_batch_log2) * *out_block_ms;
  * out_batch_log2, out_arena (arena bytes), out_prologue_ms (the
  * slice-invariant ops) and out_block_ms (one block) may be NULL.
  */
 int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                         const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
-                        const int32_t *tree, tn_form form, int batch_log2, int64_t arena_budget, double *out_ms,
-                        int *out_batch_log2, int64_t *out_arena, double *out_prologue_ms, double *out_block_ms);
+                        const int32_t *tree, tn_form form, const tn_plan_opts *opts, int batch_log2,
+                        int64_t arena_budget, double *out_ms, int *out_batch_log2, int64_t *out_arena,
+                        double *out_prologue_ms, double *out_block_ms);
 
 /*
  * The plan tn_estimate_tree_ms prices, as text: one line per compiled op as
@@ -321,7 +323,8 @@ int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labe
  */
 int tn_describe_tree(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                      const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
-                     const int32_t *tree, tn_form form, int batch_log2, int64_t arena_budget, char *out, int cap);
+                     const int32_t *tree, tn_form form, const tn_plan_opts *opts, int batch_log2,
+                     int64_t arena_budget, char *out, int cap);
 
 /*
  * Branch merging (appendix, "Details of simulations"): in a tree, a large

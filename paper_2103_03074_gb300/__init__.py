@@ -231,7 +231,8 @@ def find_order(labels, open_labels, opts=None, max_sliced=64):
 TreeEstimate = collections.namedtuple("TreeEstimate", "ms batch_log2 arena prologue_ms block_ms")
 
 
-def estimate_tree_ms(labels, open_labels, sliced_labels, tree, form="fp32", batch_log2=-1, arena_budget=0):
+def estimate_tree_ms(labels, open_labels, sliced_labels, tree, form="fp32", batch_log2=-1, arena_budget=0,
+                     opts=None):
     """tn_estimate_tree_ms: TreeEstimate(ms for all slices, block width in
     sliced bits, arena bytes, prologue ms, ms per block) of the plan the tree
     compiles to, every op at its roofline time (host only, no GPU needed)."""
@@ -245,13 +246,15 @@ def estimate_tree_ms(labels, open_labels, sliced_labels, tree, form="fp32", batc
     nb = ctypes.c_int(0)
     arena = ctypes.c_int64(0)
     _check(_lib.tn_estimate_tree_ms(len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol),
-                                    len(sliced_labels), _ptr(sl), len(tree), _ptr(tr), f, int(batch_log2),
+                                    len(sliced_labels), _ptr(sl), len(tree), _ptr(tr), f,
+                                    ctypes.byref(opts) if opts is not None else None, int(batch_log2),
                                     ctypes.c_int64(int(arena_budget)), ctypes.byref(ms), ctypes.byref(nb),
                                     ctypes.byref(arena), ctypes.byref(pro), ctypes.byref(blk)), "tn_estimate_tree_ms")
     return TreeEstimate(ms.value, nb.value, arena.value, pro.value, blk.value)
 
 
-def describe_tree(labels, open_labels, sliced_labels, tree, form="fp32", batch_log2=-1, arena_budget=0):
+def describe_tree(labels, open_labels, sliced_labels, tree, form="fp32", batch_log2=-1, arena_budget=0,
+                  opts=None):
     """tn_describe_tree: the ops the tree's plan compiles to (host only), one
     line each with its roofline_ms."""
     ranks = np.asarray([len(l) for l in labels], dtype=np.int32)
@@ -261,7 +264,8 @@ def describe_tree(labels, open_labels, sliced_labels, tree, form="fp32", batch_l
     tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
     f = FORMS[form] if isinstance(form, str) else int(form)
     args = (len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol), len(sliced_labels), _ptr(sl),
-            len(tree), _ptr(tr), f, int(batch_log2), ctypes.c_int64(int(arena_budget)))
+            len(tree), _ptr(tr), f, ctypes.byref(opts) if opts is not None else None, int(batch_log2),
+            ctypes.c_int64(int(arena_budget)))
     n = _lib.tn_describe_tree(*args, None, 0)
     if n < 0:
         _check(n, "tn_describe_tree")

@@ -1917,13 +1917,14 @@ extern "C" int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bit
 
 extern "C" int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                                    const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels,
-                                   int n_steps, const int32_t *tree, tn_form form, int batch_log2,
-                                   int64_t arena_budget, double *out_ms, int *out_batch_log2, int64_t *out_arena,
-                                   double *out_prologue_ms, double *out_block_ms) {
+                                   int n_steps, const int32_t *tree, tn_form form, const tn_plan_opts *opts,
+                                   int batch_log2, int64_t arena_budget, double *out_ms, int *out_batch_log2,
+                                   int64_t *out_arena, double *out_prologue_ms, double *out_block_ms) {
     if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
     if (!out_ms) return fail(TN_ERR_ARG, "out_ms is NULL");
     tn_plan P;
     P.form = form;
+    if (opts) P.opts = *opts;
     P.opts.batch_log2 = -1;
     int64_t total = 0;
     int rc = plan_host_setup(P, n_tensors, ranks, labels, 0, nullptr, n_open, open_labels, n_sliced, sliced_labels,
@@ -1943,12 +1944,13 @@ extern "C" int tn_estimate_tree_ms(int n_tensors, const int32_t *ranks, const in
 
 extern "C" int tn_describe_tree(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
                                 const int32_t *open_labels, int n_sliced, const int32_t *sliced_labels, int n_steps,
-                                const int32_t *tree, tn_form form, int batch_log2, int64_t arena_budget, char *out,
-                                int cap) {
+                                const int32_t *tree, tn_form form, const tn_plan_opts *opts, int batch_log2,
+                                int64_t arena_budget, char *out, int cap) {
     if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
     if (cap < 0 || (cap > 0 && !out)) return fail(TN_ERR_ARG, "bad output buffer");
     tn_plan P;
     P.form = form;
+    if (opts) P.opts = *opts;
     P.opts.batch_log2 = -1;
     int64_t total = 0;
     int rc = plan_host_setup(P, n_tensors, ranks, labels, 0, nullptr, n_open, open_labels, n_sliced, sliced_labels,
