@@ -492,3 +492,56 @@ def test_describe_tree_lists_the_priced_ops(tn):
         assert pro == pytest.approx(e.prologue_ms, rel=1e-4) and body == pytest.approx(e.block_ms, rel=1e-4)
         gemms = [l for l in txt.splitlines() if " gemm " in l]
         assert gemms and all(("tensor-core" in l) == (form != "fp32") for l in gemms)
+
+
+def _one_step(tn, row_bits, k_bits, n_bits, form="bf16x3", k_low=False):
+    """The compiled op list of one step C[rows, N] = sum_K T[., .] S[K, N]
+    (first label = most significant: K above or below T's row labels)."""
+    rows = list(range(row_bits))
+    K = list(range(100, 100 + k_bits))
+    N = list(range(200, 200 + n_bits))
+    T = rows + K if k_low else K + rows
+    return tn.describe_tree([T, K + N], rows + N, [], [(0, 1)], form=form).strip().splitlines()
+
+
+def test_plan_compiler_kernel_selection(tn):
+    """The plan compiler's kernel choices (host logic, seen through
+    tn_describe_tree): a step whose small operand has <= 2^12 values streams
+    the big one once on the CUDA cores, one thread per row where N <= 8, in
+    row tiles staged through shared memory where K and N are 16..32 (stores
+    straight from registers when T's lowest bits are row bits, staged
+    otherwise), one thread per row again past K = 32; a larger step is a
+    GEMM, on the tensor cores after a split pass per operand in the split
+    forms, on the CUDA cores in FP32."""
+    (op,) = _one_step(tn, 22, 3, 3)
+    assert " small rows=4194304 K=8 N=8 " in op and "kernel=row" in op
+    (op,) = _one_step(tn, 21, 4, 5)
+    assert "K=16 N=32" in op and "kernel=tiled, direct C" in op
+    (op,) = _one_step(tn, 21, 4, 5, k_low=True)
+    assert "kernel=tiled, staged C" in op
+    (op,) = _one_step(tn, 21, 5, 5)
+    assert "K=32 N=32" in op and "kernel=tiled" in op
+    (op,) = _one_step(tn, 12, 6, 3)
+    assert "K=64 N=8" in op and "kernel=row" in op
+    ops = _one_step(tn, 16, 10, 10)
+    assert [o.split()[3] for o in ops] == ["split", "split", "gemm"]
+    assert "M=65536 N=1024 K=1024 tensor-core" in ops[-1]
+    (op,) = _one_step(tn, 16, 10, 10, form="fp32")
+    assert "gemm H=1 M=65536 N=1024 K=1024 fp32" in op
+
+
+@pytest.mark.parametrize("form", ["bf16x3", "tf32x3", "fp16x3"])
+def test_plan_compiler_fuses_the_split_into_the_producing_gemm(tn, form):
+    """Two GEMM steps in a chain, (A B) D: the first GEMM's epilogue writes
+    the second GEMM's hi/lo planes (out=planes), so step 1 splits only D; in
+    the scaled form the max-abs passes are for the leaves only (the producing
+    epilogue publishes its output's maximum)."""
+    rows, K1, N1, N2 = list(range(16)), list(range(100, 110)), list(range(200, 210)), list(range(300, 310))
+    ops = tn.describe_tree([K1 + rows, K1 + N1, N1 + N2], rows + N2, [], [(0, 1), (3, 2)], form=form)
+    ops = ops.strip().splitlines()
+    gemms = [o for o in ops if " gemm " in o]
+    assert len(gemms) == 2 and "out=planes" in gemms[0] and "out=complex64" in gemms[1]
+    step1_splits = [o for o in ops if o.startswith("prologue step 1 split")]
+    assert len(step1_splits) == 1 and "rank=20" in step1_splits[0]
+    maxabs = [int(o.split("n=")[1].split()[0]) for o in ops if " maxabs " in o]
+    assert sorted(maxabs) == ([2 ** 20, 2 ** 20, 2 ** 26] if form == "fp16x3" else [])
