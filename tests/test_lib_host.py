@@ -545,3 +545,21 @@ def test_plan_compiler_fuses_the_split_into_the_producing_gemm(tn, form):
     assert len(step1_splits) == 1 and "rank=20" in step1_splits[0]
     maxabs = [int(o.split("n=")[1].split()[0]) for o in ops if " maxabs " in o]
     assert sorted(maxabs) == ([2 ** 20, 2 ** 20, 2 ** 26] if form == "fp16x3" else [])
+
+
+def test_plan_compiler_runs_slice_invariant_steps_once(tn):
+    """Slicing ("Dynamic slicing"): a step whose operands hold no sliced
+    label is the same for every slice and runs once per call (prologue); a
+    step that depends on a sliced label runs once per block of slices.  With
+    the block holding every slice, the sliced label is a batch label and the
+    whole tree runs once."""
+    rows, K, N, X, s = list(range(14)), list(range(100, 110)), list(range(200, 210)), list(range(300, 306)), 500
+    L = [K + rows, K + N, N[:5] + [s] + X, [s] + N[5:]]
+    tree = [(0, 1), (2, 3), (4, 5)]
+    ops = tn.describe_tree(L, rows + X, [s], tree, form="fp32", batch_log2=0).strip().splitlines()
+    phase = {int(o.split()[2]): o.split()[0] for o in ops}
+    assert phase == {0: "prologue", 1: "batch", 2: "batch"}
+    e = tn.estimate_tree_ms(L, rows + X, [s], tree, form="fp32", batch_log2=0)
+    assert e.ms == pytest.approx(e.prologue_ms + 2 * e.block_ms, rel=1e-12)
+    ops1 = tn.describe_tree(L, rows + X, [s], tree, form="fp32", batch_log2=1).strip().splitlines()
+    assert all(o.startswith("prologue") for o in ops1)
