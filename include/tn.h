@@ -107,7 +107,7 @@ typedef struct {
 
 /* Order search options (host-side planning). */
 typedef struct {
-    int32_t trials;     /* randomised greedy trials (default 256) */
+    int32_t trials;     /* order trials, greedy or bipartition (method below; default 256) */
     uint64_t seed;      /* seed of the search's SplitMix64 stream */
     int32_t log2_cap;   /* slice until every intermediate has <= 2^log2_cap elements (-1: no cap) */
     int32_t n_sliced;   /* slice exactly this many labels (-1: as the cap needs) */
