@@ -563,3 +563,38 @@ def test_plan_compiler_runs_slice_invariant_steps_once(tn):
     assert e.ms == pytest.approx(e.prologue_ms + 2 * e.block_ms, rel=1e-12)
     ops1 = tn.describe_tree(L, rows + X, [s], tree, form="fp32", batch_log2=1).strip().splitlines()
     assert all(o.startswith("prologue") for o in ops1)
+
+
+def _fig3_costs(labels, open_labels, tree, sliced):
+    """Fig. 3: a step joining A and B costs 2^(n_A + n_B + n_AB) complex MACs
+    (the labels of A and B together; sliced labels are fixed, so they do not
+    count); a node's size is 2^(its labels minus the sliced ones)."""
+    keep, cut = set(open_labels), set(sliced)
+    nodes = [set(l) for l in labels]
+    per_slice, width = 0, max(len(s - cut) for s in nodes)
+    for a, b in tree:
+        A, B = nodes[a], nodes[b]
+        per_slice += 2 ** len((A | B) - cut)
+        C = (A | B) - ((A & B) - keep)
+        nodes.append(C)
+        width = max(width, len(C - cut))
+    return np.log2(per_slice), width
+
+
+@pytest.mark.parametrize("method", ["greedy", "bipartition"])
+def test_search_costs_follow_fig3(tn, method):
+    """The search's reported costs are Fig. 3's: per-slice MACs summed over
+    the steps of the returned tree, the total that times 2^n_sliced, and the
+    width the largest node, recomputed here from the tree alone."""
+    cases = [random_network(41, n_tensors=16, n_bonds=30, n_open=3, max_rank=8), None]
+    for net in cases:
+        if net is None:
+            cfg = make_config(2)
+            L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+        else:
+            L, O = net.labels, net.open_labels
+        tree, sl, st = tn.find_order(L, O, tn.search_opts(trials=32, n_sliced=3, method=method))
+        log2_slice, width = _fig3_costs(L, O, tree, sl)
+        assert st["log2_slice"] == pytest.approx(log2_slice, abs=1e-9)
+        assert st["log2_total"] == pytest.approx(log2_slice + len(sl), abs=1e-9)
+        assert st["log2_width"] == width
