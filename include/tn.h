@@ -327,6 +327,19 @@ int tn_describe_tree(int n_tensors, const int32_t *ranks, const int32_t *labels,
                      int64_t arena_budget, char *out, int cap);
 
 /*
+ * Slicing a given tree ("Dynamic slicing" paragraph): the search's greedy
+ * slicing (two rules, the cheaper result that meets the cap wins) applied
+ * to the caller's tree, until every intermediate has <= 2^log2_cap elements
+ * (log2_cap < 0: no cap) or, with n_sliced >= 0, exactly n_sliced labels.
+ * Network and tree as for tn_plan_create (same checks, TN_ERR_ARG).  Writes
+ * the sliced labels (up to max_sliced; TN_ERR_ARG when more are needed),
+ * their count and stats[4] as tn_find_order does.
+ */
+int tn_slice_tree(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open, const int32_t *open_labels,
+                  int n_steps, const int32_t *tree, int log2_cap, int n_sliced, int max_sliced, int32_t *out_sliced,
+                  int *out_n_sliced, double *stats);
+
+/*
  * Branch merging (appendix, "Details of simulations"): in a tree, a large
  * tensor X met by two small ones in turn, ((X a) b), is rewritten as
  * (X (a b)) when a, b and their product have rank <= max_small_rank (0: 12)

@@ -1160,3 +1160,55 @@ extern "C" int tn_merge_branches(int n_tensors, const int32_t *ranks, const int3
     }
     return TN_OK;
 }
+
+// ---------------------------------------------------------------- slicing a given tree
+// The slicing step of the search ("Dynamic slicing": bonds fixed one at a
+// time until every intermediate fits) applied to a tree the caller already
+// has: both greedy rules run and the cheaper result that meets the cap wins,
+// as in the search.
+namespace tn {
+
+extern "C" int tn_slice_tree(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                             const int32_t *open_labels, int n_steps, const int32_t *tree, int log2_cap,
+                             int n_sliced, int max_sliced, int32_t *out_sliced, int *out_n_sliced,
+                             double *stats) {
+    if (n_tensors < 1 || !ranks || !labels || n_steps != n_tensors - 1 || (n_steps > 0 && !tree) || n_open < 0 ||
+        (n_open > 0 && !open_labels) || (log2_cap < 0 && n_sliced < 0) || max_sliced < 0 ||
+        (max_sliced > 0 && !out_sliced))
+        return fail(TN_ERR_ARG, "tn_slice_tree: bad arguments");
+    std::vector<std::vector<int32_t>> labs(n_tensors);
+    size_t off = 0;
+    for (int i = 0; i < n_tensors; i++) {
+        if (ranks[i] < 0 || ranks[i] > 62) return fail(TN_ERR_ARG, "tn_slice_tree: rank out of range");
+        labs[i].assign(labels + off, labels + off + ranks[i]);
+        off += ranks[i];
+    }
+    const std::vector<int32_t> open(open_labels, open_labels + n_open);
+    if (const char *bad = check_network(labs, open)) return fail(TN_ERR_ARG, std::string("tn_slice_tree: ") + bad);
+    Problem p;
+    if (const char *bad = make_problem(labs, open, p)) return fail(TN_ERR_ARG, std::string("tn_slice_tree: ") + bad);
+    Tree t(n_steps);
+    for (int i = 0; i < n_steps; i++) t[i] = {tree[2 * i], tree[2 * i + 1]};
+    TreeSets ts;
+    if (!tree_sets(p, t, ts)) return fail(TN_ERR_ARG, "tn_slice_tree: malformed tree");
+    SliceEval e0, e1;
+    slice_tree(p, ts, 2 * p.n - 1, p.n - 1, log2_cap, n_sliced, 0, e0);
+    slice_tree(p, ts, 2 * p.n - 1, p.n - 1, log2_cap, n_sliced, 1, e1);
+    const auto key = [&](const SliceEval &e) {
+        const bool over = log2_cap >= 0 && e.log2_width > log2_cap;
+        return std::make_pair(over ? e.log2_width : 0.0, e.log2_total);
+    };
+    const SliceEval &ev = key(e1) < key(e0) ? e1 : e0;
+    if ((int)ev.sliced.size() > max_sliced) return fail(TN_ERR_ARG, "tn_slice_tree: max_sliced too small");
+    for (size_t j = 0; j < ev.sliced.size(); j++) out_sliced[j] = p.id2label[ev.sliced[j]];
+    if (out_n_sliced) *out_n_sliced = (int)ev.sliced.size();
+    if (stats) {
+        stats[0] = ev.log2_total;
+        stats[1] = ev.log2_width;
+        stats[2] = (double)ev.sliced.size();
+        stats[3] = ev.log2_slice_cost;
+    }
+    return TN_OK;
+}
+
+}  // namespace tn

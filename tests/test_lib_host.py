@@ -598,3 +598,27 @@ def test_search_costs_follow_fig3(tn, method):
         assert st["log2_slice"] == pytest.approx(log2_slice, abs=1e-9)
         assert st["log2_total"] == pytest.approx(log2_slice + len(sl), abs=1e-9)
         assert st["log2_width"] == width
+
+
+def test_slice_tree_meets_the_cap_on_a_given_tree(tn):
+    """tn_slice_tree slices a caller's tree: every intermediate then fits the
+    cap, the sliced labels are internal bonds, the reported costs are Fig. 3's
+    for that tree, and summing the FP64 oracle's slices gives the unsliced
+    contraction (the slicing invariant)."""
+    net = random_network(43, n_tensors=14, n_bonds=26, n_open=3, max_rank=8)
+    tree, _, st0 = tn.find_order(net.labels, net.open_labels, tn.search_opts(trials=16, n_sliced=0))
+    cap = int(st0["log2_width"]) - 3
+    sl, st = tn.slice_tree(net.labels, net.open_labels, tree, log2_cap=cap)
+    assert st["log2_width"] <= cap and len(sl) == st["n_sliced"] == len(set(sl)) >= 1
+    assert not set(sl) & set(net.open_labels)
+    log2_slice, width = _fig3_costs(net.labels, net.open_labels, tree, sl)
+    assert st["log2_slice"] == pytest.approx(log2_slice, abs=1e-9) and st["log2_width"] == width
+    full = oc.contract(net.labels, net.data, net.open_labels, tree=tree)
+    parts = sum(oc.slice_partial(net.labels, net.data, net.open_labels, sl, s) for s in range(1 << len(sl)))
+    assert np.abs(parts - full).max() < 1e-12 * max(1.0, np.abs(full).max())
+    sl2, st2 = tn.slice_tree(net.labels, net.open_labels, tree, n_sliced=2)
+    assert len(sl2) == 2
+    with pytest.raises(tn.TNError):
+        tn.slice_tree(net.labels, net.open_labels, tree)  # neither a cap nor a count
+    with pytest.raises(tn.TNError):
+        tn.slice_tree(net.labels, net.open_labels, [(0, 0)] * len(tree), log2_cap=cap)
