@@ -399,6 +399,20 @@ int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, const tn_search
                           int32_t *out_tail, int *out_n_tail, int *out_cut, double *out_log2_cost);
 
 /*
+ * Stage-2 slicing for tn_head_tail_amplitudes: its stage-2 network (the
+ * tail's tensors, then v_head over the cut as one more leaf, joined at the
+ * root of the tail's subtree) sliced by tn_slice_tree until every
+ * intermediate has <= 2^log2_cap elements.  The sliced labels are tail or
+ * cut labels, never open ones, as sliced_tail must be.  Tree and network as
+ * for tn_head_tail_amplitudes (the root step joins the head, without open
+ * legs, and the tail); TN_ERR_ARG otherwise, or when more than max_sliced
+ * labels are needed.  stats[4] as tn_find_order's.
+ */
+int tn_slice_stage2(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open, const int32_t *open_labels,
+                    int n_steps, const int32_t *tree, int log2_cap, int max_sliced, int32_t *out_sliced_tail,
+                    int *out_n_sliced, double *stats);
+
+/*
  * Two-stage big-head contraction ("Big-head simulation" section): the
  * tree's last step must join the head (no open label) and the tail (every
  * open label); the labels they share are the first cut C.  Stage 1

@@ -100,7 +100,7 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
             "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
-            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits", "tn_describe_tree", "tn_slice_tree"]
+            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits", "tn_describe_tree", "tn_slice_tree", "tn_slice_stage2"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -287,6 +287,23 @@ def slice_tree(labels, open_labels, tree, log2_cap=-1, n_sliced=-1, max_sliced=6
     _check(_lib.tn_slice_tree(len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol), len(tree), _ptr(tr),
                               int(log2_cap), int(n_sliced), int(max_sliced), _ptr(sl), ctypes.byref(nsl), _ptr(st)),
            "tn_slice_tree")
+    stats = dict(log2_total=st[0], log2_width=st[1], n_sliced=int(st[2]), log2_slice=st[3])
+    return [int(x) for x in sl[:nsl.value]], stats
+
+
+def slice_stage2(labels, open_labels, tree, log2_cap, max_sliced=64):
+    """tn_slice_stage2: (sliced_tail labels, stats dict) bounding the
+    intermediates of head_tail_amplitudes' stage 2 by 2^log2_cap."""
+    ranks = np.asarray([len(l) for l in labels], dtype=np.int32)
+    flat = np.asarray([x for l in labels for x in l] or [0], dtype=np.int32)
+    ol = np.asarray(list(open_labels) or [0], dtype=np.int32)
+    tr = np.asarray([x for p in tree for x in p] or [0], dtype=np.int32)
+    sl = np.zeros(max(max_sliced, 1), dtype=np.int32)
+    nsl = ctypes.c_int(0)
+    st = np.zeros(4)
+    _check(_lib.tn_slice_stage2(len(labels), _ptr(ranks), _ptr(flat), len(open_labels), _ptr(ol), len(tree),
+                                _ptr(tr), int(log2_cap), int(max_sliced), _ptr(sl), ctypes.byref(nsl), _ptr(st)),
+           "tn_slice_stage2")
     stats = dict(log2_total=st[0], log2_width=st[1], n_sliced=int(st[2]), log2_slice=st[3])
     return [int(x) for x in sl[:nsl.value]], stats
 

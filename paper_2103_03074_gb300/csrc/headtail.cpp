@@ -511,3 +511,58 @@ extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, cons
     if (out_log2_cost) *out_log2_cost = best_cost;
     return TN_OK;
 }
+
+extern "C" int tn_slice_stage2(int n_tensors, const int32_t *ranks, const int32_t *labels, int n_open,
+                               const int32_t *open_labels, int n_steps, const int32_t *tree_in, int log2_cap,
+                               int max_sliced, int32_t *out_sliced_tail, int *out_n_sliced, double *stats) {
+    if (n_tensors < 2 || !ranks || !labels || n_open < 1 || !open_labels || n_steps != n_tensors - 1 || !tree_in ||
+        log2_cap < 0)
+        return fail(TN_ERR_ARG, "tn_slice_stage2: bad arguments");
+    for (int i = 0; i < n_tensors; i++)
+        if (ranks[i] < 0 || ranks[i] > 62) return fail(TN_ERR_ARG, "tn_slice_stage2: rank out of range");
+    const int n = n_tensors;
+    const auto labs = parse_labels(n, ranks, labels);
+    Tree tree(n_steps);
+    for (int t = 0; t < n_steps; t++) tree[t] = {tree_in[2 * t], tree_in[2 * t + 1]};
+    if (!valid_tree(n, tree)) return fail(TN_ERR_ARG, "tn_slice_stage2: malformed tree");
+    // head and tail: the two sides of the root step, the tail holding the open legs
+    const std::set<int32_t> open(open_labels, open_labels + n_open);
+    std::vector<int> side[2];
+    int open_side[2] = {0, 0};
+    for (int k = 0; k < 2; k++) {
+        std::vector<char> in(n + tree.size(), 0);
+        mark_subtree(k == 0 ? tree.back().first : tree.back().second, n, tree, in);
+        for (int i = 0; i < n; i++)
+            if (in[i]) side[k].push_back(i);
+        for (int32_t x : labels_of(labs, side[k])) open_side[k] += (int)open.count(x);
+    }
+    if (open_side[0] && open_side[1])
+        return fail(TN_ERR_ARG, "tn_slice_stage2: open legs on both sides of the root step (no big-head cut)");
+    const int h = open_side[0] ? 1 : 0;
+    const std::vector<int> &head = side[h], &tail = side[1 - h];
+    const int tail_root = h == 0 ? tree.back().second : tree.back().first;
+    const std::set<int32_t> lh = labels_of(labs, head), lt = labels_of(labs, tail);
+    std::vector<int32_t> cut;
+    for (int32_t x : lh)
+        if (lt.count(x)) cut.push_back(x);
+    // stage 2 as tn_head_tail_amplitudes builds it: the tail's leaves, then
+    // v_head over the cut (increasing labels) as the last leaf, joined at the root
+    Tree tt;
+    const int tr = sub_tree(tail_root, n, tree, tail, tt);
+    const int vleaf = (int)tail.size();
+    std::vector<int32_t> r2, l2, t2;
+    for (int i : tail) {
+        r2.push_back((int32_t)labs[i].size());
+        l2.insert(l2.end(), labs[i].begin(), labs[i].end());
+    }
+    r2.push_back((int32_t)cut.size());
+    l2.insert(l2.end(), cut.begin(), cut.end());
+    for (const auto &st : tt) {
+        t2.push_back(st.first >= vleaf ? st.first + 1 : st.first);
+        t2.push_back(st.second >= vleaf ? st.second + 1 : st.second);
+    }
+    t2.push_back(tr >= vleaf ? tr + 1 : tr);
+    t2.push_back(vleaf);
+    return tn_slice_tree(vleaf + 1, r2.data(), l2.data(), n_open, open_labels, (int)t2.size() / 2, t2.data(), log2_cap,
+                         -1, max_sliced, out_sliced_tail, out_n_sliced, stats);
+}

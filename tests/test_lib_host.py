@@ -622,3 +622,52 @@ def test_slice_tree_meets_the_cap_on_a_given_tree(tn):
         tn.slice_tree(net.labels, net.open_labels, tree)  # neither a cap nor a count
     with pytest.raises(tn.TNError):
         tn.slice_tree(net.labels, net.open_labels, [(0, 0)] * len(tree), log2_cap=cap)
+
+
+def _leaves_of(tree, n, x):
+    return [x] if x < n else _leaves_of(tree, n, tree[x - n][0]) + _leaves_of(tree, n, tree[x - n][1])
+
+
+def test_slice_stage2_bounds_the_second_stage(tn):
+    """The two-stage form with its second stage sliced, end to end on the
+    FP64 oracle ("Big-head simulation": psi = v_head . v_tail): v_head is the
+    head contracted over the cut, stage 2 is the tail with v_head as one more
+    leaf, and tn_slice_stage2's labels (tail or cut bonds, never open) bound
+    its intermediates; summing the oracle's slices of stage 2 gives the state
+    vector's amplitudes."""
+    circ = sycamore_circuit("rect", 3, 4, 8, 5)
+    bits, open_q = random_bits(12, 5), [8, 9, 10, 11]
+    L, T, O = tn.circuit_network(circ, bits, open_q)
+    T = [np.asarray(t, np.complex128) for t in T]
+    n = len(L)
+    tree, _, st = tn.find_order_head_tail(L, O, opts=tn.search_opts(trials=32, n_sliced=0))
+    a, b = (_leaves_of(tree, n, r) for r in tree[-1])
+    head, tail = (a, b) if not {x for i in a for x in L[i]} & set(O) else (b, a)
+    lh, lt = {x for i in head for x in L[i]}, {x for i in tail for x in L[i]}
+    cut = sorted(lh & lt)
+    v_head = oc.contract([L[i] for i in head], [T[i] for i in head], cut)
+    L2, T2 = [L[i] for i in tail] + [cut], [T[i] for i in tail] + [v_head]
+    full = tn.slice_tree(L2, O, _stage2_tree(tree, n, tail), n_sliced=0)[1]["log2_width"]
+    cap = int(full) - 3
+    sl, st2 = tn.slice_stage2(L, O, tree, log2_cap=cap)
+    assert st2["log2_width"] <= cap and sl and not set(sl) & set(O) and set(sl) <= lt
+    amp = sum(oc.slice_partial(L2, T2, O, sl, s) for s in range(1 << len(sl))).reshape(-1)
+    ref = osv.amplitudes(circ, bits, open_q)
+    assert np.linalg.norm(amp - ref) / np.linalg.norm(ref) < 1e-6
+    with pytest.raises(tn.TNError):
+        tn.slice_stage2(L, O, tn.find_order(L, O, tn.search_opts(trials=4, n_sliced=0))[0], log2_cap=cap)
+
+
+def _stage2_tree(tree, n, tail):
+    """The stage-2 tree as tn_head_tail_amplitudes builds it: the tail's
+    subtree renumbered over the tail's leaves, then v_head (the next leaf)
+    joined at its root."""
+    idx = {x: i for i, x in enumerate(tail)}
+    m, out = len(tail), []
+    for t, (a, b) in enumerate(tree[:-1]):
+        if a in idx and b in idx:
+            out.append((idx[a] + (idx[a] >= m), idx[b] + (idx[b] >= m)))
+            idx[n + t] = m + len(out) - 1
+    root = max(idx.values())
+    out.append((root + 1 if root >= m else root, m))
+    return out
