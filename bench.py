@@ -387,7 +387,8 @@ def run_native(args):
         cfg["open_qubits"] = tn.choose_open_qubits(
             cfg["circuit"], n_open, tn.search_opts(**dict(wl["search"], trials=64), method="bipartition"))[0]
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**wl["search"], method=args.search_method,
+    search = dict(wl["search"], seed=args.seed) if args.seed is not None else wl["search"]
+    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**search, method=args.search_method,
                                                           objective=args.objective,
                                                           rank_form="bf16x3" if args.form == "all" else args.form))
     if args.branch_merge:
@@ -554,7 +555,7 @@ def run_native(args):
                    "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
                    "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],
                    "arena_bytes": r["plan"]["arena_bytes"], "order_search": args.search_method,
-                   "order_objective": args.objective,
+                   "order_objective": args.objective, "order_seed": args.seed,
                    "open_qubits": cfg["open_qubits"] if args.choose_open else "fixed (the workload's)",
                    "branch_merge": bool(args.branch_merge)},
         "complex_tflops": r["complex_tflops"],
@@ -593,6 +594,7 @@ def main():
     ap.add_argument("--objective", default="macs", choices=["macs", "roofline"],
                     help="rank the search's trees by total MACs (default) or by the roofline time of their "
                          "compiled plan (tn_estimate_tree_ms) for --form (bf16x3 with --form all)")
+    ap.add_argument("--seed", type=int, default=None, help="order-search seed (default: the library's)")
     ap.add_argument("--choose-open", action="store_true",
                     help="take the open qubits behind a small first cut (tn_choose_open_qubits) instead of the "
                          "workload's fixed set; the stored oracle amplitudes then do not apply (no error reported)")
