@@ -391,7 +391,9 @@ int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, const int32_t *
  * qubits (n_open, increasing), the tail's tensor ids in the all-open network
  * (out_tail, room for its tensor count; may be NULL), their count, the cut
  * (bonds between tail and head) and *out_log2_cost (log2 total MACs of the
- * winner's search, -1 without opts; may be NULL).  TN_ERR_ARG unless
+ * winner's search, or log2 of its plan's roofline ms when opts->objective is
+ * 1, the measure the candidates are compared by; -1 without opts; may be
+ * NULL).  TN_ERR_ARG unless
  * 1 <= n_open < n_qubits, or when no connected tail holds exactly n_open
  * ends.
  */

@@ -671,3 +671,18 @@ def _stage2_tree(tree, n, tail):
     root = max(idx.values())
     out.append((root + 1 if root >= m else root, m))
     return out
+
+
+def test_choose_open_qubits_prices_by_the_search_objective(tn):
+    """With the roofline objective the candidates are compared by their
+    plans' roofline time, and the cost returned is log2 of the winner's."""
+    cfg = make_config(2)
+    opts = tn.search_opts(trials=8, n_sliced=4, objective="roofline", rank_form="bf16x3")
+    oq, _, _, cost = tn.choose_open_qubits(cfg["circuit"], 8, opts)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], oq)
+    tree, sl, _ = tn.find_order(L, O, opts)
+    assert cost == pytest.approx(np.log2(tn.estimate_tree_ms(L, O, sl, tree, form="bf16x3").ms), abs=1e-9)
+    oq0, _, _, _ = tn.choose_open_qubits(cfg["circuit"], 8)
+    L0, T0, O0 = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], oq0)
+    t0, s0, _ = tn.find_order(L0, O0, opts)
+    assert cost <= np.log2(tn.estimate_tree_ms(L0, O0, s0, t0, form="bf16x3").ms) + 1e-9
