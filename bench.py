@@ -531,9 +531,11 @@ def run_native(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "error": {f: results[f]["error"] for f in forms}}))
         return 1
-    # headline: the fastest form within the 1e-5 amplitude error bound
-    within = [f for f in ok if (results[f]["rel_l2_err"] is not None and results[f]["rel_l2_err"] <= 1e-5)
-              or (results[f]["rel_l2_err"] is None and f in ACCURATE_FORMS)]
+    # headline: the fastest form that meets the 1e-5 amplitude error bound
+    # by construction (22+ significant bits per operand) and, where an
+    # oracle value exists, by measurement; BF16x3 (16 bits) and FP16S never
+    within = [f for f in ok if f in ACCURATE_FORMS and
+              (results[f]["rel_l2_err"] is None or results[f]["rel_l2_err"] <= 1e-5)]
     best = max(within or ok, key=lambda f: results[f]["slices_per_s"])
     r = results[best]
     cpu = None

@@ -401,6 +401,18 @@ int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, const tn_search
                           int32_t *out_tail, int *out_n_tail, int *out_cut, double *out_log2_cost);
 
 /*
+ * The candidate open sets of tn_choose_open_qubits, in the order it takes
+ * them: every connected tail with exactly n_open qubit ends that its growths
+ * reach, sorted by cut (ties in growth order); with search options the
+ * chooser prices the first 8.  Writes min(max_out, count) candidates: open
+ * qubits to out_qubits[i * n_open ...] (increasing) and the cut to
+ * out_cuts[i]; *out_n = the full count.  Host memory only; no GPU needed.
+ * TN_ERR_ARG unless 1 <= n_open < n_qubits, or when no tail qualifies.
+ */
+int tn_open_qubit_candidates(const tn_circuit *circuit, int n_open, int max_out, int32_t *out_qubits, int *out_cuts,
+                             int *out_n);
+
+/*
  * Stage-2 slicing for tn_head_tail_amplitudes: its stage-2 network (the
  * tail's tensors, then v_head over the cut as one more leaf, joined at the
  * root of the tail's subtree) sliced by tn_slice_tree until every
@@ -474,7 +486,11 @@ int tn_circuit_network(const tn_circuit *circuit, const uint8_t *fixed_bits, int
  * before any stream capture.  All calls share the array and each call
  * overwrites the part it uses, so calls that overlap on the GPU (other
  * streams, other host threads) race; order them on one stream.
- * Errors: TN_ERR_ARG (sizes, form, NULL), TN_ERR_CUDA.
+ * Synchronous: after launching, the call reads and clears the library's
+ * device error word (the GEMM's pipeline waits are bounded), which waits for
+ * the stream; C is complete when the call returns TN_OK.
+ * Errors: TN_ERR_ARG (sizes, form, NULL), TN_ERR_CUDA, TN_ERR_TIMEOUT (a
+ * bounded pipeline wait expired; C is then incomplete).
  */
 int tn_gemm_split_noalloc(const float *d_A, const float *d_B, float *d_C, int64_t M, int64_t N, int64_t K,
                           tn_form form, tn_stream_t stream);

@@ -100,7 +100,8 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_costmodel_params", "tn_costmodel_grad", "tn_costmodel_train", "tn_costmodel_predict",
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
             "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
-            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits", "tn_describe_tree", "tn_slice_tree", "tn_slice_stage2"]
+            "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits",
+            "tn_open_qubit_candidates", "tn_describe_tree", "tn_slice_tree", "tn_slice_stage2"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -340,6 +341,19 @@ def choose_open_qubits(circuit, n_open, opts=None):
                                       _ptr(oq), _ptr(tail), ctypes.byref(nt), ctypes.byref(cut),
                                       ctypes.byref(cost)), "tn_choose_open_qubits")
     return [int(x) for x in oq], [int(x) for x in tail[:nt.value]], cut.value, cost.value
+
+
+def open_qubit_candidates(circuit, n_open, max_out=64):
+    """tn_open_qubit_candidates: [(open qubits, cut)] in the order
+    tn_choose_open_qubits takes them (smallest cut first)."""
+    c, keep = marshal_circuit(circuit)
+    oq = np.zeros(max(1, max_out * n_open), dtype=np.int32)
+    cuts = np.zeros(max(1, max_out), dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(_lib.tn_open_qubit_candidates(ctypes.byref(c), int(n_open), int(max_out), _ptr(oq), _ptr(cuts),
+                                         ctypes.byref(n)), "tn_open_qubit_candidates")
+    m = min(max_out, n.value)
+    return [([int(x) for x in oq[i * n_open:(i + 1) * n_open]], int(cuts[i])) for i in range(m)]
 
 
 def find_order_head_tail(labels, open_labels, tail_max=0, opts=None, max_sliced=64):

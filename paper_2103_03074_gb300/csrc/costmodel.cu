@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "costmodel.h"
+#include "kernels.h"
 #include "tn_internal.h"
 
 namespace tn {
@@ -195,12 +196,8 @@ int cuda_err(cudaError_t e, const char *what) {
 }
 
 cudaError_t set_attrs() {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fwdbwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e == cudaSuccess) done = true;
+    cudaError_t e = set_max_dynamic_smem((const void *)fwdbwd_kernel, (int)kSmem);
+    if (e == cudaSuccess) e = set_max_dynamic_smem((const void *)predict_kernel, (int)kSmem);
     return e;
 }
 

@@ -379,11 +379,22 @@ extern "C" int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, cons
     return TN_OK;
 }
 
-extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, const tn_search_opts *opts,
-                                     int32_t *out_open_qubits, int32_t *out_tail, int *out_n_tail, int *out_cut,
-                                     double *out_log2_cost) {
-    if (!circuit || !out_open_qubits || circuit->n_qubits < 2 || n_open < 1 || n_open >= circuit->n_qubits)
-        return fail(TN_ERR_ARG, "tn_choose_open_qubits: need a circuit and 1 <= n_open < n_qubits");
+namespace {
+
+// A candidate first cut for tn_choose_open_qubits: the tail's open qubits,
+// its cut and its tensors (in the all-open network).
+struct OpenCand {
+    int cut;
+    std::vector<int32_t> qubits;
+    std::vector<char> in;
+};
+
+// Every connected tail holding exactly n_open qubit ends that the growths
+// reach, sorted by cut (stable: growth order breaks ties).  n_tensors gets the
+// all-open network's tensor count.
+int open_candidates(const tn_circuit *circuit, int n_open, std::vector<OpenCand> &cands, int &n_tensors) {
+    using Cand = OpenCand;
+    cands.clear();
     const int nq = circuit->n_qubits;
     std::vector<int32_t> all(nq);
     for (int q = 0; q < nq; q++) all[q] = q;
@@ -405,8 +416,6 @@ extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, cons
             nb[kv.second[1]].push_back(kv.second[0]);
         }
     // candidate tails: (cut, open qubits) -> the tail that reached it first
-    struct Cand { int cut; std::vector<int32_t> qubits; std::vector<char> in; };
-    std::vector<Cand> cands;
     auto record = [&](int cut, const std::vector<char> &in) {
         std::vector<int32_t> qs;
         for (int q = 0; q < nq; q++)
@@ -472,14 +481,31 @@ extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, cons
             v = pick;
         }
     }
-    if (cands.empty()) return fail(TN_ERR_ARG, "tn_choose_open_qubits: no connected tail holds exactly n_open qubit ends");
+    if (cands.empty()) return fail(TN_ERR_ARG, "no connected tail holds exactly n_open qubit ends");
     std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.cut < b.cut; });
+    n_tensors = n;
+    return TN_OK;
+}
+
+}  // namespace
+
+extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, const tn_search_opts *opts,
+                                     int32_t *out_open_qubits, int32_t *out_tail, int *out_n_tail, int *out_cut,
+                                     double *out_log2_cost) {
+    if (!circuit || !out_open_qubits || circuit->n_qubits < 2 || n_open < 1 || n_open >= circuit->n_qubits)
+        return fail(TN_ERR_ARG, "tn_choose_open_qubits: need a circuit and 1 <= n_open < n_qubits");
+    const int nq = circuit->n_qubits;
+    std::vector<OpenCand> cands;
+    int n = 0;
+    int rc = open_candidates(circuit, n_open, cands, n);
+    if (rc) return fail(rc, std::string("tn_choose_open_qubits: ") + tn_last_error());
     // with search options: of the kPick smallest cuts, the open set whose
     // network the order search contracts most cheaply (the paper tries
     // first cuts until the contraction's complexity is acceptable)
     constexpr int kPick = 8;
     int best = 0;
-    double best_cost = -1.0;
+    bool priced = false;      // a candidate's cost has been taken
+    double best_cost = -1.0;  // reported as -1 without search options
     if (opts) {
         const int m = std::min<int>(kPick, (int)cands.size());
         for (int i = 0; i < m; i++) {
@@ -502,13 +528,14 @@ extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, cons
                                                    kNominalArenaBytes);
                 cost = ms > 0 ? std::log2(ms) : INFINITY;
             }
-            if (best_cost < 0 || cost < best_cost) {
+            if (!priced || cost < best_cost) {
+                priced = true;
                 best_cost = cost;
                 best = i;
             }
         }
     }
-    const Cand &c = cands[best];
+    const OpenCand &c = cands[best];
     for (int k = 0; k < n_open; k++) out_open_qubits[k] = c.qubits[k];
     int nt = 0;
     for (int i = 0; i < n; i++)
@@ -519,6 +546,24 @@ extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, cons
     if (out_n_tail) *out_n_tail = nt;
     if (out_cut) *out_cut = c.cut;
     if (out_log2_cost) *out_log2_cost = best_cost;
+    return TN_OK;
+}
+
+extern "C" int tn_open_qubit_candidates(const tn_circuit *circuit, int n_open, int max_out, int32_t *out_qubits,
+                                        int *out_cuts, int *out_n) {
+    if (!circuit || !out_n || circuit->n_qubits < 2 || n_open < 1 || n_open >= circuit->n_qubits || max_out < 0 ||
+        (max_out > 0 && (!out_qubits || !out_cuts)))
+        return fail(TN_ERR_ARG, "tn_open_qubit_candidates: need a circuit, 1 <= n_open < n_qubits and output room");
+    std::vector<OpenCand> cands;
+    int n = 0;
+    int rc = open_candidates(circuit, n_open, cands, n);
+    if (rc) return fail(rc, std::string("tn_open_qubit_candidates: ") + tn_last_error());
+    const int m = std::min<int>(max_out, (int)cands.size());
+    for (int i = 0; i < m; i++) {
+        for (int k = 0; k < n_open; k++) out_qubits[(size_t)i * n_open + k] = cands[i].qubits[k];
+        out_cuts[i] = cands[i].cut;
+    }
+    *out_n = (int)cands.size();
     return TN_OK;
 }
 

@@ -10,6 +10,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "kernels.h"
@@ -679,13 +682,24 @@ __global__ void xeb_finalize_kernel(double *out, int scale_exp) { out[1] = ldexp
 
 }  // namespace
 
+cudaError_t set_max_dynamic_smem(const void *kernel, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> done;  // (kernel, device) -> bytes set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find({kernel, dev});
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[{kernel, dev}] = bytes;
+    return e;
+}
+
 template <int NC>
 cudaError_t launch_small_nc(const SmallArgs &a, int grid, size_t smem, cudaStream_t s) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(small_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_done = true;
-    }
+    cudaError_t e = set_max_dynamic_smem((const void *)small_kernel<NC>, 100 * 1024);
+    if (e != cudaSuccess) return e;
     small_kernel<NC><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -815,23 +829,32 @@ std::vector<std::pair<int, uint32_t>> c_tile_bits(const SmallArgs &a, int row_bi
     return bits;
 }
 
+// Resident CTAs per SM times the SM count of the current device, for a
+// kernel at a given dynamic shared-memory size (cached per device; the
+// kernel's shared-memory limit must already be raised).
+int64_t resident_ctas(const void *kernel, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<std::pair<const void *, size_t>, int>, int64_t> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(std::make_pair(kernel, smem), dev);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int occ = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem) != cudaSuccess || occ < 1) occ = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    return cache[key] = (int64_t)occ * sms;
+}
+
 template <int NK, int NN, int STORE>
 cudaError_t launch_small_tiled_t(const SmallArgs &a, cudaStream_t s) {
-    static int occ = 0;
-    static size_t occ_smem = 0;
     const size_t smem = small_tiled_smem(a);
-    if (occ == 0 || occ_smem != smem) {
-        cudaFuncSetAttribute(small_tiled_kernel<NK, NN, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             160 * 1024);
-        int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, small_tiled_kernel<NK, NN, STORE>, kThreads, smem) !=
-                cudaSuccess || o < 1)
-            o = 1;
-        occ = o;
-        occ_smem = smem;
-    }
+    const void *kernel = (const void *)small_tiled_kernel<NK, NN, STORE>;
+    cudaError_t e = set_max_dynamic_smem(kernel, 160 * 1024);
+    if (e != cudaSuccess) return e;
     const int64_t tiles = a.rows >> a.tb;
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)152 * occ);
+    const int grid = (int)std::min<int64_t>(tiles, resident_ctas(kernel, smem));
     small_tiled_kernel<NK, NN, STORE><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -900,11 +923,8 @@ void prepare_small_tiled(SmallArgs &a) {
 
 template <int NC>
 cudaError_t launch_small_ksplit_nc(const SmallArgs &a, int grid, size_t smem, cudaStream_t s) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(small_ksplit_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_done = true;
-    }
+    cudaError_t e = set_max_dynamic_smem((const void *)small_ksplit_kernel<NC>, 100 * 1024);
+    if (e != cudaSuccess) return e;
     small_ksplit_kernel<NC><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -203,6 +203,11 @@ struct AccumArgs {
 };
 
 // launchers (kernels.cu); return cudaSuccess or the launch error
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to the device, so it is set once per
+// (kernel, device) pair; thread-safe.
+cudaError_t set_max_dynamic_smem(const void *kernel, int bytes);
+
 cudaError_t launch_small(const SmallArgs &a, cudaStream_t s);
 cudaError_t launch_bitperm(const BitPermArgs &a, cudaStream_t s);
 cudaError_t launch_maxabs(const MaxAbsArgs &a, cudaStream_t s);

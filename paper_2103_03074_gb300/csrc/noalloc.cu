@@ -170,5 +170,13 @@ extern "C" int tn_gemm_split_noalloc(const float *d_A, const float *d_B, float *
     if (!tc_prepare(g)) return fail(TN_ERR_CUDA, "tn_gemm_split_noalloc: TMA descriptor encoding failed");
     e = launch_gemm_tc(g, s);
     if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("tn_gemm_split_noalloc GEMM: ") + cudaGetErrorString(e));
+    // The GEMM's pipeline waits are bounded; one that expires leaves C
+    // partial and sets the library's device error word.  Read and clear the
+    // word here (this synchronises the stream), so the caller learns of it
+    // from this call and no later call reports it.
+    if (tc_read_error(s) != 0)
+        return fail(TN_ERR_TIMEOUT, "tn_gemm_split_noalloc: a bounded tensor-core pipeline wait expired");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("tn_gemm_split_noalloc: ") + cudaGetErrorString(e));
     return TN_OK;
 }

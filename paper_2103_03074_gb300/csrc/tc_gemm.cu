@@ -49,7 +49,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "tc_gemm.h"
 
@@ -654,16 +656,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+    });
     return fn;
 }
 
@@ -734,13 +735,8 @@ bool tc_prepare(TcGemm &g) {
 template <int KIND, int CB>
 cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
     constexpr int NP = kind_split(KIND) ? 4 : 2;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<KIND, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Ring<CB, NP>::kSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = set_max_dynamic_smem((const void *)tc_gemm_kernel<KIND, CB>, Ring<CB, NP>::kSmem);
+    if (e != cudaSuccess) return e;
     const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
     const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
     tc_gemm_kernel<KIND, CB><<<grid, kThreads, Ring<CB, NP>::kSmem, s>>>(mA, mB, p);
@@ -796,15 +792,17 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     }
     // persistent: one CTA per SM (the ring and staging fill the SM's shared
     // memory), at most one per tile
-    static int sm_count[64] = {0};
+    static std::atomic<int> sm_count[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (sm_count[dev] == 0) {
-        cudaError_t e = cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+    int sms = sm_count[dev].load(std::memory_order_relaxed);
+    if (sms == 0) {
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
+        sm_count[dev].store(sms, std::memory_order_relaxed);
     }
-    dim3 grid((unsigned)(p.tiles < sm_count[dev] ? p.tiles : sm_count[dev]));
+    dim3 grid((unsigned)(p.tiles < sms ? p.tiles : sms));
     if (g.form == TN_TF32X3)
         return g.chunk_bytes == 64 ? launch_variant<kTF32, 64>(g, p, grid, s) : launch_variant<kTF32, 128>(g, p, grid, s);
     if (g.form == TN_BF16X3)

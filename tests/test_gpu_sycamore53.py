@@ -8,7 +8,10 @@ lattice with one site removed), at full size.
   each entry is the fully closed network contracted by the oracle's own
   pairwise route, written by tests/golden/make_golden.py).  Bound: relative
   L2 error over the sample <= 1e-5 for the complex64 forms (FP32, TF32x3,
-  FP16X3), 5e-5 for BF16x3 (16-bit operand pieces), 2e-3 for FP16S.
+  FP16X3), 2e-3 for FP16S.  BF16x3 keeps 16 significant bits per operand
+  and does not meet 1e-5 (2.0e-5 measured here); its check against 1e-4
+  (2^-16 times a margin for the steps along the tree) only catches a broken
+  kernel and is not a parity claim.
 * 20 cycles, 21 open qubits, intermediates capped at 2^31 elements: no
   oracle value exists at this size (one amplitude costs ~2^61 complex MACs),
   so its parity is unpinned; the checks are properties that hold at any
@@ -84,11 +87,9 @@ def test_cfg4_sampled_amplitudes(tn, cfg4_plan_inputs, form):
     e = rel(got[idx], ref)
     print(f"cfg4 {form}: {len(sliced)} sliced bonds, 2^{st['log2_slice']:.1f} MACs per slice, "
           f"relative L2 error over {len(idx)} sampled entries {e:.3e}")
-    # BF16x3 holds about 16 significant bits per operand (two bf16 pieces),
-    # so its error grows with depth past the 1e-5 bound (1.2e-5 measured on
-    # the 30-qubit workload, 2.0e-5 here); it is held to 5e-5 and is not a
-    # form that meets the stated bound.  FP16S has the scaled-FP16 bound.
-    bound = {"fp16s": 2e-3, "bf16x3": 5e-5}.get(form, 1e-5)
+    # BF16x3 (16 significant bits per operand) and FP16S have their forms'
+    # own bounds (module docstring); the others meet 1e-5
+    bound = {"fp16s": 2e-3, "bf16x3": 1e-4}.get(form, 1e-5)
     assert e < bound
     # the whole tensor: XEB from the GPU probabilities matches the FP64
     # reduction of the same amplitudes, and the marginal P(s1) is the

@@ -686,3 +686,28 @@ def test_choose_open_qubits_prices_by_the_search_objective(tn):
     L0, T0, O0 = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], oq0)
     t0, s0, _ = tn.find_order(L0, O0, opts)
     assert cost <= np.log2(tn.estimate_tree_ms(L0, O0, s0, t0, form="bf16x3").ms) + 1e-9
+
+
+def test_choose_open_qubits_takes_the_cheapest_candidate_below_1ms(tn):
+    """With the roofline objective every candidate's cost is log2 of a plan
+    time in ms, negative for plans under 1 ms.  The chooser must return the
+    smallest of the 8 smallest-cut candidates' costs, whatever their sign
+    (a negative 'nothing chosen yet' sentinel would keep the last candidate
+    instead)."""
+    from tn_inputs import sycamore_circuit, random_bits
+    circ = sycamore_circuit("rect", 3, 5, 8, 77)
+    n_open = 5
+    opts = tn.search_opts(trials=8, n_sliced=2, objective="roofline", rank_form="tf32x3")
+    cands = tn.open_qubit_candidates(circ, n_open)
+    assert cands and [c[1] for c in cands] == sorted(c[1] for c in cands)
+    costs = []
+    for oq, _ in cands[:8]:
+        L, T, O = tn.circuit_network(circ, [0] * circ.n_qubits, oq)
+        tree, sl, _ = tn.find_order(L, O, opts)
+        costs.append(np.log2(tn.estimate_tree_ms(L, O, sl, tree, form="tf32x3").ms))
+    assert max(costs) < 0, "the case needs every candidate below 1 ms"
+    oq, _, _, cost = tn.choose_open_qubits(circ, n_open, opts)
+    i = int(np.argmin(costs))
+    assert cost == pytest.approx(costs[i], abs=1e-9)
+    assert cost <= min(costs) + 1e-9
+    assert oq in [c[0] for c in cands[:8]]
