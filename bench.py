@@ -1,22 +1,35 @@
 """Benchmark of the sliced big-head contraction on one GB300 (or N, one process
 per GPU under torchrun).
 
-Workload: the 30-qubit 5x6 grid, 12 cycles, 8 open qubits, the other 22 fixed
-to a seeded bitstring, 8 sliced bonds chosen by the order search (2^8 slices).
-One step = every slice contracted and summed into the FP64 amplitude tensor,
-then the FP64 probability / XEB reduction (all kernels of the hot path).
+Default workload: the 53-qubit Sycamore-shaped lattice (6 x 9 rotated grid,
+one site removed), 14 cycles, 16 open qubits, the other 37 fixed to a seeded
+bitstring, intermediates capped at 2^30 elements by slicing, contracted with
+the stored tree of paper_2103_03074_gb300/trees/syc53_m14.json (1024
+hierarchical-bipartition trials ranked by roofline time).  One step = every
+slice of that tree contracted and summed into the FP64 amplitude tensor (the
+whole 2^16-entry tensor), then the FP64 probability / XEB reduction.  The
+error of every form is measured on the FP64 oracle's sampled entries of the
+same tensor (tests/golden/cfg4_amplitudes_sampled.txt).  The line also
+carries a short measurement of the 20-cycle, 21-open-qubit workload (cap
+2^31): the split form against plain FP32 on the same slices.
 
 Metric: slices/s (and complex TFLOP/s = 8 x complex MACs / s).
   value     device time (CUDA events on the launching stream), L2 flushed
-            between steps outside the timed events.
-  e2e       the same through the C-ABI with host buffers: every step copies
-            the leaf values host->device (pinned) and reads the amplitudes back.
+            between steps outside the timed events; the fastest form that
+            keeps 22+ significant bits per operand (FP32, TF32x3, FP16X3) and
+            measures within 1e-5 of the oracle.
+  e2e       the same through tn_contract_slices_host with host buffers: every
+            step copies the leaf values in, contracts, reduces the
+            probabilities and copies the amplitudes out (pinned memory).
   roofline  of the dominant kernel class, from the step-timing recorder's
-            CUDA events in a second pass of the same steps.
-  cpu_baseline  the CPU FP64 oracle (its own network, the same sliced bonds)
-            timed on a bounded sample of slices on this host.
+            CUDA events in a separate pass of the same step.
+  cpu_baseline  the CPU FP64 oracle on a bounded sample of the same
+            workload, on all host cores and on one.
 
---impl reference times the CPU oracle as the reference arm.
+--impl reference times the CPU FP64 oracle as the reference arm (no product
+code is loaded: the slice count comes from the stored tree's JSON file).
+--workload gemm times one batched complex GEMM step of a given shape (the
+tensor-core kernel in isolation, e.g. for ncu).
 Multi-GPU (torchrun): each rank contracts its own seeded instance (weak
 scaling, no collective on the data path); time = max over ranks.
 """
@@ -36,9 +49,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TREES = os.path.join(ROOT, "paper_2103_03074_gb300", "trees")
 SMS = 152
 FP32_LANES_PER_SM = 128
 METRIC = "slices/s & complex TFLOP/s per GB300 at <=1e-5 amp err, split-TC vs plain FP32"
+DEFAULT_WORKLOAD = "syc53_m14"
+
+# DRAM traffic per tensor-core GEMM launch of the default step, by form, from
+# the ncu capture summarised under profiles/ (dram__bytes_read.sum +
+# dram__bytes_write.sum averaged over the step's launches); a form is absent
+# until such a capture exists for the current kernel
+GEMM_TRAFFIC_PER_LAUNCH = {}
 
 
 def peaks():
@@ -57,6 +78,13 @@ def fp32_alu_peak_tflops(sm_mhz):
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+# tensor-core flops the split forms issue per complex MAC: 4 real products x
+# 3 piece products x 2 (FP16S: 4 x 1 x 2); the TF32 peak is half the bf16
+# peak (nominal dense ratio 1.1 : 2.25)
+TC_FLOPS_PER_MAC = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16x3": 24.0, "fp16s": 8.0}
+TC_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5, "fp16x3": 1.0, "fp16s": 1.0}
+
+
 def roofline_ms(row, form, pk):
     """Roofline time of one launch of a profiled step: its algorithmic bytes
     over the measured HBM bandwidth, or its flops over the peak of the unit
@@ -66,9 +94,7 @@ def roofline_ms(row, form, pk):
     if kind == "small" or (kind == "gemm" and form == "fp32"):
         t_math = 8.0 * row["macs"] / (fp32_alu_peak_tflops(pk["sm_max_mhz"]) * 1e12)
     elif kind == "gemm":
-        per_mac = 8.0 if form == "fp16s" else 24.0
-        peak = pk["bf16_tflops"] * (0.5 if form == "tf32x3" else 1.0)
-        t_math = per_mac * row["macs"] / (peak * 1e12)
+        t_math = TC_FLOPS_PER_MAC[form] * row["macs"] / (pk["bf16_tflops"] * TC_PEAK_RATIO[form] * 1e12)
     else:
         t_math = 0.0
     return 1e3 * max(t_mem, t_math)
@@ -151,23 +177,28 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# Workloads.  The default is the bench line; the 53-qubit ones are extra
-# measurement lines (--workload), with steps that take seconds.
+# Workloads.  "tree" names the stored tree (paper_2103_03074_gb300/trees/)
+# used unless --search-method asks for a fresh search; "search" is that
+# fresh search's options.  "step_slices": slices per timed step (None: all).
 WORKLOADS = {
-    "rect3x4": dict(cfg=1, search=dict(trials=256, n_sliced=0), timed_slices=None, golden=None,
+    "rect3x4": dict(cfg=1, search=dict(trials=256, n_sliced=0), tree=None, step_slices=None, golden=None,
+                    forms=["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"],
                     desc="rect3x4_m8_allopen: 12 qubits, 8 cycles, all 12 open, no slicing "
                          "(one contraction per step: a latency-bound circuit)"),
-    "rect5x6": dict(cfg=2, search=dict(trials=16384, n_sliced=8), timed_slices=None,
-                    golden="cfg2_amplitudes.txt",
+    "rect5x6": dict(cfg=2, search=dict(trials=16384, n_sliced=8), tree="rect5x6", step_slices=None,
+                    golden="cfg2_amplitudes.txt", forms=["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"],
                     desc="rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 22 fixed, "
                          "2^8 slices over 8 searched bonds"),
-    "syc53_m14": dict(cfg=4, search=dict(trials=1024, log2_cap=30), timed_slices=None,
-                      golden="cfg4_amplitudes_sampled.txt",
+    "syc53_m14": dict(cfg=4, search=dict(trials=1024, log2_cap=30), tree="syc53_m14", step_slices=None,
+                      golden="cfg4_amplitudes_sampled.txt", forms=["fp16x3", "tf32x3", "fp32", "bf16x3", "fp16s"],
                       desc="rotated6x9m1_m14_open16_cap30: 53 qubits, 14 cycles, 16 open, 37 fixed, "
-                           "intermediates <= 2^30, every slice of the searched slice set"),
-    "syc53_m20": dict(cfg=5, search=dict(trials=1024, log2_cap=31), timed_slices=64, golden=None,
+                           "intermediates <= 2^30, every slice of the stored tree's slice set (the whole "
+                           "2^16-amplitude tensor per step)"),
+    "syc53_m20": dict(cfg=5, search=dict(trials=1024, log2_cap=31), tree="syc53_m20", step_slices=64, golden=None,
+                      forms=["fp16x3", "tf32x3"],
                       desc="rotated6x9m1_m20_open21_cap31: 53 qubits, 20 cycles, 21 open, 32 fixed, "
-                           "intermediates <= 2^31, a fixed 64-slice subset (ids 0..63) of the searched slice set"),
+                           "intermediates <= 2^31, a fixed 64-slice subset (ids 0..63) of the stored tree's "
+                           "slice set per step"),
 }
 # the batched workload: 256 independent seeded circuits of uneven size
 # (16-30 qubits, 8-14 cycles, 6-10 open, 2^0-2^6 slices each) in one
@@ -176,12 +207,14 @@ WORKLOADS = {
 BATCH_DESC = ("batch256: 256 seeded circuits on rectangular grids of 16-30 qubits, 8-14 cycles, 6-10 open qubits, "
               "2^0-2^6 slices each, one multi-stream CUDA graph")
 
-# forms whose error bound is 1e-5 by construction (22+ significant bits per
-# operand): the headline may take them where no oracle value exists
+# forms that meet the 1e-5 bound by construction (22+ significant bits per
+# operand); only these can be the headline (BF16x3 keeps 16 bits, FP16S 11)
 ACCURATE_FORMS = ("fp32", "tf32x3", "fp16x3")
+DTYPE = {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "tf32x3": "tf32x3 (fp32 accumulate)",
+         "fp16x3": "fp16x3 (scaled, fp32 accumulate)", "fp16s": "f16 (scaled)"}
 
 
-def workload(name="rect5x6", seed_offset=0):
+def workload(name, seed_offset=0):
     from tn_inputs.configs import make_config, CONFIGS
     import tn_inputs
     w = WORKLOADS[name]
@@ -191,6 +224,17 @@ def workload(name="rect5x6", seed_offset=0):
         cfg["circuit"] = tn_inputs.sycamore_circuit(c["layout"], c["rows"], c["cols"], c["cycles"],
                                                     c["seed"] + seed_offset)
     return cfg
+
+
+def stored_tree_json(name):
+    """The stored tree file's contents (plain JSON; loads no product code)."""
+    if not name:
+        return None
+    p = os.path.join(TREES, f"{name}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)
 
 
 def step_roofline(tn, L, O, sliced, tree, form, slices_per_batch, n_slices, measured_ms):
@@ -209,55 +253,152 @@ def step_roofline(tn, L, O, sliced, tree, form, slices_per_batch, n_slices, meas
         return {"error": str(exc)}
 
 
-def cpu_oracle_rate(cfg, sliced, budget_s=15.0, max_slices=4):
-    """Slices/s of the CPU oracle (its own network, same sliced bonds) on a
-    bounded sample; returns (slices/s, sample description, cores)."""
-    from oracle import network as onet, contract as oc
-    L, T, O = onet.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    n_slices = 1 << len(sliced)
-    done = 0
-    t0 = time.perf_counter()
-    while done < max_slices:
-        oc.slice_partial(L, T, O, sliced, done % n_slices)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    cores = os.cpu_count()
-    ids = f"ids 0..{min(done, n_slices) - 1}" + (" repeated" if done > n_slices else "")
-    return done / dt, f"{done} slice contractions ({ids}) of the 2^{len(sliced)}-slice workload, FP64 numpy", cores
+# ---------------------------------------------------------------- CPU oracle
+class OracleSampler:
+    """The CPU FP64 oracle on bounded samples of a workload, in slices/s.
+
+    Small workloads (30 qubits and below): the oracle contracts whole slices
+    (its own one-tensor-per-gate network, the sliced bonds fixed), one after
+    another.  53-qubit workloads: one slice of the open network is out of the
+    oracle's reach (its greedy order needs ~2^54 MACs), so it contracts closed
+    amplitudes (the open qubits set to a sampled bitstring: the route of the
+    stored oracle values) pair by pair, carrying on where the previous sample
+    stopped, and the rate is extrapolated by MACs: slices/s = (MACs done / s)
+    x n_slices / (2^n_open x MACs of one closed amplitude)."""
+
+    def __init__(self, workload_name, sliced, n_slices):
+        from oracle import network as onet, contract as oc
+        self.onet, self.oc = onet, oc
+        self.cfg = workload(workload_name)
+        self.k = len(self.cfg["open_qubits"])
+        self.small = self.cfg["circuit"].n_qubits <= 30
+        self.sliced, self.n_slices = list(sliced), n_slices
+        self.it, self.idx, self.amp_macs = None, 0, None
+        self.macs, self.secs, self.units, self.finished = 0.0, 0.0, 0, 0
+        if self.small:
+            self.net = onet.circuit_network(self.cfg["circuit"], self.cfg["fixed_bits"], self.cfg["open_qubits"])
+
+    def _next_amplitude(self):
+        bits = list(self.cfg["fixed_bits"])
+        b = (0x9E3779B1 * (self.idx + 1)) % (1 << self.k)
+        for j, q in enumerate(self.cfg["open_qubits"]):
+            bits[q] = (b >> (self.k - 1 - j)) & 1
+        self.idx += 1
+        L, T, O = self.onet.circuit_network(self.cfg["circuit"], bits, [])
+        self.it = self.oc.contract_iter(L, T, O)
+
+    def run(self, budget_s):
+        """Oracle work for about budget_s seconds; returns (slices/s of this
+        sample, seconds spent)."""
+        t0 = time.perf_counter()
+        macs0, units0 = self.macs, self.units
+        while time.perf_counter() - t0 < budget_s:
+            if self.small:
+                L, T, O = self.net
+                self.oc.slice_partial(L, T, O, self.sliced, self.units % (1 << len(self.sliced)))
+                self.units += 1
+                continue
+            if self.it is None:
+                self._next_amplitude()
+            try:
+                m, tot = next(self.it)
+                self.macs += m
+                self.amp_macs = tot
+            except StopIteration:
+                self.it = None
+                self.finished += 1
+        dt = time.perf_counter() - t0
+        self.secs += dt
+        if self.small:
+            return (self.units - units0) / dt, dt
+        return (self.macs - macs0) / dt * self.n_slices / ((1 << self.k) * self.amp_macs), dt
+
+    def rate(self):
+        """slices/s over every sample so far."""
+        if self.small:
+            return self.units / self.secs
+        return self.macs / self.secs * self.n_slices / ((1 << self.k) * self.amp_macs)
+
+    def describe(self):
+        if self.small:
+            return (f"{self.units} whole-slice contractions of the 2^{len(self.sliced)}-slice workload by the FP64 "
+                    f"oracle (numpy), {self.secs:.1f} s")
+        return (f"closed-amplitude contractions of the FP64 oracle (numpy, greedy order, "
+                f"2^{math.log2(self.amp_macs):.1f} complex MACs per amplitude): {self.macs:.3g} MACs in "
+                f"{self.secs:.1f} s, {self.finished} amplitude(s) finished; slices/s = MAC rate x {self.n_slices} "
+                f"slices / (2^{self.k} amplitudes x MACs per amplitude)")
+
+
+def cpu_baseline(workload_name, sliced, n_slices, budget_s=20.0):
+    """The oracle timed on all host cores, then on one core (a subprocess with
+    one BLAS/OpenMP thread); every number says what its sample was."""
+    smp = OracleSampler(workload_name, sliced, n_slices)
+    smp.run(budget_s)
+    out = {"value": smp.rate(), "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": smp.describe()}
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload_name,
+           "--oracle-budget", str(budget_s * 2 / 3), "--oracle-sliced", json.dumps(list(sliced)),
+           "--oracle-n-slices", str(n_slices)]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        out["one_core"] = {"value": one["value"], "unit": "slices/s", "cores": 1, "sample": one["sample"]}
+    except Exception as exc:
+        out["one_core"] = {"error": str(exc)[:200]}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the CPU FP64 oracle as it stands, on this host's
+    cores, on the bench's workload; each step a bounded sample (about 4 s of
+    oracle work).  Loads no product code."""
     rank, world, local = dist_env()
     if world > 1 and rank != 0:
         return 0
-    import paper_2103_03074_gb300 as tn
-    cfg = workload()
-    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    _, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
-    from oracle import network as onet, contract as oc
-    oL, oT, oO = onet.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    for w in range(args.warmup):
-        oc.slice_partial(oL, oT, oO, sliced, w % 256)
+    name = args.workload
+    w = WORKLOADS[name]
+    st = stored_tree_json(w["tree"])
+    sliced = st["sliced"] if st else []
+    n_slices = (1 << len(sliced)) if st else 1
+    if w["step_slices"]:
+        n_slices = min(n_slices, w["step_slices"])
+    per_step = 4.0
+    smp = OracleSampler(name, sliced, n_slices)
+    for _ in range(args.warmup):
+        smp.run(per_step / 4)
+    macs0, secs0, units0 = smp.macs, smp.secs, smp.units
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        oc.slice_partial(oL, oT, oO, sliced, k % 256)
+    for _ in range(args.steps):
+        smp.run(per_step)
     dt = time.perf_counter() - t0
-    v = args.steps / dt
+    if smp.small:
+        v = (smp.units - units0) / (smp.secs - secs0)
+    else:
+        v = (smp.macs - macs0) / (smp.secs - secs0) * n_slices / ((1 << smp.k) * smp.amp_macs)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Sycamore-style circuit)",
-            "config": {"workload": WORKLOADS["rect5x6"]["desc"],
-                       "step": "one slice contracted by the CPU FP64 oracle"},
+            "config": {"workload": w["desc"], "step": "a bounded sample (~4 s) of CPU FP64 oracle work",
+                       "slices_per_gpu_step": n_slices},
             "cpu_baseline": {"value": v, "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} slices per timed run, one per step"},
+                             "sample": f"{args.steps} steps of ~{per_step:.0f} s after {args.warmup} shorter "
+                                       f"warm-up steps; in all: " + smp.describe()},
             "e2e": {"value": v, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
+def run_oracle_sample(args):
+    """Subprocess leg of cpu_baseline (one core)."""
+    smp = OracleSampler(args.oracle_sample, json.loads(args.oracle_sliced), args.oracle_n_slices)
+    smp.run(args.oracle_budget)
+    print(json.dumps({"value": smp.rate(), "sample": smp.describe()}))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
 def load_golden_amplitudes(name):
     """(indices, amplitudes) of the stored FP64 oracle output, if present."""
     import numpy as np
@@ -278,25 +419,315 @@ def l2_flush_buffer(torch):
     return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
 
-def time_steps(torch, plan, n_slices, amp, steps, warmup, stream, flush, n_open, n_qubits, d_out):
-    """Sum of per-step device times (ms); L2 flushed before each step, untimed."""
+def time_steps(torch, plan, ranges, amp, steps, warmup, stream, flush, n_open, n_qubits, d_out):
+    """Per-step device times (ms); step k contracts ranges[k % len(ranges)];
+    L2 flushed before each step, untimed."""
     import paper_2103_03074_gb300 as tn
+
+    def one(k):
+        b, e = ranges[k % len(ranges)]
+        amp.zero_()
+        plan.contract(b, e, amp, stream)
+        tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
+
     with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            amp.zero_()
-            plan.contract(0, n_slices, amp, stream)
-            tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
+        for k in range(warmup):
+            one(k)
         stream.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for k in range(steps):
             flush.fill_(float(k))
             evs[k][0].record(stream)
-            amp.zero_()
-            plan.contract(0, n_slices, amp, stream)
-            tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
+            one(k)
             evs[k][1].record(stream)
         stream.synchronize()
-    return sum(a.elapsed_time(b) for a, b in evs)
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def profile_roofline(tn, torch, L, T, O, sliced, tree, form, rng, amp, stream, pk, steps, dump=None, tag=""):
+    """Per-op CUDA events (step-timing recorder) over `steps` steps: the
+    dominant kernel class's roofline entry and every class's share."""
+    pplan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(profile=1))
+    with torch.cuda.stream(stream):
+        pplan.contract(rng[0], rng[1], amp, stream)
+        pplan.profile(reset=True)
+        for _ in range(steps):
+            pplan.contract(rng[0], rng[1], amp, stream)
+    rows = pplan.profile()
+    pplan.close()
+    if dump:
+        with open(f"{dump}.{tag}{form}.json", "w") as f:
+            json.dump({"steps": steps, "rows": rows}, f)
+    by_kind = {}
+    for r in rows:
+        d = by_kind.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "macs": 0.0, "bytes": 0.0, "t_roof": 0.0})
+        d["ms"] += r["ms"]
+        d["launches"] += r["launches"]
+        d["macs"] += r["macs"] * r["launches"]
+        d["bytes"] += r["bytes"] * r["launches"]
+        d["t_roof"] += r["launches"] * roofline_ms(r, form, pk)
+    total_ms = sum(d["ms"] for d in by_kind.values())
+    top = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    d = by_kind[top]
+    avg_ms = d["ms"] / max(d["launches"], 1)
+    if top == "gemm" and form == "fp32":
+        peak = fp32_alu_peak_tflops(pk["sm_max_mhz"])
+        achieved = 8 * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "gemm_f32_kernel (complex FP32 FMA)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
+    elif top == "gemm":
+        peak = pk["bf16_tflops"] * TC_PEAK_RATIO[form]
+        achieved = TC_FLOPS_PER_MAC[form] * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": GEMM_TRAFFIC_PER_LAUNCH.get(form), "kernel": "tc_gemm_kernel (tcgen05 split form)",
+                "peak_source": pk["source"] + (" (bf16 burst x 0.5 for TF32)" if form == "tf32x3" else " (bf16 burst)")}
+    else:
+        achieved = d["bytes"] / d["launches"] / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": top, "peak_source": pk["source"]}
+    roof["algorithmic_per_launch"] = {"flops": (TC_FLOPS_PER_MAC.get(form, 8.0) if top == "gemm" else 8.0) *
+                                      d["macs"] / d["launches"], "bytes": d["bytes"] / d["launches"]}
+    roof["share_of_step"] = d["ms"] / total_ms if total_ms else None
+    roof["launches_per_step"] = d["launches"] / steps
+    # per-launch roofline time (bytes over HBM bandwidth or flops over the
+    # unit's peak, whichever is larger) summed over the class's launches,
+    # over their measured time: the class mixes tensor-bound and HBM-bound
+    # launches, so this is its meaningful fraction
+    roof["roofline_time_frac"] = d["t_roof"] / d["ms"] if d["ms"] else None
+    share = {k: v["ms"] / total_ms for k, v in by_kind.items()}
+    return roof, share
+
+
+def plan_inputs(tn, args, wl, cfg):
+    """(L, T, O, tree, sliced, stats, how): the stored tree unless a fresh
+    search is asked for."""
+    if args.choose_open:
+        # the paper's choice: the open qubits behind a small first cut
+        cfg["open_qubits"] = tn.choose_open_qubits(
+            cfg["circuit"], len(cfg["open_qubits"]),
+            tn.search_opts(**dict(wl["search"], trials=64), method="bipartition"))[0]
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    stored = None
+    if args.search_method is None and wl["tree"]:
+        from paper_2103_03074_gb300.trees import make_trees
+        stored = make_trees.load(wl["tree"], L, O)
+    if stored is not None:
+        tree, sliced, st = stored
+        how = f"stored tree paper_2103_03074_gb300/trees/{wl['tree']}.json"
+    else:
+        method = args.search_method or "greedy"
+        search = dict(wl["search"], seed=args.seed) if args.seed is not None else dict(wl["search"])
+        tree, sliced, st = tn.find_order(L, O, tn.search_opts(**search, method=method, objective=args.objective,
+                                                              rank_form="fp16x3" if args.form == "all"
+                                                              else args.form))
+        how = f"fresh search ({method}, {args.objective})"
+    if args.branch_merge:
+        tree, _ = tn.merge_branches(L, O, sliced, tree)
+    return L, T, O, tree, sliced, st, how
+
+
+def cfg5_sample(tn, torch, stream, pk, n_slices=4):
+    """The 20-cycle, 21-open-qubit workload on its stored tree: FP16X3 against
+    plain FP32 on the same slices [0, n_slices) (one block), device time of
+    one contraction after one warm-up; no oracle value exists at this size,
+    so the split form is compared with FP32.  Returns a dict (or an error)."""
+    import numpy as np
+    try:
+        cfg = workload("syc53_m20")
+        wl = WORKLOADS["syc53_m20"]
+        L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+        from paper_2103_03074_gb300.trees import make_trees
+        stored = make_trees.load(wl["tree"], L, O)
+        if stored is None:
+            return {"error": "no stored tree"}
+        tree, sliced, st = stored
+        n_total = 1 << len(sliced)
+        out = {"workload": wl["desc"].split(",")[0] + f", slices 0..{n_slices - 1} of {n_total} (stored tree)",
+               "log2_macs_per_slice": st["log2_slice"]}
+        amps = {}
+        for form in ("fp16x3", "fp32"):
+            plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1))
+            stats = plan.stats()
+            amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+            with Clocks(torch.cuda.current_device()) as clk:
+                ms = time_steps(torch, plan, [(0, n_slices)], amp, 1, 1, stream, l2_flush_buffer(torch), len(O),
+                                cfg["circuit"].n_qubits, torch.zeros(3, dtype=torch.float64, device="cuda"))[0]
+            macs = stats["macs_batch"] * (n_slices / stats["slices_per_batch"]) + stats["macs_prologue"]
+            amps[form] = amp.cpu().numpy()
+            out[form] = {"ms": ms, "slices_per_s": n_slices / (ms / 1e3),
+                         "complex_tflops": 8 * macs / (ms / 1e3) / 1e12,
+                         "extrapolated_full_s": n_total * ms / 1e3 / n_slices, "clocks": clk.summary()}
+            plan.close()
+            del amp
+            torch.cuda.empty_cache()
+        a, b = amps["fp16x3"], amps["fp32"]
+        out["fp16x3_vs_fp32_rel_l2"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        out["speedup_fp16x3_over_fp32"] = out["fp32"]["ms"] / out["fp16x3"]["ms"]
+        return out
+    except Exception as exc:
+        return {"error": str(exc)[:300]}
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build_library()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_2103_03074_gb300 as tn
+
+    pk = peaks()
+    wl = WORKLOADS[args.workload]
+    big = args.workload in ("syc53_m14", "syc53_m20")
+    cfg = workload(args.workload, instance_seed_offset(rank))
+    n_qubits = cfg["circuit"].n_qubits
+    n_open = len(cfg["open_qubits"])
+    L, T, O, tree, sliced, st, how = plan_inputs(tn, args, wl, cfg)
+    n_total = 1 << len(sliced)
+    n_slices = min(n_total, wl["step_slices"] or n_total)
+    ranges = [(0, n_slices)]
+    forms = [args.form] if args.form != "all" else wl["forms"]
+    golden = None
+    if wl["golden"] and instance_seed_offset(rank) == 0 and not args.choose_open:
+        golden = load_golden_amplitudes(wl["golden"])
+    stream = torch.cuda.Stream()
+    flush = l2_flush_buffer(torch)
+    amp = torch.zeros(2 << n_open, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    results = {}
+    plans = {}
+    for form in forms:
+        try:
+            plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1))
+        except tn.TNError as e:
+            results[form] = {"error": str(e)}
+            continue
+        stats = plan.stats()
+        macs_step = stats["macs_batch"] * (n_slices / stats["slices_per_batch"]) + stats["macs_prologue"]
+        # FP32 (CUDA cores) is several times slower: on the 53-qubit steps it
+        # gets 3 timed steps, the split forms the full count
+        steps = args.steps if (form != "fp32" or not big) else min(args.steps, 3)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            times = time_steps(torch, plan, ranges, amp, steps, args.warmup if steps == args.steps else 1, stream,
+                               flush, n_open, n_qubits, d_out)
+        ms = max_over_ranks(sum(times), world, device="cuda")
+        per_step = ms / steps
+        err = None
+        if golden is not None:
+            a = amp.cpu().numpy()
+            got = (a[0::2] + 1j * a[1::2])[golden[0]]
+            err = float(np.linalg.norm(got - golden[1]) / np.linalg.norm(golden[1]))
+        res = {"ms_per_step": per_step, "steps": steps, "slices_per_s": world * n_slices / (per_step / 1e3),
+               "rel_l2_err": err, "complex_tflops": world * 8 * macs_step / (per_step / 1e3) / 1e12,
+               "clocks": clk.summary(), "plan": stats, "macs_per_step": macs_step,
+               "launches_per_step": stats["launches_prologue"] + stats["launches_batch"] *
+               (n_slices / stats["slices_per_batch"]) + 2}
+        res["roofline"], res["kernel_time_share"] = profile_roofline(
+            tn, torch, L, T, O, sliced, tree, form, ranges[0], amp, stream, pk, 1 if big else min(steps, 5),
+            dump=args.dump_profile)
+        res["step_roofline"] = step_roofline(tn, L, O, sliced, tree, form, stats["slices_per_batch"], n_slices,
+                                             per_step)
+        results[form] = res
+        if big:
+            plan.close()  # the 53-qubit arenas are tens of GB each
+            torch.cuda.empty_cache()
+        else:
+            plans[form] = plan
+    ok = [f for f in forms if "error" not in results[f]]
+    if not ok:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "error": {f: results[f]["error"] for f in forms}}))
+        return 1
+    # headline: the fastest form that meets the 1e-5 bound by construction
+    # (22+ significant bits per operand) and, where an oracle value exists,
+    # by measurement; BF16x3 (16 bits) and FP16S never
+    within = [f for f in ok if f in ACCURATE_FORMS and
+              (results[f]["rel_l2_err"] is None or results[f]["rel_l2_err"] <= 1e-5)]
+    best = max(within or ok, key=lambda f: results[f]["slices_per_s"])
+    r = results[best]
+    # end to end through the C-ABI with host buffers (tn_contract_slices_host)
+    plan = plans.get(best) or tn.Plan(L, T, O, sliced, tree, form=best, opts=tn.plan_opts(use_graph=1))
+    data = np.concatenate([np.stack([np.asarray(t, np.complex64).reshape(-1).real,
+                                     np.asarray(t, np.complex64).reshape(-1).imag], 1).reshape(-1)
+                           for t in T]).astype(np.float32)
+    h_in = torch.from_numpy(data).pin_memory()
+    h_amp = torch.empty(2 << n_open, dtype=torch.float64).pin_memory()
+    h_stats = torch.empty(3, dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):
+        plan.contract_host(0, n_slices, h_in, n_qubits, h_amp, h_stats, stream)
+    e2e_steps = r["steps"]
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.contract_host(0, n_slices, h_in, n_qubits, h_amp, h_stats, stream)
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world, device="cuda") / e2e_steps
+    e2e = {"value": world * n_slices / (e2e_ms / 1e3), "unit": "slices/s", "form": best,
+           "h2d_bytes_per_step": int(data.nbytes), "d2h_bytes_per_step": int(h_amp.numel() * 8 + 24),
+           "api": "tn_contract_slices_host (leaf values in, amplitudes and P(s1)/XEB/max p out, host buffers)"}
+    for p in plans.values():
+        p.close()
+    if best not in plans:
+        plan.close()
+    torch.cuda.empty_cache()
+    cfg5 = None
+    if args.workload == "syc53_m14" and not args.no_cfg5 and world == 1:
+        cfg5 = cfg5_sample(tn, torch, stream, pk)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, sliced, n_slices)
+    split = [f for f in ok if f != "fp32" and f in ACCURATE_FORMS]
+    line = {
+        "metric": METRIC, "value": r["slices_per_s"], "unit": "slices/s", "n_gpus": world, "steps": r["steps"],
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[best],
+        "data": "synthetic (seeded Sycamore-style circuit, random bitstring)",
+        "config": {"workload": wl["desc"], "form": best,
+                   "step": f"{n_slices} of {n_total} slices summed in FP64 + probabilities/XEB",
+                   "full_slice_count": n_total, "tree": how,
+                   "executor": "CUDA-graph replay of the prologue and per-block body",
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed events); the "
+                         "53-qubit intermediates are far larger than L2",
+                   "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
+                   "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],
+                   "arena_bytes": r["plan"]["arena_bytes"],
+                   "open_qubits": cfg["open_qubits"] if args.choose_open else "fixed (the workload's)",
+                   "branch_merge": bool(args.branch_merge)},
+        "complex_tflops": r["complex_tflops"],
+        "rel_l2_err_vs_fp64_oracle": r["rel_l2_err"],
+        "split_vs_fp32": ({"split_form": max(split, key=lambda f: results[f]["slices_per_s"]),
+                           "speedup": max(results[f]["slices_per_s"] for f in split) /
+                           results["fp32"]["slices_per_s"]} if split and "fp32" in ok else None),
+        "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
+                       "rel_l2_err_vs_fp64_oracle": results[f]["rel_l2_err"], "steps": results[f]["steps"],
+                       "ms_per_step": results[f]["ms_per_step"], "roofline": results[f]["roofline"],
+                       "kernel_time_share": results[f]["kernel_time_share"],
+                       "step_roofline": results[f].get("step_roofline")}
+                      if "error" not in results[f] else results[f]) for f in forms},
+        "roofline": r["roofline"],
+        "step_roofline": r.get("step_roofline"),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": r["clocks"],
+        "gpu_launches": int(r["launches_per_step"] * r["steps"]),
+        "syc53_m20": cfg5,
+    }
+    if n_slices < n_total:
+        line["extrapolated_full_s"] = n_total / r["slices_per_s"]
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
 
 
 def run_batch(args):
@@ -311,7 +742,8 @@ def run_batch(args):
     nets = []
     for m in members:
         L, T, O = tn.circuit_network(m["circuit"], m["fixed_bits"], m["open_qubits"])
-        tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=32, n_sliced=m["n_sliced"], method=args.search_method))
+        tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=32, n_sliced=m["n_sliced"],
+                                                              method=args.search_method or "greedy"))
         nets.append((L, T, O, tree, sliced, st))
     n_slices = sum(1 << len(x[4]) for x in nets)
     macs = sum((1 << len(x[4])) * 2.0 ** x[5]["log2_slice"] for x in nets)
@@ -349,237 +781,55 @@ def run_batch(args):
     r = results[best]
     line = {"metric": METRIC, "value": r["slices_per_s"], "unit": "slices/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": best, "data": "synthetic (seeded Sycamore-style circuits, random bitstrings)",
+            "vs_baseline": None, "dtype": DTYPE[best],
+            "data": "synthetic (seeded Sycamore-style circuits, random bitstrings)",
             "config": {"workload": BATCH_DESC, "form": best, "circuits": len(members), "slices_per_step": n_slices,
                        "complex_macs_per_step": macs,
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
-                       "order_search": args.search_method},
+                       "order_search": args.search_method or "greedy"},
             "complex_tflops": r["complex_tflops"], "forms": results, "clocks": r["clocks"],
             "roofline": None, "cpu_baseline": None, "e2e": None}
     print(json.dumps(line))
     return 0
 
 
-def run_native(args):
+def run_gemm(args):
+    """One batched complex GEMM step C[h,m,n] = sum_k A[h,m,k] B[h,k,n] of log2
+    shape --gemm H,M,K,N through a two-tensor plan (the h labels sliced and
+    kept as batch labels): mean device time per contraction and its complex
+    and tensor-core flop rates."""
     import numpy as np
     import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
-    if rank == 0:
-        __graft_entry__.build_library()
-    if world > 1:
-        torch.distributed.barrier()
+    __graft_entry__.build_library()
     import paper_2103_03074_gb300 as tn
-
-    pk = peaks()
-    wl = WORKLOADS[args.workload]
-    big = args.workload in ("syc53_m14", "syc53_m20")
-    cfg = workload(args.workload, instance_seed_offset(rank))
-    n_qubits = cfg["circuit"].n_qubits
-    n_open = len(cfg["open_qubits"])
-    if args.choose_open:
-        # the paper's choice: the open qubits behind a small first cut, the
-        # cheapest to contract of the smallest cuts (tn_choose_open_qubits)
-        cfg["open_qubits"] = tn.choose_open_qubits(
-            cfg["circuit"], n_open, tn.search_opts(**dict(wl["search"], trials=64), method="bipartition"))[0]
-    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    search = dict(wl["search"], seed=args.seed) if args.seed is not None else wl["search"]
-    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**search, method=args.search_method,
-                                                          objective=args.objective,
-                                                          rank_form="bf16x3" if args.form == "all" else args.form))
-    if args.branch_merge:
-        tree, _ = tn.merge_branches(L, O, sliced, tree)
-    n_total = 1 << len(sliced)
-    n_slices = min(n_total, wl["timed_slices"] or n_total)
-    if args.form != "all":
-        forms = [args.form]
-    elif args.workload == "syc53_m20":
-        forms = ["tf32x3", "fp16x3"]  # a 64-slice step takes tens of seconds per form
-    else:
-        forms = ["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"]
-    golden = None
-    if wl["golden"] and rank == 0 and instance_seed_offset(rank) == 0 and not args.choose_open:
-        golden = load_golden_amplitudes(wl["golden"])
+    h, m, k, n = (int(x) for x in args.gemm.split(","))
+    form = "fp16x3" if args.form == "all" else args.form
+    rng = np.random.default_rng(0)
+    hl, ml, kl, nl = (list(range(b, b + c)) for b, c in ((300, h), (0, m), (100, k), (200, n)))
+    A = (rng.standard_normal(2 ** (h + m + k)) + 1j * rng.standard_normal(2 ** (h + m + k))).astype(np.complex64)
+    B = (rng.standard_normal(2 ** (h + k + n)) + 1j * rng.standard_normal(2 ** (h + k + n))).astype(np.complex64)
+    plan = tn.Plan([hl + ml + kl, hl + kl + nl], [A.reshape((2,) * (h + m + k)), B.reshape((2,) * (h + k + n))],
+                   ml + nl, hl, [(0, 1)], form=form, opts=tn.plan_opts(use_graph=1))
+    amp = torch.zeros(2 << (m + n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    flush = l2_flush_buffer(torch)
-    amp = torch.zeros(2 << n_open, dtype=torch.float64, device="cuda")
-    d_out = torch.zeros(3, dtype=torch.float64, device="cuda")
-    results = {}
-    for form in forms:
-        try:
-            plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1))
-        except tn.TNError as e:
-            results[form] = {"error": str(e)}
-            continue
-        stats = plan.stats()
-        macs_step = stats["macs_batch"] * (n_slices / stats["slices_per_batch"]) + stats["macs_prologue"]
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        with Clocks(local) as clk:
-            ms = time_steps(torch, plan, n_slices, amp, args.steps, args.warmup, stream, flush, n_open,
-                            n_qubits, d_out)
-        ms = max_over_ranks(ms, world, device="cuda")
-        per_step = ms / args.steps
-        err = None
-        if golden is not None:
-            a = amp.cpu().numpy()
-            got = (a[0::2] + 1j * a[1::2])[golden[0]]
-            err = float(np.linalg.norm(got - golden[1]) / np.linalg.norm(golden[1]))
-        res = {"ms_per_step": per_step, "slices_per_s": world * n_slices / (per_step / 1e3), "rel_l2_err": err,
-               "complex_tflops": world * 8 * macs_step / (per_step / 1e3) / 1e12, "clocks": clk.summary(),
-               "plan": stats, "macs_per_step": macs_step,
-               "launches_per_step": stats["launches_prologue"] + stats["launches_batch"] *
-               (n_slices / stats["slices_per_batch"]) + 2}
-        # roofline: per-op CUDA events (step-timing recorder) over the same steps
-        pplan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(profile=1))
-        prof_steps = 1 if big else args.steps
-        with torch.cuda.stream(stream):
-            for _ in range(1 if big else args.warmup):
-                pplan.contract(0, n_slices, amp, stream)
-            pplan.profile(reset=True)
-            for _ in range(prof_steps):
-                pplan.contract(0, n_slices, amp, stream)
-        rows = pplan.profile()
-        pplan.close()
-        if args.dump_profile:
-            with open(f"{args.dump_profile}.{form}.json", "w") as f:
-                json.dump({"steps": prof_steps, "rows": rows}, f)
-        by_kind = {}
-        for r in rows:
-            d = by_kind.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "macs": 0.0, "bytes": 0.0, "t_roof": 0.0})
-            d["ms"] += r["ms"]
-            d["launches"] += r["launches"]
-            d["macs"] += r["macs"] * r["launches"]
-            d["bytes"] += r["bytes"] * r["launches"]
-            d["t_roof"] += r["launches"] * roofline_ms(r, form, pk)
-        total_ms = sum(d["ms"] for d in by_kind.values())
-        top = max(by_kind, key=lambda k: by_kind[k]["ms"])
-        d = by_kind[top]
-        avg_ms = d["ms"] / max(d["launches"], 1)
-        if top == "gemm" and form == "fp32":
-            peak = fp32_alu_peak_tflops(pk["sm_max_mhz"])
-            achieved = 8 * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "gemm_f32_kernel (complex FP32 FMA)",
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
-        elif top == "gemm":
-            # split form: tensor-core flops the method issues per complex MAC
-            # (4 real products x 3 split products x 2 flops); TF32 peak = half
-            # of the measured BF16 peak (nominal dense ratio 1.1 : 2.25)
-            per_mac = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16x3": 24.0, "fp16s": 8.0}[form]  # fp16s: 4 products
-            peak = pk["bf16_tflops"] * ({"bf16x3": 1.0, "tf32x3": 0.5, "fp16x3": 1.0, "fp16s": 1.0}[form])
-            achieved = per_mac * d["macs"] / d["launches"] / (avg_ms / 1e3) / 1e12
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "tc_gemm (tcgen05 split form)",
-                    "peak_source": pk["source"]}
-        else:
-            achieved = d["bytes"] / d["launches"] / (avg_ms / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": top, "peak_source": pk["source"]}
-        roof["share_of_step"] = d["ms"] / total_ms if total_ms else None
-        roof["launches_per_step"] = d["launches"] / prof_steps
-        # per-launch roofline time (bytes over HBM bandwidth or flops over
-        # the unit's peak, whichever is larger) summed over the class's
-        # launches, over their measured time: meaningful where a class mixes
-        # bandwidth-bound and arithmetic-bound launches (the small steps)
-        roof["roofline_time_frac"] = d["t_roof"] / d["ms"] if d["ms"] else None
-        res["roofline"] = roof
-        res["kernel_time_share"] = {k: v["ms"] / total_ms for k, v in by_kind.items()}
-        res["step_roofline"] = step_roofline(tn, L, O, sliced, tree, form, stats["slices_per_batch"], n_slices,
-                                             per_step)
-        # end to end through the C-ABI with host buffers
-        if big:
-            res["e2e"] = None
-            results[form] = res
-            plan.close()
-            continue
-        data = np.concatenate([np.stack([np.asarray(t, np.complex64).reshape(-1).real,
-                                         np.asarray(t, np.complex64).reshape(-1).imag], 1).reshape(-1)
-                               for t in T]).astype(np.float32)
-        h_in = torch.from_numpy(data).pin_memory()
-        h_out = torch.empty(2 << n_open, dtype=torch.float64).pin_memory()
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                plan.update_data(h_in, stream)
-                amp.zero_()
-                plan.contract(0, n_slices, amp, stream)
-                tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
-                h_out.copy_(amp, non_blocking=True)
-            stream.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                plan.update_data(h_in, stream)
-                amp.zero_()
-                plan.contract(0, n_slices, amp, stream)
-                tn.probabilities_xeb(amp, n_open, n_qubits, d_out=d_out, stream=stream, sync=False)
-                h_out.copy_(amp, non_blocking=True)
-            e1.record(stream)
-            stream.synchronize()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, device="cuda") / args.steps
-        res["e2e"] = {"value": world * n_slices / (e2e_ms / 1e3), "unit": "slices/s",
-                      "h2d_bytes_per_step": int(data.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 8)}
-        results[form] = res
-        plan.close()
-    ok = [f for f in forms if "error" not in results[f]]
-    if not ok:
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "error": {f: results[f]["error"] for f in forms}}))
-        return 1
-    # headline: the fastest form that meets the 1e-5 amplitude error bound
-    # by construction (22+ significant bits per operand) and, where an
-    # oracle value exists, by measurement; BF16x3 (16 bits) and FP16S never
-    within = [f for f in ok if f in ACCURATE_FORMS and
-              (results[f]["rel_l2_err"] is None or results[f]["rel_l2_err"] <= 1e-5)]
-    best = max(within or ok, key=lambda f: results[f]["slices_per_s"])
-    r = results[best]
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not big:
-        rate, sample, cores = cpu_oracle_rate(cfg, sliced)
-        cpu = {"value": rate, "unit": "slices/s", "cores": cores, "kind": "oracle", "sample": sample}
-    line = {
-        "metric": METRIC, "value": r["slices_per_s"], "unit": "slices/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)",
-                                       "tf32x3": "tf32x3", "fp16x3": "fp16x3 (scaled, fp32 accumulate)",
-                                       "fp16s": "f16"}[best],
-        "data": "synthetic (seeded Sycamore-style circuit, random bitstring)",
-        "config": {"workload": wl["desc"], "form": best,
-                   "step": f"{n_slices} of {n_total} slices summed in FP64 + probabilities/XEB",
-                   "full_slice_count": n_total,
-                   "executor": "CUDA-graph replay of the prologue and per-block body",
-                   "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
-                   "complex_macs_per_step": r["macs_per_step"], "log2_macs_per_slice": st["log2_slice"],
-                   "log2_width_per_slice": st["log2_width"], "slices_per_batch": r["plan"]["slices_per_batch"],
-                   "arena_bytes": r["plan"]["arena_bytes"], "order_search": args.search_method,
-                   "order_objective": args.objective, "order_seed": args.seed,
-                   "open_qubits": cfg["open_qubits"] if args.choose_open else "fixed (the workload's)",
-                   "branch_merge": bool(args.branch_merge)},
-        "complex_tflops": r["complex_tflops"],
-        "forms": {f: ({"slices_per_s": results[f]["slices_per_s"], "complex_tflops": results[f]["complex_tflops"],
-                       "rel_l2_err_vs_fp64_oracle": results[f]["rel_l2_err"],
-                       "ms_per_step": results[f]["ms_per_step"], "roofline": results[f]["roofline"],
-                       "kernel_time_share": results[f]["kernel_time_share"],
-                       "step_roofline": results[f].get("step_roofline")}
-                      if "error" not in results[f] else results[f]) for f in forms},
-        "roofline": r["roofline"],
-        "step_roofline": r.get("step_roofline"),
-        "cpu_baseline": cpu,
-        "e2e": r["e2e"],
-        "clocks": r["clocks"],
-        "gpu_launches": int(r["launches_per_step"] * args.steps),
-    }
-    if n_slices < n_total:
-        line["extrapolated_full_s"] = n_total / r["slices_per_s"]
-    if rank == 0:
-        print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.contract(0, 1 << h, amp, stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.contract(0, 1 << h, amp, stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    macs = 2.0 ** (h + m + k + n)
+    print(json.dumps({"gemm": {"log2_hmkn": [h, m, k, n], "form": form}, "ms_per_contraction": ms,
+                      "complex_tflops": 8 * macs / (ms / 1e3) / 1e12,
+                      "tensor_tflops": TC_FLOPS_PER_MAC.get(form, 8.0) * macs / (ms / 1e3) / 1e12,
+                      "plan": plan.describe()}))
+    plan.close()
     return 0
 
 
@@ -590,12 +840,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "all"])
-    ap.add_argument("--workload", default="rect5x6", choices=sorted(WORKLOADS) + ["batch256"])
-    ap.add_argument("--search-method", default="greedy", choices=["greedy", "bipartition", "mixed"],
-                    help="order-search trials: randomised greedy (default), hierarchical bipartition, or both")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256", "gemm"])
+    ap.add_argument("--gemm", default="0,15,11,9", help="--workload gemm: log2 H,M,K,N")
+    ap.add_argument("--search-method", default=None, choices=["greedy", "bipartition", "mixed"],
+                    help="search a fresh tree (randomised greedy, hierarchical bipartition, or both) instead of "
+                         "the workload's stored tree")
     ap.add_argument("--objective", default="macs", choices=["macs", "roofline"],
-                    help="rank the search's trees by total MACs (default) or by the roofline time of their "
-                         "compiled plan (tn_estimate_tree_ms) for --form (bf16x3 with --form all)")
+                    help="with --search-method: rank the search's trees by total MACs (default) or by the roofline "
+                         "time of their compiled plan (tn_estimate_tree_ms) for --form (fp16x3 with --form all)")
     ap.add_argument("--seed", type=int, default=None, help="order-search seed (default: the library's)")
     ap.add_argument("--choose-open", action="store_true",
                     help="take the open qubits behind a small first cut (tn_choose_open_qubits) instead of the "
@@ -603,14 +855,25 @@ def main():
     ap.add_argument("--branch-merge", action="store_true",
                     help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cfg5", action="store_true", help="skip the 20-cycle sample of the default line")
     ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-budget", type=float, default=10.0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-sliced", default="[]", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-n-slices", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:
+        return run_oracle_sample(args)
     if args.warmup < 3:
         args.warmup = 3
+    if args.choose_open and args.search_method is None:
+        args.search_method = "bipartition"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch256":
         return run_batch(args)
+    if args.workload == "gemm":
+        return run_gemm(args)
     return run_native(args)
 
 

@@ -181,6 +181,25 @@ int tn_contract_slices(tn_plan_t plan, int64_t slice_begin, int64_t slice_end, d
                        tn_stream_t stream);
 
 /*
+ * The sliced contraction with host buffers ("Dynamic slicing": slices
+ * [slice_begin, slice_end) summed in FP64), for callers that keep their data
+ * on the host: copies new leaf values in (h_data, host complex64 interleaved
+ * in tn_plan_create's concatenated layout, the plan's leaf count of values;
+ * NULL keeps the current values), zeroes a plan-owned device amplitude
+ * tensor, contracts the range into it, and when h_stats is given computes
+ * the probabilities' sums of Eq. 1 on the device (h_stats[3] = {P(s1),
+ * linear XEB, max p} for n_qubits qubits); then copies the amplitudes to
+ * h_amp (host complex128, 2^n_open entries; may be NULL) and synchronises the
+ * stream.  Pinned host memory makes the copies asynchronous to the host up to
+ * that synchronisation.  The first call allocates the plan's device
+ * amplitude tensor (2^n_open x 16 bytes + 24 bytes).
+ * Errors: as tn_contract_slices, TN_ERR_ARG (n_qubits < n_open with
+ * h_stats), TN_ERR_OOM.
+ */
+int tn_contract_slices_host(tn_plan_t plan, int64_t slice_begin, int64_t slice_end, const float *h_data,
+                            int n_qubits, double *h_amp, double *h_stats, tn_stream_t stream);
+
+/*
  * Amplitudes of a circuit over its open qubits (the big-head problem of the
  * "Big-head simulation" section): build the network (single-qubit gates
  * absorbed into two-qubit gates, boundary vectors absorbed), search an order

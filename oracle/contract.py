@@ -107,6 +107,20 @@ def contract(labels: Sequence[Sequence[int]], tensors: Sequence[np.ndarray],
     """Contract the network (with ``fixed`` labels held at their values) and
     return a complex128 array of shape (2,)*len(open_labels), axes in the order
     of ``open_labels``."""
+    it = contract_iter(labels, tensors, open_labels, fixed, tree)
+    while True:
+        try:
+            next(it)
+        except StopIteration as done:
+            return done.value
+
+
+def contract_iter(labels, tensors, open_labels, fixed=None, tree=None):
+    """contract() as a generator: after each pairwise step it yields
+    (complex MACs of that step, complex MACs of the whole tree), where a pair
+    holding the labels U in total costs 2^|U| MACs (Fig. 3); its return value
+    (StopIteration.value) is contract()'s result.  Lets a caller time a
+    bounded part of a long contraction."""
     fixed = fixed or {}
     for lab in open_labels:
         if lab in fixed:
@@ -127,8 +141,18 @@ def contract(labels: Sequence[Sequence[int]], tensors: Sequence[np.ndarray],
             t = t.sum(axis=tuple(dang))
             l = [lab for a, lab in enumerate(l) if a not in dang]
             nodes[i] = (l, t)
+    # complex MACs of every step: 2^|labels of the pair|
+    sets = {i: set(l) for i, (l, _) in nodes.items()}
+    step_macs = []
     nxt = len(labs)
     for (a, b) in tree:
+        u = sets.pop(a) | sets.pop(b)
+        step_macs.append(2.0 ** len(u))
+        sets[nxt] = {lab for lab in u if lab in open_set or sum(lab in s2 for s2 in sets.values()) > 0}
+        nxt += 1
+    total_macs = float(sum(step_macs))
+    nxt = len(labs)
+    for t, (a, b) in enumerate(tree):
         la, ta = nodes.pop(a)
         lb, tb = nodes.pop(b)
         shared = [lab for lab in la if lab in lb and lab not in open_set]
@@ -138,6 +162,7 @@ def contract(labels: Sequence[Sequence[int]], tensors: Sequence[np.ndarray],
         lc = [lab for lab in la if lab not in shared] + [lab for lab in lb if lab not in shared]
         nodes[nxt] = (lc, tc)
         nxt += 1
+        yield step_macs[t], total_macs
     # any disconnected leftovers: outer products
     items = list(nodes.values())
     lc, tc = items[0]

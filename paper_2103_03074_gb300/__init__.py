@@ -52,6 +52,7 @@ _lib.tn_last_error.restype = ctypes.c_char_p
 _lib.tn_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int,
                                 _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(PlanOpts)]
 _lib.tn_contract_slices.argtypes = [_vp, _i64, _i64, _vp, _vp]
+_lib.tn_contract_slices_host.argtypes = [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp]
 _lib.tn_amplitudes.argtypes = [ctypes.POINTER(Circuit), _vp, ctypes.c_int, _vp, ctypes.c_int,
                                ctypes.POINTER(SearchOpts), ctypes.POINTER(PlanOpts), _vp, _vp]
 _lib.tn_probabilities_xeb.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
@@ -101,7 +102,7 @@ EXPORTED = ["tn_plan_create", "tn_contract_slices", "tn_amplitudes", "tn_probabi
             "tn_plan_op_features", "tn_plan_autotune", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
             "tn_postselect_xeb", "tn_conditional_sample", "tn_probability_histogram", "tn_plan_describe",
             "tn_find_order_head_tail", "tn_head_tail_amplitudes", "tn_merge_branches", "tn_estimate_tree_ms", "tn_choose_open_qubits",
-            "tn_open_qubit_candidates", "tn_describe_tree", "tn_slice_tree", "tn_slice_stage2"]
+            "tn_open_qubit_candidates", "tn_contract_slices_host", "tn_describe_tree", "tn_slice_tree", "tn_slice_stage2"]
 PROFILE_KINDS = {0: "small", 1: "permute", 2: "gemm", 3: "extract", 4: "accumulate", 5: "split", 6: "maxabs"}
 
 
@@ -119,6 +120,17 @@ def _check(rc, where):
 
 def _ptr(a):
     return a.ctypes.data_as(_vp) if a is not None else None
+
+
+def _host_ptr(a):
+    """Host address of a numpy array or a CPU torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(_vp)
+    if getattr(a, "is_cuda", False):
+        raise ValueError("expected a host buffer")
+    return ctypes.c_void_p(a.data_ptr())
 
 
 def _stream_ptr(stream):
@@ -422,6 +434,15 @@ class Plan:
     def contract_ptr(self, begin, end, d_amp_ptr, stream_ptr=None):
         _check(_lib.tn_contract_slices(self._h, int(begin), int(end), _vp(d_amp_ptr),
                                        _vp(stream_ptr) if stream_ptr else None), "tn_contract_slices")
+
+    def contract_host(self, begin, end, h_data=None, n_qubits=0, h_amp=None, h_stats=None, stream=None):
+        """tn_contract_slices_host: host buffers in and out (numpy arrays or
+        pinned CPU tensors): optional new leaf values (float32), amplitudes
+        (float64, 2 << n_open) and {P(s1), XEB, max p} (float64, 3).
+        Synchronises the stream."""
+        _check(_lib.tn_contract_slices_host(self._h, ctypes.c_int64(int(begin)), ctypes.c_int64(int(end)),
+                                            _host_ptr(h_data), int(n_qubits), _host_ptr(h_amp),
+                                            _host_ptr(h_stats), _stream_ptr(stream)), "tn_contract_slices_host")
 
     def update_data(self, data_f32, stream=None):
         """Async H2D copy of new leaf values (flat interleaved complex64, host)."""

@@ -204,6 +204,7 @@ struct tn_plan {
     // device
     float2 *d_leaves = nullptr;
     char *d_arena = nullptr;
+    double *d_host_amp = nullptr;  // tn_contract_slices_host: amplitudes + 3 statistics
     tn::ExtractEntry *d_extract = nullptr;
     bool failed = false;
     // stats
@@ -1734,6 +1735,43 @@ extern "C" int tn_plan_op_features(tn_plan_t P, float *out, int max_ops) {
     return n;
 }
 
+extern "C" int tn_contract_slices_host(tn_plan_t P, int64_t begin, int64_t end, const float *h_data, int n_qubits,
+                                       double *h_amp, double *h_stats, tn_stream_t stream) {
+    if (!P) return fail(TN_ERR_ARG, "plan is NULL");
+    if (h_stats && n_qubits < P->n_open) return fail(TN_ERR_ARG, "n_qubits < n_open");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n_amp = (int64_t)1 << P->n_open;
+    if (!P->d_host_amp) {
+        cudaError_t e = cudaMalloc(&P->d_host_amp, sizeof(double) * (2 * n_amp + 3));
+        if (e != cudaSuccess) {
+            P->d_host_amp = nullptr;
+            cudaGetLastError();
+            return fail(TN_ERR_OOM, "tn_contract_slices_host: device amplitude tensor");
+        }
+    }
+    int rc = TN_OK;
+    if (h_data) rc = tn_plan_update_data(P, h_data, stream);
+    if (rc) return rc;
+    cudaError_t e = launch_zero_f64(P->d_host_amp, 2 * n_amp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tn_contract_slices_host");
+    rc = tn_contract_slices(P, begin, end, P->d_host_amp, stream);
+    if (rc) return rc;
+    double *d_stats = P->d_host_amp + 2 * n_amp;
+    if (h_stats) {
+        e = launch_prob_xeb(reinterpret_cast<const double2 *>(P->d_host_amp), n_amp, nullptr, d_stats,
+                            n_qubits - P->n_open, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_stats, d_stats, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tn_contract_slices_host: probabilities");
+    }
+    if (h_amp) {
+        e = cudaMemcpyAsync(h_amp, P->d_host_amp, sizeof(double) * 2 * n_amp, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tn_contract_slices_host: copy out");
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "tn_contract_slices_host");
+    return TN_OK;
+}
+
 extern "C" int tn_plan_update_data(tn_plan_t P, const float *data, tn_stream_t stream) {
     if (!P || !data) return fail(TN_ERR_ARG, "NULL argument");
     cudaError_t e = cudaMemcpyAsync(P->d_leaves, data, P->leaf_bytes, cudaMemcpyHostToDevice,
@@ -1746,6 +1784,7 @@ extern "C" void tn_plan_destroy(tn_plan_t P) {
     if (!P) return;
     if (P->d_leaves) cudaFree(P->d_leaves);
     if (P->d_arena) cudaFree(P->d_arena);
+    if (P->d_host_amp) cudaFree(P->d_host_amp);
     if (P->d_extract) cudaFree(P->d_extract);
     for (auto &ev : P->prof_ev) cudaEventDestroy(ev);
     if (P->g_pro) cudaGraphExecDestroy(P->g_pro);

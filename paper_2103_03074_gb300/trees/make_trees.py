@@ -1,0 +1,79 @@
+"""Write the stored contraction trees that bench.py and the GPU tests run.
+
+A tree search is seeded and deterministic, but its floating-point cost
+comparisons may break ties differently on another CPU architecture, so the
+trees the measurements use are searched once and stored here.  Each JSON file
+holds the search options, the SSA tree, the sliced labels, the search's
+statistics and a signature of the network (tensor count and a digest of the
+label lists) that the loader checks.
+
+    python paper_2103_03074_gb300/trees/make_trees.py [name ...]
+
+Names: rect5x6 (30-qubit 5x6 grid, 12 cycles, 8 open, 8 sliced bonds; 16384
+randomised greedy trials ranked by complex MACs), syc53_m14 (53-qubit rotated
+lattice, 14 cycles, 16 open, cap 2^30) and syc53_m20 (20 cycles, 21 open, cap
+2^31); the 53-qubit ones from 1024 hierarchical bipartition trials ranked by
+their FP16X3 plan's roofline time.
+"""
+import hashlib
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+RECIPES = {
+    "rect5x6": dict(cfg=2, search=dict(trials=16384, n_sliced=8)),
+    "syc53_m14": dict(cfg=4, search=dict(trials=1024, log2_cap=30, method="bipartition", objective="roofline",
+                                         rank_form="fp16x3")),
+    "syc53_m20": dict(cfg=5, search=dict(trials=1024, log2_cap=31, method="bipartition", objective="roofline",
+                                         rank_form="fp16x3")),
+}
+
+
+def signature(labels, open_labels):
+    h = hashlib.sha256()
+    for l in labels:
+        h.update((",".join(map(str, l)) + ";").encode())
+    h.update(("|" + ",".join(map(str, open_labels))).encode())
+    return {"n_tensors": len(labels), "sha256": h.hexdigest()}
+
+
+def path_of(name):
+    return os.path.join(HERE, f"{name}.json")
+
+
+def load(name, labels, open_labels):
+    """(tree, sliced, stats) of the stored tree `name`, or None when there is
+    no file or it was made for another network."""
+    p = path_of(name)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d["signature"] != signature(labels, open_labels):
+        return None
+    return [tuple(x) for x in d["tree"]], list(d["sliced"]), d["stats"]
+
+
+def make(name):
+    import paper_2103_03074_gb300 as tn
+    from tn_inputs.configs import make_config
+    r = RECIPES[name]
+    cfg = make_config(r["cfg"])
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, st = tn.find_order(L, O, tn.search_opts(**r["search"]))
+    d = {"name": name, "config": cfg["name"], "search": r["search"],
+         "signature": signature(L, O), "stats": {k: float(v) for k, v in st.items()},
+         "sliced": [int(x) for x in sliced], "tree": [[int(a), int(b)] for a, b in tree]}
+    with open(path_of(name), "w") as f:
+        json.dump(d, f, indent=None)
+        f.write("\n")
+    print(f"{name}: {len(sliced)} sliced, 2^{st['log2_slice']:.2f} MACs per slice, width 2^{st['log2_width']:.0f}")
+
+
+if __name__ == "__main__":
+    for n in sys.argv[1:] or sorted(RECIPES):
+        make(n)

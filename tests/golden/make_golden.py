@@ -4,7 +4,7 @@ Calls only ``oracle/`` (and the seeded inputs of ``tn_inputs``).  Each file
 holds one value per line: index, real part, imaginary part (repr of FP64),
 after a header that names the workload recipe.
 
-    python tests/golden/make_golden.py [cfg2] [cfg4]
+    python tests/golden/make_golden.py [cfg2] [cfg4] [cfg3]
 
 cfg2: the 30-qubit 5x6 grid, 12 cycles, 8 open qubits, 22 fixed bits; FP64
 Schroedinger state vector (16 GiB of host memory, several minutes on 8 cores).
@@ -15,6 +15,13 @@ computed one at a time: each entry is the fully closed network (open qubits
 set to that entry's bits) contracted by the oracle's own pairwise route in
 FP64 with its own greedy order (no slicing; about 25 GiB of host memory and
 several minutes per entry on 8 cores).  Lines are appended as they finish.
+
+cfg3: the batched workload's members of more than 20 qubits (those of 20 or
+fewer are checked against a live state vector in the tests).  Every member of
+up to 28 qubits, and a seeded sample of CFG3_SAMPLES_30 of the 30-qubit ones,
+get their full 2^k open-qubit amplitude tensor from the FP64 state vector
+(oracle.sv_native).  Lines: member index, amplitude index, real, imaginary;
+members are appended as they finish, cheapest first.
 """
 import os
 import sys
@@ -89,6 +96,53 @@ def cfg4():
         with open(path, "a") as f:
             f.write(f"{idx} {a.real!r} {a.imag!r}\n")
         print(f"cfg4 entry {idx}: {a} ({time.time() - t0:.0f} s)", flush=True)
+
+
+CFG3_SAMPLES_30 = 8
+CFG3_SAMPLE_SEED = 0x2103C3
+
+
+def cfg3_members():
+    """Indices of the batch members that get stored amplitudes: all of more
+    than 20 and at most 28 qubits, then a seeded sample of the 30-qubit
+    ones; ordered by qubit count (cheapest first)."""
+    from tn_inputs.configs import batch_recipes
+    rs = batch_recipes()
+    nq = [r["rows"] * r["cols"] for r in rs]
+    small = [i for i in range(len(rs)) if 20 < nq[i] <= 28]
+    big = [i for i in range(len(rs)) if nq[i] > 28]
+    rng = SplitMix64(CFG3_SAMPLE_SEED)
+    pick = []
+    while len(pick) < min(CFG3_SAMPLES_30, len(big)):
+        i = big[rng.below(len(big))]
+        if i not in pick:
+            pick.append(i)
+    return sorted(small, key=lambda i: (nq[i], i)) + pick
+
+
+def cfg3():
+    import time
+    from tn_inputs.configs import batch_recipes, make_batch_member
+    path = os.path.join(HERE, "cfg3_amplitudes.txt")
+    done = set()
+    if os.path.exists(path):
+        done = {int(l.split()[0]) for l in open(path) if not l.startswith("#")}
+    else:
+        with open(path, "w") as f:
+            f.write(f"# batch256 members of more than 20 qubits: all up to 28 qubits and {CFG3_SAMPLES_30} "
+                    f"seeded 30-qubit ones (sample_seed={CFG3_SAMPLE_SEED:#x}); member index, amplitude index, "
+                    "re, im; route=oracle.sv_native (FP64 state vector)\n")
+    rs = batch_recipes()
+    for i in cfg3_members():
+        if i in done:
+            continue
+        m = make_batch_member(rs[i])
+        t0 = time.time()
+        amp = sv_native.amplitudes(m["circuit"], m["fixed_bits"], m["open_qubits"])
+        with open(path, "a") as f:
+            for j, a in enumerate(amp):
+                f.write(f"{i} {j} {float(a.real)!r} {float(a.imag)!r}\n")
+        print(f"cfg3 member {i}: {m['circuit'].n_qubits} qubits ({time.time() - t0:.0f} s)", flush=True)
 
 
 if __name__ == "__main__":

@@ -44,3 +44,46 @@ def test_step_roofline_matches_the_estimate(tn, bench):
 def test_step_roofline_never_raises(tn, bench):
     r = bench.step_roofline(tn, [[0, 1], [1, 2]], [0, 2], [], [(0, 0)], "bf16x3", 1, 1, 1.0)
     assert set(r) == {"error"}
+
+
+@pytest.mark.parametrize("name,cfg_idx", [("rect5x6", 2), ("syc53_m14", 4), ("syc53_m20", 5)])
+def test_stored_trees_fit_their_networks(tn, name, cfg_idx):
+    """The trees bench.py runs by default are stored (their search's float
+    tie-breaks could differ on another CPU); each must be a full binary tree
+    over its workload's network whose slices keep every intermediate under
+    the workload's cap, with the statistics the search reported."""
+    from paper_2103_03074_gb300.trees import make_trees
+    cfg = make_config(cfg_idx)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, st = make_trees.load(name, L, O)
+    assert len(tree) == len(L) - 1
+    seen = sorted(x for p in tree for x in p)
+    assert seen == list(range(2 * len(L) - 2))  # every leaf and step but the root used once
+    assert not set(sliced) & set(O)
+    if cfg.get("log2_cap"):
+        assert st["log2_width"] <= cfg["log2_cap"]
+    # re-slicing the stored tree to the same cap finds a slice set no larger
+    if cfg.get("log2_cap"):
+        sl2, st2 = tn.slice_tree(L, O, tree, log2_cap=cfg["log2_cap"])
+        assert st2["log2_width"] <= cfg["log2_cap"]
+    # another network (other fixed bits give the same labels; other open
+    # qubits do not) is refused
+    L2, _, O2 = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"][1:])
+    assert make_trees.load(name, L2, O2) is None
+
+
+def test_reference_arm_loads_no_product_code():
+    """bench.py --impl reference times the CPU oracle and must not load the
+    CUDA library (its slice set comes from the stored tree's JSON)."""
+    import subprocess
+    code = ("import sys; sys.argv = ['bench.py', '--impl', 'reference', '--workload', 'rect3x4', '--steps', '1', "
+            "'--warmup', '1']; import bench; bench.main(); "
+            "maps = open('/proc/self/maps').read(); "
+            "print('LOADED' if ('libtn.so' in maps or 'paper_2103_03074_gb300' in sys.modules) else 'CLEAN')")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = r.stdout.strip().splitlines()
+    assert lines[-1] == "CLEAN"
+    import json
+    line = json.loads(lines[-2])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "slices/s"

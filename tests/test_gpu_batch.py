@@ -4,7 +4,12 @@ autotuner (tn_plan_autotune), against the CPU FP64 oracle.
 The batch follows the batched workload's recipe (tn_inputs.configs.batch_recipes:
 uneven rectangular grids, 8-14 cycles, 6-10 open qubits, 2^0-2^6 slices each),
 restricted to circuits of at most 24 qubits so that every circuit is checked
-against its own FP64 state vector (plain C oracle) within 1e-5.
+against its own FP64 state vector (plain C oracle) within 1e-5.  The full
+recipe (256 circuits of 16-30 qubits) checks every member against the same
+plan run alone, those of at most 20 qubits against a live FP64 state vector,
+and the larger ones whose FP64 state-vector amplitudes are stored
+(tests/golden/cfg3_amplitudes.txt: every member of up to 28 qubits and a
+seeded sample of the 30-qubit ones) against those, all within 1e-5.
 """
 import os
 
@@ -31,6 +36,22 @@ def tn():
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def stored_member_amplitudes():
+    """{member index: FP64 amplitudes} from tests/golden/cfg3_amplitudes.txt
+    (the FP64 state vectors of the batch members of more than 20 qubits that
+    tests/golden/make_golden.py has written; members appear whole)."""
+    path = os.path.join(HERE, "golden", "cfg3_amplitudes.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        i, j, re_, im_ = line.split()
+        out.setdefault(int(i), []).append((int(j), complex(float(re_), float(im_))))
+    return {i: np.array([v for _, v in sorted(vals)]) for i, vals in out.items()}
 
 
 def to_complex(t):
@@ -83,8 +104,10 @@ def test_autotune_keeps_results(tn):
 
 def test_full_batched_recipe(tn):
     """All 256 circuits of the batched workload (16-30 qubits) in one batch,
-    TF32x3.  Circuits of at most 20 qubits against their FP64 state vectors;
-    every circuit against its own plan contracted alone (eager path)."""
+    TF32x3.  Circuits of at most 20 qubits against their FP64 state vectors,
+    larger ones against their stored FP64 state-vector amplitudes where
+    present; every circuit against its own plan contracted alone (eager
+    path)."""
     import time
     import torch
     members = [make_batch_member(r) for r in batch_recipes()]
@@ -107,8 +130,9 @@ def test_full_batched_recipe(tn):
     dt = (time.perf_counter() - t0) / reps
     print(f"batched recipe: {len(members)} circuits, {n_slices} slices, {dt * 1e3:.2f} ms per batch, "
           f"{n_slices / dt:.0f} slices/s")
-    checked = 0
-    for m, p, a in zip(members, plans, amps):
+    stored = stored_member_amplitudes()
+    checked = from_store = 0
+    for mi, (m, p, a) in enumerate(zip(members, plans, amps)):
         got = to_complex(a)
         single = torch.zeros_like(a)
         p.contract(0, 1 << p.n_sliced, single)
@@ -120,7 +144,14 @@ def test_full_batched_recipe(tn):
         if m["circuit"].n_qubits <= 20:
             assert rel(got, sv_native.amplitudes(m["circuit"], m["fixed_bits"], m["open_qubits"])) < 1e-5
             checked += 1
+        elif mi in stored:
+            assert len(stored[mi]) == len(got)
+            assert rel(got, stored[mi]) < 1e-5, (mi, m["circuit"].n_qubits)
+            from_store += 1
+    print(f"batched recipe: {checked} members against a live FP64 state vector, {from_store} against stored "
+          f"FP64 state-vector amplitudes, all {len(members)} against the same plan run alone")
     assert checked >= 40
+    assert from_store == sum(1 for i in stored if i < len(members))
     batch.close()
     for p in plans:
         p.close()

@@ -12,8 +12,13 @@ lattice with one site removed), at full size.
   and does not meet 1e-5 (2.0e-5 measured here); its check against 1e-4
   (2^-16 times a margin for the steps along the tree) only catches a broken
   kernel and is not a parity claim.
-* 20 cycles, 21 open qubits, intermediates capped at 2^31 elements: no
-  oracle value exists at this size (one amplitude costs ~2^61 complex MACs),
+* The same entries from the benchmark's stored bipartition tree (a
+  different slice set and contraction order), and the benchmark's host-buffer
+  entry point against the device path.
+* 20 cycles, 21 open qubits, intermediates capped at 2^31 elements, the
+  benchmark's stored tree: no oracle value exists at this size (a closed
+  amplitude costs 2^52 complex MACs with the best order found, and the
+  oracle's own greedy order needs 2^41-element intermediates for one slice),
   so its parity is unpinned; the checks are properties that hold at any
   size: a slice range is the sum of its sub-ranges, and the split forms
   agree with the plain FP32 form on the same slices.
@@ -99,11 +104,46 @@ def test_cfg4_sampled_amplitudes(tn, cfg4_plan_inputs, form):
     assert 0.8 < p_s1 * 2.0 ** (cfg["circuit"].n_qubits - len(O)) < 1.2
 
 
+@pytest.mark.parametrize("form", ["fp16x3", "tf32x3", "fp32"])
+def test_cfg4_stored_tree_sampled_amplitudes(tn, form):
+    """The benchmark's own plan: the stored bipartition tree of the 14-cycle
+    workload (paper_2103_03074_gb300/trees/syc53_m14.json), every slice, in
+    the forms its headline may take, against the same FP64 oracle entries at
+    1e-5; the host-buffer entry point (tn_contract_slices_host, the bench's
+    end-to-end call) returns the same amplitudes and the same P(s1) and XEB
+    as the device path."""
+    import torch
+    from paper_2103_03074_gb300.trees import make_trees
+    cfg = make_config(4)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, st = make_trees.load("syc53_m14", L, O)
+    idx, ref = load_sampled("cfg4_amplitudes_sampled.txt")
+    plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1))
+    amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+    plan.contract(0, 1 << len(sliced), amp)
+    got = to_complex(amp)
+    e = rel(got[idx], ref)
+    print(f"cfg4 stored tree {form}: {len(sliced)} sliced bonds, relative L2 error over {len(idx)} sampled "
+          f"entries {e:.3e}")
+    assert e < 1e-5
+    n = cfg["circuit"].n_qubits
+    p_s1, f, pmax = tn.probabilities_xeb(amp, len(O), n)
+    h_amp = np.zeros(2 << len(O))
+    h_stats = np.zeros(3)
+    plan.contract_host(0, 1 << len(sliced), None, n, h_amp, h_stats)
+    plan.close()
+    hg = h_amp[0::2] + 1j * h_amp[1::2]
+    # same plan, same kernels: equal up to split-K atomic order
+    assert rel(hg, got) < 1e-6
+    assert abs(h_stats[1] - f) < 1e-9 and abs(h_stats[0] - p_s1) < 1e-6 * p_s1
+
+
 def test_cfg5_slice_subset_properties(tn):
     import torch
+    from paper_2103_03074_gb300.trees import make_trees
     cfg = make_config(5)
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
-    tree, sliced, st = tn.find_order(L, O, tn.search_opts(trials=1024, log2_cap=cfg["log2_cap"]))
+    tree, sliced, st = make_trees.load("syc53_m20", L, O)
     assert st["log2_width"] <= cfg["log2_cap"]
     n_sub = 4
     got = {}
