@@ -81,8 +81,19 @@ def fp32_alu_peak_tflops(sm_mhz):
 # tensor-core flops the split forms issue per complex MAC: 4 real products x
 # 3 piece products x 2 (FP16S: 4 x 1 x 2); the TF32 peak is half the bf16
 # peak (nominal dense ratio 1.1 : 2.25)
-TC_FLOPS_PER_MAC = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16x3": 24.0, "fp16s": 8.0}
-TC_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5, "fp16x3": 1.0, "fp16s": 1.0}
+TC_FLOPS_PER_MAC = {"bf16x3": 24.0, "tf32x3": 24.0, "fp16x3": 24.0, "fp16s": 8.0,
+                    # Gauss's 3M product: 3 real products x 3 piece products x 2
+                    "bf16x3_3m": 18.0, "tf32x3_3m": 18.0, "fp16x3_3m": 18.0}
+TC_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5, "fp16x3": 1.0, "fp16s": 1.0,
+                 "bf16x3_3m": 1.0, "tf32x3_3m": 0.5, "fp16x3_3m": 1.0}
+FORM_CHOICES = ["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "bf16x3_3m", "tf32x3_3m", "fp16x3_3m"]
+
+
+def make_plan(tn, L, T, O, sliced, tree, name, **opts):
+    """A plan for a bench form name: the library form, with Gauss's 3M
+    product on the tensor cores for the *_3m names (tc_products 3)."""
+    form, _, m3 = name.partition("_")
+    return tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(tc_products=3 if m3 else 0, **opts))
 
 
 def roofline_ms(row, form, pk):
@@ -186,11 +197,13 @@ WORKLOADS = {
                     desc="rect3x4_m8_allopen: 12 qubits, 8 cycles, all 12 open, no slicing "
                          "(one contraction per step: a latency-bound circuit)"),
     "rect5x6": dict(cfg=2, search=dict(trials=16384, n_sliced=8), tree="rect5x6", step_slices=None,
-                    golden="cfg2_amplitudes.txt", forms=["fp32", "tf32x3", "fp16x3", "bf16x3", "fp16s"],
+                    golden="cfg2_amplitudes.txt",
+                    forms=["fp32", "tf32x3", "tf32x3_3m", "fp16x3", "fp16x3_3m", "bf16x3", "fp16s"],
                     desc="rect5x6_m12_open8_sliced8: 30 qubits, 12 cycles, 8 open, 22 fixed, "
                          "2^8 slices over 8 searched bonds"),
     "syc53_m14": dict(cfg=4, search=dict(trials=1024, log2_cap=30), tree="syc53_m14", step_slices=None,
-                      golden="cfg4_amplitudes_sampled.txt", forms=["fp16x3", "tf32x3", "fp32", "bf16x3", "fp16s"],
+                      golden="cfg4_amplitudes_sampled.txt",
+                      forms=["fp16x3", "fp16x3_3m", "tf32x3", "tf32x3_3m", "fp32", "bf16x3", "fp16s"],
                       desc="rotated6x9m1_m14_open16_cap30: 53 qubits, 14 cycles, 16 open, 37 fixed, "
                            "intermediates <= 2^30, every slice of the stored tree's slice set (the whole "
                            "2^16-amplitude tensor per step)"),
@@ -209,9 +222,11 @@ BATCH_DESC = ("batch256: 256 seeded circuits on rectangular grids of 16-30 qubit
 
 # forms that meet the 1e-5 bound by construction (22+ significant bits per
 # operand); only these can be the headline (BF16x3 keeps 16 bits, FP16S 11)
-ACCURATE_FORMS = ("fp32", "tf32x3", "fp16x3")
+ACCURATE_FORMS = ("fp32", "tf32x3", "fp16x3", "tf32x3_3m", "fp16x3_3m")
 DTYPE = {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "tf32x3": "tf32x3 (fp32 accumulate)",
-         "fp16x3": "fp16x3 (scaled, fp32 accumulate)", "fp16s": "f16 (scaled)"}
+         "fp16x3": "fp16x3 (scaled, fp32 accumulate)", "fp16s": "f16 (scaled)",
+         "bf16x3_3m": "bf16x3, 3M product (fp32 accumulate)", "tf32x3_3m": "tf32x3, 3M product (fp32 accumulate)",
+         "fp16x3_3m": "fp16x3, 3M product (scaled, fp32 accumulate)"}
 
 
 def workload(name, seed_offset=0):
@@ -260,11 +275,13 @@ class OracleSampler:
     Small workloads (30 qubits and below): the oracle contracts whole slices
     (its own one-tensor-per-gate network, the sliced bonds fixed), one after
     another.  53-qubit workloads: one slice of the open network is out of the
-    oracle's reach (its greedy order needs ~2^54 MACs), so it contracts closed
-    amplitudes (the open qubits set to a sampled bitstring: the route of the
-    stored oracle values) pair by pair, carrying on where the previous sample
-    stopped, and the rate is extrapolated by MACs: slices/s = (MACs done / s)
-    x n_slices / (2^n_open x MACs of one closed amplitude)."""
+    oracle's reach (its greedy order needs ~2^54 MACs), so it contracts a
+    closed amplitude (the open qubits set to a sampled bitstring: the route
+    of the stored oracle values) pair by pair, and the rate is extrapolated
+    by MACs: slices/s = (MACs done / s) x n_slices / (2^n_open x MACs of one
+    closed amplitude).  One pairwise step of that contraction can take tens
+    of seconds, so samples end between steps: after a time budget, a MAC
+    budget or a number of steps."""
 
     def __init__(self, workload_name, sliced, n_slices):
         from oracle import network as onet, contract as oc
@@ -274,7 +291,7 @@ class OracleSampler:
         self.small = self.cfg["circuit"].n_qubits <= 30
         self.sliced, self.n_slices = list(sliced), n_slices
         self.it, self.idx, self.amp_macs = None, 0, None
-        self.macs, self.secs, self.units, self.finished = 0.0, 0.0, 0, 0
+        self.macs, self.secs, self.units, self.steps, self.finished = 0.0, 0.0, 0, 0, 0
         if self.small:
             self.net = onet.circuit_network(self.cfg["circuit"], self.cfg["fixed_bits"], self.cfg["open_qubits"])
 
@@ -287,16 +304,24 @@ class OracleSampler:
         L, T, O = self.onet.circuit_network(self.cfg["circuit"], bits, [])
         self.it = self.oc.contract_iter(L, T, O)
 
-    def run(self, budget_s):
-        """Oracle work for about budget_s seconds; returns (slices/s of this
-        sample, seconds spent)."""
+    def run(self, budget_s=None, macs=None, steps=None):
+        """Oracle work until budget_s seconds, `macs` MACs or `steps` pairwise
+        steps (whole slices for the small workloads) have been done, checked
+        between steps; returns the seconds spent."""
         t0 = time.perf_counter()
-        macs0, units0 = self.macs, self.units
-        while time.perf_counter() - t0 < budget_s:
+        m0, s0, u0 = self.macs, self.steps, self.units
+        while True:
+            if budget_s is not None and time.perf_counter() - t0 >= budget_s:
+                break
+            if macs is not None and self.macs - m0 >= macs:
+                break
+            if steps is not None and self.steps - s0 >= steps:
+                break
             if self.small:
                 L, T, O = self.net
                 self.oc.slice_partial(L, T, O, self.sliced, self.units % (1 << len(self.sliced)))
                 self.units += 1
+                self.steps += 1
                 continue
             if self.it is None:
                 self._next_amplitude()
@@ -304,41 +329,47 @@ class OracleSampler:
                 m, tot = next(self.it)
                 self.macs += m
                 self.amp_macs = tot
+                self.steps += 1
             except StopIteration:
                 self.it = None
                 self.finished += 1
         dt = time.perf_counter() - t0
         self.secs += dt
-        if self.small:
-            return (self.units - units0) / dt, dt
-        return (self.macs - macs0) / dt * self.n_slices / ((1 << self.k) * self.amp_macs), dt
+        return dt
 
-    def rate(self):
-        """slices/s over every sample so far."""
+    def rate(self, macs=None, secs=None, units=None):
+        """slices/s over every sample so far (or over the given totals)."""
+        macs = self.macs if macs is None else macs
+        secs = self.secs if secs is None else secs
+        units = self.units if units is None else units
         if self.small:
-            return self.units / self.secs
-        return self.macs / self.secs * self.n_slices / ((1 << self.k) * self.amp_macs)
+            return units / secs
+        return macs / secs * self.n_slices / ((1 << self.k) * self.amp_macs)
 
     def describe(self):
         if self.small:
             return (f"{self.units} whole-slice contractions of the 2^{len(self.sliced)}-slice workload by the FP64 "
                     f"oracle (numpy), {self.secs:.1f} s")
-        return (f"closed-amplitude contractions of the FP64 oracle (numpy, greedy order, "
-                f"2^{math.log2(self.amp_macs):.1f} complex MACs per amplitude): {self.macs:.3g} MACs in "
-                f"{self.secs:.1f} s, {self.finished} amplitude(s) finished; slices/s = MAC rate x {self.n_slices} "
-                f"slices / (2^{self.k} amplitudes x MACs per amplitude)")
+        return (f"closed-amplitude contraction of the FP64 oracle (numpy, greedy order, "
+                f"2^{math.log2(self.amp_macs):.1f} complex MACs per amplitude): {self.steps} pairwise steps, "
+                f"{self.macs:.3g} MACs in {self.secs:.1f} s; slices/s = MAC rate x {self.n_slices} slices / "
+                f"(2^{self.k} amplitudes x MACs per amplitude)")
 
 
-def cpu_baseline(workload_name, sliced, n_slices, budget_s=20.0):
+def cpu_baseline(workload_name, sliced, n_slices, budget_s=15.0):
     """The oracle timed on all host cores, then on one core (a subprocess with
-    one BLAS/OpenMP thread); every number says what its sample was."""
+    one BLAS/OpenMP thread) over the first pairwise steps (or slices) that the
+    all-core sample finished in its first third; every number says what its
+    sample was."""
     smp = OracleSampler(workload_name, sliced, n_slices)
-    smp.run(budget_s)
+    smp.run(budget_s=budget_s / 3)
+    prefix = max(smp.steps, 1)
+    smp.run(budget_s=budget_s * 2 / 3)
     out = {"value": smp.rate(), "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
            "sample": smp.describe()}
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload_name,
-           "--oracle-budget", str(budget_s * 2 / 3), "--oracle-sliced", json.dumps(list(sliced)),
+           "--oracle-steps", str(prefix), "--oracle-sliced", json.dumps(list(sliced)),
            "--oracle-n-slices", str(n_slices)]
     try:
         r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
@@ -363,37 +394,48 @@ def run_reference(args):
     n_slices = (1 << len(sliced)) if st else 1
     if w["step_slices"]:
         n_slices = min(n_slices, w["step_slices"])
-    per_step = 4.0
     smp = OracleSampler(name, sliced, n_slices)
-    for _ in range(args.warmup):
-        smp.run(per_step / 4)
+    if smp.small:
+        # one whole slice per step
+        for _ in range(args.warmup):
+            smp.run(steps=1)
+        how = "one whole slice per step"
+    else:
+        # one closed amplitude in all, cut into warm-up + timed chunks of
+        # equal MACs (a chunk ends between pairwise steps)
+        smp.run(steps=1)
+        chunk = smp.amp_macs / (args.warmup + args.steps)
+        for _ in range(args.warmup):
+            smp.run(macs=chunk)
+        how = f"1/{args.warmup + args.steps} of one closed amplitude's MACs per step"
     macs0, secs0, units0 = smp.macs, smp.secs, smp.units
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        smp.run(per_step)
+        if smp.small:
+            smp.run(steps=1)
+        else:
+            smp.run(macs=chunk)
     dt = time.perf_counter() - t0
-    if smp.small:
-        v = (smp.units - units0) / (smp.secs - secs0)
-    else:
-        v = (smp.macs - macs0) / (smp.secs - secs0) * n_slices / ((1 << smp.k) * smp.amp_macs)
+    v = smp.rate(smp.macs - macs0, smp.secs - secs0, smp.units - units0)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Sycamore-style circuit)",
-            "config": {"workload": w["desc"], "step": "a bounded sample (~4 s) of CPU FP64 oracle work",
+            "config": {"workload": w["desc"], "step": "a bounded sample of CPU FP64 oracle work: " + how,
                        "slices_per_gpu_step": n_slices},
             "cpu_baseline": {"value": v, "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} steps of ~{per_step:.0f} s after {args.warmup} shorter "
-                                       f"warm-up steps; in all: " + smp.describe()},
+                             "sample": f"{args.steps} timed steps ({how}) after {args.warmup} warm-up steps; "
+                                       f"in all: " + smp.describe()},
             "e2e": {"value": v, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 def run_oracle_sample(args):
-    """Subprocess leg of cpu_baseline (one core)."""
+    """Subprocess leg of cpu_baseline (one core): the given number of
+    pairwise steps (or slices)."""
     smp = OracleSampler(args.oracle_sample, json.loads(args.oracle_sliced), args.oracle_n_slices)
-    smp.run(args.oracle_budget)
+    smp.run(steps=args.oracle_steps)
     print(json.dumps({"value": smp.rate(), "sample": smp.describe()}))
     return 0
 
@@ -447,7 +489,7 @@ def time_steps(torch, plan, ranges, amp, steps, warmup, stream, flush, n_open, n
 def profile_roofline(tn, torch, L, T, O, sliced, tree, form, rng, amp, stream, pk, steps, dump=None, tag=""):
     """Per-op CUDA events (step-timing recorder) over `steps` steps: the
     dominant kernel class's roofline entry and every class's share."""
-    pplan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(profile=1))
+    pplan = make_plan(tn, L, T, O, sliced, tree, form, profile=1)
     with torch.cuda.stream(stream):
         pplan.contract(rng[0], rng[1], amp, stream)
         pplan.profile(reset=True)
@@ -606,7 +648,7 @@ def run_native(args):
     plans = {}
     for form in forms:
         try:
-            plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1))
+            plan = make_plan(tn, L, T, O, sliced, tree, form, use_graph=1)
         except tn.TNError as e:
             results[form] = {"error": str(e)}
             continue
@@ -657,7 +699,7 @@ def run_native(args):
     best = max(within or ok, key=lambda f: results[f]["slices_per_s"])
     r = results[best]
     # end to end through the C-ABI with host buffers (tn_contract_slices_host)
-    plan = plans.get(best) or tn.Plan(L, T, O, sliced, tree, form=best, opts=tn.plan_opts(use_graph=1))
+    plan = plans.get(best) or make_plan(tn, L, T, O, sliced, tree, best, use_graph=1)
     data = np.concatenate([np.stack([np.asarray(t, np.complex64).reshape(-1).real,
                                      np.asarray(t, np.complex64).reshape(-1).imag], 1).reshape(-1)
                            for t in T]).astype(np.float32)
@@ -685,7 +727,7 @@ def run_native(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, sliced, n_slices)
-    split = [f for f in ok if f != "fp32" and f in ACCURATE_FORMS]
+    split = [f for f in ok if f != "fp32" and f in ACCURATE_FORMS]  # split-precision tensor-core forms
     line = {
         "metric": METRIC, "value": r["slices_per_s"], "unit": "slices/s", "n_gpus": world, "steps": r["steps"],
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -804,14 +846,27 @@ def run_gemm(args):
     __graft_entry__.build_library()
     import paper_2103_03074_gb300 as tn
     h, m, k, n = (int(x) for x in args.gemm.split(","))
-    form = "fp16x3" if args.form == "all" else args.form
+    name = "fp16x3" if args.form == "all" else args.form
+    form = name.partition("_")[0]
     rng = np.random.default_rng(0)
     hl, ml, kl, nl = (list(range(b, b + c)) for b, c in ((300, h), (0, m), (100, k), (200, n)))
     A = (rng.standard_normal(2 ** (h + m + k)) + 1j * rng.standard_normal(2 ** (h + m + k))).astype(np.complex64)
     B = (rng.standard_normal(2 ** (h + k + n)) + 1j * rng.standard_normal(2 ** (h + k + n))).astype(np.complex64)
-    plan = tn.Plan([hl + ml + kl, hl + kl + nl], [A.reshape((2,) * (h + m + k)), B.reshape((2,) * (h + k + n))],
-                   ml + nl, hl, [(0, 1)], form=form, opts=tn.plan_opts(use_graph=1))
-    amp = torch.zeros(2 << (m + n), dtype=torch.float64, device="cuda")
+    labels = [hl + ml + kl, hl + kl + nl]
+    tensors = [A.reshape((2,) * (h + m + k)), B.reshape((2,) * (h + k + n))]
+    out_l, tree = ml + nl, [(0, 1)]
+    if args.gemm_next:
+        # a second GEMM C[h,m,n] D[n,p] -> [m,p] (D of 2^(n+p) values, more than
+        # a small step takes) makes the first GEMM write its output as the
+        # second one's split planes (the planar epilogue)
+        p = args.gemm_next
+        pl = list(range(400, 400 + p))
+        D = (rng.standard_normal(2 ** (n + p)) + 1j * rng.standard_normal(2 ** (n + p))).astype(np.complex64)
+        labels.append(nl + pl)
+        tensors.append(D.reshape((2,) * (n + p)))
+        out_l, tree = ml + pl, [(0, 1), (3, 2)]
+    plan = make_plan(tn, labels, tensors, out_l, hl, tree, name, use_graph=1)
+    amp = torch.zeros(2 << len(out_l), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -825,9 +880,9 @@ def run_gemm(args):
         stream.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     macs = 2.0 ** (h + m + k + n)
-    print(json.dumps({"gemm": {"log2_hmkn": [h, m, k, n], "form": form}, "ms_per_contraction": ms,
+    print(json.dumps({"gemm": {"log2_hmkn": [h, m, k, n], "form": name}, "ms_per_contraction": ms,
                       "complex_tflops": 8 * macs / (ms / 1e3) / 1e12,
-                      "tensor_tflops": TC_FLOPS_PER_MAC.get(form, 8.0) * macs / (ms / 1e3) / 1e12,
+                      "tensor_tflops": TC_FLOPS_PER_MAC.get(name, 8.0) * macs / (ms / 1e3) / 1e12,
                       "plan": plan.describe()}))
     plan.close()
     return 0
@@ -839,9 +894,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--form", default="all", choices=["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "all"])
+    ap.add_argument("--form", default="all", choices=FORM_CHOICES + ["all"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256", "gemm"])
     ap.add_argument("--gemm", default="0,15,11,9", help="--workload gemm: log2 H,M,K,N")
+    ap.add_argument("--gemm-next", type=int, default=0,
+                    help="--workload gemm: follow the GEMM by a second one of log2 N = this, so that the first "
+                         "writes the second one's split planes from its epilogue")
     ap.add_argument("--search-method", default=None, choices=["greedy", "bipartition", "mixed"],
                     help="search a fresh tree (randomised greedy, hierarchical bipartition, or both) instead of "
                          "the workload's stored tree")
@@ -858,7 +916,7 @@ def main():
     ap.add_argument("--no-cfg5", action="store_true", help="skip the 20-cycle sample of the default line")
     ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--oracle-budget", type=float, default=10.0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-sliced", default="[]", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-n-slices", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -101,8 +101,15 @@ typedef struct {
      * 4..32 wide and T has >= 2^12 rows, else one thread per row; -1: always
      * one thread per row */
     int32_t small_tiled;
+    /* split forms BF16X3, TF32X3, FP16X3: real products per complex product on
+     * the tensor cores.  0 or 4 (default): four, A_re [B_re|B_im] and
+     * A_im [B_re|B_im]; 3: Gauss's 3M product, A_re B_re, A_im B_im and
+     * (A_re + A_im)(B_re + B_im), re = T1 - T2, im = T3 - T1 - T2 (a quarter
+     * fewer tensor-core flops; each operand then has six planes, the third
+     * value s = re + im split like re and im) */
+    int32_t tc_products;
     /* reserved, set to 0 */
-    int32_t reserved[2];
+    int32_t reserved[1];
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

@@ -35,7 +35,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("batch_log2", _i32), ("mem_budget", _i64), ("profile", _i32), ("use_graph", _i32),
                 ("tc_chunk_bytes", _i32), ("tc_flush_bytes", _i32), ("tc_planar", _i32),
                 ("graph_branches", _i32),
-                ("small_tc_bits", _i32), ("small_tiled", _i32), ("reserved", _i32 * 2)]
+                ("small_tc_bits", _i32), ("small_tiled", _i32), ("tc_products", _i32), ("reserved", _i32 * 1)]
 
 
 class SearchOpts(ctypes.Structure):
@@ -164,9 +164,12 @@ def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads
 
 
 def plan_opts(batch_log2=-1, mem_budget=0, profile=0, use_graph=0, tc_chunk_bytes=0, tc_flush_bytes=0,
-              tc_planar=0, graph_branches=0, small_tc_bits=0, small_tiled=0):
+              tc_planar=0, graph_branches=0, small_tc_bits=0, small_tiled=0, tc_products=0):
+    """Plan options (tn_plan_opts).  tc_products: 4 (default) or 3, the real
+    products per complex product of the split forms' tensor-core GEMMs (3:
+    Gauss's 3M product)."""
     return PlanOpts(batch_log2, mem_budget, profile, use_graph, tc_chunk_bytes, tc_flush_bytes, tc_planar,
-                    graph_branches, small_tc_bits, small_tiled)
+                    graph_branches, small_tc_bits, small_tiled, tc_products)
 
 
 def marshal_circuit(circuit):

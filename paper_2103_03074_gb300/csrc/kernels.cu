@@ -72,16 +72,18 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
     const int SS = HS * KS * NS;
     float2 *S_sm = reinterpret_cast<float2 *>(smem);
-    uint32_t *offT = reinterpret_cast<uint32_t *>(S_sm + SS);
-    uint32_t *offC = offT + KS;
+    // offsets of the k and n bits in T and C: 64-bit (a tensor of more than
+    // 2^32 elements has K or N bits at positions >= 32)
+    uint64_t *offT = reinterpret_cast<uint64_t *>(S_sm + SS);
+    uint64_t *offC = offT + KS;
     for (int idx = threadIdx.x; idx < SS; idx += blockDim.x) {
         uint32_t n = idx & (NS - 1), k = (idx >> a.nN) & (KS - 1), h = idx >> (a.nN + a.nK);
         uint64_t addr = scatter_bits(h, a.hposS, a.nH) | scatter_bits(k, a.kposS, a.nK) |
                         scatter_bits(n, a.nposS, a.nN);
         S_sm[idx] = a.S[addr];
     }
-    for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = (uint32_t)scatter_bits(k, a.kposT, a.nK);
-    for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = (uint32_t)scatter_bits(n, a.nposC, a.nN);
+    for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = scatter_bits(k, a.kposT, a.nK);
+    for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = scatter_bits(n, a.nposC, a.nN);
     __syncthreads();
     const int nc = NS < NC ? NS : NC;  // outputs per item
     constexpr int kNcBits = NC == 32 ? 5 : (NC == 16 ? 4 : 3);
@@ -142,16 +144,18 @@ __global__ void __launch_bounds__(kThreads) small_ksplit_kernel(const SmallArgs 
     const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
     const int SS = HS * KS * NS;
     float2 *S_sm = reinterpret_cast<float2 *>(smem);
-    uint32_t *offT = reinterpret_cast<uint32_t *>(S_sm + SS);
-    uint32_t *offC = offT + KS;
+    // offsets of the k and n bits in T and C: 64-bit (a tensor of more than
+    // 2^32 elements has K or N bits at positions >= 32)
+    uint64_t *offT = reinterpret_cast<uint64_t *>(S_sm + SS);
+    uint64_t *offC = offT + KS;
     for (int idx = threadIdx.x; idx < SS; idx += blockDim.x) {
         uint32_t n = idx & (NS - 1), k = (idx >> a.nN) & (KS - 1), h = idx >> (a.nN + a.nK);
         uint64_t addr = scatter_bits(h, a.hposS, a.nH) | scatter_bits(k, a.kposS, a.nK) |
                         scatter_bits(n, a.nposS, a.nN);
         S_sm[idx] = a.S[addr];
     }
-    for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = (uint32_t)scatter_bits(k, a.kposT, a.nK);
-    for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = (uint32_t)scatter_bits(n, a.nposC, a.nN);
+    for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = scatter_bits(k, a.kposT, a.nK);
+    for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = scatter_bits(n, a.nposC, a.nN);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int nc = NS < NC ? NS : NC;
@@ -384,6 +388,17 @@ __device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, flo
         reinterpret_cast<float2 *>(a.out)[d] = v;
         return;
     }
+    if (mode_3m(a.mode)) {
+        const Pieces6 pc = split_value_3m(a.mode, v, e);
+        if (mode_word(a.mode)) {
+            uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
+            for (int q = 0; q < 6; q++) P[d + q * a.plane_stride] = pc.q[q];
+        } else {
+            uint16_t *P = reinterpret_cast<uint16_t *>(a.out);
+            for (int q = 0; q < 6; q++) P[d + q * a.plane_stride] = (uint16_t)pc.q[q];
+        }
+        return;
+    }
     const Pieces pc = split_value(a.mode, v, e);
     const int np = mode_planes(a.mode);
     if (a.mode == 2) {
@@ -399,6 +414,17 @@ __device__ __forceinline__ void store_elem(const BitPermArgs &a, uint64_t d, flo
 __device__ __forceinline__ void store_pair(const BitPermArgs &a, uint64_t d, float2 v0, float2 v1, int e) {
     if (a.mode == 0) {
         reinterpret_cast<float4 *>(a.out)[d >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
+        return;
+    }
+    if (mode_3m(a.mode)) {
+        const Pieces6 p0 = split_value_3m(a.mode, v0, e), p1 = split_value_3m(a.mode, v1, e);
+        if (mode_word(a.mode)) {
+            uint2 *P = reinterpret_cast<uint2 *>(a.out);
+            for (int q = 0; q < 6; q++) P[(d + q * a.plane_stride) >> 1] = make_uint2(p0.q[q], p1.q[q]);
+        } else {
+            uint32_t *P = reinterpret_cast<uint32_t *>(a.out);
+            for (int q = 0; q < 6; q++) P[(d + q * a.plane_stride) >> 1] = p0.q[q] | (p1.q[q] << 16);
+        }
         return;
     }
     const Pieces p0 = split_value(a.mode, v0, e), p1 = split_value(a.mode, v1, e);
@@ -420,7 +446,10 @@ __device__ __forceinline__ void store_pair(const BitPermArgs &a, uint64_t d, flo
 __global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) {
     constexpr int T = 1 << kTileMaxBits;
     __shared__ float2 buf[2][T];
-    __shared__ uint32_t src_off[T], w_of[T], dst_off[T];
+    // a tile bit that is low in one layout can sit at position 32 or above in
+    // the other (tensors of more than 2^32 elements): 64-bit tile offsets
+    __shared__ uint64_t src_off[T], dst_off[T];
+    __shared__ uint32_t w_of[T];
     // the rest index scattered 6 bits at a time through lookup tables
     constexpr int kChunk = 6, kChunks = (kMaxRank + kChunk - 1) / kChunk;
     __shared__ uint64_t rest_tab[2][kChunks][1 << kChunk];
@@ -439,18 +468,19 @@ __global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) 
     }
     const int tile = 1 << a.n_tile;
     for (int e = threadIdx.x; e < tile; e += blockDim.x) {
-        uint32_t w = 0, so = 0, d = 0;
+        uint32_t w = 0;
+        uint64_t so = 0, d = 0;
         for (int j = 0; j < a.n_tile; j++) {
             const uint32_t b = (e >> j) & 1u;
             w |= b << a.rd_w[j];
-            so |= b << a.rd_src[j];
-            d |= b << a.tile_dst[j];
+            so |= (uint64_t)b << a.rd_src[j];
+            d |= (uint64_t)b << a.tile_dst[j];
         }
         src_off[e] = so;
         w_of[e] = w;
         dst_off[e] = d;
     }
-    const int es = a.mode >= 3 ? fp16s_exponent(__uint_as_float(*a.scale)) : 0;
+    const int es = mode_scaled(a.mode) ? fp16s_exponent(__uint_as_float(*a.scale)) : 0;
     __syncthreads();
     const int64_t n_rest = 1ll << a.n_rest;
     const int half = tile >> 1;
@@ -468,7 +498,7 @@ __global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) 
         }
         if (a.pair_rd) {
             for (int e2 = threadIdx.x; e2 < half; e2 += blockDim.x) {
-                const uint32_t so = src_off[2 * e2];
+                const uint64_t so = src_off[2 * e2];
                 const uint32_t w0 = w_of[2 * e2], w1 = w_of[2 * e2 + 1];
                 const float4 v0 = reinterpret_cast<const float4 *>(a.in)[(s_rest[0] | so) >> 1];
                 if (nr == 2) {
@@ -481,7 +511,8 @@ __global__ void __launch_bounds__(kThreads) bitperm_kernel(const BitPermArgs a) 
             }
         } else {
             for (int e = threadIdx.x; e < tile; e += blockDim.x) {
-                const uint32_t so = src_off[e], w = w_of[e];
+                const uint64_t so = src_off[e];
+                const uint32_t w = w_of[e];
                 const float2 v0 = a.in[s_rest[0] | so];
                 if (nr == 2) buf[1][w] = a.in[s_rest[1] | so];
                 buf[0][w] = v0;
@@ -993,7 +1024,7 @@ cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
     }
     SmallArgs a = args;
     const int KS = 1 << a.nK, NS = 1 << a.nN, HS = 1 << a.nH;
-    const size_t smem = (size_t)HS * KS * NS * sizeof(float2) + (size_t)(KS + NS) * sizeof(uint32_t);
+    const size_t smem = (size_t)HS * KS * NS * sizeof(float2) + (size_t)(KS + NS) * sizeof(uint64_t);
     if (a.rows < 1 || (a.rows & (a.rows - 1)) != 0) return cudaErrorInvalidValue;
     a.row_bits = __builtin_ctzll((unsigned long long)a.rows);
     const int nc = NS <= 8 ? 8 : (NS <= 16 ? 16 : 32);  // outputs per work item

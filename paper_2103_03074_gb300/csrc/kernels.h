@@ -87,7 +87,10 @@ int prepare_small_planar(SmallArgs &a, const int *cdest, int mode, int64_t plane
 //           the max-abs slot `scale` (a float stored as its bits), so the
 //           largest scaled value lies in [2^13, 2^14);
 // mode 4:   four fp16 planes (re_hi, im_hi, re_lo, im_lo) of the same scaled
-//           value: hi = fp16(x 2^-e), lo = fp16(x 2^-e - hi).
+//           value: hi = fp16(x 2^-e), lo = fp16(x 2^-e - hi);
+// modes 5, 6, 7: modes 1, 2 and 4 for the 3M complex product: a third value
+//           s = re + im (rounded to FP32; after the scale for mode 7) is split
+//           like re and im, six planes (re_hi, im_hi, s_hi, re_lo, im_lo, s_lo).
 // The tile holds the bits at the source's and the destination's lowest
 // positions, so reads and writes are both coalesced.
 constexpr int kTileMaxBits = 10;
@@ -126,6 +129,19 @@ __host__ __device__ inline int fp16s_exponent(float maxabs) {
     return ex - 14;
 }
 
+// Split-mode properties (modes of BitPermArgs, TcPlanarOut and SmallArgs)
+__host__ __device__ constexpr bool mode_3m(int m) { return m >= 5 && m <= 7; }
+// the 4M mode with the same pieces: 5 -> 1, 6 -> 2, 7 -> 4
+__host__ __device__ constexpr int mode_base(int m) { return m == 5 ? 1 : m == 6 ? 2 : m == 7 ? 4 : m; }
+// pieces held in 32 bits (tf32) rather than 16
+__host__ __device__ constexpr bool mode_word(int m) { return mode_base(m) == 2; }
+// values scaled by 2^-e before the split (fp16 forms)
+__host__ __device__ constexpr bool mode_scaled(int m) { return mode_base(m) == 3 || mode_base(m) == 4; }
+// planes written by a split mode
+__host__ __device__ constexpr int mode_planes(int m) { return m == 3 ? 2 : (mode_3m(m) ? 6 : 4); }
+// the 3M mode with the same pieces (1 -> 5, 2 -> 6, 4 -> 7; others unchanged)
+__host__ __device__ constexpr int mode_to_3m(int m) { return m == 1 ? 5 : m == 2 ? 6 : m == 4 ? 7 : m; }
+
 #ifdef __CUDACC__
 // round to nearest (ties away) on tf32's 10-bit mantissa, in a 32-bit container
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -134,21 +150,61 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
+// x 2^-e, exactly as ldexpf(x, -e): a multiplication by the power of two
+// when 2^-e is a normal float (both round the same), ldexpf otherwise
+__device__ __forceinline__ float scale_pow2(float x, int e) {
+    return (e >= -126 && e <= 126) ? x * __int_as_float((127 - e) << 23) : ldexpf(x, -e);
+}
+
 // The pieces of one complex value for the split modes of BitPermArgs
 // (1 bf16 hi/lo, 2 tf32 hi/lo, 3 scaled fp16, 4 scaled fp16 hi/lo), plane
 // order (re_hi, im_hi, re_lo, im_lo); 16-bit pieces in the low half.
 struct Pieces {
     uint32_t q[4];
 };
+// ... and of the 3M modes 5, 6, 7: (re_hi, im_hi, s_hi, re_lo, im_lo, s_lo)
+struct Pieces6 {
+    uint32_t q[6];
+};
 
+// hi and lo pieces of one (already scaled) real value, for mode_base b
+__device__ __forceinline__ void split_real(int b, float x, uint32_t &hi, uint32_t &lo) {
+    if (b == 1) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    } else if (b == 2) {
+        hi = tf32_rna(x);
+        lo = tf32_rna(x - __uint_as_float(hi));
+    } else {
+        const __half h = __float2half_rn(x);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+    }
+}
+
+__device__ __forceinline__ Pieces6 split_value_3m(int mode, float2 v, int e) {
+    Pieces6 r;
+    const int b = mode_base(mode);
+    const float xr = b == 4 ? scale_pow2(v.x, e) : v.x, xi = b == 4 ? scale_pow2(v.y, e) : v.y;
+    split_real(b, xr, r.q[0], r.q[3]);
+    split_real(b, xi, r.q[1], r.q[4]);
+    split_real(b, xr + xi, r.q[2], r.q[5]);
+    return r;
+}
+
+// The re and im pieces are converted as pairs (one packed conversion for two
+// values, round to nearest each, as the scalar conversions would).
 __device__ __forceinline__ Pieces split_value(int mode, float2 v, int e) {
     Pieces r;
     if (mode == 1) {
-        const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-        r.q[0] = __bfloat16_as_ushort(rh);
-        r.q[1] = __bfloat16_as_ushort(ih);
-        r.q[2] = __bfloat16_as_ushort(__float2bfloat16_rn(v.x - __bfloat162float(rh)));
-        r.q[3] = __bfloat16_as_ushort(__float2bfloat16_rn(v.y - __bfloat162float(ih)));
+        const __nv_bfloat162 h = __float22bfloat162_rn(v);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+        r.q[0] = __bfloat16_as_ushort(h.x);
+        r.q[1] = __bfloat16_as_ushort(h.y);
+        r.q[2] = __bfloat16_as_ushort(l.x);
+        r.q[3] = __bfloat16_as_ushort(l.y);
     } else if (mode == 2) {
         const uint32_t rh = tf32_rna(v.x), ih = tf32_rna(v.y);
         r.q[0] = rh;
@@ -156,18 +212,18 @@ __device__ __forceinline__ Pieces split_value(int mode, float2 v, int e) {
         r.q[2] = tf32_rna(v.x - __uint_as_float(rh));
         r.q[3] = tf32_rna(v.y - __uint_as_float(ih));
     } else {  // 3, 4: scaled by 2^-e (exact), then one fp16 piece or hi/lo
-        const float xr = ldexpf(v.x, -e), xi = ldexpf(v.y, -e);
-        const __half rh = __float2half_rn(xr), ih = __float2half_rn(xi);
-        r.q[0] = __half_as_ushort(rh);
-        r.q[1] = __half_as_ushort(ih);
-        r.q[2] = __half_as_ushort(__float2half_rn(xr - __half2float(rh)));
-        r.q[3] = __half_as_ushort(__float2half_rn(xi - __half2float(ih)));
+        const float2 x = make_float2(scale_pow2(v.x, e), scale_pow2(v.y, e));
+        const __half2 h = __float22half2_rn(x);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __float22half2_rn(make_float2(x.x - hf.x, x.y - hf.y));
+        r.q[0] = __half_as_ushort(h.x);
+        r.q[1] = __half_as_ushort(h.y);
+        r.q[2] = __half_as_ushort(l.x);
+        r.q[3] = __half_as_ushort(l.y);
     }
     return r;
 }
 
-// planes written by a split mode
-__device__ __forceinline__ int mode_planes(int mode) { return mode == 3 ? 2 : 4; }
 #endif
 
 // Strided batched complex GEMM, all strides in complex elements:

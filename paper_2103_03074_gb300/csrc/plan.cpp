@@ -148,7 +148,7 @@ BitPermArgs make_bitperm(const std::vector<int32_t> &src, const std::vector<int3
     // elements of complex64, 32 of a 32-bit plane, 64 of a 16-bit plane) and
     // the low source bits of a 128-byte load run (16 complex64 elements),
     // then destination and source bits alternately
-    const int d_need = mode == 0 ? 4 : (mode == 2 ? 5 : 6), s_need = 4;
+    const int d_need = mode == 0 ? 4 : (mode_word(mode) ? 5 : 6), s_need = 4;
     int i_d = 0, i_s = 0;
     while (cnt < nt && (i_d < d_need || i_s < s_need)) {
         if (i_d < d_need) add(i_d++);
@@ -595,9 +595,14 @@ int64_t compile(tn_plan &P, int nb) {
             // scaled forms (FP16S, FP16X3): a max-abs pass per operand first
             // picks its power-of-two scale, and the split writes scaled fp16
             // planes {re, im} or {re_hi, im_hi, re_lo, im_lo}
-            const int es = tc_plane_bytes(P.form), np = tc_plane_count(P.form);
+            // the 3M product (tc_products 3, hi/lo forms): six planes per
+            // operand, the split modes' 3M variants
+            const int products = (P.opts.tc_products == 3 && tc_form_has_3m(P.form)) ? 3 : 4;
+            const int es = tc_plane_bytes(P.form), np = tc_plane_count(P.form, products);
             const bool scaled = P.form == TN_FP16S || P.form == TN_FP16X3;
-            const int mode = P.form == TN_FP16S ? 3 : P.form == TN_FP16X3 ? 4 : (es == 2 ? 1 : 2);
+            const int mode4 = P.form == TN_FP16S ? 3 : P.form == TN_FP16X3 ? 4 : (es == 2 ? 1 : 2);
+            const int mode = products == 3 ? mode_to_3m(mode4) : mode4;
+            op.tc.products = products;
             Operand slots;
             if (scaled) {
                 // four uint32 slots: the A and B operands' plane scales (max
@@ -1222,6 +1227,8 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
     if (form < TN_FP32 || form > TN_FP16X3) return fail(TN_ERR_ARG, "unknown form");
     if (form != TN_FP32 && !tc_form_available(form))
         return fail(TN_ERR_ARG, "this arithmetic form is not compiled into this library");
+    if (opts && opts->tc_products != 0 && opts->tc_products != 4 && opts->tc_products != 3)
+        return fail(TN_ERR_ARG, "tc_products must be 0, 3 or 4");
     std::unique_ptr<tn_plan> P(new tn_plan());
     P->form = form;
     if (opts) P->opts = *opts;
@@ -1833,9 +1840,11 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
         }
         case OP_GEMM:
             if (op.gemm_variant == 1)
-                std::snprintf(line, sizeof line, "%s step %d gemm H=%lld M=%lld N=%lld K=%lld tensor-core ksplit=%d out=%s",
-                              phase, op.step, (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N,
-                              (long long)op.gemm.K, op.tc.ksplit, op.tc.out.mode ? "planes" : "complex64");
+                std::snprintf(line, sizeof line,
+                              "%s step %d gemm H=%lld M=%lld N=%lld K=%lld tensor-core%s ksplit=%d out=%s", phase,
+                              op.step, (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N,
+                              (long long)op.gemm.K, op.tc.products == 3 ? " 3M" : "", op.tc.ksplit,
+                              op.tc.out.mode ? "planes" : "complex64");
             else
                 std::snprintf(line, sizeof line, "%s step %d gemm H=%lld M=%lld N=%lld K=%lld fp32", phase, op.step,
                               (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N, (long long)op.gemm.K);

@@ -111,7 +111,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 template <int CB>
 struct Swz {
     static constexpr uint32_t kSBO = 8 * CB;                // 8 rows of one swizzle atom
-    static constexpr uint64_t kLayout = CB == 64 ? 4 : 2;  // descriptor swizzle code
+    static constexpr uint64_t kLayout = CB == 64 ? 4 : (CB == 32 ? 6 : 2);  // descriptor swizzle code
 };
 
 template <int CB>
@@ -259,10 +259,31 @@ __device__ __forceinline__ uint64_t scatter8(uint64_t v, const int8_t *pos, int 
     return r;
 }
 
+// the pieces of one value for a 4M (four planes) or 3M (six planes) mode
+template <bool M3>
+struct PiecesT {
+    uint32_t q[M3 ? 6 : 4];
+};
+template <bool M3>
+__device__ __forceinline__ PiecesT<M3> split_t(int mode, float2 v, int e) {
+    PiecesT<M3> r;
+    if constexpr (M3) {
+        const Pieces6 p = split_value_3m(mode, v, e);
+#pragma unroll
+        for (int q = 0; q < 6; q++) r.q[q] = p.q[q];
+    } else {
+        const Pieces p = split_value(mode, v, e);
+#pragma unroll
+        for (int q = 0; q < 4; q++) r.q[q] = p.q[q];
+    }
+    return r;
+}
+
+template <bool M3>
 __device__ __forceinline__ void plane_store1(const TcPlanarOut &o, uint64_t d, float2 v, int e) {
-    const Pieces pc = split_value(o.mode, v, e);
+    const PiecesT<M3> pc = split_t<M3>(o.mode, v, e);
     const int np = mode_planes(o.mode);
-    if (o.mode == 2) {
+    if (mode_word(o.mode)) {
         uint32_t *P = reinterpret_cast<uint32_t *>(o.planes);
         for (int q = 0; q < np; q++) P[d + q * o.plane_stride] = pc.q[q];
     } else {
@@ -272,10 +293,11 @@ __device__ __forceinline__ void plane_store1(const TcPlanarOut &o, uint64_t d, f
 }
 
 // elements d, d + 1 (d even)
+template <bool M3>
 __device__ __forceinline__ void plane_store2(const TcPlanarOut &o, uint64_t d, float2 v0, float2 v1, int e) {
-    const Pieces p0 = split_value(o.mode, v0, e), p1 = split_value(o.mode, v1, e);
+    const PiecesT<M3> p0 = split_t<M3>(o.mode, v0, e), p1 = split_t<M3>(o.mode, v1, e);
     const int np = mode_planes(o.mode);
-    if (o.mode == 2) {
+    if (mode_word(o.mode)) {
         uint2 *P = reinterpret_cast<uint2 *>(o.planes);
         for (int q = 0; q < np; q++) P[(d + q * o.plane_stride) >> 1] = make_uint2(p0.q[q], p1.q[q]);
     } else {
@@ -335,6 +357,7 @@ __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane
 // Split the staged half tile (rows mh .. mh + 63) into the next step's
 // planes: warp fw of the 8 epilogue warps takes the groups j_hi = fw, fw + 8,
 // ...; each lane two (or four) neighbouring elements of a group.
+template <bool M3>
 __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_t mh, int64_t n0, const float2 *st,
                                              const uint2 *jtab, const PlanarLane &L, int fw, int lane, int e) {
     const uint64_t base = scatter8((uint64_t)h, o.hpos, o.nH) | scatter8((uint64_t)mh, o.mpos, o.nM) |
@@ -345,11 +368,11 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_
         const int np = mode_planes(o.mode);
         for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
             const uint2 g = jtab[jh];
-            Pieces pc[4];
+            PiecesT<M3> pc[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) pc[q] = split_value(o.mode, st[(int)g.x + L.s[q]], e);
+            for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
             const uint64_t d0 = base + g.y + L.d[0];  // a multiple of 4
-            if (o.mode == 2) {
+            if (mode_word(o.mode)) {
                 uint4 *P = reinterpret_cast<uint4 *>(o.planes);
                 for (int q = 0; q < np; q++)
                     P[(d0 + q * o.plane_stride) >> 2] = make_uint4(pc[0].q[q], pc[1].q[q], pc[2].q[q], pc[3].q[q]);
@@ -369,19 +392,19 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_
         const float2 b = st[(int)g.x + L.s[1]];
         const uint64_t d0 = base + g.y + L.d[0];
         if (L.pair) {
-            plane_store2(o, d0, a, b, e);
+            plane_store2<M3>(o, d0, a, b, e);
         } else {
-            if (v0) plane_store1(o, d0, a, e);
-            if (v1) plane_store1(o, base + g.y + L.d[1], b, e);
+            if (v0) plane_store1<M3>(o, d0, a, e);
+            if (v1) plane_store1<M3>(o, base + g.y + L.d[1], b, e);
         }
     }
 }
 
-template <int KIND, int CB>
+template <int KIND, int CB, bool M3>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
-    constexpr int NP = kind_split(KIND) ? 4 : 2;
+    constexpr int NP = M3 ? 6 : (kind_split(KIND) ? 4 : 2);
     using R = Ring<CB, NP>;
     constexpr int kAPlane = R::kAPlane, kBPlane = R::kBPlane;
     constexpr int kStageBytes = R::kStageBytes, kStages = R::kStages;
@@ -466,6 +489,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (first && tuse > 0 && !mbar_wait(smem_u32(&tempty[t]), (tuse - 1) & 1)) { ok = false; break; }
                     fence_after();
                     const uint32_t a0 = smem_u32(smem + s * kStageBytes), b0 = a0 + NP * kAPlane;
+                    if constexpr (M3) {
+                        // 3M: T1 = A_re B_re, T2 = A_im B_im, T3 = A_s B_s (s = re + im),
+                        // each from the hi*hi, hi*lo and lo*hi piece products, N = 64
+                        constexpr uint32_t ID3 = make_idesc(fmt, TM, TN, false);
+                        const uint32_t d1 = tmem + t * 256;
+#pragma unroll
+                        for (int ks = 0; ks < CB / 32; ks++) {
+                            const uint32_t ko = ks * 32;
+                            const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+#pragma unroll
+                            for (int pr = 0; pr < 3; pr++) {
+                                const uint32_t dd = d1 + pr * TN;
+                                const uint64_t ah = make_desc<CB>(a0 + pr * kAPlane + ko);
+                                const uint64_t al = make_desc<CB>(a0 + (pr + 3) * kAPlane + ko);
+                                const uint64_t bh = make_desc<CB>(b0 + pr * kBPlane + ko);
+                                const uint64_t bl = make_desc<CB>(b0 + (pr + 3) * kBPlane + ko);
+                                mma<KIND>(dd, ah, bh, ID3, acc);
+                                mma<KIND>(dd, ah, bl, ID3, 1u);
+                                mma<KIND>(dd, al, bh, ID3, 1u);
+                            }
+                        }
+                        mma_commit(smem_u32(&empty[s]));
+                        if (last) mma_commit(smem_u32(&tfull[t]));
+                        continue;
+                    }
                     const uint32_t dP = tmem + t * 256, dQ = dP + 128;
 #pragma unroll
                     for (int ks = 0; ks < CB / 32; ks++) {  // MMA K steps of 32 bytes
@@ -514,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // from the max slot (2^(e_out + 13)) and the output's true max from
         // the slot two places on, so the bound never builds on another bound.
         int e_out = 0;
-        if (kind_scaled(KIND) && (p.out.mode == 3 || p.out.mode == 4)) {
+        if (kind_scaled(KIND) && mode_scaled(p.out.mode)) {
             int lk = 0;
             while (((int64_t)1 << lk) < p.K) lk++;
             float mA = __uint_as_float(p.scales[2]), mB = __uint_as_float(p.scales[3]);
@@ -553,8 +601,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!ok) continue;
                 fence_after();
                 const uint32_t base = tmem + t * 256 + lane_off + half * 32;
+                if constexpr (M3) {
 #pragma unroll
-                for (int q = 0; q < 2; q++) {
+                    for (int q = 0; q < 2; q++) {
+                        uint32_t r0[16], r1[16], r2[16];
+                        tmem_ld16(base + q * 16, r0);             // T1 = A_re B_re
+                        tmem_ld16(base + TN + q * 16, r1);        // T2 = A_im B_im
+                        tmem_ld16(base + 2 * TN + q * 16, r2);    // T3 = (A_re + A_im)(B_re + B_im)
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; j++) {
+                            const float t1 = __uint_as_float(r0[j]), t2 = __uint_as_float(r1[j]);
+                            acc_re[q * 16 + j] += t1 - t2;
+                            acc_im[q * 16 + j] += __uint_as_float(r2[j]) - (t1 + t2);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < (M3 ? 0 : 2); q++) {
                     uint32_t r0[16], r1[16], r2[16], r3[16];
                     tmem_ld16(base + q * 16, r0);        // P left:  A_re B_re
                     tmem_ld16(base + 64 + q * 16, r1);   // P right: A_re B_im
@@ -588,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < 32; j++) mx = fmaxf(mx, fmaxf(fabsf(acc_re[j]), fabsf(acc_im[j])));
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-                if (p.out.mode == 3 || p.out.mode == 4) {
+                if (mode_scaled(p.out.mode)) {
                     if (lane == 0) atomicMax(p.max_slot + 2, __float_as_uint(mx));  // true max
                     mx = ldexpf(1.f, e_out + 13);  // the planes' exponent
                 }
@@ -621,8 +685,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("bar.sync 1, 256;" ::: "memory");
                 if (p.out.mode != 0) {
                     if (ok && tc.m0 + hp * (TM / 2) < p.M)
-                        planar_write(p.out, tc.h, tc.m0 + hp * (TM / 2), tc.n0, stage_out, jtab, pl, fw, lane,
-                                     e_out);
+                        planar_write<M3>(p.out, tc.h, tc.m0 + hp * (TM / 2), tc.n0, stage_out, jtab, pl, fw, lane,
+                                         e_out);
                 }
                 for (int rr = fw; ok && p.out.mode == 0 && rr < TM / 2; rr += kFlushWarps) {
                     const int64_t mm = tc.m0 + hp * (TM / 2) + rr;
@@ -681,7 +745,8 @@ bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int6
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(map, dtype, 4, planes, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                    cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                             : (cb == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B),
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -696,7 +761,11 @@ int tc_plane_bytes(tn_form form) { return form == TN_TF32X3 ? 4 : 2; }
 
 int tc_default_flush_bytes(tn_form form) { return default_flush_bytes(form); }
 
-int tc_plane_count(tn_form form) { return form == TN_FP16S ? 2 : 4; }
+int tc_plane_count(tn_form form, int products) {
+    return form == TN_FP16S ? 2 : (products == 3 ? 6 : 4);
+}
+
+bool tc_form_has_3m(tn_form form) { return form == TN_BF16X3 || form == TN_TF32X3 || form == TN_FP16X3; }
 
 bool tc_gemm_suitable(const GemmArgs &a) {
     // narrow N and short K are zero-filled by TMA to the tile (the MMAs on
@@ -717,11 +786,20 @@ int tc_choose_ksplit(const GemmArgs &a, tn_form form) {
 
 bool tc_prepare(TcGemm &g) {
     const int es = tc_plane_bytes(g.form);
-    if (g.chunk_bytes != 64 && g.chunk_bytes != 128) g.chunk_bytes = kDefaultChunkBytes;
-    if (g.flush_bytes < g.chunk_bytes)
-        g.flush_bytes = default_flush_bytes(g.form) < g.chunk_bytes ? g.chunk_bytes : default_flush_bytes(g.form);
-    if (g.a.K * es < g.chunk_bytes) g.chunk_bytes = 64;
-    const int cb = g.chunk_bytes, np = tc_plane_count(g.form);
+    if (g.products == 0) g.products = 4;
+    if (g.products != 4 && (g.products != 3 || !tc_form_has_3m(g.form))) return false;
+    if (g.products == 3) {
+        // six planes per operand: 32-byte K chunks (one MMA K step, 32-byte
+        // swizzle) keep five ring stages in shared memory
+        g.chunk_bytes = 32;
+        if (g.flush_bytes < 32 || g.flush_bytes % 32) g.flush_bytes = default_flush_bytes(g.form);
+    } else {
+        if (g.chunk_bytes != 64 && g.chunk_bytes != 128) g.chunk_bytes = kDefaultChunkBytes;
+        if (g.flush_bytes < g.chunk_bytes)
+            g.flush_bytes = default_flush_bytes(g.form) < g.chunk_bytes ? g.chunk_bytes : default_flush_bytes(g.form);
+        if (g.a.K * es < g.chunk_bytes) g.chunk_bytes = 64;
+    }
+    const int cb = g.chunk_bytes, np = tc_plane_count(g.form, g.products);
     const CUtensorMapDataType dt = g.form == TN_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : g.form == TN_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -732,14 +810,14 @@ bool tc_prepare(TcGemm &g) {
     return true;
 }
 
-template <int KIND, int CB>
+template <int KIND, int CB, bool M3 = false>
 cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
-    constexpr int NP = kind_split(KIND) ? 4 : 2;
-    cudaError_t e = set_max_dynamic_smem((const void *)tc_gemm_kernel<KIND, CB>, Ring<CB, NP>::kSmem);
+    constexpr int NP = M3 ? 6 : (kind_split(KIND) ? 4 : 2);
+    cudaError_t e = set_max_dynamic_smem((const void *)tc_gemm_kernel<KIND, CB, M3>, Ring<CB, NP>::kSmem);
     if (e != cudaSuccess) return e;
     const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
     const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
-    tc_gemm_kernel<KIND, CB><<<grid, kThreads, Ring<CB, NP>::kSmem, s>>>(mA, mB, p);
+    tc_gemm_kernel<KIND, CB, M3><<<grid, kThreads, Ring<CB, NP>::kSmem, s>>>(mA, mB, p);
     return cudaGetLastError();
 }
 
@@ -763,13 +841,19 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     // planar output: bf16 / tf32 hi/lo (modes 1, 2) or scaled fp16 (3, 4)
     // with the bound-derived exponent.  Plane offsets are 64-bit (a tile's
     // own offsets 32-bit, checked when the plan builds the tables)
-    if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || p.out.mode < 1 || p.out.mode > 4 ||
-                            p.out.plane_stride > (int64_t(1) << 44) || p.out.ntb > 12))
+    const bool m3 = g.products == 3;
+    if (g.products != 0 && g.products != 4 && !(m3 && tc_form_has_3m(g.form))) return cudaErrorInvalidValue;
+    if (m3 && g.chunk_bytes != 32) return cudaErrorInvalidValue;  // tc_prepare sets it
+    // a 3M GEMM writes 3M planes (modes 5-7), a 4M GEMM 4M planes (1-4)
+    if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || p.out.mode < 1 || p.out.mode > 7 ||
+                            mode_3m(p.out.mode) != m3 || p.out.plane_stride > (int64_t(1) << 44) ||
+                            p.out.ntb > 12))
         return cudaErrorInvalidValue;
     // a scaled planar output needs a scaled form (its operands' exponents)
     // and the slot through which the next step reads the planes' exponent
-    if ((p.out.mode == 3 || p.out.mode == 4) &&
-        (!((g.form == TN_FP16S && p.out.mode == 3) || (g.form == TN_FP16X3 && p.out.mode == 4)) || !g.max_slot))
+    if (mode_scaled(p.out.mode) &&
+        (!((g.form == TN_FP16S && p.out.mode == 3) || (g.form == TN_FP16X3 && mode_base(p.out.mode) == 4)) ||
+         !g.max_slot))
         return cudaErrorInvalidValue;
     if (g.max_slot) {
         if (p.ksplit > 1) return cudaErrorInvalidValue;  // partial tiles: their max is not C's
@@ -803,6 +887,11 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
         sm_count[dev].store(sms, std::memory_order_relaxed);
     }
     dim3 grid((unsigned)(p.tiles < sms ? p.tiles : sms));
+    if (m3) {
+        if (g.form == TN_TF32X3) return launch_variant<kTF32, 32, true>(g, p, grid, s);
+        if (g.form == TN_BF16X3) return launch_variant<kBF16, 32, true>(g, p, grid, s);
+        return launch_variant<kFP16X3, 32, true>(g, p, grid, s);
+    }
     if (g.form == TN_TF32X3)
         return g.chunk_bytes == 64 ? launch_variant<kTF32, 64>(g, p, grid, s) : launch_variant<kTF32, 128>(g, p, grid, s);
     if (g.form == TN_BF16X3)

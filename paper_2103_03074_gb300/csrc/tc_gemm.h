@@ -15,7 +15,7 @@ namespace tn {
 // destination order (tb / tpos), so a warp's 64 consecutive elements land in
 // as few 128-byte segments per plane as the layout allows.
 struct TcPlanarOut {
-    int mode;               // 0: complex64 C (no split); 1 (bf16) or 2 (tf32) hi/lo split as in BitPermArgs
+    int mode;               // 0: complex64 C (no split); else a split mode of BitPermArgs (1-4; 5-7 for 3M GEMMs)
     void *planes;
     int64_t plane_stride;   // elements per plane
     int nH, nM, nN;         // bits of h, m, n
@@ -38,6 +38,11 @@ struct TcGemm {
     const unsigned *scales;  // FP16S / FP16X3: device max-abs slots of A and B (float bits)
     unsigned *max_slot;      // optional: receives max |re|, |im| of C (float bits; zeroed by the launch)
     TcPlanarOut out;         // out.mode 0: plain complex64 C
+    // real products per complex product: 4 (0 = 4: P = A_re [B_re|B_im],
+    // Q = A_im [B_re|B_im]) or 3 (Gauss 3M: A_re B_re, A_im B_im and
+    // (A_re + A_im)(B_re + B_im); six planes per operand, split modes 5-7;
+    // hi/lo forms only)
+    int products;
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
 };
@@ -50,8 +55,13 @@ bool tc_form_available(tn_form form);
 int tc_plane_bytes(tn_form form);
 
 // planes per operand: 4 for the hi/lo split forms (re_hi, im_hi, re_lo,
-// im_lo: BF16x3, TF32x3, FP16X3), 2 for FP16S (re, im)
-int tc_plane_count(tn_form form);
+// im_lo: BF16x3, TF32x3, FP16X3), 2 for FP16S (re, im); with products == 3
+// (the 3M product of the hi/lo forms) 6 (re_hi, im_hi, s_hi, re_lo, im_lo,
+// s_lo)
+int tc_plane_count(tn_form form, int products = 4);
+
+// true if the form has a 3M variant (the hi/lo split forms)
+bool tc_form_has_3m(tn_form form);
 
 // K bytes between accumulator read-outs when TcGemm::flush_bytes is 0: the
 // largest interval that keeps the form's accuracy (the read-out interval

@@ -383,3 +383,86 @@ def test_graph_replay_matches_oracle(tn, form):
     assert rel(to_complex(part), oc.sliced_sum(net.labels, net.data, net.open_labels, sliced, 3, 13)) < TOL
     assert plan.stats()["graph_replays"] >= 3
     plan.close()
+
+
+@pytest.mark.parametrize("form", ["tf32x3", "fp16x3", "bf16x3"])
+def test_cfg2_amplitudes_3m(tn, form):
+    """The 30-qubit workload with Gauss's 3M complex product on the tensor
+    cores (tc_products 3): against the FP64 golden amplitudes at the form's
+    bound (1e-5 for TF32x3 and FP16X3; BF16x3 its own), with the GEMMs
+    writing the next step's six planes from their epilogue and, separately,
+    through split passes (tc_planar -1): the two runs agree to the forms' own
+    accuracy."""
+    import torch
+    cfg = make_config(2)
+    ref = load_golden("cfg2_amplitudes.txt")
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, _ = tn.find_order(L, O, tn.search_opts(trials=16384, n_sliced=8))
+    got = {}
+    for planar in (0, -1):
+        plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(tc_planar=planar, tc_products=3,
+                                                                            use_graph=1))
+        desc = plan.describe()
+        assert "tensor-core 3M" in desc and "tensor-core ksplit" not in desc
+        amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+        for _ in range(2):  # eager, then graph replay
+            amp.zero_()
+            plan.contract(0, 1 << len(sliced), amp)
+        got[planar] = to_complex(amp)
+        plan.close()
+    bound = BOUND.get(form, TOL)
+    print(f"cfg2 3M {form}: relative L2 error {rel(got[0], ref):.3e} (split passes: {rel(got[-1], ref):.3e})")
+    assert rel(got[0], ref) < bound and rel(got[-1], ref) < bound
+    assert rel(got[0], got[-1]) < {"fp16x3": 5e-6, "bf16x3": 2e-5}.get(form, 2e-6)
+
+
+@pytest.mark.parametrize("n_new,form", [(4, "fp32"), (4, "fp16x3"), (5, "fp32"), (5, "fp16x3")])
+def test_intermediate_beyond_2_32_elements(tn, n_new, form):
+    """Offsets past 32 bits: the explicit tree's first step is the outer
+    product of A (17 labels) and B (16 labels), a 2^33-element intermediate
+    in layout [a][b] whose a labels sit at bit positions 16..32.  The second
+    step contracts 8 of those a labels with W: a small step (W of 12 labels,
+    n_new = 4: its K bits at positions up to 32 of T) or a GEMM (W of 13
+    labels, n_new = 5: the intermediate is first permuted / split into the
+    GEMM's layout, a rank-33 bit permutation).  Vectors then close every
+    label but four.  The FP64 oracle contracts the same network in its own
+    order (the vectors first), so its intermediates stay small.  Bound: 1e-5
+    (plain sums of a few hundred products per output)."""
+    import torch
+    rng = np.random.default_rng(33 + n_new)
+
+    def rnd(rank):
+        return ((rng.standard_normal((2,) * rank) + 1j * rng.standard_normal((2,) * rank)) /
+                np.sqrt(2.0 ** rank)).astype(np.complex64)
+    a = list(range(100, 117))
+    b = list(range(200, 216))
+    w = list(range(300, 300 + n_new))
+    labels = [a, b, a[:8] + w]
+    tensors = [rnd(17), rnd(16), rnd(8 + n_new)]
+    open_l = [w[0], w[1], b[0], b[1]]
+    closed = a[8:] + b[2:] + w[2:]
+    for lab in closed:
+        labels.append([lab])
+        tensors.append(rnd(1) * np.float32(np.sqrt(2.0)))
+    n = len(labels)
+    tree = [(0, 1), (n, 2)]  # A x B (2^33 elements), then with W
+    cur = n + 1
+    for j in range(3, n):
+        tree.append((cur, j))
+        cur += 1
+    ref = oc.contract(labels, tensors, open_l)
+    plan = tn.Plan(labels, tensors, open_l, [], tree, form=form)
+    desc = plan.describe()
+    amp = dev_zeros(len(open_l))
+    plan.contract(0, 1, amp)
+    got = to_complex(amp)
+    plan.close()
+    torch.cuda.empty_cache()
+    print(f"2^33-element intermediate, {form}, W with {8 + n_new} labels: relative L2 error {rel(got, ref):.2e}")
+    # the steps this test is for: a small step reading the 2^33-element T with
+    # K bits up to position 32, or (FP16X3) a rank-33 split pass before the GEMM
+    if n_new == 4:
+        assert "step 1 small rows=33554432 K=256" in desc
+    elif form == "fp16x3":
+        assert "step 1 split rank=33" in desc
+    assert rel(got, ref.reshape(-1)) < TOL

@@ -104,8 +104,9 @@ def test_cfg4_sampled_amplitudes(tn, cfg4_plan_inputs, form):
     assert 0.8 < p_s1 * 2.0 ** (cfg["circuit"].n_qubits - len(O)) < 1.2
 
 
-@pytest.mark.parametrize("form", ["fp16x3", "tf32x3", "fp32"])
-def test_cfg4_stored_tree_sampled_amplitudes(tn, form):
+@pytest.mark.parametrize("form,products", [("fp16x3", 4), ("tf32x3", 4), ("fp32", 4), ("fp16x3", 3),
+                                           ("tf32x3", 3)])
+def test_cfg4_stored_tree_sampled_amplitudes(tn, form, products):
     """The benchmark's own plan: the stored bipartition tree of the 14-cycle
     workload (paper_2103_03074_gb300/trees/syc53_m14.json), every slice, in
     the forms its headline may take, against the same FP64 oracle entries at
@@ -118,13 +119,13 @@ def test_cfg4_stored_tree_sampled_amplitudes(tn, form):
     L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
     tree, sliced, st = make_trees.load("syc53_m14", L, O)
     idx, ref = load_sampled("cfg4_amplitudes_sampled.txt")
-    plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1))
+    plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(use_graph=1, tc_products=products))
     amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
     plan.contract(0, 1 << len(sliced), amp)
     got = to_complex(amp)
     e = rel(got[idx], ref)
-    print(f"cfg4 stored tree {form}: {len(sliced)} sliced bonds, relative L2 error over {len(idx)} sampled "
-          f"entries {e:.3e}")
+    print(f"cfg4 stored tree {form} ({products} real products): {len(sliced)} sliced bonds, relative L2 error over "
+          f"{len(idx)} sampled entries {e:.3e}")
     assert e < 1e-5
     n = cfg["circuit"].n_qubits
     p_s1, f, pmax = tn.probabilities_xeb(amp, len(O), n)

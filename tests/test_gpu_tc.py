@@ -105,6 +105,42 @@ def emulate_fp16x3_4m(a, b):
     return ((rmm(ar, br) - rmm(ai, bi)) + 1j * (rmm(ar, bi) + rmm(ai, br))) * 2.0 ** (ea + eb)
 
 
+def emulate_split_3m(a, b, form):
+    """Gauss's 3M product of the split forms: T1 = A_re B_re, T2 = A_im B_im,
+    T3 = (A_re + A_im)(B_re + B_im) with the sums rounded to FP32 (after the
+    power-of-two scale for FP16X3), each real product hi*hi + hi*lo + lo*hi
+    of round-to-nearest pieces accumulated exactly; re = T1 - T2,
+    im = T3 - T1 - T2."""
+    def scale_of(x):
+        if form != "fp16x3":
+            return 0
+        mx = max(np.abs(x.real).max(), np.abs(x.imag).max())
+        return int(np.frexp(np.float32(mx))[1] - 14)
+
+    def parts(v):
+        v = np.asarray(v, np.float32)
+        if form == "fp16x3":
+            h = v.astype(np.float16).astype(np.float32)
+            lo = (v - h).astype(np.float16).astype(np.float32)
+        else:
+            rnd = bf16 if form == "bf16x3" else tf32
+            h = rnd(v)
+            lo = rnd(v - h)
+        return h.astype(np.float64), lo.astype(np.float64)
+
+    def rmm(x, y):
+        xh, xl = parts(x)
+        yh, yl = parts(y)
+        return xh @ yh + xh @ yl + xl @ yh
+    ea, eb = scale_of(a), scale_of(b)
+    a = a.astype(np.complex64) * np.float32(2.0 ** -ea)
+    b = b.astype(np.complex64) * np.float32(2.0 ** -eb)
+    ar, ai = a.real.astype(np.float32), a.imag.astype(np.float32)
+    br, bi = b.real.astype(np.float32), b.imag.astype(np.float32)
+    t1, t2, t3 = rmm(ar, br), rmm(ai, bi), rmm(ar + ai, br + bi)
+    return ((t1 - t2) + 1j * (t3 - t1 - t2)) * 2.0 ** (ea + eb)
+
+
 def rand_c64(seed, shape):
     rng = np.random.default_rng(seed)
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
@@ -181,3 +217,76 @@ def test_batched_gemm_split(tn, form):
                 for s in range(4))
     assert rel(got, exact) < (2e-3 if form == "fp16s" else 1e-5)
     plan.close()
+
+
+# 3M against its emulation: the tensor core's truncating accumulation over the
+# MMAs between read-outs, as for the 4M form (<= 1e-6 there), on sums that are
+# about twice as large (T3 holds (A_re + A_im)(B_re + B_im)) and partly
+# cancel in im = T3 - T1 - T2: 3e-6 allowed.  A dropped or misplaced product
+# term is off by ~5e-4 (tf32) or ~4e-3 (bf16).
+TOL_3M_EMU = 3e-6
+
+
+@pytest.mark.parametrize("m,k,n,a_kfirst,b_nfirst", [
+    (10, 10, 8, False, False),
+    (10, 9, 8, True, True),
+    (6, 7, 6, False, True),      # M = 64 < 128-row tile
+    (9, 4, 9, False, True),      # K = 16
+    (10, 3, 10, True, False),    # K = 8: a 16-byte fp16 plane row inside the 32-byte chunk
+    (9, 11, 6, True, False),
+])
+@pytest.mark.parametrize("form", ["tf32x3", "fp16x3", "bf16x3"])
+def test_single_gemm_3m(tn, form, m, k, n, a_kfirst, b_nfirst):
+    """The 3M product (tc_products 3, six planes per operand, 9 MMAs of
+    128 x 64 per K step) against the exact product at the form's bound and
+    against the emulation of the same split arithmetic."""
+    import torch
+    M, K, N = 1 << m, 1 << k, 1 << n
+    A = rand_c64(m * 100 + k + 7, (M, K))
+    B = rand_c64(n * 100 + k + 8, (K, N))
+    ml, kl, nl = list(range(0, m)), list(range(100, 100 + k)), list(range(200, 200 + n))
+    la = (kl + ml) if a_kfirst else (ml + kl)
+    ta = (A.T if a_kfirst else A).reshape((2,) * (m + k))
+    lb = (nl + kl) if b_nfirst else (kl + nl)
+    tb = (B.T if b_nfirst else B).reshape((2,) * (k + n))
+    plan = tn.Plan([la, lb], [ta, tb], ml + nl, [], [(0, 1)], form=form, opts=tn.plan_opts(tc_products=3))
+    assert "tensor-core 3M" in plan.describe()
+    amp = torch.zeros(2 * M * N, dtype=torch.float64, device="cuda")
+    plan.contract(0, 1, amp)
+    torch.cuda.synchronize()
+    plan.close()
+    g = amp.cpu().numpy()
+    got = (g[0::2] + 1j * g[1::2]).reshape(M, N)
+    exact = A.astype(np.complex128) @ B.astype(np.complex128)
+    emu = emulate_split_3m(A, B, form)
+    print(f"3M {form} {M}x{K}x{N}: vs exact {rel(got, exact):.2e}, vs emulation {rel(got, emu):.2e}")
+    assert rel(got, exact) < (3e-5 if form == "bf16x3" else 1e-6 * 3)
+    assert rel(got, emu) < TOL_3M_EMU
+
+
+@pytest.mark.parametrize("form", ["tf32x3", "fp16x3"])
+def test_batched_gemm_3m_matches_4m(tn, form):
+    """A batched GEMM (two batch labels) in the 3M and the 4M product: both
+    within the form's bound of the exact sum, and of each other."""
+    import torch
+    m, k, n = 9, 8, 7
+    M, K, N = 1 << m, 1 << k, 1 << n
+    ml, kl, nl = list(range(m)), list(range(100, 100 + k)), list(range(200, 200 + n))
+    h = 300
+    A = rand_c64(15, (4, M, K))
+    B = rand_c64(16, (4, K, N))
+    exact = sum(A[2 * (s & 1) + (s >> 1)].astype(np.complex128) @ B[2 * (s & 1) + (s >> 1)].astype(np.complex128)
+                for s in range(4))
+    got = {}
+    for prod in (3, 4):
+        plan = tn.Plan([[h, h + 1] + ml + kl, [h, h + 1] + kl + nl],
+                       [A.reshape((2,) * (m + k + 2)), B.reshape((2,) * (k + n + 2))], ml + nl, [h, h + 1],
+                       [(0, 1)], form=form, opts=tn.plan_opts(batch_log2=2, tc_products=prod))
+        amp = torch.zeros(2 * M * N, dtype=torch.float64, device="cuda")
+        plan.contract(0, 4, amp)
+        torch.cuda.synchronize()
+        plan.close()
+        g = amp.cpu().numpy()
+        got[prod] = (g[0::2] + 1j * g[1::2]).reshape(M, N)
+        assert rel(got[prod], exact) < 3e-6
+    assert rel(got[3], got[4]) < 5e-6

@@ -84,11 +84,13 @@ def profile_plan(tn, plan, n_slices, reps=5):
 ROOF_SCALE = 16.0
 
 # Held-out error bounds of the trained model, as fractions of two baselines'
-# errors on the same held-out steps.  Measured with single-pass timings
-# (before per-step medians): model / mean-predictor 0.44, 0.48, 0.50, 0.51
-# over four runs.  The bound sits well above that spread.
+# errors on the same held-out steps.  Measured on GB300: with single-pass
+# timings, model / mean-predictor 0.44, 0.48, 0.50, 0.51 over four runs; with
+# per-step medians of 5 passes, 0.098 / 0.200 = 0.49 against the mean
+# predictor and 0.098 / 0.171 = 0.57 against the roofline time plus the mean
+# residual.  The bounds sit well above that spread.
 MODEL_VS_MEAN = 0.75
-MODEL_VS_ANALYTIC = 1.0
+MODEL_VS_ANALYTIC = 0.85
 
 
 def residual(X, y):
@@ -227,6 +229,9 @@ def test_learned_ranking_versus_analytic_cost(tn):
     print(f"ranking over {len(HELD_OUT)} held-out circuits: MAC picks {tot_a:.3f} ms, roofline-time picks "
           f"{tot_e:.3f} ms, model picks {tot_m:.3f} ms, best {tot_best:.3f} ms; gain {tot_a / tot_m:.3f}x over "
           f"MACs, {tot_e / tot_m:.3f}x over roofline time; median |log2(pred/meas)| {np.median(errs):.2f}")
+    # measured on GB300: model picks 3.223 ms, MAC picks 3.385 ms (1.050x),
+    # roofline-time picks 3.405 ms (1.056x); timing noise between repeated
+    # medians is about 1%, so 3% slack
     assert tot_m <= 1.03 * tot_a
     assert tot_m <= 1.03 * tot_e
     # the library-side ranking inside the order search uses the same model
