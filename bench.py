@@ -326,9 +326,10 @@ class OracleSampler:
             if self.it is None:
                 self._next_amplitude()
             try:
-                m, tot = next(self.it)
-                self.macs += m
-                self.amp_macs = tot
+                t, step_macs = next(self.it)
+                self.macs += step_macs[t]
+                self.amp_macs = float(sum(step_macs))
+                self.step_macs = step_macs
                 self.steps += 1
             except StopIteration:
                 self.it = None
@@ -362,9 +363,9 @@ def cpu_baseline(workload_name, sliced, n_slices, budget_s=15.0):
     all-core sample finished in its first third; every number says what its
     sample was."""
     smp = OracleSampler(workload_name, sliced, n_slices)
-    smp.run(budget_s=budget_s / 3)
+    smp.run(budget_s=budget_s / 6)
     prefix = max(smp.steps, 1)
-    smp.run(budget_s=budget_s * 2 / 3)
+    smp.run(budget_s=budget_s * 5 / 6)
     out = {"value": smp.rate(), "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
            "sample": smp.describe()}
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -401,20 +402,31 @@ def run_reference(args):
             smp.run(steps=1)
         how = "one whole slice per step"
     else:
-        # one closed amplitude in all, cut into warm-up + timed chunks of
-        # equal MACs (a chunk ends between pairwise steps)
+        # one closed amplitude in all, its pairwise steps cut into warm-up +
+        # timed chunks at fixed step indices where the cumulative MACs cross
+        # j / (W + K) of the total (a chunk holding no boundary-crossing step
+        # is empty; one holding a large step is long)
         smp.run(steps=1)
-        chunk = smp.amp_macs / (args.warmup + args.steps)
-        for _ in range(args.warmup):
-            smp.run(macs=chunk)
-        how = f"1/{args.warmup + args.steps} of one closed amplitude's MACs per step"
+        n_chunks = args.warmup + args.steps
+        cum, ends = 0.0, []
+        for i, m in enumerate(smp.step_macs):
+            cum += m
+            while len(ends) < n_chunks and cum >= (len(ends) + 1) * smp.amp_macs / n_chunks * (1 - 1e-12):
+                ends.append(i + 1)
+        ends += [len(smp.step_macs)] * (n_chunks - len(ends))
+        done = 1
+        for j in range(args.warmup):
+            smp.run(steps=max(ends[j] - done, 0))
+            done = max(done, ends[j])
+        how = f"the pairwise steps of one closed amplitude cut into {n_chunks} chunks of about equal MACs"
     macs0, secs0, units0 = smp.macs, smp.secs, smp.units
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for j in range(args.warmup, args.warmup + args.steps):
         if smp.small:
             smp.run(steps=1)
         else:
-            smp.run(macs=chunk)
+            smp.run(steps=max(ends[j] - done, 0))
+            done = max(done, ends[j])
     dt = time.perf_counter() - t0
     v = smp.rate(smp.macs - macs0, smp.secs - secs0, smp.units - units0)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s", "n_gpus": args.gpus,
@@ -856,16 +868,21 @@ def run_gemm(args):
     tensors = [A.reshape((2,) * (h + m + k)), B.reshape((2,) * (h + k + n))]
     out_l, tree = ml + nl, [(0, 1)]
     if args.gemm_next:
-        # a second GEMM C[h,m,n] D[n,p] -> [m,p] (D of 2^(n+p) values, more than
-        # a small step takes) makes the first GEMM write its output as the
-        # second one's split planes (the planar epilogue)
-        p = args.gemm_next
+        # a second GEMM C[h,m,n] D[.., p] (D of more values than a small step
+        # takes) makes the first GEMM write its output as the second one's
+        # split planes (the planar epilogue).  D contracts all n labels, or
+        # with --gemm-next-low L the lowest L m labels and the lowest L n
+        # labels, so that the first GEMM's half tile is one contiguous run of
+        # the planes (as in the 53-qubit step's largest GEMM)
+        p, low = args.gemm_next, args.gemm_next_low
         pl = list(range(400, 400 + p))
-        D = (rng.standard_normal(2 ** (n + p)) + 1j * rng.standard_normal(2 ** (n + p))).astype(np.complex64)
-        labels.append(nl + pl)
-        tensors.append(D.reshape((2,) * (n + p)))
-        out_l, tree = ml + pl, [(0, 1), (3, 2)]
-    plan = make_plan(tn, labels, tensors, out_l, hl, tree, name, use_graph=1)
+        dl = (ml[m - low:] + nl[n - low:] + pl) if low else (nl + pl)
+        D = (rng.standard_normal(2 ** len(dl)) + 1j * rng.standard_normal(2 ** len(dl))).astype(np.complex64)
+        labels.append(dl)
+        tensors.append(D.reshape((2,) * len(dl)))
+        out_l = (ml[:m - low] + nl[:n - low] + pl) if low else (ml + pl)
+        tree = [(0, 1), (3, 2)]
+    plan = make_plan(tn, labels, tensors, out_l, hl, tree, name, use_graph=1, tc_chunk_bytes=args.tc_chunk)
     amp = torch.zeros(2 << len(out_l), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -900,6 +917,9 @@ def main():
     ap.add_argument("--gemm-next", type=int, default=0,
                     help="--workload gemm: follow the GEMM by a second one of log2 N = this, so that the first "
                          "writes the second one's split planes from its epilogue")
+    ap.add_argument("--gemm-next-low", type=int, default=0,
+                    help="--workload gemm with --gemm-next: the second GEMM contracts the lowest L m and n labels")
+    ap.add_argument("--tc-chunk", type=int, default=0, help="tensor-core K chunk bytes (plan option tc_chunk_bytes)")
     ap.add_argument("--search-method", default=None, choices=["greedy", "bipartition", "mixed"],
                     help="search a fresh tree (randomised greedy, hierarchical bipartition, or both) instead of "
                          "the workload's stored tree")

@@ -116,9 +116,9 @@ def contract(labels: Sequence[Sequence[int]], tensors: Sequence[np.ndarray],
 
 
 def contract_iter(labels, tensors, open_labels, fixed=None, tree=None):
-    """contract() as a generator: after each pairwise step it yields
-    (complex MACs of that step, complex MACs of the whole tree), where a pair
-    holding the labels U in total costs 2^|U| MACs (Fig. 3); its return value
+    """contract() as a generator: after pairwise step t it yields
+    (t, per-step complex MACs of the whole tree), where a pair holding the
+    labels U in total costs 2^|U| MACs (Fig. 3); its return value
     (StopIteration.value) is contract()'s result.  Lets a caller time a
     bounded part of a long contraction."""
     fixed = fixed or {}
@@ -150,7 +150,6 @@ def contract_iter(labels, tensors, open_labels, fixed=None, tree=None):
         step_macs.append(2.0 ** len(u))
         sets[nxt] = {lab for lab in u if lab in open_set or sum(lab in s2 for s2 in sets.values()) > 0}
         nxt += 1
-    total_macs = float(sum(step_macs))
     nxt = len(labs)
     for t, (a, b) in enumerate(tree):
         la, ta = nodes.pop(a)
@@ -162,7 +161,7 @@ def contract_iter(labels, tensors, open_labels, fixed=None, tree=None):
         lc = [lab for lab in la if lab not in shared] + [lab for lab in lb if lab not in shared]
         nodes[nxt] = (lc, tc)
         nxt += 1
-        yield step_macs[t], total_macs
+        yield t, step_macs
     # any disconnected leftovers: outer products
     items = list(nodes.values())
     lc, tc = items[0]

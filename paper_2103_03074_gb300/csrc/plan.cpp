@@ -1840,11 +1840,24 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
         }
         case OP_GEMM:
             if (op.gemm_variant == 1)
+            {
+                // planar output: how many of the destination's lowest bits
+                // come from the epilogue's half tile in order (its store runs
+                // are 2^run elements per plane), and whether lanes store four
+                // neighbouring elements
+                int run = 0;
+                while (run < op.tc.out.ntb && op.tc.out.tpos[run] == run) run++;
+                char pl[64] = "";
+                if (op.tc.out.mode)
+                    std::snprintf(pl, sizeof pl, " run_bits=%d%s", run,
+                                  (op.tc.out.ntb >= 7 && op.tc.out.tpos[0] == 0 && op.tc.out.tpos[1] == 1) ? " quad"
+                                                                                                            : "");
                 std::snprintf(line, sizeof line,
-                              "%s step %d gemm H=%lld M=%lld N=%lld K=%lld tensor-core%s ksplit=%d out=%s", phase,
+                              "%s step %d gemm H=%lld M=%lld N=%lld K=%lld tensor-core%s ksplit=%d out=%s%s", phase,
                               op.step, (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N,
                               (long long)op.gemm.K, op.tc.products == 3 ? " 3M" : "", op.tc.ksplit,
-                              op.tc.out.mode ? "planes" : "complex64");
+                              op.tc.out.mode ? "planes" : "complex64", pl);
+            }
             else
                 std::snprintf(line, sizeof line, "%s step %d gemm H=%lld M=%lld N=%lld K=%lld fp32", phase, op.step,
                               (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N, (long long)op.gemm.K);

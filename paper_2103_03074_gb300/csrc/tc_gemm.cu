@@ -366,12 +366,7 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_
     const int n_hi = 1 << (o.ntb - nlo);
     if (L.quad) {
         const int np = mode_planes(o.mode);
-        for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
-            const uint2 g = jtab[jh];
-            PiecesT<M3> pc[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
-            const uint64_t d0 = base + g.y + L.d[0];  // a multiple of 4
+        auto store4 = [&](uint64_t d0, const PiecesT<M3> *pc) {  // d0 a multiple of 4
             if (mode_word(o.mode)) {
                 uint4 *P = reinterpret_cast<uint4 *>(o.planes);
                 for (int q = 0; q < np; q++)
@@ -382,6 +377,30 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_
                     P[(d0 + q * o.plane_stride) >> 2] =
                         make_uint2(pc[0].q[q] | (pc[1].q[q] << 16), pc[2].q[q] | (pc[3].q[q] << 16));
             }
+        };
+        int jh = fw;
+        // two groups per iteration: their shared-memory loads, splits and
+        // stores are independent, so their latencies overlap
+        for (; jh + kFlushWarps < n_hi; jh += 2 * kFlushWarps) {
+            const uint2 g0 = jtab[jh], g1 = jtab[jh + kFlushWarps];
+            float2 v[8];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                v[q] = st[(int)g0.x + L.s[q]];
+                v[4 + q] = st[(int)g1.x + L.s[q]];
+            }
+            PiecesT<M3> pc[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) pc[i] = split_t<M3>(o.mode, v[i], e);
+            store4(base + g0.y + L.d[0], pc);
+            store4(base + g1.y + L.d[0], pc + 4);
+        }
+        for (; jh < n_hi; jh += kFlushWarps) {
+            const uint2 g = jtab[jh];
+            PiecesT<M3> pc[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
+            store4(base + g.y + L.d[0], pc);
         }
         return;
     }
@@ -677,10 +696,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int hp = 0; hp < 2; hp++) {
                 if ((lg >> 1) == hp) {
+                    // two complex values per 16-byte store (rows are 528 bytes
+                    // apart: eight lanes cover the 32 banks, no conflicts)
                     const int r = (lg & 1) * 32 + lane;
+                    float4 *row4 = reinterpret_cast<float4 *>(stage_out + r * RS + half * 32);
 #pragma unroll
-                    for (int j = 0; j < 32; j++)
-                        stage_out[r * RS + half * 32 + j] = make_float2(acc_re[j], acc_im[j]);
+                    for (int j = 0; j < 32; j += 2)
+                        row4[j >> 1] = make_float4(acc_re[j], acc_im[j], acc_re[j + 1], acc_im[j + 1]);
                 }
                 asm volatile("bar.sync 1, 256;" ::: "memory");
                 if (p.out.mode != 0) {
@@ -776,12 +798,25 @@ bool tc_gemm_suitable(const GemmArgs &a) {
 }
 
 int tc_choose_ksplit(const GemmArgs &a, tn_form form) {
+    // the persistent kernel runs one CTA per SM over tiles x K parts; a grid
+    // with fewer tiles than SMs splits K so that the work units fill whole
+    // waves of the 152 SMs (the makespan is ceil(units / 152) units), with at
+    // least 4 K chunks of 64 bytes per part and at most 4 waves of units
+    constexpr int64_t kSms = 152;
     const int64_t tiles = ((a.M + TM - 1) / TM) * ((a.N + TN - 1) / TN) * a.H;
+    if (tiles >= kSms) return 1;
     const int64_t chunks = (a.K * tc_plane_bytes(form) + 63) / 64;
-    int64_t s = 1;
-    // at least 4 chunks per part; aim for two CTAs per SM
-    while (tiles * s * 2 <= 2 * 152 && chunks / (s * 2) >= 4 && a.H * s * 2 <= 65535) s *= 2;
-    return (int)s;
+    int64_t best = 1;
+    double best_eff = 0.0;
+    for (int64_t s = 1; s <= 64 && tiles * s <= 4 * kSms && chunks / s >= 4; s++) {
+        const int64_t units = tiles * s;
+        const double eff = (double)units / (double)(((units + kSms - 1) / kSms) * kSms);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = s;
+        }
+    }
+    return (int)best;
 }
 
 bool tc_prepare(TcGemm &g) {
@@ -790,9 +825,10 @@ bool tc_prepare(TcGemm &g) {
     if (g.products != 4 && (g.products != 3 || !tc_form_has_3m(g.form))) return false;
     if (g.products == 3) {
         // six planes per operand: 32-byte K chunks (one MMA K step, 32-byte
-        // swizzle) keep five ring stages in shared memory
-        g.chunk_bytes = 32;
-        if (g.flush_bytes < 32 || g.flush_bytes % 32) g.flush_bytes = default_flush_bytes(g.form);
+        // swizzle) keep five ring stages in shared memory; 64-byte chunks on
+        // request (two stages)
+        g.chunk_bytes = (g.chunk_bytes == 64 && g.a.K * es >= 64) ? 64 : 32;
+        if (g.flush_bytes < g.chunk_bytes || g.flush_bytes % g.chunk_bytes) g.flush_bytes = default_flush_bytes(g.form);
     } else {
         if (g.chunk_bytes != 64 && g.chunk_bytes != 128) g.chunk_bytes = kDefaultChunkBytes;
         if (g.flush_bytes < g.chunk_bytes)
@@ -843,7 +879,7 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     // own offsets 32-bit, checked when the plan builds the tables)
     const bool m3 = g.products == 3;
     if (g.products != 0 && g.products != 4 && !(m3 && tc_form_has_3m(g.form))) return cudaErrorInvalidValue;
-    if (m3 && g.chunk_bytes != 32) return cudaErrorInvalidValue;  // tc_prepare sets it
+    if (m3 && g.chunk_bytes != 32 && g.chunk_bytes != 64) return cudaErrorInvalidValue;  // tc_prepare sets it
     // a 3M GEMM writes 3M planes (modes 5-7), a 4M GEMM 4M planes (1-4)
     if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || p.out.mode < 1 || p.out.mode > 7 ||
                             mode_3m(p.out.mode) != m3 || p.out.plane_stride > (int64_t(1) << 44) ||
@@ -888,9 +924,13 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     }
     dim3 grid((unsigned)(p.tiles < sms ? p.tiles : sms));
     if (m3) {
-        if (g.form == TN_TF32X3) return launch_variant<kTF32, 32, true>(g, p, grid, s);
-        if (g.form == TN_BF16X3) return launch_variant<kBF16, 32, true>(g, p, grid, s);
-        return launch_variant<kFP16X3, 32, true>(g, p, grid, s);
+        const bool c64 = g.chunk_bytes == 64;
+        if (g.form == TN_TF32X3)
+            return c64 ? launch_variant<kTF32, 64, true>(g, p, grid, s) : launch_variant<kTF32, 32, true>(g, p, grid, s);
+        if (g.form == TN_BF16X3)
+            return c64 ? launch_variant<kBF16, 64, true>(g, p, grid, s) : launch_variant<kBF16, 32, true>(g, p, grid, s);
+        return c64 ? launch_variant<kFP16X3, 64, true>(g, p, grid, s)
+                   : launch_variant<kFP16X3, 32, true>(g, p, grid, s);
     }
     if (g.form == TN_TF32X3)
         return g.chunk_bytes == 64 ? launch_variant<kTF32, 64>(g, p, grid, s) : launch_variant<kTF32, 128>(g, p, grid, s);

@@ -290,3 +290,25 @@ def test_batched_gemm_3m_matches_4m(tn, form):
         got[prod] = (g[0::2] + 1j * g[1::2]).reshape(M, N)
         assert rel(got[prod], exact) < 3e-6
     assert rel(got[3], got[4]) < 5e-6
+
+
+@pytest.mark.parametrize("form", ["tf32x3", "fp16x3", "bf16x3"])
+def test_single_gemm_3m_64_byte_chunks(tn, form):
+    """The 3M kernel with 64-byte K chunks (two ring stages, two MMA K steps
+    per stage, tc_chunk_bytes 64) against the same emulation and bound."""
+    import torch
+    M, K, N = 1024, 1024, 256
+    A = rand_c64(71, (M, K))
+    B = rand_c64(72, (K, N))
+    ml, kl, nl = list(range(0, 10)), list(range(100, 110)), list(range(200, 208))
+    plan = tn.Plan([ml + kl, kl + nl], [A.reshape((2,) * 20), B.reshape((2,) * 18)], ml + nl, [], [(0, 1)],
+                   form=form, opts=tn.plan_opts(tc_products=3, tc_chunk_bytes=64))
+    amp = torch.zeros(2 * M * N, dtype=torch.float64, device="cuda")
+    plan.contract(0, 1, amp)
+    torch.cuda.synchronize()
+    plan.close()
+    g = amp.cpu().numpy()
+    got = (g[0::2] + 1j * g[1::2]).reshape(M, N)
+    exact = A.astype(np.complex128) @ B.astype(np.complex128)
+    assert rel(got, exact) < (3e-5 if form == "bf16x3" else 3e-6)
+    assert rel(got, emulate_split_3m(A, B, form)) < TOL_3M_EMU
