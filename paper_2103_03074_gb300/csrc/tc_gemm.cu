@@ -28,8 +28,10 @@
 // into a shared-memory ring (128-byte K chunks: 128-byte swizzle, 2 stages;
 // 64-byte chunks: 64-byte swizzle, 4 stages); warp 1 issues the MMAs of each
 // group of chunks into one of two tensor-memory accumulator sets {P, Q};
-// warps 4-11 read each finished group's accumulators (tcgen05.ld) and add
-// them into FP32 registers with round-to-nearest.  Reading out every few
+// warps 2-17 (four per tensor-memory lane group, a quarter of the tile's
+// columns each) read each finished group's accumulators (tcgen05.ld) and add
+// them into FP32 registers with round-to-nearest.  Sixteen epilogue warps (four
+// per scheduler) keep short-K GEMMs, whose time is the epilogue's, issuing.  Reading out every few
 // hundred bytes of K keeps the tensor core's truncating accumulation to a few
 // dozen MMAs (small correction addends aligned to a large running sum lose
 // their low bits, so the count of MMAs into one accumulator sets the error).
@@ -72,8 +74,12 @@ constexpr int kDefaultChunkBytes = 128;
 __host__ __device__ constexpr int default_flush_bytes(tn_form f) {
     return (f == TN_TF32X3 || f == TN_FP16X3) ? 256 : 512;
 }
-constexpr int kThreads = 384;  // 12 warps
-constexpr int kFlushWarp0 = 4, kFlushWarps = 8;
+// warp 0: TMA producer; warp 1: MMA issuer; warps 2-17: accumulator
+// read-out and epilogue, four per TMEM lane group (a warp reads the lanes
+// 32 (w mod 4) .. + 31), each a quarter of the tile's 64 complex columns
+constexpr int kFlushWarp0 = 2, kFlushWarps = 16;
+constexpr int kThreads = 32 * (kFlushWarp0 + kFlushWarps);  // 576
+constexpr int kCW = TN / (kFlushWarps / 4);                  // complex columns per epilogue warp: 16
 constexpr int kTmemCols = 512;  // 2 sets x {P, Q} x 128 columns
 
 // operand forms of the kernel template
@@ -222,7 +228,9 @@ struct GemmTcParams {
     int ksplit;        // K partitions (> 1: atomic adds into a zeroed C)
     int flush_chunks;  // chunks per accumulator read-out
     int gm, gn;        // M and N tiles
-    int64_t tiles;     // gn * gm * H * ksplit
+    int64_t tiles;     // gn * gm * H * ksplit (< 2^32: the tile decode is 32-bit)
+    int all_chunks;    // K chunks of the whole K range
+    int part_len;      // K chunks per K part (the last part may be shorter or empty)
     const unsigned *scales;  // scaled forms: max-abs slots of A and B (float bits)
     unsigned *max_slot;      // optional: atomic max of |re|, |im| over C (float bits)
     TcPlanarOut out;         // planar epilogue (out.mode > 0)
@@ -233,23 +241,27 @@ struct TileCoord {
     int64_t n0, m0;
     int h, part;
 };
-__device__ __forceinline__ TileCoord tile_coord(const GemmTcParams &p, int64_t t) {
+__device__ __forceinline__ TileCoord tile_coord(const GemmTcParams &p, int64_t tile) {
+    // 32-bit unsigned division (the launcher keeps the tile count below 2^32)
+    uint32_t t = (uint32_t)tile;
+    const uint32_t gn = (uint32_t)p.gn, gm = (uint32_t)p.gm, ks = (uint32_t)p.ksplit;
     TileCoord c;
-    c.n0 = (t % p.gn) * TN;
-    t /= p.gn;
-    c.m0 = (t % p.gm) * TM;
-    t /= p.gm;
-    c.h = (int)(t / p.ksplit);
-    c.part = (int)(t % p.ksplit);
+    uint32_t q = t / gn;
+    c.n0 = (int64_t)(t - q * gn) * TN;
+    t = q;
+    q = t / gm;
+    c.m0 = (int64_t)(t - q * gm) * TM;
+    t = q;
+    q = t / ks;
+    c.h = (int)q;
+    c.part = (int)(t - q * ks);
     return c;
 }
 
 // [c_begin, c_begin + count) = the K chunks of one K part
 __device__ __forceinline__ int part_chunks(const GemmTcParams &p, int part, int &c_begin) {
-    const int all_chunks = (int)((p.K + p.k_chunk - 1) / p.k_chunk);
-    const int per = (all_chunks + p.ksplit - 1) / p.ksplit;
-    c_begin = part * per;
-    const int c_end = min(all_chunks, c_begin + per);
+    c_begin = part * p.part_len;
+    const int c_end = min(p.all_chunks, c_begin + p.part_len);
     return c_end > c_begin ? c_end - c_begin : 0;
 }
 
@@ -357,16 +369,20 @@ __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane
 // Split the staged half tile (rows mh .. mh + 63) into the next step's
 // planes: warp fw of the 8 epilogue warps takes the groups j_hi = fw, fw + 8,
 // ...; each lane two (or four) neighbouring elements of a group.
+// base = the destination offset of the half tile's element (0, 0)
 template <bool M3>
-__device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_t mh, int64_t n0, const float2 *st,
+__device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base, const float2 *st,
                                              const uint2 *jtab, const PlanarLane &L, int fw, int lane, int e) {
-    const uint64_t base = scatter8((uint64_t)h, o.hpos, o.nH) | scatter8((uint64_t)mh, o.mpos, o.nM) |
-                          scatter8((uint64_t)n0, o.npos, o.nN);
     const int nlo = planar_nlo(o);
     const int n_hi = 1 << (o.ntb - nlo);
     if (L.quad) {
         const int np = mode_planes(o.mode);
-        auto store4 = [&](uint64_t d0, const PiecesT<M3> *pc) {  // d0 a multiple of 4
+        for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
+            const uint2 g = jtab[jh];
+            PiecesT<M3> pc[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
+            const uint64_t d0 = base + g.y + L.d[0];  // a multiple of 4
             if (mode_word(o.mode)) {
                 uint4 *P = reinterpret_cast<uint4 *>(o.planes);
                 for (int q = 0; q < np; q++)
@@ -377,30 +393,6 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_
                     P[(d0 + q * o.plane_stride) >> 2] =
                         make_uint2(pc[0].q[q] | (pc[1].q[q] << 16), pc[2].q[q] | (pc[3].q[q] << 16));
             }
-        };
-        int jh = fw;
-        // two groups per iteration: their shared-memory loads, splits and
-        // stores are independent, so their latencies overlap
-        for (; jh + kFlushWarps < n_hi; jh += 2 * kFlushWarps) {
-            const uint2 g0 = jtab[jh], g1 = jtab[jh + kFlushWarps];
-            float2 v[8];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                v[q] = st[(int)g0.x + L.s[q]];
-                v[4 + q] = st[(int)g1.x + L.s[q]];
-            }
-            PiecesT<M3> pc[8];
-#pragma unroll
-            for (int i = 0; i < 8; i++) pc[i] = split_t<M3>(o.mode, v[i], e);
-            store4(base + g0.y + L.d[0], pc);
-            store4(base + g1.y + L.d[0], pc + 4);
-        }
-        for (; jh < n_hi; jh += kFlushWarps) {
-            const uint2 g = jtab[jh];
-            PiecesT<M3> pc[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
-            store4(base + g.y + L.d[0], pc);
         }
         return;
     }
@@ -420,7 +412,7 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, int h, int64_
 }
 
 template <int KIND, int CB, bool M3>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(112)  // 576 threads x 112 registers fit the SM's 65536
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
     constexpr int NP = M3 ? 6 : (kind_split(KIND) ? 4 : 2);
@@ -565,9 +557,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (warp >= kFlushWarp0) {
-        // ---------------- accumulator read-out + epilogue (8 warps)
+        // ---------------- accumulator read-out + epilogue (16 warps)
         const int fw = warp - kFlushWarp0;
-        const int lg = warp & 3, half = fw >> 2;  // TMEM lane group, column half
+        const int lg = warp & 3, cq = fw >> 2;  // TMEM lane group, column quarter
         const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
         int e_scale = 0;
         if (kind_scaled(KIND))
@@ -610,19 +602,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const TileCoord tc = tile_coord(p, tile);
             int c_begin;
             const int n_chunks = part_chunks(p, tc.part, c_begin);
-            float acc_re[32], acc_im[32];
+            float acc_re[kCW], acc_im[kCW];
 #pragma unroll
-            for (int j = 0; j < 32; j++) acc_re[j] = acc_im[j] = 0.f;
+            for (int j = 0; j < kCW; j++) acc_re[j] = acc_im[j] = 0.f;
             const int n_groups = (n_chunks + F - 1) / F;
             for (int gi = 0; gi < n_groups; gi++, gc++) {
                 const int t = gc & 1, tuse = gc >> 1;
                 if (ok && !mbar_wait(smem_u32(&tfull[t]), tuse & 1)) ok = false;
                 if (!ok) continue;
                 fence_after();
-                const uint32_t base = tmem + t * 256 + lane_off + half * 32;
+                const uint32_t base = tmem + t * 256 + lane_off + cq * kCW;
                 if constexpr (M3) {
 #pragma unroll
-                    for (int q = 0; q < 2; q++) {
+                    for (int q = 0; q < kCW / 16; q++) {
                         uint32_t r0[16], r1[16], r2[16];
                         tmem_ld16(base + q * 16, r0);             // T1 = A_re B_re
                         tmem_ld16(base + TN + q * 16, r1);        // T2 = A_im B_im
@@ -637,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < (M3 ? 0 : 2); q++) {
+                for (int q = 0; q < (M3 ? 0 : kCW / 16); q++) {
                     uint32_t r0[16], r1[16], r2[16], r3[16];
                     tmem_ld16(base + q * 16, r0);        // P left:  A_re B_re
                     tmem_ld16(base + 64 + q * 16, r1);   // P right: A_re B_im
@@ -655,11 +647,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
             }
             if (kind_scaled(KIND)) {
-                // undo the operands' power-of-two scales (exact)
+                // undo the operands' power-of-two scales (exact): a product
+                // with 2^e_scale rounds as ldexpf does when 2^e_scale is a
+                // normal float
+                if (e_scale >= -126 && e_scale <= 127) {
+                    const float sc = __int_as_float((127 + e_scale) << 23);
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    acc_re[j] = ldexpf(acc_re[j], e_scale);
-                    acc_im[j] = ldexpf(acc_im[j], e_scale);
+                    for (int j = 0; j < kCW; j++) {
+                        acc_re[j] *= sc;
+                        acc_im[j] *= sc;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kCW; j++) {
+                        acc_re[j] = ldexpf(acc_re[j], e_scale);
+                        acc_im[j] = ldexpf(acc_im[j], e_scale);
+                    }
                 }
             }
             if (p.max_slot && ok) {
@@ -668,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // floats order like their bit patterns
                 float mx = 0.f;
 #pragma unroll
-                for (int j = 0; j < 32; j++) mx = fmaxf(mx, fmaxf(fabsf(acc_re[j]), fabsf(acc_im[j])));
+                for (int j = 0; j < kCW; j++) mx = fmaxf(mx, fmaxf(fabsf(acc_re[j]), fabsf(acc_im[j])));
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
                 if (mode_scaled(p.out.mode)) {
@@ -683,8 +686,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t m = tc.m0 + lg * 32 + lane;
                 if (ok && m < p.M && n_chunks > 0) {
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const int64_t n = tc.n0 + half * 32 + j;
+                    for (int j = 0; j < kCW; j++) {
+                        const int64_t n = tc.n0 + cq * kCW + j;
                         if (n < p.N) atomicAdd(Ch + m * p.sCm + n * p.sCn, make_float2(acc_re[j], acc_im[j]));
                     }
                 }
@@ -693,22 +696,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             // stage half a tile (64 rows) at a time, then write whole rows: a
             // warp stores one 512-byte row per instruction
             constexpr int RS = R::kOutRS;
+            // planar output: destination offset of the tile's element (0, 0)
+            const uint64_t pbase = p.out.mode != 0 ? (scatter8((uint64_t)tc.h, p.out.hpos, p.out.nH) |
+                                                      scatter8((uint64_t)tc.m0, p.out.mpos, p.out.nM) |
+                                                      scatter8((uint64_t)tc.n0, p.out.npos, p.out.nN))
+                                                   : 0;
 #pragma unroll
             for (int hp = 0; hp < 2; hp++) {
                 if ((lg >> 1) == hp) {
                     // two complex values per 16-byte store (rows are 528 bytes
                     // apart: eight lanes cover the 32 banks, no conflicts)
                     const int r = (lg & 1) * 32 + lane;
-                    float4 *row4 = reinterpret_cast<float4 *>(stage_out + r * RS + half * 32);
+                    float4 *row4 = reinterpret_cast<float4 *>(stage_out + r * RS + cq * kCW);
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2)
+                    for (int j = 0; j < kCW; j += 2)
                         row4[j >> 1] = make_float4(acc_re[j], acc_im[j], acc_re[j + 1], acc_im[j + 1]);
                 }
-                asm volatile("bar.sync 1, 256;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * kFlushWarps) : "memory");
                 if (p.out.mode != 0) {
+                    // m bit 6 is the half (m0 is a multiple of 128); with
+                    // M <= 64 the second half lies past M and is skipped
                     if (ok && tc.m0 + hp * (TM / 2) < p.M)
-                        planar_write<M3>(p.out, tc.h, tc.m0 + hp * (TM / 2), tc.n0, stage_out, jtab, pl, fw, lane,
-                                         e_out);
+                        planar_write<M3>(p.out, hp ? (pbase | (1ull << p.out.mpos[6])) : pbase, stage_out, jtab, pl,
+                                         fw, lane, e_out);
                 }
                 for (int rr = fw; ok && p.out.mode == 0 && rr < TM / 2; rr += kFlushWarps) {
                     const int64_t mm = tc.m0 + hp * (TM / 2) + rr;
@@ -723,7 +733,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (n + 1 < p.N) dst[(n + 1) * p.sCn] = stage_out[rr * RS + 2 * lane + 1];
                     }
                 }
-                asm volatile("bar.sync 1, 256;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * kFlushWarps) : "memory");
             }
         }
     }
@@ -905,6 +915,13 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.gm = (int)gm;
     p.gn = (int)gn;
     p.tiles = gm * gn * g.a.H * p.ksplit;
+    if (p.tiles >= (int64_t(1) << 32)) return cudaErrorInvalidConfiguration;  // 32-bit tile decode
+    {
+        const int64_t all = (p.K + p.k_chunk - 1) / p.k_chunk;
+        if (all > INT32_MAX) return cudaErrorInvalidConfiguration;
+        p.all_chunks = (int)all;
+        p.part_len = (int)((all + p.ksplit - 1) / p.ksplit);
+    }
     if (p.ksplit > 1) {
         // C = [H][M][N] contiguous (the plan's GEMM output layout)
         cudaError_t e = cudaMemsetAsync(g.a.C, 0, (size_t)(g.a.H * g.a.M * g.a.N) * sizeof(float2), s);

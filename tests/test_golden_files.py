@@ -5,6 +5,8 @@ oracle/ only)."""
 import importlib.util
 import os
 
+import pytest
+
 from tn_inputs.configs import make_config
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -46,3 +48,36 @@ def test_cfg4_file_holds_the_seeded_sample():
     # Porter-Thomas scale of a 53-qubit amplitude: |a|^2 averages 2^-53
     mean_p = sum(re * re + im * im for _, re, im in rows) / len(rows)
     assert 0.1 < mean_p * 2.0 ** 53 < 10
+
+
+def test_cfg3_file_holds_whole_members_in_script_order():
+    """tests/golden/cfg3_amplitudes.txt: the members make_golden.py lists,
+    in its order (a prefix while the script is still running), each with its
+    whole 2^k open-qubit tensor, and sum |a|^2 = P(s1) on the Porter-Thomas
+    scale 2^(k - n) (the sum of 2^k exponential variables: within a factor
+    of two for k >= 6)."""
+    import importlib.util
+    path = os.path.join(HERE, "golden", "cfg3_amplitudes.txt")
+    if not os.path.exists(path):
+        pytest.skip("no stored config-3 amplitudes")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    from tn_inputs.configs import batch_recipes
+    rs = batch_recipes()
+    members, vals = [], {}
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        i, j, re_, im_ = line.split()
+        i = int(i)
+        if not members or members[-1] != i:
+            members.append(i)
+        vals.setdefault(i, []).append((int(j), complex(float(re_), float(im_))))
+    assert members == mg.cfg3_members()[:len(members)]
+    for i in members:
+        k = rs[i]["n_open"]
+        n = rs[i]["rows"] * rs[i]["cols"]
+        assert sorted(j for j, _ in vals[i]) == list(range(1 << k))
+        p = sum(abs(a) ** 2 for _, a in vals[i])
+        assert 0.5 < p * 2.0 ** (n - k) < 2.0, (i, p * 2.0 ** (n - k))
