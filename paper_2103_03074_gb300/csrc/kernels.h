@@ -150,10 +150,15 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
-// x 2^-e, exactly as ldexpf(x, -e): a multiplication by the power of two
-// when 2^-e is a normal float (both round the same), ldexpf otherwise
+// x 2^-e as ldexpf(x, -e) gives it: a multiplication by the power of two
+// when 2^-e is a normal float (both round the same), else two such
+// multiplications (the same while the intermediate stays normal; e stays in
+// [-126, 126] for tensors whose largest value lies between 2^-112 and 2^140)
 __device__ __forceinline__ float scale_pow2(float x, int e) {
-    return (e >= -126 && e <= 126) ? x * __int_as_float((127 - e) << 23) : ldexpf(x, -e);
+    const int e1 = (e >= -126 && e <= 126) ? e : e / 2;
+    const int e2 = e - e1;
+    const float y = x * __int_as_float((127 - e1) << 23);
+    return e2 ? y * __int_as_float((127 - e2) << 23) : y;
 }
 
 // The pieces of one complex value for the split modes of BitPermArgs

@@ -377,21 +377,32 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
     const int n_hi = 1 << (o.ntb - nlo);
     if (L.quad) {
         const int np = mode_planes(o.mode);
+        constexpr int NPQ = M3 ? 6 : 4;
         for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
             const uint2 g = jtab[jh];
-            PiecesT<M3> pc[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
             const uint64_t d0 = base + g.y + L.d[0];  // a multiple of 4
             if (mode_word(o.mode)) {
+                PiecesT<M3> pc[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
                 uint4 *P = reinterpret_cast<uint4 *>(o.planes);
                 for (int q = 0; q < np; q++)
                     P[(d0 + q * o.plane_stride) >> 2] = make_uint4(pc[0].q[q], pc[1].q[q], pc[2].q[q], pc[3].q[q]);
             } else {
+                // 16-bit pieces: pack each plane's words as the element pairs
+                // are split (fewer live registers than four elements' pieces)
+                uint32_t w[NPQ][2];
+#pragma unroll
+                for (int h2 = 0; h2 < 2; h2++) {
+                    const PiecesT<M3> a = split_t<M3>(o.mode, st[(int)g.x + L.s[2 * h2]], e);
+                    const PiecesT<M3> b = split_t<M3>(o.mode, st[(int)g.x + L.s[2 * h2 + 1]], e);
+#pragma unroll
+                    for (int q = 0; q < NPQ; q++) w[q][h2] = a.q[q] | (b.q[q] << 16);
+                }
                 uint2 *P = reinterpret_cast<uint2 *>(o.planes);
-                for (int q = 0; q < np; q++)
-                    P[(d0 + q * o.plane_stride) >> 2] =
-                        make_uint2(pc[0].q[q] | (pc[1].q[q] << 16), pc[2].q[q] | (pc[3].q[q] << 16));
+#pragma unroll
+                for (int q = 0; q < NPQ; q++)
+                    if (q < np) P[(d0 + q * o.plane_stride) >> 2] = make_uint2(w[q][0], w[q][1]);
             }
         }
         return;
@@ -412,7 +423,7 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
 }
 
 template <int KIND, int CB, bool M3>
-__global__ void __maxnreg__(112)  // 576 threads x 112 registers fit the SM's 65536
+__global__ void __launch_bounds__(kThreads, 1)  // 18 warps: at most 96 registers (5 warps on one scheduler)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
     constexpr int NP = M3 ? 6 : (kind_split(KIND) ? 4 : 2);
@@ -630,17 +641,19 @@ __global__ void __maxnreg__(112)  // 576 threads x 112 registers fit the SM's 65
                 }
 #pragma unroll
                 for (int q = 0; q < (M3 ? 0 : kCW / 16); q++) {
-                    uint32_t r0[16], r1[16], r2[16], r3[16];
+                    // real parts, then imaginary parts: two loads in flight at
+                    // a time keep the epilogue within its register budget
+                    uint32_t r0[16], r1[16];
                     tmem_ld16(base + q * 16, r0);        // P left:  A_re B_re
-                    tmem_ld16(base + 64 + q * 16, r1);   // P right: A_re B_im
-                    tmem_ld16(base + 128 + q * 16, r2);  // Q left:  A_im B_re
-                    tmem_ld16(base + 192 + q * 16, r3);  // Q right: A_im B_im
+                    tmem_ld16(base + 192 + q * 16, r1);  // Q right: A_im B_im
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        acc_re[q * 16 + j] += __uint_as_float(r0[j]) - __uint_as_float(r3[j]);
-                        acc_im[q * 16 + j] += __uint_as_float(r1[j]) + __uint_as_float(r2[j]);
-                    }
+                    for (int j = 0; j < 16; j++) acc_re[q * 16 + j] += __uint_as_float(r0[j]) - __uint_as_float(r1[j]);
+                    tmem_ld16(base + 64 + q * 16, r0);   // P right: A_re B_im
+                    tmem_ld16(base + 128 + q * 16, r1);  // Q left:  A_im B_re
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; j++) acc_im[q * 16 + j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
                 }
                 fence_before();
                 __syncwarp();
@@ -650,18 +663,21 @@ __global__ void __maxnreg__(112)  // 576 threads x 112 registers fit the SM's 65
                 // undo the operands' power-of-two scales (exact): a product
                 // with 2^e_scale rounds as ldexpf does when 2^e_scale is a
                 // normal float
-                if (e_scale >= -126 && e_scale <= 127) {
-                    const float sc = __int_as_float((127 + e_scale) << 23);
+                // (outside the normal range of 2^e_scale, two such products;
+                // exact while the intermediate stays normal)
+                const int e1 = (e_scale >= -126 && e_scale <= 127) ? e_scale : e_scale / 2;
+                const int e2 = e_scale - e1;
+                const float sc1 = __int_as_float((127 + e1) << 23), sc2 = __int_as_float((127 + e2) << 23);
+#pragma unroll
+                for (int j = 0; j < kCW; j++) {
+                    acc_re[j] *= sc1;
+                    acc_im[j] *= sc1;
+                }
+                if (e2 != 0) {
 #pragma unroll
                     for (int j = 0; j < kCW; j++) {
-                        acc_re[j] *= sc;
-                        acc_im[j] *= sc;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kCW; j++) {
-                        acc_re[j] = ldexpf(acc_re[j], e_scale);
-                        acc_im[j] = ldexpf(acc_im[j], e_scale);
+                        acc_re[j] *= sc2;
+                        acc_im[j] *= sc2;
                     }
                 }
             }
