@@ -74,12 +74,15 @@ constexpr int kDefaultChunkBytes = 128;
 __host__ __device__ constexpr int default_flush_bytes(tn_form f) {
     return (f == TN_TF32X3 || f == TN_FP16X3) ? 256 : 512;
 }
-// warp 0: TMA producer; warp 1: MMA issuer; warps 2-17: accumulator
-// read-out and epilogue, four per TMEM lane group (a warp reads the lanes
-// 32 (w mod 4) .. + 31), each a quarter of the tile's 64 complex columns
-constexpr int kFlushWarp0 = 2, kFlushWarps = 16;
-constexpr int kThreads = 32 * (kFlushWarp0 + kFlushWarps);  // 576
-constexpr int kCW = TN / (kFlushWarps / 4);                  // complex columns per epilogue warp: 16
+// warp 0: TMA producer; warp 1: MMA issuer; warps 2 .. 2 + EW - 1: the EW
+// (8 or 16) accumulator read-out and epilogue warps, EW / 4 per TMEM lane
+// group (a warp reads the lanes 32 (w mod 4) .. + 31), each 64 / (EW / 4)
+// of the tile's complex columns.  Sixteen epilogue warps (18 in all, at most
+// 96 registers: five warps share one scheduler's 16,384 registers) serve
+// GEMMs whose tiles have one accumulator read-out (short K, the epilogue is
+// their time); eight (168 registers) the others.
+constexpr int kFlushWarp0 = 2;
+__host__ __device__ constexpr int ep_threads(int ew) { return 32 * (kFlushWarp0 + ew); }
 constexpr int kTmemCols = 512;  // 2 sets x {P, Q} x 128 columns
 
 // operand forms of the kernel template
@@ -370,7 +373,7 @@ __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane
 // planes: warp fw of the 8 epilogue warps takes the groups j_hi = fw, fw + 8,
 // ...; each lane two (or four) neighbouring elements of a group.
 // base = the destination offset of the half tile's element (0, 0)
-template <bool M3>
+template <bool M3, int EW>
 __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base, const float2 *st,
                                              const uint2 *jtab, const PlanarLane &L, int fw, int lane, int e) {
     const int nlo = planar_nlo(o);
@@ -378,7 +381,7 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
     if (L.quad) {
         const int np = mode_planes(o.mode);
         constexpr int NPQ = M3 ? 6 : 4;
-        for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
+        for (int jh = fw; jh < n_hi; jh += EW) {
             const uint2 g = jtab[jh];
             const uint64_t d0 = base + g.y + L.d[0];  // a multiple of 4
             if (mode_word(o.mode)) {
@@ -408,7 +411,7 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
         return;
     }
     const bool v1 = 2 * lane + 1 < (1 << nlo), v0 = 2 * lane < (1 << nlo);
-    for (int jh = fw; jh < n_hi; jh += kFlushWarps) {
+    for (int jh = fw; jh < n_hi; jh += EW) {
         const uint2 g = jtab[jh];
         const float2 a = st[(int)g.x + L.s[0]];
         const float2 b = st[(int)g.x + L.s[1]];
@@ -422,10 +425,12 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
     }
 }
 
-template <int KIND, int CB, bool M3>
-__global__ void __launch_bounds__(kThreads, 1)  // 18 warps: at most 96 registers (5 warps on one scheduler)
+template <int KIND, int CB, bool M3, int EW>
+__global__ void __launch_bounds__(ep_threads(EW), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const GemmTcParams p) {
+    constexpr int kFlushWarps = EW;
+    constexpr int kCW = TN / (EW / 4);  // complex columns per epilogue warp
     constexpr int NP = M3 ? 6 : (kind_split(KIND) ? 4 : 2);
     using R = Ring<CB, NP>;
     constexpr int kAPlane = R::kAPlane, kBPlane = R::kBPlane;
@@ -733,7 +738,7 @@ __global__ void __launch_bounds__(kThreads, 1)  // 18 warps: at most 96 register
                     // m bit 6 is the half (m0 is a multiple of 128); with
                     // M <= 64 the second half lies past M and is skipped
                     if (ok && tc.m0 + hp * (TM / 2) < p.M)
-                        planar_write<M3>(p.out, hp ? (pbase | (1ull << p.out.mpos[6])) : pbase, stage_out, jtab, pl,
+                        planar_write<M3, EW>(p.out, hp ? (pbase | (1ull << p.out.mpos[6])) : pbase, stage_out, jtab, pl,
                                          fw, lane, e_out);
                 }
                 for (int rr = fw; ok && p.out.mode == 0 && rr < TM / 2; rr += kFlushWarps) {
@@ -872,15 +877,23 @@ bool tc_prepare(TcGemm &g) {
     return true;
 }
 
-template <int KIND, int CB, bool M3 = false>
-cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
+template <int KIND, int CB, bool M3, int EW>
+cudaError_t launch_ew(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
     constexpr int NP = M3 ? 6 : (kind_split(KIND) ? 4 : 2);
-    cudaError_t e = set_max_dynamic_smem((const void *)tc_gemm_kernel<KIND, CB, M3>, Ring<CB, NP>::kSmem);
+    cudaError_t e = set_max_dynamic_smem((const void *)tc_gemm_kernel<KIND, CB, M3, EW>, Ring<CB, NP>::kSmem);
     if (e != cudaSuccess) return e;
     const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
     const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
-    tc_gemm_kernel<KIND, CB, M3><<<grid, kThreads, Ring<CB, NP>::kSmem, s>>>(mA, mB, p);
+    tc_gemm_kernel<KIND, CB, M3, EW><<<grid, ep_threads(EW), Ring<CB, NP>::kSmem, s>>>(mA, mB, p);
     return cudaGetLastError();
+}
+
+// sixteen epilogue warps when a tile has one accumulator read-out (short K:
+// the epilogue sets the GEMM's time), else eight
+template <int KIND, int CB, bool M3 = false>
+cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
+    const bool one_readout = p.part_len <= p.flush_chunks;
+    return one_readout ? launch_ew<KIND, CB, M3, 16>(g, p, grid, s) : launch_ew<KIND, CB, M3, 8>(g, p, grid, s);
 }
 
 cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
