@@ -138,8 +138,12 @@ typedef struct {
     /* what ranks the trials: 0 total complex MACs over all slices (default);
      * 1 the roofline time of the tree compiled for rank_form with
      * 2^rank_batch_log2 slices per block (-1: the largest block whose arena
-     * fits 160 GiB), as tn_estimate_tree_ms prices it.  Either way the
-     * learned ranking (cost_model, candidates) then picks among the best. */
+     * fits 160 GiB), as tn_estimate_tree_ms prices it; 2 that time with each
+     * tensor-core GEMM priced at no less than its output elements over the
+     * rate its epilogue writes them (measured on GB300: ~2.2e11 elements/s
+     * into split planes, ~4e11 as complex64), the bound of short-K GEMMs.
+     * Either way the learned ranking (cost_model, candidates) then picks
+     * among the best. */
     int32_t objective;
 } tn_search_opts;
 
@@ -417,9 +421,9 @@ int tn_find_order_head_tail(int n_tensors, const int32_t *ranks, const int32_t *
  * qubits (n_open, increasing), the tail's tensor ids in the all-open network
  * (out_tail, room for its tensor count; may be NULL), their count, the cut
  * (bonds between tail and head) and *out_log2_cost (log2 total MACs of the
- * winner's search, or log2 of its plan's roofline ms when opts->objective is
- * 1, the measure the candidates are compared by; -1 without opts; may be
- * NULL).  TN_ERR_ARG unless
+ * winner's search, or log2 of its plan's roofline (objective 1) or expected
+ * (objective 2) ms: the measure the candidates are compared by; -1 without
+ * opts; may be NULL).  TN_ERR_ARG unless
  * 1 <= n_open < n_qubits, or when no connected tail holds exactly n_open
  * ends.
  */

@@ -146,7 +146,7 @@ def _dev_ptr(t):
 
 
 SEARCH_METHODS = {"greedy": 0, "bipartition": 1, "mixed": 2}
-SEARCH_OBJECTIVES = {"macs": 0, "roofline": 1}
+SEARCH_OBJECTIVES = {"macs": 0, "roofline": 1, "expected": 2}
 
 
 def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads=0, candidates=0,
@@ -154,8 +154,10 @@ def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads
     """Order-search options (tn_search_opts).  method: "greedy" (randomised
     greedy trials), "bipartition" (hierarchical min-cut bipartition, greedy
     inside parts of a few dozen tensors) or "mixed" (alternating).
-    objective: "macs" (total complex MACs) or "roofline" (the tree's plan for
-    rank_form priced at its roofline time, as estimate_tree_ms does)."""
+    objective: "macs" (total complex MACs), "roofline" (the tree's plan for
+    rank_form priced at its roofline time, as estimate_tree_ms does) or
+    "expected" (that time with each tensor-core GEMM priced at no less than
+    its epilogue's measured output rate)."""
     f = FORMS[rank_form] if isinstance(rank_form, str) else int(rank_form)
     m = SEARCH_METHODS[method] if isinstance(method, str) else int(method)
     ob = SEARCH_OBJECTIVES[objective] if isinstance(objective, str) else int(objective)

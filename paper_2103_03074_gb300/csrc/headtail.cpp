@@ -521,11 +521,11 @@ extern "C" int tn_choose_open_qubits(const tn_circuit *circuit, int n_open, cons
             // the search's own measure: total MACs, or with the roofline
             // objective the compiled plan's roofline time
             double cost = r.log2_total;
-            if (opts->objective == 1) {
+            if (opts->objective >= 1) {
                 const tn_form f = (opts->rank_form >= TN_FP32 && opts->rank_form <= TN_FP16X3) ? (tn_form)opts->rank_form
                                                                                                : TN_FP32;
                 const double ms = tree_roofline_ms(labs, sub.open, r.tree, r.sliced, f, opts->rank_batch_log2,
-                                                   kNominalArenaBytes);
+                                                   kNominalArenaBytes, opts->objective == 2);
                 cost = ms > 0 ? std::log2(ms) : INFINITY;
             }
             if (!priced || cost < best_cost) {

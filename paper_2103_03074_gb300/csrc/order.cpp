@@ -824,15 +824,16 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     if (const char *bad = make_problem(labels, open, p)) return fail(TN_ERR_ARG, std::string("order search: ") + bad);
     if (p.n == 0) return fail(TN_ERR_ARG, "empty network");
     if (opts.method < 0 || opts.method > 2) return fail(TN_ERR_ARG, "unknown order-search method");
-    if (opts.objective < 0 || opts.objective > 1) return fail(TN_ERR_ARG, "unknown order-search objective");
+    if (opts.objective < 0 || opts.objective > 2) return fail(TN_ERR_ARG, "unknown order-search objective");
     const tn_form rform =
         (opts.rank_form >= TN_FP32 && opts.rank_form <= TN_FP16X3) ? (tn_form)opts.rank_form : TN_FP32;
     // the trials' score: log2 of total MACs, or of the compiled plan's roofline time
     const auto score = [&](const Tree &tree, const SliceEval &ev) {
-        if (opts.objective != 1) return ev.log2_total;
+        if (opts.objective == 0) return ev.log2_total;
         std::vector<int32_t> sl;
         for (int id : ev.sliced) sl.push_back(p.id2label[id]);
-        const double ms = tree_roofline_ms(labels, open, tree, sl, rform, opts.rank_batch_log2, kNominalArenaBytes);
+        const double ms = tree_roofline_ms(labels, open, tree, sl, rform, opts.rank_batch_log2, kNominalArenaBytes,
+                                           opts.objective == 2);
         return ms > 0 ? std::log2(ms) : (double)INFINITY;
     };
     if (p.n == 1) {
@@ -895,7 +896,7 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
             // the roofline objective also keeps the best trials by MACs:
             // reconfiguration reshapes a tree, so its time before says
             // little about its time after
-            if (opts.objective == 1)
+            if (opts.objective >= 1)
                 insert(keep_m[tid], Cand{over ? ev.log2_width : 0.0, ev.log2_total, ev.log2_width, t, tree, ev, sc});
             insert(mine, Cand{over ? ev.log2_width : 0.0, sc, ev.log2_width, t, std::move(tree), ev, sc});
         }
@@ -910,7 +911,7 @@ int search_order_top(const std::vector<std::vector<int32_t>> &labels, const std:
     std::sort(all.begin(), all.end(), better);
     if (all.empty()) return fail(TN_ERR_ARG, "order search produced no tree");
     if ((int)all.size() > kk) all.resize(kk);
-    if (opts.objective == 1) {
+    if (opts.objective >= 1) {
         // the MAC-ranked candidates first, in the order (and so with the
         // reconfiguration seeds) a MAC-ranked search gives them, then the
         // time-ranked ones it lacks: the time-ranked pick can only improve

@@ -950,6 +950,23 @@ double roofline_ms(const Op &op, tn_form form) {
     return t + floor_ms;
 }
 
+// Expected time of one step in ms, for the order search's time objective:
+// the roofline time, but a tensor-core GEMM takes at least its output
+// elements over the rate its epilogue writes them.  Measured on GB300 over
+// the short-K GEMMs of the 53-qubit 14-cycle step: about 2.2e11 elements/s
+// when the epilogue writes the next step's split planes, about 4e11 when it
+// writes complex64 (no split).  Short-K GEMMs with large outputs are bound
+// by this, not by the tensor cores or HBM.
+double expected_ms(const Op &op, tn_form form) {
+    double t = roofline_ms(op, form);
+    if (op.kind == OP_GEMM && op.gemm_variant == 1) {
+        const double out = (double)op.gemm.H * (double)op.gemm.M * (double)op.gemm.N;
+        const double rate = op.tc.out.mode != 0 ? 2.2e11 : 4.0e11;
+        t = std::max(t, out / rate * 1e3 + 2.0e-3);
+    }
+    return t;
+}
+
 // 16 step features (see tn_plan_op_features in tn.h)
 void op_features(const Op &op, tn_form form, float *f) {
     for (int i = 0; i < kCostFeatures; i++) f[i] = 0.f;
@@ -1095,7 +1112,7 @@ namespace tn {
 // n_sliced), else the largest whose arena and leaves fit `budget` bytes, as
 // tn_plan_create chooses it (0 when none fits).  Host only.
 int plan_roofline(tn_plan &P, int batch_log2, double budget, int64_t leaf_bytes, double &ms, int &nb_out,
-                  int64_t &arena_out, double *pro_out = nullptr, double *body_out = nullptr) {
+                  int64_t &arena_out, double *pro_out = nullptr, double *body_out = nullptr, bool expected = false) {
     int nb = batch_log2 >= 0 ? std::min(batch_log2, P.n_sliced) : P.n_sliced;
     int64_t arena = compile(P, nb);
     if (arena < 0) return TN_ERR_ARG;
@@ -1113,8 +1130,8 @@ int plan_roofline(tn_plan &P, int batch_log2, double budget, int64_t leaf_bytes,
         if (arena < 0) return TN_ERR_ARG;
     }
     double pro = 0, body = 0;
-    for (const auto &op : P.prologue) pro += roofline_ms(op, P.form);
-    for (const auto &op : P.batch) body += roofline_ms(op, P.form);
+    for (const auto &op : P.prologue) pro += expected ? expected_ms(op, P.form) : roofline_ms(op, P.form);
+    for (const auto &op : P.batch) body += expected ? expected_ms(op, P.form) : roofline_ms(op, P.form);
     ms = pro + std::exp2((double)(P.n_sliced - nb)) * body;
     nb_out = nb;
     arena_out = arena;
@@ -1125,7 +1142,7 @@ int plan_roofline(tn_plan &P, int batch_log2, double budget, int64_t leaf_bytes,
 
 double tree_roofline_ms(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
                         const Tree &tree, const std::vector<int32_t> &sliced, tn_form form, int batch_log2,
-                        double budget) {
+                        double budget, bool expected) {
     tn_plan P;
     P.form = form;
     P.n_tensors = (int)labels.size();
@@ -1144,7 +1161,7 @@ double tree_roofline_ms(const std::vector<std::vector<int32_t>> &labels, const s
     double ms = -1;
     int nb = 0;
     int64_t arena = 0;
-    if (plan_roofline(P, batch_log2, budget, off * 8, ms, nb, arena)) return -1.0;
+    if (plan_roofline(P, batch_log2, budget, off * 8, ms, nb, arena, nullptr, nullptr, expected)) return -1.0;
     return ms;
 }
 
@@ -1847,11 +1864,15 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
                 // neighbouring elements
                 int run = 0;
                 while (run < op.tc.out.ntb && op.tc.out.tpos[run] == run) run++;
+                // the tile's six column bits are the destination's six lowest
+                bool cols_low = op.tc.out.ntb >= 6;
+                for (int k = 0; k < 6 && cols_low; k++) cols_low = op.tc.out.tb[k] == k && op.tc.out.tpos[k] == k;
                 char pl[64] = "";
                 if (op.tc.out.mode)
-                    std::snprintf(pl, sizeof pl, " run_bits=%d%s", run,
+                    std::snprintf(pl, sizeof pl, " run_bits=%d%s%s", run,
                                   (op.tc.out.ntb >= 7 && op.tc.out.tpos[0] == 0 && op.tc.out.tpos[1] == 1) ? " quad"
-                                                                                                            : "");
+                                                                                                            : "",
+                                  cols_low ? " cols_low" : "");
                 std::snprintf(line, sizeof line,
                               "%s step %d gemm H=%lld M=%lld N=%lld K=%lld tensor-core%s ksplit=%d out=%s%s", phase,
                               op.step, (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N,

@@ -68,10 +68,12 @@ tn_search_opts default_search_opts();
 
 // plan.cpp: roofline time (ms, all slices) of a tree compiled for `form`
 // with batch_log2 batch bits (< 0: the largest batch whose arena fits
-// `budget` bytes); negative when the tree does not compile.  Host only.
+// `budget` bytes); negative when the tree does not compile.  With expected,
+// a tensor-core GEMM is priced at no less than its epilogue's measured output
+// rate (the search's expected-time objective).  Host only.
 double tree_roofline_ms(const std::vector<std::vector<int32_t>> &labels, const std::vector<int32_t> &open,
                         const Tree &tree, const std::vector<int32_t> &sliced, tn_form form, int batch_log2,
-                        double budget);
+                        double budget, bool expected = false);
 // the arena budget the search and tn_estimate_tree_ms assume when none is
 // given: 60% of a GB300's ~275 GiB of free HBM, as tn_plan_create's default
 // budget gives on an idle device

@@ -711,3 +711,20 @@ def test_choose_open_qubits_takes_the_cheapest_candidate_below_1ms(tn):
     assert cost == pytest.approx(costs[i], abs=1e-9)
     assert cost <= min(costs) + 1e-9
     assert oq in [c[0] for c in cands[:8]]
+
+
+def test_expected_time_objective(tn):
+    """objective 'expected' (2): the roofline time with each tensor-core GEMM
+    priced at no less than its epilogue's output rate.  It searches like the
+    other objectives (a valid, sliced tree, deterministic), the open-qubit
+    chooser takes it too, and an unknown objective is refused."""
+    cfg = make_config(2)
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    o2 = tn.search_opts(trials=64, n_sliced=4, objective="expected", rank_form="fp16x3")
+    tree, sl, st = tn.find_order(L, O, o2)
+    assert len(tree) == len(L) - 1 and len(sl) == 4
+    assert tn.find_order(L, O, o2)[0] == tree
+    oq, _, _, cost = tn.choose_open_qubits(cfg["circuit"], 8, o2)
+    assert len(oq) == 8 and np.isfinite(cost)
+    with pytest.raises(tn.TNError):
+        tn.find_order(L, O, tn.search_opts(trials=8, n_sliced=4, objective=3))
