@@ -56,10 +56,11 @@ METRIC = "slices/s & complex TFLOP/s per GB300 at <=1e-5 amp err, split-TC vs pl
 DEFAULT_WORKLOAD = "syc53_m14"
 
 # DRAM traffic per tensor-core GEMM launch of the default step, by form, from
-# the ncu capture summarised under profiles/ (dram__bytes_read.sum +
-# dram__bytes_write.sum averaged over the step's launches); a form is absent
-# until such a capture exists for the current kernel
-GEMM_TRAFFIC_PER_LAUNCH = {}
+# the one-pass ncu capture summarised in
+# profiles/dram_traffic_syc53_m14_fp16x3.md (dram__bytes_read.sum +
+# dram__bytes_write.sum averaged over the step's 9 GEMM launches, 10 steps);
+# a form is absent until such a capture exists for the current kernel
+GEMM_TRAFFIC_PER_LAUNCH = {"fp16x3": 17.10e9}
 
 
 def peaks():
@@ -882,7 +883,8 @@ def run_gemm(args):
         tensors.append(D.reshape((2,) * len(dl)))
         out_l = (ml[:m - low] + nl[:n - low] + pl) if low else (ml + pl)
         tree = [(0, 1), (3, 2)]
-    plan = make_plan(tn, labels, tensors, out_l, hl, tree, name, use_graph=1, tc_chunk_bytes=args.tc_chunk)
+    plan = make_plan(tn, labels, tensors, out_l, hl, tree, name, use_graph=1, tc_chunk_bytes=args.tc_chunk,
+                     tc_flush_bytes=args.tc_flush)
     amp = torch.zeros(2 << len(out_l), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -905,6 +907,75 @@ def run_gemm(args):
     return 0
 
 
+def run_rank53(args):
+    """Tree ranking on the 53-qubit 14-cycle workload: candidate trees from
+    bipartition searches with different seeds, each timed (FP16X3, CUDA
+    graph, median of 3 steps) and profiled step by step; the learned cost
+    model ranks each half of the candidates after training on the other
+    half's per-step timings (cross-fitting), against the roofline-time
+    (tn_estimate_tree_ms) and MAC rankings.  One JSON line."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_03074_gb300 as tn
+    torch.cuda.set_device(0)
+    cfg = workload("syc53_m14")
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    cands = []
+    for seed in range(1, 1 + args.rank_seeds):
+        tree, sl, st = tn.find_order(L, O, tn.search_opts(trials=256, log2_cap=30, method="bipartition",
+                                                          objective="roofline", rank_form="fp16x3", seed=seed))
+        if all(tree != c["tree"] for c in cands):
+            cands.append({"seed": seed, "tree": tree, "sliced": sl, "log2_macs": st["log2_total"],
+                          "roofline_ms": tn.estimate_tree_ms(L, O, sl, tree, form="fp16x3").ms})
+    stream = torch.cuda.Stream()
+    amp = torch.zeros(2 << len(O), dtype=torch.float64, device="cuda")
+    for c in cands:
+        n = 1 << len(c["sliced"])
+        plan = tn.Plan(L, T, O, c["sliced"], c["tree"], form="fp16x3", opts=tn.plan_opts(use_graph=1))
+        ms = time_steps(torch, plan, [(0, n)], amp, 3, 1, stream, l2_flush_buffer(torch), len(O),
+                        cfg["circuit"].n_qubits, torch.zeros(3, dtype=torch.float64, device="cuda"))
+        c["measured_ms"] = float(np.median(ms))
+        plan.close()
+        pplan = tn.Plan(L, T, O, c["sliced"], c["tree"], form="fp16x3", opts=tn.plan_opts(profile=1))
+        with torch.cuda.stream(stream):
+            pplan.contract(0, n, amp, stream)
+            pplan.profile(reset=True)
+            pplan.contract(0, n, amp, stream)
+        rows = [r for r in pplan.profile() if r["kind"] not in ("extract", "accumulate")]
+        c["X"] = pplan.op_features()
+        c["y"] = np.log2(np.maximum([r["ms"] / max(r["launches"], 1) for r in rows], 1e-4)).astype(np.float32)
+        pplan.close()
+        torch.cuda.empty_cache()
+    # cross-fitting: the model that ranks a candidate never saw its steps
+    halves = [cands[0::2], cands[1::2]]
+    for i in (0, 1):
+        train, test = halves[1 - i], halves[i]
+        if not train or not test:
+            continue
+        X = np.concatenate([c["X"] for c in train])
+        y = np.concatenate([c["y"] for c in train])
+        cm = tn.CostModel(seed=11 + i)
+        cm.train(torch.from_numpy(X).cuda(), torch.from_numpy((y - 16.0 * X[:, 14]).astype(np.float32)).cuda(),
+                 epochs=3000, lr=3e-3)
+        for c in test:
+            d = torch.zeros(len(c["X"]), dtype=torch.float32, device="cuda")
+            cm.predict(torch.from_numpy(c["X"]).cuda(), d)
+            torch.cuda.synchronize()
+            c["model_ms"] = float(np.sum(2.0 ** (16.0 * c["X"][:, 14] + d.cpu().numpy())))
+        cm.close()
+    pick = lambda key: min(cands, key=lambda c: c.get(key, float("inf")))
+    out = {"workload": WORKLOADS["syc53_m14"]["desc"].split(",")[0] + ", FP16X3, the whole tensor per step",
+           "candidates": [{k: c[k] for k in ("seed", "log2_macs", "roofline_ms", "measured_ms", "model_ms") if k in c}
+                          for c in cands],
+           "best_ms": min(c["measured_ms"] for c in cands),
+           "mac_pick_ms": pick("log2_macs")["measured_ms"], "roofline_pick_ms": pick("roofline_ms")["measured_ms"],
+           "model_pick_ms": pick("model_ms")["measured_ms"]}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -912,7 +983,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--form", default="all", choices=FORM_CHOICES + ["all"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256", "gemm"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256", "gemm", "rank53"])
+    ap.add_argument("--rank-seeds", type=int, default=8, help="--workload rank53: search seeds (candidate trees)")
     ap.add_argument("--gemm", default="0,15,11,9", help="--workload gemm: log2 H,M,K,N")
     ap.add_argument("--gemm-next", type=int, default=0,
                     help="--workload gemm: follow the GEMM by a second one of log2 N = this, so that the first "
@@ -920,6 +992,8 @@ def main():
     ap.add_argument("--gemm-next-low", type=int, default=0,
                     help="--workload gemm with --gemm-next: the second GEMM contracts the lowest L m and n labels")
     ap.add_argument("--tc-chunk", type=int, default=0, help="tensor-core K chunk bytes (plan option tc_chunk_bytes)")
+    ap.add_argument("--tc-flush", type=int, default=0,
+                    help="K bytes between accumulator read-outs (plan option tc_flush_bytes)")
     ap.add_argument("--search-method", default=None, choices=["greedy", "bipartition", "mixed"],
                     help="search a fresh tree (randomised greedy, hierarchical bipartition, or both) instead of "
                          "the workload's stored tree")
@@ -952,6 +1026,8 @@ def main():
         return run_batch(args)
     if args.workload == "gemm":
         return run_gemm(args)
+    if args.workload == "rank53":
+        return run_rank53(args)
     return run_native(args)
 
 
