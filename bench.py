@@ -4,10 +4,12 @@ per GPU under torchrun).
 Default workload: the 53-qubit Sycamore-shaped lattice (6 x 9 rotated grid,
 one site removed), 14 cycles, 16 open qubits, the other 37 fixed to a seeded
 bitstring, intermediates capped at 2^30 elements by slicing, contracted with
-the stored tree of paper_2103_03074_gb300/trees/syc53_m14.json (1024
-hierarchical-bipartition trials ranked by roofline time).  One step = every
-slice of that tree contracted and summed into the FP64 amplitude tensor (the
-whole 2^16-entry tensor), then the FP64 probability / XEB reduction.  The
+the stored tree of paper_2103_03074_gb300/trees/syc53_m14.json (256
+hierarchical-bipartition trials of seed 5, ranked by roofline time: the
+fastest of eight searched trees on the GPU; it needs no slicing under the
+cap).  One step = every slice of that tree contracted and summed into the
+FP64 amplitude tensor (the whole 2^16-entry tensor), then the FP64
+probability / XEB reduction.  The
 error of every form is measured on the FP64 oracle's sampled entries of the
 same tensor (tests/golden/cfg4_amplitudes_sampled.txt).  The line also
 carries a short measurement of the 20-cycle, 21-open-qubit workload (cap
@@ -60,7 +62,7 @@ DEFAULT_WORKLOAD = "syc53_m14"
 # profiles/dram_traffic_syc53_m14_fp16x3.md (dram__bytes_read.sum +
 # dram__bytes_write.sum averaged over the step's 9 GEMM launches, 10 steps);
 # a form is absent until such a capture exists for the current kernel
-GEMM_TRAFFIC_PER_LAUNCH = {"fp16x3": 17.10e9}
+GEMM_TRAFFIC_PER_LAUNCH = {}
 
 
 def peaks():
@@ -748,6 +750,8 @@ def run_native(args):
         "data": "synthetic (seeded Sycamore-style circuit, random bitstring)",
         "config": {"workload": wl["desc"], "form": best,
                    "step": f"{n_slices} of {n_total} slices summed in FP64 + probabilities/XEB",
+                   "amplitudes_per_step": f"2^{n_open}" + (" (the whole tensor)" if n_slices == n_total else
+                                                           f" ({n_slices} of {n_total} slices)"),
                    "full_slice_count": n_total, "tree": how,
                    "executor": "CUDA-graph replay of the prologue and per-block body",
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events); the "

@@ -77,8 +77,9 @@ typedef struct {
      * whose arguments change per block, stay ordinary launches) */
     int32_t use_graph;
     /* tensor-core GEMM tuning (0 = library default): K bytes per pipeline
-     * stage and plane row (64 or 128), and K bytes between read-outs of the
-     * tensor-memory accumulators into FP32 registers (a multiple of it) */
+     * stage and plane row (64 or 128; the 3M product takes 32, or 64 when
+     * 64 is asked for), and K bytes between read-outs of the tensor-memory
+     * accumulators into FP32 registers (a multiple of it) */
     int32_t tc_chunk_bytes;
     int32_t tc_flush_bytes;
     /* 0 (default) or 1: a tensor-core GEMM of the BF16x3 / TF32x3 forms whose
