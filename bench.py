@@ -92,11 +92,16 @@ TC_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5, "fp16x3": 1.0, "fp16s": 1.0,
 FORM_CHOICES = ["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "bf16x3_3m", "tf32x3_3m", "fp16x3_3m"]
 
 
+# plan options every bench plan takes (set from the command line)
+PLAN_DEFAULTS = {}
+
+
 def make_plan(tn, L, T, O, sliced, tree, name, **opts):
     """A plan for a bench form name: the library form, with Gauss's 3M
     product on the tensor cores for the *_3m names (tc_products 3)."""
     form, _, m3 = name.partition("_")
-    return tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(tc_products=3 if m3 else 0, **opts))
+    o = dict(PLAN_DEFAULTS, **opts)
+    return tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(tc_products=3 if m3 else 0, **o))
 
 
 def roofline_ms(row, form, pk):
@@ -105,7 +110,7 @@ def roofline_ms(row, form, pk):
     that runs it, whichever is larger."""
     kind = row["kind"]
     t_mem = row["bytes"] / (pk["hbm_gbs"] * 1e9)
-    if kind == "small" or (kind == "gemm" and form == "fp32"):
+    if kind in ("small", "tasks") or (kind == "gemm" and form == "fp32"):
         t_math = 8.0 * row["macs"] / (fp32_alu_peak_tflops(pk["sm_max_mhz"]) * 1e12)
     elif kind == "gemm":
         t_math = TC_FLOPS_PER_MAC[form] * row["macs"] / (pk["bf16_tflops"] * TC_PEAK_RATIO[form] * 1e12)
@@ -813,7 +818,7 @@ def run_batch(args):
     for form in forms:
         plans, amps = [], []
         for L, T, O, tree, sliced, st in nets:
-            plans.append(tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(batch_log2=3)))
+            plans.append(tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(**dict(PLAN_DEFAULTS, batch_log2=3))))
             amps.append(torch.zeros(2 << len(O), dtype=torch.float64, device="cuda"))
         batch = tn.Batch(plans, amps, n_streams=8)
         with torch.cuda.stream(stream):
@@ -903,11 +908,23 @@ def run_gemm(args):
         stream.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     macs = 2.0 ** (h + m + k + n)
+    desc = plan.describe()
+    plan.close()
+    # per-op device times (step-timing recorder, CUDA events around each op)
+    pplan = make_plan(tn, labels, tensors, out_l, hl, tree, name, profile=1, tc_chunk_bytes=args.tc_chunk,
+                      tc_flush_bytes=args.tc_flush)
+    with torch.cuda.stream(stream):
+        pplan.contract(0, 1 << h, amp, stream)
+        pplan.profile(reset=True)
+        for _ in range(args.steps):
+            pplan.contract(0, 1 << h, amp, stream)
+    ops = [{"kind": r["kind"], "shape": r["shape"], "ms": r["ms"] / max(r["launches"], 1)}
+           for r in pplan.profile() if r["launches"]]
+    pplan.close()
     print(json.dumps({"gemm": {"log2_hmkn": [h, m, k, n], "form": name}, "ms_per_contraction": ms,
                       "complex_tflops": 8 * macs / (ms / 1e3) / 1e12,
                       "tensor_tflops": TC_FLOPS_PER_MAC.get(name, 8.0) * macs / (ms / 1e3) / 1e12,
-                      "plan": plan.describe()}))
-    plan.close()
+                      "ops": ops, "plan": desc}))
     return 0
 
 
@@ -1010,6 +1027,8 @@ def main():
                          "workload's fixed set; the stored oracle amplitudes then do not apply (no error reported)")
     ap.add_argument("--branch-merge", action="store_true",
                     help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
+    ap.add_argument("--small-tasks", type=int, default=0,
+                    help="plan option small_tasks: 0 tiny small steps as tasks of one launch, -1 one launch each")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cfg5", action="store_true", help="skip the 20-cycle sample of the default line")
     ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
@@ -1024,6 +1043,8 @@ def main():
         args.warmup = 3
     if args.choose_open and args.search_method is None:
         args.search_method = "bipartition"
+    if args.small_tasks:
+        PLAN_DEFAULTS["small_tasks"] = args.small_tasks
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch256":

@@ -109,8 +109,12 @@ typedef struct {
      * fewer tensor-core flops; each operand then has six planes, the third
      * value s = re + im split like re and im) */
     int32_t tc_products;
-    /* reserved, set to 0 */
-    int32_t reserved[1];
+    /* tiny small steps (T and C of at most 2^small_tasks elements each, at
+     * most 2^7 K values; 0 = default 17): the ones whose inputs are leaves or
+     * each other's outputs run as the tasks of one persistent launch, which
+     * orders them by device-side completion counters (bounded waits) instead
+     * of one kernel launch each; -1: off */
+    int32_t small_tasks;
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

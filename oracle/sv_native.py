@@ -3,7 +3,9 @@ infrastructure only.  ``build()`` compiles it with gcc + OpenMP in place."""
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -15,9 +17,22 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-                               _SRC, "-o", _LIB, "-lm"])
+    """Compile liboracle_sv.so unless a digest of the source, the command
+    and the machine matches the one stored beside it (a library built from
+    another source or on another machine is never reused)."""
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", _SRC, "-o", _LIB, "-lm"]
+    h = hashlib.sha256()
+    h.update(platform.machine().encode())
+    h.update("\0".join(cmd).encode())
+    with open(_SRC, "rb") as f:
+        h.update(f.read())
+    digest = h.hexdigest()
+    stamp = _LIB + ".digest"
+    fresh = os.path.exists(_LIB) and os.path.exists(stamp) and open(stamp).read().strip() == digest
+    if force or not fresh:
+        subprocess.check_call(cmd)
+        with open(stamp, "w") as f:
+            f.write(digest + "\n")
     return _LIB
 
 

@@ -133,6 +133,145 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     }
 }
 
+// ------------------------------------ small steps as tasks of one launch
+// The small steps near the leaves of a contraction tree touch a few thousand
+// elements each: as separate launches each costs several microseconds of
+// launch and drain for well under a microsecond of work.  Here they are the
+// tasks of one persistent launch.  Blocks claim units (up to kTaskUnitItems
+// items of one task) in task order from an atomic counter; a unit first
+// waits until the tasks it reads from have finished all their units, then
+// stages its task's S in shared memory and computes its items as
+// small_kernel does.  Tasks are listed producers first and a block claims
+// its next unit only after finishing the current one, so every unit that a
+// waiting block depends on is held by a block that is running: the waits
+// end.  They are bounded all the same (task_error, then the unit is skipped).
+__device__ int task_error = 0;
+constexpr uint32_t kTaskSpinLimit = 1u << 21;
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t insert_zeros8(uint64_t x, const int8_t *pos, int n) {
+    for (int i = 0; i < n; i++) {
+        const int p = pos[i];
+        x = ((x >> p) << (p + 1)) | (x & ((1ull << p) - 1));
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint64_t scatter_bits8(uint64_t v, const int8_t *pos, int n) {
+    uint64_t r = 0;
+    for (int j = 0; j < n; j++) r |= ((v >> j) & 1ull) << pos[j];
+    return r;
+}
+
+// items [w0, w1) of task t; S staged at S_sm[h][k][n]; inputs are read
+// through L2 (ld.global.cg): a producer of this launch wrote them from
+// another SM, and this SM's L1 may hold older lines of the same arena bytes
+template <int NC>
+__device__ __forceinline__ void task_items(const SmallTask &t, const float2 *S_sm, const uint64_t *offT,
+                                           const uint64_t *offC, int64_t w0, int64_t w1) {
+    const int KS = 1 << t.nK, NS = 1 << t.nN;
+    const int nc = NS < NC ? NS : NC;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        const int64_t r = w & (t.rows - 1);
+        const int n0 = (int)(w >> t.row_bits) * NC;
+        const uint64_t tb = insert_zeros8((uint64_t)r, t.tins, t.n_tins);
+        const uint64_t cb = insert_zeros8((uint64_t)r, t.cins, t.n_cins);
+        uint32_t h = 0;
+        for (int j = 0; j < t.nH; j++) h |= (uint32_t)((r >> t.hbitR[j]) & 1) << j;
+        const float2 *Sh = S_sm + (size_t)h * KS * NS + n0;
+        float2 acc[NC];
+#pragma unroll
+        for (int j = 0; j < NC; j++) acc[j] = make_float2(0.f, 0.f);
+        for (int k = 0; k < KS; k++) {
+            const float2 tv = __ldcg(t.T + tb + offT[k]);
+            const float2 *Sk = Sh + k * NS;
+#pragma unroll
+            for (int j = 0; j < NC; j++)
+                if (j < nc) cfma(acc[j], tv, Sk[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NC; j++)
+            if (j < nc) t.C[cb + offC[n0 + j]] = acc[j];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    small_task_kernel(const SmallTask *__restrict__ tasks, const int *__restrict__ unit_task, int total_units,
+                      int *ctr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) SmallTask st;
+    __shared__ int s_unit, s_ok;
+    static_assert(sizeof(SmallTask) % 4 == 0, "task copied as words");
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(&ctr[0], 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= total_units) break;
+        const int ti = unit_task[u];
+        {
+            const int *src = reinterpret_cast<const int *>(tasks + ti);
+            int *dst = reinterpret_cast<int *>(&st);
+            for (int q = threadIdx.x; q < (int)(sizeof(SmallTask) / 4); q += blockDim.x) dst[q] = src[q];
+        }
+        if (threadIdx.x == 0) {
+            // wait (bounded) for the producing tasks; acquire pairs with
+            // their release below
+            int ok = 1;
+            const SmallTask &mine = tasks[ti];
+            for (int d = 0; d < mine.n_deps && ok; d++) {
+                const int dj = mine.dep[d];
+                const int need = tasks[dj].n_units;
+                for (uint32_t it = 0; ld_acquire_gpu(&ctr[1 + dj]) < need; it++) {
+                    if (it >= kTaskSpinLimit ||
+                        ((it & 1023u) == 1023u && *reinterpret_cast<volatile int *>(&task_error) != 0)) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            if (!ok) atomicExch(&task_error, 1);
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) {
+            const int KS = 1 << st.nK, NS = 1 << st.nN, HS = 1 << st.nH;
+            const int SS = HS * KS * NS;
+            float2 *S_sm = reinterpret_cast<float2 *>(smem);
+            uint64_t *offT = reinterpret_cast<uint64_t *>(S_sm + SS);
+            uint64_t *offC = offT + KS;
+            for (int idx = threadIdx.x; idx < SS; idx += blockDim.x) {
+                const uint32_t n = idx & (NS - 1), k = (idx >> st.nN) & (KS - 1), h = idx >> (st.nN + st.nK);
+                const uint64_t addr = scatter_bits8(h, st.hposS, st.nH) | scatter_bits8(k, st.kposS, st.nK) |
+                                      scatter_bits8(n, st.nposS, st.nN);
+                S_sm[idx] = __ldcg(st.S + addr);
+            }
+            for (int k = threadIdx.x; k < KS; k += blockDim.x) offT[k] = scatter_bits8(k, st.kposT, st.nK);
+            for (int n = threadIdx.x; n < NS; n += blockDim.x) offC[n] = scatter_bits8(n, st.nposC, st.nN);
+            __syncthreads();
+            const int nc_bits = st.nc == 32 ? 5 : (st.nc == 16 ? 4 : 3);
+            const int chunk_bits = st.nN > nc_bits ? st.nN - nc_bits : 0;
+            const int64_t items = st.rows << chunk_bits;
+            const int64_t w0 = (int64_t)(u - st.first_unit) * kTaskUnitItems;
+            const int64_t w1 = w0 + kTaskUnitItems < items ? w0 + kTaskUnitItems : items;
+            if (st.nc == 8) task_items<8>(st, S_sm, offT, offC, w0, w1);
+            else if (st.nc == 16) task_items<16>(st, S_sm, offT, offC, w0, w1);
+            else task_items<32>(st, S_sm, offT, offC, w0, w1);
+        }
+        // every thread's stores of this unit, then one release per unit
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&ctr[1 + ti], 1);
+        }
+    }
+}
+
 // ------------------------------------------------- small step, K per warp
 // For steps with a long K (>= 32) and too few (row, output chunk) items to
 // fill the GPU with one thread per item: one warp per item, lanes taking
@@ -1038,6 +1177,60 @@ cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
     if (nc == 8) return launch_small_nc<8>(a, grid, smem, s);
     if (nc == 16) return launch_small_nc<16>(a, grid, smem, s);
     return launch_small_nc<32>(a, grid, smem, s);
+}
+
+SmallTask make_small_task(const SmallArgs &a) {
+    SmallTask t;
+    std::memset(&t, 0, sizeof t);
+    t.T = a.T;
+    t.S = a.S;
+    t.C = a.C;
+    t.rows = a.rows;
+    t.row_bits = a.rows > 0 ? __builtin_ctzll((unsigned long long)a.rows) : 0;
+    t.nK = a.nK;
+    t.nN = a.nN;
+    t.nH = a.nH;
+    const int NS = 1 << a.nN;
+    t.nc = NS <= 8 ? 8 : (NS <= 16 ? 16 : 32);
+    t.n_tins = a.n_tins;
+    t.n_cins = a.n_cins;
+    for (int j = 0; j < kSmallMaxBits; j++) {
+        t.tins[j] = (int8_t)a.tins[j];
+        t.cins[j] = (int8_t)a.cins[j];
+        t.kposT[j] = (int8_t)a.kposT[j];
+        t.nposC[j] = (int8_t)a.nposC[j];
+        t.kposS[j] = (int8_t)a.kposS[j];
+        t.nposS[j] = (int8_t)a.nposS[j];
+    }
+    for (int j = 0; j < kMaxHBits; j++) {
+        t.hbitR[j] = (int8_t)a.hbitR[j];
+        t.hposS[j] = (int8_t)a.hposS[j];
+    }
+    return t;
+}
+
+cudaError_t launch_small_tasks(const SmallTask *d_tasks, const int *d_unit_task, int total_units, int *d_ctr,
+                               int n_tasks, cudaStream_t s) {
+    if (total_units <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(d_ctr, 0, sizeof(int) * (size_t)(n_tasks + 1), s);
+    if (e != cudaSuccess) return e;
+    // S of at most 2^12 values, 2^kTaskMaxK K offsets and 2^12 N offsets
+    constexpr int kSmem = 4096 * 8 + (1 << kTaskMaxK) * 8 + 4096 * 8;
+    e = set_max_dynamic_smem((const void *)small_task_kernel, kSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(total_units, 2 * sms);
+    small_task_kernel<<<grid, kThreads, kSmem, s>>>(d_tasks, d_unit_task, total_units, d_ctr);
+    return cudaGetLastError();
+}
+
+int small_task_read_error(cudaStream_t s) {
+    int v = 0, zero = 0;
+    cudaMemcpyFromSymbolAsync(&v, task_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyToSymbolAsync(task_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    return v;
 }
 
 cudaError_t launch_bitperm(const BitPermArgs &args, cudaStream_t s) {

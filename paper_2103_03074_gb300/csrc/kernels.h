@@ -263,6 +263,28 @@ struct AccumArgs {
     int64_t b_lo, b_hi;
 };
 
+// One small step run as a task of the persistent task launch
+// (launch_small_tasks): the one-thread-per-item form of SmallArgs (item =
+// row r and a chunk of nc outputs), its items cut into units of at most
+// kTaskUnitItems, and the tasks of the same launch whose outputs it reads.
+// Bit positions fit int8_t (tensor ranks stay below 64).
+constexpr int kTaskUnitItems = 1024;  // 4 items per thread of a 256-thread block
+constexpr int kTaskMaxK = 7;          // tasks loop over at most 2^7 K values per item
+struct SmallTask {
+    const float2 *T;
+    const float2 *S;
+    float2 *C;
+    int64_t rows;  // a power of two
+    int row_bits, nK, nN, nH;
+    int nc;        // outputs per item: 8, 16 or 32
+    int n_tins, n_cins;
+    int first_unit, n_units;
+    int n_deps;
+    int dep[2];    // producing tasks of this launch (indices below this task's)
+    int8_t tins[kSmallMaxBits], cins[kSmallMaxBits], kposT[kSmallMaxBits], nposC[kSmallMaxBits];
+    int8_t hbitR[kMaxHBits], hposS[kMaxHBits], kposS[kSmallMaxBits], nposS[kSmallMaxBits];
+};
+
 // launchers (kernels.cu); return cudaSuccess or the launch error
 // Raise a kernel's dynamic shared-memory limit to `bytes` on the current
 // device.  The attribute belongs to the device, so it is set once per
@@ -270,6 +292,18 @@ struct AccumArgs {
 cudaError_t set_max_dynamic_smem(const void *kernel, int bytes);
 
 cudaError_t launch_small(const SmallArgs &a, cudaStream_t s);
+// Many small steps in one persistent launch.  d_tasks[0 .. n_tasks) in
+// dependency order; d_unit_task[u] = the task of unit u (units of a task are
+// consecutive, tasks in order); d_ctr holds n_tasks + 1 ints that this call
+// zeroes first (a unit counter, then the finished units of each task).
+cudaError_t launch_small_tasks(const SmallTask *d_tasks, const int *d_unit_task, int total_units, int *d_ctr,
+                               int n_tasks, cudaStream_t s);
+// SmallTask of a one-thread-per-row small step (host; a's bit maps complete,
+// rows set; nK <= kTaskMaxK); pointers are copied as they are
+SmallTask make_small_task(const SmallArgs &a);
+// reads and clears the task launches' error word (a dependency wait that
+// gave up); synchronises the stream
+int small_task_read_error(cudaStream_t s);
 cudaError_t launch_bitperm(const BitPermArgs &a, cudaStream_t s);
 cudaError_t launch_maxabs(const MaxAbsArgs &a, cudaStream_t s);
 cudaError_t launch_gemm_f32(const GemmArgs &a, cudaStream_t s);

@@ -46,7 +46,7 @@ namespace tn {
 namespace {
 
 // values double as the step-timing recorder's kind codes (3 = extract, 4 = sum)
-enum OpKind { OP_SMALL = 0, OP_PERMUTE = 1, OP_GEMM = 2, OP_SPLIT = 5, OP_MAXABS = 6 };
+enum OpKind { OP_SMALL = 0, OP_PERMUTE = 1, OP_GEMM = 2, OP_SPLIT = 5, OP_MAXABS = 6, OP_TASKS = 7 };
 
 struct Operand {  // where an op reads or writes: static leaf or arena buffer
     int buf = -1;        // arena buffer id, or -1
@@ -73,7 +73,32 @@ struct Op {
     double macs = 0, bytes = 0;
     int gemm_variant = 0;  // 0: FP32 CUDA cores, 1: tensor-core split form
     std::string note;      // plan-time decisions, for tn_plan_describe
+    // OP_TASKS: small steps run as the tasks of one persistent launch, in
+    // dependency order; the longest chain of members that feed each other;
+    // the device task table (resolved after arena allocation, owned by the
+    // plan)
+    std::vector<Op> members;
+    int task_levels = 0;
+    std::vector<SmallTask> tasks;
+    std::vector<int> unit_task;
+    SmallTask *d_tasks = nullptr;
+    int *d_unit_task = nullptr, *d_ctr = nullptr;
 };
+
+// f(operand, written) for every operand an op reads or writes (an OP_TASKS
+// op: those of its members)
+template <typename F>
+void for_each_operand(const Op &op, F &&f) {
+    if (op.kind == OP_TASKS) {
+        for (const Op &m : op.members) for_each_operand(m, f);
+        return;
+    }
+    f(op.in0, false);
+    f(op.in1, false);
+    f(op.aux, false);
+    f(op.out, true);
+    f(op.maxout, true);
+}
 
 struct Buf {
     int64_t elems = 0;
@@ -206,6 +231,7 @@ struct tn_plan {
     char *d_arena = nullptr;
     double *d_host_amp = nullptr;  // tn_contract_slices_host: amplitudes + 3 statistics
     tn::ExtractEntry *d_extract = nullptr;
+    std::vector<void *> task_mem;  // device task tables of OP_TASKS ops
     bool failed = false;
     // stats
     double macs_batch = 0, macs_prologue = 0, bytes_batch = 0, bytes_prologue = 0;
@@ -287,6 +313,78 @@ bool make_planar(const std::vector<int32_t> &src, const std::vector<int32_t> &ds
         if (bits[k].first == k && run == k) run++;
     }
     return run >= min_run;
+}
+
+// Small steps whose T and C each hold at most 2^bits elements (and whose K
+// has at most 2^kTaskMaxK values) run as the tasks of one persistent launch
+// (OP_TASKS) instead of one launch each.  Scanning the op list in order, such
+// a step joins the latest task group when each of its inputs comes from a
+// member of that group or from an op before the group's position; otherwise
+// it opens a new group at its own position.  A group runs where its first
+// member stood, all members in one launch, so the timeline gives every member
+// that one time (no member's buffer shares arena bytes with another's).
+constexpr int kDefaultTaskBits = 17;
+
+void group_tasks(std::vector<Op> &ops, int bits) {
+    const int n = (int)ops.size();
+    std::unordered_map<int, int> prod;  // arena buffer -> producing op
+    for (int i = 0; i < n; i++)
+        if (ops[i].out.buf >= 0) prod[ops[i].out.buf] = i;
+    auto eligible = [&](const Op &op) {
+        // (a step set up for the tiled kernel keeps its one-thread-per-row
+        // fields; one that stores the next step's planes does not qualify)
+        if (op.kind != OP_SMALL || op.small.tiled == 3 || op.small.nK > kTaskMaxK) return false;
+        const double elems = (double)op.small.rows * std::exp2((double)std::max(op.small.nK, op.small.nN));
+        return elems <= std::exp2((double)bits);
+    };
+    std::vector<int> group(n, -1), level(n, 0), gpos, count;
+    for (int i = 0; i < n; i++) {
+        if (!eligible(ops[i])) continue;
+        int p[2] = {-1, -1};
+        const Operand *in[2] = {&ops[i].in0, &ops[i].in1};
+        for (int q = 0; q < 2; q++)
+            if (in[q]->buf >= 0) {
+                auto it = prod.find(in[q]->buf);
+                if (it != prod.end()) p[q] = it->second;
+            }
+        int g = (int)gpos.size() - 1;
+        bool join = g >= 0;
+        for (int q = 0; q < 2 && join; q++)
+            if (p[q] >= 0 && !(p[q] < gpos[g] || group[p[q]] == g)) join = false;
+        if (!join) {
+            gpos.push_back(i);
+            count.push_back(0);
+            g = (int)gpos.size() - 1;
+        }
+        group[i] = g;
+        count[g]++;
+        for (int q = 0; q < 2; q++)
+            if (p[q] >= 0 && group[p[q]] == g) level[i] = std::max(level[i], level[p[q]] + 1);
+    }
+    std::vector<Op> out;
+    out.reserve(n);
+    std::vector<int> gop(gpos.size(), -1);  // index in `out` of group g's op
+    for (int i = 0; i < n; i++) {
+        const int g = group[i];
+        if (g < 0 || count[g] < 2) {
+            out.push_back(std::move(ops[i]));
+            continue;
+        }
+        if (gop[g] < 0) {
+            Op t;
+            t.kind = OP_TASKS;
+            t.step = ops[i].step;
+            t.dep = ops[i].dep;
+            gop[g] = (int)out.size();
+            out.push_back(std::move(t));
+        }
+        Op &t = out[gop[g]];
+        t.task_levels = std::max(t.task_levels, level[i] + 1);
+        t.macs += ops[i].macs;
+        t.bytes += ops[i].bytes;
+        t.members.push_back(std::move(ops[i]));
+    }
+    ops.swap(out);
 }
 
 // Compile the op lists for batch width nb.  Returns the arena size or -1 on
@@ -751,8 +849,14 @@ int64_t compile(tn_plan &P, int nb) {
     P.root = rt.where;
     const bool root_dep = rt.dep;
 
-    // split into prologue (slice-invariant) and per-block ops; timeline
+    // split into prologue (slice-invariant) and per-block ops; the tiny
+    // small steps of each become tasks of persistent launches; timeline
     for (auto &op : ops) (op.dep ? P.batch : P.prologue).push_back(op);
+    const int task_bits = P.opts.small_tasks == 0 ? kDefaultTaskBits : P.opts.small_tasks;
+    if (task_bits > 0) {
+        group_tasks(P.prologue, task_bits);
+        group_tasks(P.batch, task_bits);
+    }
     const int T_pro = (int)P.prologue.size();
     const int T_ext = T_pro;                       // extraction at the start of a block
     const int T_acc = T_pro + 1 + (int)P.batch.size();
@@ -770,26 +874,17 @@ int64_t compile(tn_plan &P, int nb) {
         touch(Operand{b, -1}, T_ext);
         buf_dep[b] = 1;
     }
-    for (int i = 0; i < T_pro; i++) {
-        Op &op = P.prologue[i];
-        touch(op.in0, i);
-        touch(op.in1, i);
-        touch(op.out, i);
-        touch(op.aux, i);
-        touch(op.maxout, i);
-        if (op.out.buf >= 0) buf_pro[op.out.buf] = 1;
-        if (op.maxout.buf >= 0) buf_pro[op.maxout.buf] = 1;
-    }
+    for (int i = 0; i < T_pro; i++)
+        for_each_operand(P.prologue[i], [&](const Operand &w, bool written) {
+            touch(w, i);
+            if (written && w.buf >= 0) buf_pro[w.buf] = 1;
+        });
     for (int i = 0; i < (int)P.batch.size(); i++) {
-        Op &op = P.batch[i];
-        int time = T_pro + 1 + i;
-        touch(op.in0, time);
-        touch(op.in1, time);
-        touch(op.out, time);
-        touch(op.aux, time);
-        touch(op.maxout, time);
-        if (op.out.buf >= 0) buf_dep[op.out.buf] = 1;
-        if (op.maxout.buf >= 0) buf_dep[op.maxout.buf] = 1;
+        const int time = T_pro + 1 + i;
+        for_each_operand(P.batch[i], [&](const Operand &w, bool written) {
+            touch(w, time);
+            if (written && w.buf >= 0) buf_dep[w.buf] = 1;
+        });
     }
     touch(P.root, T_acc);
     // an invariant buffer read inside the block loop lives to the loop's end
@@ -848,9 +943,43 @@ float2 *resolve(tn_plan &P, const Operand &w) {
     return P.d_leaves + w.leaf_off;
 }
 
+// The device-side table of an OP_TASKS op (host copy): one SmallTask per
+// member with resolved pointers, units of up to kTaskUnitItems items, and
+// each member's producers among the earlier members.
+void build_task_table(Op &op) {
+    op.tasks.clear();
+    op.unit_task.clear();
+    std::unordered_map<int, int> prod;  // arena buffer -> member
+    for (int i = 0; i < (int)op.members.size(); i++) {
+        const Op &m = op.members[i];
+        SmallTask t = make_small_task(m.small);
+        const int nc_bits = t.nc == 32 ? 5 : (t.nc == 16 ? 4 : 3);
+        const int64_t items = m.small.rows << (m.small.nN > nc_bits ? m.small.nN - nc_bits : 0);
+        t.first_unit = (int)op.unit_task.size();
+        t.n_units = (int)((items + kTaskUnitItems - 1) / kTaskUnitItems);
+        for (const Operand *w : {&m.in0, &m.in1})
+            if (w->buf >= 0) {
+                auto it = prod.find(w->buf);
+                if (it != prod.end() && t.n_deps < 2 && (t.n_deps == 0 || t.dep[0] != it->second))
+                    t.dep[t.n_deps++] = it->second;
+            }
+        for (int u = 0; u < t.n_units; u++) op.unit_task.push_back(i);
+        op.tasks.push_back(t);
+        if (m.out.buf >= 0) prod[m.out.buf] = i;
+    }
+}
+
 void resolve_all(tn_plan &P) {
     auto fix = [&](Op &op) {
         switch (op.kind) {
+        case OP_TASKS:
+            for (Op &m : op.members) {
+                m.small.T = resolve(P, m.in0);
+                m.small.S = resolve(P, m.in1);
+                m.small.C = resolve(P, m.out);
+            }
+            build_task_table(op);
+            break;
         case OP_SMALL:
             op.small.T = resolve(P, op.in0);
             op.small.S = resolve(P, op.in1);
@@ -911,8 +1040,19 @@ cudaError_t run_op(const tn_plan &P, const Op &op, cudaStream_t s) {
         return launch_gemm_f32(op.gemm, s);
     case OP_SPLIT: return launch_bitperm(op.bp, s);
     case OP_MAXABS: return launch_maxabs(op.mx, s);
+    case OP_TASKS:
+        return launch_small_tasks(op.d_tasks, op.d_unit_task, (int)op.unit_task.size(), op.d_ctr,
+                                  (int)op.tasks.size(), s);
     }
     return cudaErrorInvalidValue;
+}
+
+// reads and clears the error words of the bounded device waits (tensor-core
+// pipeline, task dependencies); synchronises the stream
+bool device_wait_error(cudaStream_t s) {
+    const int a = tc_read_error(s);
+    const int b = small_task_read_error(s);
+    return a != 0 || b != 0;
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -928,6 +1068,9 @@ namespace {
 
 inline float l2f(double x) { return (float)(std::log2(x + 1.0) / 32.0); }
 
+// time per dependency level of a task launch (wait, stage S, compute, release)
+constexpr double kTaskLevelMs = 3.0e-3;
+
 // Roofline time of one step in ms: the larger of its algorithmic bytes over
 // HBM bandwidth and its arithmetic over the peak of the unit that runs it,
 // plus a launch floor.  Nominal GB300 figures: 7 TB/s HBM3e, 80 TFLOP/s FP32
@@ -940,6 +1083,12 @@ inline float l2f(double x) { return (float)(std::log2(x + 1.0) / 32.0); }
 double roofline_ms(const Op &op, tn_form form) {
     const double hbm = 7.0e12, fp32 = 80.0e12, floor_ms = 2.0e-3;
     double flops = 0.0, peak = fp32;
+    if (op.kind == OP_TASKS) {
+        // one launch; the chain of members that feed each other runs one
+        // dependency wait (a few microseconds) per link
+        const double t = std::max(op.bytes / hbm, 8.0 * op.macs / fp32) * 1e3;
+        return t + floor_ms + kTaskLevelMs * (op.task_levels - 1);
+    }
     if (op.kind == OP_SMALL || (op.kind == OP_GEMM && op.gemm_variant != 1)) {
         flops = 8.0 * op.macs;
     } else if (op.kind == OP_GEMM) {
@@ -973,6 +1122,13 @@ void op_features(const Op &op, tn_form form, float *f) {
     double sh[4] = {0, 0, 0, 0}, units = 1, ksplit = 1;
     int kind = 0;
     switch (op.kind) {
+    case OP_TASKS:  // many small steps: the small-step kind, units of all members
+        kind = 0;
+        sh[0] = (double)op.members.size();
+        sh[1] = (double)op.task_levels;
+        units = 0;
+        for (const Op &m : op.members) units += (double)m.small.rows;
+        break;
     case OP_SMALL: {
         kind = 0;
         const double nc = (1 << op.small.nN) <= 32 ? 1.0 : (double)((1 << op.small.nN) / 32);
@@ -1288,6 +1444,24 @@ extern "C" int tn_plan_create(tn_plan_t *out, int n_tensors, const int32_t *rank
         for (auto &op : *ops)
             if (op.kind == OP_GEMM && op.gemm_variant == 1 && !tc_prepare(op.tc))
                 return fail(TN_ERR_CUDA, "TMA descriptor encoding failed");
+    // task tables: tasks, unit -> task map and counters in one allocation
+    for (auto *ops : {&P->prologue, &P->batch})
+        for (auto &op : *ops) {
+            if (op.kind != OP_TASKS) continue;
+            const size_t tb = sizeof(SmallTask) * op.tasks.size();
+            const size_t ub = sizeof(int) * op.unit_task.size();
+            const size_t cb = sizeof(int) * (op.tasks.size() + 1);
+            char *mem = nullptr;
+            e = cudaMalloc(&mem, tb + ub + cb);
+            if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc task table");
+            P->task_mem.push_back(mem);
+            op.d_tasks = reinterpret_cast<SmallTask *>(mem);
+            op.d_unit_task = reinterpret_cast<int *>(mem + tb);
+            op.d_ctr = reinterpret_cast<int *>(mem + tb + ub);
+            e = cudaMemcpy(op.d_tasks, op.tasks.data(), tb, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(op.d_unit_task, op.unit_task.data(), ub, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "copy task table");
+        }
     if (!P->extract.empty()) {
         e = cudaMalloc(&P->d_extract, sizeof(ExtractEntry) * P->extract.size());
         if (e != cudaSuccess) return fail(TN_ERR_OOM, "cudaMalloc extract table");
@@ -1317,6 +1491,10 @@ tn_plan::ProfRow prof_row(int phase, int idx, const Op &op) {
         r.shape[1] = (double)op.bp.plane_stride;
     } else if (op.kind == OP_MAXABS) {
         r.shape[1] = (double)op.mx.n;
+    } else if (op.kind == OP_TASKS) {
+        r.shape[0] = (double)op.members.size();
+        r.shape[1] = (double)op.unit_task.size();
+        r.shape[2] = (double)op.task_levels;
     }
     return r;
 }
@@ -1351,12 +1529,12 @@ cudaError_t capture_ops(const tn_plan &P, const std::vector<Op> &ops, cudaGraphE
         return {b.off, b.off + b.elems * 8};
     };
     auto hit = [](const Rg &a, const Rg &b) { return a.lo < a.hi && b.lo < b.hi && a.lo < b.hi && b.lo < a.hi; };
-    std::vector<std::array<Rg, 3>> rd(n);
-    std::vector<std::array<Rg, 2>> wr(n);
-    for (int i = 0; i < n; i++) {
-        rd[i] = {range(ops[i].in0), range(ops[i].in1), range(ops[i].aux)};
-        wr[i] = {range(ops[i].out), range(ops[i].maxout)};
-    }
+    std::vector<std::vector<Rg>> rd(n), wr(n);
+    for (int i = 0; i < n; i++)
+        for_each_operand(ops[i], [&](const Operand &w, bool written) {
+            const Rg r = range(w);
+            if (r.lo < r.hi) (written ? wr[i] : rd[i]).push_back(r);
+        });
     std::vector<std::vector<int>> deps(n);
     for (int i = 0; i < n; i++)
         for (int j = 0; j < i; j++) {
@@ -1512,9 +1690,9 @@ extern "C" int tn_contract_slices(tn_plan_t P, int64_t begin, int64_t end, doubl
             return cuda_fail(e, "profile");
         }
     }
-    if (prof && tc_read_error(s) != 0) {
+    if (prof && device_wait_error(s)) {
         P->failed = true;
-        return fail(TN_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
+        return fail(TN_ERR_TIMEOUT, "a bounded device wait expired (tensor-core pipeline or task dependency)");
     }
     if (P->opts.use_graph && !prof && !P->graphs_ready && (e = build_graphs(*P)) != cudaSuccess) {
         P->failed = true;
@@ -1609,7 +1787,8 @@ extern "C" int tn_plan_autotune(tn_plan_t P, int reps, tn_stream_t stream) {
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc == TN_OK && tc_read_error(s) != 0) rc = fail(TN_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
+    if (rc == TN_OK && device_wait_error(s))
+        rc = fail(TN_ERR_TIMEOUT, "a bounded device wait expired (tensor-core pipeline or task dependency)");
     if (rc) P->failed = true;
     // graphs captured earlier hold the old configuration
     if (P->graphs_ready) {
@@ -1810,6 +1989,7 @@ extern "C" void tn_plan_destroy(tn_plan_t P) {
     if (P->d_arena) cudaFree(P->d_arena);
     if (P->d_host_amp) cudaFree(P->d_host_amp);
     if (P->d_extract) cudaFree(P->d_extract);
+    for (void *m : P->task_mem) cudaFree(m);
     for (auto &ev : P->prof_ev) cudaEventDestroy(ev);
     if (P->g_pro) cudaGraphExecDestroy(P->g_pro);
     if (P->g_body) cudaGraphExecDestroy(P->g_body);
@@ -1847,6 +2027,17 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
     char line[512];
     auto put = [&](const char *phase, const Op &op) {
         switch (op.kind) {
+        case OP_TASKS: {
+            int64_t rows = 0;
+            for (const Op &m : op.members) rows += m.small.rows;
+            std::snprintf(line, sizeof line, "%s step %d tasks n=%d levels=%d rows=%lld (steps", phase, op.step,
+                          (int)op.members.size(), op.task_levels, (long long)rows);
+            std::string l(line);
+            for (size_t i = 0; i < op.members.size() && i < 8; i++) l += " " + std::to_string(op.members[i].step);
+            l += op.members.size() > 8 ? " ...)" : ")";
+            std::snprintf(line, sizeof line, "%s", l.c_str());
+            break;
+        }
         case OP_SMALL: {
             const SmallArgs &a = op.small;
             const char *kern = a.tiled == 1 ? "tiled, staged C" : a.tiled == 2 ? "tiled, direct C"
@@ -1991,7 +2182,8 @@ extern "C" int tn_amplitudes(const tn_circuit *circuit, const uint8_t *fixed_bit
     if (rc == TN_OK) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "contract");
-        else if (tc_read_error(s) != 0) rc = fail(TN_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
+        else if (device_wait_error(s))
+            rc = fail(TN_ERR_TIMEOUT, "a bounded device wait expired (tensor-core pipeline or task dependency)");
     }
     tn_plan_destroy(plan);
     return rc;

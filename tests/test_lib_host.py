@@ -398,7 +398,7 @@ def test_roofline_objective_ranks_trees_by_estimated_time(tn):
         est[ob] = tn.estimate_tree_ms(L, O, sl, tree, form="fp16x3")[0]
     assert est["roofline"] <= est["macs"] * 1.0001, est
     with pytest.raises(tn.TNError):
-        tn.find_order(L, O, tn.search_opts(trials=2, objective=2))
+        tn.find_order(L, O, tn.search_opts(trials=2, objective=3))
 
 
 def _best_connected_tail(L, O, nq, k):
