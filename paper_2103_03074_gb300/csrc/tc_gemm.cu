@@ -274,50 +274,106 @@ __device__ __forceinline__ uint64_t scatter8(uint64_t v, const int8_t *pos, int 
     return r;
 }
 
-// the pieces of one value for a 4M (four planes) or 3M (six planes) mode
-template <bool M3>
-struct PiecesT {
-    uint32_t q[M3 ? 6 : 4];
+// The split mode of the planes a GEMM of kernel form KIND writes for the
+// next step of the same form: 1 bf16 hi/lo, 2 tf32 hi/lo, 3 scaled fp16, 4
+// scaled fp16 hi/lo; 5-7 the 3M modes of 1, 2 and 4 (a third value re + im).
+__host__ __device__ constexpr int planar_mode_of(int kind, bool m3) {
+    return kind == kBF16 ? (m3 ? 5 : 1) : kind == kTF32 ? (m3 ? 6 : 2) : kind == kFP16 ? 3 : (m3 ? 7 : 4);
+}
+
+// Pieces of two values x0, x1 that the epilogue has already scaled (the
+// scaled modes' 2^-e is folded into the accumulator scale): round to
+// nearest hi = piece(x), lo = piece(x - hi), as the split pass rounds them.
+// 16-bit modes pack the two values' pieces into one word each (x0 low).
+template <int MODE>
+__device__ __forceinline__ void pieces_pair16(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+    if constexpr (mode_base(MODE) == 1) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(x0, x1);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        if constexpr (mode_base(MODE) == 4) {
+            const float2 hf = __half22float2(h);
+            const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+            lo = *reinterpret_cast<const uint32_t *>(&l);
+        } else {
+            lo = 0u;
+        }
+    }
+}
+
+// the values an element contributes to the planes: re, im (and re + im for
+// the 3M modes)
+template <int MODE>
+__device__ __forceinline__ float value_of(float2 v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : v.x + v.y);
+}
+
+template <int MODE>
+struct PlaneShape {
+    static constexpr int kValues = mode_3m(MODE) ? 3 : 2;     // values per element
+    static constexpr int kPieces = MODE == 3 ? 1 : 2;         // hi (and lo) per value; plane q =
+                                                              // piece * kValues + value
+    static constexpr bool kWord = mode_word(MODE);            // 32-bit (tf32) pieces
 };
-template <bool M3>
-__device__ __forceinline__ PiecesT<M3> split_t(int mode, float2 v, int e) {
-    PiecesT<M3> r;
-    if constexpr (M3) {
-        const Pieces6 p = split_value_3m(mode, v, e);
-#pragma unroll
-        for (int q = 0; q < 6; q++) r.q[q] = p.q[q];
-    } else {
-        const Pieces p = split_value(mode, v, e);
-#pragma unroll
-        for (int q = 0; q < 4; q++) r.q[q] = p.q[q];
-    }
-    return r;
-}
 
-template <bool M3>
-__device__ __forceinline__ void plane_store1(const TcPlanarOut &o, uint64_t d, float2 v, int e) {
-    const PiecesT<M3> pc = split_t<M3>(o.mode, v, e);
-    const int np = mode_planes(o.mode);
-    if (mode_word(o.mode)) {
-        uint32_t *P = reinterpret_cast<uint32_t *>(o.planes);
-        for (int q = 0; q < np; q++) P[d + q * o.plane_stride] = pc.q[q];
+// Store the pieces of n (1, 2 or 4) neighbouring elements v[0 .. n) at plane
+// offset d (a multiple of n) of every plane.
+template <int MODE, int NE>
+__device__ __forceinline__ void plane_store(const TcPlanarOut &o, uint64_t d, const float2 *v) {
+    using PS = PlaneShape<MODE>;
+    if constexpr (PS::kWord) {
+        uint32_t *P = reinterpret_cast<uint32_t *>(o.planes) + d;
+#pragma unroll
+        for (int c = 0; c < PS::kValues; c++) {
+            uint32_t hi[NE], lo[NE];
+#pragma unroll
+            for (int e = 0; e < NE; e++) {
+                const float x = value_of<MODE>(v[e], c);
+                hi[e] = tf32_rna(x);
+                lo[e] = tf32_rna(x - __uint_as_float(hi[e]));
+            }
+            uint32_t *Ph = P + (int64_t)c * o.plane_stride, *Pl = P + (int64_t)(PS::kValues + c) * o.plane_stride;
+            if constexpr (NE == 4) {
+                *reinterpret_cast<uint4 *>(Ph) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4 *>(Pl) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            } else if constexpr (NE == 2) {
+                *reinterpret_cast<uint2 *>(Ph) = make_uint2(hi[0], hi[1]);
+                *reinterpret_cast<uint2 *>(Pl) = make_uint2(lo[0], lo[1]);
+            } else {
+                *Ph = hi[0];
+                *Pl = lo[0];
+            }
+        }
     } else {
-        uint16_t *P = reinterpret_cast<uint16_t *>(o.planes);
-        for (int q = 0; q < np; q++) P[d + q * o.plane_stride] = (uint16_t)pc.q[q];
-    }
-}
-
-// elements d, d + 1 (d even)
-template <bool M3>
-__device__ __forceinline__ void plane_store2(const TcPlanarOut &o, uint64_t d, float2 v0, float2 v1, int e) {
-    const PiecesT<M3> p0 = split_t<M3>(o.mode, v0, e), p1 = split_t<M3>(o.mode, v1, e);
-    const int np = mode_planes(o.mode);
-    if (mode_word(o.mode)) {
-        uint2 *P = reinterpret_cast<uint2 *>(o.planes);
-        for (int q = 0; q < np; q++) P[(d + q * o.plane_stride) >> 1] = make_uint2(p0.q[q], p1.q[q]);
-    } else {
-        uint32_t *P = reinterpret_cast<uint32_t *>(o.planes);
-        for (int q = 0; q < np; q++) P[(d + q * o.plane_stride) >> 1] = p0.q[q] | (p1.q[q] << 16);
+        uint16_t *P = reinterpret_cast<uint16_t *>(o.planes) + d;
+#pragma unroll
+        for (int c = 0; c < PS::kValues; c++) {
+            uint16_t *Ph = P + (int64_t)c * o.plane_stride;
+            uint16_t *Pl = P + (int64_t)(PS::kValues + c) * o.plane_stride;
+            if constexpr (NE == 1) {
+                uint32_t hi, lo;
+                pieces_pair16<MODE>(value_of<MODE>(v[0], c), 0.f, hi, lo);
+                *Ph = (uint16_t)hi;
+                if constexpr (PS::kPieces == 2) *Pl = (uint16_t)lo;
+            } else {
+                uint32_t hi[NE / 2], lo[NE / 2];
+#pragma unroll
+                for (int e = 0; e < NE / 2; e++)
+                    pieces_pair16<MODE>(value_of<MODE>(v[2 * e], c), value_of<MODE>(v[2 * e + 1], c), hi[e], lo[e]);
+                if constexpr (NE == 4) {
+                    *reinterpret_cast<uint2 *>(Ph) = make_uint2(hi[0], hi[1]);
+                    if constexpr (PS::kPieces == 2) *reinterpret_cast<uint2 *>(Pl) = make_uint2(lo[0], lo[1]);
+                } else {
+                    *reinterpret_cast<uint32_t *>(Ph) = hi[0];
+                    if constexpr (PS::kPieces == 2) *reinterpret_cast<uint32_t *>(Pl) = lo[0];
+                }
+            }
+        }
     }
 }
 
@@ -370,57 +426,36 @@ __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane
 }
 
 // Split the staged half tile (rows mh .. mh + 63) into the next step's
-// planes: warp fw of the 8 epilogue warps takes the groups j_hi = fw, fw + 8,
-// ...; each lane two (or four) neighbouring elements of a group.
-// base = the destination offset of the half tile's element (0, 0)
-template <bool M3, int EW>
+// planes: epilogue warp fw takes the groups j_hi = fw, fw + EW, ...; each
+// lane two (or four) neighbouring elements of a group.  The staged values
+// are already scaled for the planes.  base = the destination offset of the
+// half tile's element (0, 0).
+template <int MODE, int EW>
 __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base, const float2 *st,
-                                             const uint2 *jtab, const PlanarLane &L, int fw, int lane, int e) {
+                                             const uint2 *jtab, const PlanarLane &L, int fw, int lane) {
     const int nlo = planar_nlo(o);
     const int n_hi = 1 << (o.ntb - nlo);
     if (L.quad) {
-        const int np = mode_planes(o.mode);
-        constexpr int NPQ = M3 ? 6 : 4;
         for (int jh = fw; jh < n_hi; jh += EW) {
             const uint2 g = jtab[jh];
-            const uint64_t d0 = base + g.y + L.d[0];  // a multiple of 4
-            if (mode_word(o.mode)) {
-                PiecesT<M3> pc[4];
+            float2 v[4];
 #pragma unroll
-                for (int q = 0; q < 4; q++) pc[q] = split_t<M3>(o.mode, st[(int)g.x + L.s[q]], e);
-                uint4 *P = reinterpret_cast<uint4 *>(o.planes);
-                for (int q = 0; q < np; q++)
-                    P[(d0 + q * o.plane_stride) >> 2] = make_uint4(pc[0].q[q], pc[1].q[q], pc[2].q[q], pc[3].q[q]);
-            } else {
-                // 16-bit pieces: pack each plane's words as the element pairs
-                // are split (fewer live registers than four elements' pieces)
-                uint32_t w[NPQ][2];
-#pragma unroll
-                for (int h2 = 0; h2 < 2; h2++) {
-                    const PiecesT<M3> a = split_t<M3>(o.mode, st[(int)g.x + L.s[2 * h2]], e);
-                    const PiecesT<M3> b = split_t<M3>(o.mode, st[(int)g.x + L.s[2 * h2 + 1]], e);
-#pragma unroll
-                    for (int q = 0; q < NPQ; q++) w[q][h2] = a.q[q] | (b.q[q] << 16);
-                }
-                uint2 *P = reinterpret_cast<uint2 *>(o.planes);
-#pragma unroll
-                for (int q = 0; q < NPQ; q++)
-                    if (q < np) P[(d0 + q * o.plane_stride) >> 2] = make_uint2(w[q][0], w[q][1]);
-            }
+            for (int q = 0; q < 4; q++) v[q] = st[(int)g.x + L.s[q]];
+            plane_store<MODE, 4>(o, base + g.y + L.d[0], v);  // offset a multiple of 4
         }
         return;
     }
     const bool v1 = 2 * lane + 1 < (1 << nlo), v0 = 2 * lane < (1 << nlo);
     for (int jh = fw; jh < n_hi; jh += EW) {
         const uint2 g = jtab[jh];
-        const float2 a = st[(int)g.x + L.s[0]];
-        const float2 b = st[(int)g.x + L.s[1]];
-        const uint64_t d0 = base + g.y + L.d[0];
+        float2 v[2];
+        v[0] = st[(int)g.x + L.s[0]];
+        v[1] = st[(int)g.x + L.s[1]];
         if (L.pair) {
-            plane_store2<M3>(o, d0, a, b, e);
+            plane_store<MODE, 2>(o, base + g.y + L.d[0], v);
         } else {
-            if (v0) plane_store1<M3>(o, d0, a, e);
-            if (v1) plane_store1<M3>(o, base + g.y + L.d[1], b, e);
+            if (v0) plane_store<MODE, 1>(o, base + g.y + L.d[0], v);
+            if (v1) plane_store<MODE, 1>(o, base + g.y + L.d[1], v + 1);
         }
     }
 }
@@ -597,6 +632,11 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
             if (!(mB > 0.f)) mB = __uint_as_float(p.scales[1]);
             e_out = fp16s_exponent(mA) + fp16s_exponent(mB) + 15 + lk;
         }
+        // accumulator scale 2^(e_scale - e_out) as one or two normal powers of two
+        const int e_acc = e_scale - e_out;
+        const int e_1 = (e_acc >= -126 && e_acc <= 127) ? e_acc : e_acc / 2;
+        const float sc1 = __int_as_float((127 + e_1) << 23), sc2 = __int_as_float((127 + e_acc - e_1) << 23);
+        float run_max = 0.f;
         // every flush warp walks every tile of this CTA and reaches the same
         // named barriers even after a failed wait (it then skips waits,
         // tensor-memory reads and stores), so the warps never part ways
@@ -665,20 +705,17 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                 if (lane == 0) mbar_arrive(smem_u32(&tempty[t]));
             }
             if (kind_scaled(KIND)) {
-                // undo the operands' power-of-two scales (exact): a product
-                // with 2^e_scale rounds as ldexpf does when 2^e_scale is a
-                // normal float
-                // (outside the normal range of 2^e_scale, two such products;
-                // exact while the intermediate stays normal)
-                const int e1 = (e_scale >= -126 && e_scale <= 127) ? e_scale : e_scale / 2;
-                const int e2 = e_scale - e1;
-                const float sc1 = __int_as_float((127 + e1) << 23), sc2 = __int_as_float((127 + e2) << 23);
+                // undo the operands' power-of-two scales and, for scaled
+                // planes, apply the planes' 2^-e_out in the same product
+                // (exact: a product with a normal power of two; outside the
+                // normal range two such products, exact while the
+                // intermediate stays normal)
 #pragma unroll
                 for (int j = 0; j < kCW; j++) {
                     acc_re[j] *= sc1;
                     acc_im[j] *= sc1;
                 }
-                if (e2 != 0) {
+                if (sc2 != 1.f) {
 #pragma unroll
                     for (int j = 0; j < kCW; j++) {
                         acc_re[j] *= sc2;
@@ -687,19 +724,11 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                 }
             }
             if (p.max_slot && ok) {
-                // max |re|, |im| of the tile (rows and columns past the edge
-                // hold zeros: their operand rows were zero-filled); non-negative
-                // floats order like their bit patterns
-                float mx = 0.f;
+                // running max |re|, |im| of the values written (rows and
+                // columns past the edge hold zeros: their operand rows were
+                // zero-filled); published once per warp after the last tile
 #pragma unroll
-                for (int j = 0; j < kCW; j++) mx = fmaxf(mx, fmaxf(fabsf(acc_re[j]), fabsf(acc_im[j])));
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-                if (mode_scaled(p.out.mode)) {
-                    if (lane == 0) atomicMax(p.max_slot + 2, __float_as_uint(mx));  // true max
-                    mx = ldexpf(1.f, e_out + 13);  // the planes' exponent
-                }
-                if (lane == 0) atomicMax(p.max_slot, __float_as_uint(mx));
+                for (int j = 0; j < kCW; j++) run_max = fmaxf(run_max, fmaxf(fabsf(acc_re[j]), fabsf(acc_im[j])));
             }
             float2 *Ch = p.C + (int64_t)tc.h * p.sCh;
             if (p.ksplit > 1) {
@@ -738,8 +767,8 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                     // m bit 6 is the half (m0 is a multiple of 128); with
                     // M <= 64 the second half lies past M and is skipped
                     if (ok && tc.m0 + hp * (TM / 2) < p.M)
-                        planar_write<M3, EW>(p.out, hp ? (pbase | (1ull << p.out.mpos[6])) : pbase, stage_out, jtab, pl,
-                                         fw, lane, e_out);
+                        planar_write<planar_mode_of(KIND, M3), EW>(
+                            p.out, hp ? (pbase | (1ull << p.out.mpos[6])) : pbase, stage_out, jtab, pl, fw, lane);
                 }
                 for (int rr = fw; ok && p.out.mode == 0 && rr < TM / 2; rr += kFlushWarps) {
                     const int64_t mm = tc.m0 + hp * (TM / 2) + rr;
@@ -755,6 +784,23 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                     }
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(32 * kFlushWarps) : "memory");
+            }
+        }
+        if (p.max_slot && ok) {
+            // one atomic per warp and launch; non-negative floats order like
+            // their bit patterns
+            float mx = run_max;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+            if (lane == 0) {
+                if (mode_scaled(p.out.mode)) {
+                    // the written values carry 2^-e_out: the output's true max
+                    // (exact), and the planes' exponent for the next step
+                    atomicMax(p.max_slot + 2, __float_as_uint(ldexpf(mx, e_out)));
+                    atomicMax(p.max_slot, __float_as_uint(ldexpf(1.f, e_out + 13)));
+                } else {
+                    atomicMax(p.max_slot, __float_as_uint(mx));
+                }
             }
         }
     }
@@ -919,8 +965,14 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     const bool m3 = g.products == 3;
     if (g.products != 0 && g.products != 4 && !(m3 && tc_form_has_3m(g.form))) return cudaErrorInvalidValue;
     if (m3 && g.chunk_bytes != 32 && g.chunk_bytes != 64) return cudaErrorInvalidValue;  // tc_prepare sets it
-    // a 3M GEMM writes 3M planes (modes 5-7), a 4M GEMM 4M planes (1-4)
-    if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || p.out.mode < 1 || p.out.mode > 7 ||
+    // a GEMM writes the planes of its own form's split (4M or 3M); the
+    // kernel's planar epilogue is compiled for that mode only
+    const int own_mode = planar_mode_of(g.form == TN_TF32X3   ? kTF32
+                                        : g.form == TN_BF16X3 ? kBF16
+                                        : g.form == TN_FP16S  ? kFP16
+                                                              : kFP16X3,
+                                        m3);
+    if (p.out.mode != 0 && (p.ksplit > 1 || !p.out.planes || p.out.mode != own_mode ||
                             mode_3m(p.out.mode) != m3 || p.out.plane_stride > (int64_t(1) << 44) ||
                             p.out.ntb > 12))
         return cudaErrorInvalidValue;

@@ -18,10 +18,12 @@ several minutes per entry on 8 cores).  Lines are appended as they finish.
 
 cfg3: the batched workload's members of more than 20 qubits (those of 20 or
 fewer are checked against a live state vector in the tests).  Every member of
-up to 28 qubits, and a seeded sample of CFG3_SAMPLES_30 of the 30-qubit ones,
-get their full 2^k open-qubit amplitude tensor from the FP64 state vector
-(oracle.sv_native).  Lines: member index, amplitude index, real, imaginary;
-members are appended as they finish, cheapest first.
+up to 28 qubits, then the 30-qubit ones in a seeded order (CFG3_SAMPLES_30 of
+them: all), get their full 2^k open-qubit amplitude tensor from the FP64
+state vector (oracle.sv_native; about ten minutes per 30-qubit member on 8
+cores).  Lines: member index, amplitude index, real, imaginary; members are
+appended as they finish, cheapest first, so a partly written file holds a
+prefix of that order.
 """
 import os
 import sys
@@ -98,7 +100,7 @@ def cfg4():
         print(f"cfg4 entry {idx}: {a} ({time.time() - t0:.0f} s)", flush=True)
 
 
-CFG3_SAMPLES_30 = 8
+CFG3_SAMPLES_30 = 42  # every 30-qubit member (the first 8 of the seeded order were written first)
 CFG3_SAMPLE_SEED = 0x2103C3
 
 
@@ -124,14 +126,20 @@ def cfg3():
     import time
     from tn_inputs.configs import batch_recipes, make_batch_member
     path = os.path.join(HERE, "cfg3_amplitudes.txt")
+    header = (f"# batch256 members of more than 20 qubits: all up to 28 qubits, then up to {CFG3_SAMPLES_30} "
+              f"30-qubit ones in a seeded order (sample_seed={CFG3_SAMPLE_SEED:#x}; a prefix while being written); "
+              "member index, amplitude index, re, im; route=oracle.sv_native (FP64 state vector)\n")
     done = set()
     if os.path.exists(path):
-        done = {int(l.split()[0]) for l in open(path) if not l.startswith("#")}
+        lines = open(path).readlines()
+        done = {int(l.split()[0]) for l in lines if not l.startswith("#")}
+        if lines and lines[0] != header:  # the recipe's description changed, not its values
+            lines[0] = header
+            with open(path, "w") as f:
+                f.writelines(lines)
     else:
         with open(path, "w") as f:
-            f.write(f"# batch256 members of more than 20 qubits: all up to 28 qubits and {CFG3_SAMPLES_30} "
-                    f"seeded 30-qubit ones (sample_seed={CFG3_SAMPLE_SEED:#x}); member index, amplitude index, "
-                    "re, im; route=oracle.sv_native (FP64 state vector)\n")
+            f.write(header)
     rs = batch_recipes()
     for i in cfg3_members():
         if i in done:
