@@ -2058,12 +2058,23 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
                 // the tile's six column bits are the destination's six lowest
                 bool cols_low = op.tc.out.ntb >= 6;
                 for (int k = 0; k < 6 && cols_low; k++) cols_low = op.tc.out.tb[k] == k && op.tc.out.tpos[k] == k;
-                char pl[64] = "";
-                if (op.tc.out.mode)
-                    std::snprintf(pl, sizeof pl, " run_bits=%d%s%s", run,
+                char pl[160] = "";
+                if (op.tc.out.mode) {
+                    // the half tile's bits in destination order (c: column of
+                    // the tile, r: row) with their destination positions
+                    std::string tbits;
+                    for (int k = 0; k < op.tc.out.ntb; k++)
+                        tbits += (k ? "," : "") + std::string(op.tc.out.tb[k] < 6 ? "c" : "r") +
+                                 std::to_string(op.tc.out.tb[k] < 6 ? op.tc.out.tb[k] : op.tc.out.tb[k] - 6) + "@" +
+                                 std::to_string(op.tc.out.tpos[k]);
+                    const int direct = tc_planar_direct_run(op.tc.out);
+                    std::snprintf(pl, sizeof pl, " run_bits=%d%s%s%s tile_bits=%s", run,
                                   (op.tc.out.ntb >= 7 && op.tc.out.tpos[0] == 0 && op.tc.out.tpos[1] == 1) ? " quad"
                                                                                                             : "",
-                                  cols_low ? " cols_low" : "");
+                                  cols_low ? " cols_low" : "",
+                                  direct ? (" direct=" + std::to_string(1 << direct)).c_str() : " staged",
+                                  tbits.c_str());
+                }
                 std::snprintf(line, sizeof line,
                               "%s step %d gemm H=%lld M=%lld N=%lld K=%lld tensor-core%s ksplit=%d out=%s%s", phase,
                               op.step, (long long)op.gemm.H, (long long)op.gemm.M, (long long)op.gemm.N,

@@ -237,6 +237,11 @@ struct GemmTcParams {
     const unsigned *scales;  // scaled forms: max-abs slots of A and B (float bits)
     unsigned *max_slot;      // optional: atomic max of |re|, |im| over C (float bits)
     TcPlanarOut out;         // planar epilogue (out.mode > 0)
+    // planar output whose lowest destination bits are the tile's column bits
+    // c0, c1, ...: log2 of the runs of consecutive destination elements a
+    // lane stores straight from its registers (0: staged through shared
+    // memory)
+    int direct_run;
 };
 
 // tile t -> (n tile, m tile, batch h, K part); N tiles vary fastest
@@ -377,6 +382,63 @@ __device__ __forceinline__ void plane_store(const TcPlanarOut &o, uint64_t d, co
     }
 }
 
+// NW consecutive 32-bit words to p (16-byte aligned for NW >= 4, 8-byte for 2)
+template <int NW>
+__device__ __forceinline__ void store_words(void *p, const uint32_t *w) {
+    if constexpr (NW == 1) {
+        *reinterpret_cast<uint32_t *>(p) = w[0];
+    } else if constexpr (NW == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NW / 4; i++)
+            reinterpret_cast<uint4 *>(p)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    }
+}
+
+// Direct planar store of one lane's KCW columns of its row (re[], im[], the
+// values already scaled for the planes): the columns form KCW / R runs of R
+// consecutive destination elements (the destination's lowest log2 R bits
+// are the tile's lowest column bits); run_off4[v] is the destination offset
+// of the lane's columns 4v .. 4v + 3 relative to rbase.
+template <int MODE, int KCW, int R>
+__device__ __forceinline__ void direct_store(const TcPlanarOut &o, uint64_t rbase, const uint32_t *run_off4,
+                                             const float *re, const float *im) {
+    using PS = PlaneShape<MODE>;
+#pragma unroll
+    for (int u = 0; u < KCW / R; u++) {
+        const uint64_t d = rbase + run_off4[u * (R / 4)];
+#pragma unroll
+        for (int c = 0; c < PS::kValues; c++) {
+            if constexpr (PS::kWord) {
+                uint32_t hi[R], lo[R];
+#pragma unroll
+                for (int e = 0; e < R; e++) {
+                    const int i = u * R + e;
+                    const float x = c == 0 ? re[i] : (c == 1 ? im[i] : re[i] + im[i]);
+                    hi[e] = tf32_rna(x);
+                    lo[e] = tf32_rna(x - __uint_as_float(hi[e]));
+                }
+                uint32_t *P = reinterpret_cast<uint32_t *>(o.planes) + d;
+                store_words<R>(P + (int64_t)c * o.plane_stride, hi);
+                store_words<R>(P + (int64_t)(PS::kValues + c) * o.plane_stride, lo);
+            } else {
+                uint32_t hi[R / 2], lo[R / 2];
+#pragma unroll
+                for (int e = 0; e < R / 2; e++) {
+                    const int i = u * R + 2 * e;
+                    const float x0 = c == 0 ? re[i] : (c == 1 ? im[i] : re[i] + im[i]);
+                    const float x1 = c == 0 ? re[i + 1] : (c == 1 ? im[i + 1] : re[i + 1] + im[i + 1]);
+                    pieces_pair16<MODE>(x0, x1, hi[e], lo[e]);
+                }
+                uint16_t *P = reinterpret_cast<uint16_t *>(o.planes) + d;
+                store_words<R / 2>(P + (int64_t)c * o.plane_stride, hi);
+                if constexpr (PS::kPieces == 2) store_words<R / 2>(P + (int64_t)(PS::kValues + c) * o.plane_stride, lo);
+            }
+        }
+    }
+}
+
 // Planar epilogue tables.  The half tile's elements are enumerated in
 // destination order j = (j_hi, j_lo): j_lo (6 bits; 7 for quads) is lane
 // k l + q (k = 2 elements per lane, or 4 when the destination's two lowest
@@ -388,6 +450,7 @@ struct PlanarLane {
     uint32_t d[4];  // destination offset
     bool pair;      // d[1] = d[0] + 1 with d[0] even: one vector store per plane
     bool quad;      // d[q] = d[0] + q with d[0] a multiple of 4
+    bool row4;      // quad, and s[q] = s[0] + q (neighbours in one staged row)
 };
 
 __device__ __forceinline__ bool planar_quad(const TcPlanarOut &o) {
@@ -422,6 +485,7 @@ __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane
         if (q < per) planar_bits(o, per * lane + q, 0, nlo, RS, L.s[q], L.d[q]);
     }
     L.pair = o.ntb >= 6 && o.tpos[0] == 0;
+    L.row4 = L.quad && L.s[1] == L.s[0] + 1 && L.s[2] == L.s[0] + 2 && L.s[3] == L.s[0] + 3;
     return L;
 }
 
@@ -439,8 +503,20 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
         for (int jh = fw; jh < n_hi; jh += EW) {
             const uint2 g = jtab[jh];
             float2 v[4];
+            const int s0 = (int)g.x + L.s[0];
+            if (L.row4 && (s0 & 1) == 0) {
+                // the four elements are neighbours in one staged row: two
+                // 16-byte reads
+                const float4 a = *reinterpret_cast<const float4 *>(st + s0);
+                const float4 b = *reinterpret_cast<const float4 *>(st + s0 + 2);
+                v[0] = make_float2(a.x, a.y);
+                v[1] = make_float2(a.z, a.w);
+                v[2] = make_float2(b.x, b.y);
+                v[3] = make_float2(b.z, b.w);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; q++) v[q] = st[(int)g.x + L.s[q]];
+                for (int q = 0; q < 4; q++) v[q] = st[(int)g.x + L.s[q]];
+            }
             plane_store<MODE, 4>(o, base + g.y + L.d[0], v);  // offset a multiple of 4
         }
         return;
@@ -640,6 +716,27 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
         // every flush warp walks every tile of this CTA and reaches the same
         // named barriers even after a failed wait (it then skips waits,
         // tensor-memory reads and stores), so the warps never part ways
+        // direct planar store: the destination offset of this lane's row
+        // (TMEM lane = tile row) and of its columns' 4-element runs
+        constexpr int kRuns4 = kCW / 4;
+        uint32_t run_off4[kRuns4];
+        uint64_t row_off = 0;
+        if (p.direct_run > 0) {
+            const int row = lg * 32 + lane;
+#pragma unroll
+            for (int v = 0; v < kRuns4; v++) run_off4[v] = 0;
+            for (int k = 0; k < p.out.ntb; k++) {
+                const int b = p.out.tb[k];
+                if (b >= 6) {
+                    if ((row >> (b - 6)) & 1) row_off |= 1ull << p.out.tpos[k];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < kRuns4; v++)
+                        if (((cq * kCW + 4 * v) >> b) & 1) run_off4[v] |= 1u << p.out.tpos[k];
+                }
+            }
+            if (row >> 6) row_off |= 1ull << p.out.mpos[6];
+        }
         PlanarLane pl;
         if (p.out.mode != 0) {
             pl = planar_lane(p.out, lane, R::kOutRS);
@@ -751,6 +848,16 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                                                       scatter8((uint64_t)tc.m0, p.out.mpos, p.out.nM) |
                                                       scatter8((uint64_t)tc.n0, p.out.npos, p.out.nN))
                                                    : 0;
+            if (p.direct_run > 0) {
+                // full tiles only (the launcher checks M and N): every lane
+                // stores its own row's columns, no staging
+                if (ok) {
+                    constexpr int MODE = planar_mode_of(KIND, M3);
+                    const uint64_t rb = pbase + row_off;
+                    direct_store<MODE, kCW, mode_word(MODE) ? 4 : 8>(p.out, rb, run_off4, acc_re, acc_im);
+                }
+                continue;
+            }
 #pragma unroll
             for (int hp = 0; hp < 2; hp++) {
                 if ((lg >> 1) == hp) {
@@ -851,6 +958,21 @@ bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int6
 }
 
 }  // namespace
+
+int tc_planar_direct_run(const TcPlanarOut &o) {
+    // Full 128 x 64 tiles whose destination starts with 16 bytes of one row
+    // (the tile's column bits c0 .. c(J-1) at positions 0 .. J-1: 8 elements
+    // of a 16-bit plane, 4 of a 32-bit one) followed by the row bit r0 at
+    // position J: the lanes (rows) of a warp then store 16 bytes each, two
+    // neighbouring lanes one whole 32-byte sector, from registers.  Other
+    // layouts go through the shared-memory staging (whole 512-byte rows).
+    if (o.mode == 0 || o.nN < 6 || o.nM < 7) return 0;
+    const int J = mode_word(o.mode) ? 2 : 3;
+    if (o.ntb <= J) return 0;
+    for (int k = 0; k < J; k++)
+        if (o.tb[k] != k || o.tpos[k] != k) return 0;
+    return (o.tb[J] == 6 && o.tpos[J] == J) ? J : 0;
+}
 
 bool tc_form_available(tn_form form) {
     return (form == TN_BF16X3 || form == TN_TF32X3 || form == TN_FP16S || form == TN_FP16X3) && encode_fn() != nullptr;
@@ -991,6 +1113,7 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     if ((g.form == TN_FP16S || g.form == TN_FP16X3) && !g.scales) return cudaErrorInvalidValue;
+    p.direct_run = tc_planar_direct_run(p.out);
     const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
     if (gm > INT32_MAX || gn > INT32_MAX) return cudaErrorInvalidConfiguration;
     p.gm = (int)gm;

@@ -47,6 +47,11 @@ struct TcGemm {
     alignas(64) unsigned char mapB[128];
 };
 
+// log2 of the runs a planar epilogue stores straight from registers (the
+// destination's lowest bits are the tile's lowest column bits, full tiles),
+// or 0 when it stages the tile through shared memory
+int tc_planar_direct_run(const TcPlanarOut &o);
+
 // true if `form` has a tensor-core GEMM compiled into this library (and the
 // driver entry point for TMA descriptors is reachable)
 bool tc_form_available(tn_form form);
