@@ -92,8 +92,10 @@ TC_PEAK_RATIO = {"bf16x3": 1.0, "tf32x3": 0.5, "fp16x3": 1.0, "fp16s": 1.0,
 FORM_CHOICES = ["fp32", "bf16x3", "tf32x3", "fp16x3", "fp16s", "bf16x3_3m", "tf32x3_3m", "fp16x3_3m"]
 
 
-# plan options every bench plan takes (set from the command line)
+# plan options every bench plan takes, and whether plans autotune their
+# tensor-core GEMMs before use (set from the command line)
 PLAN_DEFAULTS = {}
+AUTOTUNE = []
 
 
 def make_plan(tn, L, T, O, sliced, tree, name, **opts):
@@ -101,7 +103,10 @@ def make_plan(tn, L, T, O, sliced, tree, name, **opts):
     product on the tensor cores for the *_3m names (tc_products 3)."""
     form, _, m3 = name.partition("_")
     o = dict(PLAN_DEFAULTS, **opts)
-    return tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(tc_products=3 if m3 else 0, **o))
+    plan = tn.Plan(L, T, O, sliced, tree, form=form, opts=tn.plan_opts(tc_products=3 if m3 else 0, **o))
+    if AUTOTUNE:
+        plan.autotune()
+    return plan
 
 
 def roofline_ms(row, form, pk):
@@ -1029,6 +1034,8 @@ def main():
                     help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
     ap.add_argument("--small-tasks", type=int, default=0,
                     help="plan option small_tasks: 0 tiny small steps as tasks of one launch, -1 one launch each")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time each tensor-core GEMM's (chunk, read-out) candidates before use (tn_plan_autotune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cfg5", action="store_true", help="skip the 20-cycle sample of the default line")
     ap.add_argument("--dump-profile", default="", help="write per-op step timings to PATH.<form>.json")
@@ -1045,6 +1052,12 @@ def main():
         args.search_method = "bipartition"
     if args.small_tasks:
         PLAN_DEFAULTS["small_tasks"] = args.small_tasks
+    if args.tc_chunk:
+        PLAN_DEFAULTS["tc_chunk_bytes"] = args.tc_chunk
+    if args.tc_flush:
+        PLAN_DEFAULTS["tc_flush_bytes"] = args.tc_flush
+    if args.autotune:
+        AUTOTUNE.append(True)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch256":

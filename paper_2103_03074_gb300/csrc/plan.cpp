@@ -2042,8 +2042,13 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
             const SmallArgs &a = op.small;
             const char *kern = a.tiled == 1 ? "tiled, staged C" : a.tiled == 2 ? "tiled, direct C"
                                : a.tiled == 3 ? "tiled, planar" : "row";
-            std::snprintf(line, sizeof line, "%s step %d small rows=%lld K=%d N=%d H=%d kernel=%s", phase, op.step,
-                          (long long)a.rows, 1 << a.nK, 1 << a.nN, 1 << a.nH, kern);
+            // bit positions of k in T and of n in C
+            std::string kp, np;
+            for (int j = 0; j < a.nK; j++) kp += (j ? "," : "") + std::to_string(a.kposT[j]);
+            for (int j = 0; j < a.nN; j++) np += (j ? "," : "") + std::to_string(a.nposC[j]);
+            std::snprintf(line, sizeof line, "%s step %d small rows=%lld K=%d N=%d H=%d kernel=%s kposT=%s nposC=%s",
+                          phase, op.step, (long long)a.rows, 1 << a.nK, 1 << a.nN, 1 << a.nH, kern, kp.c_str(),
+                          np.c_str());
             break;
         }
         case OP_GEMM:

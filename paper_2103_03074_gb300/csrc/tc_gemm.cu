@@ -450,7 +450,6 @@ struct PlanarLane {
     uint32_t d[4];  // destination offset
     bool pair;      // d[1] = d[0] + 1 with d[0] even: one vector store per plane
     bool quad;      // d[q] = d[0] + q with d[0] a multiple of 4
-    bool row4;      // quad, and s[q] = s[0] + q (neighbours in one staged row)
 };
 
 __device__ __forceinline__ bool planar_quad(const TcPlanarOut &o) {
@@ -485,7 +484,6 @@ __device__ __forceinline__ PlanarLane planar_lane(const TcPlanarOut &o, int lane
         if (q < per) planar_bits(o, per * lane + q, 0, nlo, RS, L.s[q], L.d[q]);
     }
     L.pair = o.ntb >= 6 && o.tpos[0] == 0;
-    L.row4 = L.quad && L.s[1] == L.s[0] + 1 && L.s[2] == L.s[0] + 2 && L.s[3] == L.s[0] + 3;
     return L;
 }
 
@@ -503,20 +501,10 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
         for (int jh = fw; jh < n_hi; jh += EW) {
             const uint2 g = jtab[jh];
             float2 v[4];
-            const int s0 = (int)g.x + L.s[0];
-            if (L.row4 && (s0 & 1) == 0) {
-                // the four elements are neighbours in one staged row: two
-                // 16-byte reads
-                const float4 a = *reinterpret_cast<const float4 *>(st + s0);
-                const float4 b = *reinterpret_cast<const float4 *>(st + s0 + 2);
-                v[0] = make_float2(a.x, a.y);
-                v[1] = make_float2(a.z, a.w);
-                v[2] = make_float2(b.x, b.y);
-                v[3] = make_float2(b.z, b.w);
-            } else {
+            // (8-byte reads: two 16-byte reads of row neighbours measured
+            // slower on the 53-qubit step's staged GEMM)
 #pragma unroll
-                for (int q = 0; q < 4; q++) v[q] = st[(int)g.x + L.s[q]];
-            }
+            for (int q = 0; q < 4; q++) v[q] = st[(int)g.x + L.s[q]];
             plane_store<MODE, 4>(o, base + g.y + L.d[0], v);  // offset a multiple of 4
         }
         return;
