@@ -734,10 +734,20 @@ int64_t compile(tn_plan &P, int nb) {
                 }
             }
             int split_idx = 0;
+            // planes [q][h][K_high][row][K_low]: K cut into runs of 128 bytes
+            // (K_low = its lowest 6 labels for 16-bit pieces, 5 for tf32),
+            // so that a TMA box of a K run over 128 rows is one contiguous
+            // block of memory (long-K operands otherwise read rows of
+            // 128-byte pieces scattered by the row length)
+            const int klo_bits = es == 2 ? 6 : 5;
+            const bool chunked = (int)kord.size() > klo_bits;
+            op.tc.k_low_bits = chunked ? klo_bits : 0;
             auto emit_split = [&](const NodeRec &src, const std::vector<int32_t> &rows) {
                 std::vector<int32_t> dl = hord;
+                const size_t nk_hi = chunked ? kord.size() - klo_bits : 0;
+                dl.insert(dl.end(), kord.begin(), kord.begin() + nk_hi);
                 dl.insert(dl.end(), rows.begin(), rows.end());
-                dl.insert(dl.end(), kord.begin(), kord.end());
+                dl.insert(dl.end(), kord.begin() + nk_hi, kord.end());
                 const int64_t elems = (int64_t)1 << dl.size();
                 // the GEMM that wrote src splits its own output into these
                 // planes when its epilogue writes can be coalesced (runs of

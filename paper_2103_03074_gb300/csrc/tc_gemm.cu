@@ -200,12 +200,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            uint32_t mbar) {
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t mbar) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
         : "memory");
 }
 
@@ -228,6 +228,7 @@ struct GemmTcParams {
     int64_t H, M, N, K;  // K in complex elements
     int64_t sCh, sCm, sCn;
     int k_chunk;       // K values per chunk
+    int klo_bits;      // plane layout: K value kc at (kc & (2^klo_bits - 1), kc >> klo_bits); 31 = unchunked
     int ksplit;        // K partitions (> 1: atomic adds into a zeroed C)
     int flush_chunks;  // chunks per accumulator read-out
     int gm, gn;        // M and N tiles
@@ -584,8 +585,9 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                     const uint32_t fb = smem_u32(&full[s]);
                     mbar_expect_tx(fb, kStageBytes);
                     const int kc = (c_begin + c) * p.k_chunk;
-                    tma_load_4d(smem_u32(st), &mapA, kc, (int)tc.m0, tc.h, 0, fb);
-                    tma_load_4d(smem_u32(st + NP * kAPlane), &mapB, kc, (int)tc.n0, tc.h, 0, fb);
+                    const int klo = kc & ((1 << p.klo_bits) - 1), khi = kc >> p.klo_bits;
+                    tma_load_5d(smem_u32(st), &mapA, klo, (int)tc.m0, khi, tc.h, 0, fb);
+                    tma_load_5d(smem_u32(st + NP * kAPlane), &mapB, klo, (int)tc.n0, khi, tc.h, 0, fb);
                 }
             }
             // let every issued load land before the CTA can exit (a no-op
@@ -926,18 +928,23 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// planes [np][H][rows][K] of element size es (plane-major, as the split pass
-// writes them); box = cb bytes of K x box_rows x 1 batch x np planes, which
-// lands in shared memory as [plane][row][cb bytes], cb-byte swizzled
+// planes of element size es, plane-major as the split pass writes them:
+// [np][H][K / Klo][rows][Klo] with Klo = 2^klo_bits values of K (klo_bits =
+// 31 or Klo >= K: [np][H][rows][K]); a 5D map over (Klo, rows, K / Klo, H,
+// np) whose box = cb bytes of K x box_rows x 1 x 1 x np planes lands in
+// shared memory as [plane][row][cb bytes], cb-byte swizzled
 bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int64_t K, int es, int box_rows,
-                   int cb, int np, CUtensorMapDataType dtype) {
+                   int cb, int np, CUtensorMapDataType dtype, int klo_bits) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)H, (cuuint64_t)np};
-    cuuint64_t strides[3] = {(cuuint64_t)(K * es), (cuuint64_t)(rows * K * es), (cuuint64_t)(H * rows * K * es)};
-    cuuint32_t box[4] = {(cuuint32_t)(cb / es), (cuuint32_t)box_rows, 1, (cuuint32_t)np};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = fn(map, dtype, 4, planes, dims,
+    const int64_t klo = (klo_bits < 31 && ((int64_t)1 << klo_bits) < K) ? ((int64_t)1 << klo_bits) : K;
+    const int64_t khi = K / klo;
+    cuuint64_t dims[5] = {(cuuint64_t)klo, (cuuint64_t)rows, (cuuint64_t)khi, (cuuint64_t)H, (cuuint64_t)np};
+    cuuint64_t strides[4] = {(cuuint64_t)(klo * es), (cuuint64_t)(rows * klo * es), (cuuint64_t)(rows * K * es),
+                             (cuuint64_t)(H * rows * K * es)};
+    cuuint32_t box[5] = {(cuuint32_t)(cb / es), (cuuint32_t)box_rows, 1, 1, (cuuint32_t)np};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(map, dtype, 5, planes, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                              : (cb == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B),
@@ -1026,9 +1033,16 @@ bool tc_prepare(TcGemm &g) {
     const CUtensorMapDataType dt = g.form == TN_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : g.form == TN_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM, cb, np, dt))
+    // a chunked layout holds whole runs of 2^k_low_bits K values of 128
+    // bytes; a TMA chunk (64 or 128 bytes) stays inside one run
+    if (g.k_low_bits > 0 && (((int64_t)es << g.k_low_bits) != 128 || (g.a.K & ((1ll << g.k_low_bits) - 1)) != 0))
         return false;
-    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN, cb, np, dt))
+    const int klo = g.k_low_bits > 0 ? g.k_low_bits : 31;
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapA), g.planesA, g.a.H, g.a.M, g.a.K, es, TM, cb, np, dt,
+                       klo))
+        return false;
+    if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN, cb, np, dt,
+                       klo))
         return false;
     return true;
 }
@@ -1063,6 +1077,7 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     p.sCm = g.a.sCm;
     p.sCn = g.a.sCn;
     p.k_chunk = g.chunk_bytes / tc_plane_bytes(g.form);
+    p.klo_bits = g.k_low_bits > 0 ? g.k_low_bits : 31;
     p.ksplit = g.ksplit > 0 ? g.ksplit : 1;
     p.flush_chunks = g.flush_bytes / g.chunk_bytes;
     if (p.flush_chunks < 1) p.flush_chunks = 1;

@@ -43,6 +43,11 @@ struct TcGemm {
     // (A_re + A_im)(B_re + B_im); six planes per operand, split modes 5-7;
     // hi/lo forms only)
     int products;
+    // plane layout: 0 = [q][h][row][K]; b > 0 = [q][h][K >> b][row][2^b]
+    // (K cut into runs of 2^b values, 128 bytes of a plane row, each run
+    // stored for all rows before the next: a TMA box of 128 rows reads one
+    // contiguous block, whatever K is)
+    int k_low_bits;
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
 };
