@@ -752,6 +752,9 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
             for (int gi = 0; gi < n_groups; gi++, gc++) {
                 const int t = gc & 1, tuse = gc >> 1;
                 if (ok && !mbar_wait(smem_u32(&tfull[t]), tuse & 1)) ok = false;
+                // one outcome per warp: the tensor-memory loads below are
+                // warp-collective (.sync.aligned)
+                ok = __all_sync(0xffffffffu, ok);
                 if (!ok) continue;
                 fence_after();
                 const uint32_t base = tmem + t * 256 + lane_off + cq * kCW;
