@@ -58,11 +58,11 @@ METRIC = "slices/s & complex TFLOP/s per GB300 at <=1e-5 amp err, split-TC vs pl
 DEFAULT_WORKLOAD = "syc53_m14"
 
 # DRAM traffic per tensor-core GEMM launch of the default step, by form, from
-# the one-pass ncu capture summarised in
-# profiles/dram_traffic_syc53_m14_fp16x3.md (dram__bytes_read.sum +
-# dram__bytes_write.sum averaged over the step's 9 GEMM launches, 10 steps);
-# a form is absent until such a capture exists for the current kernel
-GEMM_TRAFFIC_PER_LAUNCH = {}
+# the one-pass ncu capture summarised in profiles/launches_syc53_m14_fp16x3.md
+# (dram__bytes_read.sum + dram__bytes_write.sum averaged over the step's 6
+# GEMM launches, 10 executions of the step); a form is absent until such a
+# capture exists for the current kernel and tree
+GEMM_TRAFFIC_PER_LAUNCH = {"fp16x3": 7.576e9}
 
 
 def peaks():
@@ -1034,6 +1034,8 @@ def main():
                     help="rewrite ((X a) b) into (X (a b)) where the step-time estimate drops (tn_merge_branches)")
     ap.add_argument("--small-tasks", type=int, default=0,
                     help="plan option small_tasks: 0 tiny small steps as tasks of one launch, -1 one launch each")
+    ap.add_argument("--small-tc-bits", type=int, default=0,
+                    help="plan option small_tc_bits: small steps with K + N of at least this many bits on the tensor cores")
     ap.add_argument("--autotune", action="store_true",
                     help="time each tensor-core GEMM's (chunk, read-out) candidates before use (tn_plan_autotune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1052,6 +1054,8 @@ def main():
         args.search_method = "bipartition"
     if args.small_tasks:
         PLAN_DEFAULTS["small_tasks"] = args.small_tasks
+    if args.small_tc_bits:
+        PLAN_DEFAULTS["small_tc_bits"] = args.small_tc_bits
     if args.tc_chunk:
         PLAN_DEFAULTS["tc_chunk_bytes"] = args.tc_chunk
     if args.tc_flush:
