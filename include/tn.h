@@ -115,6 +115,12 @@ typedef struct {
      * orders them by device-side completion counters (bounded waits) instead
      * of one kernel launch each; -1: off */
     int32_t small_tasks;
+    /* split forms (TF32X3, FP16X3, BF16X3): 0 (default) runs a large small
+     * step (K and N of 16 or 32 values, at least 2^16 rows, no batch labels,
+     * its rows' 7 lowest bits lowest in T and C) on the tensor cores, T split
+     * into pieces in shared memory (each 128-row tile of T scaled by its own
+     * power of two in FP16X3) with the form's products; -1: CUDA cores */
+    int32_t small_tc;
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

@@ -53,6 +53,16 @@ __device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
     acc.y = fmaf(a.y, b.x, acc.y);
 }
 
+// One atomic max per warp of the per-thread maxima mx (non-negative floats
+// order like their bit patterns); every lane of the warp calls it.
+__device__ __forceinline__ void publish_max(unsigned *slot, float mx) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, __float_as_uint(mx));
+}
+
+__device__ __forceinline__ float absmax2(float m, float2 v) { return fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))); }
+
 int grid_for(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
     if (b < 1) b = 1;
@@ -90,6 +100,7 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
     const int chunk_bits = a.nN > kNcBits ? a.nN - kNcBits : 0;
     const int rbits = a.row_bits;
     const int64_t items = a.rows << chunk_bits;
+    float mx = 0.f;  // of the values stored (max_slot)
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < items; w += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = w & (a.rows - 1);
         const int n0 = (int)(w >> rbits) * NC;
@@ -129,8 +140,12 @@ __global__ void __launch_bounds__(kThreads) small_kernel(const SmallArgs a) {
         }
 #pragma unroll
         for (int j = 0; j < NC; j++)
-            if (j < nc) a.C[cb + offC[n0 + j]] = acc[j];
+            if (j < nc) {
+                a.C[cb + offC[n0 + j]] = acc[j];
+                mx = absmax2(mx, acc[j]);
+            }
     }
+    if (a.max_slot) publish_max(a.max_slot, mx);
 }
 
 // ------------------------------------ small steps as tasks of one launch
@@ -303,6 +318,7 @@ __global__ void __launch_bounds__(kThreads) small_ksplit_kernel(const SmallArgs 
     const int rbits = a.row_bits;
     const int64_t items = a.rows << chunk_bits;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float mx = 0.f;  // of the values stored (max_slot)
     for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < items; w += warps) {
         const int64_t r = w & (a.rows - 1);
         const int n0 = (int)(w >> rbits) * NC;
@@ -330,8 +346,12 @@ __global__ void __launch_bounds__(kThreads) small_ksplit_kernel(const SmallArgs 
             }
             if (lane == j) mine = acc[j];
         }
-        if (lane < nc) a.C[cb + offC[n0 + lane]] = mine;
+        if (lane < nc) {
+            a.C[cb + offC[n0 + lane]] = mine;
+            mx = absmax2(mx, mine);
+        }
     }
+    if (a.max_slot) publish_max(a.max_slot, mx);
 }
 
 // ------------------------------------------------------ small step, tiled
@@ -435,6 +455,7 @@ __global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArg
         }
     };
     int stage = 0;
+    float mx = 0.f;  // of the values computed (max_slot; complex64 stores only)
     if ((int64_t)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
     cp_async_commit();
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -468,6 +489,12 @@ __global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArg
             for (int i = 0; i < RPT; i++)
 #pragma unroll
                 for (int j = 0; j < NPT; j++) cfma(acc[i][j], tv[i], sv[j]);
+        }
+        if (STORE != 2 && a.max_slot) {
+#pragma unroll
+            for (int i = 0; i < RPT; i++)
+#pragma unroll
+                for (int j = 0; j < NPT; j++) mx = absmax2(mx, acc[i][j]);
         }
         if (DIRECT) {
             __syncthreads();  // every thread's reads of this stage are done
@@ -518,6 +545,7 @@ __global__ void __launch_bounds__(kThreads, 3) small_tiled_kernel(const SmallArg
         // first barrier, after every thread's reads of C_s
     }
     cp_async_wait_all();
+    if (STORE != 2 && a.max_slot) publish_max(a.max_slot, mx);
 }
 
 // ------------------------------------------------------- tiled bit permute
@@ -1152,6 +1180,12 @@ int prepare_small_planar(SmallArgs &a, const int *cdest, int mode, int64_t plane
 }
 
 cudaError_t launch_small(const SmallArgs &args, cudaStream_t s) {
+    if (args.max_slot) {
+        if (args.tiled == 3) return cudaErrorInvalidValue;  // planes out: no complex64 max
+        cudaError_t e = cudaMemsetAsync(args.max_slot, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(args.max_slot + 2, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
     if (args.tiled) {
         switch (args.nK) {
         case 2: return launch_small_tiled_k<2>(args, s);

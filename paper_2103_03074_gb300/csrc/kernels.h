@@ -62,6 +62,15 @@ struct SmallArgs {
     int planar_mode;
     int64_t plane_stride;
     int8_t drow[kMaxRank];
+    // optional (complex64 C only): receives max |re|, |im| of C (float bits,
+    // atomic max; the launcher zeroes it and the slot two places on, which a
+    // consumer reads as "no separate true max"), so that the scaled split of
+    // C needs no max-abs pass of its own
+    unsigned *max_slot;
+    // tensor-core form (tn_form of a split form) when the step runs on the
+    // tensor cores with T split in shared memory (launch_small_tc); 0: CUDA
+    // cores
+    int tc_form;
 };
 
 // Decide whether a small step takes the tiled kernel and fill its tables

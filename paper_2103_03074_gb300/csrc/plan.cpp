@@ -333,7 +333,7 @@ void group_tasks(std::vector<Op> &ops, int bits) {
     auto eligible = [&](const Op &op) {
         // (a step set up for the tiled kernel keeps its one-thread-per-row
         // fields; one that stores the next step's planes does not qualify)
-        if (op.kind != OP_SMALL || op.small.tiled == 3 || op.small.nK > kTaskMaxK) return false;
+        if (op.kind != OP_SMALL || op.small.tiled == 3 || op.small.nK > kTaskMaxK || op.maxout.buf >= 0) return false;
         const double elems = (double)op.small.rows * std::exp2((double)std::max(op.small.nK, op.small.nN));
         return elems <= std::exp2((double)bits);
     };
@@ -562,6 +562,7 @@ int64_t compile(tn_plan &P, int nb) {
                 s.hposS[j] = pos_of(S.lay, H[j]);
             }
             if (P.opts.small_tiled >= 0) prepare_small_tiled(s);
+            if (P.opts.small_tc >= 0 && small_tc_suitable(s, P.form)) s.tc_form = (int)P.form;
             op.in0 = T.where;  // T
             op.in1 = S.where;  // S
             nc.where.buf = new_buf((int64_t)1 << nc.lay.size());
@@ -720,6 +721,13 @@ int64_t compile(tn_plan &P, int nb) {
                         prod->maxout_idx = idx++;
                         continue;
                     }
+                    // likewise a small step (it keeps a running max of the
+                    // values it stores)
+                    if (prod && prod->kind == OP_SMALL && prod->small.tiled != 3 && prod->maxout.buf < 0) {
+                        prod->maxout = slots;
+                        prod->maxout_idx = idx++;
+                        continue;
+                    }
                     Op mo;
                     mo.kind = OP_MAXABS;
                     mo.step = t;
@@ -758,7 +766,7 @@ int64_t compile(tn_plan &P, int nb) {
                 // planes in destination runs
                 if (P.opts.tc_planar >= 0 && !scaled && (mode == 1 || mode == 2) && src.lay.size() == dl.size()) {
                     Op *prod = producer_of(ops, src.where);
-                    if (prod && prod->kind == OP_SMALL && prod->small.tiled) {
+                    if (prod && prod->kind == OP_SMALL && prod->small.tiled && !prod->small.tc_form) {
                         const int r = (int)dl.size();
                         std::vector<int> cdest(r, -1);
                         for (int q = 0; q < r; q++) {
@@ -994,6 +1002,9 @@ void resolve_all(tn_plan &P) {
             op.small.T = resolve(P, op.in0);
             op.small.S = resolve(P, op.in1);
             op.small.C = resolve(P, op.out);
+            op.small.max_slot = op.maxout.buf >= 0
+                                    ? reinterpret_cast<unsigned *>(resolve(P, op.maxout)) + op.maxout_idx
+                                    : nullptr;
             break;
         case OP_PERMUTE:
         case OP_SPLIT:
@@ -1043,7 +1054,13 @@ void resolve_all(tn_plan &P) {
 
 cudaError_t run_op(const tn_plan &P, const Op &op, cudaStream_t s) {
     switch (op.kind) {
-    case OP_SMALL: return launch_small(op.small, s);
+    case OP_SMALL:
+        if (op.small.tc_form) {
+            // T not 16-byte aligned (a leaf at an odd offset): the CUDA-core kernel
+            const cudaError_t e = launch_small_tc(op.small, (tn_form)op.small.tc_form, s);
+            if (e != cudaErrorMisalignedAddress) return e;
+        }
+        return launch_small(op.small, s);
     case OP_PERMUTE: return launch_bitperm(op.bp, s);
     case OP_GEMM:
         if (op.gemm_variant == 1) return launch_gemm_tc(op.tc, s);
@@ -1099,7 +1116,10 @@ double roofline_ms(const Op &op, tn_form form) {
         const double t = std::max(op.bytes / hbm, 8.0 * op.macs / fp32) * 1e3;
         return t + floor_ms + kTaskLevelMs * (op.task_levels - 1);
     }
-    if (op.kind == OP_SMALL || (op.kind == OP_GEMM && op.gemm_variant != 1)) {
+    if (op.kind == OP_SMALL && op.small.tc_form) {
+        flops = 24.0 * op.macs;
+        peak = form == TN_TF32X3 ? 1.125e15 : 2.25e15;
+    } else if (op.kind == OP_SMALL || (op.kind == OP_GEMM && op.gemm_variant != 1)) {
         flops = 8.0 * op.macs;
     } else if (op.kind == OP_GEMM) {
         flops = (form == TN_FP16S ? 8.0 : 24.0) * op.macs;
@@ -2050,7 +2070,8 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
         }
         case OP_SMALL: {
             const SmallArgs &a = op.small;
-            const char *kern = a.tiled == 1 ? "tiled, staged C" : a.tiled == 2 ? "tiled, direct C"
+            const char *kern = a.tc_form ? "tensor cores, split in shared memory"
+                               : a.tiled == 1 ? "tiled, staged C" : a.tiled == 2 ? "tiled, direct C"
                                : a.tiled == 3 ? "tiled, planar" : "row";
             // bit positions of k in T and of n in C
             std::string kp, np;

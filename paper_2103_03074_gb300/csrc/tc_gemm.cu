@@ -51,6 +51,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -218,6 +219,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -912,6 +919,331 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
     }
 }
 
+// ------------------------------------------- small step on the tensor cores
+// A small step C[r, n] = sum_k T[r, k] S[k, n] (S of K x N values, K and N of
+// 16 or 32; T and C with their rows' 7 lowest bits at their 7 lowest
+// positions, so every (k, 128-row tile) of T and (n, tile) of C is 1 KB of
+// consecutive memory) with the split of T into pieces done in shared memory:
+// no split pass over T, and the complex multiply-adds on the tensor cores
+// instead of the CUDA cores' FP32 pipe.  One CTA of 256 threads walks
+// 128-row tiles: cp.async brings the next tile's T while the current one is
+// split (per tile: FP16X3 scales the tile by 2^-e_t, e_t from its own
+// largest |re|, |im|, which is exact because every row of C depends on its
+// own row of T only), multiplied (P = A_re [S_re | S_im], Q = A_im [S_re |
+// S_im], three piece products each, one elected thread) and read back from
+// tensor memory into C.  S is split once per CTA (FP16X3: scaled by its own
+// max).  Pieces, products and the FP32 read-out are those of the GEMM, so
+// the step has the GEMM's accuracy.
+struct SmallTcParams {
+    const float2 *T;
+    const float2 *S;
+    float2 *C;
+    int64_t tiles;  // rows / 128
+    int nK, nN;
+    int n_tins, n_cins;
+    int tins[kSmallMaxBits], cins[kSmallMaxBits];
+    uint64_t offT[32];  // T offset of k
+    uint64_t offC[32];  // C offset of n
+    uint32_t offS[32 * 32];  // S offset of (k, n): k * N + n
+    unsigned *max_slot;  // optional: max |re|, |im| of C (float bits)
+};
+
+constexpr int kSmallTcThreads = 256;
+
+__device__ __forceinline__ uint64_t small_tc_insert(uint64_t x, const int *pos, int n) {
+    for (int i = 0; i < n; i++) {
+        const int q = pos[i];
+        x = ((x >> q) << (q + 1)) | (x & ((1ull << q) - 1));
+    }
+    return x;
+}
+
+// byte offset of (row, 16-byte chunk c) in a K-major operand of CB-byte rows
+// with the CB-byte swizzle (the layout TMA writes and the MMA descriptors of
+// make_desc<CB> read): address bits 4.. XOR address bits 7..
+template <int CB>
+__device__ __forceinline__ uint32_t swz_off(int row, int c) {
+    const uint32_t lin = (uint32_t)row * CB + (uint32_t)c * 16;
+    constexpr uint32_t kMask = CB == 128 ? 7u : (CB == 64 ? 3u : 1u);
+    return lin ^ (((lin >> 7) & kMask) << 4);
+}
+
+// pieces of 8 consecutive K values x[0..7] of one row into the hi and lo
+// words of one 16-byte chunk (16-bit pieces: 8 values; tf32: 4 values use
+// words 0..3 of hi/lo, the caller passes them in two halves)
+template <int KIND>
+__device__ __forceinline__ void small_tc_pieces(const float *x, uint32_t *hi, uint32_t *lo) {
+    if constexpr (KIND == kTF32) {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            hi[e] = tf32_rna(x[e]);
+            lo[e] = tf32_rna(x[e] - __uint_as_float(hi[e]));
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if constexpr (KIND == kBF16) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(x[2 * e] - hf.x, x[2 * e + 1] - hf.y);
+                hi[e] = *reinterpret_cast<const uint32_t *>(&h);
+                lo[e] = *reinterpret_cast<const uint32_t *>(&l);
+            } else {
+                const __half2 h = __floats2half2_rn(x[2 * e], x[2 * e + 1]);
+                const float2 hf = __half22float2(h);
+                const __half2 l = __floats2half2_rn(x[2 * e] - hf.x, x[2 * e + 1] - hf.y);
+                hi[e] = *reinterpret_cast<const uint32_t *>(&h);
+                lo[e] = *reinterpret_cast<const uint32_t *>(&l);
+            }
+        }
+    }
+}
+
+// Shared memory of the small-step kernel (CB = K bytes of a plane row,
+// NK K values): T staging, two tiles of [k][128 rows] complex64; A planes
+// (re_hi, im_hi, re_lo, im_lo) of 128 rows; B planes (hi, lo) of 2N rows
+// ([S_re | S_im] transposed); tile scalars; barrier and tensor-memory slot.
+template <int CB, int NK>
+struct SmallTcSmem {
+    static constexpr int kStage = NK * 128 * 8;
+    static constexpr int kAPlane = 128 * CB;
+    static constexpr int kBPlane = 64 * CB;  // up to 2N = 64 rows
+    static constexpr int kA = 2 * kStage;                  // offsets (1024-aligned)
+    static constexpr int kB = kA + 4 * kAPlane;
+    static constexpr int kMisc = kB + 2 * kBPlane;
+    static constexpr int kBytes = kMisc + 256 + 1024;      // + alignment slack
+};
+
+template <int KIND, int CB>
+__global__ void __launch_bounds__(kSmallTcThreads, 2) small_tc_kernel(const SmallTcParams p) {
+    constexpr int ES = KIND == kTF32 ? 4 : 2;  // piece bytes
+    constexpr int NK = CB / ES;                 // K values (16 or 32)
+    using L = SmallTcSmem<CB, NK>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float2 *stg = reinterpret_cast<float2 *>(smem);
+    unsigned char *Ap = smem + L::kA, *Bp = smem + L::kB;
+    float *red = reinterpret_cast<float *>(smem + L::kMisc);        // 8 warp maxima
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::kMisc + 64);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc + 128);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NS = 1 << p.nN;
+    constexpr uint32_t kCols = 128;  // P: 2N columns, Q: 2N columns (N <= 32)
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // S: largest |re|, |im| (FP16X3 scale), then its planes: B row n' < N is
+    // S_re[., n'], row N + n' is S_im[., n'], K-major
+    float smax = 0.f;
+    for (int i = tid; i < NK * NS; i += kSmallTcThreads) {
+        const float2 v = p.S[p.offS[i]];
+        smax = fmaxf(smax, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+    if (lane == 0) red[warp] = smax;
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    smax = 0.f;
+#pragma unroll
+    for (int w = 0; w < kSmallTcThreads / 32; w++) smax = fmaxf(smax, red[w]);
+    const int eS = KIND == kFP16X3 ? fp16s_exponent(smax) : 0;
+    for (int task = tid; task < 2 * NS * (NK / 8); task += kSmallTcThreads) {
+        // one 16-byte chunk of 8 K values (4 for tf32: two chunks per 8) of B row
+        const int row = task / (NK / 8), c8 = task % (NK / 8);
+        const int n = row % NS;
+        const bool im = row >= NS;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const float2 v = p.S[p.offS[(c8 * 8 + e) * NS + n]];
+            const float y = im ? v.y : v.x;
+            x[e] = KIND == kFP16X3 ? y * __int_as_float((127 - eS) << 23) : y;
+        }
+        uint32_t hi[8], lo[8];
+        small_tc_pieces<KIND>(x, hi, lo);
+        if constexpr (KIND == kTF32) {
+            small_tc_pieces<KIND>(x + 4, hi + 4, lo + 4);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t o = swz_off<CB>(row, 2 * c8 + h);
+                *reinterpret_cast<uint4 *>(Bp + o) = make_uint4(hi[4 * h], hi[4 * h + 1], hi[4 * h + 2], hi[4 * h + 3]);
+                *reinterpret_cast<uint4 *>(Bp + L::kBPlane + o) =
+                    make_uint4(lo[4 * h], lo[4 * h + 1], lo[4 * h + 2], lo[4 * h + 3]);
+            }
+        } else {
+            const uint32_t o = swz_off<CB>(row, c8);
+            *reinterpret_cast<uint4 *>(Bp + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(Bp + L::kBPlane + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+    // T tile `tile` into stage `st`: element (k, i) at stg[st][k * 128 + i]
+    auto issue = [&](int64_t tile, int st) {
+        const uint64_t base = small_tc_insert((uint64_t)tile << 7, p.tins, p.n_tins);
+        const uint32_t dst0 = smem_u32(stg + st * (NK * 128));
+        for (int c = tid; c < NK * 64; c += kSmallTcThreads) {  // 16-byte pieces: 2 rows
+            const int k = c >> 6, i2 = (c & 63) * 2;
+            const float2 *src = p.T + base + p.offT[k] + i2;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + (uint32_t)(k * 128 + i2) * 8),
+                         "l"(src)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const uint32_t idesc = make_idesc(KIND == kTF32 ? 2u : (KIND == kBF16 ? 1u : 0u), 128, 2 * NS, false);
+    const int row = tid & 127, half = tid >> 7;  // conversion: one row, half of its K values
+    const int lg = warp & 3, ch = warp >> 2;     // read-out: TMEM lane group, half of the N columns
+    float cmax = 0.f;
+    bool ok = true;
+    int st = 0;
+    uint32_t phase = 0;
+    if ((int64_t)blockIdx.x < p.tiles) issue(blockIdx.x, 0);
+    for (int64_t tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
+        const int64_t next = tile + gridDim.x;
+        if (next < p.tiles) {
+            issue(next, st ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float2 *T_s = stg + st * (NK * 128);
+        // per-tile scale (FP16X3): largest |re|, |im| of the tile
+        float x_re[NK / 2], x_im[NK / 2];
+        float tmax = 0.f;
+#pragma unroll
+        for (int e = 0; e < NK / 2; e++) {
+            const float2 v = T_s[(half * (NK / 2) + e) * 128 + row];
+            x_re[e] = v.x;
+            x_im[e] = v.y;
+            tmax = fmaxf(tmax, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        int eT = 0;
+        if constexpr (KIND == kFP16X3) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+            if (lane == 0) red[warp] = tmax;
+            __syncthreads();
+            tmax = 0.f;
+#pragma unroll
+            for (int w = 0; w < kSmallTcThreads / 32; w++) tmax = fmaxf(tmax, red[w]);
+            eT = fp16s_exponent(tmax);
+            const float sc = __int_as_float((127 - eT) << 23);
+#pragma unroll
+            for (int e = 0; e < NK / 2; e++) {
+                x_re[e] *= sc;
+                x_im[e] *= sc;
+            }
+        }
+        // A planes: this thread's row, K values [half * NK / 2, + NK / 2)
+#pragma unroll
+        for (int c8 = 0; c8 < NK / 16; c8++) {
+#pragma unroll
+            for (int comp = 0; comp < 2; comp++) {
+                const float *x = (comp ? x_im : x_re) + c8 * 8;
+                uint32_t hi[8], lo[8];
+                small_tc_pieces<KIND>(x, hi, lo);
+                unsigned char *Ph = Ap + comp * L::kAPlane, *Pl = Ap + (2 + comp) * L::kAPlane;
+                if constexpr (KIND == kTF32) {
+                    small_tc_pieces<KIND>(x + 4, hi + 4, lo + 4);
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const uint32_t o = swz_off<CB>(row, half * (NK / 8) + 2 * c8 + h);
+                        *reinterpret_cast<uint4 *>(Ph + o) =
+                            make_uint4(hi[4 * h], hi[4 * h + 1], hi[4 * h + 2], hi[4 * h + 3]);
+                        *reinterpret_cast<uint4 *>(Pl + o) =
+                            make_uint4(lo[4 * h], lo[4 * h + 1], lo[4 * h + 2], lo[4 * h + 3]);
+                    }
+                } else {
+                    const uint32_t o = swz_off<CB>(row, half * (NK / 16) + c8);
+                    *reinterpret_cast<uint4 *>(Ph + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(Pl + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+        }
+        // generic-proxy shared-memory writes, then the tensor core reads them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const uint32_t a0 = smem_u32(Ap), b0 = smem_u32(Bp);
+            const uint32_t dP = tmem, dQ = tmem + 2 * NS;
+#pragma unroll
+            for (int ks = 0; ks < CB / 32; ks++) {
+                const uint32_t ko = ks * 32;
+                const uint64_t ar = make_desc<CB>(a0 + ko), ai = make_desc<CB>(a0 + L::kAPlane + ko);
+                const uint64_t arl = make_desc<CB>(a0 + 2 * L::kAPlane + ko);
+                const uint64_t ail = make_desc<CB>(a0 + 3 * L::kAPlane + ko);
+                const uint64_t S = make_desc<CB>(b0 + ko), Sl = make_desc<CB>(b0 + L::kBPlane + ko);
+                const uint32_t acc = ks == 0 ? 0u : 1u;
+                mma<KIND>(dP, ar, S, idesc, acc);
+                mma<KIND>(dQ, ai, S, idesc, acc);
+                mma<KIND>(dP, ar, Sl, idesc, 1u);
+                mma<KIND>(dP, arl, S, idesc, 1u);
+                mma<KIND>(dQ, ai, Sl, idesc, 1u);
+                mma<KIND>(dQ, ail, S, idesc, 1u);
+            }
+            mma_commit(smem_u32(bar));
+        }
+        // every thread waits for the products (bounded); one outcome for the
+        // block: on expiry it stops after this tile (the products still in
+        // flight are drained before the tensor memory is freed)
+        if (!mbar_wait(smem_u32(bar), phase)) ok = false;
+        ok = __syncthreads_and(ok) != 0;
+        fence_after();
+        if (ok) {
+            phase ^= 1;
+            // this warp: rows 32 lg .., columns n in [ch * N / 2, + N / 2)
+            const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16);
+            const uint64_t cbase = small_tc_insert((uint64_t)tile << 7, p.cins, p.n_cins) + lg * 32 + lane;
+            const float sc = KIND == kFP16X3 ? __int_as_float((127 + eT + eS) << 23) : 1.f;
+            for (int n0 = ch * (NS / 2); n0 < (ch + 1) * (NS / 2); n0 += 8) {
+                uint32_t pr[8], pi[8], qr[8], qi[8];
+                tmem_ld8(base + n0, pr);           // P left:  A_re S_re
+                tmem_ld8(base + NS + n0, pi);      // P right: A_re S_im
+                tmem_ld8(base + 2 * NS + n0, qr);  // Q left:  A_im S_re
+                tmem_ld8(base + 3 * NS + n0, qi);  // Q right: A_im S_im
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const float re = (__uint_as_float(pr[j]) - __uint_as_float(qi[j])) * sc;
+                    const float im = (__uint_as_float(pi[j]) + __uint_as_float(qr[j])) * sc;
+                    p.C[cbase + p.offC[n0 + j]] = make_float2(re, im);
+                    cmax = fmaxf(cmax, fmaxf(fabsf(re), fabsf(im)));
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();  // tensor memory read and A planes free for the next tile
+        if (!ok) break;
+        st ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok && tid == 0) mbar_drain(smem_u32(bar), phase);
+    if (p.max_slot && ok) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
+        if (lane == 0) atomicMax(p.max_slot, __float_as_uint(cmax));
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+    }
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -1167,6 +1499,99 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
         return g.chunk_bytes == 64 ? launch_variant<kFP16X3, 64>(g, p, grid, s)
                                    : launch_variant<kFP16X3, 128>(g, p, grid, s);
     return g.chunk_bytes == 64 ? launch_variant<kFP16, 64>(g, p, grid, s) : launch_variant<kFP16, 128>(g, p, grid, s);
+}
+
+bool small_tc_suitable(const SmallArgs &a, tn_form form) {
+    // split forms with 22+ significant bits and bf16x3; K and N of 16 or 32;
+    // no batch bits; whole 128-row tiles whose T and C runs are 128 rows
+    if (form != TN_FP16X3 && form != TN_TF32X3 && form != TN_BF16X3) return false;
+    if (a.nH != 0 || a.nK < 4 || a.nK > 5 || a.nN < 4 || a.nN > 5 || a.tiled == 3) return false;
+    if (a.rows < (1 << 16) || (a.rows & (a.rows - 1)) != 0) return false;
+    for (int j = 0; j < a.nK; j++)
+        if (a.kposT[j] < 7) return false;
+    for (int j = 0; j < a.nN; j++)
+        if (a.nposC[j] < 7) return false;
+    return true;
+}
+
+template <int KIND, int CB>
+cudaError_t launch_small_tc_t(const SmallTcParams &p, cudaStream_t s) {
+    constexpr int ES = KIND == kTF32 ? 4 : 2;
+    using L = SmallTcSmem<CB, CB / ES>;
+    static_assert(L::kBytes <= 232448, "shared memory per CTA");
+    cudaError_t e = set_max_dynamic_smem((const void *)small_tc_kernel<KIND, CB>, L::kBytes);
+    if (e != cudaSuccess) return e;
+    static std::atomic<int> sm_count[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    int sms = sm_count[dev].load(std::memory_order_relaxed);
+    if (sms == 0) {
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        sm_count[dev].store(sms, std::memory_order_relaxed);
+    }
+    // two CTAs per SM where shared memory allows (one tile's split and
+    // products overlap the other's loads and stores)
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_tc_kernel<KIND, CB>, kSmallTcThreads,
+                                                      L::kBytes) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int grid = (int)std::min<int64_t>(p.tiles, (int64_t)sms * std::min(per_sm, 2));
+    small_tc_kernel<KIND, CB><<<grid, kSmallTcThreads, L::kBytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small_tc(const SmallArgs &a, tn_form form, cudaStream_t s) {
+    if (!small_tc_suitable(a, form)) return cudaErrorInvalidValue;
+    // 16-byte copies of T rows need a 16-byte aligned T
+    if ((reinterpret_cast<uintptr_t>(a.T) & 15) != 0) return cudaErrorMisalignedAddress;
+    SmallTcParams p;
+    std::memset(&p, 0, sizeof p);
+    p.T = a.T;
+    p.S = a.S;
+    p.C = a.C;
+    p.tiles = a.rows >> 7;
+    p.nK = a.nK;
+    p.nN = a.nN;
+    p.n_tins = a.n_tins;
+    p.n_cins = a.n_cins;
+    for (int j = 0; j < kSmallMaxBits; j++) {
+        p.tins[j] = a.tins[j];
+        p.cins[j] = a.cins[j];
+    }
+    const int KS = 1 << a.nK, NS = 1 << a.nN;
+    for (int k = 0; k < KS; k++) {
+        uint64_t o = 0, os = 0;
+        for (int j = 0; j < a.nK; j++)
+            if ((k >> j) & 1) {
+                o |= 1ull << a.kposT[j];
+                os |= 1ull << a.kposS[j];
+            }
+        p.offT[k] = o;
+        for (int n = 0; n < NS; n++) {
+            uint64_t on = os;
+            for (int j = 0; j < a.nN; j++)
+                if ((n >> j) & 1) on |= 1ull << a.nposS[j];
+            p.offS[k * NS + n] = (uint32_t)on;
+        }
+    }
+    for (int n = 0; n < NS; n++) {
+        uint64_t o = 0;
+        for (int j = 0; j < a.nN; j++)
+            if ((n >> j) & 1) o |= 1ull << a.nposC[j];
+        p.offC[n] = o;
+    }
+    p.max_slot = a.max_slot;
+    if (a.max_slot) {
+        cudaError_t e = cudaMemsetAsync(a.max_slot, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.max_slot + 2, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (form == TN_TF32X3) return a.nK == 4 ? launch_small_tc_t<kTF32, 64>(p, s) : launch_small_tc_t<kTF32, 128>(p, s);
+    if (form == TN_BF16X3) return a.nK == 4 ? launch_small_tc_t<kBF16, 32>(p, s) : launch_small_tc_t<kBF16, 64>(p, s);
+    return a.nK == 4 ? launch_small_tc_t<kFP16X3, 32>(p, s) : launch_small_tc_t<kFP16X3, 64>(p, s);
 }
 
 int tc_read_error(cudaStream_t s) {

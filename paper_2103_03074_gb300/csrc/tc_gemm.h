@@ -86,6 +86,14 @@ bool tc_gemm_suitable(const GemmArgs &a);
 // driver rejects them.
 bool tc_prepare(TcGemm &g);
 
+// A small step on the tensor cores, T split into pieces in shared memory (no
+// split pass): for the split forms with K and N of 16 or 32 values, no batch
+// bits, at least 2^16 rows, and the rows' 7 lowest bits at T's and C's 7
+// lowest positions.  launch_small_tc returns cudaErrorMisalignedAddress when
+// T is not 16-byte aligned (the caller then takes the CUDA-core kernel).
+bool small_tc_suitable(const SmallArgs &a, tn_form form);
+cudaError_t launch_small_tc(const SmallArgs &a, tn_form form, cudaStream_t s);
+
 // K partitions for a GEMM whose tile grid alone would leave SMs idle.
 int tc_choose_ksplit(const GemmArgs &a, tn_form form);
 

@@ -510,16 +510,24 @@ def test_plan_compiler_kernel_selection(tn):
     the big one once on the CUDA cores, one thread per row where N <= 8, in
     row tiles staged through shared memory where K and N are 16..32 (stores
     straight from registers when T's lowest bits are row bits, staged
-    otherwise), one thread per row again past K = 32; a larger step is a
-    GEMM, on the tensor cores after a split pass per operand in the split
-    forms, on the CUDA cores in FP32."""
+    otherwise), one thread per row again past K = 32; in the split forms a
+    step of at least 2^16 rows with K and N of 16 or 32 whose rows' 7 lowest
+    bits are T's and C's lowest runs on the tensor cores, T split in shared
+    memory; a larger step is a GEMM, on the tensor cores after a split pass
+    per operand in the split forms, on the CUDA cores in FP32."""
     (op,) = _one_step(tn, 22, 3, 3)
     assert " small rows=4194304 K=8 N=8 " in op and "kernel=row" in op
     (op,) = _one_step(tn, 21, 4, 5)
+    assert "K=16 N=32" in op and "kernel=tensor cores, split in shared memory" in op
+    (op,) = _one_step(tn, 21, 4, 5, form="fp32")
     assert "K=16 N=32" in op and "kernel=tiled, direct C" in op
     (op,) = _one_step(tn, 21, 4, 5, k_low=True)
     assert "kernel=tiled, staged C" in op
     (op,) = _one_step(tn, 21, 5, 5)
+    assert "K=32 N=32" in op and "kernel=tensor cores" in op
+    (op,) = _one_step(tn, 15, 5, 5)  # fewer than 2^16 rows
+    assert "K=32 N=32" in op and "kernel=tiled" in op
+    (op,) = _one_step(tn, 21, 5, 5, form="fp32")
     assert "K=32 N=32" in op and "kernel=tiled" in op
     (op,) = _one_step(tn, 12, 6, 3)
     assert "K=64 N=8" in op and "kernel=row" in op
