@@ -1532,13 +1532,13 @@ cudaError_t launch_small_tc_t(const SmallTcParams &p, cudaStream_t s) {
         sm_count[dev].store(sms, std::memory_order_relaxed);
     }
     // two CTAs per SM where shared memory allows (one tile's split and
-    // products overlap the other's loads and stores)
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_tc_kernel<KIND, CB>, kSmallTcThreads,
-                                                      L::kBytes) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    const int grid = (int)std::min<int64_t>(p.tiles, (int64_t)sms * std::min(per_sm, 2));
+    // products overlap the other's loads and stores): 228 KB per SM, 1 KB
+    // of it reserved per CTA
+    e = cudaFuncSetAttribute((const void *)small_tc_kernel<KIND, CB>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    const int per_sm = (2 * (L::kBytes + 1024) <= 228 * 1024) ? 2 : 1;
+    const int grid = (int)std::min<int64_t>(p.tiles, (int64_t)sms * per_sm);
     small_tc_kernel<KIND, CB><<<grid, kSmallTcThreads, L::kBytes, s>>>(p);
     return cudaGetLastError();
 }
