@@ -147,9 +147,14 @@ def cfg3():
         m = make_batch_member(rs[i])
         t0 = time.time()
         amp = sv_native.amplitudes(m["circuit"], m["fixed_bits"], m["open_qubits"])
-        with open(path, "a") as f:
-            for j, a in enumerate(amp):
-                f.write(f"{i} {j} {float(a.real)!r} {float(a.imag)!r}\n")
+        # the whole file is rewritten and renamed into place, so a reader
+        # never sees a member that is only partly written
+        with open(path) as f:
+            text = f.read()
+        text += "".join(f"{i} {j} {float(a.real)!r} {float(a.imag)!r}\n" for j, a in enumerate(amp))
+        with open(path + ".tmp", "w") as f:
+            f.write(text)
+        os.replace(path + ".tmp", path)
         print(f"cfg3 member {i}: {m['circuit'].n_qubits} qubits ({time.time() - t0:.0f} s)", flush=True)
 
 
