@@ -1036,6 +1036,9 @@ def main():
                     help="plan option small_tasks: 0 tiny small steps as tasks of one launch, -1 one launch each")
     ap.add_argument("--small-tc-bits", type=int, default=0,
                     help="plan option small_tc_bits: small steps with K + N of at least this many bits on the tensor cores")
+    ap.add_argument("--tc-tma-store", type=int, default=0,
+                    help="plan option tc_tma_store: 0 (default) staged planar GEMM outputs stored by TMA where "
+                         "their layout allows, -1 from the epilogue warps")
     ap.add_argument("--autotune", action="store_true",
                     help="time each tensor-core GEMM's (chunk, read-out) candidates before use (tn_plan_autotune)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1060,6 +1063,8 @@ def main():
         PLAN_DEFAULTS["tc_chunk_bytes"] = args.tc_chunk
     if args.tc_flush:
         PLAN_DEFAULTS["tc_flush_bytes"] = args.tc_flush
+    if args.tc_tma_store:
+        PLAN_DEFAULTS["tc_tma_store"] = args.tc_tma_store
     if args.autotune:
         AUTOTUNE.append(True)
     if args.impl == "reference":

@@ -121,6 +121,13 @@ typedef struct {
      * into pieces in shared memory (each 128-row tile of T scaled by its own
      * power of two in FP16X3) with the form's products; -1: CUDA cores */
     int32_t small_tc;
+    /* split forms with 16-bit planes (BF16X3, FP16X3, FP16S, four products):
+     * 0 (default) lets a GEMM whose planar output would be staged through
+     * shared memory and stored by its epilogue warps write the planes to
+     * shared memory in the order of a destination box instead, stored by TMA
+     * (where the half tile's destination bits fit a five-dimensional box
+     * view whose rows are 128 bytes); -1: off */
+    int32_t tc_tma_store;
 } tn_plan_opts;
 
 /* Order search options (host-side planning). */

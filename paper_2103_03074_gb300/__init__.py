@@ -36,7 +36,7 @@ class PlanOpts(ctypes.Structure):
                 ("tc_chunk_bytes", _i32), ("tc_flush_bytes", _i32), ("tc_planar", _i32),
                 ("graph_branches", _i32),
                 ("small_tc_bits", _i32), ("small_tiled", _i32), ("tc_products", _i32), ("small_tasks", _i32),
-                ("small_tc", _i32)]
+                ("small_tc", _i32), ("tc_tma_store", _i32)]
 
 
 class SearchOpts(ctypes.Structure):
@@ -169,16 +169,17 @@ def search_opts(trials=256, seed=0x2103030740, log2_cap=-1, n_sliced=-1, threads
 
 def plan_opts(batch_log2=-1, mem_budget=0, profile=0, use_graph=0, tc_chunk_bytes=0, tc_flush_bytes=0,
               tc_planar=0, graph_branches=0, small_tc_bits=0, small_tiled=0, tc_products=0, small_tasks=0,
-              small_tc=0):
+              small_tc=0, tc_tma_store=0):
     """Plan options (tn_plan_opts).  tc_products: 4 (default) or 3, the real
     products per complex product of the split forms' tensor-core GEMMs (3:
     Gauss's 3M product).  small_tasks: 0 (default) runs tiny small steps as
     tasks of persistent launches, -1 one launch per step, > 0 the size bound
     (log2 elements) of a task.  small_tc: 0 (default) large small steps of
     the split forms on the tensor cores (T split in shared memory), -1 on the
-    CUDA cores."""
+    CUDA cores.  tc_tma_store: 0 (default) GEMMs store a staged planar output
+    by TMA where its layout allows, -1 from the epilogue warps."""
     return PlanOpts(batch_log2, mem_budget, profile, use_graph, tc_chunk_bytes, tc_flush_bytes, tc_planar,
-                    graph_branches, small_tc_bits, small_tiled, tc_products, small_tasks, small_tc)
+                    graph_branches, small_tc_bits, small_tiled, tc_products, small_tasks, small_tc, tc_tma_store)
 
 
 def marshal_circuit(circuit):

@@ -680,6 +680,7 @@ int64_t compile(tn_plan &P, int nb) {
         Op op;
         op.kind = OP_GEMM;
         std::memset(&op.tc, 0, sizeof op.tc);
+        op.tc.tma_out_ok = P.opts.tc_tma_store >= 0 ? 1 : 0;
         op.step = t;
         op.dep = nc.dep;
         GemmArgs &g = op.gemm;
@@ -2094,7 +2095,7 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
                 // the tile's six column bits are the destination's six lowest
                 bool cols_low = op.tc.out.ntb >= 6;
                 for (int k = 0; k < 6 && cols_low; k++) cols_low = op.tc.out.tb[k] == k && op.tc.out.tpos[k] == k;
-                char pl[160] = "";
+                char pl[320] = "";
                 if (op.tc.out.mode) {
                     // the half tile's bits in destination order (c: column of
                     // the tile, r: row) with their destination positions
@@ -2104,11 +2105,26 @@ std::string describe_ops(const tn_plan &P, bool with_roofline) {
                                  std::to_string(op.tc.out.tb[k] < 6 ? op.tc.out.tb[k] : op.tc.out.tb[k] - 6) + "@" +
                                  std::to_string(op.tc.out.tpos[k]);
                     const int direct = tc_planar_direct_run(op.tc.out);
+                    // TMA store: the box's extent per dimension (destination bits start@log2 box)
+                    TcTmaOut tm;
+                    std::string tma = " staged";
+                    // (eight-warp kernel only: tiles with more than one accumulator read-out)
+                    const int es = tc_plane_bytes(P.form);
+                    const int chunk = P.opts.tc_chunk_bytes == 64 ? 64 : 128;
+                    int flush = P.opts.tc_flush_bytes > 0 ? P.opts.tc_flush_bytes : tc_default_flush_bytes(P.form);
+                    if (flush < chunk) flush = chunk;
+                    const bool one_readout = (op.gemm.K * es + chunk - 1) / chunk <= flush / chunk;
+                    if (!direct && !one_readout && op.tc.tma_out_ok && op.tc.products != 3 &&
+                        tc_planar_tma_fits(op.tc.out, &tm)) {
+                        tma = " tma box=";
+                        for (int i = 0; i < tm.nd; i++)
+                            tma += (i ? "," : "") + std::to_string(tm.start[i]) + "@" + std::to_string(tm.box[i]);
+                    }
                     std::snprintf(pl, sizeof pl, " run_bits=%d%s%s%s tile_bits=%s", run,
                                   (op.tc.out.ntb >= 7 && op.tc.out.tpos[0] == 0 && op.tc.out.tpos[1] == 1) ? " quad"
                                                                                                             : "",
                                   cols_low ? " cols_low" : "",
-                                  direct ? (" direct=" + std::to_string(1 << direct)).c_str() : " staged",
+                                  direct ? (" direct=" + std::to_string(1 << direct)).c_str() : tma.c_str(),
                                   tbits.c_str());
                 }
                 std::snprintf(line, sizeof line,

@@ -112,6 +112,9 @@ struct Ring {
     static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 constexpr uint32_t kSpinLimit = 1u << 24;
+// planar output by TMA: one plane's half tile (64 x 64 16-bit pieces) per
+// 8 KB of the epilogue's staging area
+constexpr int kTmaPlaneBytes = 8192;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -210,6 +213,27 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t *w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
+}
+
+// bulk tensor store of a shared-memory box (bulk-group completion)
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, uint32_t src, int c0, int c1, int c2, int c3,
+                                             int c4) {
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the committed stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// the committed stores have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the bulk copies
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -250,6 +274,7 @@ struct GemmTcParams {
     // lane stores straight from its registers (0: staged through shared
     // memory)
     int direct_run;
+    TcTmaOut tma;  // tma.on: planar output written to shared memory in box order and stored by TMA
 };
 
 // tile t -> (n tile, m tile, batch h, K part); N tiles vary fastest
@@ -535,7 +560,7 @@ __device__ __forceinline__ void planar_write(const TcPlanarOut &o, uint64_t base
 template <int KIND, int CB, bool M3, int EW>
 __global__ void __launch_bounds__(ep_threads(EW), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   const GemmTcParams p) {
+                   const __grid_constant__ CUtensorMap mapC, const GemmTcParams p) {
     constexpr int kFlushWarps = EW;
     constexpr int kCW = TN / (EW / 4);  // complex columns per epilogue warp
     constexpr int NP = M3 ? 6 : (kind_split(KIND) ? 4 : 2);
@@ -543,6 +568,9 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
     constexpr int kAPlane = R::kAPlane, kBPlane = R::kBPlane;
     constexpr int kStageBytes = R::kStageBytes, kStages = R::kStages;
     const int F = p.flush_chunks;
+    // the TMA-stored planar output reuses the staging area: four planes of
+    // 8 KB, 1024-byte aligned (128-byte swizzle)
+    static_assert(4 * kTmaPlaneBytes <= R::kOutBytes && (kStages * kStageBytes) % 1024 == 0, "TMA staging");
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -848,6 +876,79 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                                                       scatter8((uint64_t)tc.m0, p.out.mpos, p.out.nM) |
                                                       scatter8((uint64_t)tc.n0, p.out.npos, p.out.nN))
                                                    : 0;
+            constexpr int kMode = planar_mode_of(KIND, M3);
+            if constexpr (!mode_word(kMode) && !mode_3m(kMode) && EW == 8) {
+                if (p.tma.on) {
+                    // planar output by TMA (full tiles, 16-bit planes): per
+                    // half tile, the writing lanes put their rows' pieces in
+                    // shared memory in the order of the destination box
+                    // (128-byte rows, 128-byte swizzle: the 16-byte chunk
+                    // index is XORed with the row index mod 8), then one
+                    // thread stores each plane's box with one bulk tensor
+                    // copy.  Every epilogue warp reaches both barriers of
+                    // each half.
+                    using PS = PlaneShape<kMode>;
+                    const bool issuer = fw == 0 && lane == 0;
+                    const int r = (lg & 1) * 32 + lane;  // row within the half tile
+                    uint32_t erow = 0;
+#pragma unroll
+                    for (int i = 0; i < 6; i++) erow |= (uint32_t)((r >> i) & 1) << p.tma.boxbit[6 + i];
+                    const uint32_t sbase = smem_u32(stage_out);
+#pragma unroll
+                    for (int hp = 0; hp < 2; hp++) {
+                        if (issuer) bulk_wait_read();  // the previous boxes have left shared memory
+                        asm volatile("bar.sync 1, %0;" ::"n"(32 * kFlushWarps) : "memory");
+                        if ((lg >> 1) == hp && ok) {
+#pragma unroll
+                            for (int u = 0; u < kCW / 8; u++) {
+                                // eight columns c0..c2 = 0..7: 16 consecutive bytes of the box
+                                const int col0 = cq * kCW + 8 * u;
+                                uint32_t e = erow;
+#pragma unroll
+                                for (int i = 3; i < 6; i++) e |= (uint32_t)((col0 >> i) & 1) << p.tma.boxbit[i];
+                                const uint32_t o = 2u * e;
+                                const uint32_t sw = o ^ (((o >> 7) & 7u) << 4);
+#pragma unroll
+                                for (int c = 0; c < PS::kValues; c++) {
+                                    uint32_t hi[4], lo[4];
+#pragma unroll
+                                    for (int w = 0; w < 4; w++) {
+                                        const int j = 8 * u + 2 * w;
+                                        pieces_pair16<kMode>(c == 0 ? acc_re[j] : acc_im[j],
+                                                             c == 0 ? acc_re[j + 1] : acc_im[j + 1], hi[w], lo[w]);
+                                    }
+                                    st_shared_v4(sbase + c * kTmaPlaneBytes + sw, hi);
+                                    if constexpr (PS::kPieces == 2)
+                                        st_shared_v4(sbase + (PS::kValues + c) * kTmaPlaneBytes + sw, lo);
+                                }
+                            }
+                            fence_proxy_async();
+                        }
+                        asm volatile("bar.sync 1, %0;" ::"n"(32 * kFlushWarps) : "memory");
+                        if (issuer && ok) {
+                            // box coordinates: the half tile's destination
+                            // base cut into the dimensions' bit fields (its
+                            // tile bits are zero: every coordinate is a
+                            // whole box, the innermost one 0)
+                            const uint64_t db = hp ? (pbase | (1ull << p.out.mpos[6])) : pbase;
+                            int crd[5];
+#pragma unroll
+                            for (int i = 0; i < 5; i++) {
+                                const uint64_t f = i < p.tma.nd ? (db >> p.tma.start[i]) : 0;
+                                crd[i] = (int)(i < p.tma.nd - 1 ? (f & ((1ull << p.tma.bits[i]) - 1)) : f);
+                            }
+                            for (int q = 0; q < p.tma.np; q++) {
+                                int cq5[5] = {crd[0], crd[1], crd[2], crd[3], crd[4]};
+                                cq5[p.tma.nd - 1] += (int)(q * p.tma.plane_step);
+                                tma_store_5d(&mapC, sbase + q * kTmaPlaneBytes, cq5[0], cq5[1], cq5[2], cq5[3],
+                                             cq5[4]);
+                            }
+                            bulk_commit();
+                        }
+                    }
+                    continue;
+                }
+            }
             if (p.direct_run > 0) {
                 // full tiles only (the launcher checks M and N): every lane
                 // stores its own row's columns, no staging
@@ -893,6 +994,8 @@ __global__ void __launch_bounds__(ep_threads(EW), 1)
                 asm volatile("bar.sync 1, %0;" ::"n"(32 * kFlushWarps) : "memory");
             }
         }
+        // the planes' last boxes are written before the CTA exits
+        if (p.tma.on && fw == 0 && lane == 0) bulk_wait_all();
         if (p.max_slot && ok) {
             // one atomic per warp and launch; non-negative floats order like
             // their bit patterns
@@ -1287,7 +1390,89 @@ bool encode_planes(CUtensorMap *map, void *planes, int64_t H, int64_t rows, int6
     return r == CUDA_SUCCESS;
 }
 
+// The box view of a planar output for TMA stores (TcTmaOut), or false when
+// the layout does not fit one: 16-bit planes of a 4-product form (hi/lo or
+// one scaled piece), full tiles, the half tile's columns c0..c2 at
+// destination bits 0..2 (a lane's eight columns are 16 consecutive bytes)
+// and bits 0..5 all tile bits (128-byte box rows), at most five dimensions.
+bool plan_tma_out(const TcPlanarOut &o, TcTmaOut &t) {
+    std::memset(&t, 0, sizeof t);
+    if (o.mode != 1 && o.mode != 3 && o.mode != 4) return false;
+    if (o.nN < 6 || o.nM < 7 || o.ntb != 12) return false;
+    if (o.plane_stride <= 0 || (o.plane_stride & (o.plane_stride - 1)) != 0) return false;
+    const int r = __builtin_ctzll((uint64_t)o.plane_stride);
+    for (int k = 0; k < 6; k++)
+        if (o.tpos[k] != k) return false;
+    for (int k = 0; k < 3; k++)
+        if (o.tb[k] != k) return false;
+    t.np = o.mode == 3 ? 2 : 4;
+    t.start[0] = 0;
+    t.bits[0] = 6;
+    t.box[0] = 6;
+    for (int k = 0; k < 6; k++) t.boxbit[o.tb[k]] = (int8_t)k;
+    int nd = 1, bb = 6, pos = 6;
+    for (int k = 6; k < 12;) {
+        const int p0 = o.tpos[k];
+        int len = 1;
+        while (k + len < 12 && o.tpos[k + len] == p0 + len) len++;
+        if (p0 > pos) {  // a gap of non-tile bits: box 1
+            if (nd == 5) return false;
+            t.start[nd] = (int8_t)pos;
+            t.bits[nd] = (int8_t)(p0 - pos);
+            t.box[nd] = 0;
+            nd++;
+        }
+        if (nd == 5) return false;
+        t.start[nd] = (int8_t)p0;
+        t.bits[nd] = (int8_t)len;
+        t.box[nd] = (int8_t)len;
+        for (int j = 0; j < len; j++) t.boxbit[o.tb[k + j]] = (int8_t)(bb + j);
+        bb += len;
+        nd++;
+        pos = p0 + len;
+        k += len;
+    }
+    if (pos > r) return false;
+    // the last dimension runs to the top of a plane; the planes follow it
+    t.bits[nd - 1] = (int8_t)(r - t.start[nd - 1]);
+    t.plane_step = (int64_t)1 << t.bits[nd - 1];
+    t.nd = nd;
+    t.on = 1;
+    return true;
+}
+
+bool encode_tma_out(CUtensorMap *map, const TcPlanarOut &o, const TcTmaOut &t) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    const int r = __builtin_ctzll((uint64_t)o.plane_stride);
+    for (int i = 0; i < 5; i++) {
+        if (i < t.nd) {
+            dims[i] = (cuuint64_t)1 << t.bits[i];
+            if (i == t.nd - 1) dims[i] *= (cuuint64_t)t.np;
+            box[i] = 1u << t.box[i];
+        } else {
+            dims[i] = 1;  // unused dimensions: extent 1 past the planes
+            box[i] = 1;
+        }
+        // byte strides (dimension 0 is contiguous)
+        if (i > 0) strides[i - 1] = i < t.nd ? ((cuuint64_t)2 << t.start[i]) : ((cuuint64_t)t.np * 2 << r);
+    }
+    CUresult res = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, o.planes, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return res == CUDA_SUCCESS;
+}
+
 }  // namespace
+
+bool tc_planar_tma_fits(const TcPlanarOut &o, TcTmaOut *out) {
+    TcTmaOut t;
+    const bool fits = tc_planar_direct_run(o) == 0 && plan_tma_out(o, t);
+    if (out) *out = t;
+    return fits;
+}
 
 int tc_planar_direct_run(const TcPlanarOut &o) {
     // Full 128 x 64 tiles whose destination starts with 16 bytes of one row
@@ -1379,6 +1564,17 @@ bool tc_prepare(TcGemm &g) {
     if (!encode_planes(reinterpret_cast<CUtensorMap *>(g.mapB), g.planesB, g.a.H, g.a.N, g.a.K, es, TN, cb, np, dt,
                        klo))
         return false;
+    // planar output stored by TMA where the layout fits a box view and the
+    // epilogue would otherwise stage it (the direct register stores stay)
+    std::memset(g.mapC, 0, sizeof g.mapC);
+    TcTmaOut t;
+    if (g.tma_out_ok && g.products == 4 && g.ksplit <= 1 && g.out.planes && tc_planar_direct_run(g.out) == 0 &&
+        plan_tma_out(g.out, t)) {
+        if (!encode_tma_out(reinterpret_cast<CUtensorMap *>(g.mapC), g.out, t)) return false;
+        g.out_tma = t;
+    } else {
+        std::memset(&g.out_tma, 0, sizeof g.out_tma);
+    }
     return true;
 }
 
@@ -1389,15 +1585,19 @@ cudaError_t launch_ew(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStr
     if (e != cudaSuccess) return e;
     const CUtensorMap &mA = *reinterpret_cast<const CUtensorMap *>(g.mapA);
     const CUtensorMap &mB = *reinterpret_cast<const CUtensorMap *>(g.mapB);
-    tc_gemm_kernel<KIND, CB, M3, EW><<<grid, ep_threads(EW), Ring<CB, NP>::kSmem, s>>>(mA, mB, p);
+    const CUtensorMap &mC = *reinterpret_cast<const CUtensorMap *>(g.mapC);
+    tc_gemm_kernel<KIND, CB, M3, EW><<<grid, ep_threads(EW), Ring<CB, NP>::kSmem, s>>>(mA, mB, mC, p);
     return cudaGetLastError();
 }
 
 // sixteen epilogue warps when a tile has one accumulator read-out (short K:
 // the epilogue sets the GEMM's time), else eight
 template <int KIND, int CB, bool M3 = false>
-cudaError_t launch_variant(const TcGemm &g, const GemmTcParams &p, dim3 grid, cudaStream_t s) {
+cudaError_t launch_variant(const TcGemm &g, GemmTcParams p, dim3 grid, cudaStream_t s) {
     const bool one_readout = p.part_len <= p.flush_chunks;
+    // the TMA-stored planar output is compiled into the eight-warp kernel
+    // only (the sixteen-warp one has 96 registers a thread): staged there
+    if (one_readout) p.tma.on = 0;
     return one_readout ? launch_ew<KIND, CB, M3, 16>(g, p, grid, s) : launch_ew<KIND, CB, M3, 8>(g, p, grid, s);
 }
 
@@ -1452,6 +1652,8 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
     }
     if ((g.form == TN_FP16S || g.form == TN_FP16X3) && !g.scales) return cudaErrorInvalidValue;
     p.direct_run = tc_planar_direct_run(p.out);
+    p.tma = g.out_tma;
+    if (p.tma.on && (p.out.mode == 0 || p.ksplit > 1 || g.out.planes == nullptr)) return cudaErrorInvalidValue;
     const int64_t gm = (g.a.M + TM - 1) / TM, gn = (g.a.N + TN - 1) / TN;
     if (gm > INT32_MAX || gn > INT32_MAX) return cudaErrorInvalidConfiguration;
     p.gm = (int)gm;

@@ -25,6 +25,26 @@ struct TcPlanarOut {
     int8_t tpos[12];        //   their destination positions
 };
 
+// Planar output stored by TMA from shared memory (16-bit planes: bf16 or
+// fp16 hi/lo, or scaled fp16): the epilogue writes the half tile's 4,096
+// elements of each plane to shared memory in the order of one box of a
+// five-dimensional view of the destination, then one bulk tensor store per
+// plane writes them.  Dimension 0 = destination bits 0..5 (the half tile's
+// 64 lowest destination elements, 128 bytes); each further run of
+// consecutive tile-bit positions is a dimension whose box spans the run, each
+// gap between runs a dimension with a box of 1; the last dimension runs to
+// the top of the planes (plane q at coordinate q * plane_step).
+struct TcTmaOut {
+    int on;              // 1: planes stored by TMA (tc_prepare decides and encodes mapC)
+    int np;              // planes
+    int nd;              // dimensions in use (at most 5; the rest have extent 1)
+    int8_t start[5];     // destination bit where dimension i starts
+    int8_t bits[5];      // log2 of its extent (the last: to the top of a plane)
+    int8_t box[5];       // log2 of its box
+    int8_t boxbit[12];   // box-order bit of tile bit b (0..5: column c_b, 6..11: row r_(b-6))
+    int64_t plane_step;  // last-dimension coordinate distance between planes
+};
+
 // One tensor-core GEMM: the GemmArgs contract (C = [H][M][N] contiguous) plus
 // the split planes of A (rows = M) and B (rows = N), planes[q][h][row][k], and
 // their TMA descriptors.
@@ -48,14 +68,20 @@ struct TcGemm {
     // stored for all rows before the next: a TMA box of 128 rows reads one
     // contiguous block, whatever K is)
     int k_low_bits;
+    int tma_out_ok;    // 1: a planar output may be stored by TMA (tc_prepare decides from its layout)
+    TcTmaOut out_tma;  // set by tc_prepare from `out` (out_tma.on 0: stores from the epilogue warps)
     alignas(64) unsigned char mapA[128];
     alignas(64) unsigned char mapB[128];
+    alignas(64) unsigned char mapC[128];
 };
 
 // log2 of the runs a planar epilogue stores straight from registers (the
 // destination's lowest bits are the tile's lowest column bits, full tiles),
 // or 0 when it stages the tile through shared memory
 int tc_planar_direct_run(const TcPlanarOut &o);
+// true if a planar output that the epilogue would stage fits the box view of
+// a TMA store (TcTmaOut; 16-bit planes of a four-product form)
+bool tc_planar_tma_fits(const TcPlanarOut &o, TcTmaOut *out = nullptr);
 
 // true if `form` has a tensor-core GEMM compiled into this library (and the
 // driver entry point for TMA descriptors is reachable)

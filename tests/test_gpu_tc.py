@@ -312,3 +312,42 @@ def test_single_gemm_3m_64_byte_chunks(tn, form):
     exact = A.astype(np.complex128) @ B.astype(np.complex128)
     assert rel(got, exact) < (3e-5 if form == "bf16x3" else 3e-6)
     assert rel(got, emulate_split_3m(A, B, form)) < TOL_3M_EMU
+
+
+@pytest.mark.parametrize("form", ["fp16x3", "bf16x3", "fp16s"])
+def test_planar_tma_store(tn, form):
+    """A GEMM whose output is the next GEMM's 16-bit planes, with several
+    accumulator read-outs per tile (K = 2^9), writes the planes to shared
+    memory in the order of a destination box and stores them by TMA ("tma
+    box=" in its plan line).  The two-GEMM product (A B) D against the same
+    plan with the planes stored by the epilogue warps (tc_tma_store -1) --
+    the same pieces in the same places, so the results are identical -- and
+    against a separate split pass (tc_planar -1) and the exact product, with
+    the bounds of the planar-epilogue parity test."""
+    import torch
+    m, k, n, p = 14, 9, 9, 4
+    ml, kl, nl, pl = (list(range(b, b + c)) for b, c in ((0, m), (100, k), (200, n), (400, p)))
+    A = rand_c64(91, (1 << m, 1 << k))
+    B = rand_c64(92, (1 << k, 1 << n))
+    D = rand_c64(93, (1 << n, 1 << p))
+    labels = [ml + kl, kl + nl, nl + pl]
+    tensors = [A.reshape((2,) * (m + k)), B.reshape((2,) * (k + n)), D.reshape((2,) * (n + p))]
+    got = {}
+    for key, opts in (("tma", dict()), ("staged", dict(tc_tma_store=-1)), ("split", dict(tc_planar=-1))):
+        plan = tn.Plan(labels, tensors, ml + pl, [], [(0, 1), (3, 2)], form=form, opts=tn.plan_opts(**opts))
+        first = [l for l in plan.describe().splitlines() if "gemm" in l][0]
+        assert ("tma box=" in first) == (key == "tma"), first
+        amp = torch.zeros(2 << (m + p), dtype=torch.float64, device="cuda")
+        plan.contract(0, 1, amp)
+        torch.cuda.synchronize()
+        plan.close()
+        g = amp.cpu().numpy()
+        got[key] = g[0::2] + 1j * g[1::2]
+    exact = ((A.astype(np.complex128) @ B.astype(np.complex128)) @ D.astype(np.complex128)).reshape(-1)
+    agree = {"fp16x3": 5e-6, "fp16s": 2e-3}.get(form, 1e-6)
+    bound = {"bf16x3": 1e-4, "fp16s": 2e-3}.get(form, 1e-5)
+    print(f"{form}: tma vs staged {rel(got['tma'], got['staged']):.2e}, vs split pass "
+          f"{rel(got['tma'], got['split']):.2e}, vs exact {rel(got['tma'], exact):.2e}")
+    assert rel(got["tma"], got["staged"]) < 1e-7
+    assert rel(got["tma"], got["split"]) < agree
+    assert rel(got["tma"], exact) < bound
