@@ -562,6 +562,9 @@ def profile_roofline(tn, torch, L, T, O, sliced, tree, form, rng, amp, stream, p
     # over their measured time: the class mixes tensor-bound and HBM-bound
     # launches, so this is its meaningful fraction
     roof["roofline_time_frac"] = d["t_roof"] / d["ms"] if d["ms"] else None
+    # the same over every launch of the step (measured peaks), the step's
+    # kernel time against its per-launch roofline time
+    roof["step_roofline_time_frac"] = (sum(v["t_roof"] for v in by_kind.values()) / total_ms) if total_ms else None
     share = {k: v["ms"] / total_ms for k, v in by_kind.items()}
     return roof, share
 

@@ -116,7 +116,7 @@ typedef struct {
      * of one kernel launch each; -1: off */
     int32_t small_tasks;
     /* split forms (TF32X3, FP16X3, BF16X3): 0 (default) runs a large small
-     * step (K and N of 16 or 32 values, at least 2^16 rows, no batch labels,
+     * step (K of 16 or 32 values, N of 8, 16 or 32, at least 2^16 rows, no batch labels,
      * its rows' 7 lowest bits lowest in T and C) on the tensor cores, T split
      * into pieces in shared memory (each 128-row tile of T scaled by its own
      * power of two in FP16X3) with the form's products; -1: CUDA cores */

@@ -1308,10 +1308,13 @@ __global__ void __launch_bounds__(kSmallTcThreads, 2) small_tc_kernel(const Smal
         if (ok) {
             phase ^= 1;
             // this warp: rows 32 lg .., columns n in [ch * N / 2, + N / 2)
+            // (N = 8: all eight columns in the warps of ch 0)
             const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16);
             const uint64_t cbase = small_tc_insert((uint64_t)tile << 7, p.cins, p.n_cins) + lg * 32 + lane;
             const float sc = KIND == kFP16X3 ? __int_as_float((127 + eT + eS) << 23) : 1.f;
-            for (int n0 = ch * (NS / 2); n0 < (ch + 1) * (NS / 2); n0 += 8) {
+            const int n_lo = NS >= 16 ? ch * (NS / 2) : (ch ? NS : 0);
+            const int n_hi = NS >= 16 ? (ch + 1) * (NS / 2) : NS;
+            for (int n0 = n_lo; n0 < n_hi; n0 += 8) {
                 uint32_t pr[8], pi[8], qr[8], qi[8];
                 tmem_ld8(base + n0, pr);           // P left:  A_re S_re
                 tmem_ld8(base + NS + n0, pi);      // P right: A_re S_im
@@ -1704,10 +1707,11 @@ cudaError_t launch_gemm_tc(const TcGemm &g, cudaStream_t s) {
 }
 
 bool small_tc_suitable(const SmallArgs &a, tn_form form) {
-    // split forms with 22+ significant bits and bf16x3; K and N of 16 or 32;
-    // no batch bits; whole 128-row tiles whose T and C runs are 128 rows
+    // split forms with 22+ significant bits and bf16x3; K of 16 or 32, N of
+    // 8, 16 or 32; no batch bits; whole 128-row tiles whose T and C runs are
+    // 128 rows
     if (form != TN_FP16X3 && form != TN_TF32X3 && form != TN_BF16X3) return false;
-    if (a.nH != 0 || a.nK < 4 || a.nK > 5 || a.nN < 4 || a.nN > 5 || a.tiled == 3) return false;
+    if (a.nH != 0 || a.nK < 4 || a.nK > 5 || a.nN < 3 || a.nN > 5 || a.tiled == 3) return false;
     if (a.rows < (1 << 16) || (a.rows & (a.rows - 1)) != 0) return false;
     for (int j = 0; j < a.nK; j++)
         if (a.kposT[j] < 7) return false;

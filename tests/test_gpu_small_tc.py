@@ -96,7 +96,7 @@ def run(tn, labels, data, out, tree, form, **opts):
 
 @pytest.mark.parametrize("form", ["fp16x3", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("kpos,n_bits", [((7, 9, 12, 15), 5), ((8, 15, 17, 19, 20), 5), ((10, 11, 12, 13), 4),
-                                         ((7, 8, 9, 10, 16), 4)])
+                                         ((7, 8, 9, 10, 16), 4), ((8, 15, 17, 19, 20), 3), ((9, 10, 14, 16), 3)])
 def test_small_step_on_tensor_cores(tn, form, kpos, n_bits):
     row_bits = 17
     labels, data, out = step_network(row_bits, kpos, n_bits, seed=len(kpos) * 10 + n_bits)
