@@ -736,3 +736,30 @@ def test_expected_time_objective(tn):
     assert len(oq) == 8 and np.isfinite(cost)
     with pytest.raises(tn.TNError):
         tn.find_order(L, O, tn.search_opts(trials=8, n_sliced=4, objective=3))
+
+
+def test_plan_compiler_tma_store_box_views(tn):
+    """The box view that a TMA-stored planar epilogue writes through (host
+    side of tc_tma_store, shown in the plan line as start@log2-box per
+    dimension): a GEMM whose half tile is the destination's 4,096 lowest
+    elements (c0..c5, then r0..r5) gets two dimensions; the bench tree's
+    largest GEMM (c0..c4 r0 at bits 0..5, c5 at 7, r1..r5 at 16..20) gets
+    five, gaps as boxes of one.  TF32 planes, single read-out tiles (the
+    sixteen-warp kernel) and tc_tma_store -1 keep the staged store."""
+    m, n, p = 14, 9, 4
+    ml, nl, pl = list(range(m)), list(range(200, 200 + n)), list(range(400, 400 + p))
+    for k, form, opts, want in [(9, "fp16x3", None, "tma box=0@6,6@6"), (9, "bf16x3", None, "tma box=0@6,6@6"),
+                                (9, "fp16s", None, "tma box=0@6,6@6"), (7, "fp16x3", None, "staged"),
+                                (9, "tf32x3", None, "staged"), (9, "fp16x3", tn.plan_opts(tc_tma_store=-1), "staged")]:
+        kl = list(range(100, 100 + k))
+        ops = tn.describe_tree([ml + kl, kl + nl, nl + pl], ml + pl, [], [(0, 1), (3, 2)], form=form, opts=opts)
+        first = [o for o in ops.splitlines() if " gemm " in o][0]
+        assert "out=planes" in first and f" {want} " in first, (form, k, first)
+    import bench
+    from paper_2103_03074_gb300.trees import make_trees
+    cfg = bench.workload("syc53_m14")
+    L, T, O = tn.circuit_network(cfg["circuit"], cfg["fixed_bits"], cfg["open_qubits"])
+    tree, sliced, _ = make_trees.load("syc53_m14", L, O)
+    ops = tn.describe_tree(L, O, sliced, tree, form="fp16x3")
+    big = [o for o in ops.splitlines() if " gemm " in o and "M=4194304 N=256 K=256" in o]
+    assert len(big) == 1 and "tma box=0@6,6@0,7@1,8@0,16@5 " in big[0], big
