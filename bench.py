@@ -525,6 +525,13 @@ def profile_roofline(tn, torch, L, T, O, sliced, tree, form, rng, amp, stream, p
     if dump:
         with open(f"{dump}.{tag}{form}.json", "w") as f:
             json.dump({"steps": steps, "rows": rows}, f)
+    return summarise_profile(rows, form, pk, steps)
+
+
+def summarise_profile(rows, form, pk, steps):
+    """(roofline entry of the kernel class with the largest share, share of
+    every class) from step-timing rows (kind, ms, launches, macs and bytes
+    per launch) recorded over `steps` steps."""
     by_kind = {}
     for r in rows:
         d = by_kind.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "macs": 0.0, "bytes": 0.0, "t_roof": 0.0})

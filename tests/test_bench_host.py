@@ -87,3 +87,32 @@ def test_reference_arm_loads_no_product_code():
     import json
     line = json.loads(lines[-2])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "slices/s"
+
+
+def test_profile_summary_arithmetic(bench):
+    """The bench line's roofline entry from step-timing rows, against numbers
+    worked out by hand: over 2 recorded steps, a tensor-core GEMM class (two
+    launches per step of 2^40 complex MACs and 2^33 bytes, 2 ms each) and a
+    small step (one launch per step, 2^32 bytes, 1 ms).  Peaks: HBM 8192 GB/s,
+    bf16 2000 TFLOP/s, FP32 ALU from 2070 MHz."""
+    pk = dict(hbm_gbs=8192.0, bf16_tflops=2000.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0,
+              source="test")
+    rows = [dict(kind="gemm", ms=8.0, launches=4, macs=2.0 ** 40, bytes=2.0 ** 33),
+            dict(kind="small", ms=2.0, launches=2, macs=2.0 ** 26, bytes=2.0 ** 32)]
+    roof, share = bench.summarise_profile(rows, "fp16x3", pk, steps=2)
+    # the GEMM class dominates: 8 of 10 ms
+    assert share == {"gemm": 0.8, "small": 0.2}
+    assert roof["bound"] == "tensor" and roof["peak"] == 2000.0
+    # 24 flops per complex MAC, 2^40 MACs per launch, 2 ms per launch
+    achieved = 24.0 * 2.0 ** 40 / 2e-3 / 1e12
+    assert abs(roof["achieved"] - achieved) < 1e-9 * achieved
+    assert abs(roof["frac"] - achieved / 2000.0) < 1e-12
+    assert roof["launches_per_step"] == 2.0 and roof["share_of_step"] == 0.8
+    # per launch: tensor time 24 * 2^40 / 2e15 s = 13.19 ms > HBM time
+    # 2^33 / 8.192e12 s = 1.05 ms, so the class's roofline time is 4 x 13.19 ms
+    t_gemm = 24.0 * 2.0 ** 40 / 2e15 * 1e3
+    assert abs(roof["roofline_time_frac"] - 4 * t_gemm / 8.0) < 1e-9
+    # the small step: HBM 2^32 / 8.192e12 s = 0.524 ms against FP32 ALU
+    # 8 * 2^26 / (152 * 128 * 2 * 2.07e9) s = 0.0068 ms
+    t_small = 2.0 ** 32 / 8.192e12 * 1e3
+    assert abs(roof["step_roofline_time_frac"] - (4 * t_gemm + 2 * t_small) / 10.0) < 1e-9
