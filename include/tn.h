@@ -126,7 +126,8 @@ typedef struct {
      * shared memory and stored by its epilogue warps write the planes to
      * shared memory in the order of a destination box instead, stored by TMA
      * (where the half tile's destination bits fit a five-dimensional box
-     * view whose rows are 128 bytes); -1: off */
+     * view whose rows are 128 bytes, in GEMMs whose tiles have more than one
+     * accumulator read-out); -1: off */
     int32_t tc_tma_store;
 } tn_plan_opts;
 
