@@ -511,12 +511,19 @@ def test_plan_compiler_kernel_selection(tn):
     row tiles staged through shared memory where K and N are 16..32 (stores
     straight from registers when T's lowest bits are row bits, staged
     otherwise), one thread per row again past K = 32; in the split forms a
-    step of at least 2^16 rows with K and N of 16 or 32 whose rows' 7 lowest
-    bits are T's and C's lowest runs on the tensor cores, T split in shared
-    memory; a larger step is a GEMM, on the tensor cores after a split pass
-    per operand in the split forms, on the CUDA cores in FP32."""
+    step of at least 2^16 rows with K of 16 or 32 and N of 8, 16 or 32 whose
+    rows' 7 lowest bits are T's and C's lowest runs on the tensor cores, T
+    split in shared memory; a larger step is a GEMM, on the tensor cores
+    after a split pass per operand in the split forms, on the CUDA cores in
+    FP32."""
     (op,) = _one_step(tn, 22, 3, 3)
     assert " small rows=4194304 K=8 N=8 " in op and "kernel=row" in op
+    (op,) = _one_step(tn, 21, 5, 3)
+    assert "K=32 N=8" in op and "kernel=tensor cores, split in shared memory" in op
+    (op,) = _one_step(tn, 21, 5, 2)
+    assert "K=32 N=4" in op and "kernel=row" in op
+    (op,) = _one_step(tn, 21, 5, 3, form="fp32")
+    assert "K=32 N=8" in op and "kernel=row" in op
     (op,) = _one_step(tn, 21, 4, 5)
     assert "K=16 N=32" in op and "kernel=tensor cores, split in shared memory" in op
     (op,) = _one_step(tn, 21, 4, 5, form="fp32")
