@@ -116,3 +116,24 @@ def test_profile_summary_arithmetic(bench):
     # 8 * 2^26 / (152 * 128 * 2 * 2.07e9) s = 0.0068 ms
     t_small = 2.0 ** 32 / 8.192e12 * 1e3
     assert abs(roof["step_roofline_time_frac"] - (4 * t_gemm + 2 * t_small) / 10.0) < 1e-9
+
+
+@pytest.mark.parametrize("form,flops_per_mac,peak_ratio", [("tf32x3", 24.0, 0.5), ("fp16x3_3m", 18.0, 1.0),
+                                                           ("fp16s", 8.0, 1.0)])
+def test_profile_summary_per_form(bench, form, flops_per_mac, peak_ratio):
+    """The tensor-core class is priced per form: 24 tensor flops per complex
+    MAC for the four-product hi/lo forms, 18 for Gauss's 3M product, 8 for
+    the single-piece FP16S; TF32 against half the bf16 peak.  The FP32 form's
+    GEMM class is priced against the derived FP32 ALU peak (8 flops per
+    complex MAC)."""
+    pk = dict(hbm_gbs=8192.0, bf16_tflops=2000.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0,
+              source="test")
+    rows = [dict(kind="gemm", ms=4.0, launches=2, macs=2.0 ** 38, bytes=2.0 ** 30)]
+    roof, _ = bench.summarise_profile(rows, form, pk, steps=1)
+    achieved = flops_per_mac * 2.0 ** 38 / 2e-3 / 1e12
+    assert roof["bound"] == "tensor" and abs(roof["peak"] - 2000.0 * peak_ratio) < 1e-9
+    assert abs(roof["achieved"] - achieved) < 1e-9 * achieved
+    roof, _ = bench.summarise_profile(rows, "fp32", pk, steps=1)
+    alu = 152 * 128 * 2 * 2.07e9 / 1e12
+    assert roof["bound"] == "alu" and abs(roof["peak"] - alu) < 1e-9 * alu
+    assert abs(roof["achieved"] - 8.0 * 2.0 ** 38 / 2e-3 / 1e12) < 1e-6
